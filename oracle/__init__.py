@@ -1,0 +1,294 @@
+"""FP64 CPU oracle for Boundary Value Caching (Miller et al., SIGGRAPH 2023).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  The
+product (``paper_2302_11825_gb300``) never imports, loads or calls it, and it
+imports nothing from the product: the two sides meet only through the seeded
+input generators in ``paper_2302_11825_gb300.workloads``.
+
+The arithmetic lives in ``bvc_oracle.c`` (plain C, double precision); this
+module compiles it with gcc on first use and wraps it with ctypes.  Each
+function cites the passage of the paper it follows.
+
+Parity status: every function here is pinned by tests in ``tests/`` against
+closed forms, a deterministic Green's-identity quadrature, brute force, the
+mean-value property or published known answers, except as noted:
+  (none: ``sample_source2d`` is pinned by the exact polygon area and the
+  closed-form Newtonian potential of a disk, see tests/test_oracle_sampling.py)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bvc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+TAG_WALK = 0
+TAG_BOUNDARY = 1
+TAG_SOURCE = 2
+TAG_POINTWISE = 3
+
+
+def build(force: bool = False) -> str:
+    """Compile ``bvc_oracle.c`` into ``oracle/_build/liboracle.so``."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            i64, i32, u64, u32, f64 = C.c_int64, C.c_int32, C.c_uint64, C.c_uint32, C.c_double
+            sig = {
+                "orc_philox4x32_10": (None, [P, P, P]),
+                "orc_u01": (f64, [u32]),
+                "orc_fn_eval": (f64, [P, C.c_int, P]),
+                "orc_green": (None, [C.c_int, P, P, P, P]),
+                "orc_closest_brute64": (None, [C.c_int, P, i64, P, i64, P, i64, P, P, P]),
+                "orc_closest_brute32": (None, [C.c_int, P, i64, P, i64, P, i64, P, P]),
+                "orc_inside2d_f32": (None, [P, P, i64, P, i64, P]),
+                "orc_bvh_create": (P, [C.c_int, P, i64, P, i64]),
+                "orc_bvh_free": (None, [P]),
+                "orc_bvh_closest": (None, [P, P, i64, P, P, P]),
+                "orc_boundary_measure": (f64, [C.c_int, P, P, i64]),
+                "orc_sample_boundary": (None, [C.c_int, P, P, i64, i64, f64, u64, P, P, P]),
+                "orc_walks": (None, [P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P]),
+                "orc_reduce_walks": (None, [C.c_int, i64, i32, P, P, P, P, P]),
+                "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P]),
+                "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P]),
+                "orc_sphere_step": (None, [C.c_int, f64, f64, f64, f64, P, P, P, P]),
+                "orc_num_threads": (C.c_int, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+# ---------------------------------------------------------------- Philox
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox-4x32-10 block (Salmon et al., SC'11): 4 counter words, 2 key words."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib.orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def u01(r: int) -> float:
+    """Uniform in (0,1) from one 32-bit word: (2*(r>>9)+1) * 2^-24."""
+    return float(_load().orc_u01(int(r) & 0xFFFFFFFF))
+
+
+# ---------------------------------------------------------------- functions
+def encode_function(terms) -> np.ndarray:
+    """[(kind, coeffs), ...] -> flat array [n_terms, kind, n, coeffs..., ...]."""
+    out = [float(len(terms))]
+    for kind, coeffs in terms:
+        coeffs = [float(c) for c in np.asarray(coeffs, dtype=np.float64).ravel()]
+        out += [float(kind), float(len(coeffs))] + coeffs
+    return np.asarray(out, dtype=np.float64)
+
+
+def fn_eval(terms, dim: int, x) -> np.ndarray:
+    """Evaluate a problem function (g or f of Eq. 1) at points x[n, dim]."""
+    lib = _load()
+    spec = encode_function(terms)
+    x = _f64(np.atleast_2d(x))
+    return np.array([lib.orc_fn_eval(_p(spec), dim, _p(x[i])) for i in range(x.shape[0])])
+
+
+# ---------------------------------------------------------------- Green's functions
+def green(dim: int, x, y, ny) -> np.ndarray:
+    """App. A: [G, dG/dx (dim), dG/dn_y, d2G/dx dn_y (dim)] for one pair."""
+    lib = _load()
+    out = np.zeros(2 + 2 * dim)
+    lib.orc_green(dim, _p(_f64(x)), _p(_f64(y)), _p(_f64(ny)), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- geometry
+def closest_brute64(V, F, pts):
+    lib = _load()
+    V, F, pts = _f32(V), _i32(F), _f64(pts)
+    dim = V.shape[1]
+    n = pts.shape[0]
+    dist, prim, cp = np.zeros(n), np.zeros(n, np.int32), np.zeros((n, dim))
+    lib.orc_closest_brute64(dim, _p(V), V.shape[0], _p(F), F.shape[0], _p(pts), n, _p(dist), _p(prim), _p(cp))
+    return dist, prim, cp
+
+
+def closest_brute32(V, F, pts):
+    """Canonical FP32 brute force: (squared distance, primitive index)."""
+    lib = _load()
+    V, F, pts = _f32(V), _i32(F), _f32(pts)
+    dim = V.shape[1]
+    n = pts.shape[0]
+    d2, prim = np.zeros(n, np.float32), np.zeros(n, np.int32)
+    lib.orc_closest_brute32(dim, _p(V), V.shape[0], _p(F), F.shape[0], _p(pts), n, _p(d2), _p(prim))
+    return d2, prim
+
+
+def inside2d_f32(V, F, pts) -> np.ndarray:
+    lib = _load()
+    V, F, pts = _f32(V), _i32(F), _f32(pts)
+    out = np.zeros(pts.shape[0], np.int32)
+    lib.orc_inside2d_f32(_p(V), _p(F), F.shape[0], _p(pts), pts.shape[0], _p(out))
+    return out
+
+
+class BVH:
+    """The oracle's own FP64 median-split BVH over a polygon/triangle mesh."""
+
+    def __init__(self, V, F):
+        self._lib = _load()
+        self.V, self.F = _f32(V), _i32(F)
+        self.dim = self.V.shape[1]
+        self.h = self._lib.orc_bvh_create(self.dim, _p(self.V), self.V.shape[0], _p(self.F), self.F.shape[0])
+
+    def closest(self, pts):
+        pts = _f64(pts)
+        n = pts.shape[0]
+        dist, prim, cp = np.zeros(n), np.zeros(n, np.int32), np.zeros((n, self.dim))
+        self._lib.orc_bvh_closest(self.h, _p(pts), n, _p(dist), _p(prim), _p(cp))
+        return dist, prim, cp
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._lib.orc_bvh_free(self.h)
+            self.h = None
+
+
+def boundary_measure(V, F) -> float:
+    V, F = _f32(V), _i32(F)
+    return float(_load().orc_boundary_measure(V.shape[1], _p(V), _p(F), F.shape[0]))
+
+
+def sample_boundary(V, F, N: int, l: float, seed: int):
+    """Sec. 4 Sampling + Sec. 3.2 offset: (z[N,dim], n[N,dim], element[N]) in FP64."""
+    lib = _load()
+    V, F = _f32(V), _i32(F)
+    dim = V.shape[1]
+    z, n, e = np.zeros((N, dim)), np.zeros((N, dim)), np.zeros(N, np.int32)
+    lib.orc_sample_boundary(dim, _p(V), _p(F), F.shape[0], N, float(l), int(seed), _p(z), _p(n), _p(e))
+    return z, n, e
+
+
+def sphere_step(dim: int, R: float, u0: float, u1: float, u2: float):
+    """Sec. 3.1 step: (direction w, source radius rho, w_u, w_g) for ball radius R."""
+    lib = _load()
+    om = np.zeros(3)
+    rho, wu, wg = C.c_double(), C.c_double(), C.c_double()
+    lib.orc_sphere_step(dim, float(R), float(u0), float(u1), float(u2), _p(om), C.byref(rho), C.byref(wu),
+                        C.byref(wg))
+    return om[:dim].copy(), rho.value, wu.value, wg.value
+
+
+def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int, seed: int,
+          id_base: int = 0, tag: int = TAG_WALK, want_pend: bool = False):
+    """Sec. 3.1 / Eq. 7: W walks from each FP32 start point.
+
+    Returns dict with per-walk U, grad[.., dim], steps, prim (and pend)."""
+    lib = _load()
+    starts = _f32(starts)
+    n, dim = starts.shape
+    T = n * W
+    U, grad = np.zeros(T), np.zeros((T, dim))
+    steps, prim = np.zeros(T, np.int32), np.zeros(T, np.int32)
+    pend = np.zeros((T, dim)) if want_pend else None
+    g = encode_function(g_terms)
+    f = encode_function(f_terms)
+    lib.orc_walks(bvh.h, _p(g), _p(f), _p(starts), n, int(W), float(eps), int(max_steps), int(seed),
+                  int(id_base), int(tag), _p(U), _p(grad), _p(steps), _p(prim), _p(pend))
+    out = {"U": U, "grad": grad, "steps": steps, "prim": prim}
+    if want_pend:
+        out["pend"] = pend
+    return out
+
+
+def reduce_walks(U, grad, nrm, W: int):
+    """Alg. 1: u^ and du/dn^ per sample as means over its W walks."""
+    lib = _load()
+    U, grad = _f64(U), _f64(grad)
+    dim = grad.shape[1]
+    n = U.shape[0] // W
+    nrm_a = None if nrm is None else _f32(nrm)
+    u_hat = np.zeros(n)
+    q_hat = np.zeros(n) if nrm is not None else None
+    lib.orc_reduce_walks(dim, n, int(W), _p(U), _p(grad), _p(nrm_a), _p(u_hat), _p(q_hat))
+    return u_hat, q_hat
+
+
+def sample_source2d(V, F, grid, seed: int, f_terms):
+    """Sec. 4 Sampling: jittered grid over the bounding box, kept if inside.
+
+    Returns (y[kept,2] FP32, c[kept] = f(y)|box| FP64, n_candidates)."""
+    lib = _load()
+    V, F = _f32(V), _i32(F)
+    G0, G1 = int(grid[0]), int(grid[1])
+    y = np.zeros((G0 * G1, 2), np.float32)
+    c = np.zeros(G0 * G1)
+    f = encode_function(f_terms)
+    kept = lib.orc_sample_source2d(_p(V), V.shape[0], _p(F), F.shape[0], G0, G1, int(seed), _p(f), _p(y), _p(c))
+    return y[:kept].copy(), c[:kept].copy(), G0 * G1
+
+
+def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None):
+    """Eq. 3-6 / Alg. 1 splat: FP64 running sums (u_bnd, u_src, g_bnd, g_src)."""
+    lib = _load()
+    z, nz, x = _f64(z), _f64(nz), _f64(x)
+    dim = x.shape[1]
+    N, M = z.shape[0], x.shape[0]
+    u_hat, q_hat = _f64(u_hat), _f64(q_hat)
+    if y is None:
+        y = np.zeros((0, dim))
+        c = np.zeros(0)
+    y, c = _f64(y), _f64(c)
+    ub, us = np.zeros(M), np.zeros(M)
+    gb, gs = np.zeros((M, dim)), np.zeros((M, dim))
+    lib.orc_gather(dim, N, _p(z), _p(nz), _p(u_hat), _p(q_hat), float(bnd_measure), y.shape[0], _p(y), _p(c),
+                   M, _p(x), _p(ub), _p(us), _p(gb), _p(gs))
+    return ub, us, gb, gs

@@ -1,0 +1,919 @@
+/*
+ * bvc_oracle.c -- plain, slow FP64 CPU oracle for Boundary Value Caching
+ * (Miller, Sawhney, Crane, Gkioulekas, "Boundary Value Caching for Walk on
+ * Spheres", SIGGRAPH 2023).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header or constant table
+ * with the CUDA library; the two meet only through the seeded inputs.
+ *
+ * Every routine follows the paper's definitions in the paper's order, in
+ * double precision, with no blocking or fusion:
+ *   - free-space Green's functions and derivatives ........ App. A, Eq. A1-A4
+ *     (reading: G_3D = -1/(4 pi r), the sign implied by the printed
+ *      gradient, normal derivative and second derivative)
+ *   - boundary estimator, source estimator, gradients ..... Eq. 3-6, Alg. 1
+ *   - walk on spheres with the ball Green's function ...... Sec. 3.1, Eq. 7
+ *   - boundary sampling by a CDF over element measures .... Sec. 4 "Sampling"
+ *   - offset Dirichlet boundary (samples moved by -l n) ... Sec. 3.2
+ *   - stratified uniform source samples ................... Sec. 4 "Sampling"
+ * Randomness: Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11), written here from that definition.
+ *
+ * Decisions that pick an integer (closest primitive index, inside/outside
+ * test of a candidate source point) have, besides the FP64 versions, a
+ * "canonical FP32" form with a fixed operation order (explicit fmaf, no
+ * contraction) so that the GPU path, which takes them in FP32, can be
+ * checked bit-exactly.  This file must be compiled with -ffp-contract=off.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Philox-4x32-10 (SC'11).  Round: two 32x32->64 multiplies by the round     */
+/* constants, a swap and xor with the key; the key is bumped by the Weyl     */
+/* constants between rounds.                                                  */
+/* ------------------------------------------------------------------------ */
+static void philox_round(uint32_t c[4], const uint32_t k[2]) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+  const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+  const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+  c[0] = n0;
+  c[1] = lo1;
+  c[2] = n2;
+  c[3] = lo0;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  uint32_t k[2] = {key[0], key[1]};
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k[0] += 0x9E3779B9u;
+      k[1] += 0xBB67AE85u;
+    }
+    philox_round(c, k);
+  }
+  memcpy(out, c, sizeof(c));
+}
+
+/* Uniform in the open interval (0,1): odd multiples of 2^-24.  Every value is
+ * exact in FP32 and FP64, so both sides of a parity test see the same number. */
+double orc_u01(uint32_t r) { return ((double)(r >> 9) * 2.0 + 1.0) * 0x1p-24; }
+
+/* One Philox draw for (id, word2, tag) under a 64-bit seed. */
+static void draw(uint64_t seed, uint64_t id, uint32_t word2, uint32_t tag, double u[4]) {
+  uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), word2, tag};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t r[4];
+  orc_philox4x32_10(ctr, key, r);
+  for (int i = 0; i < 4; ++i) u[i] = orc_u01(r[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem functions g and f (Eq. 1).  The paper passes them as callbacks;   */
+/* here a function is a sum of terms from a few closed families, encoded as  */
+/* a flat array: [n_terms, (kind, n_coeffs, coeffs...) x n_terms].           */
+/*   kind 1 POLY: monomials x^i y^j (z^k), total degree <= 4, ordered by      */
+/*          degree t = 0..4, then i = t..0, then (3D) j = t-i..0.             */
+/*   kind 2 GAUSS: [s, A_1, c_1(dim), A_2, c_2, ...]:                         */
+/*          sum A_k exp(-|x-c_k|^2 / (2 s^2)).                                */
+/*   kind 3 GAUSS_LAPLACIAN: same coefficients, value = Laplacian of GAUSS:   */
+/*          sum A_k (|x-c_k|^2/s^4 - dim/s^2) exp(-|x-c_k|^2/(2 s^2)).       */
+/*   kind 4 EXP_TRIG (3D): [A, alpha, beta, gamma]:                           */
+/*          A exp(alpha z) cos(beta x) sin(gamma y).                          */
+/* ------------------------------------------------------------------------ */
+static double ipow(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
+}
+
+static double poly_eval(int dim, const double* c, int nc, const double* x) {
+  double s = 0.0;
+  int idx = 0;
+  for (int t = 0; t <= 4 && idx < nc; ++t) {
+    if (dim == 2) {
+      for (int i = t; i >= 0 && idx < nc; --i, ++idx) s += c[idx] * ipow(x[0], i) * ipow(x[1], t - i);
+    } else {
+      for (int i = t; i >= 0 && idx < nc; --i)
+        for (int j = t - i; j >= 0 && idx < nc; --j, ++idx)
+          s += c[idx] * ipow(x[0], i) * ipow(x[1], j) * ipow(x[2], t - i - j);
+    }
+  }
+  return s;
+}
+
+static double gauss_eval(int dim, const double* c, int nc, const double* x, int laplacian) {
+  const double s = c[0];
+  const int per = 1 + dim;
+  double v = 0.0;
+  for (int k = 0; 1 + (k + 1) * per <= nc; ++k) {
+    const double* b = c + 1 + k * per;
+    double r2 = 0.0;
+    for (int a = 0; a < dim; ++a) r2 += (x[a] - b[1 + a]) * (x[a] - b[1 + a]);
+    const double e = exp(-r2 / (2.0 * s * s));
+    v += laplacian ? b[0] * (r2 / (s * s * s * s) - dim / (s * s)) * e : b[0] * e;
+  }
+  return v;
+}
+
+double orc_fn_eval(const double* spec, int dim, const double* x) {
+  const int nt = (int)spec[0];
+  const double* p = spec + 1;
+  double v = 0.0;
+  for (int t = 0; t < nt; ++t) {
+    const int kind = (int)p[0], nc = (int)p[1];
+    const double* c = p + 2;
+    switch (kind) {
+      case 1: v += poly_eval(dim, c, nc, x); break;
+      case 2: v += gauss_eval(dim, c, nc, x, 0); break;
+      case 3: v += gauss_eval(dim, c, nc, x, 1); break;
+      case 4: v += c[0] * exp(c[1] * x[2]) * cos(c[2] * x[0]) * sin(c[3] * x[1]); break;
+      default: break;
+    }
+    p += 2 + nc;
+  }
+  return v;
+}
+
+static int fn_is_zero(const double* spec) { return spec == NULL || (int)spec[0] == 0; }
+
+/* ------------------------------------------------------------------------ */
+/* Free-space Green's function of the Laplacian and its derivatives, App. A. */
+/* d = y - x, r = |d|.  out = [G, dG/dx (dim), dG/dn_y, d2G/dx dn_y (dim)].  */
+/* ------------------------------------------------------------------------ */
+void orc_green(int dim, const double* x, const double* y, const double* ny, double* out) {
+  double d[3] = {0, 0, 0}, r2 = 0.0, nd = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    d[a] = y[a] - x[a];
+    r2 += d[a] * d[a];
+    nd += ny[a] * d[a];
+  }
+  const double r = sqrt(r2);
+  if (dim == 2) {
+    out[0] = log(r) / (2.0 * ORC_PI);
+    for (int a = 0; a < 2; ++a) out[1 + a] = -d[a] / (2.0 * ORC_PI * r2);
+    out[3] = nd / (2.0 * ORC_PI * r2);
+    for (int a = 0; a < 2; ++a)
+      out[4 + a] = 2.0 * nd * d[a] / (2.0 * ORC_PI * r2 * r2) - ny[a] / (2.0 * ORC_PI * r2);
+  } else {
+    const double r3 = r2 * r, r5 = r3 * r2;
+    out[0] = -1.0 / (4.0 * ORC_PI * r);
+    for (int a = 0; a < 3; ++a) out[1 + a] = -d[a] / (4.0 * ORC_PI * r3);
+    out[4] = nd / (4.0 * ORC_PI * r3);
+    for (int a = 0; a < 3; ++a) out[5 + a] = 3.0 * nd * d[a] / (4.0 * ORC_PI * r5) - ny[a] / (4.0 * ORC_PI * r3);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry: closest point on a segment / triangle, FP64.                    */
+/* Triangle: Voronoi-region method (Ericson, Real-Time Collision Detection,  */
+/* Sec. 5.1.5).  Each returns the squared distance and the closest point.    */
+/* ------------------------------------------------------------------------ */
+static double seg_closest64(const double* a, const double* b, const double* p, double* c) {
+  const double abx = b[0] - a[0], aby = b[1] - a[1];
+  const double apx = p[0] - a[0], apy = p[1] - a[1];
+  const double num = apx * abx + apy * aby, den = abx * abx + aby * aby;
+  double t = num <= 0.0 ? 0.0 : (num >= den ? 1.0 : num / den);
+  c[0] = a[0] + t * abx;
+  c[1] = a[1] + t * aby;
+  const double dx = p[0] - c[0], dy = p[1] - c[1];
+  return dx * dx + dy * dy;
+}
+
+static double dot3d(const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; }
+
+static double tri_closest64(const double* a, const double* b, const double* cc, const double* p, double* c) {
+  double ab[3], ac[3], ap[3], bp[3], cp[3];
+  for (int i = 0; i < 3; ++i) {
+    ab[i] = b[i] - a[i];
+    ac[i] = cc[i] - a[i];
+    ap[i] = p[i] - a[i];
+  }
+  const double d1 = dot3d(ab, ap), d2 = dot3d(ac, ap);
+  if (d1 <= 0.0 && d2 <= 0.0) {
+    memcpy(c, a, 3 * sizeof(double));
+    goto done;
+  }
+  for (int i = 0; i < 3; ++i) bp[i] = p[i] - b[i];
+  const double d3 = dot3d(ab, bp), d4 = dot3d(ac, bp);
+  if (d3 >= 0.0 && d4 <= d3) {
+    memcpy(c, b, 3 * sizeof(double));
+    goto done;
+  }
+  const double vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+    const double v = d1 / (d1 - d3);
+    for (int i = 0; i < 3; ++i) c[i] = a[i] + v * ab[i];
+    goto done;
+  }
+  for (int i = 0; i < 3; ++i) cp[i] = p[i] - cc[i];
+  const double d5 = dot3d(ab, cp), d6 = dot3d(ac, cp);
+  if (d6 >= 0.0 && d5 <= d6) {
+    memcpy(c, cc, 3 * sizeof(double));
+    goto done;
+  }
+  const double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+    const double w = d2 / (d2 - d6);
+    for (int i = 0; i < 3; ++i) c[i] = a[i] + w * ac[i];
+    goto done;
+  }
+  const double va = d3 * d6 - d5 * d4;
+  if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
+    const double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    for (int i = 0; i < 3; ++i) c[i] = b[i] + w * (cc[i] - b[i]);
+    goto done;
+  }
+  {
+    const double denom = 1.0 / (va + vb + vc);
+    const double v = vb * denom, w = vc * denom;
+    for (int i = 0; i < 3; ++i) c[i] = a[i] + ab[i] * v + ac[i] * w;
+  }
+done : {
+  double s = 0.0;
+  for (int i = 0; i < 3; ++i) s += (p[i] - c[i]) * (p[i] - c[i]);
+  return s;
+}
+}
+
+typedef struct {
+  int dim;
+  int64_t nv, np;
+  double* V;   /* nv x dim */
+  int32_t* F;  /* np x dim vertex indices */
+} mesh_t;
+
+static double prim_closest64(const mesh_t* m, int64_t e, const double* p, double* c) {
+  const int32_t* f = m->F + e * m->dim;
+  if (m->dim == 2) return seg_closest64(m->V + 2 * f[0], m->V + 2 * f[1], p, c);
+  return tri_closest64(m->V + 3 * f[0], m->V + 3 * f[1], m->V + 3 * f[2], p, c);
+}
+
+/* Brute force over every primitive; ties go to the lowest index. */
+void orc_closest_brute64(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const double* pts,
+                         int64_t n, double* dist, int32_t* prim, double* cp) {
+  mesh_t m = {dim, nv, np, NULL, (int32_t*)F};
+  m.V = (double*)malloc(sizeof(double) * nv * dim);
+  for (int64_t i = 0; i < nv * dim; ++i) m.V[i] = V[i];
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < n; ++q) {
+    double best = INFINITY, c[3], bc[3] = {0, 0, 0};
+    int32_t bi = -1;
+    for (int64_t e = 0; e < np; ++e) {
+      const double d2 = prim_closest64(&m, e, pts + q * dim, c);
+      if (d2 < best) {
+        best = d2;
+        bi = (int32_t)e;
+        memcpy(bc, c, sizeof(c));
+      }
+    }
+    dist[q] = sqrt(best);
+    prim[q] = bi;
+    if (cp) memcpy(cp + q * dim, bc, sizeof(double) * dim);
+  }
+  free(m.V);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Canonical FP32 closest-point distances.  Fixed operation order with      */
+/* explicit fmaf; the primitive is (a, ab = b-a, [ac = c-a]) in FP32.        */
+/* Used only to check the GPU's primitive index bit-exactly.                 */
+/* ------------------------------------------------------------------------ */
+static float seg_d2_f32(float ax, float ay, float abx, float aby, float px, float py) {
+  const float apx = px - ax, apy = py - ay;
+  const float num = fmaf(apy, aby, apx * abx);
+  const float den = fmaf(aby, aby, abx * abx);
+  float t;
+  if (num <= 0.0f)
+    t = 0.0f;
+  else if (num >= den)
+    t = 1.0f;
+  else
+    t = num / den;
+  const float dx = fmaf(-t, abx, apx), dy = fmaf(-t, aby, apy);
+  return fmaf(dy, dy, dx * dx);
+}
+
+static float dot3f(const float* u, const float* v) { return fmaf(u[2], v[2], fmaf(u[1], v[1], u[0] * v[0])); }
+
+static float tri_d2_f32(const float* a, const float* ab, const float* ac, const float* p) {
+  float ap[3], bp[3], cp[3], df[3];
+  for (int i = 0; i < 3; ++i) ap[i] = p[i] - a[i];
+  const float d1 = dot3f(ab, ap), d2 = dot3f(ac, ap);
+  if (d1 <= 0.0f && d2 <= 0.0f) return dot3f(ap, ap);
+  for (int i = 0; i < 3; ++i) bp[i] = ap[i] - ab[i];
+  const float d3 = dot3f(ab, bp), d4 = dot3f(ac, bp);
+  if (d3 >= 0.0f && d4 <= d3) return dot3f(bp, bp);
+  const float vc = fmaf(d1, d4, -(d3 * d2));
+  if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) {
+    const float v = d1 / (d1 - d3);
+    for (int i = 0; i < 3; ++i) df[i] = fmaf(-v, ab[i], ap[i]);
+    return dot3f(df, df);
+  }
+  for (int i = 0; i < 3; ++i) cp[i] = ap[i] - ac[i];
+  const float d5 = dot3f(ab, cp), d6 = dot3f(ac, cp);
+  if (d6 >= 0.0f && d5 <= d6) return dot3f(cp, cp);
+  const float vb = fmaf(d5, d2, -(d1 * d6));
+  if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) {
+    const float w = d2 / (d2 - d6);
+    for (int i = 0; i < 3; ++i) df[i] = fmaf(-w, ac[i], ap[i]);
+    return dot3f(df, df);
+  }
+  const float va = fmaf(d3, d6, -(d5 * d4));
+  const float e43 = d4 - d3, e56 = d5 - d6;
+  if (va <= 0.0f && e43 >= 0.0f && e56 >= 0.0f) {
+    const float w = e43 / (e43 + e56);
+    for (int i = 0; i < 3; ++i) df[i] = fmaf(-w, ac[i] - ab[i], bp[i]);
+    return dot3f(df, df);
+  }
+  const float denom = 1.0f / (va + vb + vc);
+  const float v = vb * denom, w = vc * denom;
+  for (int i = 0; i < 3; ++i) df[i] = fmaf(-w, ac[i], fmaf(-v, ab[i], ap[i]));
+  return dot3f(df, df);
+}
+
+/* FP32 brute-force argmin of the canonical squared distance; ties -> lowest index. */
+void orc_closest_brute32(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const float* pts,
+                         int64_t n, float* d2_out, int32_t* prim) {
+  (void)nv;
+  float* P = (float*)malloc(sizeof(float) * np * 9);
+  for (int64_t e = 0; e < np; ++e) {
+    const int32_t* f = F + e * dim;
+    for (int a = 0; a < dim; ++a) {
+      const float va = V[(int64_t)f[0] * dim + a];
+      P[e * 9 + a] = va;
+      P[e * 9 + 3 + a] = V[(int64_t)f[1] * dim + a] - va;
+      if (dim == 3) P[e * 9 + 6 + a] = V[(int64_t)f[2] * dim + a] - va;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < n; ++q) {
+    float best = INFINITY;
+    int32_t bi = -1;
+    const float* p = pts + q * dim;
+    for (int64_t e = 0; e < np; ++e) {
+      const float* r = P + e * 9;
+      const float d2 = dim == 2 ? seg_d2_f32(r[0], r[1], r[3], r[4], p[0], p[1]) : tri_d2_f32(r, r + 3, r + 6, p);
+      if (d2 < best) {
+        best = d2;
+        bi = (int32_t)e;
+      }
+    }
+    d2_out[q] = best;
+    prim[q] = bi;
+  }
+  free(P);
+}
+
+/* Canonical FP32 crossing-number inside test (2D polygon, +x ray). */
+static int inside2d_f32(const float* V, const int32_t* F, int64_t np, float px, float py) {
+  int c = 0;
+  for (int64_t e = 0; e < np; ++e) {
+    const float ax = V[2 * F[2 * e]], ay = V[2 * F[2 * e] + 1];
+    const float bx = V[2 * F[2 * e + 1]], by = V[2 * F[2 * e + 1] + 1];
+    if ((ay > py) != (by > py)) {
+      const float t = (py - ay) / (by - ay);
+      const float xi = fmaf(t, bx - ax, ax);
+      if (px < xi) c ^= 1;
+    }
+  }
+  return c;
+}
+
+void orc_inside2d_f32(const float* V, const int32_t* F, int64_t np, const float* pts, int64_t n, int32_t* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < n; ++q) out[q] = inside2d_f32(V, F, np, pts[2 * q], pts[2 * q + 1]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* A plain FP64 BVH (median split on the longest centroid axis) so that the */
+/* oracle's walks finish on large meshes.  The query returns exactly what   */
+/* the brute force above returns (checked in the tests).                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double lo[3], hi[3];
+  int64_t left, right; /* children, or -1 */
+  int64_t start, count;
+} bnode_t;
+
+typedef struct {
+  mesh_t m;
+  bnode_t* nodes;
+  int64_t n_nodes;
+  int64_t* order;
+  double* cen;
+  double slack;
+} obvh_t;
+
+static int g_sort_axis;
+static const double* g_sort_cen;
+static int cmp_cen(const void* x, const void* y) {
+  const double a = g_sort_cen[*(const int64_t*)x * 3 + g_sort_axis];
+  const double b = g_sort_cen[*(const int64_t*)y * 3 + g_sort_axis];
+  if (a < b) return -1;
+  if (a > b) return 1;
+  const int64_t ia = *(const int64_t*)x, ib = *(const int64_t*)y;
+  return (ia > ib) - (ia < ib);
+}
+
+static void prim_box(const mesh_t* m, int64_t e, double* lo, double* hi) {
+  const int32_t* f = m->F + e * m->dim;
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = INFINITY;
+    hi[a] = -INFINITY;
+  }
+  for (int v = 0; v < m->dim; ++v)
+    for (int a = 0; a < m->dim; ++a) {
+      const double x = m->V[(int64_t)f[v] * m->dim + a];
+      if (x < lo[a]) lo[a] = x;
+      if (x > hi[a]) hi[a] = x;
+    }
+  for (int a = m->dim; a < 3; ++a) lo[a] = hi[a] = 0.0;
+}
+
+static int64_t bvh_build_rec(obvh_t* b, int64_t start, int64_t count) {
+  const int64_t id = b->n_nodes++;
+  bnode_t* nd = &b->nodes[id];
+  for (int a = 0; a < 3; ++a) {
+    nd->lo[a] = INFINITY;
+    nd->hi[a] = -INFINITY;
+  }
+  double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = start; i < start + count; ++i) {
+    double lo[3], hi[3];
+    prim_box(&b->m, b->order[i], lo, hi);
+    for (int a = 0; a < 3; ++a) {
+      if (lo[a] < nd->lo[a]) nd->lo[a] = lo[a];
+      if (hi[a] > nd->hi[a]) nd->hi[a] = hi[a];
+      const double c = b->cen[b->order[i] * 3 + a];
+      if (c < clo[a]) clo[a] = c;
+      if (c > chi[a]) chi[a] = c;
+    }
+  }
+  nd->start = start;
+  nd->count = count;
+  nd->left = nd->right = -1;
+  if (count <= 4) return id;
+  int axis = 0;
+  for (int a = 1; a < b->m.dim; ++a)
+    if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+  g_sort_axis = axis;
+  g_sort_cen = b->cen;
+  qsort(b->order + start, (size_t)count, sizeof(int64_t), cmp_cen);
+  const int64_t half = count / 2;
+  const int64_t l = bvh_build_rec(b, start, half);
+  const int64_t r = bvh_build_rec(b, start + half, count - half);
+  b->nodes[id].left = l;
+  b->nodes[id].right = r;
+  return id;
+}
+
+void* orc_bvh_create(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np) {
+  obvh_t* b = (obvh_t*)calloc(1, sizeof(obvh_t));
+  b->m.dim = dim;
+  b->m.nv = nv;
+  b->m.np = np;
+  b->m.V = (double*)malloc(sizeof(double) * nv * dim);
+  for (int64_t i = 0; i < nv * dim; ++i) b->m.V[i] = V[i];
+  b->m.F = (int32_t*)malloc(sizeof(int32_t) * np * dim);
+  memcpy(b->m.F, F, sizeof(int32_t) * np * dim);
+  b->order = (int64_t*)malloc(sizeof(int64_t) * np);
+  b->cen = (double*)calloc((size_t)np * 3, sizeof(double));
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t e = 0; e < np; ++e) {
+    b->order[e] = e;
+    const int32_t* f = b->m.F + e * dim;
+    for (int a = 0; a < dim; ++a) {
+      double s = 0.0;
+      for (int v = 0; v < dim; ++v) s += b->m.V[(int64_t)f[v] * dim + a];
+      b->cen[e * 3 + a] = s / dim;
+    }
+  }
+  for (int64_t i = 0; i < nv * dim; ++i) {
+    const int a = (int)(i % dim);
+    if (b->m.V[i] < lo[a]) lo[a] = b->m.V[i];
+    if (b->m.V[i] > hi[a]) hi[a] = b->m.V[i];
+  }
+  double diag = 0.0;
+  for (int a = 0; a < dim; ++a) diag += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+  b->slack = 1e-12 * sqrt(diag);
+  b->nodes = (bnode_t*)malloc(sizeof(bnode_t) * (2 * np + 1));
+  b->n_nodes = 0;
+  if (np > 0) bvh_build_rec(b, 0, np);
+  return b;
+}
+
+void orc_bvh_free(void* h) {
+  obvh_t* b = (obvh_t*)h;
+  if (!b) return;
+  free(b->m.V);
+  free(b->m.F);
+  free(b->order);
+  free(b->cen);
+  free(b->nodes);
+  free(b);
+}
+
+static double box_d2(const bnode_t* n, const double* p, int dim) {
+  double s = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    double d = 0.0;
+    if (p[a] < n->lo[a])
+      d = n->lo[a] - p[a];
+    else if (p[a] > n->hi[a])
+      d = p[a] - n->hi[a];
+    s += d * d;
+  }
+  return s;
+}
+
+/* Closest primitive: nodes are skipped only when their box is farther than */
+/* the best distance plus a tiny slack, so ties and rounding never prune    */
+/* the true minimum; ties go to the lowest primitive index.                 */
+static double bvh_closest(const obvh_t* b, const double* p, double* cbest, int64_t* ibest) {
+  double best = INFINITY, bd = INFINITY;
+  int64_t bi = -1;
+  int64_t stack[128];
+  int sp = 0;
+  if (b->n_nodes) stack[sp++] = 0;
+  const int dim = b->m.dim;
+  while (sp) {
+    const bnode_t* n = &b->nodes[stack[--sp]];
+    const double lim = bd + b->slack;
+    if (box_d2(n, p, dim) > lim * lim) continue;
+    if (n->left < 0) {
+      for (int64_t i = n->start; i < n->start + n->count; ++i) {
+        const int64_t e = b->order[i];
+        double c[3];
+        const double d2 = prim_closest64(&b->m, e, p, c);
+        if (d2 < best || (d2 == best && e < bi)) {
+          best = d2;
+          bd = sqrt(d2);
+          bi = e;
+          memcpy(cbest, c, sizeof(double) * dim);
+        }
+      }
+    } else {
+      const double dl = box_d2(&b->nodes[n->left], p, dim), dr = box_d2(&b->nodes[n->right], p, dim);
+      if (dl <= dr) {
+        stack[sp++] = n->right;
+        stack[sp++] = n->left;
+      } else {
+        stack[sp++] = n->left;
+        stack[sp++] = n->right;
+      }
+    }
+  }
+  *ibest = bi;
+  return best;
+}
+
+void orc_bvh_closest(void* h, const double* pts, int64_t n, double* dist, int32_t* prim, double* cp) {
+  const obvh_t* b = (const obvh_t*)h;
+  const int dim = b->m.dim;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < n; ++q) {
+    double c[3];
+    int64_t e;
+    const double d2 = bvh_closest(b, pts + q * dim, c, &e);
+    dist[q] = sqrt(d2);
+    prim[q] = (int32_t)e;
+    if (cp) memcpy(cp + q * dim, c, sizeof(double) * dim);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Element measures, outward normals and the boundary sampler (Sec. 4       */
+/* "Sampling"; Alg. 1 draws z, n_z ~ p on the boundary; Sec. 3.2 moves the  */
+/* Dirichlet samples inward by l along the element normal).                 */
+/* Polygons are counter-clockwise, triangles wind counter-clockwise seen    */
+/* from outside, so the outward normal of a->b is (dy, -dx)/len in 2D and   */
+/* (b-a)x(c-a)/|.| in 3D.                                                    */
+/* ------------------------------------------------------------------------ */
+static double elem_measure_normal(int dim, const float* V, const int32_t* f, double* nrm) {
+  if (dim == 2) {
+    const double ax = V[2 * f[0]], ay = V[2 * f[0] + 1], bx = V[2 * f[1]], by = V[2 * f[1] + 1];
+    const double dx = bx - ax, dy = by - ay;
+    const double len = sqrt(dx * dx + dy * dy);
+    nrm[0] = dy / len;
+    nrm[1] = -dx / len;
+    return len;
+  }
+  double e1[3], e2[3], c[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = (double)V[3 * f[1] + a] - (double)V[3 * f[0] + a];
+    e2[a] = (double)V[3 * f[2] + a] - (double)V[3 * f[0] + a];
+  }
+  c[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  c[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  c[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  for (int a = 0; a < 3; ++a) nrm[a] = c[a] / len;
+  return 0.5 * len;
+}
+
+/* Total boundary measure |dOmega| as the sequential sum of element measures. */
+double orc_boundary_measure(int dim, const float* V, const int32_t* F, int64_t np) {
+  double s = 0.0, n[3];
+  for (int64_t e = 0; e < np; ++e) s += elem_measure_normal(dim, V, F + e * dim, n);
+  return s;
+}
+
+/* N stratified boundary samples.  Sample i draws (u0,u1,u2) from Philox    */
+/* (id = i, word2 = 0, tag = 1); s = (i + u0)/N picks the element through   */
+/* the CDF of element measures; 2D reuses the position of s inside the      */
+/* element's CDF interval as the arclength parameter, 3D places the point   */
+/* uniformly on the triangle from (u1,u2) (barycentrics 1-sqrt(u1),         */
+/* sqrt(u1)(1-u2), sqrt(u1)u2).  z = p - l n.                               */
+void orc_sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l, uint64_t seed,
+                         double* z, double* nrm, int32_t* elem) {
+  double* cdf = (double*)malloc(sizeof(double) * (np + 1));
+  double n[3];
+  cdf[0] = 0.0;
+  for (int64_t e = 0; e < np; ++e) cdf[e + 1] = cdf[e] + elem_measure_normal(dim, V, F + e * dim, n);
+  const double total = cdf[np];
+  for (int64_t i = 0; i < N; ++i) {
+    double u[4];
+    draw(seed, (uint64_t)i, 0u, 1u, u);
+    const double s = ((double)i + u[0]) / (double)N;
+    const double t = s * total;
+    /* smallest e with cdf[e+1] > t */
+    int64_t lo = 0, hi = np - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (cdf[mid + 1] > t)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    const int64_t e = lo;
+    const int32_t* f = F + e * dim;
+    const double meas = elem_measure_normal(dim, V, f, n);
+    double p[3];
+    if (dim == 2) {
+      double lam = (t - cdf[e]) / meas;
+      if (lam < 0.0) lam = 0.0;
+      if (lam > 1.0) lam = 1.0;
+      for (int a = 0; a < 2; ++a) {
+        const double va = V[2 * f[0] + a], vb = V[2 * f[1] + a];
+        p[a] = va + lam * (vb - va);
+      }
+    } else {
+      const double sq = sqrt(u[1]);
+      const double b1 = sq * (1.0 - u[2]), b2 = sq * u[2];
+      for (int a = 0; a < 3; ++a) {
+        const double v0 = V[3 * f[0] + a], v1 = V[3 * f[1] + a], v2 = V[3 * f[2] + a];
+        p[a] = v0 + b1 * (v1 - v0) + b2 * (v2 - v0);
+      }
+    }
+    for (int a = 0; a < dim; ++a) {
+      z[i * dim + a] = p[a] - l * n[a];
+      nrm[i * dim + a] = n[a];
+    }
+    elem[i] = (int32_t)e;
+  }
+  free(cdf);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Walk on spheres (Sec. 3.1) for Laplace(u) = f, u = g on the boundary.    */
+/*                                                                          */
+/* Ball B(x,R), R = distance to the boundary.  With G^B the Green's         */
+/* function of -Laplacian on the ball (zero on its sphere):                 */
+/*   u(x)      = mean_{sphere} u  -  int_B G^B(x,y) f(y) dy                  */
+/*   grad u(x) = (d/R) mean_{sphere}[u(z) nu]  -  int_B grad_x G^B f dy     */
+/* (the second is Eq. 7 with the ball's Poisson-kernel derivative at the    */
+/* centre).  Step k draws Philox (id = walk id, word2 = k, tag):            */
+/*   direction from (u0,u1): 2D (cos 2pi u0, sin 2pi u0); 3D z = 1-2u0,     */
+/*   phi = 2pi u1; source point y = x + rho w with rho = R u2 (uniform      */
+/*   radius, density 1/(R |S| rho^(d-1))) giving the weights                */
+/*     w_u    = -R rho ln(R/rho)    (2D)   or  -rho (R - rho)      (3D)     */
+/*     w_grad = -R (1 - (rho/R)^d) w                                         */
+/* A walk stops at the first closest-point query with distance < eps       */
+/* (eps shell) and returns g at the closest boundary point; it is capped    */
+/* after max_steps queries.                                                 */
+/* Per walk:  U = g(pbar_end) + sum_k w_u,k f(y_k)                           */
+/*            grad = nu0 [ (d/R0)(U - w_u,0 f(y_0) - g(pbar_0)) + w_g,0 ]    */
+/* where g(pbar_0), a constant independent of the step-0 direction, is a    */
+/* control variate (mean of nu over the sphere is zero).  A walk whose      */
+/* start is already inside the shell has grad = 0.                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const obvh_t* bvh;
+  const double* g;
+  const double* f;
+  double eps;
+  int max_steps;
+  uint64_t seed;
+  uint32_t tag;
+} walk_ctx_t;
+
+/* One sphere step: direction w from (u0,u1) and, for radius R, the source  */
+/* point radius rho = R u2 with its weights w_u and the scalar w_g such     */
+/* that the step-0 gradient source term is w_g * w.                          */
+void orc_sphere_step(int dim, double R, double u0, double u1, double u2, double* om, double* rho, double* wu,
+                     double* wg) {
+  if (dim == 2) {
+    om[0] = cos(2.0 * ORC_PI * u0);
+    om[1] = sin(2.0 * ORC_PI * u0);
+  } else {
+    const double zc = 1.0 - 2.0 * u0, phi = 2.0 * ORC_PI * u1;
+    const double s = sqrt(fmax(0.0, 1.0 - zc * zc));
+    om[0] = s * cos(phi);
+    om[1] = s * sin(phi);
+    om[2] = zc;
+  }
+  const double r = R * u2;
+  *rho = r;
+  *wu = dim == 2 ? -R * r * log(R / r) : -r * (R - r);
+  *wg = -R * (1.0 - ipow(r / R, dim));
+}
+
+static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double* U_out, double* grad_out,
+                     int32_t* steps_out, int32_t* prim_out, double* pend_out) {
+  const int dim = w->bvh->m.dim;
+  const int has_f = !fn_is_zero(w->f);
+  double x[3] = {0, 0, 0}, pbar[3] = {0, 0, 0}, nu[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) x[a] = x0[a];
+  double usrc = 0.0, wf0 = 0.0, wg0 = 0.0, R0 = 0.0, cv = 0.0;
+  int k = 0;
+  int64_t prim = -1;
+  for (;;) {
+    const double d = sqrt(bvh_closest(w->bvh, x, pbar, &prim));
+    ++k;
+    if (k == 1) cv = orc_fn_eval(w->g, dim, pbar);
+    if (d < w->eps || k >= w->max_steps) break;
+    const double R = d;
+    double u[4];
+    draw(w->seed, wid, (uint32_t)(k - 1), w->tag, u);
+    double om[3] = {0, 0, 0}, rho, wu, wg;
+    orc_sphere_step(dim, R, u[0], u[1], u[2], om, &rho, &wu, &wg);
+    if (has_f) {
+      double y[3] = {0, 0, 0};
+      for (int a = 0; a < dim; ++a) y[a] = x[a] + rho * om[a];
+      const double fy = orc_fn_eval(w->f, dim, y);
+      usrc += wu * fy;
+      if (k == 1) {
+        wf0 = wu * fy;
+        wg0 = wg * fy;
+      }
+    }
+    if (k == 1) {
+      R0 = R;
+      for (int a = 0; a < dim; ++a) nu[a] = om[a];
+    }
+    for (int a = 0; a < dim; ++a) x[a] += R * om[a];
+  }
+  const double U = orc_fn_eval(w->g, dim, pbar) + usrc;
+  *U_out = U;
+  if (k == 1) {
+    for (int a = 0; a < dim; ++a) grad_out[a] = 0.0;
+  } else {
+    const double s = ((double)dim / R0) * (U - wf0 - cv) + wg0;
+    for (int a = 0; a < dim; ++a) grad_out[a] = s * nu[a];
+  }
+  *steps_out = k;
+  *prim_out = (int32_t)prim;
+  if (pend_out)
+    for (int a = 0; a < dim; ++a) pend_out[a] = pbar[a];
+}
+
+/* W walks from each of n start points; walk j of start i has id            */
+/* id_base + i*W + j.  Outputs are per walk: U[n*W], grad[n*W*dim],         */
+/* steps[n*W], prim[n*W], pend[n*W*dim] (pend may be NULL).                  */
+void orc_walks(void* bvh, const double* g, const double* f, const float* starts, int64_t n, int32_t W, double eps,
+               int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
+               int32_t* steps, int32_t* prim, double* pend) {
+  walk_ctx_t w = {(const obvh_t*)bvh, g, f, eps, max_steps, seed, tag};
+  const int dim = w.bvh->m.dim;
+  const int64_t total = n * (int64_t)W;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t t = 0; t < total; ++t) {
+    const int64_t i = t / W;
+    double x0[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) x0[a] = starts[i * dim + a];
+    walk_one(&w, x0, id_base + (uint64_t)t, &U[t], &grad[t * dim], &steps[t], &prim[t],
+             pend ? &pend[t * dim] : NULL);
+  }
+}
+
+/* Per-sample means over the W walks of each start (Alg. 1: the pointwise   */
+/* estimates u^ and du/dn^ of a boundary sample).  du/dn^ = n . grad.        */
+void orc_reduce_walks(int dim, int64_t n, int32_t W, const double* U, const double* grad, const float* nrm,
+                      double* u_hat, double* q_hat) {
+  for (int64_t i = 0; i < n; ++i) {
+    double su = 0.0, sq = 0.0;
+    for (int32_t j = 0; j < W; ++j) {
+      const int64_t t = i * W + j;
+      su += U[t];
+      if (nrm) {
+        double g = 0.0;
+        for (int a = 0; a < dim; ++a) g += (double)nrm[i * dim + a] * grad[t * dim + a];
+        sq += g;
+      }
+    }
+    u_hat[i] = su / W;
+    if (q_hat) q_hat[i] = sq / W;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Source samples (Sec. 4 "Sampling", Alg. 1 y ~ p^R): a jittered grid of   */
+/* G0 x G1 cells over the boundary's bounding box; candidate c draws        */
+/* (u0,u1) from Philox (id = c, word2 = 0, tag = 2); kept when the canonical */
+/* FP32 crossing test puts it inside.  With p = 1/|box| on the box and the  */
+/* indicator of the domain, the weight of a kept sample is f(y) |box| and    */
+/* the source estimator divides by the number of candidates G0*G1.          */
+/* Kept samples are returned in candidate order.                            */
+/* ------------------------------------------------------------------------ */
+int64_t orc_sample_source2d(const float* V, int64_t nv, const int32_t* F, int64_t np, int32_t G0, int32_t G1,
+                            uint64_t seed, const double* f, float* y_out, double* c_out) {
+  float lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+  for (int64_t i = 0; i < nv; ++i)
+    for (int a = 0; a < 2; ++a) {
+      if (V[2 * i + a] < lo[a]) lo[a] = V[2 * i + a];
+      if (V[2 * i + a] > hi[a]) hi[a] = V[2 * i + a];
+    }
+  const double ext0 = (double)hi[0] - (double)lo[0], ext1 = (double)hi[1] - (double)lo[1];
+  const double area = ext0 * ext1;
+  const int64_t ncand = (int64_t)G0 * G1;
+  int64_t kept = 0;
+  for (int64_t c = 0; c < ncand; ++c) {
+    double u[4];
+    draw(seed, (uint64_t)c, 0u, 2u, u);
+    const int64_t c0 = c % G0, c1 = c / G0;
+    const double y0 = (double)lo[0] + ((double)c0 + u[0]) * (ext0 / G0);
+    const double y1 = (double)lo[1] + ((double)c1 + u[1]) * (ext1 / G1);
+    const float fy0 = (float)y0, fy1 = (float)y1;
+    if (!inside2d_f32(V, F, np, fy0, fy1)) continue;
+    const double yy[2] = {fy0, fy1};
+    y_out[2 * kept] = fy0;
+    y_out[2 * kept + 1] = fy1;
+    c_out[kept] = orc_fn_eval(f, 2, yy) * area;
+    ++kept;
+  }
+  return kept;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The gather: Eq. 3-6 and the splat loops of Alg. 1, as a direct double    */
+/* loop.  For every evaluation point x and boundary sample (z, n, u^, q^):  */
+/*   u_bnd    += (dG/dn(x,z) u^ - G(x,z) q^) / p,        p = 1/|dOmega|      */
+/*   grad_bnd += (d2G/dxdn(x,z) u^ - dG/dx(x,z) q^) / p                      */
+/* and for every source sample (y, c = f(y)/p^Omega):                        */
+/*   u_src    += G(x,y) c,    grad_src += dG/dx(x,y) c                       */
+/* Returns SUMS (Alg. 1 running sums); the caller divides by N and M.       */
+/* ------------------------------------------------------------------------ */
+void orc_gather(int dim, int64_t N, const double* z, const double* nz, const double* u_hat, const double* q_hat,
+                double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M, const double* x,
+                double* u_bnd, double* u_src, double* g_bnd, double* g_src) {
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t k = 0; k < M; ++k) {
+    double xk[3] = {0, 0, 0}, zz[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, G[8];
+    for (int a = 0; a < dim; ++a) xk[a] = x[k * dim + a];
+    double ub = 0.0, us = 0.0, gb[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
+    for (int64_t i = 0; i < N; ++i) {
+      for (int a = 0; a < dim; ++a) {
+        zz[a] = z[i * dim + a];
+        nn[a] = nz[i * dim + a];
+      }
+      orc_green(dim, xk, zz, nn, G);
+      const double dGdn = G[1 + dim];
+      ub += (dGdn * u_hat[i] - G[0] * q_hat[i]) * bnd_measure;
+      for (int a = 0; a < dim; ++a) gb[a] += (G[2 + dim + a] * u_hat[i] - G[1 + a] * q_hat[i]) * bnd_measure;
+    }
+    for (int64_t j = 0; j < Ms; ++j) {
+      for (int a = 0; a < dim; ++a) zz[a] = y[j * dim + a];
+      orc_green(dim, xk, zz, nn, G);
+      us += G[0] * c[j];
+      for (int a = 0; a < dim; ++a) gs[a] += G[1 + a] * c[j];
+    }
+    u_bnd[k] = ub;
+    u_src[k] = us;
+    for (int a = 0; a < dim; ++a) {
+      if (g_bnd) g_bnd[k * dim + a] = gb[a];
+      if (g_src) g_src[k * dim + a] = gs[a];
+    }
+  }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,386 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no step of the method.  It builds the inputs that both the
+CUDA path and the CPU oracle consume:
+
+* boundary meshes: a regular polygon (unit circle), a noisy 7-lobed star
+  polygon, and a radially perturbed icosphere -- counter-clockwise polygons
+  and outward-wound triangles, as the library requires;
+* evaluation point sets (grids clipped to the domain, uniform random
+  interior points);
+* the coefficients of the boundary data g and source f of Eq. 1, as term
+  lists ``[(kind, coeffs), ...]`` in the library's function encoding;
+* closed-form exact solutions (value and gradient) used to measure error.
+
+Function encoding (the library's ``bvc_term``): kind 1 POLY (monomials of
+total degree <= 4, ordered by degree t, then power of x descending, then (3D)
+power of y descending), kind 2 GAUSS ``[s, A_1, c_1, A_2, c_2, ...]`` =
+sum A_k exp(-|x-c_k|^2/(2 s^2)), kind 3 GAUSS_LAPLACIAN (its Laplacian, same
+coefficients), kind 4 EXP_TRIG ``[A, alpha, beta, gamma]`` =
+A exp(alpha z) cos(beta x) sin(gamma y).
+
+The paper's own scenes (wind tunnel, cage, spacesuit, gallery) are not
+available; these generators stand in for them with the sizes of the
+benchmark configurations.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+POLY, GAUSS, GAUSS_LAPLACIAN, EXP_TRIG = 1, 2, 3, 4
+
+
+# ---------------------------------------------------------------- meshes
+def circle_polygon(n_seg: int, radius: float = 1.0):
+    """Regular n-gon inscribed in a circle, counter-clockwise."""
+    th = 2.0 * np.pi * np.arange(n_seg) / n_seg
+    V = np.stack([radius * np.cos(th), radius * np.sin(th)], 1).astype(np.float32)
+    F = np.stack([np.arange(n_seg), (np.arange(n_seg) + 1) % n_seg], 1).astype(np.int32)
+    return V, F
+
+
+def _fourier_noise(seed: int, n_modes: int = 16):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(n_modes)
+    b = rng.standard_normal(n_modes)
+    k = np.arange(1, n_modes + 1)
+
+    def noise(th):
+        th = np.asarray(th, dtype=np.float64)
+        return (a[None, :] * np.cos(np.outer(th, k)) + b[None, :] * np.sin(np.outer(th, k))) @ (1.0 / k)
+
+    fine = np.linspace(0.0, 2.0 * np.pi, 1 << 16, endpoint=False)
+    scale = 1.0 / np.max(np.abs(noise(fine)))
+    return lambda th: scale * noise(th)
+
+
+def star_radius_fn(seed: int, lobes: int = 7, amp: float = 0.3, noise_amp: float = 0.05):
+    """r(theta) = 1 + amp sin(lobes theta) + noise_amp * n(theta), where n is a
+    smooth seeded Fourier series (16 modes, N(0,1)/k coefficients) scaled to
+    max |n| = 1."""
+    noise = _fourier_noise(seed)
+    return lambda th: 1.0 + amp * np.sin(lobes * np.asarray(th)) + noise_amp * noise(th)
+
+
+def star_polygon(n_seg: int, seed: int):
+    """Nonconvex star polygon, vertices at uniform angles, counter-clockwise."""
+    r = star_radius_fn(seed)
+    th = 2.0 * np.pi * np.arange(n_seg) / n_seg
+    rr = r(th)
+    V = np.stack([rr * np.cos(th), rr * np.sin(th)], 1).astype(np.float32)
+    F = np.stack([np.arange(n_seg), (np.arange(n_seg) + 1) % n_seg], 1).astype(np.int32)
+    return V, F
+
+
+def inside_star_polygon(V: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Exact inside test for a polygon star-shaped about the origin whose
+    vertices sit at uniform angles (as built by ``star_polygon``)."""
+    n = V.shape[0]
+    pts = np.asarray(pts, dtype=np.float64)
+    th = np.mod(np.arctan2(pts[:, 1], pts[:, 0]), 2.0 * np.pi)
+    i = np.minimum((th / (2.0 * np.pi) * n).astype(np.int64), n - 1)
+    a = V[i].astype(np.float64)
+    b = V[(i + 1) % n].astype(np.float64)
+    cross = (b[:, 0] - a[:, 0]) * (pts[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (pts[:, 0] - a[:, 0])
+    return cross > 0.0
+
+
+def distance_to_polygon(V: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Brute-force distance from points to a closed polygon (generator use)."""
+    a = V.astype(np.float64)
+    b = np.roll(a, -1, axis=0)
+    ab = b - a
+    den = np.sum(ab * ab, 1)
+    out = np.empty(pts.shape[0])
+    for s in range(0, pts.shape[0], 256):
+        p = pts[s:s + 256, None, :].astype(np.float64)
+        t = np.clip(np.sum((p - a[None]) * ab[None], 2) / den[None], 0.0, 1.0)
+        c = a[None] + t[..., None] * ab[None]
+        out[s:s + 256] = np.sqrt(np.min(np.sum((p - c) ** 2, 2), 1))
+    return out
+
+
+_ICO_T = (1.0 + 5.0 ** 0.5) / 2.0
+
+
+def icosphere(subdiv: int):
+    """Unit icosphere: 20 * 4^subdiv triangles, outward counter-clockwise."""
+    t = _ICO_T
+    V = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+                  [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+                  [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    F = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+                  [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+                  [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+                  [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    for _ in range(subdiv):
+        a, b, c = F[:, 0], F[:, 1], F[:, 2]
+        e = np.concatenate([np.stack([a, b], 1), np.stack([b, c], 1), np.stack([c, a], 1)])
+        key = np.sort(e, 1)
+        uniq, inv = np.unique(key[:, 0] * (V.shape[0] + 1) + key[:, 1], return_inverse=True)
+        i0 = uniq // (V.shape[0] + 1)
+        i1 = uniq % (V.shape[0] + 1)
+        mid = V[i0] + V[i1]
+        mid /= np.linalg.norm(mid, axis=1, keepdims=True)
+        nf = F.shape[0]
+        m = V.shape[0] + inv
+        ab, bc, ca = m[:nf], m[nf:2 * nf], m[2 * nf:]
+        V = np.concatenate([V, mid])
+        F = np.concatenate([np.stack([a, ab, ca], 1), np.stack([b, bc, ab], 1),
+                            np.stack([c, ca, bc], 1), np.stack([ab, bc, ca], 1)])
+    return V, F.astype(np.int32)
+
+
+def radial_noise_fn(seed: int, n_waves: int = 16):
+    """n(p) = sum_j cos(k_j . p + phi_j), |k_j| ~ U[2,8], directions uniform,
+    phases uniform; normalised below so that max |n| = 1 on the mesh."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal((n_waves, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    k = d * rng.uniform(2.0, 8.0, (n_waves, 1))
+    phi = rng.uniform(0.0, 2.0 * np.pi, n_waves)
+    return lambda p: np.cos(np.asarray(p, dtype=np.float64) @ k.T + phi[None, :]).sum(1)
+
+
+def perturbed_icosphere(subdiv: int, seed: int, amp: float = 0.02):
+    """Icosphere with vertices moved radially by a factor 1 + amp * n(p),
+    n a seeded sum of plane waves scaled to max |n| = 1 over the vertices.
+    Returns (V float32, F int32, radius function r(unit direction))."""
+    V, F = icosphere(subdiv)
+    noise = radial_noise_fn(seed)
+    nv = noise(V)
+    scale = 1.0 / np.max(np.abs(nv))
+
+    def r(u):
+        return 1.0 + amp * scale * noise(u)
+
+    V = V * r(V)[:, None]
+    return V.astype(np.float32), F, r
+
+
+# ---------------------------------------------------------------- evaluation sets
+def grid_points(lo, hi, n: int) -> np.ndarray:
+    """Cell centres of an n x n grid over the box [lo, hi] (2D)."""
+    xs = lo[0] + (np.arange(n) + 0.5) * (hi[0] - lo[0]) / n
+    ys = lo[1] + (np.arange(n) + 0.5) * (hi[1] - lo[1]) / n
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    return np.stack([X.ravel(), Y.ravel()], 1)
+
+
+def random_in_star_body(n: int, r_fn, seed: int, shrink: float = 0.99) -> np.ndarray:
+    """Uniform points in the body {|p| <= shrink r(p/|p|)} (star-shaped about 0):
+    uniform direction, accepted with probability (r/r_max)^3, radius
+    shrink r xi^(1/3)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    have = 0
+    rmax = 1.0 + 0.021
+    while have < n:
+        m = 2 * (n - have) + 1024
+        d = rng.standard_normal((m, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        r = r_fn(d)
+        keep = rng.uniform(size=m) < (r / rmax) ** 3
+        d, r = d[keep], r[keep]
+        rad = shrink * r * rng.uniform(size=d.shape[0]) ** (1.0 / 3.0)
+        out.append(d * rad[:, None])
+        have += d.shape[0]
+    return np.concatenate(out)[:n]
+
+
+# ---------------------------------------------------------------- problem data
+def poly2d_coeffs(monomials: dict) -> list:
+    """{(i, j): c} for c x^i y^j -> POLY coefficient list (2D order)."""
+    out = []
+    for t in range(5):
+        for i in range(t, -1, -1):
+            out.append(float(monomials.get((i, t - i), 0.0)))
+    while out and out[-1] == 0.0 and len(out) > 1:
+        out.pop()
+    return out
+
+
+def poly3d_coeffs(monomials: dict) -> list:
+    """{(i, j, k): c} for c x^i y^j z^k -> POLY coefficient list (3D order)."""
+    out = []
+    for t in range(5):
+        for i in range(t, -1, -1):
+            for j in range(t - i, -1, -1):
+                out.append(float(monomials.get((i, j, t - i - j), 0.0)))
+    while out and out[-1] == 0.0 and len(out) > 1:
+        out.pop()
+    return out
+
+
+def gauss_coeffs(sigma: float, amps, centres) -> list:
+    out = [float(sigma)]
+    for a, c in zip(amps, centres):
+        out += [float(a)] + [float(x) for x in c]
+    return out
+
+
+def eval_terms(terms, dim: int, x: np.ndarray):
+    """Closed-form value and gradient of a term list at points x[n, dim]."""
+    x = np.asarray(x, dtype=np.float64)
+    val = np.zeros(x.shape[0])
+    grad = np.zeros((x.shape[0], dim))
+    for kind, coeffs in terms:
+        c = np.asarray(coeffs, dtype=np.float64)
+        if kind == POLY:
+            idx = 0
+            for t in range(5):
+                if dim == 2:
+                    exps = [(i, t - i) for i in range(t, -1, -1)]
+                else:
+                    exps = [(i, j, t - i - j) for i in range(t, -1, -1) for j in range(t - i, -1, -1)]
+                for e in exps:
+                    if idx >= c.size:
+                        break
+                    if c[idx] != 0.0:
+                        mono = np.prod([x[:, a] ** e[a] for a in range(dim)], 0)
+                        val += c[idx] * mono
+                        for a in range(dim):
+                            if e[a] > 0:
+                                ee = list(e)
+                                ee[a] -= 1
+                                grad[:, a] += c[idx] * e[a] * np.prod([x[:, b] ** ee[b] for b in range(dim)], 0)
+                    idx += 1
+        elif kind in (GAUSS, GAUSS_LAPLACIAN):
+            s = c[0]
+            per = 1 + dim
+            nb = (c.size - 1) // per
+            for k in range(nb):
+                A = c[1 + k * per]
+                ctr = c[2 + k * per: 2 + k * per + dim]
+                dx = x - ctr[None, :]
+                r2 = np.sum(dx * dx, 1)
+                e = np.exp(-r2 / (2 * s * s))
+                if kind == GAUSS:
+                    val += A * e
+                    grad += (A * e * (-1.0 / (s * s)))[:, None] * dx
+                else:
+                    q = r2 / s ** 4 - dim / s ** 2
+                    val += A * q * e
+                    dq = 2.0 / s ** 4
+                    grad += (A * e * (dq - q / (s * s)))[:, None] * dx
+        elif kind == EXP_TRIG:
+            A, al, be, ga = c[:4]
+            ez = np.exp(al * x[:, 2])
+            cx, sx = np.cos(be * x[:, 0]), np.sin(be * x[:, 0])
+            cy, sy = np.cos(ga * x[:, 1]), np.sin(ga * x[:, 1])
+            val += A * ez * cx * sy
+            grad[:, 0] += A * ez * (-be * sx) * sy
+            grad[:, 1] += A * ez * cx * (ga * cy)
+            grad[:, 2] += A * al * ez * cx * sy
+        else:
+            raise ValueError(f"unknown term kind {kind}")
+    return val, grad
+
+
+# ---------------------------------------------------------------- configurations
+@dataclass
+class Workload:
+    """One synthetic problem: mesh, data, cache sizes and evaluation set."""
+    name: str
+    dim: int
+    V: np.ndarray
+    F: np.ndarray
+    g: list
+    f: list
+    n_samples: int
+    walks: int
+    offset_l: float
+    eps: float
+    eval_pts: np.ndarray
+    src_grid: tuple = (0, 0)
+    exact: list | None = None          # closed-form solution terms, if any
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+
+def bbox_diagonal(V: np.ndarray) -> float:
+    return float(np.linalg.norm(V.max(0).astype(np.float64) - V.min(0).astype(np.float64)))
+
+
+def circle_laplace(n_samples: int = 1024, walks: int = 64, grid: int = 64, n_seg: int = 256,
+                   seed: int = 0) -> Workload:
+    """2D Laplace on the unit circle as a 256-gon; g = Re(z^3) = x^3 - 3xy^2
+    (harmonic, so u = g); 1024 samples offset l = 1e-3 inward x 64 walks;
+    u and grad u on a 64x64 grid clipped to r < 0.95.  The shell is l/5."""
+    V, F = circle_polygon(n_seg)
+    g = [(POLY, poly2d_coeffs({(3, 0): 1.0, (1, 2): -3.0}))]
+    pts = grid_points((-1.0, -1.0), (1.0, 1.0), grid)
+    pts = pts[np.sum(pts * pts, 1) < 0.95 ** 2]
+    l = 1e-3
+    return Workload("circle_laplace_256seg", 2, V, F, g, [], n_samples, walks, l, l / 5.0,
+                    pts.astype(np.float32), exact=g, seed=seed)
+
+
+def star_poisson(n_samples: int = 65536, walks: int = 256, grid: int = 1024, n_seg: int = 20000,
+                 src_grid=(256, 256), seed: int = 0, manufactured: bool = False,
+                 n_bumps: int = 8, sigma: float = 0.05) -> Workload:
+    """2D Poisson on a nonconvex 20k-segment star, r = 1 + 0.3 sin 7t + 0.05 n(t);
+    f = 8 Gaussian bumps (sigma 0.05, amplitudes U[-10,10], centres uniform in
+    the domain at distance >= 3 sigma from the boundary); g = x^2 - y^2;
+    65536 samples x 256 walks; 65536 source candidates; 1024^2 grid clipped to
+    the domain.  eps = 1e-3 x bbox diagonal, l = 5 eps.
+
+    ``manufactured=True`` keeps the geometry, sizes and bump centres but sets
+    u* = x^2 - y^2 + sum A_k exp(-|x-c_k|^2/(2 sigma^2)), f = Laplacian(u*),
+    g = u* on the boundary, so that the exact solution is known."""
+    V, F = star_polygon(n_seg, seed)
+    rng = np.random.default_rng(seed + 1)
+    amps = rng.uniform(-10.0, 10.0, n_bumps)
+    lo, hi = V.min(0).astype(np.float64), V.max(0).astype(np.float64)
+    centres = []
+    while len(centres) < n_bumps:
+        c = rng.uniform(lo, hi, (64, 2))
+        ok = inside_star_polygon(V, c)
+        c = c[ok]
+        if c.shape[0]:
+            d = distance_to_polygon(V, c)
+            c = c[d >= 3.0 * sigma]
+        centres += [tuple(p) for p in c[: n_bumps - len(centres)]]
+    centres = np.asarray(centres)
+    quad = [(POLY, poly2d_coeffs({(2, 0): 1.0, (0, 2): -1.0}))]
+    bumps = gauss_coeffs(sigma, amps, centres)
+    if manufactured:
+        g = quad + [(GAUSS, bumps)]
+        f = [(GAUSS_LAPLACIAN, bumps)]
+        exact = g
+    else:
+        g = quad
+        f = [(GAUSS, bumps)]
+        exact = None
+    pts = grid_points(lo, hi, grid)
+    pts = pts[inside_star_polygon(V, pts)]
+    eps = 1e-3 * bbox_diagonal(V)
+    name = "star_poisson_20kseg" + ("_manufactured" if manufactured else "")
+    return Workload(name, 2, V, F, g, f, n_samples, walks, 5.0 * eps, eps, pts.astype(np.float32),
+                    src_grid=tuple(src_grid), exact=exact, seed=seed,
+                    meta={"amps": amps, "centres": centres, "sigma": sigma})
+
+
+def icosphere_laplace(subdiv: int = 8, n_samples: int = 262144, walks: int = 128, plane: int = 512,
+                      n_random: int = 1_000_000, seed: int = 0) -> Workload:
+    """3D Laplace on a perturbed icosphere (subdivision 8: 1,310,720 triangles,
+    radial noise 2%); g = exp(0.5 z) cos(0.3 x) sin(0.4 y) (harmonic);
+    262144 samples x 128 walks; evaluate a 512 x 512 slice plane z = 0 plus
+    1M uniform random interior points.  eps = 1e-3 x bbox diagonal, l = 5 eps."""
+    V, F, r = perturbed_icosphere(subdiv, seed)
+    g = [(EXP_TRIG, [1.0, 0.5, 0.3, 0.4])]
+    lo, hi = V.min(0).astype(np.float64), V.max(0).astype(np.float64)
+    pl = grid_points(lo[:2], hi[:2], plane)
+    pl3 = np.concatenate([pl, np.zeros((pl.shape[0], 1))], 1)
+    rad = np.linalg.norm(pl3, axis=1)
+    u = pl3 / np.maximum(rad, 1e-30)[:, None]
+    pl3 = pl3[rad < r(u) * (1.0 - 1e-5)]
+    rnd = random_in_star_body(n_random, r, seed + 7)
+    pts = np.concatenate([pl3, rnd]).astype(np.float32)
+    eps = 1e-3 * bbox_diagonal(V)
+    return Workload(f"icosphere{subdiv}_laplace", 3, V, F, g, [], n_samples, walks, 5.0 * eps, eps, pts,
+                    exact=g, seed=seed, meta={"n_plane": pl3.shape[0], "n_random": rnd.shape[0]})

@@ -1,0 +1,40 @@
+"""Alg. 1 (UpdateSolution + GetSolution) composed from the oracle's steps.
+
+Test helper: builds one boundary cache (and source cache) with the oracle and
+evaluates u, grad u at points.  The cache positions and normals are rounded
+to FP32 before the walks and the gather, as the library stores them.
+"""
+import numpy as np
+
+import oracle
+
+
+def oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid=None, max_steps=1 << 14, bvh=None):
+    bvh = bvh or oracle.BVH(V, F)
+    z, n, e = oracle.sample_boundary(V, F, N, l, seed)
+    z32, n32 = z.astype(np.float32), n.astype(np.float32)
+    out = oracle.walks(bvh, g, f, z32, W, eps, max_steps, seed, id_base=0, tag=oracle.TAG_WALK)
+    u_hat, q_hat = oracle.reduce_walks(out["U"], out["grad"], n32, W)
+    cache = {"z": z32, "n": n32, "u_hat": u_hat, "q_hat": q_hat, "elem": e,
+             "measure": oracle.boundary_measure(V, F), "walks": out, "N": N,
+             "y": None, "c": None, "n_src": 0}
+    if f and src_grid is not None:
+        y, c, ncand = oracle.sample_source2d(V, F, src_grid, seed, f)
+        cache.update(y=y, c=c, n_src=ncand)
+    return cache
+
+
+def oracle_evaluate(cache, pts):
+    ub, us, gb, gs = oracle.gather(cache["z"], cache["n"], cache["u_hat"], cache["q_hat"], cache["measure"],
+                                   pts, cache["y"], cache["c"])
+    u = ub / cache["N"]
+    grad = gb / cache["N"]
+    if cache["n_src"]:
+        u = u + us / cache["n_src"]
+        grad = grad + gs / cache["n_src"]
+    return u, grad
+
+
+def oracle_bvc(V, F, g, f, N, W, l, eps, pts, seed, src_grid=None, max_steps=1 << 14, bvh=None):
+    cache = oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid, max_steps, bvh)
+    return oracle_evaluate(cache, pts)
