@@ -1,0 +1,287 @@
+/*
+ * bvc.h -- C ABI of the GB300 (sm_103a) Boundary Value Caching library.
+ *
+ * Method: Miller, Sawhney, Crane, Gkioulekas, "Boundary Value Caching for
+ * Walk on Spheres", ACM TOG 42(4), SIGGRAPH 2023.  The library solves
+ *     Laplacian(u) = f in Omega,  u = g on the boundary      (Eq. 1, sigma = 0,
+ *                                                            Dirichlet only)
+ * by the paper's cache (Alg. 1): walk on spheres (Sec. 3.1) estimates u and
+ * du/dn at samples of an inward-offset boundary (Sec. 3.2); the boundary
+ * integral equation (Eq. 2) is then evaluated at interior points by the
+ * Monte Carlo sums of Eq. 3-6.
+ *
+ * Conventions for every entry point:
+ *  - Plain pointers and sizes only.  "device" pointers are CUDA device
+ *    memory owned by the caller (the library never frees them); "host"
+ *    pointers are read during the call only.
+ *  - Point arrays are structure-of-arrays: a [dim][count] float array,
+ *    coordinate a of point i at index a*count + i.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL means
+ *    the legacy default stream).  Argument errors are returned synchronously
+ *    and enqueue nothing.  Errors raised inside kernels (a wait that ran out,
+ *    walks stopped at max_steps) are latched in the geometry's device status
+ *    word; read it with bvc_geometry_stats.
+ *  - Randomness is Philox-4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
+ *    seed, counter = (id low, id high, word2, tag); tags: 0 cache walks,
+ *    1 boundary samples, 2 source samples, 3 pointwise walks.  Results are
+ *    bit-reproducible for a given seed and launch-independent.
+ *  - The functions g and f are sums of closed-form terms (bvc_function);
+ *    they stand in for the paper's callbacks (Sec. 4 "Setup").
+ *  - Nothing here allocates device memory except bvc_geometry_create, which
+ *    owns the BVH until bvc_geometry_destroy.  Scratch memory is passed in
+ *    as a workspace; each *_workspace_size call says how much is needed.
+ */
+#ifndef BVC_H_
+#define BVC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* bvc_stream;
+
+typedef enum {
+  BVC_OK = 0,
+  BVC_ERR_INVALID_ARG = 1,     /* null pointer, bad size or dimension */
+  BVC_ERR_DEGENERATE_MESH = 2, /* non-finite vertex, index out of range, zero-measure element */
+  BVC_ERR_OOM = 3,             /* device allocation failed (geometry only) */
+  BVC_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+  BVC_ERR_TIMEOUT = 5,         /* a bounded in-kernel wait ran out (device status) */
+  BVC_ERR_UNSUPPORTED = 6,     /* valid request the library does not implement */
+  BVC_ERR_WORKSPACE = 7,       /* workspace too small for even one chunk */
+  BVC_WARN_WALK_CAP = 8        /* some walks stopped at max_steps (device status) */
+} bvc_status;
+
+/* ------------------------------------------------------------------ g, f */
+/* A problem function (g or f of Eq. 1) is a sum of up to BVC_MAX_TERMS
+ * closed-form terms; coefficients are read on the host during the call.
+ *   BVC_FN_POLY: monomials x^i y^j (z^k) of total degree <= 4, ordered by
+ *     degree t = 0..4, then i = t..0, then (3D) j = t-i..0; up to 15 (2D) or
+ *     35 (3D) coefficients, missing trailing ones are zero.
+ *   BVC_FN_GAUSS: [s, A_1, c_1 (dim), A_2, c_2, ...] ->
+ *     sum_k A_k exp(-|x - c_k|^2 / (2 s^2)).
+ *   BVC_FN_GAUSS_LAPLACIAN: same coefficients -> the Laplacian of GAUSS,
+ *     sum_k A_k (|x - c_k|^2 / s^4 - dim / s^2) exp(-|x - c_k|^2 / (2 s^2)).
+ *   BVC_FN_EXP_TRIG (3D): [A, alpha, beta, gamma] ->
+ *     A exp(alpha z) cos(beta x) sin(gamma y).
+ * The total coefficient count over all terms is at most BVC_MAX_COEFFS. */
+#define BVC_MAX_TERMS 4
+#define BVC_MAX_COEFFS 120
+typedef enum { BVC_FN_POLY = 1, BVC_FN_GAUSS = 2, BVC_FN_GAUSS_LAPLACIAN = 3, BVC_FN_EXP_TRIG = 4 } bvc_fn_kind;
+typedef struct {
+  int32_t kind;
+  int32_t n_coeffs;
+  const double* coeffs; /* host */
+} bvc_term;
+typedef struct {
+  int32_t n_terms; /* 0 = the zero function */
+  bvc_term terms[BVC_MAX_TERMS];
+} bvc_function;
+
+/* -------------------------------------------------------------- geometry */
+/* Boundary mesh and its closest-point BVH (Sec. 4 "Setup": a bounding
+ * volume hierarchy answers the closest-point queries of walk on spheres).
+ * dim = 2: counter-clockwise polygon(s), prims = segment vertex pairs.
+ * dim = 3: triangles wound counter-clockwise seen from outside.
+ * verts: host float[n_verts][dim] (row-major); prims: host int32[n_prims][dim].
+ * Validation: finite vertices, indices in range, no zero-length or
+ * zero-area element (BVC_ERR_DEGENERATE_MESH).  The BVH is built on the host
+ * (binned SAH) and copied to device memory the handle owns; the copy is
+ * enqueued on `stream` and the call returns once it is complete.  The
+ * handle also holds the element-measure CDF used by boundary sampling
+ * (Sec. 4 "Sampling") and a small device status/statistics block. */
+typedef struct bvc_geometry_s* bvc_geometry;
+
+bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
+                               int64_t n_prims, bvc_stream stream, bvc_geometry* out);
+bvc_status bvc_geometry_destroy(bvc_geometry g);
+
+typedef struct {
+  int32_t dim;
+  int64_t n_verts, n_prims, n_nodes;
+  double boundary_measure; /* |dOmega|: total length (2D) or area (3D), FP64 sequential sum */
+  float bbox_lo[3], bbox_hi[3];
+  size_t device_bytes; /* device memory owned by the handle */
+} bvc_geometry_info;
+bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* info);
+
+/* Device status/statistics block: out[0] total walk steps (closest-point
+ * queries made by walks), out[1] walks stopped at max_steps, out[2] error
+ * flags (bit 0: timeout), out[3] reserved.  Synchronises `stream`.  With
+ * reset != 0 the block is cleared after reading.  Returns BVC_ERR_TIMEOUT if
+ * the error bit is set, BVC_WARN_WALK_CAP if capped walks were seen. */
+bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[4], int32_t reset, bvc_stream stream);
+
+/* Closest boundary point of m query points (the query WoS makes each step,
+ * Sec. 3.1).  pts: device [dim][m].  d2: device float[m], squared distance;
+ * prim: device int32[m], index of the closest element in the caller's
+ * numbering (ties -> lowest index); cp: device float[dim][m] closest points
+ * or NULL.  The distance is the canonical FP32 expression documented in
+ * csrc/bvc_device.cuh, so the chosen index is reproducible bit for bit. */
+bvc_status bvc_query_closest(bvc_geometry g, const float* pts, int64_t m, float* d2, int32_t* prim, float* cp,
+                             bvc_stream stream);
+
+/* Flag evaluation points closer than `l` to the boundary (Sec. 3.2: such
+ * points get pointwise walk-on-spheres estimates instead of the cache).
+ * near: device uint8[m], 1 if distance < l. */
+bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_t m, float l, uint8_t* near,
+                             bvc_stream stream);
+
+/* ----------------------------------------------------- cache build steps */
+/* K1 -- boundary samples (Alg. 1 "b.z, b.n_z ~ p", Sec. 4 "Sampling",
+ * Sec. 3.2 offset).  Sample i draws Philox(id = i, word2 = 0, tag = 1) ->
+ * (u0, u1, u2); s = (i + u0)/n selects the element by the FP64 CDF of
+ * element measures (stratified); in 2D the remainder of s inside the
+ * element is the arclength position, in 3D (u1, u2) place the point
+ * uniformly on the triangle (barycentrics 1 - sqrt(u1), sqrt(u1)(1 - u2),
+ * sqrt(u1) u2).  Output z = p - l n (FP64 arithmetic, rounded to FP32),
+ * n the outward unit normal of the element; p = 1/|dOmega|.
+ * z, nrm: device float[dim][n]; elem: device int32[n] or NULL. */
+bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
+                               int32_t* elem, bvc_stream stream);
+
+/* K2 / K6 -- walks on spheres (Sec. 3.1) from n start points, `walks` each;
+ * walk j of start i has id = id_base + i*walks + j and step k draws
+ * Philox(id, word2 = k, tag).  Each step: closest point (distance R); stop
+ * if R < eps (return g at the closest point) or after max_steps queries;
+ * else direction w uniform on the sphere, source point y = x + R u2 w with
+ * weights w_u = -R rho ln(R/rho) (2D) or -rho(R - rho) (3D) on f(y) (ball
+ * Green's function), and x += R w.  The first step also gives the gradient
+ * estimate of Eq. 7 with control variate g(closest point of the start):
+ *   grad = w0 [ (dim/R0)(U - w_u,0 f(y0) - g(pbar0)) - R0 (1 - (rho0/R0)^dim) f(y0) ].
+ * Output per walk t (t = i*walks + j), FP32, structure of arrays:
+ *   rec[t]                    U (estimate of u at the start)
+ *   rec[n*walks*(1+a) + t]    if nrm != NULL: a = 0 only, n_i . grad (du/dn);
+ *                             else a = 0..dim-1, grad component a.
+ * starts, nrm: device float[dim][n]; rec: device float[(1 + planes) * n * walks]
+ * with planes = 1 (nrm given) or dim.  steps, prim: device int32[n*walks] or
+ * NULL (per-walk step count and last closest element, for replay checks).
+ * Step totals and capped-walk counts go to the geometry's status block,
+ * whose spare word also serves as this call's work counter: bvc_walk calls
+ * on one geometry must not overlap on the GPU (the chunked drivers below
+ * keep their counter in their workspace instead). */
+bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* starts,
+                    const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                    uint64_t id_base, uint32_t tag, float* rec, int32_t* steps, int32_t* prim, bvc_stream stream);
+
+/* K3 -- per-start reduction of walk records (Alg. 1: the pointwise
+ * estimates of a boundary sample).  rec as written by bvc_walk with
+ * `planes` extra planes.  mode 0: out[p][i] = mean_j rec[p][i*walks + j];
+ * mode 1: out[p][i] += sum_j rec[p][i*walks + j] (progressive sums).
+ * out: device double[(1 + planes)][n].  Deterministic fixed-order FP64 sums. */
+bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walks, int32_t planes, int32_t mode, double* out,
+                            bvc_stream stream);
+
+/* The boundary and source caches (Alg. 1 boundarySamples / sourceSamples).
+ * All arrays are caller-owned device memory of the stated sizes. */
+typedef struct {
+  int32_t dim;
+  int64_t n;            /* N boundary samples */
+  float* z;             /* [dim][n] sample positions on the offset boundary */
+  float* nrm;           /* [dim][n] unit outward normals */
+  double* u_hat;        /* [n] estimates of u */
+  double* dudn_hat;     /* [n] estimates of du/dn */
+  float* packed;        /* [n][8] (2D) or [n][12] (3D) gather tiles, written by bvc_cache_pack */
+  double bnd_measure;   /* |dOmega| = 1/p of the boundary samples */
+  int64_t n_src_cand;   /* source candidates M (denominator of Eq. 4/6); 0 = no source cache */
+  float* src_y;         /* [dim][n_src_cand] kept source points (first n_src_dev[0] valid) */
+  double* src_c;        /* [n_src_cand] f(y) / p for kept points */
+  float* src_packed;    /* [n_src_cand][4] gather tiles */
+  int64_t* n_src_dev;   /* [1] number of kept source samples (written on device) */
+} bvc_cache;
+
+/* K4 -- source samples (Alg. 1 "y ~ p^R", Sec. 4 "Sampling"): a jittered
+ * grid[0] x grid[1] grid of candidates over the boundary's bounding box;
+ * candidate c draws Philox(id = c, word2 = 0, tag = 2) for its position in
+ * its cell; it is kept when the canonical FP32 crossing test puts it inside
+ * the polygon.  With p = 1/|box| on the box times the indicator of Omega,
+ * a kept sample carries c = f(y) |box| and the estimator divides by the
+ * candidate count.  Kept samples are stored in candidate order.  2D only
+ * (BVC_ERR_UNSUPPORTED in 3D).  Requires cache->n_src_cand = grid[0]*grid[1].
+ * Workspace: bvc_sample_source_workspace_size. */
+bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes);
+bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[2], uint64_t seed,
+                             bvc_cache* cache, void* workspace, size_t workspace_bytes, bvc_stream stream);
+
+/* Pack z, nrm, u_hat, dudn_hat (and the kept source samples) into the
+ * gather's tile layout, folding 1/p and the Green's function constants of
+ * App. A into the per-sample coefficients. */
+bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream);
+
+typedef struct {
+  int64_t n_samples;        /* N */
+  int32_t walks_per_sample; /* nWalks of Alg. 1 */
+  int32_t max_steps;        /* cap on closest-point queries per walk (e.g. 1 << 14) */
+  double offset_l;          /* Sec. 3.2 offset l > eps */
+  double eps;               /* epsilon shell width */
+  uint64_t seed;
+  uint64_t walk_id_base;    /* first walk id: distinct caches of one seed use disjoint ranges */
+  int32_t src_grid[2];      /* source candidate grid, {0,0} = no source cache */
+} bvc_cache_opts;
+
+/* The whole cache: K1 -> K2 (chunked through the workspace) -> K3 -> K4 -> pack.
+ * cache->n must equal opts->n_samples; n_src_cand must equal the grid size.
+ * Any workspace of at least bvc_cache_build_workspace_size(min) bytes works;
+ * larger ones (up to `full`) run the walks in fewer chunks. */
+bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+                                          size_t* full_bytes);
+bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                           const bvc_cache_opts* opts, bvc_cache* cache, void* workspace, size_t workspace_bytes,
+                           bvc_stream stream);
+
+/* ------------------------------------------------------------ evaluation */
+/* Running sums of Alg. 1's EvaluationPoint for m points (every point of a
+ * set receives the same samples, so the counts are kept once per set). */
+typedef struct {
+  int32_t dim;
+  int64_t m;
+  const float* x;   /* [dim][m] evaluation points */
+  double* u_bnd;    /* [m] sum of boundary terms (Eq. 3 numerators) */
+  double* u_src;    /* [m] sum of source terms (Eq. 4) */
+  double* grad_bnd; /* [dim][m] Eq. 5 sums, or NULL */
+  double* grad_src; /* [dim][m] Eq. 6 sums, or NULL */
+  int64_t* counts;  /* [2] N and M accumulated so far */
+} bvc_eval_state;
+
+/* K5 -- the all-pairs gather (Alg. 1 splat loops, Eq. 3-6): adds every
+ * cache sample's contribution to every point's sums and adds N and M to the
+ * counts.  Cache tiles are staged in shared memory by bulk asynchronous
+ * copies (TMA); pair terms are FP32, partial sums over at most 128 samples
+ * are flushed to FP64.  Workspace: bvc_evaluate_workspace_size. */
+bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const bvc_eval_state* state, size_t* bytes);
+bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state, void* workspace, size_t workspace_bytes,
+                        bvc_stream stream);
+
+/* a6 -- Alg. 1 GetSolution: u = u_bnd/N + u_src/M (a term is dropped when
+ * its count is 0); grad likewise.  u: device double[m]; grad: device
+ * double[dim][m] or NULL. */
+bvc_status bvc_get_solution(const bvc_eval_state* state, double* u, double* grad, bvc_stream stream);
+
+/* K6 -- pointwise walk on spheres at m points (the comparison estimator,
+ * and the estimate used within l of the boundary, Sec. 3.2): `walks` walks
+ * per point with tag 3, ids id_base + k*walks + j.  Adds the FP64 sums of
+ * the walks' U and gradient estimates: u_sum[k] += sum_j U, grad_sum[a][k]
+ * += sum_j grad_a (grad_sum may be NULL).  Workspace chunks the walks. */
+bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
+                                       size_t* full_bytes);
+bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* pts,
+                        int64_t m, int32_t walks, float eps, int32_t max_steps, uint64_t seed, uint64_t id_base,
+                        double* u_sum, double* grad_sum, void* workspace, size_t workspace_bytes,
+                        bvc_stream stream);
+
+/* Gather device status word (bit 0: a bounded wait for a tile copy ran
+ * out).  Synchronises the device; reset != 0 clears it. */
+bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
+
+/* ------------------------------------------------------------------ misc */
+const char* bvc_status_string(bvc_status s);
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t bvc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BVC_H_ */

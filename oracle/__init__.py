@@ -72,10 +72,10 @@ def _load():
                 "orc_bvh_closest": (None, [P, P, i64, P, P, P]),
                 "orc_boundary_measure": (f64, [C.c_int, P, P, i64]),
                 "orc_sample_boundary": (None, [C.c_int, P, P, i64, i64, f64, u64, P, P, P]),
-                "orc_walks": (None, [P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P]),
+                "orc_walks": (None, [P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_reduce_walks": (None, [C.c_int, i64, i32, P, P, P, P, P]),
                 "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P]),
-                "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P]),
+                "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
                 "orc_sphere_step": (None, [C.c_int, f64, f64, f64, f64, P, P, P, P]),
                 "orc_num_threads": (C.c_int, []),
             }
@@ -231,7 +231,9 @@ def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int
           id_base: int = 0, tag: int = TAG_WALK, want_pend: bool = False):
     """Sec. 3.1 / Eq. 7: W walks from each FP32 start point.
 
-    Returns dict with per-walk U, grad[.., dim], steps, prim (and pend)."""
+    Returns dict with per-walk U, grad[.., dim], steps, prim, scale[.., 2]
+    (magnitudes of the terms forming U and the gradient, for error scaling)
+    and, if asked, pend (final closest point)."""
     lib = _load()
     starts = _f32(starts)
     n, dim = starts.shape
@@ -239,11 +241,12 @@ def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int
     U, grad = np.zeros(T), np.zeros((T, dim))
     steps, prim = np.zeros(T, np.int32), np.zeros(T, np.int32)
     pend = np.zeros((T, dim)) if want_pend else None
+    scale = np.zeros((T, 2))
     g = encode_function(g_terms)
     f = encode_function(f_terms)
     lib.orc_walks(bvh.h, _p(g), _p(f), _p(starts), n, int(W), float(eps), int(max_steps), int(seed),
-                  int(id_base), int(tag), _p(U), _p(grad), _p(steps), _p(prim), _p(pend))
-    out = {"U": U, "grad": grad, "steps": steps, "prim": prim}
+                  int(id_base), int(tag), _p(U), _p(grad), _p(steps), _p(prim), _p(pend), _p(scale))
+    out = {"U": U, "grad": grad, "steps": steps, "prim": prim, "scale": scale}
     if want_pend:
         out["pend"] = pend
     return out
@@ -276,8 +279,11 @@ def sample_source2d(V, F, grid, seed: int, f_terms):
     return y[:kept].copy(), c[:kept].copy(), G0 * G1
 
 
-def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None):
-    """Eq. 3-6 / Alg. 1 splat: FP64 running sums (u_bnd, u_src, g_bnd, g_src)."""
+def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs: bool = False):
+    """Eq. 3-6 / Alg. 1 splat: FP64 running sums (u_bnd, u_src, g_bnd, g_src).
+
+    With want_abs, also the per-point sums of |term| (for error scaling):
+    array [M, 2 + 2 dim] = [u_bnd, g_bnd(dim), u_src, g_src(dim)]."""
     lib = _load()
     z, nz, x = _f64(z), _f64(nz), _f64(x)
     dim = x.shape[1]
@@ -289,6 +295,9 @@ def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None):
     y, c = _f64(y), _f64(c)
     ub, us = np.zeros(M), np.zeros(M)
     gb, gs = np.zeros((M, dim)), np.zeros((M, dim))
+    ab = np.zeros((M, 2 + 2 * dim)) if want_abs else None
     lib.orc_gather(dim, N, _p(z), _p(nz), _p(u_hat), _p(q_hat), float(bnd_measure), y.shape[0], _p(y), _p(c),
-                   M, _p(x), _p(ub), _p(us), _p(gb), _p(gs))
+                   M, _p(x), _p(ub), _p(us), _p(gb), _p(gs), _p(ab))
+    if want_abs:
+        return ub, us, gb, gs, ab
     return ub, us, gb, gs

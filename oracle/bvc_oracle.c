@@ -743,12 +743,12 @@ void orc_sphere_step(int dim, double R, double u0, double u1, double u2, double*
 }
 
 static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double* U_out, double* grad_out,
-                     int32_t* steps_out, int32_t* prim_out, double* pend_out) {
+                     int32_t* steps_out, int32_t* prim_out, double* pend_out, double* scale_out) {
   const int dim = w->bvh->m.dim;
   const int has_f = !fn_is_zero(w->f);
   double x[3] = {0, 0, 0}, pbar[3] = {0, 0, 0}, nu[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) x[a] = x0[a];
-  double usrc = 0.0, wf0 = 0.0, wg0 = 0.0, R0 = 0.0, cv = 0.0;
+  double usrc = 0.0, uabs = 0.0, wf0 = 0.0, wg0 = 0.0, R0 = 0.0, cv = 0.0;
   int k = 0;
   int64_t prim = -1;
   for (;;) {
@@ -766,6 +766,7 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
       for (int a = 0; a < dim; ++a) y[a] = x[a] + rho * om[a];
       const double fy = orc_fn_eval(w->f, dim, y);
       usrc += wu * fy;
+      uabs += fabs(wu * fy);
       if (k == 1) {
         wf0 = wu * fy;
         wg0 = wg * fy;
@@ -777,8 +778,14 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
     }
     for (int a = 0; a < dim; ++a) x[a] += R * om[a];
   }
-  const double U = orc_fn_eval(w->g, dim, pbar) + usrc;
+  const double gend = orc_fn_eval(w->g, dim, pbar);
+  const double U = gend + usrc;
   *U_out = U;
+  /* magnitudes of the terms that form U and the gradient (test scaling only) */
+  if (scale_out) {
+    scale_out[0] = fabs(gend) + uabs;
+    scale_out[1] = k == 1 ? 0.0 : ((double)dim / R0) * (fabs(gend) + uabs + fabs(wf0) + fabs(cv)) + fabs(wg0);
+  }
   if (k == 1) {
     for (int a = 0; a < dim; ++a) grad_out[a] = 0.0;
   } else {
@@ -796,7 +803,7 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
 /* steps[n*W], prim[n*W], pend[n*W*dim] (pend may be NULL).                  */
 void orc_walks(void* bvh, const double* g, const double* f, const float* starts, int64_t n, int32_t W, double eps,
                int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
-               int32_t* steps, int32_t* prim, double* pend) {
+               int32_t* steps, int32_t* prim, double* pend, double* scale) {
   walk_ctx_t w = {(const obvh_t*)bvh, g, f, eps, max_steps, seed, tag};
   const int dim = w.bvh->m.dim;
   const int64_t total = n * (int64_t)W;
@@ -806,7 +813,7 @@ void orc_walks(void* bvh, const double* g, const double* f, const float* starts,
     double x0[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) x0[a] = starts[i * dim + a];
     walk_one(&w, x0, id_base + (uint64_t)t, &U[t], &grad[t * dim], &steps[t], &prim[t],
-             pend ? &pend[t * dim] : NULL);
+             pend ? &pend[t * dim] : NULL, scale ? &scale[2 * t] : NULL);
   }
 }
 
@@ -879,12 +886,14 @@ int64_t orc_sample_source2d(const float* V, int64_t nv, const int32_t* F, int64_
 /* ------------------------------------------------------------------------ */
 void orc_gather(int dim, int64_t N, const double* z, const double* nz, const double* u_hat, const double* q_hat,
                 double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M, const double* x,
-                double* u_bnd, double* u_src, double* g_bnd, double* g_src) {
+                double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t k = 0; k < M; ++k) {
     double xk[3] = {0, 0, 0}, zz[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, G[8];
     for (int a = 0; a < dim; ++a) xk[a] = x[k * dim + a];
     double ub = 0.0, us = 0.0, gb[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
+    /* sums of |term| (test scaling only): [u_bnd, g_bnd(dim), u_src, g_src(dim)] */
+    double ab[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t i = 0; i < N; ++i) {
       for (int a = 0; a < dim; ++a) {
         zz[a] = z[i * dim + a];
@@ -892,17 +901,29 @@ void orc_gather(int dim, int64_t N, const double* z, const double* nz, const dou
       }
       orc_green(dim, xk, zz, nn, G);
       const double dGdn = G[1 + dim];
-      ub += (dGdn * u_hat[i] - G[0] * q_hat[i]) * bnd_measure;
-      for (int a = 0; a < dim; ++a) gb[a] += (G[2 + dim + a] * u_hat[i] - G[1 + a] * q_hat[i]) * bnd_measure;
+      const double tu = (dGdn * u_hat[i] - G[0] * q_hat[i]) * bnd_measure;
+      ub += tu;
+      ab[0] += fabs(tu);
+      for (int a = 0; a < dim; ++a) {
+        const double tg = (G[2 + dim + a] * u_hat[i] - G[1 + a] * q_hat[i]) * bnd_measure;
+        gb[a] += tg;
+        ab[1 + a] += fabs(tg);
+      }
     }
     for (int64_t j = 0; j < Ms; ++j) {
       for (int a = 0; a < dim; ++a) zz[a] = y[j * dim + a];
       orc_green(dim, xk, zz, nn, G);
       us += G[0] * c[j];
-      for (int a = 0; a < dim; ++a) gs[a] += G[1 + a] * c[j];
+      ab[1 + dim] += fabs(G[0] * c[j]);
+      for (int a = 0; a < dim; ++a) {
+        gs[a] += G[1 + a] * c[j];
+        ab[2 + dim + a] += fabs(G[1 + a] * c[j]);
+      }
     }
     u_bnd[k] = ub;
     u_src[k] = us;
+    if (abs_out)
+      for (int q = 0; q < 2 + 2 * dim; ++q) abs_out[k * (2 + 2 * dim) + q] = ab[q];
     for (int a = 0; a < dim; ++a) {
       if (g_bnd) g_bnd[k * dim + a] = gb[a];
       if (g_src) g_src[k * dim + a] = gs[a];

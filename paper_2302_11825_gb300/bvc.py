@@ -1,0 +1,434 @@
+"""Thin ctypes binding of ``libbvc.so`` (C ABI in ``include/bvc.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory (tensors) and streams.  The
+library is loaded from ``paper_2302_11825_gb300/_build/libbvc.so``; if it is
+missing it is built with nvcc, and if that is impossible the first call
+raises -- there is no CPU fallback.
+
+Point arrays are structure-of-arrays tensors of shape ``(dim, count)``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_DEGENERATE_MESH, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_WORKSPACE, \
+    WARN_WALK_CAP = range(9)
+FN_POLY, FN_GAUSS, FN_GAUSS_LAPLACIAN, FN_EXP_TRIG = 1, 2, 3, 4
+MAX_TERMS = 4
+TAG_WALK, TAG_BOUNDARY, TAG_SOURCE, TAG_POINTWISE = 0, 1, 2, 3
+
+
+class BvcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class Term(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_coeffs", C.c_int32), ("coeffs", C.POINTER(C.c_double))]
+
+
+class Function(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("terms", Term * MAX_TERMS)]
+
+
+class GeometryInfo(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_verts", C.c_int64), ("n_prims", C.c_int64), ("n_nodes", C.c_int64),
+                ("boundary_measure", C.c_double), ("bbox_lo", C.c_float * 3), ("bbox_hi", C.c_float * 3),
+                ("device_bytes", C.c_size_t)]
+
+
+class CacheStruct(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("z", C.c_void_p), ("nrm", C.c_void_p),
+                ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p), ("packed", C.c_void_p),
+                ("bnd_measure", C.c_double), ("n_src_cand", C.c_int64), ("src_y", C.c_void_p),
+                ("src_c", C.c_void_p), ("src_packed", C.c_void_p), ("n_src_dev", C.c_void_p)]
+
+
+class CacheOpts(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("walks_per_sample", C.c_int32), ("max_steps", C.c_int32),
+                ("offset_l", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64),
+                ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 2)]
+
+
+class EvalStateStruct(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("m", C.c_int64), ("x", C.c_void_p), ("u_bnd", C.c_void_p),
+                ("u_src", C.c_void_p), ("grad_bnd", C.c_void_p), ("grad_src", C.c_void_p),
+                ("counts", C.c_void_p)]
+
+
+def _declare(lib):
+    P, i32, i64, u32, u64, f32, f64, sz = (C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float,
+                                          C.c_double, C.c_size_t)
+    S = C.c_int
+    sig = {
+        "bvc_geometry_create": (S, [i32, P, i64, P, i64, P, C.POINTER(C.c_void_p)]),
+        "bvc_geometry_destroy": (S, [P]),
+        "bvc_geometry_get_info": (S, [P, C.POINTER(GeometryInfo)]),
+        "bvc_geometry_stats": (S, [P, C.POINTER(C.c_uint64), i32, P]),
+        "bvc_query_closest": (S, [P, P, i64, P, P, P, P]),
+        "bvc_classify_near": (S, [P, P, i64, f32, P, P]),
+        "bvc_sample_boundary": (S, [P, i64, f64, u64, P, P, P, P]),
+        "bvc_walk": (S, [P, C.POINTER(Function), C.POINTER(Function), P, P, i64, i32, f32, i32, u64, u64, u32, P, P,
+                         P, P]),
+        "bvc_reduce_walks": (S, [P, i64, i32, i32, i32, P, P]),
+        "bvc_sample_source_workspace_size": (S, [i64, C.POINTER(sz)]),
+        "bvc_sample_source": (S, [P, C.POINTER(Function), C.POINTER(C.c_int32), u64, C.POINTER(CacheStruct), P, sz,
+                                  P]),
+        "bvc_cache_pack": (S, [C.POINTER(CacheStruct), P]),
+        "bvc_cache_build_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz), C.POINTER(sz)]),
+        "bvc_cache_build": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(CacheOpts),
+                                C.POINTER(CacheStruct), P, sz, P]),
+        "bvc_evaluate_workspace_size": (S, [C.POINTER(CacheStruct), C.POINTER(EvalStateStruct), C.POINTER(sz)]),
+        "bvc_evaluate": (S, [C.POINTER(CacheStruct), C.POINTER(EvalStateStruct), P, sz, P]),
+        "bvc_get_solution": (S, [C.POINTER(EvalStateStruct), P, P, P]),
+        "wos_estimate_workspace_size": (S, [i32, i64, i32, C.POINTER(sz), C.POINTER(sz)]),
+        "wos_estimate": (S, [P, C.POINTER(Function), C.POINTER(Function), P, i64, i32, f32, i32, u64, u64, P, P, P,
+                             sz, P]),
+        "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
+        "bvc_status_string": (C.c_char_p, [S]),
+        "bvc_version": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def lib():
+    """The loaded CUDA library (built in-tree on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or _build._stale(path):
+                path = _build.build()
+            handle = C.CDLL(path)
+            _declare(handle)
+            _lib = handle
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def status_string(s: int) -> str:
+    return lib().bvc_status_string(int(s)).decode()
+
+
+def _check(status: int, what: str, allow=(OK,)):
+    if status not in allow:
+        raise BvcError(status, what)
+    return status
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def make_function(terms) -> Function:
+    """[(kind, coeffs), ...] -> bvc_function (the coefficient arrays are kept
+    alive on the returned structure)."""
+    f = Function()
+    terms = list(terms or [])
+    if len(terms) > MAX_TERMS:
+        raise ValueError("too many terms")
+    f.n_terms = len(terms)
+    keep = []
+    for i, (kind, coeffs) in enumerate(terms):
+        arr = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64).ravel())
+        keep.append(arr)
+        f.terms[i].kind = int(kind)
+        f.terms[i].n_coeffs = int(arr.size)
+        f.terms[i].coeffs = arr.ctypes.data_as(C.POINTER(C.c_double))
+    f._keep = keep
+    return f
+
+
+def soa(points, device="cuda") -> torch.Tensor:
+    """(count, dim) array -> contiguous (dim, count) float32 CUDA tensor."""
+    a = np.ascontiguousarray(np.asarray(points, dtype=np.float32).T)
+    return torch.from_numpy(a).to(device)
+
+
+# ---------------------------------------------------------------- geometry
+class Geometry:
+    """bvc_geometry_create / bvc_geometry_destroy (library-owned BVH)."""
+
+    def __init__(self, V, F, stream=None):
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        self.dim = int(V.shape[1])
+        h = C.c_void_p()
+        _check(lib().bvc_geometry_create(self.dim, V.ctypes.data_as(C.c_void_p), V.shape[0],
+                                         F.ctypes.data_as(C.c_void_p), F.shape[0], _stream(stream), C.byref(h)),
+               "bvc_geometry_create")
+        self.h = h
+
+    def info(self) -> GeometryInfo:
+        inf = GeometryInfo()
+        _check(lib().bvc_geometry_get_info(self.h, C.byref(inf)), "bvc_geometry_get_info")
+        return inf
+
+    @property
+    def boundary_measure(self) -> float:
+        return float(self.info().boundary_measure)
+
+    def stats(self, reset=False, stream=None):
+        out = (C.c_uint64 * 4)()
+        st = lib().bvc_geometry_stats(self.h, out, int(bool(reset)), _stream(stream))
+        _check(st, "bvc_geometry_stats", allow=(OK, WARN_WALK_CAP))
+        return {"steps": int(out[0]), "capped": int(out[1]), "flags": int(out[2]), "status": st}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bvc_geometry_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def query_closest(geom: Geometry, pts: torch.Tensor, want_cp=False, stream=None):
+    _dev(pts, torch.float32)
+    m = pts.shape[1]
+    d2 = torch.empty(m, dtype=torch.float32, device=pts.device)
+    prim = torch.empty(m, dtype=torch.int32, device=pts.device)
+    cp = torch.empty_like(pts) if want_cp else None
+    _check(lib().bvc_query_closest(geom.h, _ptr(pts), m, _ptr(d2), _ptr(prim), _ptr(cp), _stream(stream)),
+           "bvc_query_closest")
+    return d2, prim, cp
+
+
+def classify_near(geom: Geometry, pts: torch.Tensor, l: float, stream=None) -> torch.Tensor:
+    _dev(pts, torch.float32)
+    near = torch.empty(pts.shape[1], dtype=torch.uint8, device=pts.device)
+    _check(lib().bvc_classify_near(geom.h, _ptr(pts), pts.shape[1], float(l), _ptr(near), _stream(stream)),
+           "bvc_classify_near")
+    return near
+
+
+def sample_boundary(geom: Geometry, n: int, l: float, seed: int, want_elem=True, stream=None):
+    z = torch.empty((geom.dim, n), dtype=torch.float32, device="cuda")
+    nrm = torch.empty_like(z)
+    elem = torch.empty(n, dtype=torch.int32, device="cuda") if want_elem else None
+    _check(lib().bvc_sample_boundary(geom.h, n, float(l), int(seed), _ptr(z), _ptr(nrm), _ptr(elem),
+                                     _stream(stream)), "bvc_sample_boundary")
+    return z, nrm, elem
+
+
+def walk(geom: Geometry, g_terms, f_terms, starts, nrm, walks: int, eps: float, max_steps: int, seed: int,
+         id_base: int = 0, tag: int = TAG_WALK, debug=False, stream=None):
+    """bvc_walk: per-walk records (U, and n.grad or grad) as a (planes, n*walks) tensor."""
+    _dev(starts, torch.float32)
+    n = starts.shape[1]
+    planes = 1 if nrm is not None else geom.dim
+    rec = torch.empty((1 + planes, n * walks), dtype=torch.float32, device="cuda")
+    steps = torch.empty(n * walks, dtype=torch.int32, device="cuda") if debug else None
+    prim = torch.empty(n * walks, dtype=torch.int32, device="cuda") if debug else None
+    g, f = make_function(g_terms), make_function(f_terms)
+    _check(lib().bvc_walk(geom.h, C.byref(g), C.byref(f), _ptr(starts), _ptr(nrm), n, int(walks), float(eps),
+                          int(max_steps), int(seed), int(id_base), int(tag), _ptr(rec), _ptr(steps), _ptr(prim),
+                          _stream(stream)), "bvc_walk")
+    return rec, steps, prim
+
+
+def reduce_walks(rec: torch.Tensor, n: int, walks: int, mode: int = 0, out=None, stream=None):
+    planes = rec.shape[0] - 1
+    if out is None:
+        out = torch.zeros((1 + planes, n), dtype=torch.float64, device="cuda")
+    _check(lib().bvc_reduce_walks(_ptr(rec), n, int(walks), planes, int(mode), _ptr(out), _stream(stream)),
+           "bvc_reduce_walks")
+    return out
+
+
+# ---------------------------------------------------------------- caches
+class Cache:
+    """Caller-owned device buffers of a bvc_cache (Alg. 1 boundarySamples /
+    sourceSamples) as torch tensors."""
+
+    def __init__(self, dim: int, n: int, n_src_cand: int = 0, device="cuda"):
+        self.dim, self.n, self.n_src_cand = dim, n, n_src_cand
+        self.z = torch.zeros((dim, n), dtype=torch.float32, device=device)
+        self.nrm = torch.zeros((dim, n), dtype=torch.float32, device=device)
+        self.u_hat = torch.zeros(n, dtype=torch.float64, device=device)
+        self.dudn_hat = torch.zeros(n, dtype=torch.float64, device=device)
+        self.packed = torch.zeros((n, 8 if dim == 2 else 12), dtype=torch.float32, device=device)
+        ms = max(n_src_cand, 1)
+        self.src_y = torch.zeros((dim, ms), dtype=torch.float32, device=device)
+        self.src_c = torch.zeros(ms, dtype=torch.float64, device=device)
+        self.src_packed = torch.zeros((ms, 4), dtype=torch.float32, device=device)
+        self.n_src_dev = torch.zeros(1, dtype=torch.int64, device=device)
+        self.bnd_measure = 0.0
+        self.struct = self._make_struct()
+
+    def _make_struct(self):
+        s = CacheStruct()
+        s.dim, s.n = self.dim, self.n
+        s.z, s.nrm, s.u_hat, s.dudn_hat, s.packed = (_ptr(self.z), _ptr(self.nrm), _ptr(self.u_hat),
+                                                     _ptr(self.dudn_hat), _ptr(self.packed))
+        s.bnd_measure = float(self.bnd_measure)
+        s.n_src_cand = self.n_src_cand
+        s.src_y, s.src_c, s.src_packed, s.n_src_dev = (_ptr(self.src_y), _ptr(self.src_c), _ptr(self.src_packed),
+                                                       _ptr(self.n_src_dev))
+        return s
+
+    def set_measure(self, m: float):
+        self.bnd_measure = float(m)
+        self.struct.bnd_measure = float(m)
+
+    def sync_from_struct(self):
+        self.bnd_measure = float(self.struct.bnd_measure)
+
+
+def cache_opts(n_samples, walks, offset_l, eps, seed, max_steps=1 << 14, walk_id_base=0, src_grid=(0, 0)):
+    o = CacheOpts()
+    o.n_samples, o.walks_per_sample, o.max_steps = int(n_samples), int(walks), int(max_steps)
+    o.offset_l, o.eps, o.seed, o.walk_id_base = float(offset_l), float(eps), int(seed), int(walk_id_base)
+    o.src_grid[0], o.src_grid[1] = int(src_grid[0]), int(src_grid[1])
+    return o
+
+
+def cache_build_workspace_size(geom: Geometry, opts: CacheOpts):
+    mn, full = C.c_size_t(), C.c_size_t()
+    _check(lib().bvc_cache_build_workspace_size(geom.h, C.byref(opts), C.byref(mn), C.byref(full)),
+           "bvc_cache_build_workspace_size")
+    return int(mn.value), int(full.value)
+
+
+def workspace(nbytes: int) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
+
+
+def cache_build(geom: Geometry, g_terms, f_terms, opts: CacheOpts, cache: Cache, ws: torch.Tensor = None,
+                stream=None):
+    if ws is None:
+        ws = workspace(cache_build_workspace_size(geom, opts)[1])
+    g, f = make_function(g_terms), make_function(f_terms)
+    _check(lib().bvc_cache_build(geom.h, C.byref(g), C.byref(f), C.byref(opts), C.byref(cache.struct), _ptr(ws),
+                                 ws.numel(), _stream(stream)), "bvc_cache_build")
+    cache.sync_from_struct()
+    return cache
+
+
+def sample_source(geom: Geometry, f_terms, grid, seed: int, cache: Cache, ws: torch.Tensor = None, stream=None):
+    need = C.c_size_t()
+    _check(lib().bvc_sample_source_workspace_size(cache.n_src_cand, C.byref(need)), "workspace size")
+    if ws is None:
+        ws = workspace(need.value)
+    f = make_function(f_terms)
+    gr = (C.c_int32 * 2)(int(grid[0]), int(grid[1]))
+    _check(lib().bvc_sample_source(geom.h, C.byref(f), gr, int(seed), C.byref(cache.struct), _ptr(ws), ws.numel(),
+                                   _stream(stream)), "bvc_sample_source")
+
+
+def cache_pack(cache: Cache, stream=None):
+    _check(lib().bvc_cache_pack(C.byref(cache.struct), _stream(stream)), "bvc_cache_pack")
+
+
+# ---------------------------------------------------------------- evaluation
+class EvalState:
+    """Alg. 1 EvaluationPoint running sums for a set of points (dim, m)."""
+
+    def __init__(self, pts: torch.Tensor, grad=True):
+        _dev(pts, torch.float32)
+        self.x = pts
+        self.dim, self.m = pts.shape
+        dev = pts.device
+        self.u_bnd = torch.zeros(self.m, dtype=torch.float64, device=dev)
+        self.u_src = torch.zeros(self.m, dtype=torch.float64, device=dev)
+        self.grad_bnd = torch.zeros((self.dim, self.m), dtype=torch.float64, device=dev) if grad else None
+        self.grad_src = torch.zeros((self.dim, self.m), dtype=torch.float64, device=dev) if grad else None
+        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        s = EvalStateStruct()
+        s.dim, s.m, s.x = self.dim, self.m, _ptr(pts)
+        s.u_bnd, s.u_src = _ptr(self.u_bnd), _ptr(self.u_src)
+        s.grad_bnd, s.grad_src = _ptr(self.grad_bnd), _ptr(self.grad_src)
+        s.counts = _ptr(self.counts)
+        self.struct = s
+
+    def reset(self):
+        for t in (self.u_bnd, self.u_src, self.grad_bnd, self.grad_src, self.counts):
+            if t is not None:
+                t.zero_()
+
+
+def evaluate_workspace_size(cache: Cache, state: EvalState) -> int:
+    b = C.c_size_t()
+    _check(lib().bvc_evaluate_workspace_size(C.byref(cache.struct), C.byref(state.struct), C.byref(b)),
+           "bvc_evaluate_workspace_size")
+    return int(b.value)
+
+
+def evaluate(cache: Cache, state: EvalState, ws: torch.Tensor = None, stream=None):
+    if ws is None:
+        ws = workspace(evaluate_workspace_size(cache, state))
+    _check(lib().bvc_evaluate(C.byref(cache.struct), C.byref(state.struct), _ptr(ws), ws.numel(), _stream(stream)),
+           "bvc_evaluate")
+
+
+def get_solution(state: EvalState, u=None, grad=None, stream=None):
+    if u is None:
+        u = torch.empty(state.m, dtype=torch.float64, device=state.x.device)
+    if grad is None and state.grad_bnd is not None:
+        grad = torch.empty((state.dim, state.m), dtype=torch.float64, device=state.x.device)
+    _check(lib().bvc_get_solution(C.byref(state.struct), _ptr(u), _ptr(grad), _stream(stream)), "bvc_get_solution")
+    return u, grad
+
+
+def wos_workspace_size(dim: int, m: int, walks: int):
+    mn, full = C.c_size_t(), C.c_size_t()
+    _check(lib().wos_estimate_workspace_size(dim, m, walks, C.byref(mn), C.byref(full)), "wos workspace size")
+    return int(mn.value), int(full.value)
+
+
+def wos_estimate(geom: Geometry, g_terms, f_terms, pts: torch.Tensor, walks: int, eps: float, max_steps: int,
+                 seed: int, id_base: int = 0, u_sum=None, grad_sum=None, want_grad=True, ws: torch.Tensor = None,
+                 stream=None):
+    """Pointwise walk on spheres: adds FP64 sums of `walks` walks per point."""
+    _dev(pts, torch.float32)
+    dim, m = pts.shape
+    if u_sum is None:
+        u_sum = torch.zeros(m, dtype=torch.float64, device=pts.device)
+    if grad_sum is None and want_grad:
+        grad_sum = torch.zeros((dim, m), dtype=torch.float64, device=pts.device)
+    if ws is None:
+        ws = workspace(wos_workspace_size(dim, m, walks)[1])
+    g, f = make_function(g_terms), make_function(f_terms)
+    _check(lib().wos_estimate(geom.h, C.byref(g), C.byref(f), _ptr(pts), m, int(walks), float(eps), int(max_steps),
+                              int(seed), int(id_base), _ptr(u_sum), _ptr(grad_sum), _ptr(ws), ws.numel(),
+                              _stream(stream)), "wos_estimate")
+    return u_sum, grad_sum
+
+
+def gather_status(reset=False):
+    f = C.c_uint64()
+    st = lib().bvc_gather_status(C.byref(f), int(bool(reset)))
+    return int(f.value), st

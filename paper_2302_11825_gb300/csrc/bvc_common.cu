@@ -1,0 +1,98 @@
+// bvc_common.cu -- host helpers: problem-function conversion, device
+// properties, status strings.
+#include <cmath>
+#include <mutex>
+
+#include "bvc_internal.h"
+
+namespace bvc {
+
+bool make_dev_function(const bvc_function* f, int dim, DevFunction* out) {
+  *out = DevFunction{};
+  if (f == nullptr || f->n_terms == 0) return true;
+  if (f->n_terms < 0 || f->n_terms > BVC_MAX_TERMS) return false;
+  int used = 0;
+  out->n_terms = f->n_terms;
+  for (int t = 0; t < f->n_terms; ++t) {
+    const bvc_term& tm = f->terms[t];
+    const int nc = tm.n_coeffs;
+    if (nc < 0 || (nc > 0 && tm.coeffs == nullptr)) return false;
+    for (int i = 0; i < nc; ++i)
+      if (!std::isfinite(tm.coeffs[i])) return false;
+    out->kind[t] = tm.kind;
+    out->off[t] = used;
+    float* c = out->c + used;
+    int dn = nc;
+    switch (tm.kind) {
+      case BVC_FN_POLY:
+        if (nc > (dim == 2 ? 15 : 35)) return false;
+        if (used + nc > BVC_MAX_COEFFS) return false;
+        for (int i = 0; i < nc; ++i) c[i] = (float)tm.coeffs[i];
+        break;
+      case BVC_FN_GAUSS:
+      case BVC_FN_GAUSS_LAPLACIAN: {
+        if (nc < 1 || (nc - 1) % (1 + dim) != 0) return false;
+        const double s = tm.coeffs[0];
+        if (!(s > 0.0)) return false;
+        const int head = tm.kind == BVC_FN_GAUSS ? 1 : 3;
+        dn = head + (nc - 1);
+        if (used + dn > BVC_MAX_COEFFS + 8) return false;
+        c[0] = (float)(-1.0 / (2.0 * s * s));
+        if (head == 3) {
+          c[1] = (float)(1.0 / (s * s * s * s));
+          c[2] = (float)(-(double)dim / (s * s));
+        }
+        for (int i = 1; i < nc; ++i) c[head + i - 1] = (float)tm.coeffs[i];
+        break;
+      }
+      case BVC_FN_EXP_TRIG:
+        if (dim != 3 || nc != 4) return false;
+        if (used + nc > BVC_MAX_COEFFS) return false;
+        for (int i = 0; i < 4; ++i) c[i] = (float)tm.coeffs[i];
+        break;
+      default:
+        return false;
+    }
+    out->nc[t] = dn;
+    used += dn;
+  }
+  return true;
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev < 0 || dev >= 64) return 1;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+int max_blocks_per_sm(const void* kernel, int block, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess || n <= 0) n = 1;
+  return n;
+}
+
+}  // namespace bvc
+
+extern "C" const char* bvc_status_string(bvc_status s) {
+  switch (s) {
+    case BVC_OK: return "ok";
+    case BVC_ERR_INVALID_ARG: return "invalid argument";
+    case BVC_ERR_DEGENERATE_MESH: return "degenerate mesh";
+    case BVC_ERR_OOM: return "out of device memory";
+    case BVC_ERR_CUDA: return "CUDA runtime error";
+    case BVC_ERR_TIMEOUT: return "in-kernel wait timed out";
+    case BVC_ERR_UNSUPPORTED: return "unsupported";
+    case BVC_ERR_WORKSPACE: return "workspace too small";
+    case BVC_WARN_WALK_CAP: return "walks stopped at max_steps";
+  }
+  return "unknown status";
+}
+
+extern "C" int32_t bvc_version(void) { return 100; }

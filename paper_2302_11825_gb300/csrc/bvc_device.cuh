@@ -1,0 +1,340 @@
+// bvc_device.cuh -- device building blocks shared by the library's kernels:
+// Philox-4x32-10, problem-function evaluation, the canonical FP32
+// closest-point distance and the BVH closest-point traversal.
+//
+// Canonical closest-point distance.  The primitive is stored as a (first
+// vertex) and ab = b - a (and ac = c - a), each difference one FP32
+// subtraction.  The squared distance from p is the following fixed sequence
+// of correctly rounded FP32 operations (no contraction):
+//   segment:  ap = p - a; num = fma(ap.y, ab.y, ap.x*ab.x);
+//             den = fma(ab.y, ab.y, ab.x*ab.x);
+//             t = num <= 0 ? 0 : num >= den ? 1 : num/den;
+//             d = (fma(-t, ab.x, ap.x), fma(-t, ab.y, ap.y)); d2 = fma(d.y, d.y, d.x*d.x)
+//   triangle: the Voronoi-region classification of Ericson, "Real-Time
+//             Collision Detection" Sec. 5.1.5, written on (ap, ab, ac) with
+//             dot(u,v) = fma(u.z, v.z, fma(u.y, v.y, u.x*v.x)),
+//             bp = ap - ab, cp = ap - ac and the difference vector p - closest
+//             formed directly with fma (see tri_closest below).
+// Ties in d2 go to the lowest primitive index.  The BVH prunes a box only
+// when its distance exceeds sqrt(best) + tau (tau = 2^-18 x bbox diagonal,
+// far above the rounding of the expressions above), so the traversal
+// returns exactly the brute-force argmin of these FP32 numbers.
+#pragma once
+
+#include <cstdint>
+
+#include "bvc_internal.h"
+
+namespace bvc {
+
+constexpr float kPiF = 3.14159265358979323846f;
+
+// ----------------------------------------------------------------- Philox
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32
+// multiplies by the round constants, xor of the high halves with the other
+// counter words and the key, and a Weyl bump of the key between rounds.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                            uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ U4 philox_draw(uint64_t seed, uint64_t id, uint32_t word2, uint32_t tag) {
+  return philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), word2, tag, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Uniform in (0,1): odd multiples of 2^-24, exact in FP32 and FP64.
+__device__ __forceinline__ float u01f(uint32_t r) { return (float)((r >> 9) * 2u + 1u) * 0x1p-24f; }
+__device__ __forceinline__ double u01d(uint32_t r) { return (double)((r >> 9) * 2u + 1u) * 0x1p-24; }
+
+// ------------------------------------------------------- problem functions
+template <int D>
+__device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) {
+  float v = 0.0f;
+  for (int t = 0; t < fn.n_terms; ++t) {
+    const float* c = fn.c + fn.off[t];
+    const int nc = fn.nc[t];
+    switch (fn.kind[t]) {
+      case BVC_FN_POLY: {
+        float xp[5], yp[5], zp[5];
+        xp[0] = yp[0] = zp[0] = 1.0f;
+#pragma unroll
+        for (int e = 1; e < 5; ++e) {
+          xp[e] = xp[e - 1] * x[0];
+          yp[e] = yp[e - 1] * x[1];
+          zp[e] = D == 3 ? zp[e - 1] * x[D == 3 ? 2 : 0] : 0.0f;
+        }
+        int idx = 0;
+        for (int tt = 0; tt <= 4 && idx < nc; ++tt) {
+          if (D == 2) {
+            for (int i = tt; i >= 0 && idx < nc; --i, ++idx) v = fmaf(c[idx], xp[i] * yp[tt - i], v);
+          } else {
+            for (int i = tt; i >= 0 && idx < nc; --i)
+              for (int j = tt - i; j >= 0 && idx < nc; --j, ++idx) v = fmaf(c[idx], xp[i] * yp[j] * zp[tt - i - j], v);
+          }
+        }
+        break;
+      }
+      case BVC_FN_GAUSS: {  // device layout: [-1/(2s^2), (A, c[D])...]
+        const float neg = c[0];
+        for (int k = 1; k + D < nc; k += 1 + D) {
+          float r2 = 0.0f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const float d = x[a] - c[k + 1 + a];
+            r2 = fmaf(d, d, r2);
+          }
+          v = fmaf(c[k], expf(r2 * neg), v);
+        }
+        break;
+      }
+      case BVC_FN_GAUSS_LAPLACIAN: {  // device layout: [-1/(2s^2), 1/s^4, -D/s^2, (A, c[D])...]
+        const float neg = c[0], q4 = c[1], qd = c[2];
+        for (int k = 3; k + D < nc; k += 1 + D) {
+          float r2 = 0.0f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const float d = x[a] - c[k + 1 + a];
+            r2 = fmaf(d, d, r2);
+          }
+          v = fmaf(c[k] * fmaf(r2, q4, qd), expf(r2 * neg), v);
+        }
+        break;
+      }
+      case BVC_FN_EXP_TRIG:
+        if (D == 3) v = fmaf(c[0] * expf(c[1] * x[D == 3 ? 2 : 0]), cosf(c[2] * x[0]) * sinf(c[3] * x[1]), v);
+        break;
+      default:
+        break;
+    }
+  }
+  return v;
+}
+
+// ------------------------------------------- canonical closest-point distance
+__device__ __forceinline__ float seg_closest(float ax, float ay, float abx, float aby, float px, float py,
+                                             float& dx, float& dy) {
+  const float apx = __fsub_rn(px, ax), apy = __fsub_rn(py, ay);
+  const float num = __fmaf_rn(apy, aby, __fmul_rn(apx, abx));
+  const float den = __fmaf_rn(aby, aby, __fmul_rn(abx, abx));
+  float t;
+  if (num <= 0.0f)
+    t = 0.0f;
+  else if (num >= den)
+    t = 1.0f;
+  else
+    t = __fdiv_rn(num, den);
+  dx = __fmaf_rn(-t, abx, apx);
+  dy = __fmaf_rn(-t, aby, apy);
+  return __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+}
+
+__device__ __forceinline__ float dot3c(float ux, float uy, float uz, float vx, float vy, float vz) {
+  return __fmaf_rn(uz, vz, __fmaf_rn(uy, vy, __fmul_rn(ux, vx)));
+}
+
+// Returns d2 and the difference vector df = p - closest point.
+__device__ __forceinline__ float tri_closest(const float4 A, const float4 B, const float4 Cc, const float* p,
+                                             float* df) {
+  const float apx = __fsub_rn(p[0], A.x), apy = __fsub_rn(p[1], A.y), apz = __fsub_rn(p[2], A.z);
+  const float abx = B.x, aby = B.y, abz = B.z, acx = Cc.x, acy = Cc.y, acz = Cc.z;
+  const float d1 = dot3c(abx, aby, abz, apx, apy, apz), d2 = dot3c(acx, acy, acz, apx, apy, apz);
+  if (d1 <= 0.0f && d2 <= 0.0f) {
+    df[0] = apx;
+    df[1] = apy;
+    df[2] = apz;
+    return dot3c(apx, apy, apz, apx, apy, apz);
+  }
+  const float bpx = __fsub_rn(apx, abx), bpy = __fsub_rn(apy, aby), bpz = __fsub_rn(apz, abz);
+  const float d3 = dot3c(abx, aby, abz, bpx, bpy, bpz), d4 = dot3c(acx, acy, acz, bpx, bpy, bpz);
+  if (d3 >= 0.0f && d4 <= d3) {
+    df[0] = bpx;
+    df[1] = bpy;
+    df[2] = bpz;
+    return dot3c(bpx, bpy, bpz, bpx, bpy, bpz);
+  }
+  const float vc = __fmaf_rn(d1, d4, -__fmul_rn(d3, d2));
+  if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) {
+    const float v = __fdiv_rn(d1, __fsub_rn(d1, d3));
+    df[0] = __fmaf_rn(-v, abx, apx);
+    df[1] = __fmaf_rn(-v, aby, apy);
+    df[2] = __fmaf_rn(-v, abz, apz);
+    return dot3c(df[0], df[1], df[2], df[0], df[1], df[2]);
+  }
+  const float cpx = __fsub_rn(apx, acx), cpy = __fsub_rn(apy, acy), cpz = __fsub_rn(apz, acz);
+  const float d5 = dot3c(abx, aby, abz, cpx, cpy, cpz), d6 = dot3c(acx, acy, acz, cpx, cpy, cpz);
+  if (d6 >= 0.0f && d5 <= d6) {
+    df[0] = cpx;
+    df[1] = cpy;
+    df[2] = cpz;
+    return dot3c(cpx, cpy, cpz, cpx, cpy, cpz);
+  }
+  const float vb = __fmaf_rn(d5, d2, -__fmul_rn(d1, d6));
+  if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) {
+    const float w = __fdiv_rn(d2, __fsub_rn(d2, d6));
+    df[0] = __fmaf_rn(-w, acx, apx);
+    df[1] = __fmaf_rn(-w, acy, apy);
+    df[2] = __fmaf_rn(-w, acz, apz);
+    return dot3c(df[0], df[1], df[2], df[0], df[1], df[2]);
+  }
+  const float va = __fmaf_rn(d3, d6, -__fmul_rn(d5, d4));
+  const float e43 = __fsub_rn(d4, d3), e56 = __fsub_rn(d5, d6);
+  if (va <= 0.0f && e43 >= 0.0f && e56 >= 0.0f) {
+    const float w = __fdiv_rn(e43, __fadd_rn(e43, e56));
+    df[0] = __fmaf_rn(-w, __fsub_rn(acx, abx), bpx);
+    df[1] = __fmaf_rn(-w, __fsub_rn(acy, aby), bpy);
+    df[2] = __fmaf_rn(-w, __fsub_rn(acz, abz), bpz);
+    return dot3c(df[0], df[1], df[2], df[0], df[1], df[2]);
+  }
+  const float denom = __frcp_rn(__fadd_rn(__fadd_rn(va, vb), vc));
+  const float v = __fmul_rn(vb, denom), w = __fmul_rn(vc, denom);
+  df[0] = __fmaf_rn(-w, acx, __fmaf_rn(-v, abx, apx));
+  df[1] = __fmaf_rn(-w, acy, __fmaf_rn(-v, aby, apy));
+  df[2] = __fmaf_rn(-w, acz, __fmaf_rn(-v, abz, apz));
+  return dot3c(df[0], df[1], df[2], df[0], df[1], df[2]);
+}
+
+// ------------------------------------------------------- BVH traversal
+template <int D>
+struct Hit {
+  float d2;
+  int32_t id;  // caller's element index
+  float df[D]; // p - closest point
+};
+
+__device__ __forceinline__ float box_d2_2(float lox, float loy, float hix, float hiy, const float* p) {
+  const float dx = fmaxf(fmaxf(lox - p[0], p[0] - hix), 0.0f);
+  const float dy = fmaxf(fmaxf(loy - p[1], p[1] - hiy), 0.0f);
+  return fmaf(dy, dy, dx * dx);
+}
+
+__device__ __forceinline__ float box_d2_3(float lox, float loy, float loz, float hix, float hiy, float hiz,
+                                          const float* p) {
+  const float dx = fmaxf(fmaxf(lox - p[0], p[0] - hix), 0.0f);
+  const float dy = fmaxf(fmaxf(loy - p[1], p[1] - hiy), 0.0f);
+  const float dz = fmaxf(fmaxf(loz - p[2], p[2] - hiz), 0.0f);
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+template <int D>
+__device__ __forceinline__ void test_leaf(const DevGeometry& G, int32_t enc, const float* p, Hit<D>& h, float& thr) {
+  const int32_t e = ~enc;
+  const int32_t first = e >> 3, count = e & 7;
+  for (int32_t q = first; q < first + count; ++q) {
+    float df[D];
+    float d2;
+    if (D == 2) {
+      const float4 s = __ldg(&G.prims[q]);
+      d2 = seg_closest(s.x, s.y, s.z, s.w, p[0], p[1], df[0], df[D > 1 ? 1 : 0]);
+    } else {
+      const float4 A = __ldg(&G.prims[3 * q]), B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
+      d2 = tri_closest(A, B, Cc, p, df);
+    }
+    if (d2 <= h.d2) {
+      const int32_t id = __ldg(&G.prim_ids[q]);
+      if (d2 < h.d2 || id < h.id) {
+        h.d2 = d2;
+        h.id = id;
+#pragma unroll
+        for (int a = 0; a < D; ++a) h.df[a] = df[a];
+        const float s = sqrtf(d2) + G.tau;
+        thr = s * s;
+      }
+    }
+  }
+}
+
+// Closest primitive to p.  Stack in shared memory: stack[k * stride + lane_slot].
+template <int D>
+__device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p, Hit<D>& h, int* snode,
+                                            float* sdist, int stride) {
+  h.d2 = __int_as_float(0x7f800000);
+  h.id = 0x7fffffff;
+#pragma unroll
+  for (int a = 0; a < D; ++a) h.df[a] = 0.0f;
+  float thr = __int_as_float(0x7f800000);
+  int sp = 0;
+  int node = 0;
+  for (;;) {
+    int32_t cl, cr;
+    float dl, dr;
+    if (D == 2) {
+      const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
+      const float4 C = __ldg(&G.nodes[3 * node + 2]);
+      dl = box_d2_2(L.x, L.y, L.z, L.w, p);
+      dr = box_d2_2(R.x, R.y, R.z, R.w, p);
+      cl = __float_as_int(C.x);
+      cr = __float_as_int(C.y);
+    } else {
+      const float4 a = __ldg(&G.nodes[4 * node]), b = __ldg(&G.nodes[4 * node + 1]);
+      const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
+      dl = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, p);
+      dr = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, p);
+      cl = __float_as_int(e.x);
+      cr = __float_as_int(e.y);
+    }
+    if (dr < dl) {
+      const int32_t tc = cl;
+      cl = cr;
+      cr = tc;
+      const float td = dl;
+      dl = dr;
+      dr = td;
+    }
+    bool tl = dl <= thr, tr = dr <= thr;
+    if (tl && cl < 0) {
+      test_leaf<D>(G, cl, p, h, thr);
+      tl = false;
+      tr = dr <= thr;
+    }
+    if (tr && cr < 0) {
+      test_leaf<D>(G, cr, p, h, thr);
+      tr = false;
+    }
+    if (tl && tr) {
+      snode[sp * stride] = cr;
+      sdist[sp * stride] = dr;
+      ++sp;
+      node = cl;
+      continue;
+    }
+    if (tl) {
+      node = cl;
+      continue;
+    }
+    if (tr) {
+      node = cr;
+      continue;
+    }
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      if (sdist[sp * stride] <= thr) {
+        node = snode[sp * stride];
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+}
+
+}  // namespace bvc

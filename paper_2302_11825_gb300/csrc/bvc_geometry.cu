@@ -1,0 +1,302 @@
+// bvc_geometry.cu -- boundary mesh handle, closest-point queries and the
+// boundary sampler (K1).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bvc_device.cuh"
+#include "bvc_internal.h"
+
+namespace bvc {
+
+int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::vector<float4>& nodes_out,
+                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out);
+
+// Measure and outward unit normal of element e in FP64 (Sec. 4 "Sampling":
+// elements are chosen in proportion to their measure).  This exact sequence
+// of operations is also evaluated on the device by the sampler, so both
+// see the same numbers.  Compiled with -ffp-contract=off.
+static double elem_measure(int dim, const float* V, const int32_t* f) {
+  if (dim == 2) {
+    const double ax = V[2 * f[0]], ay = V[2 * f[0] + 1], bx = V[2 * f[1]], by = V[2 * f[1] + 1];
+    const double dx = bx - ax, dy = by - ay;
+    return std::sqrt(dx * dx + dy * dy);
+  }
+  double e1[3], e2[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = (double)V[3 * f[1] + a] - (double)V[3 * f[0] + a];
+    e2[a] = (double)V[3 * f[2] + a] - (double)V[3 * f[0] + a];
+  }
+  const double c0 = e1[1] * e2[2] - e1[2] * e2[1];
+  const double c1 = e1[2] * e2[0] - e1[0] * e2[2];
+  const double c2 = e1[0] * e2[1] - e1[1] * e2[0];
+  return 0.5 * std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------- kernels
+template <int D>
+__global__ void __launch_bounds__(128) k_query_closest(DevGeometry G, const float* __restrict__ pts, int64_t m,
+                                                       float* __restrict__ d2, int32_t* __restrict__ prim,
+                                                       float* __restrict__ cp, float near_l2,
+                                                       uint8_t* __restrict__ near) {
+  __shared__ int snode[32 * 128];
+  __shared__ float sdist[32 * 128];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float p[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) p[a] = pts[a * m + i];
+    Hit<D> h;
+    bvh_closest<D>(G, p, h, snode + threadIdx.x, sdist + threadIdx.x, 128);
+    if (d2) d2[i] = h.d2;
+    if (prim) prim[i] = h.id;
+    if (cp)
+#pragma unroll
+      for (int a = 0; a < D; ++a) cp[a * m + i] = p[a] - h.df[a];
+    if (near) near[i] = h.d2 < near_l2 ? 1 : 0;
+  }
+}
+
+// K1: stratified boundary samples through the FP64 measure CDF, offset by
+// -l n.  The FP64 operations use explicit round-to-nearest intrinsics (no
+// contraction), in the same order as the host's measure computation.
+template <int D>
+__global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t n, double l, uint64_t seed,
+                                                         float* __restrict__ z, float* __restrict__ nrm,
+                                                         int32_t* __restrict__ elem) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const U4 r = philox_draw(seed, (uint64_t)i, 0u, 1u);
+  const double u0 = u01d(r.x), u1 = u01d(r.y), u2 = u01d(r.z);
+  const int64_t np = G.n_prims;
+  const double total = G.cdf[np];
+  const double s = __ddiv_rn(__dadd_rn((double)i, u0), (double)n);
+  const double t = __dmul_rn(s, total);
+  int64_t lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (G.cdf[mid + 1] > t)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  const int64_t e = lo;
+  const int32_t* f = G.idx + e * D;
+  double p[3], nn[3];
+  if (D == 2) {
+    const double ax = G.verts[2 * f[0]], ay = G.verts[2 * f[0] + 1];
+    const double bx = G.verts[2 * f[1]], by = G.verts[2 * f[1] + 1];
+    const double dx = __dsub_rn(bx, ax), dy = __dsub_rn(by, ay);
+    const double len = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+    nn[0] = __ddiv_rn(dy, len);
+    nn[1] = __ddiv_rn(-dx, len);
+    double lam = __ddiv_rn(__dsub_rn(t, G.cdf[e]), len);
+    lam = fmin(fmax(lam, 0.0), 1.0);
+    p[0] = __dadd_rn(ax, __dmul_rn(lam, dx));
+    p[1] = __dadd_rn(ay, __dmul_rn(lam, dy));
+  } else {
+    double v0[3], e1[3], e2[3];
+    for (int a = 0; a < 3; ++a) {
+      v0[a] = G.verts[3 * f[0] + a];
+      e1[a] = __dsub_rn((double)G.verts[3 * f[1] + a], v0[a]);
+      e2[a] = __dsub_rn((double)G.verts[3 * f[2] + a], v0[a]);
+    }
+    const double c0 = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
+    const double c1 = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
+    const double c2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
+    const double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2)));
+    nn[0] = __ddiv_rn(c0, len);
+    nn[1] = __ddiv_rn(c1, len);
+    nn[2] = __ddiv_rn(c2, len);
+    const double sq = __dsqrt_rn(u1);
+    const double b1 = __dmul_rn(sq, __dsub_rn(1.0, u2)), b2 = __dmul_rn(sq, u2);
+    for (int a = 0; a < 3; ++a) p[a] = __dadd_rn(__dadd_rn(v0[a], __dmul_rn(b1, e1[a])), __dmul_rn(b2, e2[a]));
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    z[a * n + i] = __double2float_rn(__dsub_rn(p[a], __dmul_rn(l, nn[a])));
+    nrm[a * n + i] = __double2float_rn(nn[a]);
+  }
+  if (elem) elem[i] = (int32_t)e;
+}
+
+static int grid_for(int64_t n, int block) {
+  const int64_t g = (n + block - 1) / block;
+  const int64_t cap = (int64_t)num_sms() * 32;
+  return (int)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+}  // namespace bvc
+
+using namespace bvc;
+
+extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
+                                          int64_t n_prims, bvc_stream stream, bvc_geometry* out) {
+  if (out == nullptr) return BVC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((dim != 2 && dim != 3) || verts == nullptr || prims == nullptr || n_verts <= 0 || n_prims <= 0)
+    return BVC_ERR_INVALID_ARG;
+  if (n_prims >= (int64_t(1) << 28) || n_verts >= (int64_t(1) << 31)) return BVC_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n_verts * dim; ++i)
+    if (!std::isfinite(verts[i])) return BVC_ERR_DEGENERATE_MESH;
+  for (int64_t i = 0; i < n_prims * dim; ++i)
+    if (prims[i] < 0 || prims[i] >= n_verts) return BVC_ERR_DEGENERATE_MESH;
+  std::vector<double> cdf(n_prims + 1);
+  cdf[0] = 0.0;
+  for (int64_t e = 0; e < n_prims; ++e) {
+    const double m = elem_measure(dim, verts, prims + e * dim);
+    if (!(m > 0.0)) return BVC_ERR_DEGENERATE_MESH;
+    cdf[e + 1] = cdf[e] + m;
+  }
+  std::vector<float4> nodes, pr;
+  std::vector<int32_t> ids;
+  const int64_t n_nodes = build_bvh(dim, verts, prims, n_prims, nodes, pr, ids);
+
+  bvc_geometry g = new bvc_geometry_s();
+  g->dim = dim;
+  g->n_verts = n_verts;
+  g->n_prims = n_prims;
+  g->n_nodes = n_nodes;
+  g->measure = cdf[n_prims];
+  for (int a = 0; a < 3; ++a) {
+    g->lo[a] = a < dim ? INFINITY : 0.0f;
+    g->hi[a] = a < dim ? -INFINITY : 0.0f;
+  }
+  for (int64_t i = 0; i < n_verts; ++i)
+    for (int a = 0; a < dim; ++a) {
+      g->lo[a] = fminf(g->lo[a], verts[i * dim + a]);
+      g->hi[a] = fmaxf(g->hi[a], verts[i * dim + a]);
+    }
+  double diag = 0.0;
+  for (int a = 0; a < dim; ++a) diag += ((double)g->hi[a] - g->lo[a]) * ((double)g->hi[a] - g->lo[a]);
+  diag = std::sqrt(diag);
+
+  const size_t b_nodes = align256(nodes.size() * sizeof(float4));
+  const size_t b_prims = align256(pr.size() * sizeof(float4));
+  const size_t b_ids = align256(ids.size() * sizeof(int32_t));
+  const size_t b_cdf = align256(cdf.size() * sizeof(double));
+  const size_t b_verts = align256((size_t)n_verts * dim * sizeof(float));
+  const size_t b_idx = align256((size_t)n_prims * dim * sizeof(int32_t));
+  const size_t b_stats = 256;
+  g->arena_bytes = b_nodes + b_prims + b_ids + b_cdf + b_verts + b_idx + b_stats;
+  if (cudaMalloc(&g->arena, g->arena_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete g;
+    return BVC_ERR_OOM;
+  }
+  char* base = (char*)g->arena;
+  DevGeometry& d = g->dev;
+  d.nodes = (const float4*)base;
+  d.prims = (const float4*)(base += b_nodes);
+  d.prim_ids = (const int32_t*)(base += b_prims);
+  d.cdf = (const double*)(base += b_ids);
+  d.verts = (const float*)(base += b_cdf);
+  d.idx = (const int32_t*)(base += b_verts);
+  d.stats = (unsigned long long*)(base += b_idx);
+  d.n_prims = n_prims;
+  d.n_verts = n_verts;
+  d.tau = (float)(std::ldexp(1.0, -18) * (diag > 0 ? diag : 1.0));
+  for (int a = 0; a < 3; ++a) {
+    d.lo[a] = g->lo[a];
+    d.hi[a] = g->hi[a];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  bool ok = cudaMemcpyAsync((void*)d.nodes, nodes.data(), nodes.size() * sizeof(float4), cudaMemcpyHostToDevice, s) ==
+                cudaSuccess &&
+            cudaMemcpyAsync((void*)d.prims, pr.data(), pr.size() * sizeof(float4), cudaMemcpyHostToDevice, s) ==
+                cudaSuccess &&
+            cudaMemcpyAsync((void*)d.prim_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync((void*)d.cdf, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync((void*)d.verts, verts, (size_t)n_verts * dim * 4, cudaMemcpyHostToDevice, s) ==
+                cudaSuccess &&
+            cudaMemcpyAsync((void*)d.idx, prims, (size_t)n_prims * dim * 4, cudaMemcpyHostToDevice, s) ==
+                cudaSuccess &&
+            cudaMemsetAsync(d.stats, 0, b_stats, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    cudaFree(g->arena);
+    delete g;
+    return BVC_ERR_CUDA;
+  }
+  *out = g;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_geometry_destroy(bvc_geometry g) {
+  if (g == nullptr) return BVC_ERR_INVALID_ARG;
+  const cudaError_t e = cudaFree(g->arena);
+  delete g;
+  return e == cudaSuccess ? BVC_OK : BVC_ERR_CUDA;
+}
+
+extern "C" bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* info) {
+  if (g == nullptr || info == nullptr) return BVC_ERR_INVALID_ARG;
+  info->dim = g->dim;
+  info->n_verts = g->n_verts;
+  info->n_prims = g->n_prims;
+  info->n_nodes = g->n_nodes;
+  info->boundary_measure = g->measure;
+  for (int a = 0; a < 3; ++a) {
+    info->bbox_lo[a] = g->lo[a];
+    info->bbox_hi[a] = g->hi[a];
+  }
+  info->device_bytes = g->arena_bytes;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[4], int32_t reset, bvc_stream stream) {
+  if (g == nullptr || out == nullptr) return BVC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h[4];
+  BVC_CUDA_TRY(cudaMemcpyAsync(h, g->dev.stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  if (reset) BVC_CUDA_TRY(cudaMemsetAsync(g->dev.stats, 0, sizeof(h), s));
+  BVC_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < 4; ++i) out[i] = h[i];
+  if (h[kStatFlags] & kFlagTimeout) return BVC_ERR_TIMEOUT;
+  if (h[kStatCapped]) return BVC_WARN_WALK_CAP;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_query_closest(bvc_geometry g, const float* pts, int64_t m, float* d2, int32_t* prim,
+                                        float* cp, bvc_stream stream) {
+  if (g == nullptr || m < 0 || (m > 0 && pts == nullptr)) return BVC_ERR_INVALID_ARG;
+  if (m == 0) return BVC_OK;
+  const int grid = grid_for(m, 128);
+  if (g->dim == 2)
+    k_query_closest<2><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, d2, prim, cp, 0.0f, nullptr);
+  else
+    k_query_closest<3><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, d2, prim, cp, 0.0f, nullptr);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_t m, float l, uint8_t* near,
+                                        bvc_stream stream) {
+  if (g == nullptr || m < 0 || (m > 0 && (pts == nullptr || near == nullptr)) || !(l >= 0.0f))
+    return BVC_ERR_INVALID_ARG;
+  if (m == 0) return BVC_OK;
+  const int grid = grid_for(m, 128);
+  if (g->dim == 2)
+    k_query_closest<2><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, nullptr, nullptr, nullptr, l * l,
+                                                              near);
+  else
+    k_query_closest<3><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, nullptr, nullptr, nullptr, l * l,
+                                                              near);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
+                                          int32_t* elem, bvc_stream stream) {
+  if (g == nullptr || n < 0 || (n > 0 && (z == nullptr || nrm == nullptr)) || !std::isfinite(l))
+    return BVC_ERR_INVALID_ARG;
+  if (n == 0) return BVC_OK;
+  const int grid = (int)((n + 255) / 256);
+  if (g->dim == 2)
+    k_sample_boundary<2><<<grid, 256, 0, (cudaStream_t)stream>>>(g->dev, n, l, seed, z, nrm, elem);
+  else
+    k_sample_boundary<3><<<grid, 256, 0, (cudaStream_t)stream>>>(g->dev, n, l, seed, z, nrm, elem);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}

@@ -1,0 +1,82 @@
+// bvc_internal.h -- structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/bvc.h"
+
+namespace bvc {
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// A problem function in device form, passed by value as a kernel parameter.
+// Per term: kind, offset and count of its coefficients in c[] (FP32).
+// GAUSS is stored as [-1/(2s^2), (A, centre)...]; GAUSS_LAPLACIAN as
+// [-1/(2s^2), 1/s^4, -dim/s^2, (A, centre)...]; POLY and EXP_TRIG verbatim.
+struct DevFunction {
+  int32_t n_terms;
+  int32_t kind[BVC_MAX_TERMS];
+  int32_t off[BVC_MAX_TERMS];
+  int32_t nc[BVC_MAX_TERMS];
+  float c[BVC_MAX_COEFFS + 8];
+};
+
+// Device view of the geometry, passed by value to kernels.
+//  nodes: 2D 3 float4 per node  [L.lo.x L.lo.y L.hi.x L.hi.y] [R ...] [cl cr - -]
+//         3D 4 float4 per node  [L.lo.xyz L.hi.x] [L.hi.yz R.lo.xy] [R.lo.z R.hi.xyz] [cl cr - -]
+//         child >= 0: internal node; child < 0: leaf, ~child = first << 3 | count.
+//  prims: BVH order; 2D one float4 (a, ab); 3D three float4 (a,-) (ab,-) (ac,-).
+//  prim_ids: caller's index of each BVH-ordered primitive.
+struct DevGeometry {
+  const float4* nodes;
+  const float4* prims;
+  const int32_t* prim_ids;
+  const double* cdf;      // [n_prims + 1] FP64 prefix sums of element measures (caller order)
+  const float* verts;     // [n_verts][dim] caller's vertices
+  const int32_t* idx;     // [n_prims][dim] caller's element indices
+  unsigned long long* stats;  // [4] status block
+  int64_t n_prims, n_verts;
+  float tau;              // traversal slack, 2^-18 x bbox diagonal
+  float lo[3], hi[3];     // bbox
+};
+
+constexpr int kStatSteps = 0, kStatCapped = 1, kStatFlags = 2;
+constexpr unsigned long long kFlagTimeout = 1ull;
+
+}  // namespace bvc
+
+struct bvc_geometry_s {
+  int32_t dim;
+  int64_t n_verts, n_prims, n_nodes;
+  double measure;
+  float lo[3], hi[3];
+  void* arena;            // one device allocation holding everything below
+  size_t arena_bytes;
+  bvc::DevGeometry dev;
+};
+
+namespace bvc {
+
+// Host helpers (bvc_common.cu)
+bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);
+int num_sms();
+int max_blocks_per_sm(const void* kernel, int block, size_t smem);
+
+}  // namespace bvc
+
+#define BVC_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return BVC_ERR_CUDA;    \
+  } while (0)
+
+#define BVC_LAUNCH_CHECK()                                   \
+  do {                                                       \
+    if (cudaPeekAtLastError() != cudaSuccess) {              \
+      (void)cudaGetLastError();                              \
+      return BVC_ERR_CUDA;                                   \
+    }                                                        \
+  } while (0)

@@ -1,0 +1,176 @@
+// bvc_source.cu -- source samples (K4): jittered candidates over the
+// bounding box, kept by the canonical FP32 crossing test, compacted in
+// candidate order by a deterministic block scan.
+#include <cmath>
+
+#include "bvc_device.cuh"
+#include "bvc_internal.h"
+
+namespace bvc {
+
+constexpr int kSrcBlock = 256;
+constexpr int kSegTile = 1024;
+
+struct SrcParams {
+  DevGeometry G;
+  DevFunction f;
+  int32_t G0, G1;
+  uint64_t seed;
+  double lo0, lo1, h0, h1, box;
+  int64_t ncand;
+  float* yc;          // [2][ncand] candidate positions (workspace)
+  uint8_t* flag;      // [ncand] (workspace)
+  int64_t* bcount;    // [nblocks] (workspace)
+  int64_t* boff;      // [nblocks] (workspace)
+  float* src_y;       // [2][ncand]
+  double* src_c;      // [ncand]
+  int64_t* n_src;     // [1]
+  int64_t nblocks;
+};
+
+// Candidate position (FP64, rounded to FP32) and the crossing-number test
+// against every segment, staged through shared memory.
+__global__ void __launch_bounds__(kSrcBlock) k_src_classify(const SrcParams S) {
+  __shared__ float4 seg[kSegTile];
+  const int64_t c = blockIdx.x * (int64_t)kSrcBlock + threadIdx.x;
+  float px = 0.0f, py = 0.0f;
+  if (c < S.ncand) {
+    const U4 r = philox_draw(S.seed, (uint64_t)c, 0u, 2u);
+    const int64_t c0 = c % S.G0, c1 = c / S.G0;
+    const double y0 = __dadd_rn(S.lo0, __dmul_rn(__dadd_rn((double)c0, u01d(r.x)), S.h0));
+    const double y1 = __dadd_rn(S.lo1, __dmul_rn(__dadd_rn((double)c1, u01d(r.y)), S.h1));
+    px = __double2float_rn(y0);
+    py = __double2float_rn(y1);
+    S.yc[c] = px;
+    S.yc[S.ncand + c] = py;
+  }
+  int par = 0;
+  const int64_t np = S.G.n_prims;
+  for (int64_t base = 0; base < np; base += kSegTile) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kSegTile && base + q < np; q += kSrcBlock) {
+      const int32_t* f = S.G.idx + 2 * (base + q);
+      seg[q] = make_float4(S.G.verts[2 * f[0]], S.G.verts[2 * f[0] + 1], S.G.verts[2 * f[1]], S.G.verts[2 * f[1] + 1]);
+    }
+    __syncthreads();
+    const int cnt = (int)min64(kSegTile, np - base);
+    for (int q = 0; q < cnt; ++q) {
+      const float4 s = seg[q];
+      if ((s.y > py) != (s.w > py)) {
+        const float t = __fdiv_rn(__fsub_rn(py, s.y), __fsub_rn(s.w, s.y));
+        const float xi = __fmaf_rn(t, __fsub_rn(s.z, s.x), s.x);
+        if (px < xi) par ^= 1;
+      }
+    }
+  }
+  const int keep = (c < S.ncand) ? par : 0;
+  if (c < S.ncand) S.flag[c] = (uint8_t)keep;
+  const int cnt = __syncthreads_count(keep);
+  if (threadIdx.x == 0) S.bcount[blockIdx.x] = cnt;
+}
+
+// Exclusive scan of the block counts (one block, fixed order).
+__global__ void __launch_bounds__(1024) k_src_scan(const SrcParams S) {
+  __shared__ int64_t part[1024];
+  const int64_t nb = S.nblocks;
+  const int64_t per = (nb + 1023) / 1024;
+  const int64_t b0 = threadIdx.x * per, b1 = min64(nb, b0 + per);
+  int64_t s = 0;
+  for (int64_t b = b0; b < b1; ++b) s += S.bcount[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int q = 0; q < 1024; ++q) {
+      const int64_t v = part[q];
+      part[q] = acc;
+      acc += v;
+    }
+    *S.n_src = acc;
+  }
+  __syncthreads();
+  int64_t acc = part[threadIdx.x];
+  for (int64_t b = b0; b < b1; ++b) {
+    S.boff[b] = acc;
+    acc += S.bcount[b];
+  }
+}
+
+// Stable scatter of kept candidates; weight f(y) |box| (p = 1/|box| on the box).
+__global__ void __launch_bounds__(kSrcBlock) k_src_scatter(const SrcParams S) {
+  __shared__ int wsum[kSrcBlock / 32];
+  const int64_t c = blockIdx.x * (int64_t)kSrcBlock + threadIdx.x;
+  const int keep = c < S.ncand ? S.flag[c] : 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if (lane == 0) wsum[w] = __popc(bal);
+  __syncthreads();
+  int before = 0;
+  for (int q = 0; q < w; ++q) before += wsum[q];
+  before += __popc(bal & ((1u << lane) - 1u));
+  if (keep) {
+    const int64_t j = S.boff[blockIdx.x] + before;
+    float y[2] = {S.yc[c], S.yc[S.ncand + c]};
+    S.src_y[j] = y[0];
+    S.src_y[S.ncand + j] = y[1];
+    S.src_c[j] = (double)eval_fn<2>(S.f, y) * S.box;
+  }
+}
+
+}  // namespace bvc
+
+using namespace bvc;
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+extern "C" bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes) {
+  if (n_cand < 0 || bytes == nullptr) return BVC_ERR_INVALID_ARG;
+  const int64_t nb = (n_cand + kSrcBlock - 1) / kSrcBlock;
+  *bytes = al256((size_t)n_cand * 2 * sizeof(float)) + al256((size_t)n_cand) + 2 * al256((size_t)nb * 8);
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[2], uint64_t seed,
+                                        bvc_cache* cache, void* workspace, size_t workspace_bytes,
+                                        bvc_stream stream) {
+  if (g == nullptr || grid == nullptr || cache == nullptr) return BVC_ERR_INVALID_ARG;
+  if (g->dim != 2) return BVC_ERR_UNSUPPORTED;
+  const int64_t ncand = (int64_t)grid[0] * grid[1];
+  if (grid[0] < 1 || grid[1] < 1 || ncand != cache->n_src_cand || cache->src_y == nullptr ||
+      cache->src_c == nullptr || cache->n_src_dev == nullptr || workspace == nullptr)
+    return BVC_ERR_INVALID_ARG;
+  size_t need = 0;
+  bvc_sample_source_workspace_size(ncand, &need);
+  if (workspace_bytes < need) return BVC_ERR_WORKSPACE;
+  SrcParams S{};
+  S.G = g->dev;
+  if (!make_dev_function(ffn, 2, &S.f)) return BVC_ERR_INVALID_ARG;
+  S.G0 = grid[0];
+  S.G1 = grid[1];
+  S.seed = seed;
+  S.lo0 = g->lo[0];
+  S.lo1 = g->lo[1];
+  const double ext0 = (double)g->hi[0] - (double)g->lo[0], ext1 = (double)g->hi[1] - (double)g->lo[1];
+  S.h0 = ext0 / grid[0];
+  S.h1 = ext1 / grid[1];
+  S.box = ext0 * ext1;
+  S.ncand = ncand;
+  S.nblocks = (ncand + kSrcBlock - 1) / kSrcBlock;
+  char* w = (char*)workspace;
+  S.yc = (float*)w;
+  w += al256((size_t)ncand * 2 * sizeof(float));
+  S.flag = (uint8_t*)w;
+  w += al256((size_t)ncand);
+  S.bcount = (int64_t*)w;
+  w += al256((size_t)S.nblocks * 8);
+  S.boff = (int64_t*)w;
+  S.src_y = cache->src_y;
+  S.src_c = cache->src_c;
+  S.n_src = cache->n_src_dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_src_classify<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+  k_src_scan<<<1, 1024, 0, s>>>(S);
+  k_src_scatter<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}

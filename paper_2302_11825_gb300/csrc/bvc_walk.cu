@@ -1,0 +1,434 @@
+// bvc_walk.cu -- walk on spheres (K2 cache walks, K6 pointwise walks), the
+// per-start reduction (K3), and the cache build / pointwise estimate entry
+// points.
+//
+// Walk kernel design.  One thread carries one walk at a time; a persistent
+// grid (all SMs, as many blocks as fit) pulls walks from a global counter in
+// chunks of 128 per warp.  Whenever lanes finish, the warp refills exactly
+// those lanes from its chunk before the next step, so every lane of every
+// warp keeps stepping while work remains (warp-level compaction of finished
+// walks) and all lanes execute the same step code together.  Each step is
+// one BVH closest-point query (fixed-size traversal stack in shared memory),
+// one Philox draw and, when f is non-zero, one source-term evaluation.
+// Per-walk results go to FP32 records; K3 reduces them in FP64 in a fixed
+// order, so results do not depend on scheduling.
+#include <cmath>
+
+#include "bvc_device.cuh"
+#include "bvc_internal.h"
+
+namespace bvc {
+
+constexpr int kWalkBlock = 128;
+constexpr int kStack = 32;
+constexpr int64_t kChunk = 128;
+
+struct WalkParams {
+  DevGeometry G;
+  DevFunction g, f;
+  const float* starts;  // [D][pt_stride]
+  const float* nrm;     // [D][pt_stride] or null
+  int64_t pt_stride;
+  int64_t i0;           // first start of this launch
+  int32_t W;
+  int64_t total;        // walks in this launch
+  uint64_t wid0;        // walk id of walk 0 of this launch
+  float eps;
+  int32_t max_steps;
+  uint64_t seed;
+  uint32_t tag;
+  float* rec;           // planes of `total` floats
+  int32_t* steps;       // optional per-walk debug output
+  int32_t* prim;
+  unsigned long long* counter;
+};
+
+template <int D, bool HAS_F, bool GN>
+__global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
+  __shared__ int snode[kStack * kWalkBlock];
+  __shared__ float sdist[kStack * kWalkBlock];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int64_t q_next = 0, q_end = 0;
+  bool more = true, active = false;
+  int64_t t = 0, i = 0;
+  float x[D], nu[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) x[a] = nu[a] = 0.0f;
+  float R0 = 0.0f, usrc = 0.0f, wf0 = 0.0f, wg0 = 0.0f, cv = 0.0f;
+  int k = 0;
+  unsigned long long my_steps = 0, my_capped = 0;
+  for (;;) {
+    unsigned need = __ballot_sync(FULL, !active);
+    while (need != 0u && more) {
+      if (q_next >= q_end) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)kChunk);
+        base = __shfl_sync(FULL, base, 0);
+        if ((int64_t)base >= P.total) {
+          more = false;
+          break;
+        }
+        q_next = (int64_t)base;
+        q_end = min64((int64_t)base + kChunk, P.total);
+      }
+      const int avail = (int)min64(q_end - q_next, (int64_t)__popc(need));
+      const int rank = __popc(need & ((1u << lane) - 1u));
+      if (!active && rank < avail) {
+        t = q_next + rank;
+        i = P.i0 + t / P.W;
+#pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = P.starts[a * P.pt_stride + i];
+        k = 0;
+        R0 = usrc = wf0 = wg0 = cv = 0.0f;
+        active = true;
+      }
+      q_next += avail;
+      need = __ballot_sync(FULL, !active);
+    }
+    if (!__any_sync(FULL, active)) break;
+    if (active) {
+      Hit<D> h;
+      bvh_closest<D>(P.G, x, h, snode + threadIdx.x, sdist + threadIdx.x, kWalkBlock);
+      ++k;
+      float pbar[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
+      const float d = sqrtf(h.d2);
+      if (k == 1) cv = eval_fn<D>(P.g, pbar);
+      if (d < P.eps || k >= P.max_steps) {
+        const float U = (k == 1 ? cv : eval_fn<D>(P.g, pbar)) + usrc;
+        const float s = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
+        P.rec[t] = U;
+        if (GN) {
+          float nn = 0.0f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) nn = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn);
+          P.rec[P.total + t] = s * nn;
+        } else {
+#pragma unroll
+          for (int a = 0; a < D; ++a) P.rec[(1 + a) * P.total + t] = s * nu[a];
+        }
+        if (P.steps) P.steps[t] = k;
+        if (P.prim) P.prim[t] = h.id;
+        my_steps += (unsigned long long)k;
+        if (!(d < P.eps)) ++my_capped;
+        active = false;
+      } else {
+        const float R = d;
+        const U4 r = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
+        const float u0 = u01f(r.x);
+        float om[D];
+        if (D == 2) {
+          float sn, cs;
+          sincospif(2.0f * u0, &sn, &cs);
+          om[0] = cs;
+          om[D - 1] = sn;
+        } else {
+          const float u1 = u01f(r.y);
+          const float zc = 1.0f - 2.0f * u0;
+          const float st = 2.0f * sqrtf(u0 * (1.0f - u0));
+          float sn, cs;
+          sincospif(2.0f * u1, &sn, &cs);
+          om[0] = st * cs;
+          om[1] = st * sn;
+          om[D - 1] = zc;
+        }
+        if (HAS_F) {
+          const float u2 = u01f(r.z);
+          const float rho = R * u2;
+          float y[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
+          const float fy = eval_fn<D>(P.f, y);
+          // ball Green's function weights: -R rho ln(R/rho) (2D), -rho (R - rho) (3D)
+          const float wu = D == 2 ? R * rho * logf(u2) : -rho * (R - rho);
+          usrc = fmaf(wu, fy, usrc);
+          if (k == 1) {
+            wf0 = wu * fy;
+            const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
+            wg0 = -R * (1.0f - q) * fy;
+          }
+        }
+        if (k == 1) {
+          R0 = R;
+#pragma unroll
+          for (int a = 0; a < D; ++a) nu[a] = om[a];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = fmaf(R, om[a], x[a]);
+      }
+    }
+  }
+  // one atomic per warp for the step and cap counters
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my_steps += __shfl_xor_sync(FULL, my_steps, o);
+    my_capped += __shfl_xor_sync(FULL, my_capped, o);
+  }
+  if (lane == 0) {
+    if (my_steps) atomicAdd(&P.G.stats[kStatSteps], my_steps);
+    if (my_capped) atomicAdd(&P.G.stats[kStatCapped], my_capped);
+  }
+}
+
+// K3: one warp per start; lanes stride the start's walks, FP64 partials are
+// combined by a fixed xor-shuffle tree (deterministic).
+struct ReduceParams {
+  const float* rec;
+  int64_t n;       // starts in this launch
+  int32_t W;
+  int32_t planes;  // 1 + extra planes
+  int64_t stride;  // plane stride of rec
+  int32_t mode;    // 0 mean, 1 accumulate sum
+  double* out[4];  // per plane, already offset to the launch's first start
+};
+
+__global__ void __launch_bounds__(256) k_reduce(const ReduceParams R) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < R.n; i += nwarps) {
+    for (int p = 0; p < R.planes; ++p) {
+      const float* r = R.rec + p * R.stride + i * R.W;
+      double s = 0.0;
+      for (int j = lane; j < R.W; j += 32) s += (double)r[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        if (R.mode == 0)
+          R.out[p][i] = s / (double)R.W;
+        else
+          R.out[p][i] += s;
+      }
+    }
+  }
+}
+
+static int walk_grid(const void* kern) {
+  static int cached[2][2][2] = {};
+  (void)cached;
+  return num_sms() * max_blocks_per_sm(kern, kWalkBlock, 0);
+}
+
+static bvc_status launch_walk(int dim, bool has_f, bool gn, const WalkParams& P, cudaStream_t s) {
+  const void* kern = nullptr;
+  if (dim == 2) {
+    if (has_f)
+      kern = gn ? (const void*)k_walk<2, true, true> : (const void*)k_walk<2, true, false>;
+    else
+      kern = gn ? (const void*)k_walk<2, false, true> : (const void*)k_walk<2, false, false>;
+  } else {
+    if (has_f)
+      kern = gn ? (const void*)k_walk<3, true, true> : (const void*)k_walk<3, true, false>;
+    else
+      kern = gn ? (const void*)k_walk<3, false, true> : (const void*)k_walk<3, false, false>;
+  }
+  const int64_t want = (P.total + 31) / 32;
+  int grid = walk_grid(kern);
+  const int64_t need_blocks = (want + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
+  if (need_blocks < grid) grid = (int)(need_blocks > 0 ? need_blocks : 1);
+  BVC_CUDA_TRY(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
+  void* args[] = {(void*)&P};
+  BVC_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kWalkBlock), args, 0, s));
+  return BVC_OK;
+}
+
+static bvc_status launch_reduce(const ReduceParams& R, cudaStream_t s) {
+  const int64_t warps = R.n;
+  int64_t blocks = (warps * 32 + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_reduce<<<(int)blocks, 256, 0, s>>>(R);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+static bool valid_walk_args(float eps, int32_t max_steps, int32_t walks) {
+  return std::isfinite(eps) && eps > 0.0f && max_steps >= 1 && walks >= 1;
+}
+
+}  // namespace bvc
+
+using namespace bvc;
+
+extern "C" bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* starts,
+                               const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps,
+                               uint64_t seed, uint64_t id_base, uint32_t tag, float* rec, int32_t* steps,
+                               int32_t* prim, bvc_stream stream) {
+  if (g == nullptr || n < 0 || !valid_walk_args(eps, max_steps, walks)) return BVC_ERR_INVALID_ARG;
+  if (n == 0) return BVC_OK;
+  if (starts == nullptr || rec == nullptr) return BVC_ERR_INVALID_ARG;
+  WalkParams P{};
+  P.G = g->dev;
+  if (!make_dev_function(gfn, g->dim, &P.g) || !make_dev_function(ffn, g->dim, &P.f)) return BVC_ERR_INVALID_ARG;
+  P.starts = starts;
+  P.nrm = nrm;
+  P.pt_stride = n;
+  P.i0 = 0;
+  P.W = walks;
+  P.total = n * (int64_t)walks;
+  P.wid0 = id_base;
+  P.eps = eps;
+  P.max_steps = max_steps;
+  P.seed = seed;
+  P.tag = tag;
+  P.rec = rec;
+  P.steps = steps;
+  P.prim = prim;
+  // the work counter lives in the status block's spare word
+  P.counter = g->dev.stats + 3;
+  return launch_walk(g->dim, P.f.n_terms > 0, nrm != nullptr, P, (cudaStream_t)stream);
+}
+
+extern "C" bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walks, int32_t planes, int32_t mode,
+                                       double* out, bvc_stream stream) {
+  if (rec == nullptr || out == nullptr || n < 0 || walks < 1 || planes < 0 || planes > 3 || (mode != 0 && mode != 1))
+    return BVC_ERR_INVALID_ARG;
+  if (n == 0) return BVC_OK;
+  ReduceParams R{};
+  R.rec = rec;
+  R.n = n;
+  R.W = walks;
+  R.planes = 1 + planes;
+  R.stride = n * (int64_t)walks;
+  R.mode = mode;
+  for (int p = 0; p < R.planes; ++p) R.out[p] = out + p * n;
+  return launch_reduce(R, (cudaStream_t)stream);
+}
+
+// Workspace layout for the chunked drivers: [0, 256) work counter, then records.
+static constexpr size_t kWsHead = 256;
+
+extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+                                                     size_t* full_bytes) {
+  if (g == nullptr || opts == nullptr || opts->n_samples < 0 || opts->walks_per_sample < 1)
+    return BVC_ERR_INVALID_ARG;
+  const size_t per_sample = (size_t)opts->walks_per_sample * 2 * sizeof(float);
+  size_t src = 0;
+  const int64_t ncand = (int64_t)opts->src_grid[0] * opts->src_grid[1];
+  if (ncand > 0) bvc_sample_source_workspace_size(ncand, &src);
+  const size_t mn = kWsHead + per_sample, full = kWsHead + per_sample * (size_t)opts->n_samples;
+  if (min_bytes) *min_bytes = mn > src ? mn : src;
+  if (full_bytes) *full_bytes = full > src ? full : src;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                      const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
+                                      size_t workspace_bytes, bvc_stream stream) {
+  if (g == nullptr || opts == nullptr || cache == nullptr) return BVC_ERR_INVALID_ARG;
+  const int D = g->dim;
+  const int64_t N = opts->n_samples;
+  const int32_t W = opts->walks_per_sample;
+  if (cache->dim != D || cache->n != N || N < 1 || !valid_walk_args((float)opts->eps, opts->max_steps, W) ||
+      !(opts->offset_l > 0.0) || cache->z == nullptr || cache->nrm == nullptr || cache->u_hat == nullptr ||
+      cache->dudn_hat == nullptr || cache->packed == nullptr || workspace == nullptr)
+    return BVC_ERR_INVALID_ARG;
+  const int64_t ncand = (int64_t)opts->src_grid[0] * opts->src_grid[1];
+  if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
+  WalkParams P{};
+  P.G = g->dev;
+  if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
+  const size_t per_sample = (size_t)W * 2 * sizeof(float);
+  if (workspace_bytes < kWsHead + per_sample) return BVC_ERR_WORKSPACE;
+  int64_t chunk = (int64_t)((workspace_bytes - kWsHead) / per_sample);
+  if (chunk > N) chunk = N;
+  cudaStream_t s = (cudaStream_t)stream;
+  cache->bnd_measure = g->measure;
+  bvc_status st = bvc_sample_boundary(g, N, opts->offset_l, opts->seed, cache->z, cache->nrm, nullptr, stream);
+  if (st != BVC_OK) return st;
+  P.starts = cache->z;
+  P.nrm = cache->nrm;
+  P.pt_stride = N;
+  P.W = W;
+  P.eps = (float)opts->eps;
+  P.max_steps = opts->max_steps;
+  P.seed = opts->seed;
+  P.tag = 0;
+  P.counter = (unsigned long long*)workspace;
+  P.rec = (float*)((char*)workspace + kWsHead);
+  for (int64_t i0 = 0; i0 < N; i0 += chunk) {
+    const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
+    P.i0 = i0;
+    P.total = c * (int64_t)W;
+    P.wid0 = opts->walk_id_base + (uint64_t)i0 * (uint64_t)W;
+    st = launch_walk(D, P.f.n_terms > 0, true, P, s);
+    if (st != BVC_OK) return st;
+    ReduceParams R{};
+    R.rec = P.rec;
+    R.n = c;
+    R.W = W;
+    R.planes = 2;
+    R.stride = P.total;
+    R.mode = 0;
+    R.out[0] = cache->u_hat + i0;
+    R.out[1] = cache->dudn_hat + i0;
+    st = launch_reduce(R, s);
+    if (st != BVC_OK) return st;
+  }
+  if (ncand > 0) {
+    st = bvc_sample_source(g, ffn, opts->src_grid, opts->seed, cache, workspace, workspace_bytes, stream);
+    if (st != BVC_OK) return st;
+  }
+  return bvc_cache_pack(cache, stream);
+}
+
+extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
+                                                  size_t* full_bytes) {
+  if ((dim != 2 && dim != 3) || m < 0 || walks < 1) return BVC_ERR_INVALID_ARG;
+  const size_t per_pt = (size_t)walks * (1 + dim) * sizeof(float);
+  if (min_bytes) *min_bytes = kWsHead + per_pt;
+  if (full_bytes) *full_bytes = kWsHead + per_pt * (size_t)m;
+  return BVC_OK;
+}
+
+extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* pts,
+                                   int64_t m, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                                   uint64_t id_base, double* u_sum, double* grad_sum, void* workspace,
+                                   size_t workspace_bytes, bvc_stream stream) {
+  if (g == nullptr || m < 0 || !valid_walk_args(eps, max_steps, walks)) return BVC_ERR_INVALID_ARG;
+  if (m == 0) return BVC_OK;
+  if (pts == nullptr || u_sum == nullptr || workspace == nullptr) return BVC_ERR_INVALID_ARG;
+  const int D = g->dim;
+  WalkParams P{};
+  P.G = g->dev;
+  if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
+  const size_t per_pt = (size_t)walks * (1 + D) * sizeof(float);
+  if (workspace_bytes < kWsHead + per_pt) return BVC_ERR_WORKSPACE;
+  int64_t chunk = (int64_t)((workspace_bytes - kWsHead) / per_pt);
+  if (chunk > m) chunk = m;
+  cudaStream_t s = (cudaStream_t)stream;
+  P.starts = pts;
+  P.nrm = nullptr;
+  P.pt_stride = m;
+  P.W = walks;
+  P.eps = eps;
+  P.max_steps = max_steps;
+  P.seed = seed;
+  P.tag = 3;
+  P.counter = (unsigned long long*)workspace;
+  P.rec = (float*)((char*)workspace + kWsHead);
+  for (int64_t i0 = 0; i0 < m; i0 += chunk) {
+    const int64_t c = (m - i0) < chunk ? (m - i0) : chunk;
+    P.i0 = i0;
+    P.total = c * (int64_t)walks;
+    P.wid0 = id_base + (uint64_t)i0 * (uint64_t)walks;
+    bvc_status st = launch_walk(D, P.f.n_terms > 0, false, P, s);
+    if (st != BVC_OK) return st;
+    ReduceParams R{};
+    R.rec = P.rec;
+    R.n = c;
+    R.W = walks;
+    R.planes = grad_sum ? 1 + D : 1;
+    R.stride = P.total;
+    R.mode = 1;
+    R.out[0] = u_sum + i0;
+    if (grad_sum)
+      for (int a = 0; a < D; ++a) R.out[1 + a] = grad_sum + (int64_t)a * m + i0;
+    st = launch_reduce(R, s);
+    if (st != BVC_OK) return st;
+  }
+  return BVC_OK;
+}

@@ -1,0 +1,258 @@
+// bvh_build.cpp -- host construction of the closest-point BVH (Sec. 4
+// "Setup": walk on spheres answers its closest-point queries with a
+// bounding volume hierarchy).
+//
+// Binary tree, binned SAH (16 bins per axis on primitive centroids; box
+// perimeter in 2D, surface area in 3D), leaves of at most 4 primitives.
+// Where the remaining depth budget would not fit a balanced subtree the
+// split falls back to the centroid median, which bounds the depth by
+// kMaxDepth so the traversal's fixed-size stack never overflows.  The tree is
+// flattened in depth-first order (a parent precedes its children) with both
+// child boxes stored in the parent, so one node fetch (48 B in 2D, 64 B in
+// 3D, 16-byte vector loads) decides the visiting order of both children.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <vector_types.h>
+
+static inline float4 make_float4(float x, float y, float z, float w) {
+  float4 r;
+  r.x = x;
+  r.y = y;
+  r.z = z;
+  r.w = w;
+  return r;
+}
+
+namespace bvc {
+
+constexpr int kLeafMax = 4;
+constexpr int kMaxDepth = 30;  // traversal stack holds 32 entries
+constexpr int kBins = 16;
+
+struct Box {
+  float lo[3], hi[3];
+  void reset() {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = INFINITY;
+      hi[a] = -INFINITY;
+    }
+  }
+  void grow(const Box& b) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], b.lo[a]);
+      hi[a] = std::max(hi[a], b.hi[a]);
+    }
+  }
+  void grow(const float* p) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], p[a]);
+      hi[a] = std::max(hi[a], p[a]);
+    }
+  }
+  double cost(int dim) const {
+    if (lo[0] > hi[0]) return 0.0;
+    const double ex = (double)hi[0] - lo[0], ey = (double)hi[1] - lo[1];
+    if (dim == 2) return ex + ey;
+    const double ez = (double)hi[2] - lo[2];
+    return ex * ey + ey * ez + ez * ex;
+  }
+};
+
+struct Builder {
+  int dim;
+  std::vector<Box> pbox;
+  std::vector<float> cen;  // 3 per prim
+  std::vector<int32_t> order;
+  std::vector<float4> nodes;
+  int per_node;
+
+  static int32_t leaf(int64_t first, int64_t count) { return ~(int32_t)((first << 3) | count); }
+
+  static int ceil_log2(int64_t x) {
+    int r = 0;
+    while ((int64_t(1) << r) < x) ++r;
+    return r;
+  }
+
+  int64_t median_split(int64_t start, int64_t count, const Box& cb) {
+    int axis = 0;
+    for (int a = 1; a < dim; ++a)
+      if (cb.hi[a] - cb.lo[a] > cb.hi[axis] - cb.lo[axis]) axis = a;
+    const int64_t mid = start + count / 2;
+    std::nth_element(order.begin() + start, order.begin() + mid, order.begin() + start + count,
+                     [&](int32_t x, int32_t y) {
+                       const float a = cen[3 * x + axis], b = cen[3 * y + axis];
+                       return a < b || (a == b && x < y);
+                     });
+    return mid;
+  }
+
+  int64_t sah_split(int64_t start, int64_t count, const Box& cb) {
+    double best = INFINITY;
+    int best_axis = -1, best_bin = -1;
+    for (int a = 0; a < dim; ++a) {
+      const float ext = cb.hi[a] - cb.lo[a];
+      if (!(ext > 0.0f)) continue;
+      Box bb[kBins];
+      int64_t bn[kBins] = {0};
+      for (int b = 0; b < kBins; ++b) bb[b].reset();
+      const float sc = kBins / ext;
+      for (int64_t i = start; i < start + count; ++i) {
+        const int32_t p = order[i];
+        int b = (int)((cen[3 * p + a] - cb.lo[a]) * sc);
+        b = std::min(std::max(b, 0), kBins - 1);
+        bb[b].grow(pbox[p]);
+        ++bn[b];
+      }
+      double lc[kBins];
+      int64_t ln[kBins];
+      Box acc;
+      acc.reset();
+      int64_t n = 0;
+      for (int b = 0; b < kBins - 1; ++b) {
+        acc.grow(bb[b]);
+        n += bn[b];
+        lc[b] = acc.cost(dim);
+        ln[b] = n;
+      }
+      acc.reset();
+      n = 0;
+      for (int b = kBins - 1; b > 0; --b) {
+        acc.grow(bb[b]);
+        n += bn[b];
+        if (ln[b - 1] == 0 || n == 0) continue;
+        const double c = lc[b - 1] * ln[b - 1] + acc.cost(dim) * n;
+        if (c < best) {
+          best = c;
+          best_axis = a;
+          best_bin = b - 1;
+        }
+      }
+    }
+    if (best_axis < 0) return -1;
+    const float sc = kBins / (cb.hi[best_axis] - cb.lo[best_axis]);
+    auto it = std::partition(order.begin() + start, order.begin() + start + count, [&](int32_t p) {
+      int b = (int)((cen[3 * p + best_axis] - cb.lo[best_axis]) * sc);
+      b = std::min(std::max(b, 0), kBins - 1);
+      return b <= best_bin;
+    });
+    const int64_t mid = it - order.begin();
+    if (mid == start || mid == start + count) return -1;
+    return mid;
+  }
+
+  // Returns the child encoding; fills the subtree's box.
+  int32_t build(int64_t start, int64_t count, int depth, Box& out) {
+    Box b, cb;
+    b.reset();
+    cb.reset();
+    for (int64_t i = start; i < start + count; ++i) {
+      b.grow(pbox[order[i]]);
+      cb.grow(&cen[3 * order[i]]);
+    }
+    out = b;
+    if (count <= kLeafMax) return leaf(start, count);
+    int64_t mid = -1;
+    const bool tight = depth + ceil_log2((count + kLeafMax - 1) / kLeafMax) + 1 >= kMaxDepth;
+    if (!tight) mid = sah_split(start, count, cb);
+    if (mid < 0) mid = median_split(start, count, cb);
+    const int64_t id = (int64_t)nodes.size() / per_node;
+    nodes.resize(nodes.size() + per_node);
+    Box bl, br;
+    const int32_t cl = build(start, mid - start, depth + 1, bl);
+    const int32_t cr = build(mid, start + count - mid, depth + 1, br);
+    write_node(id, bl, br, cl, cr);
+    return (int32_t)id;
+  }
+
+  void write_node(int64_t id, const Box& L, const Box& R, int32_t cl, int32_t cr) {
+    float4* n = &nodes[id * per_node];
+    float ci[2];
+    std::memcpy(&ci[0], &cl, 4);
+    std::memcpy(&ci[1], &cr, 4);
+    if (dim == 2) {
+      n[0] = make_float4(L.lo[0], L.lo[1], L.hi[0], L.hi[1]);
+      n[1] = make_float4(R.lo[0], R.lo[1], R.hi[0], R.hi[1]);
+      n[2] = make_float4(ci[0], ci[1], 0.0f, 0.0f);
+    } else {
+      n[0] = make_float4(L.lo[0], L.lo[1], L.lo[2], L.hi[0]);
+      n[1] = make_float4(L.hi[1], L.hi[2], R.lo[0], R.lo[1]);
+      n[2] = make_float4(R.lo[2], R.hi[0], R.hi[1], R.hi[2]);
+      n[3] = make_float4(ci[0], ci[1], 0.0f, 0.0f);
+    }
+  }
+};
+
+// Builds the flattened BVH.  prims_out: BVH-ordered primitive records
+// (2D: (a, b - a); 3D: (a, -), (b - a, -), (c - a, -)), ids_out: caller's
+// index per record.  Returns the node count.
+int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::vector<float4>& nodes_out,
+                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out) {
+  Builder B;
+  B.dim = dim;
+  B.per_node = dim == 2 ? 3 : 4;
+  B.pbox.resize(np);
+  B.cen.assign(3 * np, 0.0f);
+  B.order.resize(np);
+  for (int64_t e = 0; e < np; ++e) {
+    Box b;
+    b.reset();
+    double c[3] = {0, 0, 0};
+    for (int v = 0; v < dim; ++v) {
+      float p[3] = {0, 0, 0};
+      for (int a = 0; a < dim; ++a) p[a] = V[(int64_t)F[e * dim + v] * dim + a];
+      b.grow(p);
+      for (int a = 0; a < dim; ++a) c[a] += p[a];
+    }
+    for (int a = dim; a < 3; ++a) b.lo[a] = b.hi[a] = 0.0f;
+    B.pbox[e] = b;
+    for (int a = 0; a < 3; ++a) B.cen[3 * e + a] = (float)(c[a] / dim);
+    B.order[e] = (int32_t)e;
+  }
+  // Root is always an internal node.
+  B.nodes.resize(B.per_node);
+  Box bl, br;
+  int32_t cl, cr;
+  if (np <= kLeafMax) {
+    Box dummy;
+    cl = B.build(0, np, 1, bl);
+    br.reset();
+    cr = Builder::leaf(0, 0);
+  } else {
+    Box cb;
+    cb.reset();
+    for (int64_t i = 0; i < np; ++i) cb.grow(&B.cen[3 * i]);
+    int64_t mid = B.sah_split(0, np, cb);
+    if (mid < 0) mid = B.median_split(0, np, cb);
+    cl = B.build(0, mid, 1, bl);
+    cr = B.build(mid, np - mid, 1, br);
+  }
+  B.write_node(0, bl, br, cl, cr);
+  nodes_out.swap(B.nodes);
+  const int per_prim = dim == 2 ? 1 : 3;
+  prims_out.assign(np * per_prim, make_float4(0, 0, 0, 0));
+  ids_out.resize(np);
+  for (int64_t q = 0; q < np; ++q) {
+    const int32_t e = B.order[q];
+    ids_out[q] = e;
+    const int32_t* f = F + (int64_t)e * dim;
+    if (dim == 2) {
+      const float ax = V[2 * f[0]], ay = V[2 * f[0] + 1];
+      prims_out[q] = make_float4(ax, ay, V[2 * f[1]] - ax, V[2 * f[1] + 1] - ay);
+    } else {
+      const float* a = V + 3 * (int64_t)f[0];
+      const float* b = V + 3 * (int64_t)f[1];
+      const float* c = V + 3 * (int64_t)f[2];
+      prims_out[3 * q] = make_float4(a[0], a[1], a[2], 0.0f);
+      prims_out[3 * q + 1] = make_float4(b[0] - a[0], b[1] - a[1], b[2] - a[2], 0.0f);
+      prims_out[3 * q + 2] = make_float4(c[0] - a[0], c[1] - a[1], c[2] - a[2], 0.0f);
+    }
+  }
+  return (int64_t)nodes_out.size() / B.per_node;
+}
+
+}  // namespace bvc

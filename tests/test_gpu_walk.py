@@ -1,0 +1,130 @@
+"""GPU parity for the walks (K2 cache walks, K6 pointwise walks) and the
+per-start reduction (K3): walks replayed from the same Philox streams as the
+FP64 oracle agree to 1e-4 relative unless their discrete history (step
+count, final closest element) differs; the fraction of such diverging walks
+is reported and bounded."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_11825_gb300 import bvc
+from paper_2302_11825_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+def _rel(a, b, scale, floor):
+    return np.abs(a - b) / np.maximum(scale, floor)
+
+
+def _replay(V, F, g, f, starts, nrm, W, eps, seed, tag=0, max_steps=1 << 14, bvh=None, label=""):
+    geom = bvc.Geometry(V, F)
+    dim = V.shape[1]
+    starts = np.ascontiguousarray(starts, np.float32)
+    rec, steps, prim = bvc.walk(geom, g, f, bvc.soa(starts), None if nrm is None else bvc.soa(nrm), W, eps,
+                                max_steps, seed, 0, tag, debug=True)
+    torch.cuda.synchronize()
+    rec = rec.cpu().numpy().astype(np.float64)
+    steps, prim = steps.cpu().numpy(), prim.cpu().numpy()
+    o = oracle.walks(bvh or oracle.BVH(V, F), g, f, starts, W, eps, max_steps, seed, 0, tag)
+    if nrm is not None:
+        nn = np.repeat(np.asarray(nrm, np.float32).astype(np.float64), W, axis=0)
+        go = np.sum(o["grad"] * nn, 1)[None, :]
+    else:
+        go = o["grad"].T
+    same = (steps == o["steps"]) & (prim == o["prim"])
+    div = 1.0 - same.mean()
+    eu = _rel(rec[0], o["U"], o["scale"][:, 0], 1e-3 * np.abs(o["U"]).max())[same]
+    eg = np.max(_rel(rec[1:], go, o["scale"][:, 1][None, :], 1e-3 * np.abs(go).max() + 1e-30), axis=0)[same]
+    print(f"[walk replay {label}] walks={len(same)} diverging={div:.2e} max_rel_U={eu.max():.2e} "
+          f"max_rel_grad={eg.max():.2e} mean_steps={o['steps'].mean():.2f}")
+    return div, eu, eg, steps, o
+
+
+def test_replay_circle_configuration():
+    w = wl.circle_laplace()
+    z, n, _ = oracle.sample_boundary(w.V, w.F, w.n_samples, w.offset_l, seed=0)
+    div, eu, eg, steps, o = _replay(w.V, w.F, w.g, w.f, z.astype(np.float32), n.astype(np.float32), w.walks,
+                                    w.eps, 0, label="circle 1024x64")
+    assert div < 0.01
+    assert eu.max() < REL_TOL and eg.max() < REL_TOL
+
+
+def test_replay_star_poisson_subset():
+    w = wl.star_poisson(grid=16)
+    z, n, _ = oracle.sample_boundary(w.V, w.F, w.n_samples, w.offset_l, seed=1)
+    sel = np.arange(0, w.n_samples, 128)  # 512 samples spread over the boundary
+    div, eu, eg, _, _ = _replay(w.V, w.F, w.g, w.f, z[sel].astype(np.float32), n[sel].astype(np.float32), 32,
+                                w.eps, 1, label="star 512x32 with source")
+    assert div < 0.02
+    assert eu.max() < REL_TOL and eg.max() < REL_TOL
+
+
+def test_replay_icosphere_full_mesh_subset():
+    V, F, _ = wl.perturbed_icosphere(8, 0)
+    eps = 1e-3 * wl.bbox_diagonal(V)
+    z, n, _ = oracle.sample_boundary(V, F, 262144, 5 * eps, seed=2)
+    sel = np.arange(0, 262144, 1024)
+    g = [(wl.EXP_TRIG, [1.0, 0.5, 0.3, 0.4])]
+    div, eu, eg, _, _ = _replay(V, F, g, [], z[sel].astype(np.float32), n[sel].astype(np.float32), 16, eps, 2,
+                                label="icosphere8 256x16")
+    assert div < 0.02
+    assert eu.max() < REL_TOL and eg.max() < REL_TOL
+
+
+def test_replay_pointwise_gradient_3d():
+    V, F, _ = wl.perturbed_icosphere(4, 0)
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(-0.5, 0.5, (300, 3)).astype(np.float32)
+    g = [(wl.POLY, wl.poly3d_coeffs({(1, 1, 1): 1.0, (2, 0, 0): 0.5, (0, 0, 2): -0.5}))]
+    f = [(wl.POLY, [0.7])]
+    div, eu, eg, _, _ = _replay(V, F, g, f, pts, None, 8, 1e-3, 9, tag=3, label="pointwise 3D")
+    assert div < 0.02
+    assert eu.max() < REL_TOL and eg.max() < REL_TOL
+
+
+def test_step_cap_and_status():
+    V, F = wl.circle_polygon(256)
+    geom = bvc.Geometry(V, F)
+    geom.stats(reset=True)
+    pts = bvc.soa(np.zeros((64, 2), np.float32))
+    rec, steps, _ = bvc.walk(geom, [(wl.POLY, [1.0])], [], pts, None, 4, 1e-6, 3, 0, debug=True)
+    st = geom.stats(reset=True)
+    assert steps.max().item() <= 3
+    assert st["capped"] > 0 and st["status"] == bvc.WARN_WALK_CAP
+    assert st["steps"] == int(steps.sum().item())
+
+
+def test_reduce_matches_oracle():
+    rng = np.random.default_rng(4)
+    n, W = 777, 37
+    rec = rng.standard_normal((3, n * W)).astype(np.float32)
+    out = bvc.reduce_walks(torch.from_numpy(rec).cuda(), n, W, mode=0)
+    torch.cuda.synchronize()
+    U = rec[0].astype(np.float64)
+    grad = rec[1:].T.astype(np.float64)
+    uh, _ = oracle.reduce_walks(U, grad, None, W)
+    np.testing.assert_allclose(out[0].cpu().numpy(), uh, rtol=1e-12, atol=1e-14)
+    g0, _ = oracle.reduce_walks(rec[1].astype(np.float64), grad, None, W)
+    np.testing.assert_allclose(out[1].cpu().numpy(), g0, rtol=1e-12, atol=1e-14)
+    # accumulate mode adds sums
+    acc = torch.ones((3, n), dtype=torch.float64, device="cuda")
+    bvc.reduce_walks(torch.from_numpy(rec).cuda(), n, W, mode=1, out=acc)
+    np.testing.assert_allclose(acc[0].cpu().numpy(), 1.0 + uh * W, rtol=1e-12)
+
+
+def test_cache_build_chunking_is_bit_identical():
+    w = wl.circle_laplace(n_samples=1000, walks=16)
+    geom = bvc.Geometry(w.V, w.F)
+    opts = bvc.cache_opts(w.n_samples, w.walks, w.offset_l, w.eps, seed=3)
+    mn, full = bvc.cache_build_workspace_size(geom, opts)
+    a = bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, w.n_samples), ws=bvc.workspace(full))
+    b = bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, w.n_samples), ws=bvc.workspace(mn + 7 * 16 * 8))
+    torch.cuda.synchronize()
+    assert torch.equal(a.u_hat, b.u_hat) and torch.equal(a.dudn_hat, b.dudn_hat)
+    with pytest.raises(bvc.BvcError) as e:
+        bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, w.n_samples), ws=bvc.workspace(mn - 64))
+    assert e.value.status == bvc.ERR_WORKSPACE

@@ -1,0 +1,112 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/bvc.h declares; host-side argument validation needs no GPU; the
+product package never touches the oracle."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bvc.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b((?:bvc|wos)_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2302_11825_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["bvc_geometry_create", "bvc_cache_build", "bvc_evaluate", "wos_estimate",
+                     "bvc_query_closest", "bvc_walk", "bvc_sample_boundary", "bvc_get_solution"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    lib.bvc_version.restype = C.c_int32
+    assert lib.bvc_version() >= 100
+    lib.bvc_status_string.restype = C.c_char_p
+    lib.bvc_status_string.argtypes = [C.c_int]
+    assert lib.bvc_status_string(0) == b"ok"
+    assert b"workspace" in lib.bvc_status_string(7)
+
+
+def _create(lib, V, F):
+    lib.bvc_geometry_create.restype = C.c_int
+    lib.bvc_geometry_create.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.POINTER(C.c_void_p)]
+    h = C.c_void_p()
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    st = lib.bvc_geometry_create(V.shape[1], V.ctypes.data_as(C.c_void_p), V.shape[0],
+                                 F.ctypes.data_as(C.c_void_p), F.shape[0], None, C.byref(h))
+    return st, h
+
+
+def test_geometry_validation_on_host(lib):
+    # every rejection below happens before any CUDA call
+    V = np.array([[0, 0], [1, 0], [0, 1]], np.float32)
+    F = np.array([[0, 1], [1, 2], [2, 0]], np.int32)
+    bad_v = V.copy()
+    bad_v[1, 0] = np.nan
+    assert _create(lib, bad_v, F)[0] == 2          # non-finite vertex
+    assert _create(lib, V, np.array([[0, 1], [1, 5], [2, 0]]))[0] == 2  # index out of range
+    assert _create(lib, V, np.array([[0, 1], [1, 1], [2, 0]]))[0] == 2  # zero-length segment
+    tri = np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0]], np.float32)
+    assert _create(lib, tri, np.array([[0, 1, 2]]))[0] == 2             # zero-area triangle
+    lib.bvc_geometry_create.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.POINTER(C.c_void_p)]
+    h = C.c_void_p()
+    assert lib.bvc_geometry_create(4, None, 3, None, 3, None, C.byref(h)) == 1
+    assert lib.bvc_geometry_create(2, None, 3, None, 3, None, None) == 1
+
+
+def test_entry_points_reject_null_handles(lib):
+    lib.bvc_query_closest.restype = C.c_int
+    assert lib.bvc_query_closest(None, None, C.c_int64(4), None, None, None, None) == 1
+    lib.bvc_walk.restype = C.c_int
+    assert lib.bvc_walk(None, None, None, None, None, C.c_int64(1), C.c_int32(1), C.c_float(1e-3), C.c_int32(10),
+                        C.c_uint64(0), C.c_uint64(0), C.c_uint32(0), None, None, None, None) == 1
+    lib.bvc_cache_build.restype = C.c_int
+    assert lib.bvc_cache_build(None, None, None, None, None, None, C.c_size_t(0), None) == 1
+    lib.bvc_evaluate.restype = C.c_int
+    assert lib.bvc_evaluate(None, None, None, C.c_size_t(0), None) == 1
+    lib.wos_estimate.restype = C.c_int
+    assert lib.wos_estimate(None, None, None, None, C.c_int64(1), C.c_int32(1), C.c_float(1e-3), C.c_int32(1),
+                            C.c_uint64(0), C.c_uint64(0), None, None, None, C.c_size_t(0), None) == 1
+
+
+def test_workspace_size_queries_are_host_only(lib):
+    lib.wos_estimate_workspace_size.restype = C.c_int
+    mn, full = C.c_size_t(), C.c_size_t()
+    assert lib.wos_estimate_workspace_size(2, C.c_int64(1000), 64, C.byref(mn), C.byref(full)) == 0
+    assert full.value == 256 + 1000 * 64 * 3 * 4 and mn.value == 256 + 64 * 3 * 4
+    lib.bvc_sample_source_workspace_size.restype = C.c_int
+    b = C.c_size_t()
+    assert lib.bvc_sample_source_workspace_size(C.c_int64(65536), C.byref(b)) == 0 and b.value > 65536 * 8
+
+
+def test_product_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2302_11825_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "liboracle" not in text and "bvc_oracle" not in text, f
