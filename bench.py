@@ -1,0 +1,556 @@
+"""Benchmark: boundary value caching on one GB300 (and N-GPU replicas).
+
+One step = one full BVC solve of the 2D Poisson workload (nonconvex star
+polygon with 20k segments, 8 Gaussian-bump sources, g = x^2 - y^2):
+  cache build (boundary samples, 65536 x 256 walks, per-sample reduction,
+  65536 source candidates, packing) -> all-pairs gather at every interior
+  grid point farther than l from the boundary -> pointwise walk on spheres
+  (256 walks) at the points within l -> GetSolution for both sets.
+value = interior points solved per second (device-resident inputs); e2e =
+the same through the C ABI with the evaluation points copied in from pinned
+host memory and u, grad u copied out every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload star|circle|sphere] [--no-cpu-baseline] [--no-fixed-rmse]
+
+Under torchrun every rank solves its own replica (its own seeds); timing is
+bracketed by a barrier and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "interior pts/s at fixed RMSE (BVC vs pointwise WoS, 1 GB300); WoS steps/s; pairs/s"
+UNIT = "interior pts/s"
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+MAX_STEPS = 1 << 14
+
+# Algorithmic work per unit: bytes per BVH node fetch and
+# per primitive test, per-walk input/output bytes, FP32 flops per pair.
+BYTES_NODE = {2: 48, 3: 64}
+BYTES_PRIM = {2: 16, 3: 48}
+FLOPS_PAIR_BND = {2: 25, 3: 37}
+FLOPS_PAIR_SRC = {2: 9, 3: 13}
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, local, ws
+
+
+def init_dist(backend):
+    import torch.distributed as td
+    rank, _, ws = dist_env()
+    if ws > 1 and not td.is_initialized():
+        td.init_process_group(backend=backend)
+    return rank, ws
+
+
+def barrier():
+    import torch.distributed as td
+    if td.is_available() and td.is_initialized():
+        td.barrier()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+            os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_11825_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary for this kernel and
+    workload, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str):
+    from paper_2302_11825_gb300 import workloads as wl
+    if name == "star":
+        return wl.star_poisson()
+    if name == "circle":
+        return wl.circle_laplace()
+    if name == "sphere":
+        return wl.icosphere_laplace()
+    raise ValueError(name)
+
+
+class Solver:
+    """Device buffers and the step sequence of one BVC solve."""
+
+    def __init__(self, w, device):
+        import torch
+        from paper_2302_11825_gb300 import bvc
+        self.bvc, self.torch, self.w = bvc, torch, w
+        t0 = time.perf_counter()
+        self.geom = bvc.Geometry(w.V, w.F)
+        torch.cuda.synchronize()
+        self.geometry_build_s = time.perf_counter() - t0
+        pts = bvc.soa(w.eval_pts)
+        near = bvc.classify_near(self.geom, pts, w.offset_l).bool()
+        torch.cuda.synchronize()
+        self.far_pts = pts[:, ~near].contiguous()
+        self.near_pts = pts[:, near].contiguous()
+        self.m_far, self.m_near = self.far_pts.shape[1], self.near_pts.shape[1]
+        n_src = w.src_grid[0] * w.src_grid[1] if w.f else 0
+        self.opts = bvc.cache_opts(w.n_samples, w.walks, w.offset_l, w.eps, 0, MAX_STEPS,
+                                   src_grid=w.src_grid if n_src else (0, 0))
+        self.cache = bvc.Cache(w.dim, w.n_samples, n_src_cand=n_src)
+        self.ws_cache = bvc.workspace(bvc.cache_build_workspace_size(self.geom, self.opts)[1])
+        self.far = bvc.EvalState(self.far_pts)
+        self.near = bvc.EvalState(self.near_pts)
+        self.ws_eval = bvc.workspace(bvc.evaluate_workspace_size(self.cache, self.far))
+        self.ws_wos = bvc.workspace(bvc.wos_workspace_size(w.dim, max(self.m_near, 1), w.walks)[1])
+        self.u_far = torch.empty(self.m_far, dtype=torch.float64, device=device)
+        self.g_far = torch.empty((w.dim, self.m_far), dtype=torch.float64, device=device)
+        self.u_near = torch.empty(self.m_near, dtype=torch.float64, device=device)
+        self.g_near = torch.empty((w.dim, self.m_near), dtype=torch.float64, device=device)
+
+    def step(self, seed: int):
+        bvc, w = self.bvc, self.w
+        bvc.eval_state_reset(self.far)
+        bvc.eval_state_reset(self.near)
+        self.opts.seed = seed
+        bvc.cache_build(self.geom, w.g, w.f, self.opts, self.cache, self.ws_cache)
+        bvc.evaluate(self.cache, self.far, self.ws_eval)
+        bvc.get_solution(self.far, self.u_far, self.g_far)
+        if self.m_near:
+            bvc.wos_estimate(self.geom, w.g, w.f, self.near, w.walks, w.eps, MAX_STEPS, seed, 0, self.ws_wos)
+            bvc.get_solution(self.near, self.u_near, self.g_near)
+
+    def counting_pass(self, seed: int):
+        """Deterministic walks: one counted pass gives the node fetches and
+        primitive tests of every later pass with the same seed."""
+        g = self.geom
+        g.stats(reset=True)
+        g.set_counting(True)
+        self.bvc.eval_state_reset(self.far)
+        self.opts.seed = seed
+        self.bvc.cache_build(g, self.w.g, self.w.f, self.opts, self.cache, self.ws_cache)
+        cache_stats = g.stats(reset=True)
+        if self.m_near:
+            self.bvc.eval_state_reset(self.near)
+            self.bvc.wos_estimate(g, self.w.g, self.w.f, self.near, self.w.walks, self.w.eps, MAX_STEPS, seed, 0,
+                                  self.ws_wos)
+        near_stats = g.stats(reset=True)
+        g.set_counting(False)
+        return cache_stats, near_stats
+
+
+def walk_bytes(stats, dim, n_walks):
+    return (stats["nodes"] * BYTES_NODE[dim] + stats["prims"] * BYTES_PRIM[dim]
+            + n_walks * (2 * dim * 4 + 8))
+
+
+def fixed_rmse_comparison(device, w_lit):
+    """Manufactured variant of the same workload (same geometry and sizes,
+    closed-form u): BVC RMSE tau at the configured sizes, then the number of
+    pointwise walks per point that reaches RMSE <= tau, and both rates."""
+    import torch
+    from paper_2302_11825_gb300 import bvc
+    from paper_2302_11825_gb300 import workloads as wl
+    if w_lit.name.startswith("star"):
+        w = wl.star_poisson(manufactured=True)
+    else:
+        w = w_lit
+    if w.exact is None:
+        return None
+    s = Solver(w, device)
+    s.step(7)
+    torch.cuda.synchronize()
+    ex_far, _ = wl.eval_terms(w.exact, w.dim, s.far_pts.cpu().numpy().T.astype(np.float64))
+    ex_near, _ = wl.eval_terms(w.exact, w.dim, s.near_pts.cpu().numpy().T.astype(np.float64))
+    err = np.concatenate([s.u_far.cpu().numpy() - ex_far, s.u_near.cpu().numpy() - ex_near])
+    tau = float(np.sqrt(np.mean(err ** 2)))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for k in range(3):
+        s.step(100 + k)
+    ev1.record()
+    torch.cuda.synchronize()
+    bvc_rate = (s.m_far + s.m_near) * 3 / (ev0.elapsed_time(ev1) / 1e3)
+    # pointwise walk on spheres on a random subset of interior points
+    rng = np.random.default_rng(3)
+    allp = np.concatenate([s.far_pts.cpu().numpy().T, s.near_pts.cpu().numpy().T])
+    sub = allp[rng.choice(allp.shape[0], min(8192, allp.shape[0]), replace=False)]
+    ex_sub, _ = wl.eval_terms(w.exact, w.dim, sub.astype(np.float64))
+    pts = bvc.soa(sub)
+    st = bvc.EvalState(pts, grad=False)
+
+    def wos_rmse(k, seed):
+        bvc.eval_state_reset(st)
+        ws = bvc.workspace(bvc.wos_workspace_size(w.dim, st.m, k)[1])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bvc.wos_estimate(s.geom, w.g, w.f, st, k, w.eps, MAX_STEPS, seed, 0, ws)
+        u, _ = bvc.get_solution(st)
+        e1.record()
+        torch.cuda.synchronize()
+        return float(np.sqrt(np.mean((u.cpu().numpy() - ex_sub) ** 2))), e0.elapsed_time(e1) / 1e3
+
+    kmax = 1 << 16
+    r0, _ = wos_rmse(64, 11)
+    k = int(min(kmax, max(64, np.ceil(64 * (r0 / tau) ** 2))))
+    r, t = wos_rmse(k, 12)
+    while r > tau and k < kmax:
+        k = min(kmax, int(k * 1.25) + 1)
+        r, t = wos_rmse(k, 13)
+    wos_rate = st.m / t
+    return {"variant": w.name, "tau_rmse": tau, "bvc_pts_per_s": bvc_rate, "wos_walks_per_point": k,
+            "wos_rmse": r, "wos_pts_per_s": wos_rate, "bvc_over_wos": bvc_rate / wos_rate,
+            "wos_subset_points": int(st.m)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample_rates(w, budget_s: float = 20.0):
+    """Times the FP64 oracle on bounded samples of the workload and
+    extrapolates the time of one full step.  Returns (step seconds, info)."""
+    import oracle
+    from tests.oracle_pipeline import oracle_cache  # noqa: F401  (same composition as the tests)
+    bvh = oracle.BVH(w.V, w.F)
+    z, n, _ = oracle.sample_boundary(w.V, w.F, 4096, w.offset_l, 0)
+    # walks: grow the sample until ~budget/3
+    ns = 64
+    while True:
+        t0 = time.perf_counter()
+        oracle.walks(bvh, w.g, w.f, z[:ns].astype(np.float32), w.walks, w.eps, MAX_STEPS, 0, 0, 0)
+        tw = time.perf_counter() - t0
+        if tw > budget_s / 6 or ns >= 4096:
+            break
+        ns = min(4096, ns * 4)
+    walk_rate = ns * w.walks / tw
+    # gather: a few points against the full-size cache
+    N = w.n_samples
+    rng = np.random.default_rng(1)
+    zc = rng.standard_normal((N, w.dim)) * 0.5
+    nc = rng.standard_normal((N, w.dim))
+    nc /= np.linalg.norm(nc, axis=1, keepdims=True)
+    mp = 128
+    t0 = time.perf_counter()
+    oracle.gather(zc, nc, rng.standard_normal(N), rng.standard_normal(N), 1.0, w.eval_pts[:mp])
+    tg = time.perf_counter() - t0
+    pair_rate = mp * N / tg
+    # source candidates (2D): inside test on a sample of candidates
+    src_s = 0.0
+    n_src_cand = w.src_grid[0] * w.src_grid[1] if w.f else 0
+    if n_src_cand:
+        t0 = time.perf_counter()
+        oracle.sample_source2d(w.V, w.F, (64, 16), 0, w.f)
+        src_s = (time.perf_counter() - t0) * n_src_cand / (64 * 16)
+    M = w.eval_pts.shape[0]
+    kept_src = 0.45 * n_src_cand
+    t_step = (N * w.walks) / walk_rate + M * (N + kept_src) / pair_rate + src_s
+    info = {"walks_per_s": walk_rate, "pairs_per_s": pair_rate, "walk_sample": f"{ns} samples x {w.walks} walks",
+            "gather_sample": f"{mp} points x {N} samples", "source_s": src_s, "threads": oracle.num_threads()}
+    return t_step, info
+
+
+def reference_arm(args, w):
+    """The oracle as the reference arm: each step times a bounded sample."""
+    import oracle
+    steps = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        t, info = oracle_sample_rates(w, budget_s=6.0)
+        if k >= args.warmup:
+            steps.append(t)
+    t = statistics.mean(steps)
+    M = w.eval_pts.shape[0]
+    val = M / t
+    return {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "eval_points": int(M)},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{info['walk_sample']}; {info['gather_sample']}; extrapolated to the "
+                                       f"full step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="star", choices=["star", "circle", "sphere"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fixed-rmse", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, local, ws = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w = make_workload(args.workload)
+        print(json.dumps(reference_arm(args, w)))
+        return 0
+
+    import torch
+    from paper_2302_11825_gb300 import bvc
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    rank, ws = init_dist("nccl")
+    w = make_workload(args.workload)
+    s = Solver(w, device)
+    M = s.m_far + s.m_near
+    dim = w.dim
+
+    cache_stats, near_stats = s.counting_pass(1)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    for k in range(args.warmup):
+        s.step(10_000 * rank + k)
+    torch.cuda.synchronize()
+    s.geom.stats(reset=True)
+
+    # ---- timed region (device-resident inputs)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        bvc.profile_begin()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record()
+            s.step(1_000_000 + 10_000 * rank + k)
+            evs[k][1].record()
+        prof = bvc.profile_end()
+        torch.cuda.synchronize()
+    barrier()
+    t_local = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    t_max = max_over_ranks(t_local, device)
+    clocks = clk.summary()
+    run_stats = s.geom.stats(reset=True)
+
+    # ---- end to end through the C ABI with host buffers
+    far_h = s.far_pts.cpu().pin_memory()
+    near_h = s.near_pts.cpu().pin_memory()
+    u_far_h = torch.empty(s.m_far, dtype=torch.float64).pin_memory()
+    g_far_h = torch.empty((dim, s.m_far), dtype=torch.float64).pin_memory()
+    u_near_h = torch.empty(s.m_near, dtype=torch.float64).pin_memory()
+    g_near_h = torch.empty((dim, s.m_near), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        s.far_pts.copy_(far_h, non_blocking=True)
+        s.near_pts.copy_(near_h, non_blocking=True)
+        s.step(2_000_000 + 10_000 * rank + k)
+        u_far_h.copy_(s.u_far, non_blocking=True)
+        g_far_h.copy_(s.g_far, non_blocking=True)
+        u_near_h.copy_(s.u_near, non_blocking=True)
+        g_near_h.copy_(s.g_near, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, device)
+    h2d = (s.m_far + s.m_near) * dim * 4
+    d2h = (s.m_far + s.m_near) * (1 + dim) * 8
+    assert np.all(np.isfinite(u_far_h.numpy())) and np.all(np.isfinite(u_near_h.numpy()))
+
+    # ---- per-kernel breakdown and the roofline of the dominant kernel
+    K = args.steps
+    total_ms = sum(v[1] for v in prof.values())
+    kernels = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1), "share": v[1] / total_ms}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    launches = sum(v[0] for v in prof.values())
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    n_walks_cache = w.n_samples * w.walks
+    walk_cache_bytes = walk_bytes(cache_stats, dim, n_walks_cache)
+    n_src_kept = int(s.cache.n_src_dev.item()) if s.cache.n_src_cand else 0
+    pairs_bnd = s.m_far * w.n_samples
+    pairs_src = s.m_far * n_src_kept
+    dominant = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    gb_ms = prof.get("gather_boundary", (1, float("nan")))[1] / max(prof.get("gather_boundary", (1, 1))[0], 1)
+    gs_ms = prof.get("gather_source", (1, 0.0))[1] / max(prof.get("gather_source", (1, 1))[0], 1)
+    walk_ms_total = prof.get("walk", (0, 0.0))[1] / K
+    steps_cache = cache_stats["steps"]
+    steps_near = near_stats["steps"]
+    if dominant == "walk":
+        # average over the step's walk launches: algorithmic bytes of both / their time
+        bytes_step = walk_cache_bytes + walk_bytes(near_stats, dim, s.m_near * w.walks)
+        launches_per_step = prof["walk"][0] / K
+        achieved = bytes_step / launches_per_step / (kernels["walk"]["avg_ms"] / 1e3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": profile_traffic("walk", w.name), "kernel": "walk",
+                    "peak_source": f"{peak_src} (hbm_gbs)",
+                    "note": "BVH and mesh are L2-resident; bytes are algorithmic (node fetches x bytes/node + "
+                            "primitive tests x bytes/primitive + per-walk I/O)"}
+    else:
+        kname = dominant
+        if kname == "gather_boundary":
+            flops = pairs_bnd * FLOPS_PAIR_BND[dim]
+        else:
+            flops = pairs_src * FLOPS_PAIR_SRC[dim]
+        achieved = flops / (kernels[kname]["avg_ms"] / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak_tflops, "traffic": profile_traffic(kname, w.name),
+                    "kernel": kname,
+                    "peak_source": f"FP32 FMA peak = {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max} MHz"}
+    # secondary rooflines, reported beside the main one
+    extra = {}
+    if "gather_boundary" in prof:
+        a = pairs_bnd * FLOPS_PAIR_BND[dim] / (gb_ms / 1e3) / 1e12
+        extra["gather_boundary"] = {"bound": "alu", "achieved_tflops": a, "frac_fp32_peak": a / fp32_peak_tflops,
+                                    "pairs_per_launch": pairs_bnd, "avg_ms": gb_ms}
+    if "gather_source" in prof and pairs_src:
+        a = pairs_src * FLOPS_PAIR_SRC[dim] / (gs_ms / 1e3) / 1e12
+        extra["gather_source"] = {"bound": "alu", "achieved_tflops": a, "frac_fp32_peak": a / fp32_peak_tflops,
+                                  "pairs_per_launch": pairs_src, "avg_ms": gs_ms}
+    if "walk" in prof:
+        bytes_step = walk_cache_bytes + walk_bytes(near_stats, dim, s.m_near * w.walks)
+        a = bytes_step / (walk_ms_total / 1e3) / 1e9
+        extra["walk"] = {"bound": "hbm", "achieved_gbs": a, "frac_hbm_peak": a / float(peaks["hbm_gbs"]),
+                         "steps_per_launch_cache": steps_cache, "steps_per_launch_near": steps_near,
+                         "nodes_per_step": (cache_stats["nodes"] + near_stats["nodes"]) / max(steps_cache + steps_near, 1),
+                         "prims_per_step": (cache_stats["prims"] + near_stats["prims"]) / max(steps_cache + steps_near, 1),
+                         "ms_per_step_total": walk_ms_total}
+
+    value = M * K * ws / t_max
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "dim": dim, "n_prims": int(w.F.shape[0]), "n_samples": w.n_samples,
+                   "walks_per_sample": w.walks, "src_candidates": int(s.cache.n_src_cand), "src_kept": n_src_kept,
+                   "eval_points": int(M), "eval_far": int(s.m_far), "eval_near_pointwise": int(s.m_near),
+                   "near_walks": w.walks, "eps": w.eps, "offset_l": w.offset_l,
+                   "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}",
+                   "sums": "fp64"},
+        "roofline": roofline,
+        "kernels": kernels, "rooflines_all": extra,
+        "wos_steps_per_s": (run_stats["steps"]) / max(walk_ms_total * K / 1e3, 1e-12),
+        "pairs_per_s": (pairs_bnd + pairs_src) / ((gb_ms + gs_ms) / 1e3) if "gather_boundary" in prof else None,
+        "e2e": {"value": M * e2e_steps * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "geometry_build_s": s.geometry_build_s,
+        "walk_caps": run_stats["capped"],
+    }
+    if rank == 0 and ws == 1 and not args.no_fixed_rmse:
+        out["fixed_rmse"] = fixed_rmse_comparison(device, w)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_cpu, info = oracle_sample_rates(w)
+        out["cpu_baseline"] = {"value": M / t_cpu, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
+                               "sample": f"{info['walk_sample']}; {info['gather_sample']}; source test on 1024 "
+                                         f"candidates; extrapolated to one full step",
+                               "walks_per_s": info["walks_per_s"], "pairs_per_s": info["pairs_per_s"]}
+    if rank == 0:
+        print(json.dumps(out))
+    import torch.distributed as td
+    if td.is_initialized():
+        td.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

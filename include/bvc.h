@@ -110,10 +110,18 @@ bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* info);
 
 /* Device status/statistics block: out[0] total walk steps (closest-point
  * queries made by walks), out[1] walks stopped at max_steps, out[2] error
- * flags (bit 0: timeout), out[3] reserved.  Synchronises `stream`.  With
- * reset != 0 the block is cleared after reading.  Returns BVC_ERR_TIMEOUT if
- * the error bit is set, BVC_WARN_WALK_CAP if capped walks were seen. */
-bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[4], int32_t reset, bvc_stream stream);
+ * flags (bit 0: timeout), out[3] internal, out[4] BVH nodes fetched and
+ * out[5] primitives tested by walks while counting is on, out[6..7]
+ * reserved.  Synchronises `stream`.  With reset != 0 the block is cleared
+ * after reading.  Returns BVC_ERR_TIMEOUT if the error bit is set,
+ * BVC_WARN_WALK_CAP if capped walks were seen. */
+bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[8], int32_t reset, bvc_stream stream);
+
+/* Counting mode (on != 0): later walks on this geometry run a variant that
+ * also counts BVH node fetches and primitive tests into the status block,
+ * from which the algorithmic bytes of a walk step are derived.  The walks'
+ * results are identical in both modes; counting costs a little speed. */
+bvc_status bvc_geometry_set_counting(bvc_geometry g, int32_t on);
 
 /* Closest boundary point of m query points (the query WoS makes each step,
  * Sec. 3.1).  pts: device [dim][m].  d2: device float[m], squared distance;
@@ -255,26 +263,45 @@ bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const bvc_eval_st
 bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state, void* workspace, size_t workspace_bytes,
                         bvc_stream stream);
 
+/* Zero the running sums and counts of a state (cudaMemsetAsync, no kernel). */
+bvc_status bvc_eval_state_reset(const bvc_eval_state* state, bvc_stream stream);
+
 /* a6 -- Alg. 1 GetSolution: u = u_bnd/N + u_src/M (a term is dropped when
  * its count is 0); grad likewise.  u: device double[m]; grad: device
  * double[dim][m] or NULL. */
 bvc_status bvc_get_solution(const bvc_eval_state* state, double* u, double* grad, bvc_stream stream);
 
-/* K6 -- pointwise walk on spheres at m points (the comparison estimator,
- * and the estimate used within l of the boundary, Sec. 3.2): `walks` walks
- * per point with tag 3, ids id_base + k*walks + j.  Adds the FP64 sums of
- * the walks' U and gradient estimates: u_sum[k] += sum_j U, grad_sum[a][k]
- * += sum_j grad_a (grad_sum may be NULL).  Workspace chunks the walks. */
+/* K6 -- pointwise walk on spheres at the m points of `state` (the
+ * comparison estimator, and the estimate used within l of the boundary,
+ * Sec. 3.2): `walks` walks per point with tag 3, ids id_base + k*walks + j.
+ * The walks' sums go into the state's running sums like a cache's would:
+ * u_bnd[k] += sum_j U, grad_bnd[a][k] += sum_j grad_a (if grad_bnd is set),
+ * counts[0] += walks -- so bvc_get_solution returns the pointwise means and
+ * successive calls with disjoint id ranges refine them progressively.
+ * Workspace chunks the walks by points. */
 bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
                                        size_t* full_bytes);
-bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* pts,
-                        int64_t m, int32_t walks, float eps, int32_t max_steps, uint64_t seed, uint64_t id_base,
-                        double* u_sum, double* grad_sum, void* workspace, size_t workspace_bytes,
-                        bvc_stream stream);
+bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, bvc_eval_state* state,
+                        int32_t walks, float eps, int32_t max_steps, uint64_t seed, uint64_t id_base,
+                        void* workspace, size_t workspace_bytes, bvc_stream stream);
 
 /* Gather device status word (bit 0: a bounded wait for a tile copy ran
  * out).  Synchronises the device; reset != 0 clears it. */
 bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
+
+/* ------------------------------------------------------------- profiling */
+/* Between bvc_profile_begin and bvc_profile_end every kernel the library
+ * launches is bracketed by CUDA events on its own stream.  bvc_profile_end
+ * waits for them and returns per-kernel totals (launch count, summed
+ * duration), at most max_out entries.  Not thread-safe: profile one host
+ * thread's calls at a time. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} bvc_kernel_time;
+bvc_status bvc_profile_begin(void);
+bvc_status bvc_profile_end(bvc_kernel_time* out, int32_t max_out, int32_t* n_out);
 
 /* ------------------------------------------------------------------ misc */
 const char* bvc_status_string(bvc_status s);

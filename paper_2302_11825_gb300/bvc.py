@@ -62,6 +62,10 @@ class CacheOpts(C.Structure):
                 ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 2)]
 
 
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
 class EvalStateStruct(C.Structure):
     _fields_ = [("dim", C.c_int32), ("m", C.c_int64), ("x", C.c_void_p), ("u_bnd", C.c_void_p),
                 ("u_src", C.c_void_p), ("grad_bnd", C.c_void_p), ("grad_src", C.c_void_p),
@@ -94,8 +98,12 @@ def _declare(lib):
         "bvc_evaluate": (S, [C.POINTER(CacheStruct), C.POINTER(EvalStateStruct), P, sz, P]),
         "bvc_get_solution": (S, [C.POINTER(EvalStateStruct), P, P, P]),
         "wos_estimate_workspace_size": (S, [i32, i64, i32, C.POINTER(sz), C.POINTER(sz)]),
-        "wos_estimate": (S, [P, C.POINTER(Function), C.POINTER(Function), P, i64, i32, f32, i32, u64, u64, P, P, P,
-                             sz, P]),
+        "wos_estimate": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct), i32, f32, i32,
+                             u64, u64, P, sz, P]),
+        "bvc_eval_state_reset": (S, [C.POINTER(EvalStateStruct), P]),
+        "bvc_geometry_set_counting": (S, [P, i32]),
+        "bvc_profile_begin": (S, []),
+        "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
         "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
         "bvc_status_string": (C.c_char_p, [S]),
         "bvc_version": (i32, []),
@@ -199,10 +207,14 @@ class Geometry:
         return float(self.info().boundary_measure)
 
     def stats(self, reset=False, stream=None):
-        out = (C.c_uint64 * 4)()
+        out = (C.c_uint64 * 8)()
         st = lib().bvc_geometry_stats(self.h, out, int(bool(reset)), _stream(stream))
         _check(st, "bvc_geometry_stats", allow=(OK, WARN_WALK_CAP))
-        return {"steps": int(out[0]), "capped": int(out[1]), "flags": int(out[2]), "status": st}
+        return {"steps": int(out[0]), "capped": int(out[1]), "flags": int(out[2]), "nodes": int(out[4]),
+                "prims": int(out[5]), "status": st}
+
+    def set_counting(self, on: bool):
+        _check(lib().bvc_geometry_set_counting(self.h, int(bool(on))), "bvc_geometry_set_counting")
 
     def close(self):
         if getattr(self, "h", None):
@@ -409,23 +421,33 @@ def wos_workspace_size(dim: int, m: int, walks: int):
     return int(mn.value), int(full.value)
 
 
-def wos_estimate(geom: Geometry, g_terms, f_terms, pts: torch.Tensor, walks: int, eps: float, max_steps: int,
-                 seed: int, id_base: int = 0, u_sum=None, grad_sum=None, want_grad=True, ws: torch.Tensor = None,
-                 stream=None):
-    """Pointwise walk on spheres: adds FP64 sums of `walks` walks per point."""
-    _dev(pts, torch.float32)
-    dim, m = pts.shape
-    if u_sum is None:
-        u_sum = torch.zeros(m, dtype=torch.float64, device=pts.device)
-    if grad_sum is None and want_grad:
-        grad_sum = torch.zeros((dim, m), dtype=torch.float64, device=pts.device)
+def eval_state_reset(state: EvalState, stream=None):
+    _check(lib().bvc_eval_state_reset(C.byref(state.struct), _stream(stream)), "bvc_eval_state_reset")
+
+
+def wos_estimate(geom: Geometry, g_terms, f_terms, state: EvalState, walks: int, eps: float, max_steps: int,
+                 seed: int, id_base: int = 0, ws: torch.Tensor = None, stream=None):
+    """Pointwise walk on spheres: adds `walks` walks per point of `state` to
+    its running sums (finalise with get_solution)."""
     if ws is None:
-        ws = workspace(wos_workspace_size(dim, m, walks)[1])
+        ws = workspace(wos_workspace_size(state.dim, state.m, walks)[1])
     g, f = make_function(g_terms), make_function(f_terms)
-    _check(lib().wos_estimate(geom.h, C.byref(g), C.byref(f), _ptr(pts), m, int(walks), float(eps), int(max_steps),
-                              int(seed), int(id_base), _ptr(u_sum), _ptr(grad_sum), _ptr(ws), ws.numel(),
-                              _stream(stream)), "wos_estimate")
-    return u_sum, grad_sum
+    _check(lib().wos_estimate(geom.h, C.byref(g), C.byref(f), C.byref(state.struct), int(walks), float(eps),
+                              int(max_steps), int(seed), int(id_base), _ptr(ws), ws.numel(), _stream(stream)),
+           "wos_estimate")
+    return state
+
+
+def profile_begin():
+    _check(lib().bvc_profile_begin(), "bvc_profile_begin")
+
+
+def profile_end():
+    """Per-kernel {name: (launches, total_ms)} since profile_begin (synchronises)."""
+    out = (KernelTime * 64)()
+    n = C.c_int32()
+    _check(lib().bvc_profile_end(out, 64, C.byref(n)), "bvc_profile_end")
+    return {out[i].name.decode(): (int(out[i].launches), float(out[i].total_ms)) for i in range(n.value)}
 
 
 def gather_status(reset=False):

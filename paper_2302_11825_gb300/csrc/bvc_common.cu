@@ -1,7 +1,9 @@
 // bvc_common.cu -- host helpers: problem-function conversion, device
 // properties, status strings.
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "bvc_internal.h"
 
@@ -78,7 +80,101 @@ int max_blocks_per_sm(const void* kernel, int block, size_t smem) {
   return n;
 }
 
+namespace {
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+};
+Profiler& prof() {
+  static Profiler p;
+  return p;
+}
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : slot_(-1), s_(s) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  if (!P.on) return;
+  ProfRec r{name, P.get(), P.get()};
+  if (r.a == nullptr || r.b == nullptr) return;
+  if (cudaEventRecord(r.a, s) != cudaSuccess) return;
+  slot_ = (int)P.recs.size();
+  P.recs.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (slot_ < 0) return;
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  if (slot_ < (int)P.recs.size()) cudaEventRecord(P.recs[slot_].b, s_);
+}
+
 }  // namespace bvc
+
+extern "C" bvc_status bvc_profile_begin(void) {
+  bvc::Profiler& P = bvc::prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  for (auto& r : P.recs) {
+    P.pool.push_back(r.a);
+    P.pool.push_back(r.b);
+  }
+  P.recs.clear();
+  P.on = true;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_profile_end(bvc_kernel_time* out, int32_t max_out, int32_t* n_out) {
+  bvc::Profiler& P = bvc::prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  P.on = false;
+  int32_t n = 0;
+  bvc_status st = BVC_OK;
+  for (auto& r : P.recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) {
+      st = BVC_ERR_CUDA;
+      continue;
+    }
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      st = BVC_ERR_CUDA;
+      continue;
+    }
+    int32_t k = 0;
+    while (k < n && std::strncmp(out[k].name, r.name, sizeof(out[k].name)) != 0) ++k;
+    if (k == n) {
+      if (out == nullptr || n >= max_out) continue;
+      std::memset(&out[k], 0, sizeof(out[k]));
+      std::strncpy(out[k].name, r.name, sizeof(out[k].name) - 1);
+      ++n;
+    }
+    out[k].launches += 1;
+    out[k].total_ms += ms;
+  }
+  for (auto& r : P.recs) {
+    P.pool.push_back(r.a);
+    P.pool.push_back(r.b);
+  }
+  P.recs.clear();
+  if (n_out) *n_out = n;
+  (void)cudaGetLastError();
+  return st;
+}
 
 extern "C" const char* bvc_status_string(bvc_status s) {
   switch (s) {

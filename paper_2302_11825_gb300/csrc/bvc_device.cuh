@@ -234,10 +234,17 @@ __device__ __forceinline__ float box_d2_3(float lox, float loy, float loz, float
   return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 
-template <int D>
-__device__ __forceinline__ void test_leaf(const DevGeometry& G, int32_t enc, const float* p, Hit<D>& h, float& thr) {
+// Work counters of the counting variant (node fetches, primitive tests).
+struct TravCount {
+  uint32_t nodes, prims;
+};
+
+template <int D, bool CNT>
+__device__ __forceinline__ void test_leaf(const DevGeometry& G, int32_t enc, const float* p, Hit<D>& h, float& thr,
+                                          TravCount& tc) {
   const int32_t e = ~enc;
   const int32_t first = e >> 3, count = e & 7;
+  if (CNT) tc.prims += (uint32_t)count;
   for (int32_t q = first; q < first + count; ++q) {
     float df[D];
     float d2;
@@ -263,9 +270,9 @@ __device__ __forceinline__ void test_leaf(const DevGeometry& G, int32_t enc, con
 }
 
 // Closest primitive to p.  Stack in shared memory: stack[k * stride + lane_slot].
-template <int D>
+template <int D, bool CNT = false>
 __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p, Hit<D>& h, int* snode,
-                                            float* sdist, int stride) {
+                                            float* sdist, int stride, TravCount& tc) {
   h.d2 = __int_as_float(0x7f800000);
   h.id = 0x7fffffff;
 #pragma unroll
@@ -276,6 +283,7 @@ __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p
   for (;;) {
     int32_t cl, cr;
     float dl, dr;
+    if (CNT) ++tc.nodes;
     if (D == 2) {
       const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
       const float4 C = __ldg(&G.nodes[3 * node + 2]);
@@ -301,12 +309,12 @@ __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p
     }
     bool tl = dl <= thr, tr = dr <= thr;
     if (tl && cl < 0) {
-      test_leaf<D>(G, cl, p, h, thr);
+      test_leaf<D, CNT>(G, cl, p, h, thr, tc);
       tl = false;
       tr = dr <= thr;
     }
     if (tr && cr < 0) {
-      test_leaf<D>(G, cr, p, h, thr);
+      test_leaf<D, CNT>(G, cr, p, h, thr, tc);
       tr = false;
     }
     if (tl && tr) {

@@ -408,6 +408,7 @@ extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) 
   if (cache->n > 0) {
     if (!cache->z || !cache->nrm || !cache->u_hat || !cache->dudn_hat || !cache->packed) return BVC_ERR_INVALID_ARG;
     const unsigned grid = (unsigned)((cache->n + 255) / 256);
+    ProfScope ps("pack_boundary", s);
     if (cache->dim == 2)
       k_pack_bnd<2><<<grid, 256, 0, s>>>(*cache);
     else
@@ -416,6 +417,7 @@ extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) 
   if (cache->n_src_cand > 0) {
     if (!cache->src_y || !cache->src_c || !cache->src_packed || !cache->n_src_dev) return BVC_ERR_INVALID_ARG;
     const unsigned grid = (unsigned)((cache->n_src_cand + 255) / 256);
+    ProfScope ps("pack_source", s);
     if (cache->dim == 2)
       k_pack_src<2><<<grid, 256, 0, s>>>(*cache);
     else
@@ -466,11 +468,15 @@ static bvc_status run_part(int D, int kind, bool grad, const float* x, int64_t m
     A.part = (double*)ws;
   }
   void* args[] = {(void*)&A};
-  BVC_CUDA_TRY(cudaLaunchKernel(kern, dim3((unsigned)(P.pblocks * P.n_splits)), dim3(kGBlock), args, 0, s));
+  {
+    ProfScope ps(kind == 0 ? "gather_boundary" : "gather_source", s);
+    BVC_CUDA_TRY(cudaLaunchKernel(kern, dim3((unsigned)(P.pblocks * P.n_splits)), dim3(kGBlock), args, 0, s));
+  }
   if (P.n_splits > 1) {
     int64_t blocks = (m + 255) / 256;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
+    ProfScope ps("gather_reduce", s);
     k_gather_reduce<<<(unsigned)blocks, 256, 0, s>>>(A, planes);
     BVC_LAUNCH_CHECK();
   }
@@ -503,8 +509,27 @@ extern "C" bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state
       if (st != BVC_OK) return st;
     }
   }
-  k_add_counts<<<1, 32, 0, s>>>(state->counts, cache->n, cache->n_src_cand);
+  {
+    ProfScope ps("add_counts", s);
+    k_add_counts<<<1, 32, 0, s>>>(state->counts, cache->n, cache->n_src_cand);
+  }
   BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_eval_state_reset(const bvc_eval_state* state, bvc_stream stream) {
+  if (state == nullptr || state->m < 0 || state->counts == nullptr || (state->dim != 2 && state->dim != 3))
+    return BVC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t mb = (size_t)state->m * sizeof(double);
+  if (state->m > 0) {
+    if (state->u_bnd == nullptr || state->u_src == nullptr) return BVC_ERR_INVALID_ARG;
+    BVC_CUDA_TRY(cudaMemsetAsync(state->u_bnd, 0, mb, s));
+    BVC_CUDA_TRY(cudaMemsetAsync(state->u_src, 0, mb, s));
+    if (state->grad_bnd) BVC_CUDA_TRY(cudaMemsetAsync(state->grad_bnd, 0, mb * state->dim, s));
+    if (state->grad_src) BVC_CUDA_TRY(cudaMemsetAsync(state->grad_src, 0, mb * state->dim, s));
+  }
+  BVC_CUDA_TRY(cudaMemsetAsync(state->counts, 0, 2 * sizeof(int64_t), s));
   return BVC_OK;
 }
 
@@ -516,6 +541,7 @@ extern "C" bvc_status bvc_get_solution(const bvc_eval_state* state, double* u, d
   int64_t blocks = (state->m + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
+  ProfScope ps("get_solution", (cudaStream_t)stream);
   if (state->dim == 2)
     k_get_solution<2><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(*state, u, grad);
   else

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(128) k_query_closest(DevGeometry G, const floa
 #pragma unroll
     for (int a = 0; a < D; ++a) p[a] = pts[a * m + i];
     Hit<D> h;
-    bvh_closest<D>(G, p, h, snode + threadIdx.x, sdist + threadIdx.x, 128);
+    TravCount tc{0, 0};
+    bvh_closest<D>(G, p, h, snode + threadIdx.x, sdist + threadIdx.x, 128, tc);
     if (d2) d2[i] = h.d2;
     if (prim) prim[i] = h.id;
     if (cp)
@@ -245,14 +246,20 @@ extern "C" bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* i
   return BVC_OK;
 }
 
-extern "C" bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[4], int32_t reset, bvc_stream stream) {
+extern "C" bvc_status bvc_geometry_set_counting(bvc_geometry g, int32_t on) {
+  if (g == nullptr) return BVC_ERR_INVALID_ARG;
+  g->counting = on ? 1 : 0;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[8], int32_t reset, bvc_stream stream) {
   if (g == nullptr || out == nullptr) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned long long h[4];
+  unsigned long long h[8];
   BVC_CUDA_TRY(cudaMemcpyAsync(h, g->dev.stats, sizeof(h), cudaMemcpyDeviceToHost, s));
   if (reset) BVC_CUDA_TRY(cudaMemsetAsync(g->dev.stats, 0, sizeof(h), s));
   BVC_CUDA_TRY(cudaStreamSynchronize(s));
-  for (int i = 0; i < 4; ++i) out[i] = h[i];
+  for (int i = 0; i < 8; ++i) out[i] = h[i];
   if (h[kStatFlags] & kFlagTimeout) return BVC_ERR_TIMEOUT;
   if (h[kStatCapped]) return BVC_WARN_WALK_CAP;
   return BVC_OK;
@@ -263,6 +270,7 @@ extern "C" bvc_status bvc_query_closest(bvc_geometry g, const float* pts, int64_
   if (g == nullptr || m < 0 || (m > 0 && pts == nullptr)) return BVC_ERR_INVALID_ARG;
   if (m == 0) return BVC_OK;
   const int grid = grid_for(m, 128);
+  ProfScope ps("query_closest", (cudaStream_t)stream);
   if (g->dim == 2)
     k_query_closest<2><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, d2, prim, cp, 0.0f, nullptr);
   else
@@ -277,6 +285,7 @@ extern "C" bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_
     return BVC_ERR_INVALID_ARG;
   if (m == 0) return BVC_OK;
   const int grid = grid_for(m, 128);
+  ProfScope ps("classify_near", (cudaStream_t)stream);
   if (g->dim == 2)
     k_query_closest<2><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, nullptr, nullptr, nullptr, l * l,
                                                               near);
@@ -293,6 +302,7 @@ extern "C" bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, u
     return BVC_ERR_INVALID_ARG;
   if (n == 0) return BVC_OK;
   const int grid = (int)((n + 255) / 256);
+  ProfScope ps("sample_boundary", (cudaStream_t)stream);
   if (g->dim == 2)
     k_sample_boundary<2><<<grid, 256, 0, (cudaStream_t)stream>>>(g->dev, n, l, seed, z, nrm, elem);
   else

@@ -43,7 +43,7 @@ struct DevGeometry {
   float lo[3], hi[3];     // bbox
 };
 
-constexpr int kStatSteps = 0, kStatCapped = 1, kStatFlags = 2;
+constexpr int kStatSteps = 0, kStatCapped = 1, kStatFlags = 2, kStatCounter = 3, kStatNodes = 4, kStatPrims = 5;
 constexpr unsigned long long kFlagTimeout = 1ull;
 
 }  // namespace bvc
@@ -55,6 +55,7 @@ struct bvc_geometry_s {
   float lo[3], hi[3];
   void* arena;            // one device allocation holding everything below
   size_t arena_bytes;
+  int32_t counting;       // walks count node fetches and primitive tests
   bvc::DevGeometry dev;
 };
 
@@ -64,6 +65,21 @@ namespace bvc {
 bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);
 int num_sms();
 int max_blocks_per_sm(const void* kernel, int block, size_t smem);
+
+// Kernel timing: while bvc_profile_begin .. bvc_profile_end is active, every
+// kernel launch of the library is bracketed by CUDA events recorded on the
+// stream it is launched on.  ProfScope is placed around exactly one launch.
+class ProfScope {
+ public:
+  ProfScope(const char* name, cudaStream_t s);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  int slot_;
+  cudaStream_t s_;
+};
 
 }  // namespace bvc
 

@@ -168,9 +168,18 @@ extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn,
   S.src_c = cache->src_c;
   S.n_src = cache->n_src_dev;
   cudaStream_t s = (cudaStream_t)stream;
-  k_src_classify<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
-  k_src_scan<<<1, 1024, 0, s>>>(S);
-  k_src_scatter<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+  {
+    ProfScope ps("source_classify", s);
+    k_src_classify<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+  }
+  {
+    ProfScope ps("source_scan", s);
+    k_src_scan<<<1, 1024, 0, s>>>(S);
+  }
+  {
+    ProfScope ps("source_scatter", s);
+    k_src_scatter<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+  }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }

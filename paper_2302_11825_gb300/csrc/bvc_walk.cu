@@ -43,7 +43,7 @@ struct WalkParams {
   unsigned long long* counter;
 };
 
-template <int D, bool HAS_F, bool GN>
+template <int D, bool HAS_F, bool GN, bool CNT>
 __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
   __shared__ int snode[kStack * kWalkBlock];
   __shared__ float sdist[kStack * kWalkBlock];
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
   for (int a = 0; a < D; ++a) x[a] = nu[a] = 0.0f;
   float R0 = 0.0f, usrc = 0.0f, wf0 = 0.0f, wg0 = 0.0f, cv = 0.0f;
   int k = 0;
-  unsigned long long my_steps = 0, my_capped = 0;
+  unsigned long long my_steps = 0, my_capped = 0, my_nodes = 0, my_prims = 0;
   for (;;) {
     unsigned need = __ballot_sync(FULL, !active);
     while (need != 0u && more) {
@@ -89,7 +89,12 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
     if (!__any_sync(FULL, active)) break;
     if (active) {
       Hit<D> h;
-      bvh_closest<D>(P.G, x, h, snode + threadIdx.x, sdist + threadIdx.x, kWalkBlock);
+      TravCount tc{0, 0};
+      bvh_closest<D, CNT>(P.G, x, h, snode + threadIdx.x, sdist + threadIdx.x, kWalkBlock, tc);
+      if (CNT) {
+        my_nodes += tc.nodes;
+        my_prims += tc.prims;
+      }
       ++k;
       float pbar[D];
 #pragma unroll
@@ -165,10 +170,18 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
   for (int o = 16; o > 0; o >>= 1) {
     my_steps += __shfl_xor_sync(FULL, my_steps, o);
     my_capped += __shfl_xor_sync(FULL, my_capped, o);
+    if (CNT) {
+      my_nodes += __shfl_xor_sync(FULL, my_nodes, o);
+      my_prims += __shfl_xor_sync(FULL, my_prims, o);
+    }
   }
   if (lane == 0) {
     if (my_steps) atomicAdd(&P.G.stats[kStatSteps], my_steps);
     if (my_capped) atomicAdd(&P.G.stats[kStatCapped], my_capped);
+    if (CNT) {
+      atomicAdd(&P.G.stats[kStatNodes], my_nodes);
+      atomicAdd(&P.G.stats[kStatPrims], my_prims);
+    }
   }
 }
 
@@ -205,31 +218,29 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceParams R) {
   }
 }
 
-static int walk_grid(const void* kern) {
-  static int cached[2][2][2] = {};
-  (void)cached;
-  return num_sms() * max_blocks_per_sm(kern, kWalkBlock, 0);
+template <int D, bool HAS_F, bool GN>
+static const void* walk_kernel(bool cnt) {
+  return cnt ? (const void*)k_walk<D, HAS_F, GN, true> : (const void*)k_walk<D, HAS_F, GN, false>;
 }
 
-static bvc_status launch_walk(int dim, bool has_f, bool gn, const WalkParams& P, cudaStream_t s) {
-  const void* kern = nullptr;
+static const void* pick_walk(int dim, bool has_f, bool gn, bool cnt) {
   if (dim == 2) {
-    if (has_f)
-      kern = gn ? (const void*)k_walk<2, true, true> : (const void*)k_walk<2, true, false>;
-    else
-      kern = gn ? (const void*)k_walk<2, false, true> : (const void*)k_walk<2, false, false>;
-  } else {
-    if (has_f)
-      kern = gn ? (const void*)k_walk<3, true, true> : (const void*)k_walk<3, true, false>;
-    else
-      kern = gn ? (const void*)k_walk<3, false, true> : (const void*)k_walk<3, false, false>;
+    if (has_f) return gn ? walk_kernel<2, true, true>(cnt) : walk_kernel<2, true, false>(cnt);
+    return gn ? walk_kernel<2, false, true>(cnt) : walk_kernel<2, false, false>(cnt);
   }
+  if (has_f) return gn ? walk_kernel<3, true, true>(cnt) : walk_kernel<3, true, false>(cnt);
+  return gn ? walk_kernel<3, false, true>(cnt) : walk_kernel<3, false, false>(cnt);
+}
+
+static bvc_status launch_walk(int dim, bool has_f, bool gn, bool cnt, const WalkParams& P, cudaStream_t s) {
+  const void* kern = pick_walk(dim, has_f, gn, cnt);
   const int64_t want = (P.total + 31) / 32;
-  int grid = walk_grid(kern);
+  int grid = num_sms() * max_blocks_per_sm(kern, kWalkBlock, 0);
   const int64_t need_blocks = (want + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
   if (need_blocks < grid) grid = (int)(need_blocks > 0 ? need_blocks : 1);
   BVC_CUDA_TRY(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
   void* args[] = {(void*)&P};
+  ProfScope ps("walk", s);
   BVC_CUDA_TRY(cudaLaunchKernel(kern, dim3(grid), dim3(kWalkBlock), args, 0, s));
   return BVC_OK;
 }
@@ -240,6 +251,7 @@ static bvc_status launch_reduce(const ReduceParams& R, cudaStream_t s) {
   const int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
+  ProfScope ps("reduce_walks", s);
   k_reduce<<<(int)blocks, 256, 0, s>>>(R);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
@@ -279,7 +291,7 @@ extern "C" bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bv
   P.prim = prim;
   // the work counter lives in the status block's spare word
   P.counter = g->dev.stats + 3;
-  return launch_walk(g->dim, P.f.n_terms > 0, nrm != nullptr, P, (cudaStream_t)stream);
+  return launch_walk(g->dim, P.f.n_terms > 0, nrm != nullptr, g->counting != 0, P, (cudaStream_t)stream);
 }
 
 extern "C" bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walks, int32_t planes, int32_t mode,
@@ -354,7 +366,7 @@ extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, c
     P.i0 = i0;
     P.total = c * (int64_t)W;
     P.wid0 = opts->walk_id_base + (uint64_t)i0 * (uint64_t)W;
-    st = launch_walk(D, P.f.n_terms > 0, true, P, s);
+    st = launch_walk(D, P.f.n_terms > 0, true, g->counting != 0, P, s);
     if (st != BVC_OK) return st;
     ReduceParams R{};
     R.rec = P.rec;
@@ -384,51 +396,64 @@ extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_
   return BVC_OK;
 }
 
-extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* pts,
-                                   int64_t m, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
-                                   uint64_t id_base, double* u_sum, double* grad_sum, void* workspace,
-                                   size_t workspace_bytes, bvc_stream stream) {
-  if (g == nullptr || m < 0 || !valid_walk_args(eps, max_steps, walks)) return BVC_ERR_INVALID_ARG;
-  if (m == 0) return BVC_OK;
-  if (pts == nullptr || u_sum == nullptr || workspace == nullptr) return BVC_ERR_INVALID_ARG;
+__global__ void k_add_walk_count(int64_t* counts, int64_t w) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) counts[0] += w;
+}
+
+extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                   bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                                   uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  if (g == nullptr || state == nullptr || state->dim != g->dim || state->m < 0 || state->counts == nullptr ||
+      !valid_walk_args(eps, max_steps, walks))
+    return BVC_ERR_INVALID_ARG;
+  const int64_t m = state->m;
+  if (m > 0 && (state->x == nullptr || state->u_bnd == nullptr || workspace == nullptr)) return BVC_ERR_INVALID_ARG;
   const int D = g->dim;
   WalkParams P{};
   P.G = g->dev;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
-  const size_t per_pt = (size_t)walks * (1 + D) * sizeof(float);
-  if (workspace_bytes < kWsHead + per_pt) return BVC_ERR_WORKSPACE;
-  int64_t chunk = (int64_t)((workspace_bytes - kWsHead) / per_pt);
-  if (chunk > m) chunk = m;
   cudaStream_t s = (cudaStream_t)stream;
-  P.starts = pts;
-  P.nrm = nullptr;
-  P.pt_stride = m;
-  P.W = walks;
-  P.eps = eps;
-  P.max_steps = max_steps;
-  P.seed = seed;
-  P.tag = 3;
-  P.counter = (unsigned long long*)workspace;
-  P.rec = (float*)((char*)workspace + kWsHead);
-  for (int64_t i0 = 0; i0 < m; i0 += chunk) {
-    const int64_t c = (m - i0) < chunk ? (m - i0) : chunk;
-    P.i0 = i0;
-    P.total = c * (int64_t)walks;
-    P.wid0 = id_base + (uint64_t)i0 * (uint64_t)walks;
-    bvc_status st = launch_walk(D, P.f.n_terms > 0, false, P, s);
-    if (st != BVC_OK) return st;
-    ReduceParams R{};
-    R.rec = P.rec;
-    R.n = c;
-    R.W = walks;
-    R.planes = grad_sum ? 1 + D : 1;
-    R.stride = P.total;
-    R.mode = 1;
-    R.out[0] = u_sum + i0;
-    if (grad_sum)
-      for (int a = 0; a < D; ++a) R.out[1 + a] = grad_sum + (int64_t)a * m + i0;
-    st = launch_reduce(R, s);
-    if (st != BVC_OK) return st;
+  if (m > 0) {
+    const size_t per_pt = (size_t)walks * (1 + D) * sizeof(float);
+    if (workspace_bytes < kWsHead + per_pt) return BVC_ERR_WORKSPACE;
+    int64_t chunk = (int64_t)((workspace_bytes - kWsHead) / per_pt);
+    if (chunk > m) chunk = m;
+    P.starts = state->x;
+    P.nrm = nullptr;
+    P.pt_stride = m;
+    P.W = walks;
+    P.eps = eps;
+    P.max_steps = max_steps;
+    P.seed = seed;
+    P.tag = 3;
+    P.counter = (unsigned long long*)workspace;
+    P.rec = (float*)((char*)workspace + kWsHead);
+    const bool grad = state->grad_bnd != nullptr;
+    for (int64_t i0 = 0; i0 < m; i0 += chunk) {
+      const int64_t c = (m - i0) < chunk ? (m - i0) : chunk;
+      P.i0 = i0;
+      P.total = c * (int64_t)walks;
+      P.wid0 = id_base + (uint64_t)i0 * (uint64_t)walks;
+      bvc_status st = launch_walk(D, P.f.n_terms > 0, false, g->counting != 0, P, s);
+      if (st != BVC_OK) return st;
+      ReduceParams R{};
+      R.rec = P.rec;
+      R.n = c;
+      R.W = walks;
+      R.planes = grad ? 1 + D : 1;
+      R.stride = P.total;
+      R.mode = 1;
+      R.out[0] = state->u_bnd + i0;
+      if (grad)
+        for (int a = 0; a < D; ++a) R.out[1 + a] = state->grad_bnd + (int64_t)a * m + i0;
+      st = launch_reduce(R, s);
+      if (st != BVC_OK) return st;
+    }
   }
+  {
+    ProfScope ps("add_counts", s);
+    k_add_walk_count<<<1, 32, 0, s>>>(state->counts, walks);
+  }
+  BVC_LAUNCH_CHECK();
   return BVC_OK;
 }

@@ -76,19 +76,57 @@ def test_wos_estimate_replays_oracle():
     near = bvc.classify_near(geom, bvc.soa(w.eval_pts), w.offset_l).cpu().numpy().astype(bool)
     pts = w.eval_pts[~near][:257]
     W = 64
-    u_sum, g_sum = bvc.wos_estimate(geom, w.g, w.f, bvc.soa(pts), W, w.eps, 1 << 14, seed=4)
+    st = bvc.EvalState(bvc.soa(pts))
+    bvc.wos_estimate(geom, w.g, w.f, st, W, w.eps, 1 << 14, seed=4)
+    ug, gg = bvc.get_solution(st)
     torch.cuda.synchronize()
+    assert st.counts.cpu().tolist() == [W, 0]
     o = oracle.walks(oracle.BVH(w.V, w.F), w.g, w.f, pts, W, w.eps, 1 << 14, 4, 0, oracle.TAG_POINTWISE)
     uo = o["U"].reshape(-1, W).mean(1)
-    ug = u_sum.cpu().numpy() / W
+    go = o["grad"].reshape(-1, W, 2).mean(1)
+    ug = ug.cpu().numpy()
     rng_u = np.abs(o["U"]).max()
     agree = np.abs(ug - uo) <= 1e-4 * rng_u
     exact, _ = wl.eval_terms(w.exact, 2, pts.astype(np.float64))
     print(f"[wos pointwise] points={pts.shape[0]} agree={agree.mean():.3f} "
-          f"RMSE_vs_oracle={np.sqrt(np.mean((ug - uo) ** 2)):.3e} RMSE_vs_exact={np.sqrt(np.mean((ug - exact) ** 2)):.3e}")
+          f"RMSE_vs_oracle={np.sqrt(np.mean((ug - uo) ** 2)):.3e} RMSE_vs_exact={np.sqrt(np.mean((ug - exact) ** 2)):.3e} "
+          f"gradRMSE_vs_oracle={np.sqrt(np.mean((gg.cpu().numpy().T - go) ** 2)):.3e}")
     assert agree.mean() >= 0.97
-    # progressive: a second call with the next id range accumulates
-    bvc.wos_estimate(geom, w.g, w.f, bvc.soa(pts), W, w.eps, 1 << 14, seed=4, id_base=pts.shape[0] * W,
-                     u_sum=u_sum, grad_sum=g_sum)
+    # progressive: a second call with the next id range refines the same sums
+    bvc.wos_estimate(geom, w.g, w.f, st, W, w.eps, 1 << 14, seed=4, id_base=pts.shape[0] * W)
+    u2, _ = bvc.get_solution(st)
     torch.cuda.synchronize()
-    assert np.all(np.isfinite(u_sum.cpu().numpy()))
+    assert st.counts.cpu().tolist() == [2 * W, 0]
+    o2 = oracle.walks(oracle.BVH(w.V, w.F), w.g, w.f, pts, W, w.eps, 1 << 14, 4, pts.shape[0] * W,
+                      oracle.TAG_POINTWISE)
+    u2o = (o["U"].reshape(-1, W).sum(1) + o2["U"].reshape(-1, W).sum(1)) / (2 * W)
+    assert np.mean(np.abs(u2.cpu().numpy() - u2o) <= 1e-4 * rng_u) >= 0.97
+
+
+def test_profiler_counts_library_launches():
+    w = wl.circle_laplace(n_samples=256, walks=8)
+    geom = bvc.Geometry(w.V, w.F)
+    opts = bvc.cache_opts(w.n_samples, w.walks, w.offset_l, w.eps, seed=1)
+    cache = bvc.Cache(2, w.n_samples)
+    st = bvc.EvalState(bvc.soa(w.eval_pts))
+    bvc.profile_begin()
+    bvc.cache_build(geom, w.g, w.f, opts, cache)
+    bvc.evaluate(cache, st)
+    bvc.get_solution(st)
+    prof = bvc.profile_end()
+    for k in ("sample_boundary", "walk", "reduce_walks", "pack_boundary", "gather_boundary", "get_solution"):
+        assert prof[k][0] >= 1 and prof[k][1] > 0.0, (k, prof)
+
+
+def test_counting_mode_gives_same_walks():
+    w = wl.circle_laplace(n_samples=256, walks=8)
+    geom = bvc.Geometry(w.V, w.F)
+    opts = bvc.cache_opts(w.n_samples, w.walks, w.offset_l, w.eps, seed=1)
+    a = bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, w.n_samples))
+    geom.stats(reset=True)
+    geom.set_counting(True)
+    b = bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, w.n_samples))
+    s = geom.stats(reset=True)
+    geom.set_counting(False)
+    assert torch.equal(a.u_hat, b.u_hat) and torch.equal(a.dudn_hat, b.dudn_hat)
+    assert s["nodes"] >= s["steps"] > 0 and s["prims"] >= s["steps"]
