@@ -41,7 +41,7 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MAX_STEPS = 1 << 14
 
-# Algorithmic work per unit (see DESIGN.md): bytes per BVH node fetch and
+# Algorithmic work per unit: bytes per BVH node fetch and
 # per primitive test, per-walk input/output bytes, FP32 flops per pair.
 BYTES_NODE = {2: 48, 3: 64}
 BYTES_PRIM = {2: 16, 3: 48}
