@@ -289,6 +289,28 @@ bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_funct
  * out).  Synchronises the device; reset != 0 clears it. */
 bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
 
+/* wos_estimate with no caller workspace and no allocation.  The paper has
+ * no counterpart: this is an interface for callers that must not allocate
+ * device memory -- for example code that runs inside another framework
+ * whose allocator owns all device memory, host callbacks where CUDA
+ * allocation calls are not permitted, or latency-critical loops that cannot
+ * afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * The walk records live in a 16 MiB array of static device memory inside
+ * this library (held on every GPU that loads the library until the process
+ * exits); points are processed in chunks that fit it, so m is unbounded but
+ * one point's records, walks * (1 + dim) * 4 bytes, must fit beside a
+ * 256-byte counter: walks > 1,398,080 (2D) or 1,048,560 (3D) returns
+ * BVC_ERR_WORKSPACE.  Arguments, results and state semantics are those of
+ * wos_estimate.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (on different streams, or from several threads) race on it and must be
+ * serialised by the caller.  The work counter in the array is cleared at
+ * the start of every call. */
+bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                       bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps,
+                                       uint64_t seed, uint64_t id_base, bvc_stream stream);
+
 /* ------------------------------------------------------------- profiling */
 /* Between bvc_profile_begin and bvc_profile_end every kernel the library
  * launches is bracketed by CUDA events on its own stream.  bvc_profile_end

@@ -101,6 +101,8 @@ def _declare(lib):
         "wos_estimate": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct), i32, f32, i32,
                              u64, u64, P, sz, P]),
         "bvc_eval_state_reset": (S, [C.POINTER(EvalStateStruct), P]),
+        "wos_estimate_static_scratch": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct),
+                                            i32, f32, i32, u64, u64, P]),
         "bvc_geometry_set_counting": (S, [P, i32]),
         "bvc_profile_begin": (S, []),
         "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
@@ -435,6 +437,17 @@ def wos_estimate(geom: Geometry, g_terms, f_terms, state: EvalState, walks: int,
     _check(lib().wos_estimate(geom.h, C.byref(g), C.byref(f), C.byref(state.struct), int(walks), float(eps),
                               int(max_steps), int(seed), int(id_base), _ptr(ws), ws.numel(), _stream(stream)),
            "wos_estimate")
+    return state
+
+
+def wos_estimate_static_scratch(geom: Geometry, g_terms, f_terms, state: EvalState, walks: int, eps: float,
+                                max_steps: int, seed: int, id_base: int = 0, stream=None):
+    """wos_estimate for callers that cannot allocate: the library's own static
+    16 MiB device scratch replaces the workspace (see include/bvc.h)."""
+    g, f = make_function(g_terms), make_function(f_terms)
+    _check(lib().wos_estimate_static_scratch(geom.h, C.byref(g), C.byref(f), C.byref(state.struct), int(walks),
+                                             float(eps), int(max_steps), int(seed), int(id_base), _stream(stream)),
+           "wos_estimate_static_scratch")
     return state
 
 

@@ -13,6 +13,7 @@
 // Per-walk results go to FP32 records; K3 reduces them in FP64 in a fixed
 // order, so results do not depend on scheduling.
 #include <cmath>
+#include <mutex>
 
 #include "bvc_device.cuh"
 #include "bvc_internal.h"
@@ -456,4 +457,53 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
   }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// wos_estimate_static_scratch: the pointwise estimator for callers that may
+// not allocate device memory.  Its scratch (walk records and the work
+// counter) is this file-scope array, so it needs no workspace from the
+// caller and performs no allocation.  Every GPU that loads the library keeps
+// the array resident until the process exits.
+namespace {
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_wos_scratch[kStaticScratchBytes];
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+bvc_status static_scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return BVC_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= 64) return BVC_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_wos_scratch) != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();
+      return BVC_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return BVC_OK;
+}
+}  // namespace
+
+extern "C" bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                                  bvc_eval_state* state, int32_t walks, float eps,
+                                                  int32_t max_steps, uint64_t seed, uint64_t id_base,
+                                                  bvc_stream stream) {
+  if (g == nullptr || state == nullptr || walks < 1) return BVC_ERR_INVALID_ARG;
+  // the records of one point's walks must fit beside the counter
+  const size_t per_pt = (size_t)walks * (1 + g->dim) * sizeof(float);
+  if (kWsHead + per_pt > kStaticScratchBytes) return BVC_ERR_WORKSPACE;
+  void* scratch = nullptr;
+  const bvc_status st = static_scratch_address(&scratch);
+  if (st != BVC_OK) return st;
+  return wos_estimate(g, gfn, ffn, state, walks, eps, max_steps, seed, id_base, scratch, kStaticScratchBytes, stream);
 }
