@@ -4,12 +4,16 @@
 //
 // Walk kernel design.  One thread carries one walk at a time; a persistent
 // grid (all SMs, as many blocks as fit) pulls walks from a global counter in
-// chunks of 128 per warp.  Whenever lanes finish, the warp refills exactly
-// those lanes from its chunk before the next step, so every lane of every
-// warp keeps stepping while work remains (warp-level compaction of finished
-// walks) and all lanes execute the same step code together.  Each step is
-// one BVH closest-point query (fixed-size traversal stack in shared memory),
-// one Philox draw and, when f is non-zero, one source-term evaluation.
+// chunks of 128 per warp, and whenever lanes finish their walks the warp
+// refills exactly those lanes (warp-level compaction of finished walks).
+// A walk step is one BVH closest-point query (stack in shared memory), then
+// the step itself (termination test, one Philox draw, sphere sample and,
+// when f is non-zero, one source-term evaluation).  Each lane is always in
+// one of three states -- at an internal BVH node, at a leaf, or at the step
+// -- and on every iteration the warp runs only the most populated kind of
+// work (the step once at least half the working lanes wait for it), so the
+// lanes of a warp execute the same instructions instead of diverging along
+// different tree paths, and no lane waits for the slowest query in its warp.
 // Per-walk results go to FP32 records; K3 reduces them in FP64 in a fixed
 // order, so results do not depend on scheduling.
 #include <cmath>
@@ -21,7 +25,7 @@
 namespace bvc {
 
 constexpr int kWalkBlock = 128;
-constexpr int kStack = 32;
+constexpr int kStack = 24;  // the BVH builder bounds the depth by 24
 constexpr int64_t kChunk = 128;
 
 struct WalkParams {
@@ -44,23 +48,65 @@ struct WalkParams {
   unsigned long long* counter;
 };
 
+// Lane states of the walk kernel.
+constexpr int kIdle = 0;   // holds no walk
+constexpr int kQuery = 1;  // inside a closest-point query (cur = node >= 0 or leaf < 0)
+constexpr int kStep = 2;   // query done: termination test, sphere sample, source term
+
 template <int D, bool HAS_F, bool GN, bool CNT>
 __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
   __shared__ int snode[kStack * kWalkBlock];
   __shared__ float sdist[kStack * kWalkBlock];
+  int* const stk_node = snode + threadIdx.x;  // entry e at [e * kWalkBlock]
+  float* const stk_dist = sdist + threadIdx.x;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const float kInf = __int_as_float(0x7f800000);
+  const DevGeometry& G = P.G;
+  // warp-uniform work queue
   int64_t q_next = 0, q_end = 0;
-  bool more = true, active = false;
+  bool more = true;
+  // walk state
+  int phase = kIdle;
   int64_t t = 0, i = 0;
   float x[D], nu[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) x[a] = nu[a] = 0.0f;
   float R0 = 0.0f, usrc = 0.0f, wf0 = 0.0f, wg0 = 0.0f, cv = 0.0f;
   int k = 0;
+  // query state
+  int cur = 0, sp = 0;
+  float thr = kInf;
+  Hit<D> h;
+  h.d2 = kInf;
+  h.id = 0x7fffffff;
+#pragma unroll
+  for (int a = 0; a < D; ++a) h.df[a] = 0.0f;
   unsigned long long my_steps = 0, my_capped = 0, my_nodes = 0, my_prims = 0;
+
+  auto begin_query = [&]() {
+    phase = kQuery;
+    cur = 0;
+    sp = 0;
+    thr = kInf;
+    h.d2 = kInf;
+    h.id = 0x7fffffff;
+  };
+  // Next stacked item still within reach, else the query is complete.
+  auto pop = [&]() {
+    while (sp > 0) {
+      --sp;
+      if (stk_dist[sp * kWalkBlock] <= thr) {
+        cur = stk_node[sp * kWalkBlock];
+        return;
+      }
+    }
+    phase = kStep;
+  };
+
   for (;;) {
-    unsigned need = __ballot_sync(FULL, !active);
+    // ---- refill lanes without a walk (warp-converged)
+    unsigned need = __ballot_sync(FULL, phase == kIdle);
     while (need != 0u && more) {
       if (q_next >= q_end) {
         unsigned long long base = 0;
@@ -75,94 +121,153 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
       }
       const int avail = (int)min64(q_end - q_next, (int64_t)__popc(need));
       const int rank = __popc(need & ((1u << lane) - 1u));
-      if (!active && rank < avail) {
+      if (phase == kIdle && rank < avail) {
         t = q_next + rank;
         i = P.i0 + t / P.W;
 #pragma unroll
         for (int a = 0; a < D; ++a) x[a] = P.starts[a * P.pt_stride + i];
         k = 0;
         R0 = usrc = wf0 = wg0 = cv = 0.0f;
-        active = true;
+        begin_query();
       }
       q_next += avail;
-      need = __ballot_sync(FULL, !active);
+      need = __ballot_sync(FULL, phase == kIdle);
     }
-    if (!__any_sync(FULL, active)) break;
-    if (active) {
-      Hit<D> h;
-      TravCount tc{0, 0};
-      bvh_closest<D, CNT>(P.G, x, h, snode + threadIdx.x, sdist + threadIdx.x, kWalkBlock, tc);
-      if (CNT) {
-        my_nodes += tc.nodes;
-        my_prims += tc.prims;
-      }
-      ++k;
-      float pbar[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
-      const float d = sqrtf(h.d2);
-      if (k == 1) cv = eval_fn<D>(P.g, pbar);
-      if (d < P.eps || k >= P.max_steps) {
-        const float U = (k == 1 ? cv : eval_fn<D>(P.g, pbar)) + usrc;
-        const float s = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
-        P.rec[t] = U;
-        if (GN) {
-          float nn = 0.0f;
-#pragma unroll
-          for (int a = 0; a < D; ++a) nn = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn);
-          P.rec[P.total + t] = s * nn;
-        } else {
-#pragma unroll
-          for (int a = 0; a < D; ++a) P.rec[(1 + a) * P.total + t] = s * nu[a];
-        }
-        if (P.steps) P.steps[t] = k;
-        if (P.prim) P.prim[t] = h.id;
-        my_steps += (unsigned long long)k;
-        if (!(d < P.eps)) ++my_capped;
-        active = false;
-      } else {
-        const float R = d;
-        const U4 r = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
-        const float u0 = u01f(r.x);
-        float om[D];
+    // ---- pick the most populated kind of work; the whole warp runs only it
+    const unsigned m_node = __ballot_sync(FULL, phase == kQuery && cur >= 0);
+    const unsigned m_leaf = __ballot_sync(FULL, phase == kQuery && cur < 0);
+    const unsigned m_step = __ballot_sync(FULL, phase == kStep);
+    const int nn = __popc(m_node), nl = __popc(m_leaf), ns = __popc(m_step);
+    if (nn + nl + ns == 0) break;
+    int choice;
+    if (ns > 0 && (2 * ns >= nn + nl + ns || nn + nl == 0))
+      choice = kStep;
+    else
+      choice = nl > nn ? 1 : 0;
+
+    if (choice == 0) {
+      // ---- one internal node: order the children, descend into the nearer
+      if (phase == kQuery && cur >= 0) {
+        if (CNT) ++my_nodes;
+        int32_t cl, cr;
+        float dl, dr;
         if (D == 2) {
-          float sn, cs;
-          sincospif(2.0f * u0, &sn, &cs);
-          om[0] = cs;
-          om[D - 1] = sn;
+          const float4 L = __ldg(&G.nodes[3 * cur]), R = __ldg(&G.nodes[3 * cur + 1]);
+          const float4 C = __ldg(&G.nodes[3 * cur + 2]);
+          dl = box_d2_2(L.x, L.y, L.z, L.w, x);
+          dr = box_d2_2(R.x, R.y, R.z, R.w, x);
+          cl = __float_as_int(C.x);
+          cr = __float_as_int(C.y);
         } else {
-          const float u1 = u01f(r.y);
-          const float zc = 1.0f - 2.0f * u0;
-          const float st = 2.0f * sqrtf(u0 * (1.0f - u0));
-          float sn, cs;
-          sincospif(2.0f * u1, &sn, &cs);
-          om[0] = st * cs;
-          om[1] = st * sn;
-          om[D - 1] = zc;
+          const float4 a = __ldg(&G.nodes[4 * cur]), b = __ldg(&G.nodes[4 * cur + 1]);
+          const float4 c = __ldg(&G.nodes[4 * cur + 2]), e = __ldg(&G.nodes[4 * cur + 3]);
+          dl = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, x);
+          dr = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, x);
+          cl = __float_as_int(e.x);
+          cr = __float_as_int(e.y);
         }
-        if (HAS_F) {
-          const float u2 = u01f(r.z);
-          const float rho = R * u2;
-          float y[D];
+        if (dr < dl) {
+          const int32_t tc = cl;
+          cl = cr;
+          cr = tc;
+          const float td = dl;
+          dl = dr;
+          dr = td;
+        }
+        const bool tl = dl <= thr, tr = dr <= thr;
+        if (tl && tr) {
+          stk_node[sp * kWalkBlock] = cr;
+          stk_dist[sp * kWalkBlock] = dr;
+          ++sp;
+          cur = cl;
+        } else if (tl) {
+          cur = cl;
+        } else if (tr) {
+          cur = cr;
+        } else {
+          pop();
+        }
+      }
+    } else if (choice == 1) {
+      // ---- one leaf: canonical FP32 distances, ties to the lowest index
+      if (phase == kQuery && cur < 0) {
+        TravCount tc{0, 0};
+        test_leaf<D, CNT>(G, cur, x, h, thr, tc);
+        if (CNT) my_prims += tc.prims;
+        pop();
+      }
+    } else {
+      // ---- walk step on the finished query
+      if (phase == kStep) {
+        ++k;
+        float pbar[D];
 #pragma unroll
-          for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
-          const float fy = eval_fn<D>(P.f, y);
-          // ball Green's function weights: -R rho ln(R/rho) (2D), -rho (R - rho) (3D)
-          const float wu = D == 2 ? R * rho * logf(u2) : -rho * (R - rho);
-          usrc = fmaf(wu, fy, usrc);
-          if (k == 1) {
-            wf0 = wu * fy;
-            const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
-            wg0 = -R * (1.0f - q) * fy;
+        for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
+        const float d = sqrtf(h.d2);
+        if (k == 1) cv = eval_fn<D>(P.g, pbar);
+        if (d < P.eps || k >= P.max_steps) {
+          const float U = (k == 1 ? cv : eval_fn<D>(P.g, pbar)) + usrc;
+          const float sc = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
+          P.rec[t] = U;
+          if (GN) {
+            float nn2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn2);
+            P.rec[P.total + t] = sc * nn2;
+          } else {
+#pragma unroll
+            for (int a = 0; a < D; ++a) P.rec[(1 + a) * P.total + t] = sc * nu[a];
           }
-        }
-        if (k == 1) {
-          R0 = R;
+          if (P.steps) P.steps[t] = k;
+          if (P.prim) P.prim[t] = h.id;
+          my_steps += (unsigned long long)k;
+          if (!(d < P.eps)) ++my_capped;
+          phase = kIdle;
+        } else {
+          const float R = d;
+          const U4 r = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
+          const float u0 = u01f(r.x);
+          float om[D];
+          if (D == 2) {
+            float sn, cs;
+            sincospif(2.0f * u0, &sn, &cs);
+            om[0] = cs;
+            om[D - 1] = sn;
+          } else {
+            const float u1 = u01f(r.y);
+            const float zc = 1.0f - 2.0f * u0;
+            const float st = 2.0f * sqrtf(u0 * (1.0f - u0));
+            float sn, cs;
+            sincospif(2.0f * u1, &sn, &cs);
+            om[0] = st * cs;
+            om[1] = st * sn;
+            om[D - 1] = zc;
+          }
+          if (HAS_F) {
+            const float u2 = u01f(r.z);
+            const float rho = R * u2;
+            float y[D];
 #pragma unroll
-          for (int a = 0; a < D; ++a) nu[a] = om[a];
-        }
+            for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
+            const float fy = eval_fn<D>(P.f, y);
+            // ball Green's function weights: -R rho ln(R/rho) (2D), -rho (R - rho) (3D)
+            const float wu = D == 2 ? R * rho * logf(u2) : -rho * (R - rho);
+            usrc = fmaf(wu, fy, usrc);
+            if (k == 1) {
+              wf0 = wu * fy;
+              const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
+              wg0 = -R * (1.0f - q) * fy;
+            }
+          }
+          if (k == 1) {
+            R0 = R;
 #pragma unroll
-        for (int a = 0; a < D; ++a) x[a] = fmaf(R, om[a], x[a]);
+            for (int a = 0; a < D; ++a) nu[a] = om[a];
+          }
+#pragma unroll
+          for (int a = 0; a < D; ++a) x[a] = fmaf(R, om[a], x[a]);
+          begin_query();
+        }
       }
     }
   }

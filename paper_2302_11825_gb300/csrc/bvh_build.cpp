@@ -30,7 +30,7 @@ static inline float4 make_float4(float x, float y, float z, float w) {
 namespace bvc {
 
 constexpr int kLeafMax = 4;
-constexpr int kMaxDepth = 30;  // traversal stack holds 32 entries
+constexpr int kMaxDepth = 24;  // traversal stacks hold 24 entries
 constexpr int kBins = 16;
 
 struct Box {
