@@ -44,7 +44,7 @@ MAX_STEPS = 1 << 14
 # Algorithmic work per unit: bytes per BVH node fetch and
 # per primitive test, per-walk input/output bytes, FP32 flops per pair.
 BYTES_NODE = {2: 48, 3: 64}
-BYTES_PRIM = {2: 16, 3: 48}
+BYTES_PRIM = {2: 32, 3: 48}
 FLOPS_PAIR_BND = {2: 25, 3: 37}
 FLOPS_PAIR_SRC = {2: 9, 3: 13}
 

@@ -290,21 +290,22 @@ void orc_closest_brute64(int dim, const float* V, int64_t nv, const int32_t* F, 
 /* ------------------------------------------------------------------------ */
 /* Canonical FP32 closest-point distances.  Fixed operation order with      */
 /* explicit fmaf; the primitive is (a, ab = b-a, [ac = c-a]) in FP32.        */
-/* Used only to check the GPU's primitive index bit-exactly.                 */
+/* Segment: with num = ab.ap, den = |ab|^2 and inv = 1/den (one FP32         */
+/* division per segment): |ap|^2 if num <= 0, |ap-ab|^2 if num >= den, else  */
+/* cross(ap,ab)^2 * inv.  Triangle: Ericson's Voronoi regions.  Used only to */
+/* check the GPU's primitive index bit-exactly.                             */
 /* ------------------------------------------------------------------------ */
-static float seg_d2_f32(float ax, float ay, float abx, float aby, float px, float py) {
+static float seg_d2_f32(float ax, float ay, float abx, float aby, float inv, float px, float py) {
   const float apx = px - ax, apy = py - ay;
   const float num = fmaf(apy, aby, apx * abx);
   const float den = fmaf(aby, aby, abx * abx);
-  float t;
-  if (num <= 0.0f)
-    t = 0.0f;
-  else if (num >= den)
-    t = 1.0f;
-  else
-    t = num / den;
-  const float dx = fmaf(-t, abx, apx), dy = fmaf(-t, aby, apy);
-  return fmaf(dy, dy, dx * dx);
+  if (num <= 0.0f) return fmaf(apy, apy, apx * apx);
+  if (num >= den) {
+    const float bx = apx - abx, by = apy - aby;
+    return fmaf(by, by, bx * bx);
+  }
+  const float c = fmaf(apx, aby, -(apy * abx));
+  return (c * c) * inv;
 }
 
 static float dot3f(const float* u, const float* v) { return fmaf(u[2], v[2], fmaf(u[1], v[1], u[0] * v[0])); }
@@ -358,6 +359,7 @@ void orc_closest_brute32(int dim, const float* V, int64_t nv, const int32_t* F, 
       P[e * 9 + 3 + a] = V[(int64_t)f[1] * dim + a] - va;
       if (dim == 3) P[e * 9 + 6 + a] = V[(int64_t)f[2] * dim + a] - va;
     }
+    if (dim == 2) P[e * 9 + 6] = 1.0f / fmaf(P[e * 9 + 4], P[e * 9 + 4], P[e * 9 + 3] * P[e * 9 + 3]);
   }
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t q = 0; q < n; ++q) {
@@ -366,7 +368,7 @@ void orc_closest_brute32(int dim, const float* V, int64_t nv, const int32_t* F, 
     const float* p = pts + q * dim;
     for (int64_t e = 0; e < np; ++e) {
       const float* r = P + e * 9;
-      const float d2 = dim == 2 ? seg_d2_f32(r[0], r[1], r[3], r[4], p[0], p[1]) : tri_d2_f32(r, r + 3, r + 6, p);
+      const float d2 = dim == 2 ? seg_d2_f32(r[0], r[1], r[3], r[4], r[6], p[0], p[1]) : tri_d2_f32(r, r + 3, r + 6, p);
       if (d2 < best) {
         best = d2;
         bi = (int32_t)e;

@@ -7,9 +7,11 @@
 // subtraction.  The squared distance from p is the following fixed sequence
 // of correctly rounded FP32 operations (no contraction):
 //   segment:  ap = p - a; num = fma(ap.y, ab.y, ap.x*ab.x);
-//             den = fma(ab.y, ab.y, ab.x*ab.x);
-//             t = num <= 0 ? 0 : num >= den ? 1 : num/den;
-//             d = (fma(-t, ab.x, ap.x), fma(-t, ab.y, ap.y)); d2 = fma(d.y, d.y, d.x*d.x)
+//             den = fma(ab.y, ab.y, ab.x*ab.x); inv = 1/den (one FP32
+//             division, precomputed per segment);
+//             num <= 0:    d2 = fma(ap.y, ap.y, ap.x*ap.x)
+//             num >= den:  bp = ap - ab; d2 = fma(bp.y, bp.y, bp.x*bp.x)
+//             otherwise:   c = fma(ap.x, ab.y, -(ap.y*ab.x)); d2 = (c*c)*inv
 //   triangle: the Voronoi-region classification of Ericson, "Real-Time
 //             Collision Detection" Sec. 5.1.5, written on (ap, ab, ac) with
 //             dot(u,v) = fma(u.z, v.z, fma(u.y, v.y, u.x*v.x)),
@@ -66,7 +68,14 @@ __device__ __forceinline__ float u01f(uint32_t r) { return (float)((r >> 9) * 2u
 __device__ __forceinline__ double u01d(uint32_t r) { return (double)((r >> 9) * 2u + 1u) * 0x1p-24; }
 
 // ------------------------------------------------------- problem functions
-template <int D>
+// FAST: exp via the SFU (__expf, a few ulp), for the walks; the accurate
+// expf elsewhere.
+template <int D, bool FAST = false>
+__device__ __forceinline__ float ex(float v) {
+  return FAST ? __expf(v) : expf(v);
+}
+
+template <int D, bool FAST = false>
 __device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) {
   float v = 0.0f;
   for (int t = 0; t < fn.n_terms; ++t) {
@@ -102,7 +111,7 @@ __device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) 
             const float d = x[a] - c[k + 1 + a];
             r2 = fmaf(d, d, r2);
           }
-          v = fmaf(c[k], expf(r2 * neg), v);
+          v = fmaf(c[k], ex<D, FAST>(r2 * neg), v);
         }
         break;
       }
@@ -115,12 +124,12 @@ __device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) 
             const float d = x[a] - c[k + 1 + a];
             r2 = fmaf(d, d, r2);
           }
-          v = fmaf(c[k] * fmaf(r2, q4, qd), expf(r2 * neg), v);
+          v = fmaf(c[k] * fmaf(r2, q4, qd), ex<D, FAST>(r2 * neg), v);
         }
         break;
       }
       case BVC_FN_EXP_TRIG:
-        if (D == 3) v = fmaf(c[0] * expf(c[1] * x[D == 3 ? 2 : 0]), cosf(c[2] * x[0]) * sinf(c[3] * x[1]), v);
+        if (D == 3) v = fmaf(c[0] * ex<D, FAST>(c[1] * x[D == 3 ? 2 : 0]), cosf(c[2] * x[0]) * sinf(c[3] * x[1]), v);
         break;
       default:
         break;
@@ -130,21 +139,27 @@ __device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) 
 }
 
 // ------------------------------------------- canonical closest-point distance
-__device__ __forceinline__ float seg_closest(float ax, float ay, float abx, float aby, float px, float py,
-                                             float& dx, float& dy) {
-  const float apx = __fsub_rn(px, ax), apy = __fsub_rn(py, ay);
-  const float num = __fmaf_rn(apy, aby, __fmul_rn(apx, abx));
-  const float den = __fmaf_rn(aby, aby, __fmul_rn(abx, abx));
-  float t;
-  if (num <= 0.0f)
-    t = 0.0f;
-  else if (num >= den)
-    t = 1.0f;
-  else
-    t = __fdiv_rn(num, den);
-  dx = __fmaf_rn(-t, abx, apx);
-  dy = __fmaf_rn(-t, aby, apy);
-  return __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+// S = (a.x, a.y, ab.x, ab.y), inv = 1/|ab|^2.
+__device__ __forceinline__ float seg_d2(const float4 S, float inv, float px, float py) {
+  const float apx = __fsub_rn(px, S.x), apy = __fsub_rn(py, S.y);
+  const float num = __fmaf_rn(apy, S.w, __fmul_rn(apx, S.z));
+  const float den = __fmaf_rn(S.w, S.w, __fmul_rn(S.z, S.z));
+  const float bx = __fsub_rn(apx, S.z), by = __fsub_rn(apy, S.w);
+  const float c = __fmaf_rn(apx, S.w, -__fmul_rn(apy, S.z));
+  const float da = __fmaf_rn(apy, apy, __fmul_rn(apx, apx));
+  const float db = __fmaf_rn(by, by, __fmul_rn(bx, bx));
+  const float dc = __fmul_rn(__fmul_rn(c, c), inv);
+  return num <= 0.0f ? da : (num >= den ? db : dc);
+}
+
+// p - (closest point on the segment), for the winning segment of a query.
+__device__ __forceinline__ void seg_diff(const float4 S, float inv, float px, float py, float& dx, float& dy) {
+  const float apx = __fsub_rn(px, S.x), apy = __fsub_rn(py, S.y);
+  const float num = __fmaf_rn(apy, S.w, __fmul_rn(apx, S.z));
+  const float den = __fmaf_rn(S.w, S.w, __fmul_rn(S.z, S.z));
+  const float t = num <= 0.0f ? 0.0f : (num >= den ? 1.0f : __fmul_rn(num, inv));
+  dx = __fmaf_rn(-t, S.z, apx);
+  dy = __fmaf_rn(-t, S.w, apy);
 }
 
 __device__ __forceinline__ float dot3c(float ux, float uy, float uz, float vx, float vy, float vz) {
@@ -216,8 +231,9 @@ __device__ __forceinline__ float tri_closest(const float4 A, const float4 B, con
 template <int D>
 struct Hit {
   float d2;
-  int32_t id;  // caller's element index
-  float df[D]; // p - closest point
+  int32_t id;   // caller's element index
+  int32_t q;    // BVH-order record of the element
+  float df[D];  // p - closest point (3D: kept during the query; 2D: by finish_hit)
 };
 
 __device__ __forceinline__ float box_d2_2(float lox, float loy, float hix, float hiy, const float* p) {
@@ -246,26 +262,41 @@ __device__ __forceinline__ void test_leaf(const DevGeometry& G, int32_t enc, con
   const int32_t first = e >> 3, count = e & 7;
   if (CNT) tc.prims += (uint32_t)count;
   for (int32_t q = first; q < first + count; ++q) {
-    float df[D];
-    float d2;
     if (D == 2) {
-      const float4 s = __ldg(&G.prims[q]);
-      d2 = seg_closest(s.x, s.y, s.z, s.w, p[0], p[1], df[0], df[D > 1 ? 1 : 0]);
-    } else {
-      const float4 A = __ldg(&G.prims[3 * q]), B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
-      d2 = tri_closest(A, B, Cc, p, df);
-    }
-    if (d2 <= h.d2) {
-      const int32_t id = __ldg(&G.prim_ids[q]);
-      if (d2 < h.d2 || id < h.id) {
+      const float4 S = __ldg(&G.prims[2 * q]), T = __ldg(&G.prims[2 * q + 1]);
+      const float d2 = seg_d2(S, T.x, p[0], p[1]);
+      const int32_t id = __float_as_int(T.y);
+      if (d2 < h.d2 || (d2 == h.d2 && id < h.id)) {
         h.d2 = d2;
         h.id = id;
+        h.q = q;
+        const float sr = sqrtf(d2) + G.tau;
+        thr = sr * sr;
+      }
+    } else {
+      const float4 A = __ldg(&G.prims[3 * q]), B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
+      float df[3];
+      const float d2 = tri_closest(A, B, Cc, p, df);
+      const int32_t id = __float_as_int(A.w);
+      if (d2 < h.d2 || (d2 == h.d2 && id < h.id)) {
+        h.d2 = d2;
+        h.id = id;
+        h.q = q;
 #pragma unroll
-        for (int a = 0; a < D; ++a) h.df[a] = df[a];
-        const float s = sqrtf(d2) + G.tau;
-        thr = s * s;
+        for (int a = 0; a < D; ++a) h.df[a] = df[D == 3 ? a : 0];
+        const float sr = sqrtf(d2) + G.tau;
+        thr = sr * sr;
       }
     }
+  }
+}
+
+// Completes a hit: the difference vector p - closest point of the winner.
+template <int D>
+__device__ __forceinline__ void finish_hit(const DevGeometry& G, const float* p, Hit<D>& h) {
+  if (D == 2 && h.q >= 0) {
+    const float4 S = __ldg(&G.prims[2 * h.q]), T = __ldg(&G.prims[2 * h.q + 1]);
+    seg_diff(S, T.x, p[0], p[1], h.df[0], h.df[D - 1]);
   }
 }
 
@@ -275,6 +306,7 @@ __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p
                                             float* sdist, int stride, TravCount& tc) {
   h.d2 = __int_as_float(0x7f800000);
   h.id = 0x7fffffff;
+  h.q = -1;
 #pragma unroll
   for (int a = 0; a < D; ++a) h.df[a] = 0.0f;
   float thr = __int_as_float(0x7f800000);
@@ -343,6 +375,7 @@ __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p
     }
     if (!found) break;
   }
+  finish_hit<D>(G, p, h);
 }
 
 }  // namespace bvc

@@ -148,6 +148,12 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   for (int64_t e = 0; e < n_prims; ++e) {
     const double m = elem_measure(dim, verts, prims + e * dim);
     if (!(m > 0.0)) return BVC_ERR_DEGENERATE_MESH;
+    if (dim == 2) {  // the FP32 squared length must be a normal positive number
+      const int32_t* f = prims + e * dim;
+      const float dx = verts[2 * f[1]] - verts[2 * f[0]], dy = verts[2 * f[1] + 1] - verts[2 * f[0] + 1];
+      const float den = std::fmaf(dy, dy, dx * dx);
+      if (!(den >= 1.17549435e-38f) || !std::isfinite(1.0f / den)) return BVC_ERR_DEGENERATE_MESH;
+    }
     cdf[e + 1] = cdf[e] + m;
   }
   std::vector<float4> nodes, pr;
@@ -175,12 +181,11 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
 
   const size_t b_nodes = align256(nodes.size() * sizeof(float4));
   const size_t b_prims = align256(pr.size() * sizeof(float4));
-  const size_t b_ids = align256(ids.size() * sizeof(int32_t));
   const size_t b_cdf = align256(cdf.size() * sizeof(double));
   const size_t b_verts = align256((size_t)n_verts * dim * sizeof(float));
   const size_t b_idx = align256((size_t)n_prims * dim * sizeof(int32_t));
   const size_t b_stats = 256;
-  g->arena_bytes = b_nodes + b_prims + b_ids + b_cdf + b_verts + b_idx + b_stats;
+  g->arena_bytes = b_nodes + b_prims + b_cdf + b_verts + b_idx + b_stats;
   if (cudaMalloc(&g->arena, g->arena_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     delete g;
@@ -190,8 +195,7 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   DevGeometry& d = g->dev;
   d.nodes = (const float4*)base;
   d.prims = (const float4*)(base += b_nodes);
-  d.prim_ids = (const int32_t*)(base += b_prims);
-  d.cdf = (const double*)(base += b_ids);
+  d.cdf = (const double*)(base += b_prims);
   d.verts = (const float*)(base += b_cdf);
   d.idx = (const int32_t*)(base += b_verts);
   d.stats = (unsigned long long*)(base += b_idx);
@@ -207,7 +211,6 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
                 cudaSuccess &&
             cudaMemcpyAsync((void*)d.prims, pr.data(), pr.size() * sizeof(float4), cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
-            cudaMemcpyAsync((void*)d.prim_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
             cudaMemcpyAsync((void*)d.cdf, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
             cudaMemcpyAsync((void*)d.verts, verts, (size_t)n_verts * dim * 4, cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&

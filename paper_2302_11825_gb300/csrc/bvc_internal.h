@@ -28,12 +28,11 @@ struct DevFunction {
 //  nodes: 2D 3 float4 per node  [L.lo.x L.lo.y L.hi.x L.hi.y] [R ...] [cl cr - -]
 //         3D 4 float4 per node  [L.lo.xyz L.hi.x] [L.hi.yz R.lo.xy] [R.lo.z R.hi.xyz] [cl cr - -]
 //         child >= 0: internal node; child < 0: leaf, ~child = first << 3 | count.
-//  prims: BVH order; 2D one float4 (a, ab); 3D three float4 (a,-) (ab,-) (ac,-).
-//  prim_ids: caller's index of each BVH-ordered primitive.
+//  prims: BVH order; 2D two float4 (a, ab) (1/|ab|^2, id, -, -); 3D three
+//         float4 (a, id) (ab, -) (ac, -); id = caller's element index (int bits).
 struct DevGeometry {
   const float4* nodes;
   const float4* prims;
-  const int32_t* prim_ids;
   const double* cdf;      // [n_prims + 1] FP64 prefix sums of element measures (caller order)
   const float* verts;     // [n_verts][dim] caller's vertices
   const int32_t* idx;     // [n_prims][dim] caller's element indices

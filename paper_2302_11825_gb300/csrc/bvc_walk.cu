@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
     thr = kInf;
     h.d2 = kInf;
     h.id = 0x7fffffff;
+    h.q = -1;
   };
   // Next stacked item still within reach, else the query is complete.
   auto pop = [&]() {
@@ -146,8 +147,10 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
       choice = nl > nn ? 1 : 0;
 
     if (choice == 0) {
-      // ---- one internal node: order the children, descend into the nearer
-      if (phase == kQuery && cur >= 0) {
+      // ---- up to two internal nodes: order the children, descend into the nearer
+#pragma unroll 1
+      for (int rep = 0; rep < 2; ++rep) {
+        if (!(phase == kQuery && cur >= 0)) break;
         if (CNT) ++my_nodes;
         int32_t cl, cr;
         float dl, dr;
@@ -200,13 +203,14 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
       // ---- walk step on the finished query
       if (phase == kStep) {
         ++k;
+        finish_hit<D>(G, x, h);
         float pbar[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
         const float d = sqrtf(h.d2);
-        if (k == 1) cv = eval_fn<D>(P.g, pbar);
+        if (k == 1) cv = eval_fn<D, true>(P.g, pbar);
         if (d < P.eps || k >= P.max_steps) {
-          const float U = (k == 1 ? cv : eval_fn<D>(P.g, pbar)) + usrc;
+          const float U = (k == 1 ? cv : eval_fn<D, true>(P.g, pbar)) + usrc;
           const float sc = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
           P.rec[t] = U;
           if (GN) {
@@ -249,9 +253,9 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
             float y[D];
 #pragma unroll
             for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
-            const float fy = eval_fn<D>(P.f, y);
+            const float fy = eval_fn<D, true>(P.f, y);
             // ball Green's function weights: -R rho ln(R/rho) (2D), -rho (R - rho) (3D)
-            const float wu = D == 2 ? R * rho * logf(u2) : -rho * (R - rho);
+            const float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho);
             usrc = fmaf(wu, fy, usrc);
             if (k == 1) {
               wf0 = wu * fy;

@@ -188,8 +188,9 @@ struct Builder {
 };
 
 // Builds the flattened BVH.  prims_out: BVH-ordered primitive records
-// (2D: (a, b - a); 3D: (a, -), (b - a, -), (c - a, -)), ids_out: caller's
-// index per record.  Returns the node count.
+// (2D: (a, b - a), (1/|b - a|^2, id, 0, 0) with |.|^2 = fma(dy, dy, dx*dx);
+// 3D: (a, id), (b - a, 0), (c - a, 0); id stored as int bits), ids_out:
+// caller's index per record.  Returns the node count.
 int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::vector<float4>& nodes_out,
                   std::vector<float4>& prims_out, std::vector<int32_t>& ids_out) {
   Builder B;
@@ -233,21 +234,26 @@ int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::ve
   }
   B.write_node(0, bl, br, cl, cr);
   nodes_out.swap(B.nodes);
-  const int per_prim = dim == 2 ? 1 : 3;
+  const int per_prim = dim == 2 ? 2 : 3;
   prims_out.assign(np * per_prim, make_float4(0, 0, 0, 0));
   ids_out.resize(np);
   for (int64_t q = 0; q < np; ++q) {
     const int32_t e = B.order[q];
     ids_out[q] = e;
     const int32_t* f = F + (int64_t)e * dim;
+    float idf;
+    std::memcpy(&idf, &e, 4);
     if (dim == 2) {
       const float ax = V[2 * f[0]], ay = V[2 * f[0] + 1];
-      prims_out[q] = make_float4(ax, ay, V[2 * f[1]] - ax, V[2 * f[1] + 1] - ay);
+      const float abx = V[2 * f[1]] - ax, aby = V[2 * f[1] + 1] - ay;
+      const float den = std::fmaf(aby, aby, abx * abx);
+      prims_out[2 * q] = make_float4(ax, ay, abx, aby);
+      prims_out[2 * q + 1] = make_float4(1.0f / den, idf, 0.0f, 0.0f);
     } else {
       const float* a = V + 3 * (int64_t)f[0];
       const float* b = V + 3 * (int64_t)f[1];
       const float* c = V + 3 * (int64_t)f[2];
-      prims_out[3 * q] = make_float4(a[0], a[1], a[2], 0.0f);
+      prims_out[3 * q] = make_float4(a[0], a[1], a[2], idf);
       prims_out[3 * q + 1] = make_float4(b[0] - a[0], b[1] - a[1], b[2] - a[2], 0.0f);
       prims_out[3 * q + 2] = make_float4(c[0] - a[0], c[1] - a[1], c[2] - a[2], 0.0f);
     }
