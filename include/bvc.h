@@ -192,12 +192,12 @@ typedef struct {
   float* nrm;           /* [dim][n] unit outward normals */
   double* u_hat;        /* [n] estimates of u */
   double* dudn_hat;     /* [n] estimates of du/dn */
-  float* packed;        /* [n][8] (2D) or [n][12] (3D) gather tiles, written by bvc_cache_pack */
+  float* packed;        /* [n][20] gather tiles, written by bvc_cache_pack */
   double bnd_measure;   /* |dOmega| = 1/p of the boundary samples */
   int64_t n_src_cand;   /* source candidates M (denominator of Eq. 4/6); 0 = no source cache */
   float* src_y;         /* [dim][n_src_cand] kept source points (first n_src_dev[0] valid) */
   double* src_c;        /* [n_src_cand] f(y) / p for kept points */
-  float* src_packed;    /* [n_src_cand][4] gather tiles */
+  float* src_packed;    /* [n_src_cand][8] gather tiles */
   int64_t* n_src_dev;   /* [1] number of kept source samples (written on device) */
 } bvc_cache;
 

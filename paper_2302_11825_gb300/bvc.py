@@ -294,11 +294,11 @@ class Cache:
         self.nrm = torch.zeros((dim, n), dtype=torch.float32, device=device)
         self.u_hat = torch.zeros(n, dtype=torch.float64, device=device)
         self.dudn_hat = torch.zeros(n, dtype=torch.float64, device=device)
-        self.packed = torch.zeros((n, 8 if dim == 2 else 12), dtype=torch.float32, device=device)
+        self.packed = torch.zeros((n, 20), dtype=torch.float32, device=device)
         ms = max(n_src_cand, 1)
         self.src_y = torch.zeros((dim, ms), dtype=torch.float32, device=device)
         self.src_c = torch.zeros(ms, dtype=torch.float64, device=device)
-        self.src_packed = torch.zeros((ms, 4), dtype=torch.float32, device=device)
+        self.src_packed = torch.zeros((ms, 8), dtype=torch.float32, device=device)
         self.n_src_dev = torch.zeros(1, dtype=torch.int64, device=device)
         self.bnd_measure = 0.0
         self.struct = self._make_struct()

@@ -2,23 +2,27 @@
 // the cache packing that feeds it, and Alg. 1's GetSolution.
 //
 // Per pair the terms are FP32: 2D needs one reciprocal and one log2 of r^2
-// (both on the SFU), 3D one reciprocal square root; everything else is FMA.
-// Cache samples are packed with 1/p and the Green's-function constants of
-// App. A folded into per-sample coefficients:
-//   2D boundary (8 floats):  z.x z.y n.x n.y | a 2a b b ln2/2
+// (both on the SFU), 3D one reciprocal square root; everything else is
+// packed FP32x2 arithmetic (fma/mul/add .f32x2), two evaluation points per
+// instruction.  Cache samples are packed with 1/p and the Green's-function
+// constants of App. A folded into per-sample coefficients, each value
+// stored twice so that one 16-byte shared-memory load yields two ready
+// (value, value) operand pairs:
+//   2D boundary (20 floats): z, n, a, -a, 2a, b, -b ln2/2
 //      a = u^ |dOmega| / (2 pi), b = du/dn^ |dOmega| / (2 pi)
 //      u    += a (n.d)/r^2 - b ln r
 //      grad += d (2a (n.d)/r^2 + b)/r^2 - a n / r^2            (d = z - x)
-//   3D boundary (12 floats): z n a b 3a (a, b with 4 pi)
+//   3D boundary (20 floats): z, n, a, -a, 3a, b   (a, b with 4 pi)
 //      u    += a (n.d)/r^3 + b/r
 //      grad += d (3a (n.d)/r^2 + b)/r^3 - a n / r^3
-//   2D source (4 floats): y.x y.y c/(2 pi) c ln2/(4 pi):  u += c/(2 pi) ln r,  grad -= c/(2 pi) d/r^2
-//   3D source (4 floats): y c/(4 pi):                    u -= c/(4 pi)/r,     grad -= c/(4 pi) d/r^3
+//   2D source (8 floats): y, c ln2/(4 pi), -c/(2 pi):  u += c/(2 pi) ln r,  grad -= c/(2 pi) d/r^2
+//   3D source (8 floats): y, -c/(4 pi):                u -= c/(4 pi)/r,     grad -= c/(4 pi) d/r^3
 // (G_2D = ln r/(2 pi), G_3D = -1/(4 pi r), the sign that makes Eq. 2 hold.)
 //
 // Tiles of 128 samples are brought into shared memory by bulk asynchronous
 // copies (cp.async.bulk, completion on an mbarrier), double-buffered; one
-// thread issues them while 256 threads each carry 4 evaluation points.  The
+// thread issues them while 256 threads each carry 6 (boundary) or 2
+// (source) evaluation points.  The
 // FP32 sums over a tile are added to FP64 accumulators once per tile.
 // Large cache sizes are split across CTAs; split partials are reduced in a
 // fixed order, so results are deterministic.
@@ -29,9 +33,17 @@
 namespace bvc {
 
 constexpr int kGBlock = 256;
-constexpr int kGPts = 4;       // evaluation points per thread
-constexpr int kTile = 128;     // samples per tile (FP32 partial-sum length)
-constexpr int kPtsPerCta = kGBlock * kGPts;
+constexpr int kTile = 128;  // samples per tile (FP32 partial-sum length)
+// Evaluation points per thread and resident CTAs per SM, per kind of sample
+// (measured on GB300: boundary tiles are FMA/SFU-bound and gain from reuse
+// of each shared-memory sample across 6 points; source tiles are SFU-bound
+// and gain from occupancy).
+template <int KIND>
+struct GatherShape {
+  static constexpr int kPts = KIND == 0 ? 6 : 2;
+  static constexpr int kMinBlocks = KIND == 0 ? 2 : 4;
+  static constexpr int kPtsPerCta = kGBlock * kPts;
+};
 
 __device__ unsigned long long g_gather_status = 0ull;
 
@@ -93,71 +105,115 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
+// ------------------------------------------------------------ packed FP32x2
+typedef unsigned long long f2;  // two FP32 lanes in one 64-bit register pair
+__device__ __forceinline__ f2 pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 rcp2(f2 v) {
+  float a, b;
+  upk(v, a, b);
+  return pk(rcp_approx(a), rcp_approx(b));
+}
+__device__ __forceinline__ f2 lg22(f2 v) {
+  float a, b;
+  upk(v, a, b);
+  return pk(lg2_approx(a), lg2_approx(b));
+}
+__device__ __forceinline__ f2 rsqrt2(f2 v) {
+  float a, b;
+  upk(v, a, b);
+  return pk(rsqrt_approx(a), rsqrt_approx(b));
+}
+
 // ------------------------------------------------------------ pair terms
+// T: the sample's packed float4s viewed as pairs; (px, py[, pz]) hold -x of
+// two evaluation points; acc = [u, grad...] pairs of the two points.
 template <bool GRAD>
-__device__ __forceinline__ void pair_bnd2(const float4 A, const float4 B, const float* p, float* acc) {
-  const float dx = A.x - p[0], dy = A.y - p[1];
-  const float r2 = fmaf(dy, dy, dx * dx);
-  const float inv = rcp_approx(r2);
-  const float l2 = lg2_approx(r2);
-  const float nd = fmaf(A.w, dy, A.z * dx);
-  const float s = nd * inv;
-  acc[0] = fmaf(B.x, s, acc[0]);
-  acc[0] = fmaf(-B.w, l2, acc[0]);
+__device__ __forceinline__ void pair_bnd2(const ulonglong2* T, f2 px, f2 py, f2* acc) {
+  const ulonglong2 zz = T[0], nn = T[1], aa = T[2], bb = T[3], cc = T[4];
+  // zz = (z.x, z.y), nn = (n.x, n.y), aa = (a, -a), bb = (2a, b), cc = (-b ln2/2, -)
+  const f2 dx = add2(zz.x, px), dy = add2(zz.y, py);
+  const f2 r2 = fma2(dy, dy, mul2(dx, dx));
+  const f2 inv = rcp2(r2);
+  const f2 l2 = lg22(r2);
+  const f2 nd = fma2(nn.y, dy, mul2(nn.x, dx));
+  const f2 s = mul2(nd, inv);
+  acc[0] = fma2(aa.x, s, acc[0]);
+  acc[0] = fma2(cc.x, l2, acc[0]);
   if (GRAD) {
-    const float ai = B.x * inv;
-    const float k = fmaf(B.y, s, B.z) * inv;
-    acc[1] = fmaf(k, dx, acc[1]);
-    acc[1] = fmaf(-ai, A.z, acc[1]);
-    acc[2] = fmaf(k, dy, acc[2]);
-    acc[2] = fmaf(-ai, A.w, acc[2]);
+    const f2 nai = mul2(aa.y, inv);
+    const f2 k = mul2(fma2(bb.x, s, bb.y), inv);
+    acc[1] = fma2(nai, nn.x, fma2(k, dx, acc[1]));
+    acc[2] = fma2(nai, nn.y, fma2(k, dy, acc[2]));
   }
 }
 
 template <bool GRAD>
-__device__ __forceinline__ void pair_bnd3(const float4 A, const float4 B, const float4 C, const float* p,
-                                          float* acc) {
-  const float dx = A.x - p[0], dy = A.y - p[1], dz = A.z - p[2];
-  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-  const float ir = rsqrt_approx(r2);
-  const float ir2 = ir * ir;
-  const float ir3 = ir2 * ir;
-  const float nd = fmaf(B.z, dz, fmaf(B.y, dy, B.x * dx));
-  acc[0] = fmaf(A.w * nd, ir3, acc[0]);
-  acc[0] = fmaf(B.w, ir, acc[0]);
+__device__ __forceinline__ void pair_bnd3(const ulonglong2* T, f2 px, f2 py, f2 pz, f2* acc) {
+  const ulonglong2 t0 = T[0], t1 = T[1], t2 = T[2], t3 = T[3], t4 = T[4];
+  // t0 = (z.x, z.y), t1 = (z.z, n.x), t2 = (n.y, n.z), t3 = (a, -a), t4 = (3a, b)
+  const f2 dx = add2(t0.x, px), dy = add2(t0.y, py), dz = add2(t1.x, pz);
+  const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+  const f2 ir = rsqrt2(r2);
+  const f2 ir2 = mul2(ir, ir);
+  const f2 ir3 = mul2(ir2, ir);
+  const f2 nd = fma2(t2.y, dz, fma2(t2.x, dy, mul2(t1.y, dx)));
+  acc[0] = fma2(mul2(t3.x, nd), ir3, acc[0]);
+  acc[0] = fma2(t4.y, ir, acc[0]);
   if (GRAD) {
-    const float k = fmaf(C.x, nd * ir2, B.w) * ir3;
-    const float ai = A.w * ir3;
-    acc[1] = fmaf(k, dx, acc[1]);
-    acc[1] = fmaf(-ai, B.x, acc[1]);
-    acc[2] = fmaf(k, dy, acc[2]);
-    acc[2] = fmaf(-ai, B.y, acc[2]);
-    acc[3] = fmaf(k, dz, acc[3]);
-    acc[3] = fmaf(-ai, B.z, acc[3]);
+    const f2 k = mul2(fma2(t4.x, mul2(nd, ir2), t4.y), ir3);
+    const f2 nai = mul2(t3.y, ir3);
+    acc[1] = fma2(nai, t1.y, fma2(k, dx, acc[1]));
+    acc[2] = fma2(nai, t2.x, fma2(k, dy, acc[2]));
+    acc[3] = fma2(nai, t2.y, fma2(k, dz, acc[3]));
   }
 }
 
 template <int D, bool GRAD>
-__device__ __forceinline__ void pair_src(const float4 A, const float* p, float* acc) {
+__device__ __forceinline__ void pair_src(const ulonglong2* T, f2 px, f2 py, f2 pz, f2* acc) {
+  const ulonglong2 t0 = T[0], t1 = T[1];
   if (D == 2) {
-    const float dx = A.x - p[0], dy = A.y - p[1];
-    const float r2 = fmaf(dy, dy, dx * dx);
-    acc[0] = fmaf(A.w, lg2_approx(r2), acc[0]);
+    // t0 = (y.x, y.y), t1 = (c ln2/(4 pi), -c/(2 pi))
+    const f2 dx = add2(t0.x, px), dy = add2(t0.y, py);
+    const f2 r2 = fma2(dy, dy, mul2(dx, dx));
+    acc[0] = fma2(t1.x, lg22(r2), acc[0]);
     if (GRAD) {
-      const float ci = A.z * rcp_approx(r2);
-      acc[1] = fmaf(-ci, dx, acc[1]);
-      acc[2] = fmaf(-ci, dy, acc[2]);
+      const f2 ci = mul2(t1.y, rcp2(r2));
+      acc[1] = fma2(ci, dx, acc[1]);
+      acc[2] = fma2(ci, dy, acc[2]);
     }
   } else {
-    const float dx = A.x - p[0], dy = A.y - p[1], dz = A.z - p[2];
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const float ir = rsqrt_approx(r2);
-    acc[0] = fmaf(-A.w, ir, acc[0]);
+    // t0 = (y.x, y.y), t1 = (y.z, -c/(4 pi))
+    const f2 dx = add2(t0.x, px), dy = add2(t0.y, py), dz = add2(t1.x, pz);
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    const f2 ir = rsqrt2(r2);
+    acc[0] = fma2(t1.y, ir, acc[0]);
     if (GRAD) {
-      const float ci = A.w * ir * ir * ir;
-      acc[1] = fmaf(-ci, dx, acc[1]);
-      acc[2] = fmaf(-ci, dy, acc[2]);
-      acc[3] = fmaf(-ci, dz, acc[3]);
+      const f2 ci = mul2(t1.y, mul2(mul2(ir, ir), ir));
+      acc[1] = fma2(ci, dx, acc[1]);
+      acc[2] = fma2(ci, dy, acc[2]);
+      acc[3] = fma2(ci, dz, acc[3]);
     }
   }
 }
@@ -178,8 +234,10 @@ struct GatherArgs {
 };
 
 template <int D, int KIND, bool GRAD>
-__global__ void __launch_bounds__(kGBlock) k_gather(const GatherArgs A) {
-  constexpr int SPF = KIND == 1 ? 1 : (D == 2 ? 2 : 3);
+__global__ void __launch_bounds__(kGBlock, GatherShape<KIND>::kMinBlocks) k_gather(const GatherArgs A) {
+  constexpr int kGPts = GatherShape<KIND>::kPts;
+  constexpr int kPtsPerCta = GatherShape<KIND>::kPtsPerCta;
+  constexpr int SPF = KIND == 1 ? 2 : 5;
   constexpr int NA = GRAD ? 1 + D : 1;
   __shared__ __align__(128) float4 tile[2][kTile * SPF];
   __shared__ __align__(8) uint64_t bar[2];
@@ -191,14 +249,24 @@ __global__ void __launch_bounds__(kGBlock) k_gather(const GatherArgs A) {
   const int64_t s1 = min64(n, s0 + A.split_len);
   const int64_t nt = s1 > s0 ? (s1 - s0 + kTile - 1) / kTile : 0;
 
-  // evaluation points of this thread (out-of-range points sit far away)
-  float p[kGPts][D];
+  // evaluation points of this thread (out-of-range points sit far away),
+  // negated and packed two per register pair
+  constexpr int NP = kGPts / 2;
+  f2 px[NP], py[NP], pz[NP];
   int64_t kidx[kGPts];
 #pragma unroll
-  for (int j = 0; j < kGPts; ++j) {
-    kidx[j] = (int64_t)pb * kPtsPerCta + j * kGBlock + threadIdx.x;
+  for (int j = 0; j < kGPts; ++j) kidx[j] = (int64_t)pb * kPtsPerCta + j * kGBlock + threadIdx.x;
 #pragma unroll
-    for (int a = 0; a < D; ++a) p[j][a] = kidx[j] < A.m ? A.x[a * A.m + kidx[j]] : 1.0e4f + (float)a;
+  for (int j = 0; j < NP; ++j) {
+    float c[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        c[h][a] = (a < D && kidx[2 * j + h] < A.m) ? -A.x[a * A.m + kidx[2 * j + h]] : -(1.0e4f + (float)a);
+    px[j] = pk(c[0][0], c[1][0]);
+    py[j] = pk(c[0][1], c[1][1]);
+    pz[j] = pk(c[0][2], c[1][2]);
   }
   double acc64[kGPts][NA];
 #pragma unroll
@@ -234,32 +302,34 @@ __global__ void __launch_bounds__(kGBlock) k_gather(const GatherArgs A) {
         return;
       }
       const int cnt = (int)min64(kTile, s1 - (s0 + it * kTile));
-      float acc[kGPts][NA];
+      f2 acc[NP][NA];
 #pragma unroll
-      for (int j = 0; j < kGPts; ++j)
+      for (int j = 0; j < NP; ++j)
 #pragma unroll
-        for (int q = 0; q < NA; ++q) acc[j][q] = 0.0f;
-      const float4* T = tile[b];
+        for (int q = 0; q < NA; ++q) acc[j][q] = 0ull;
+      const ulonglong2* T = reinterpret_cast<const ulonglong2*>(tile[b]);
 #pragma unroll 2
       for (int s = 0; s < cnt; ++s) {
-        if (KIND == 1) {
-          const float4 S0 = T[s];
+        const ulonglong2* Ts = T + s * SPF;
 #pragma unroll
-          for (int j = 0; j < kGPts; ++j) pair_src<D, GRAD>(S0, p[j], acc[j]);
-        } else if (D == 2) {
-          const float4 S0 = T[2 * s], S1 = T[2 * s + 1];
-#pragma unroll
-          for (int j = 0; j < kGPts; ++j) pair_bnd2<GRAD>(S0, S1, p[j], acc[j]);
-        } else {
-          const float4 S0 = T[3 * s], S1 = T[3 * s + 1], S2 = T[3 * s + 2];
-#pragma unroll
-          for (int j = 0; j < kGPts; ++j) pair_bnd3<GRAD>(S0, S1, S2, p[j], acc[j]);
+        for (int j = 0; j < NP; ++j) {
+          if (KIND == 1)
+            pair_src<D, GRAD>(Ts, px[j], py[j], pz[j], acc[j]);
+          else if (D == 2)
+            pair_bnd2<GRAD>(Ts, px[j], py[j], acc[j]);
+          else
+            pair_bnd3<GRAD>(Ts, px[j], py[j], pz[j], acc[j]);
         }
       }
 #pragma unroll
-      for (int j = 0; j < kGPts; ++j)
+      for (int j = 0; j < NP; ++j)
 #pragma unroll
-        for (int q = 0; q < NA; ++q) acc64[j][q] += (double)acc[j][q];
+        for (int q = 0; q < NA; ++q) {
+          float lo, hi;
+          upk(acc[j][q], lo, hi);
+          acc64[2 * j][q] += (double)lo;
+          acc64[2 * j + 1][q] += (double)hi;
+        }
       __syncthreads();  // every thread is done with tile[b]
       if (threadIdx.x == 0 && it + 2 < nt) {
         fence_proxy_async();
@@ -310,19 +380,28 @@ __global__ void __launch_bounds__(256) k_pack_bnd(const bvc_cache C) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= C.n) return;
   const double two_pi = 6.283185307179586476925, four_pi = 12.566370614359172953850;
+  float4* o = (float4*)C.packed + 5 * i;
   if (D == 2) {
     const double a = C.u_hat[i] * C.bnd_measure / two_pi;
     const double b = C.dudn_hat[i] * C.bnd_measure / two_pi;
-    float4* o = (float4*)C.packed + 2 * i;
-    o[0] = make_float4(C.z[i], C.z[C.n + i], C.nrm[i], C.nrm[C.n + i]);
-    o[1] = make_float4((float)a, (float)(2.0 * a), (float)b, (float)(b * 0.34657359027997265471));
+    const float zx = C.z[i], zy = C.z[C.n + i], nx = C.nrm[i], ny = C.nrm[C.n + i];
+    const float fa = (float)a, fb = (float)b, a2 = (float)(2.0 * a), nbl = (float)(-b * 0.34657359027997265471);
+    o[0] = make_float4(zx, zx, zy, zy);
+    o[1] = make_float4(nx, nx, ny, ny);
+    o[2] = make_float4(fa, fa, -fa, -fa);
+    o[3] = make_float4(a2, a2, fb, fb);
+    o[4] = make_float4(nbl, nbl, 0.0f, 0.0f);
   } else {
     const double a = C.u_hat[i] * C.bnd_measure / four_pi;
     const double b = C.dudn_hat[i] * C.bnd_measure / four_pi;
-    float4* o = (float4*)C.packed + 3 * i;
-    o[0] = make_float4(C.z[i], C.z[C.n + i], C.z[2 * C.n + i], (float)a);
-    o[1] = make_float4(C.nrm[i], C.nrm[C.n + i], C.nrm[2 * C.n + i], (float)b);
-    o[2] = make_float4((float)(3.0 * a), 0.0f, 0.0f, 0.0f);
+    const float zx = C.z[i], zy = C.z[C.n + i], zz = C.z[2 * C.n + i];
+    const float nx = C.nrm[i], ny = C.nrm[C.n + i], nz = C.nrm[2 * C.n + i];
+    const float fa = (float)a, fb = (float)b, a3 = (float)(3.0 * a);
+    o[0] = make_float4(zx, zx, zy, zy);
+    o[1] = make_float4(zz, zz, nx, nx);
+    o[2] = make_float4(ny, ny, nz, nz);
+    o[3] = make_float4(fa, fa, -fa, -fa);
+    o[4] = make_float4(a3, a3, fb, fb);
   }
 }
 
@@ -331,13 +410,17 @@ __global__ void __launch_bounds__(256) k_pack_src(const bvc_cache C) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= C.n_src_cand || j >= *C.n_src_dev) return;
   const double c = C.src_c[j];
-  float4* o = (float4*)C.src_packed + j;
+  float4* o = (float4*)C.src_packed + 2 * j;
   const int64_t M = C.n_src_cand;
+  const float yx = C.src_y[j], yy = C.src_y[M + j];
+  o[0] = make_float4(yx, yx, yy, yy);
   if (D == 2) {
     const double c1 = c / 6.283185307179586476925;
-    o[0] = make_float4(C.src_y[j], C.src_y[M + j], (float)c1, (float)(c1 * 0.34657359027997265471));
+    const float cl = (float)(c1 * 0.34657359027997265471), nc = (float)(-c1);
+    o[1] = make_float4(cl, cl, nc, nc);
   } else {
-    o[0] = make_float4(C.src_y[j], C.src_y[M + j], C.src_y[2 * M + j], (float)(c / 12.566370614359172953850));
+    const float yz = C.src_y[2 * M + j], nc = (float)(-c / 12.566370614359172953850);
+    o[1] = make_float4(yz, yz, nc, nc);
   }
 }
 
@@ -364,9 +447,10 @@ struct Plan {
   int64_t split_len;
 };
 
-static Plan plan_gather(int64_t m, int64_t n, const void* kern) {
+static Plan plan_gather(int64_t m, int64_t n, int kind, const void* kern) {
   Plan P;
-  P.pblocks = (int32_t)((m + kPtsPerCta - 1) / kPtsPerCta);
+  const int64_t per_cta = kind == 0 ? GatherShape<0>::kPtsPerCta : GatherShape<1>::kPtsPerCta;
+  P.pblocks = (int32_t)((m + per_cta - 1) / per_cta);
   const int64_t tiles = (n + kTile - 1) / kTile;
   const int64_t conc = (int64_t)num_sms() * max_blocks_per_sm(kern, kGBlock, 0);
   int64_t want = (4 * conc + P.pblocks - 1) / P.pblocks;
@@ -435,11 +519,11 @@ extern "C" bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const 
   const int planes = grad ? 1 + D : 1;
   size_t b = 0;
   if (cache->n > 0) {
-    const Plan P = plan_gather(state->m, cache->n, pick(D, 0, grad));
+    const Plan P = plan_gather(state->m, cache->n, 0, pick(D, 0, grad));
     b = part_bytes(P, planes, state->m);
   }
   if (cache->n_src_cand > 0) {
-    const Plan P = plan_gather(state->m, cache->n_src_cand, pick(D, 1, grad));
+    const Plan P = plan_gather(state->m, cache->n_src_cand, 1, pick(D, 1, grad));
     const size_t bs = part_bytes(P, planes, state->m);
     b = bs > b ? bs : b;
   }
@@ -450,7 +534,7 @@ extern "C" bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const 
 static bvc_status run_part(int D, int kind, bool grad, const float* x, int64_t m, const float4* samples, int64_t n,
                            const int64_t* n_dev, double* u, double* g, void* ws, size_t ws_bytes, cudaStream_t s) {
   const void* kern = pick(D, kind, grad);
-  const Plan P = plan_gather(m, n, kern);
+  const Plan P = plan_gather(m, n, kind, kern);
   const int planes = grad ? 1 + D : 1;
   GatherArgs A{};
   A.x = x;
