@@ -81,6 +81,17 @@ def max_over_ranks(x: float, device=None) -> float:
     return float(t.item())
 
 
+def step_value(points: int, steps: int, world: int, t_max: float) -> float:
+    """Whole-job interior points per second: every rank solves `points` per
+    step; the slowest rank's time counts."""
+    return points * steps * world / t_max
+
+
+def rank_seed(rank: int, k: int, base: int) -> int:
+    """Disjoint Philox seeds per rank and step (replicas are independent)."""
+    return base + 10_000 * rank + k
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -405,7 +416,7 @@ def main():
     cache_stats, near_stats = s.counting_pass(1)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     for k in range(args.warmup):
-        s.step(10_000 * rank + k)
+        s.step(rank_seed(rank, k, 0))
     torch.cuda.synchronize()
     s.geom.stats(reset=True)
 
@@ -418,7 +429,7 @@ def main():
         for k in range(args.steps):
             flush.zero_()
             evs[k][0].record()
-            s.step(1_000_000 + 10_000 * rank + k)
+            s.step(rank_seed(rank, k, 1_000_000))
             evs[k][1].record()
         prof = bvc.profile_end()
         torch.cuda.synchronize()
@@ -442,7 +453,7 @@ def main():
     for k in range(e2e_steps):
         s.far_pts.copy_(far_h, non_blocking=True)
         s.near_pts.copy_(near_h, non_blocking=True)
-        s.step(2_000_000 + 10_000 * rank + k)
+        s.step(rank_seed(rank, k, 2_000_000))
         u_far_h.copy_(s.u_far, non_blocking=True)
         g_far_h.copy_(s.g_far, non_blocking=True)
         u_near_h.copy_(s.u_near, non_blocking=True)
@@ -514,7 +525,7 @@ def main():
                          "prims_per_step": (cache_stats["prims"] + near_stats["prims"]) / max(steps_cache + steps_near, 1),
                          "ms_per_step_total": walk_ms_total}
 
-    value = M * K * ws / t_max
+    value = step_value(M, K, ws, t_max)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -529,7 +540,7 @@ def main():
         "kernels": kernels, "rooflines_all": extra,
         "wos_steps_per_s": (run_stats["steps"]) / max(walk_ms_total * K / 1e3, 1e-12),
         "pairs_per_s": (pairs_bnd + pairs_src) / ((gb_ms + gs_ms) / 1e3) if "gather_boundary" in prof else None,
-        "e2e": {"value": M * e2e_steps * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": step_value(M, e2e_steps, ws, t_e2e), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "gpu_launches": int(launches),
         "clocks": clocks,
