@@ -481,7 +481,8 @@ def main():
     dominant = max(prof.items(), key=lambda kv: kv[1][1])[0]
     gb_ms = prof.get("gather_boundary", (1, float("nan")))[1] / max(prof.get("gather_boundary", (1, 1))[0], 1)
     gs_ms = prof.get("gather_source", (1, 0.0))[1] / max(prof.get("gather_source", (1, 1))[0], 1)
-    walk_ms_total = prof.get("walk", (0, 0.0))[1] / K
+    # walk time per step includes the once-per-start first queries
+    walk_ms_total = (prof.get("walk", (0, 0.0))[1] + prof.get("first_hits", (0, 0.0))[1]) / K
     steps_cache = cache_stats["steps"]
     steps_near = near_stats["steps"]
     if dominant == "walk":

@@ -298,10 +298,9 @@ bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
  * The walk records live in a 16 MiB array of static device memory inside
  * this library (held on every GPU that loads the library until the process
  * exits); points are processed in chunks that fit it, so m is unbounded but
- * one point's records, walks * (1 + dim) * 4 bytes, must fit beside a
- * 256-byte counter: walks > 1,398,080 (2D) or 1,048,560 (3D) returns
- * BVC_ERR_WORKSPACE.  Arguments, results and state semantics are those of
- * wos_estimate.  The first call on each device looks up the array's device
+ * the scratch of one point (wos_estimate_workspace_size with m = 1) must
+ * fit: walks > 1,398,057 (2D) or 1,048,542 (3D) returns BVC_ERR_WORKSPACE.
+ * Arguments, results and state semantics are those of wos_estimate.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array: calls that overlap on the GPU
  * (on different streams, or from several threads) race on it and must be

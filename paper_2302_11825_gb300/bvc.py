@@ -275,7 +275,10 @@ def walk(geom: Geometry, g_terms, f_terms, starts, nrm, walks: int, eps: float, 
 
 
 def reduce_walks(rec: torch.Tensor, n: int, walks: int, mode: int = 0, out=None, stream=None):
+    _dev(rec, torch.float32)
     planes = rec.shape[0] - 1
+    if rec.dim() != 2 or rec.shape[1] != n * walks:
+        raise ValueError(f"records of shape {tuple(rec.shape)} do not hold {n} x {walks} walks")
     if out is None:
         out = torch.zeros((1 + planes, n), dtype=torch.float64, device="cuda")
     _check(lib().bvc_reduce_walks(_ptr(rec), n, int(walks), planes, int(mode), _ptr(out), _stream(stream)),

@@ -16,6 +16,8 @@
 // different tree paths, and no lane waits for the slowest query in its warp.
 // Per-walk results go to FP32 records; K3 reduces them in FP64 in a fixed
 // order, so results do not depend on scheduling.
+#include <cuda_fp16.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -24,6 +26,14 @@
 
 namespace bvc {
 
+// Resident blocks per SM the walk kernel is compiled for (2D: 56 registers,
+// 9 x 4 warps, measured best on GB300; 3D needs more registers).
+#ifndef BVC_WALK_MINB
+#define BVC_WALK_MINB(D) ((D) == 2 ? 9 : 7)
+#endif
+#ifndef BVC_WALK_POLICY
+#define BVC_WALK_POLICY 0
+#endif
 constexpr int kWalkBlock = 128;
 constexpr int kStack = 24;  // the BVH builder bounds the depth by 24
 constexpr int64_t kChunk = 128;
@@ -46,7 +56,31 @@ struct WalkParams {
   int32_t* steps;       // optional per-walk debug output
   int32_t* prim;
   unsigned long long* counter;
+  // First closest-point query of every start of this launch, shared by its
+  // walks (they all begin at the same point), or null: planes of
+  // (total / W) floats: d2, p - closest (D), element id bits.
+  const float* first;
 };
+
+// The first query of each start of a launch, once per start.
+template <int D>
+__global__ void __launch_bounds__(128) k_first_hits(DevGeometry G, const float* __restrict__ starts,
+                                                    int64_t pt_stride, int64_t i0, int64_t c, float* __restrict__ fh) {
+  __shared__ int snode[kStack * 128];
+  __shared__ float sdist[kStack * 128];
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < c; r += (int64_t)gridDim.x * blockDim.x) {
+    float p[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) p[a] = starts[a * pt_stride + i0 + r];
+    Hit<D> h;
+    TravCount tc{0, 0};
+    bvh_closest<D>(G, p, h, snode + threadIdx.x, sdist + threadIdx.x, 128, tc);
+    fh[r] = h.d2;
+#pragma unroll
+    for (int a = 0; a < D; ++a) fh[(1 + a) * c + r] = h.df[a];
+    fh[(1 + D) * c + r] = __int_as_float(h.id);
+  }
+}
 
 // Lane states of the walk kernel.
 constexpr int kIdle = 0;   // holds no walk
@@ -54,11 +88,14 @@ constexpr int kQuery = 1;  // inside a closest-point query (cur = node >= 0 or l
 constexpr int kStep = 2;   // query done: termination test, sphere sample, source term
 
 template <int D, bool HAS_F, bool GN, bool CNT>
-__global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
+__global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const WalkParams P) {
+  // Traversal stacks: node links and box distances, the latter in FP16
+  // rounded down (a smaller stored distance can only cost an extra visit,
+  // never prune a box that must be visited).
   __shared__ int snode[kStack * kWalkBlock];
-  __shared__ float sdist[kStack * kWalkBlock];
+  __shared__ __half sdist[kStack * kWalkBlock];
   int* const stk_node = snode + threadIdx.x;  // entry e at [e * kWalkBlock]
-  float* const stk_dist = sdist + threadIdx.x;
+  __half* const stk_dist = sdist + threadIdx.x;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const float kInf = __int_as_float(0x7f800000);
@@ -97,7 +134,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
   auto pop = [&]() {
     while (sp > 0) {
       --sp;
-      if (stk_dist[sp * kWalkBlock] <= thr) {
+      if (__half2float(stk_dist[sp * kWalkBlock]) <= thr) {
         cur = stk_node[sp * kWalkBlock];
         return;
       }
@@ -124,12 +161,23 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
       const int rank = __popc(need & ((1u << lane) - 1u));
       if (phase == kIdle && rank < avail) {
         t = q_next + rank;
-        i = P.i0 + t / P.W;
+        const int64_t r = t / P.W;
+        i = P.i0 + r;
 #pragma unroll
         for (int a = 0; a < D; ++a) x[a] = P.starts[a * P.pt_stride + i];
         k = 0;
         R0 = usrc = wf0 = wg0 = cv = 0.0f;
-        begin_query();
+        if (P.first) {
+          const int64_t c = P.total / P.W;
+          h.d2 = P.first[r];
+#pragma unroll
+          for (int a = 0; a < D; ++a) h.df[a] = P.first[(1 + a) * c + r];
+          h.id = __float_as_int(P.first[(1 + D) * c + r]);
+          h.q = -1;  // closest-point vector already final
+          phase = kStep;
+        } else {
+          begin_query();
+        }
       }
       q_next += avail;
       need = __ballot_sync(FULL, phase == kIdle);
@@ -141,7 +189,14 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
     const int nn = __popc(m_node), nl = __popc(m_leaf), ns = __popc(m_step);
     if (nn + nl + ns == 0) break;
     int choice;
-    if (ns > 0 && (2 * ns >= nn + nl + ns || nn + nl == 0))
+    bool take_step;
+    if (BVC_WALK_POLICY == 1)
+      take_step = ns >= nn && ns >= nl;
+    else if (BVC_WALK_POLICY == 2)
+      take_step = 3 * ns >= nn + nl + ns;
+    else
+      take_step = 2 * ns >= nn + nl + ns;
+    if (ns > 0 && (take_step || nn + nl == 0))
       choice = kStep;
     else
       choice = nl > nn ? 1 : 0;
@@ -180,7 +235,7 @@ __global__ void __launch_bounds__(kWalkBlock) k_walk(const WalkParams P) {
         const bool tl = dl <= thr, tr = dr <= thr;
         if (tl && tr) {
           stk_node[sp * kWalkBlock] = cr;
-          stk_dist[sp * kWalkBlock] = dr;
+          stk_dist[sp * kWalkBlock] = __float2half_rd(dr);
           ++sp;
           cur = cl;
         } else if (tl) {
@@ -355,6 +410,21 @@ static bvc_status launch_walk(int dim, bool has_f, bool gn, bool cnt, const Walk
   return BVC_OK;
 }
 
+static bvc_status launch_first_hits(int dim, const DevGeometry& G, const float* starts, int64_t pt_stride, int64_t i0,
+                                    int64_t c, float* fh, cudaStream_t s) {
+  int64_t blocks = (c + 127) / 128;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  ProfScope ps("first_hits", s);
+  if (dim == 2)
+    k_first_hits<2><<<(unsigned)blocks, 128, 0, s>>>(G, starts, pt_stride, i0, c, fh);
+  else
+    k_first_hits<3><<<(unsigned)blocks, 128, 0, s>>>(G, starts, pt_stride, i0, c, fh);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
 static bvc_status launch_reduce(const ReduceParams& R, cudaStream_t s) {
   const int64_t warps = R.n;
   int64_t blocks = (warps * 32 + 255) / 256;
@@ -420,18 +490,30 @@ extern "C" bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walk
   return launch_reduce(R, (cudaStream_t)stream);
 }
 
-// Workspace layout for the chunked drivers: [0, 256) work counter, then records.
+// Workspace layout for the chunked drivers: [0, 256) work counter, then the
+// first hits of the chunk's starts, then (256-byte aligned) the walk records.
 static constexpr size_t kWsHead = 256;
+static size_t ws_per_start(int dim, int32_t walks, int planes) {
+  return (size_t)walks * (1 + planes) * sizeof(float) + (size_t)(2 + dim) * sizeof(float);
+}
+static int64_t ws_chunk(size_t ws_bytes, size_t per_start) {
+  return ws_bytes < 2 * kWsHead + per_start ? 0 : (int64_t)((ws_bytes - 2 * kWsHead) / per_start);
+}
+static float* ws_first(void* ws) { return (float*)((char*)ws + kWsHead); }
+static float* ws_records(void* ws, int64_t c, int dim) {
+  const size_t off = kWsHead + (((size_t)c * (2 + dim) * sizeof(float) + kWsHead - 1) / kWsHead) * kWsHead;
+  return (float*)((char*)ws + off);
+}
 
 extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
                                                      size_t* full_bytes) {
   if (g == nullptr || opts == nullptr || opts->n_samples < 0 || opts->walks_per_sample < 1)
     return BVC_ERR_INVALID_ARG;
-  const size_t per_sample = (size_t)opts->walks_per_sample * 2 * sizeof(float);
+  const size_t per_sample = ws_per_start(g->dim, opts->walks_per_sample, 1);
   size_t src = 0;
   const int64_t ncand = (int64_t)opts->src_grid[0] * opts->src_grid[1];
   if (ncand > 0) bvc_sample_source_workspace_size(ncand, &src);
-  const size_t mn = kWsHead + per_sample, full = kWsHead + per_sample * (size_t)opts->n_samples;
+  const size_t mn = 2 * kWsHead + per_sample, full = 2 * kWsHead + per_sample * (size_t)opts->n_samples;
   if (min_bytes) *min_bytes = mn > src ? mn : src;
   if (full_bytes) *full_bytes = full > src ? full : src;
   return BVC_OK;
@@ -453,9 +535,9 @@ extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, c
   WalkParams P{};
   P.G = g->dev;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
-  const size_t per_sample = (size_t)W * 2 * sizeof(float);
-  if (workspace_bytes < kWsHead + per_sample) return BVC_ERR_WORKSPACE;
-  int64_t chunk = (int64_t)((workspace_bytes - kWsHead) / per_sample);
+  const size_t per_sample = ws_per_start(D, W, 1);
+  int64_t chunk = ws_chunk(workspace_bytes, per_sample);
+  if (chunk < 1) return BVC_ERR_WORKSPACE;
   if (chunk > N) chunk = N;
   cudaStream_t s = (cudaStream_t)stream;
   cache->bnd_measure = g->measure;
@@ -470,12 +552,16 @@ extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, c
   P.seed = opts->seed;
   P.tag = 0;
   P.counter = (unsigned long long*)workspace;
-  P.rec = (float*)((char*)workspace + kWsHead);
   for (int64_t i0 = 0; i0 < N; i0 += chunk) {
     const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
     P.i0 = i0;
     P.total = c * (int64_t)W;
     P.wid0 = opts->walk_id_base + (uint64_t)i0 * (uint64_t)W;
+    float* fh = ws_first(workspace);
+    P.rec = ws_records(workspace, c, D);
+    P.first = fh;
+    st = launch_first_hits(D, g->dev, P.starts, N, i0, c, fh, s);
+    if (st != BVC_OK) return st;
     st = launch_walk(D, P.f.n_terms > 0, true, g->counting != 0, P, s);
     if (st != BVC_OK) return st;
     ReduceParams R{};
@@ -500,9 +586,9 @@ extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, c
 extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
                                                   size_t* full_bytes) {
   if ((dim != 2 && dim != 3) || m < 0 || walks < 1) return BVC_ERR_INVALID_ARG;
-  const size_t per_pt = (size_t)walks * (1 + dim) * sizeof(float);
-  if (min_bytes) *min_bytes = kWsHead + per_pt;
-  if (full_bytes) *full_bytes = kWsHead + per_pt * (size_t)m;
+  const size_t per_pt = ws_per_start(dim, walks, dim);
+  if (min_bytes) *min_bytes = 2 * kWsHead + per_pt;
+  if (full_bytes) *full_bytes = 2 * kWsHead + per_pt * (size_t)m;
   return BVC_OK;
 }
 
@@ -524,9 +610,9 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (m > 0) {
-    const size_t per_pt = (size_t)walks * (1 + D) * sizeof(float);
-    if (workspace_bytes < kWsHead + per_pt) return BVC_ERR_WORKSPACE;
-    int64_t chunk = (int64_t)((workspace_bytes - kWsHead) / per_pt);
+    const size_t per_pt = ws_per_start(D, walks, D);
+    int64_t chunk = ws_chunk(workspace_bytes, per_pt);
+    if (chunk < 1) return BVC_ERR_WORKSPACE;
     if (chunk > m) chunk = m;
     P.starts = state->x;
     P.nrm = nullptr;
@@ -537,14 +623,18 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
     P.seed = seed;
     P.tag = 3;
     P.counter = (unsigned long long*)workspace;
-    P.rec = (float*)((char*)workspace + kWsHead);
     const bool grad = state->grad_bnd != nullptr;
     for (int64_t i0 = 0; i0 < m; i0 += chunk) {
       const int64_t c = (m - i0) < chunk ? (m - i0) : chunk;
       P.i0 = i0;
       P.total = c * (int64_t)walks;
       P.wid0 = id_base + (uint64_t)i0 * (uint64_t)walks;
-      bvc_status st = launch_walk(D, P.f.n_terms > 0, false, g->counting != 0, P, s);
+      float* fh = ws_first(workspace);
+      P.rec = ws_records(workspace, c, D);
+      P.first = fh;
+      bvc_status st = launch_first_hits(D, g->dev, P.starts, m, i0, c, fh, s);
+      if (st != BVC_OK) return st;
+      st = launch_walk(D, P.f.n_terms > 0, false, g->counting != 0, P, s);
       if (st != BVC_OK) return st;
       ReduceParams R{};
       R.rec = P.rec;
@@ -608,9 +698,10 @@ extern "C" bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_func
                                                   int32_t max_steps, uint64_t seed, uint64_t id_base,
                                                   bvc_stream stream) {
   if (g == nullptr || state == nullptr || walks < 1) return BVC_ERR_INVALID_ARG;
-  // the records of one point's walks must fit beside the counter
-  const size_t per_pt = (size_t)walks * (1 + g->dim) * sizeof(float);
-  if (kWsHead + per_pt > kStaticScratchBytes) return BVC_ERR_WORKSPACE;
+  // one point's first hit and walk records must fit beside the counter
+  size_t need = 0;
+  if (wos_estimate_workspace_size(g->dim, 1, walks, &need, nullptr) != BVC_OK) return BVC_ERR_INVALID_ARG;
+  if (need > kStaticScratchBytes) return BVC_ERR_WORKSPACE;
   void* scratch = nullptr;
   const bvc_status st = static_scratch_address(&scratch);
   if (st != BVC_OK) return st;

@@ -136,3 +136,25 @@ def test_cache_build_chunking_is_bit_identical():
     with pytest.raises(bvc.BvcError) as e:
         bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, w.n_samples), ws=bvc.workspace(mn - 64))
     assert e.value.status == bvc.ERR_WORKSPACE
+
+
+def test_shared_first_query_gives_identical_walks():
+    # The drivers query the closest point of each start once for all its walks;
+    # the raw walk kernel queries it per walk.  Both must give the same bits.
+    w = wl.star_poisson(n_samples=500, walks=24, grid=16, n_seg=4000)
+    geom = bvc.Geometry(w.V, w.F)
+    opts = bvc.cache_opts(w.n_samples, w.walks, w.offset_l, w.eps, seed=5)
+    cache = bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, w.n_samples))
+    rec, _, _ = bvc.walk(geom, w.g, w.f, cache.z, cache.nrm, w.walks, w.eps, 1 << 14, 5, 0, 0)
+    out = bvc.reduce_walks(rec, w.n_samples, w.walks, mode=0)
+    torch.cuda.synchronize()
+    assert torch.equal(out[0], cache.u_hat) and torch.equal(out[1], cache.dudn_hat)
+    pts = bvc.soa(w.eval_pts[:300])
+    m = pts.shape[1]
+    st = bvc.EvalState(pts)
+    bvc.wos_estimate(geom, w.g, w.f, st, 16, w.eps, 1 << 14, seed=6)
+    rec2, _, _ = bvc.walk(geom, w.g, w.f, pts, None, 16, w.eps, 1 << 14, 6, 0, bvc.TAG_POINTWISE)
+    assert rec2.shape == (3, m * 16)
+    sums = bvc.reduce_walks(rec2, m, 16, mode=1)
+    torch.cuda.synchronize()
+    assert torch.equal(sums[0], st.u_bnd) and torch.equal(sums[1:], st.grad_bnd)

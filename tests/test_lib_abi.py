@@ -96,7 +96,8 @@ def test_workspace_size_queries_are_host_only(lib):
     lib.wos_estimate_workspace_size.restype = C.c_int
     mn, full = C.c_size_t(), C.c_size_t()
     assert lib.wos_estimate_workspace_size(2, C.c_int64(1000), 64, C.byref(mn), C.byref(full)) == 0
-    assert full.value == 256 + 1000 * 64 * 3 * 4 and mn.value == 256 + 64 * 3 * 4
+    per_point = 64 * 3 * 4 + 4 * 4  # walk records + the shared first closest-point hit
+    assert full.value == 512 + 1000 * per_point and mn.value == 512 + per_point
     lib.bvc_sample_source_workspace_size.restype = C.c_int
     b = C.c_size_t()
     assert lib.bvc_sample_source_workspace_size(C.c_int64(65536), C.byref(b)) == 0 and b.value > 65536 * 8
