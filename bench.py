@@ -220,18 +220,26 @@ class Solver:
         self.g_far = torch.empty((w.dim, self.m_far), dtype=torch.float64, device=device)
         self.u_near = torch.empty(self.m_near, dtype=torch.float64, device=device)
         self.g_near = torch.empty((w.dim, self.m_near), dtype=torch.float64, device=device)
+        # the pointwise estimates near the boundary do not depend on the cache:
+        # they run on a second stream, overlapping the cache build and gather
+        self.side = torch.cuda.Stream(device=device)
 
     def step(self, seed: int):
-        bvc, w = self.bvc, self.w
+        bvc, w, torch = self.bvc, self.w, self.torch
+        main = torch.cuda.current_stream()
+        if self.m_near:
+            self.side.wait_stream(main)
+            with torch.cuda.stream(self.side):
+                bvc.eval_state_reset(self.near)
+                bvc.wos_estimate(self.geom, w.g, w.f, self.near, w.walks, w.eps, MAX_STEPS, seed, 0, self.ws_wos)
+                bvc.get_solution(self.near, self.u_near, self.g_near)
         bvc.eval_state_reset(self.far)
-        bvc.eval_state_reset(self.near)
         self.opts.seed = seed
         bvc.cache_build(self.geom, w.g, w.f, self.opts, self.cache, self.ws_cache)
         bvc.evaluate(self.cache, self.far, self.ws_eval)
         bvc.get_solution(self.far, self.u_far, self.g_far)
         if self.m_near:
-            bvc.wos_estimate(self.geom, w.g, w.f, self.near, w.walks, w.eps, MAX_STEPS, seed, 0, self.ws_wos)
-            bvc.get_solution(self.near, self.u_near, self.g_near)
+            main.wait_stream(self.side)
 
     def counting_pass(self, seed: int):
         """Deterministic walks: one counted pass gives the node fetches and

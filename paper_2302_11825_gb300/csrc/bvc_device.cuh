@@ -259,7 +259,7 @@ template <int D, bool CNT>
 __device__ __forceinline__ void test_leaf(const DevGeometry& G, int32_t enc, const float* p, Hit<D>& h, float& thr,
                                           TravCount& tc) {
   const int32_t e = ~enc;
-  const int32_t first = e >> 3, count = e & 7;
+  const int32_t first = e >> 4, count = e & 15;
   if (CNT) tc.prims += (uint32_t)count;
   for (int32_t q = first; q < first + count; ++q) {
     if (D == 2) {

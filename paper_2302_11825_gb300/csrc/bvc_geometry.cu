@@ -138,7 +138,7 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   *out = nullptr;
   if ((dim != 2 && dim != 3) || verts == nullptr || prims == nullptr || n_verts <= 0 || n_prims <= 0)
     return BVC_ERR_INVALID_ARG;
-  if (n_prims >= (int64_t(1) << 28) || n_verts >= (int64_t(1) << 31)) return BVC_ERR_INVALID_ARG;
+  if (n_prims >= (int64_t(1) << 27) || n_verts >= (int64_t(1) << 31)) return BVC_ERR_INVALID_ARG;
   for (int64_t i = 0; i < n_verts * dim; ++i)
     if (!std::isfinite(verts[i])) return BVC_ERR_DEGENERATE_MESH;
   for (int64_t i = 0; i < n_prims * dim; ++i)

@@ -27,7 +27,7 @@ struct DevFunction {
 // Device view of the geometry, passed by value to kernels.
 //  nodes: 2D 3 float4 per node  [L.lo.x L.lo.y L.hi.x L.hi.y] [R ...] [cl cr - -]
 //         3D 4 float4 per node  [L.lo.xyz L.hi.x] [L.hi.yz R.lo.xy] [R.lo.z R.hi.xyz] [cl cr - -]
-//         child >= 0: internal node; child < 0: leaf, ~child = first << 3 | count.
+//         child >= 0: internal node; child < 0: leaf, ~child = first << 4 | count.
 //  prims: BVH order; 2D two float4 (a, ab) (1/|ab|^2, id, -, -); 3D three
 //         float4 (a, id) (ab, -) (ac, -); id = caller's element index (int bits).
 struct DevGeometry {
