@@ -289,6 +289,49 @@ bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_funct
  * out).  Synchronises the device; reset != 0 clears it. */
 bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
 
+/* ---------------------------------------------- many right-hand sides */
+/* Batching of right-hand sides for the Laplace equation (f = 0): K
+ * Dirichlet data g_k = sum_m C[k][m] phi_m over the BVC_FN_POLY monomials
+ * phi_m (total degree <= 4; bvc_poly_terms(dim) = 15 in 2D, 35 in 3D).
+ * Without a source term a walk's path does not depend on g and each walk's
+ * U and n.grad (Sec. 3.1, Eq. 7) are linear in g, so one set of walks per
+ * cache serves every right-hand side: the walks record their end points,
+ * per-sample moments of the monomials are reduced once (FP64), and each
+ * right-hand side's u^ and du/dn^ are projections of the moments -- the
+ * estimates the single-RHS path gives for g_k, up to rounding.  The gather
+ * then evaluates Eq. 3 for all right-hand sides at once.  All arrays are
+ * caller-owned device memory. */
+#define BVC_MULTI_GROUP 32 /* right-hand sides per gather pass */
+typedef struct {
+  int32_t dim;
+  int64_t n;           /* boundary samples */
+  int32_t k;           /* right-hand sides */
+  float* z;            /* [dim][n] */
+  float* nrm;          /* [dim][n] */
+  double* mom_u;       /* [n][bvc_poly_terms(dim)] means of phi_m at walk ends */
+  double* mom_q;       /* [n][bvc_poly_terms(dim)] means of s (phi_m(end) - phi_m(p0)) */
+  double* u_hat;       /* [k][n] */
+  double* dudn_hat;    /* [k][n] */
+  float* packed;       /* [ceil(k/32)][n][8 + 64] gather tiles */
+  double bnd_measure;  /* |dOmega|, set by the build */
+} bvc_multi_cache;
+
+int32_t bvc_poly_terms(int32_t dim);
+bvc_status bvc_multi_cache_build_workspace_size(bvc_geometry g, int64_t n, int32_t walks, size_t* min_bytes,
+                                                size_t* full_bytes);
+/* K1 boundary samples, end-point walks (tag 0, ids as bvc_cache_build),
+ * moments and the projection onto coeffs (device double[k][terms]).
+ * opts->src_grid must be {0, 0} (BVC_ERR_UNSUPPORTED otherwise). */
+bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs, const bvc_cache_opts* opts,
+                                 bvc_multi_cache* cache, void* workspace, size_t workspace_bytes, bvc_stream stream);
+/* Re-project the stored moments onto new coefficients (no walks). */
+bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_cache* cache, bvc_stream stream);
+/* Eq. 3 for every right-hand side at m points: u[k][x] = (1/n) sum_i
+ * (dG/dn(x, z_i) u^_ik - G(x, z_i) du/dn^_ik) / p  (overwritten; u only).
+ * pts: device [dim][m]; u: device double[k][m]. */
+bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
+                              bvc_stream stream);
+
 /* wos_estimate with no caller workspace and no allocation.  The paper has
  * no counterpart: this is an interface for callers that must not allocate
  * device memory -- for example code that runs inside another framework

@@ -62,6 +62,12 @@ class CacheOpts(C.Structure):
                 ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 2)]
 
 
+class MultiCacheStruct(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("k", C.c_int32), ("z", C.c_void_p), ("nrm", C.c_void_p),
+                ("mom_u", C.c_void_p), ("mom_q", C.c_void_p), ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p),
+                ("packed", C.c_void_p), ("bnd_measure", C.c_double)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -104,6 +110,11 @@ def _declare(lib):
         "wos_estimate_static_scratch": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct),
                                             i32, f32, i32, u64, u64, P]),
         "bvc_geometry_set_counting": (S, [P, i32]),
+        "bvc_poly_terms": (i32, [i32]),
+        "bvc_multi_cache_build_workspace_size": (S, [P, i64, i32, C.POINTER(sz), C.POINTER(sz)]),
+        "bvc_multi_cache_build": (S, [P, P, C.POINTER(CacheOpts), C.POINTER(MultiCacheStruct), P, sz, P]),
+        "bvc_multi_cache_project": (S, [P, C.POINTER(MultiCacheStruct), P]),
+        "bvc_evaluate_multi": (S, [C.POINTER(MultiCacheStruct), P, i64, P, P]),
         "bvc_profile_begin": (S, []),
         "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
         "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
@@ -452,6 +463,75 @@ def wos_estimate_static_scratch(geom: Geometry, g_terms, f_terms, state: EvalSta
                                              float(eps), int(max_steps), int(seed), int(id_base), _stream(stream)),
            "wos_estimate_static_scratch")
     return state
+
+
+# ---------------------------------------------------------------- many right-hand sides
+MULTI_GROUP = 32
+
+
+def poly_terms(dim: int) -> int:
+    return int(lib().bvc_poly_terms(dim))
+
+
+class MultiCache:
+    """Caller-owned device buffers of a bvc_multi_cache (k right-hand sides)."""
+
+    def __init__(self, dim: int, n: int, k: int, device="cuda"):
+        self.dim, self.n, self.k = dim, n, k
+        t = poly_terms(dim)
+        groups = (k + MULTI_GROUP - 1) // MULTI_GROUP
+        self.z = torch.zeros((dim, n), dtype=torch.float32, device=device)
+        self.nrm = torch.zeros((dim, n), dtype=torch.float32, device=device)
+        self.mom_u = torch.zeros((n, t), dtype=torch.float64, device=device)
+        self.mom_q = torch.zeros((n, t), dtype=torch.float64, device=device)
+        self.u_hat = torch.zeros((k, n), dtype=torch.float64, device=device)
+        self.dudn_hat = torch.zeros((k, n), dtype=torch.float64, device=device)
+        self.packed = torch.zeros((groups, n, 8 + 2 * MULTI_GROUP), dtype=torch.float32, device=device)
+        st = MultiCacheStruct()
+        st.dim, st.n, st.k = dim, n, k
+        st.z, st.nrm, st.mom_u, st.mom_q = _ptr(self.z), _ptr(self.nrm), _ptr(self.mom_u), _ptr(self.mom_q)
+        st.u_hat, st.dudn_hat, st.packed = _ptr(self.u_hat), _ptr(self.dudn_hat), _ptr(self.packed)
+        st.bnd_measure = 0.0
+        self.struct = st
+
+
+def multi_cache_build_workspace_size(geom: Geometry, n: int, walks: int):
+    mn, full = C.c_size_t(), C.c_size_t()
+    _check(lib().bvc_multi_cache_build_workspace_size(geom.h, n, walks, C.byref(mn), C.byref(full)),
+           "bvc_multi_cache_build_workspace_size")
+    return int(mn.value), int(full.value)
+
+
+def multi_cache_build(geom: Geometry, coeffs: torch.Tensor, opts: CacheOpts, cache: MultiCache,
+                      ws: torch.Tensor = None, stream=None):
+    """coeffs: CUDA float64 [k][poly_terms(dim)] monomial coefficients of each g_k."""
+    _dev(coeffs, torch.float64)
+    if tuple(coeffs.shape) != (cache.k, poly_terms(cache.dim)):
+        raise ValueError("coefficients must be [k][poly_terms(dim)]")
+    if ws is None:
+        ws = workspace(multi_cache_build_workspace_size(geom, cache.n, opts.walks_per_sample)[1])
+    _check(lib().bvc_multi_cache_build(geom.h, _ptr(coeffs), C.byref(opts), C.byref(cache.struct), _ptr(ws),
+                                       ws.numel(), _stream(stream)), "bvc_multi_cache_build")
+    return cache
+
+
+def multi_cache_project(coeffs: torch.Tensor, cache: MultiCache, stream=None):
+    _dev(coeffs, torch.float64)
+    if tuple(coeffs.shape) != (cache.k, poly_terms(cache.dim)):
+        raise ValueError("coefficients must be [k][poly_terms(dim)]")
+    _check(lib().bvc_multi_cache_project(_ptr(coeffs), C.byref(cache.struct), _stream(stream)),
+           "bvc_multi_cache_project")
+
+
+def evaluate_multi(cache: MultiCache, pts: torch.Tensor, u: torch.Tensor = None, stream=None):
+    """u[k][x] for every right-hand side (Eq. 3, boundary term only)."""
+    _dev(pts, torch.float32)
+    m = pts.shape[1]
+    if u is None:
+        u = torch.empty((cache.k, m), dtype=torch.float64, device=pts.device)
+    _check(lib().bvc_evaluate_multi(C.byref(cache.struct), _ptr(pts), m, _ptr(u), _stream(stream)),
+           "bvc_evaluate_multi")
+    return u
 
 
 def profile_begin():

@@ -645,3 +645,127 @@ extern "C" bvc_status bvc_gather_status(uint64_t* flags, int32_t reset) {
   *flags = h;
   return (h & 1ull) ? BVC_ERR_TIMEOUT : BVC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Eq. 3 for many right-hand sides: per pair the two kernel values
+// (2D: (n.d)/r^2 and lg2 r^2; 3D: (n.d)/r^3 and 1/r) are computed once and
+// applied to the BVC_MULTI_GROUP coefficient pairs of the tile's samples.
+// One thread per evaluation point, 32 FP32 partial sums flushed to FP64
+// every tile of 32 samples; tiles staged by bulk asynchronous copies.
+namespace bvc {
+
+constexpr int kMG = BVC_MULTI_GROUP;
+constexpr int kMTile = 32;
+constexpr int kMStride = 8 + 2 * kMG;  // floats per packed sample row
+
+template <int D>
+__global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict__ x, int64_t m,
+                                                         const float* __restrict__ packed, int64_t n, int32_t K,
+                                                         double* __restrict__ u) {
+  __shared__ __align__(128) float tile[2][kMTile * kMStride];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int g = blockIdx.y;
+  const float* base = packed + (int64_t)g * n * kMStride;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float pc[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pc[a] = (a < D && p < m) ? x[a * m + p] : 1.0e4f + (float)a;
+  float acc[kMG];
+  double acc64[kMG];
+#pragma unroll
+  for (int q = 0; q < kMG; ++q) acc64[q] = 0.0;
+  const int64_t nt = (n + kMTile - 1) / kMTile;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2 && b < nt; ++b) {
+      const int64_t st = (int64_t)b * kMTile;
+      const uint32_t bytes = (uint32_t)min64(kMTile, n - st) * kMStride * 4u;
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_g2s(&tile[b][0], base + st * kMStride, bytes, &bar[b]);
+    }
+  }
+  for (int64_t it = 0; it < nt; ++it) {
+    const int b = (int)(it & 1);
+    const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&g_gather_status, 1ull);
+        for (int64_t k2 = it; k2 < it + 2 && k2 < nt; ++k2)
+          (void)mbar_wait_bounded(&bar[k2 & 1], (uint32_t)((k2 >> 1) & 1));
+      }
+      return;
+    }
+    const int cnt = (int)min64(kMTile, n - it * kMTile);
+#pragma unroll
+    for (int q = 0; q < kMG; ++q) acc[q] = 0.0f;
+    const float4* T = reinterpret_cast<const float4*>(tile[b]);
+    for (int s = 0; s < cnt; ++s) {
+      const float4* row = T + s * (kMStride / 4);
+      const float4 zz = row[0], nn = row[1];
+      const float dx = zz.x - pc[0], dy = zz.y - pc[1], dz = zz.z - pc[2];
+      float k1, k2;
+      if (D == 2) {
+        const float r2 = fmaf(dy, dy, dx * dx);
+        const float inv = rcp_approx(r2);
+        k1 = fmaf(nn.y, dy, nn.x * dx) * inv;
+        k2 = lg2_approx(r2);
+      } else {
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float ir = rsqrt_approx(r2);
+        k1 = fmaf(nn.z, dz, fmaf(nn.y, dy, nn.x * dx)) * (ir * ir * ir);
+        k2 = ir;
+      }
+#pragma unroll
+      for (int q = 0; q < kMG / 4; ++q) {
+        const float4 a4 = row[2 + q], b4 = row[2 + kMG / 4 + q];
+        acc[4 * q + 0] = fmaf(b4.x, k2, fmaf(a4.x, k1, acc[4 * q + 0]));
+        acc[4 * q + 1] = fmaf(b4.y, k2, fmaf(a4.y, k1, acc[4 * q + 1]));
+        acc[4 * q + 2] = fmaf(b4.z, k2, fmaf(a4.z, k1, acc[4 * q + 2]));
+        acc[4 * q + 3] = fmaf(b4.w, k2, fmaf(a4.w, k1, acc[4 * q + 3]));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kMG; ++q) acc64[q] += (double)acc[q];
+    __syncthreads();
+    if (threadIdx.x == 0 && it + 2 < nt) {
+      fence_proxy_async();
+      const int64_t st = (it + 2) * kMTile;
+      const uint32_t bytes = (uint32_t)min64(kMTile, n - st) * kMStride * 4u;
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_g2s(&tile[b][0], base + st * kMStride, bytes, &bar[b]);
+    }
+  }
+  if (p < m) {
+    const int kk = (K - g * kMG) < kMG ? (K - g * kMG) : kMG;
+    const double inv_n = 1.0 / (double)n;
+#pragma unroll
+    for (int q = 0; q < kMG; ++q)
+      if (q < kk) u[(int64_t)(g * kMG + q) * m + p] = acc64[q] * inv_n;
+  }
+}
+
+}  // namespace bvc
+
+extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
+                                         bvc_stream stream) {
+  if (cache == nullptr || (cache->dim != 2 && cache->dim != 3) || cache->n < 1 || cache->k < 1 ||
+      cache->packed == nullptr || m < 0 || (m > 0 && (pts == nullptr || u == nullptr)))
+    return BVC_ERR_INVALID_ARG;
+  const int groups = (cache->k + kMG - 1) / kMG;
+  if (groups > 65535) return BVC_ERR_INVALID_ARG;  // grid.y limit
+  if (m == 0) return BVC_OK;
+  const dim3 grid((unsigned)((m + 255) / 256), (unsigned)groups);
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps("gather_multi", s);
+  if (cache->dim == 2)
+    k_gather_multi<2><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u);
+  else
+    k_gather_multi<3><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}

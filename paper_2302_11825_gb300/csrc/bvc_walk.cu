@@ -87,7 +87,16 @@ constexpr int kIdle = 0;   // holds no walk
 constexpr int kQuery = 1;  // inside a closest-point query (cur = node >= 0 or leaf < 0)
 constexpr int kStep = 2;   // query done: termination test, sphere sample, source term
 
-template <int D, bool HAS_F, bool GN, bool CNT>
+// Record kinds: per walk t, with `total` walks in the launch,
+//   kRecGn   rec[t] = U, rec[total + t] = n . grad            (cache walks)
+//   kRecGrad rec[t] = U, rec[(1 + a) total + t] = grad_a      (pointwise walks)
+//   kRecEnd  rec[a total + t] = closest point at the end (a < D),
+//            rec[D total + t] = (D / R0)(n . w0) (0 if the walk stopped at
+//            its start); for f = 0 a walk's path does not depend on g, and
+//            U = g(end), n . grad = rec[D] (g(end) - g(closest point of start)).
+constexpr int kRecGn = 0, kRecGrad = 1, kRecEnd = 2;
+
+template <int D, bool HAS_F, int REC, bool CNT>
 __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const WalkParams P) {
   // Traversal stacks: node links and box distances, the latter in FP16
   // rounded down (a smaller stored distance can only cost an extra visit,
@@ -263,19 +272,28 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
 #pragma unroll
         for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
         const float d = sqrtf(h.d2);
-        if (k == 1) cv = eval_fn<D, true>(P.g, pbar);
+        if (REC != kRecEnd && k == 1) cv = eval_fn<D, true>(P.g, pbar);
         if (d < P.eps || k >= P.max_steps) {
-          const float U = (k == 1 ? cv : eval_fn<D, true>(P.g, pbar)) + usrc;
-          const float sc = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
-          P.rec[t] = U;
-          if (GN) {
+          if (REC == kRecEnd) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) P.rec[a * P.total + t] = pbar[a];
             float nn2 = 0.0f;
 #pragma unroll
             for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn2);
-            P.rec[P.total + t] = sc * nn2;
+            P.rec[D * P.total + t] = k > 1 ? ((float)D / R0) * nn2 : 0.0f;
           } else {
+            const float U = (k == 1 ? cv : eval_fn<D, true>(P.g, pbar)) + usrc;
+            const float sc = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
+            P.rec[t] = U;
+            if (REC == kRecGn) {
+              float nn2 = 0.0f;
 #pragma unroll
-            for (int a = 0; a < D; ++a) P.rec[(1 + a) * P.total + t] = sc * nu[a];
+              for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn2);
+              P.rec[P.total + t] = sc * nn2;
+            } else {
+#pragma unroll
+              for (int a = 0; a < D; ++a) P.rec[(1 + a) * P.total + t] = sc * nu[a];
+            }
           }
           if (P.steps) P.steps[t] = k;
           if (P.prim) P.prim[t] = h.id;
@@ -383,22 +401,25 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceParams R) {
   }
 }
 
-template <int D, bool HAS_F, bool GN>
+template <int D, bool HAS_F, int REC>
 static const void* walk_kernel(bool cnt) {
-  return cnt ? (const void*)k_walk<D, HAS_F, GN, true> : (const void*)k_walk<D, HAS_F, GN, false>;
+  return cnt ? (const void*)k_walk<D, HAS_F, REC, true> : (const void*)k_walk<D, HAS_F, REC, false>;
 }
 
-static const void* pick_walk(int dim, bool has_f, bool gn, bool cnt) {
+// rec: kRecGn / kRecGrad / kRecEnd (the last only without a source term).
+static const void* pick_walk(int dim, bool has_f, int rec, bool cnt) {
+  if (rec == kRecEnd) return dim == 2 ? walk_kernel<2, false, kRecEnd>(cnt) : walk_kernel<3, false, kRecEnd>(cnt);
+  const bool gn = rec == kRecGn;
   if (dim == 2) {
-    if (has_f) return gn ? walk_kernel<2, true, true>(cnt) : walk_kernel<2, true, false>(cnt);
-    return gn ? walk_kernel<2, false, true>(cnt) : walk_kernel<2, false, false>(cnt);
+    if (has_f) return gn ? walk_kernel<2, true, kRecGn>(cnt) : walk_kernel<2, true, kRecGrad>(cnt);
+    return gn ? walk_kernel<2, false, kRecGn>(cnt) : walk_kernel<2, false, kRecGrad>(cnt);
   }
-  if (has_f) return gn ? walk_kernel<3, true, true>(cnt) : walk_kernel<3, true, false>(cnt);
-  return gn ? walk_kernel<3, false, true>(cnt) : walk_kernel<3, false, false>(cnt);
+  if (has_f) return gn ? walk_kernel<3, true, kRecGn>(cnt) : walk_kernel<3, true, kRecGrad>(cnt);
+  return gn ? walk_kernel<3, false, kRecGn>(cnt) : walk_kernel<3, false, kRecGrad>(cnt);
 }
 
-static bvc_status launch_walk(int dim, bool has_f, bool gn, bool cnt, const WalkParams& P, cudaStream_t s) {
-  const void* kern = pick_walk(dim, has_f, gn, cnt);
+static bvc_status launch_walk(int dim, bool has_f, int rec, bool cnt, const WalkParams& P, cudaStream_t s) {
+  const void* kern = pick_walk(dim, has_f, rec, cnt);
   const int64_t want = (P.total + 31) / 32;
   int grid = num_sms() * max_blocks_per_sm(kern, kWalkBlock, 0);
   const int64_t need_blocks = (want + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
@@ -471,7 +492,8 @@ extern "C" bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bv
   P.prim = prim;
   // the work counter lives in the status block's spare word
   P.counter = g->dev.stats + 3;
-  return launch_walk(g->dim, P.f.n_terms > 0, nrm != nullptr, g->counting != 0, P, (cudaStream_t)stream);
+  return launch_walk(g->dim, P.f.n_terms > 0, nrm != nullptr ? kRecGn : kRecGrad, g->counting != 0, P,
+                     (cudaStream_t)stream);
 }
 
 extern "C" bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walks, int32_t planes, int32_t mode,
@@ -562,7 +584,7 @@ extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, c
     P.first = fh;
     st = launch_first_hits(D, g->dev, P.starts, N, i0, c, fh, s);
     if (st != BVC_OK) return st;
-    st = launch_walk(D, P.f.n_terms > 0, true, g->counting != 0, P, s);
+    st = launch_walk(D, P.f.n_terms > 0, kRecGn, g->counting != 0, P, s);
     if (st != BVC_OK) return st;
     ReduceParams R{};
     R.rec = P.rec;
@@ -634,7 +656,7 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
       P.first = fh;
       bvc_status st = launch_first_hits(D, g->dev, P.starts, m, i0, c, fh, s);
       if (st != BVC_OK) return st;
-      st = launch_walk(D, P.f.n_terms > 0, false, g->counting != 0, P, s);
+      st = launch_walk(D, P.f.n_terms > 0, kRecGrad, g->counting != 0, P, s);
       if (st != BVC_OK) return st;
       ReduceParams R{};
       R.rec = P.rec;
@@ -656,6 +678,280 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
   }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Many right-hand sides (Laplace, f = 0).  With no source term a walk's path
+// does not depend on g, so the walks of a cache are run once, recording
+// their end points, and every right-hand side g_k = sum_m C[k][m] phi_m
+// (phi_m the POLY monomials) is recovered from per-sample moments:
+//   mom_u[i][m] = mean_j phi_m(end_ij)
+//   mom_q[i][m] = mean_j s_ij (phi_m(end_ij) - phi_m(p0_i))
+// where p0_i is the closest point of sample i and s_ij = (d/R0)(n . w0);
+// then u^_ik = sum_m C[k][m] mom_u[i][m] and du/dn^_ik likewise -- the same
+// estimates the single-RHS walks give, by linearity (each walk's U and
+// n.grad are linear in g).
+namespace bvc {
+
+template <int D>
+struct Mono {
+  static constexpr int kN = D == 2 ? 15 : 35;
+};
+
+// Exponents of monomial m in the POLY order (degree t, then x power
+// descending, then y power descending).
+template <int D>
+__host__ __device__ constexpr void mono_exp(int m, int& i, int& j, int& k) {
+  int idx = 0;
+  for (int t = 0; t <= 4; ++t)
+    for (int a = t; a >= 0; --a) {
+      if (D == 2) {
+        if (idx == m) {
+          i = a;
+          j = t - a;
+          k = 0;
+          return;
+        }
+        ++idx;
+      } else {
+        for (int b = t - a; b >= 0; --b) {
+          if (idx == m) {
+            i = a;
+            j = b;
+            k = t - a - b;
+            return;
+          }
+          ++idx;
+        }
+      }
+    }
+  i = j = k = 0;
+}
+
+template <int D>
+__device__ __forceinline__ void powers(const float* p, float (&xp)[5], float (&yp)[5], float (&zp)[5]) {
+  xp[0] = yp[0] = zp[0] = 1.0f;
+#pragma unroll
+  for (int e = 1; e < 5; ++e) {
+    xp[e] = xp[e - 1] * p[0];
+    yp[e] = yp[e - 1] * p[1];
+    zp[e] = D == 3 ? zp[e - 1] * p[D - 1] : 0.0f;
+  }
+}
+
+template <int D, int M>
+__device__ __forceinline__ float mono(const float (&xp)[5], const float (&yp)[5], const float (&zp)[5]) {
+  constexpr int i = []() { int a = 0, b = 0, c = 0; mono_exp<D>(M, a, b, c); return a; }();
+  constexpr int j = []() { int a = 0, b = 0, c = 0; mono_exp<D>(M, a, b, c); return b; }();
+  constexpr int k = []() { int a = 0, b = 0, c = 0; mono_exp<D>(M, a, b, c); return c; }();
+  return D == 2 ? xp[i] * yp[j] : xp[i] * yp[j] * zp[k];
+}
+
+template <int D, int M, int NM>
+struct MonoLoop {
+  __device__ __forceinline__ static void acc(const float (&xp)[5], const float (&yp)[5], const float (&zp)[5],
+                                             const float (&x0)[5], const float (&y0)[5], const float (&z0)[5],
+                                             float sj, float* au, float* aq) {
+    const float ph = mono<D, M>(xp, yp, zp);
+    au[M] += ph;
+    aq[M] = fmaf(sj, ph - mono<D, M>(x0, y0, z0), aq[M]);
+    MonoLoop<D, M + 1, NM>::acc(xp, yp, zp, x0, y0, z0, sj, au, aq);
+  }
+};
+template <int D, int NM>
+struct MonoLoop<D, NM, NM> {
+  __device__ __forceinline__ static void acc(const float (&)[5], const float (&)[5], const float (&)[5],
+                                             const float (&)[5], const float (&)[5], const float (&)[5], float,
+                                             float*, float*) {}
+};
+
+// One warp per sample: FP32 partials per lane over its walks, FP64
+// fixed-order warp sums.
+template <int D>
+__global__ void __launch_bounds__(256) k_moments(const float* __restrict__ rec, int64_t c, int32_t W,
+                                                 const float* __restrict__ starts, int64_t pt_stride, int64_t i0,
+                                                 const float* __restrict__ fh, double* __restrict__ mom_u,
+                                                 double* __restrict__ mom_q) {
+  constexpr int NM = Mono<D>::kN;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = c * (int64_t)W;
+  for (int64_t r = warp; r < c; r += nwarps) {
+    float p0[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) p0[a] = starts[a * pt_stride + i0 + r] - fh[(1 + a) * c + r];
+    float x0[5], y0[5], z0[5];
+    powers<D>(p0, x0, y0, z0);
+    float au[NM], aq[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) au[m] = aq[m] = 0.0f;
+    for (int j = lane; j < W; j += 32) {
+      const int64_t t = r * W + j;
+      float pe[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) pe[a] = rec[a * total + t];
+      const float sj = rec[D * total + t];
+      float xp[5], yp[5], zp[5];
+      powers<D>(pe, xp, yp, zp);
+      MonoLoop<D, 0, NM>::acc(xp, yp, zp, x0, y0, z0, sj, au, aq);
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      double su = (double)au[m], sq = (double)aq[m];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      }
+      if (lane == 0) {
+        mom_u[(i0 + r) * NM + m] = su / (double)W;
+        mom_q[(i0 + r) * NM + m] = sq / (double)W;
+      }
+    }
+  }
+}
+
+// Per sample: u^_k, du/dn^_k for every right-hand side (FP64) and the
+// gather tiles, grouped by BVC_MULTI_GROUP right-hand sides:
+// [group][sample][8 + 2 G] floats = z (4), n (4), a_k (G), b_k (G) with
+//   2D  a = u^ |dOmega|/(2 pi),  b = -du/dn^ |dOmega|/(2 pi) ln2/2   (u += a (n.d)/r^2 + b lg2 r^2)
+//   3D  a = u^ |dOmega|/(4 pi),  b = du/dn^ |dOmega|/(4 pi)          (u += a (n.d)/r^3 + b/r)
+template <int D>
+__global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, int32_t K, int64_t n,
+                                                 const double* __restrict__ mom_u, const double* __restrict__ mom_q,
+                                                 const float* __restrict__ z, const float* __restrict__ nrm,
+                                                 double meas, double* __restrict__ u_hat,
+                                                 double* __restrict__ q_hat, float* __restrict__ packed) {
+  constexpr int NM = Mono<D>::kN;
+  constexpr int G = BVC_MULTI_GROUP;
+  constexpr int S = 8 + 2 * G;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double mu[NM], mq[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    mu[m] = mom_u[i * NM + m];
+    mq[m] = mom_q[i * NM + m];
+  }
+  const int groups = (K + G - 1) / G;
+  const double ca = D == 2 ? meas / 6.283185307179586476925 : meas / 12.566370614359172953850;
+  const double cb = D == 2 ? -ca * 0.34657359027997265471 : ca;
+  for (int g = 0; g < groups; ++g) {
+    float* row = packed + ((int64_t)g * n + i) * S;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      row[a] = a < D ? z[a * n + i] : 0.0f;
+      row[4 + a] = a < D ? nrm[a * n + i] : 0.0f;
+    }
+    for (int s = 0; s < G; ++s) {
+      const int k = g * G + s;
+      double u = 0.0, q = 0.0;
+      if (k < K) {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          u = fma(C[k * NM + m], mu[m], u);
+          q = fma(C[k * NM + m], mq[m], q);
+        }
+        u_hat[(int64_t)k * n + i] = u;
+        q_hat[(int64_t)k * n + i] = q;
+      }
+      row[8 + s] = (float)(u * ca);
+      row[8 + G + s] = (float)(q * cb);
+    }
+  }
+}
+
+}  // namespace bvc
+
+static bool valid_multi(const bvc_multi_cache* c, int dim) {
+  return c != nullptr && c->dim == dim && c->n >= 1 && c->k >= 1 && c->z && c->nrm && c->mom_u && c->mom_q &&
+         c->u_hat && c->dudn_hat && c->packed;
+}
+
+static bvc_status launch_project(const double* coeffs, bvc_multi_cache* c, cudaStream_t s) {
+  const unsigned grid = (unsigned)((c->n + 127) / 128);
+  ProfScope ps("multi_project", s);
+  if (c->dim == 2)
+    k_project<2><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->bnd_measure, c->u_hat,
+                                      c->dudn_hat, c->packed);
+  else
+    k_project<3><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->bnd_measure, c->u_hat,
+                                      c->dudn_hat, c->packed);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+extern "C" int32_t bvc_poly_terms(int32_t dim) { return dim == 2 ? 15 : (dim == 3 ? 35 : 0); }
+
+extern "C" bvc_status bvc_multi_cache_build_workspace_size(bvc_geometry g, int64_t n, int32_t walks,
+                                                           size_t* min_bytes, size_t* full_bytes) {
+  if (g == nullptr || n < 1 || walks < 1) return BVC_ERR_INVALID_ARG;
+  const size_t per = ws_per_start(g->dim, walks, g->dim);
+  if (min_bytes) *min_bytes = 2 * kWsHead + per;
+  if (full_bytes) *full_bytes = 2 * kWsHead + per * (size_t)n;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs, const bvc_cache_opts* opts,
+                                            bvc_multi_cache* cache, void* workspace, size_t workspace_bytes,
+                                            bvc_stream stream) {
+  if (g == nullptr || opts == nullptr || coeffs == nullptr || workspace == nullptr) return BVC_ERR_INVALID_ARG;
+  const int D = g->dim;
+  const int64_t N = opts->n_samples;
+  const int32_t W = opts->walks_per_sample;
+  if (!valid_multi(cache, D) || cache->n != N || !valid_walk_args((float)opts->eps, opts->max_steps, W) ||
+      !(opts->offset_l > 0.0))
+    return BVC_ERR_INVALID_ARG;
+  if (opts->src_grid[0] * opts->src_grid[1] != 0) return BVC_ERR_UNSUPPORTED;  // f = 0 only
+  const size_t per = ws_per_start(D, W, D);
+  int64_t chunk = ws_chunk(workspace_bytes, per);
+  if (chunk < 1) return BVC_ERR_WORKSPACE;
+  if (chunk > N) chunk = N;
+  cudaStream_t s = (cudaStream_t)stream;
+  cache->bnd_measure = g->measure;
+  bvc_status st = bvc_sample_boundary(g, N, opts->offset_l, opts->seed, cache->z, cache->nrm, nullptr, stream);
+  if (st != BVC_OK) return st;
+  WalkParams P{};
+  P.G = g->dev;
+  P.starts = cache->z;
+  P.nrm = cache->nrm;
+  P.pt_stride = N;
+  P.W = W;
+  P.eps = (float)opts->eps;
+  P.max_steps = opts->max_steps;
+  P.seed = opts->seed;
+  P.tag = 0;
+  P.counter = (unsigned long long*)workspace;
+  for (int64_t i0 = 0; i0 < N; i0 += chunk) {
+    const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
+    P.i0 = i0;
+    P.total = c * (int64_t)W;
+    P.wid0 = opts->walk_id_base + (uint64_t)i0 * (uint64_t)W;
+    float* fh = ws_first(workspace);
+    P.rec = ws_records(workspace, c, D);
+    P.first = fh;
+    st = launch_first_hits(D, g->dev, P.starts, N, i0, c, fh, s);
+    if (st != BVC_OK) return st;
+    st = launch_walk(D, false, kRecEnd, g->counting != 0, P, s);
+    if (st != BVC_OK) return st;
+    int64_t blocks = (c * 32 + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    ProfScope ps("multi_moments", s);
+    if (D == 2)
+      k_moments<2><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
+    else
+      k_moments<3><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
+    BVC_LAUNCH_CHECK();
+  }
+  return launch_project(coeffs, cache, s);
+}
+
+extern "C" bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_cache* cache, bvc_stream stream) {
+  if (coeffs == nullptr || cache == nullptr || (cache->dim != 2 && cache->dim != 3) || !valid_multi(cache, cache->dim))
+    return BVC_ERR_INVALID_ARG;
+  return launch_project(coeffs, cache, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -384,3 +384,98 @@ def icosphere_laplace(subdiv: int = 8, n_samples: int = 262144, walks: int = 128
     eps = 1e-3 * bbox_diagonal(V)
     return Workload(f"icosphere{subdiv}_laplace", 3, V, F, g, [], n_samples, walks, 5.0 * eps, eps, pts,
                     exact=g, seed=seed, meta={"n_plane": pl3.shape[0], "n_random": rnd.shape[0]})
+
+
+# ---------------------------------------------------------------- many right-hand sides
+def poly_exponents(dim: int):
+    """Exponent tuples of the POLY monomials (degree <= 4) in library order."""
+    out = []
+    for t in range(5):
+        for i in range(t, -1, -1):
+            if dim == 2:
+                out.append((i, t - i))
+            else:
+                for j in range(t - i, -1, -1):
+                    out.append((i, j, t - i - j))
+    return out
+
+
+def harmonic_basis(dim: int) -> np.ndarray:
+    """Orthonormal basis (rows, in monomial coefficients) of the harmonic
+    polynomials of degree <= 4: the null space of the Laplacian on the
+    monomial coefficients (9 functions in 2D, 25 in 3D)."""
+    ex = poly_exponents(dim)
+    index = {e: n for n, e in enumerate(ex)}
+    L = np.zeros((len(ex), len(ex)))
+    for col, e in enumerate(ex):
+        for a in range(dim):
+            if e[a] >= 2:
+                f = list(e)
+                f[a] -= 2
+                L[index[tuple(f)], col] += e[a] * (e[a] - 1)
+    _, sv, vt = np.linalg.svd(L)
+    rank = int(np.sum(sv > 1e-9))
+    return vt[rank:]
+
+
+def random_harmonic_polys(dim: int, k: int, seed: int) -> np.ndarray:
+    """k random harmonic polynomials up to degree 4 with N(0,1) coordinates
+    in an orthonormal harmonic basis: [k][n_monomials] coefficients."""
+    B = harmonic_basis(dim)
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((k, B.shape[0])) @ B
+
+
+def perturbed_ellipsoid(subdiv: int, axes, seed: int, amp: float = 0.02, centre=(0.0, 0.0, 0.0)):
+    """An icosphere stretched to the given semi-axes, radially perturbed,
+    moved to `centre`; outward counter-clockwise triangles."""
+    V, F, _ = perturbed_icosphere(subdiv, seed, amp)
+    V = V.astype(np.float64) * np.asarray(axes)[None, :] + np.asarray(centre)[None, :]
+    return V.astype(np.float32), F
+
+
+def batched_meshes(n_meshes: int = 16, seed: int = 0):
+    """Meshes of uneven size (about 10k to 500k triangles): perturbed
+    icospheres and ellipsoids, and unions of two disjoint ellipsoids.
+    Returns a list of (name, V, F, inside(p) predicate)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_meshes):
+        kind = i % 4
+        sub = [5, 6, 7, 6][kind] if i % 8 < 4 else [6, 5, 6, 7][kind]
+        if kind == 0 or (kind == 2 and sub == 7):
+            V, F, r = perturbed_icosphere(sub, seed + i)
+            out.append((f"icosphere{sub}_{i}", V, F, ("sphere", (0.0, 0.0, 0.0), (0.97, 0.97, 0.97))))
+        elif kind in (1, 2):
+            ax = tuple(rng.uniform(0.6, 1.4, 3))
+            V, F = perturbed_ellipsoid(sub, ax, seed + i)
+            out.append((f"ellipsoid{sub}_{i}", V, F, ("ellipsoid", (0.0, 0.0, 0.0), tuple(0.97 * a for a in ax))))
+        else:
+            ax1 = tuple(rng.uniform(0.5, 0.9, 3))
+            ax2 = tuple(rng.uniform(0.5, 0.9, 3))
+            c1, c2 = (-1.2, 0.0, 0.0), (1.2, 0.0, 0.0)
+            V1, F1 = perturbed_ellipsoid(sub - 1, ax1, seed + i, centre=c1)
+            V2, F2 = perturbed_ellipsoid(sub - 1, ax2, seed + 100 + i, centre=c2)
+            V = np.concatenate([V1, V2])
+            F = np.concatenate([F1, F2 + V1.shape[0]]).astype(np.int32)
+            out.append((f"union{sub - 1}x2_{i}", V, F,
+                        ("union", (c1, c2), (tuple(0.97 * a for a in ax1), tuple(0.97 * a for a in ax2)))))
+    return out
+
+
+def random_points_in(shape, n: int, seed: int) -> np.ndarray:
+    """Uniform points inside the shrunk body described by `shape` (the 0.97
+    shrink keeps them inside the radially perturbed surfaces)."""
+    rng = np.random.default_rng(seed)
+    kind = shape[0]
+    if kind == "union":
+        (c1, c2), (a1, a2) = shape[1], shape[2]
+        v1, v2 = np.prod(a1), np.prod(a2)
+        n1 = int(round(n * v1 / (v1 + v2)))
+        return np.concatenate([random_points_in(("ellipsoid", c1, a1), n1, seed + 1),
+                               random_points_in(("ellipsoid", c2, a2), n - n1, seed + 2)])
+    c, a = np.asarray(shape[1]), np.asarray(shape[2])
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = rng.uniform(size=n) ** (1.0 / 3.0) * 0.98
+    return (c[None, :] + d * r[:, None] * a[None, :]).astype(np.float32)

@@ -111,3 +111,34 @@ def test_product_does_not_use_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text and "bvc_oracle" not in text, f
+
+
+def test_multi_rhs_host_checks(lib):
+    lib.bvc_poly_terms.restype = C.c_int32
+    assert [lib.bvc_poly_terms(d) for d in (1, 2, 3, 4)] == [0, 15, 35, 0]
+    lib.bvc_multi_cache_build_workspace_size.restype = C.c_int
+    mn = C.c_size_t()
+    assert lib.bvc_multi_cache_build_workspace_size(None, C.c_int64(10), 4, C.byref(mn), None) == 1
+    lib.bvc_multi_cache_build.restype = C.c_int
+    assert lib.bvc_multi_cache_build(None, None, None, None, None, C.c_size_t(0), None) == 1
+    lib.bvc_multi_cache_project.restype = C.c_int
+    assert lib.bvc_multi_cache_project(None, None, None) == 1
+    lib.bvc_evaluate_multi.restype = C.c_int
+    assert lib.bvc_evaluate_multi(None, None, C.c_int64(0), None, None) == 1
+
+
+def test_harmonic_polynomial_generator():
+    # the random right-hand sides of the batched workload are harmonic:
+    # the Laplacian of each, by central differences, vanishes
+    from paper_2302_11825_gb300 import workloads as wl
+    for dim, nb in ((2, 9), (3, 25)):
+        assert wl.harmonic_basis(dim).shape == (nb, 15 if dim == 2 else 35)
+        C = wl.random_harmonic_polys(dim, 4, seed=1)
+        x = np.random.default_rng(2).uniform(-1, 1, (50, dim))
+        h = 1e-3
+        for k in range(4):
+            t = [(wl.POLY, C[k])]
+            f0 = wl.eval_terms(t, dim, x)[0]
+            lap = sum(wl.eval_terms(t, dim, x + h * e)[0] + wl.eval_terms(t, dim, x - h * e)[0] - 2 * f0
+                      for e in np.eye(dim)) / h ** 2
+            assert np.abs(lap).max() < 1e-4 * max(1.0, np.abs(f0).max())
