@@ -332,6 +332,50 @@ bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_cache* cache,
 bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
                               bvc_stream stream);
 
+/* ---------------------------------------------- many meshes in one launch */
+/* A batch of independent Laplace problems on meshes of the same dimension
+ * and uneven size, each with K polynomial right-hand sides as above.  The
+ * batch concatenates the meshes' BVHs into one forest (indices rebased,
+ * device memory owned by the batch), so the walks of every mesh run in one
+ * persistent launch and the gather of every mesh in one launch.  Walk ids
+ * and boundary samples are those of bvc_multi_cache_build on each mesh alone
+ * with walk_id_base = (first sample of the mesh in the batch) x walks and the
+ * same seed, so every mesh's results equal the single-mesh results bit for
+ * bit.  bvc_batch_build and bvc_batch_evaluate only launch kernels and clear
+ * device words on the stream (no allocation, no synchronisation), so they
+ * may be captured in a CUDA graph. */
+typedef struct bvc_batch_s* bvc_batch;
+typedef struct {
+  bvc_geometry geom; /* borrowed: must outlive the batch */
+  int64_t n_samples; /* boundary samples (>= 1) */
+  double offset_l;   /* inward offset of the samples (Sec. 3.2) */
+  float eps;         /* epsilon-shell of this mesh's walks */
+  int64_t n_points;  /* evaluation points (>= 0) */
+} bvc_batch_mesh;
+
+/* Builds the forest (synchronous on `stream`).  All meshes must share one
+ * dimension; count >= 1; walks, max_steps >= 1; k >= 1.  Samples of mesh j
+ * occupy [sum_{i<j} n_samples_i, ...) of the batch's sample range and its
+ * points [sum_{i<j} n_points_i, ...) of the point range. */
+bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t count, int32_t walks, int32_t max_steps,
+                            int32_t k, bvc_stream stream, bvc_batch* out);
+bvc_status bvc_batch_destroy(bvc_batch b);
+/* n_total, m_total: sums of n_samples and n_points. */
+bvc_status bvc_batch_get_info(bvc_batch b, int32_t* dim, int64_t* n_total, int64_t* m_total);
+bvc_status bvc_batch_build_workspace_size(bvc_batch b, size_t* min_bytes, size_t* full_bytes);
+/* coeffs: device double[count][k][bvc_poly_terms(dim)]; cache: a
+ * bvc_multi_cache with n = n_total and k = the batch's k (its bnd_measure
+ * is left 0: each mesh's measure is held by the batch). */
+bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, uint64_t seed, bvc_multi_cache* cache,
+                           void* workspace, size_t workspace_bytes, bvc_stream stream);
+/* Re-project the stored moments onto new coefficients (no walks). */
+bvc_status bvc_batch_project(bvc_batch b, const double* coeffs, bvc_multi_cache* cache, bvc_stream stream);
+/* Eq. 3 for every mesh and right-hand side: pts device [dim][m_total];
+ * u device double[k][m_total] (overwritten), point p of mesh j gathered
+ * over mesh j's samples only. */
+bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
+                              bvc_stream stream);
+
 /* wos_estimate with no caller workspace and no allocation.  The paper has
  * no counterpart: this is an interface for callers that must not allocate
  * device memory -- for example code that runs inside another framework

@@ -68,6 +68,11 @@ class MultiCacheStruct(C.Structure):
                 ("packed", C.c_void_p), ("bnd_measure", C.c_double)]
 
 
+class BatchMeshStruct(C.Structure):
+    _fields_ = [("geom", C.c_void_p), ("n_samples", C.c_int64), ("offset_l", C.c_double), ("eps", C.c_float),
+                ("n_points", C.c_int64)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -115,6 +120,13 @@ def _declare(lib):
         "bvc_multi_cache_build": (S, [P, P, C.POINTER(CacheOpts), C.POINTER(MultiCacheStruct), P, sz, P]),
         "bvc_multi_cache_project": (S, [P, C.POINTER(MultiCacheStruct), P]),
         "bvc_evaluate_multi": (S, [C.POINTER(MultiCacheStruct), P, i64, P, P]),
+        "bvc_batch_create": (S, [P, i32, i32, i32, i32, P, C.POINTER(C.c_void_p)]),
+        "bvc_batch_destroy": (S, [P]),
+        "bvc_batch_get_info": (S, [P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "bvc_batch_build_workspace_size": (S, [P, C.POINTER(sz), C.POINTER(sz)]),
+        "bvc_batch_build": (S, [P, P, u64, C.POINTER(MultiCacheStruct), P, sz, P]),
+        "bvc_batch_project": (S, [P, P, C.POINTER(MultiCacheStruct), P]),
+        "bvc_batch_evaluate": (S, [P, C.POINTER(MultiCacheStruct), P, P, P]),
         "bvc_profile_begin": (S, []),
         "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
         "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
@@ -532,6 +544,77 @@ def evaluate_multi(cache: MultiCache, pts: torch.Tensor, u: torch.Tensor = None,
     _check(lib().bvc_evaluate_multi(C.byref(cache.struct), _ptr(pts), m, _ptr(u), _stream(stream)),
            "bvc_evaluate_multi")
     return u
+
+
+class Batch:
+    """bvc_batch_create / bvc_batch_destroy: independent problems on several
+    meshes of one dimension, walked and gathered in one launch each.
+    meshes: list of (Geometry, n_samples, offset_l, eps, n_points)."""
+
+    def __init__(self, meshes, walks: int, max_steps: int, k: int, stream=None):
+        self.geoms = [m[0] for m in meshes]  # keep the borrowed geometries alive
+        arr = (BatchMeshStruct * len(meshes))()
+        for j, (g, n, l, eps, m) in enumerate(meshes):
+            arr[j].geom, arr[j].n_samples, arr[j].offset_l = g.h.value, int(n), float(l)
+            arr[j].eps, arr[j].n_points = float(eps), int(m)
+        h = C.c_void_p()
+        _check(lib().bvc_batch_create(C.cast(arr, C.c_void_p), len(meshes), int(walks), int(max_steps), int(k),
+                                      _stream(stream), C.byref(h)), "bvc_batch_create")
+        self.h = h
+        dim, n, m = C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().bvc_batch_get_info(h, C.byref(dim), C.byref(n), C.byref(m)), "bvc_batch_get_info")
+        self.dim, self.n_total, self.m_total, self.k = dim.value, n.value, m.value, int(k)
+        self.sample_offsets = np.concatenate([[0], np.cumsum([int(x[1]) for x in meshes])])
+        self.point_offsets = np.concatenate([[0], np.cumsum([int(x[4]) for x in meshes])])
+
+    def workspace_size(self):
+        mn, full = C.c_size_t(), C.c_size_t()
+        _check(lib().bvc_batch_build_workspace_size(self.h, C.byref(mn), C.byref(full)),
+               "bvc_batch_build_workspace_size")
+        return int(mn.value), int(full.value)
+
+    def cache(self, device="cuda") -> MultiCache:
+        return MultiCache(self.dim, self.n_total, self.k, device)
+
+    def build(self, coeffs: torch.Tensor, seed: int, cache: MultiCache, ws: torch.Tensor = None, stream=None):
+        """coeffs: CUDA float64 [meshes][k][poly_terms(dim)]."""
+        _dev(coeffs, torch.float64)
+        if tuple(coeffs.shape) != (len(self.geoms), self.k, poly_terms(self.dim)):
+            raise ValueError("coefficients must be [meshes][k][poly_terms(dim)]")
+        if ws is None:
+            ws = workspace(self.workspace_size()[1])
+        _check(lib().bvc_batch_build(self.h, _ptr(coeffs), int(seed), C.byref(cache.struct), _ptr(ws), ws.numel(),
+                                     _stream(stream)), "bvc_batch_build")
+        return cache
+
+    def project(self, coeffs: torch.Tensor, cache: MultiCache, stream=None):
+        _dev(coeffs, torch.float64)
+        if tuple(coeffs.shape) != (len(self.geoms), self.k, poly_terms(self.dim)):
+            raise ValueError("coefficients must be [meshes][k][poly_terms(dim)]")
+        _check(lib().bvc_batch_project(self.h, _ptr(coeffs), C.byref(cache.struct), _stream(stream)),
+               "bvc_batch_project")
+
+    def evaluate(self, cache: MultiCache, pts: torch.Tensor, u: torch.Tensor = None, stream=None):
+        """pts: CUDA float32 [dim][m_total]; returns u [k][m_total] (float64)."""
+        _dev(pts, torch.float32)
+        if tuple(pts.shape) != (self.dim, self.m_total):
+            raise ValueError("points must be [dim][m_total]")
+        if u is None:
+            u = torch.empty((self.k, self.m_total), dtype=torch.float64, device=pts.device)
+        _check(lib().bvc_batch_evaluate(self.h, C.byref(cache.struct), _ptr(pts), _ptr(u), _stream(stream)),
+               "bvc_batch_evaluate")
+        return u
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bvc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def profile_begin():

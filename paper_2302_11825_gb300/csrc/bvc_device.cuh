@@ -303,7 +303,7 @@ __device__ __forceinline__ void finish_hit(const DevGeometry& G, const float* p,
 // Closest primitive to p.  Stack in shared memory: stack[k * stride + lane_slot].
 template <int D, bool CNT = false>
 __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p, Hit<D>& h, int* snode,
-                                            float* sdist, int stride, TravCount& tc) {
+                                            float* sdist, int stride, TravCount& tc, int root = 0) {
   h.d2 = __int_as_float(0x7f800000);
   h.id = 0x7fffffff;
   h.q = -1;
@@ -311,7 +311,7 @@ __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p
   for (int a = 0; a < D; ++a) h.df[a] = 0.0f;
   float thr = __int_as_float(0x7f800000);
   int sp = 0;
-  int node = 0;
+  int node = root;
   for (;;) {
     int32_t cl, cr;
     float dl, dr;

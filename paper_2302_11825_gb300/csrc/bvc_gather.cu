@@ -658,23 +658,46 @@ constexpr int kMG = BVC_MULTI_GROUP;
 constexpr int kMTile = 32;
 constexpr int kMStride = 8 + 2 * kMG;  // floats per packed sample row
 
+// One mesh (meshes == null): m points [D][m] against n samples.  A batch:
+// block x belongs to the mesh whose gather blocks hold it; its points lie in
+// that mesh's range of the [D][m] point planes and its samples in that
+// mesh's range of the n sample rows of each group.
 template <int D>
 __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict__ x, int64_t m,
                                                          const float* __restrict__ packed, int64_t n, int32_t K,
-                                                         double* __restrict__ u) {
+                                                         double* __restrict__ u, const BatchMeshDev* __restrict__ meshes,
+                                                         int32_t count) {
   __shared__ __align__(128) float tile[2][kMTile * kMStride];
   __shared__ __align__(8) uint64_t bar[2];
   const int g = blockIdx.y;
-  const float* base = packed + (int64_t)g * n * kMStride;
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t blk = blockIdx.x, pt_off = 0, n_pts = m, smp_off = 0, n_smp = n;
+  if (meshes != nullptr) {
+    int lo = 0, hi = count - 1;  // the last mesh whose first block is <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (meshes[mid].blk_off <= (int64_t)blockIdx.x)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const BatchMeshDev M = meshes[lo];
+    blk -= M.blk_off;
+    pt_off = M.pt_off;
+    n_pts = M.n_pts;
+    smp_off = M.smp_off;
+    n_smp = M.n_smp;
+  }
+  const float* base = packed + ((int64_t)g * n + smp_off) * kMStride;
+  const int64_t pl = blk * blockDim.x + threadIdx.x;  // point within the mesh
+  const int64_t p = pt_off + pl;
   float pc[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) pc[a] = (a < D && p < m) ? x[a * m + p] : 1.0e4f + (float)a;
+  for (int a = 0; a < 3; ++a) pc[a] = (a < D && pl < n_pts) ? x[a * m + p] : 1.0e4f + (float)a;
   float acc[kMG];
   double acc64[kMG];
 #pragma unroll
   for (int q = 0; q < kMG; ++q) acc64[q] = 0.0;
-  const int64_t nt = (n + kMTile - 1) / kMTile;
+  const int64_t nt = (n_smp + kMTile - 1) / kMTile;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -684,7 +707,7 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
   if (threadIdx.x == 0) {
     for (int b = 0; b < 2 && b < nt; ++b) {
       const int64_t st = (int64_t)b * kMTile;
-      const uint32_t bytes = (uint32_t)min64(kMTile, n - st) * kMStride * 4u;
+      const uint32_t bytes = (uint32_t)min64(kMTile, n_smp - st) * kMStride * 4u;
       mbar_expect_tx(&bar[b], bytes);
       bulk_g2s(&tile[b][0], base + st * kMStride, bytes, &bar[b]);
     }
@@ -700,7 +723,7 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
       }
       return;
     }
-    const int cnt = (int)min64(kMTile, n - it * kMTile);
+    const int cnt = (int)min64(kMTile, n_smp - it * kMTile);
 #pragma unroll
     for (int q = 0; q < kMG; ++q) acc[q] = 0.0f;
     const float4* T = reinterpret_cast<const float4*>(tile[b]);
@@ -735,14 +758,14 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
     if (threadIdx.x == 0 && it + 2 < nt) {
       fence_proxy_async();
       const int64_t st = (it + 2) * kMTile;
-      const uint32_t bytes = (uint32_t)min64(kMTile, n - st) * kMStride * 4u;
+      const uint32_t bytes = (uint32_t)min64(kMTile, n_smp - st) * kMStride * 4u;
       mbar_expect_tx(&bar[b], bytes);
       bulk_g2s(&tile[b][0], base + st * kMStride, bytes, &bar[b]);
     }
   }
-  if (p < m) {
+  if (pl < n_pts) {
     const int kk = (K - g * kMG) < kMG ? (K - g * kMG) : kMG;
-    const double inv_n = 1.0 / (double)n;
+    const double inv_n = 1.0 / (double)n_smp;
 #pragma unroll
     for (int q = 0; q < kMG; ++q)
       if (q < kk) u[(int64_t)(g * kMG + q) * m + p] = acc64[q] * inv_n;
@@ -763,9 +786,30 @@ extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const flo
   cudaStream_t s = (cudaStream_t)stream;
   ProfScope ps("gather_multi", s);
   if (cache->dim == 2)
-    k_gather_multi<2><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u);
+    k_gather_multi<2><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
   else
-    k_gather_multi<3><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u);
+    k_gather_multi<3><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
+                                         bvc_stream stream) {
+  if (b == nullptr || cache == nullptr || cache->dim != b->dim || cache->n != b->n_total || cache->k != b->k ||
+      cache->packed == nullptr || (b->m_total > 0 && (pts == nullptr || u == nullptr)))
+    return BVC_ERR_INVALID_ARG;
+  const int groups = (cache->k + kMG - 1) / kMG;
+  if (groups > 65535 || b->blocks_total > 0x7fffffffLL) return BVC_ERR_INVALID_ARG;  // grid limits
+  if (b->blocks_total == 0) return BVC_OK;
+  const dim3 grid((unsigned)b->blocks_total, (unsigned)groups);
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps("gather_multi", s);
+  if (b->dim == 2)
+    k_gather_multi<2><<<grid, 256, 0, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u, b->table,
+                                           b->count);
+  else
+    k_gather_multi<3><<<grid, 256, 0, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u, b->table,
+                                           b->count);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }

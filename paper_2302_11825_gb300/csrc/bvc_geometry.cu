@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_query_closest(DevGeometry G, const floa
 template <int D>
 __global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t n, double l, uint64_t seed,
                                                          float* __restrict__ z, float* __restrict__ nrm,
-                                                         int32_t* __restrict__ elem) {
+                                                         int32_t* __restrict__ elem, int64_t stride) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const U4 r = philox_draw(seed, (uint64_t)i, 0u, 1u);
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t 
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    z[a * n + i] = __double2float_rn(__dsub_rn(p[a], __dmul_rn(l, nn[a])));
-    nrm[a * n + i] = __double2float_rn(nn[a]);
+    z[a * stride + i] = __double2float_rn(__dsub_rn(p[a], __dmul_rn(l, nn[a])));
+    nrm[a * stride + i] = __double2float_rn(nn[a]);
   }
   if (elem) elem[i] = (int32_t)e;
 }
@@ -299,17 +299,26 @@ extern "C" bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_
   return BVC_OK;
 }
 
+namespace bvc {
+// K1 into planes of `stride` floats (a batch writes each mesh's samples into
+// its range of the batch's sample planes).
+bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
+                                  int32_t* elem, int64_t stride, cudaStream_t s) {
+  if (n == 0) return BVC_OK;
+  const int grid = (int)((n + 255) / 256);
+  ProfScope ps("sample_boundary", s);
+  if (g->dim == 2)
+    k_sample_boundary<2><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride);
+  else
+    k_sample_boundary<3><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+}  // namespace bvc
+
 extern "C" bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
                                           int32_t* elem, bvc_stream stream) {
   if (g == nullptr || n < 0 || (n > 0 && (z == nullptr || nrm == nullptr)) || !std::isfinite(l))
     return BVC_ERR_INVALID_ARG;
-  if (n == 0) return BVC_OK;
-  const int grid = (int)((n + 255) / 256);
-  ProfScope ps("sample_boundary", (cudaStream_t)stream);
-  if (g->dim == 2)
-    k_sample_boundary<2><<<grid, 256, 0, (cudaStream_t)stream>>>(g->dev, n, l, seed, z, nrm, elem);
-  else
-    k_sample_boundary<3><<<grid, 256, 0, (cudaStream_t)stream>>>(g->dev, n, l, seed, z, nrm, elem);
-  BVC_LAUNCH_CHECK();
-  return BVC_OK;
+  return launch_sample_boundary(g, n, l, seed, z, nrm, elem, n, (cudaStream_t)stream);
 }

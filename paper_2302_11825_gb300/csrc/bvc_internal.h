@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -42,10 +44,34 @@ struct DevGeometry {
   float lo[3], hi[3];     // bbox
 };
 
+// One mesh of a batch (bvc_batch): its tree inside the forest, its shell,
+// measure and its sample, point and gather-block ranges.
+struct BatchMeshDev {
+  int32_t root;     // forest node index of the mesh's root
+  float eps;        // epsilon-shell
+  double measure;   // |dOmega|
+  int64_t smp_off, n_smp;
+  int64_t pt_off, n_pts;
+  int64_t blk_off;  // first gather block of the mesh (256 points per block)
+};
+
 constexpr int kStatSteps = 0, kStatCapped = 1, kStatFlags = 2, kStatCounter = 3, kStatNodes = 4, kStatPrims = 5;
 constexpr unsigned long long kFlagTimeout = 1ull;
 
 }  // namespace bvc
+
+struct bvc_batch_s {
+  int32_t dim, count, walks, max_steps, k;
+  int64_t n_total, m_total, blocks_total;
+  std::vector<bvc::BatchMeshDev> mesh;  // host copy of the table
+  std::vector<double> offset_l;
+  std::vector<bvc_geometry> geoms;      // borrowed
+  void* arena;
+  size_t arena_bytes;
+  bvc::DevGeometry forest;              // concatenated nodes and primitives
+  int32_t* sample_mesh;                 // [n_total] mesh of every sample
+  bvc::BatchMeshDev* table;             // [count]
+};
 
 struct bvc_geometry_s {
   int32_t dim;
@@ -63,6 +89,8 @@ namespace bvc {
 // Host helpers (bvc_common.cu)
 bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);
 int num_sms();
+bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
+                                  int32_t* elem, int64_t stride, cudaStream_t s);
 int max_blocks_per_sm(const void* kernel, int block, size_t smem);
 
 // Kernel timing: while bvc_profile_begin .. bvc_profile_end is active, every

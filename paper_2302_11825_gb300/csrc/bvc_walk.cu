@@ -60,12 +60,18 @@ struct WalkParams {
   // walks (they all begin at the same point), or null: planes of
   // (total / W) floats: d2, p - closest (D), element id bits.
   const float* first;
+  // Batches of meshes (kRecEnd walks only): the mesh of every start, and the
+  // meshes' roots and shells; null for one mesh (root 0, shell eps).
+  const int32_t* sample_mesh;
+  const BatchMeshDev* meshes;
 };
 
 // The first query of each start of a launch, once per start.
 template <int D>
 __global__ void __launch_bounds__(128) k_first_hits(DevGeometry G, const float* __restrict__ starts,
-                                                    int64_t pt_stride, int64_t i0, int64_t c, float* __restrict__ fh) {
+                                                    int64_t pt_stride, int64_t i0, int64_t c, float* __restrict__ fh,
+                                                    const int32_t* __restrict__ sample_mesh,
+                                                    const BatchMeshDev* __restrict__ meshes) {
   __shared__ int snode[kStack * 128];
   __shared__ float sdist[kStack * 128];
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < c; r += (int64_t)gridDim.x * blockDim.x) {
@@ -74,7 +80,8 @@ __global__ void __launch_bounds__(128) k_first_hits(DevGeometry G, const float* 
     for (int a = 0; a < D; ++a) p[a] = starts[a * pt_stride + i0 + r];
     Hit<D> h;
     TravCount tc{0, 0};
-    bvh_closest<D>(G, p, h, snode + threadIdx.x, sdist + threadIdx.x, 128, tc);
+    const int root = sample_mesh ? meshes[sample_mesh[i0 + r]].root : 0;
+    bvh_closest<D>(G, p, h, snode + threadIdx.x, sdist + threadIdx.x, 128, tc, root);
     fh[r] = h.d2;
 #pragma unroll
     for (int a = 0; a < D; ++a) fh[(1 + a) * c + r] = h.df[a];
@@ -120,6 +127,9 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
   for (int a = 0; a < D; ++a) x[a] = nu[a] = 0.0f;
   float R0 = 0.0f, usrc = 0.0f, wf0 = 0.0f, wg0 = 0.0f, cv = 0.0f;
   int k = 0;
+  // the walk's tree and shell (per mesh in a batch)
+  int root = 0;
+  float eps = P.eps;
   // query state
   int cur = 0, sp = 0;
   float thr = kInf;
@@ -132,7 +142,7 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
 
   auto begin_query = [&]() {
     phase = kQuery;
-    cur = 0;
+    cur = root;
     sp = 0;
     thr = kInf;
     h.d2 = kInf;
@@ -174,6 +184,11 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
         i = P.i0 + r;
 #pragma unroll
         for (int a = 0; a < D; ++a) x[a] = P.starts[a * P.pt_stride + i];
+        if (REC == kRecEnd && P.sample_mesh != nullptr) {
+          const BatchMeshDev* M = P.meshes + P.sample_mesh[i];
+          root = M->root;
+          eps = M->eps;
+        }
         k = 0;
         R0 = usrc = wf0 = wg0 = cv = 0.0f;
         if (P.first) {
@@ -273,7 +288,7 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
         for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
         const float d = sqrtf(h.d2);
         if (REC != kRecEnd && k == 1) cv = eval_fn<D, true>(P.g, pbar);
-        if (d < P.eps || k >= P.max_steps) {
+        if (d < eps || k >= P.max_steps) {
           if (REC == kRecEnd) {
 #pragma unroll
             for (int a = 0; a < D; ++a) P.rec[a * P.total + t] = pbar[a];
@@ -298,7 +313,7 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
           if (P.steps) P.steps[t] = k;
           if (P.prim) P.prim[t] = h.id;
           my_steps += (unsigned long long)k;
-          if (!(d < P.eps)) ++my_capped;
+          if (!(d < eps)) ++my_capped;
           phase = kIdle;
         } else {
           const float R = d;
@@ -432,16 +447,17 @@ static bvc_status launch_walk(int dim, bool has_f, int rec, bool cnt, const Walk
 }
 
 static bvc_status launch_first_hits(int dim, const DevGeometry& G, const float* starts, int64_t pt_stride, int64_t i0,
-                                    int64_t c, float* fh, cudaStream_t s) {
+                                    int64_t c, float* fh, cudaStream_t s, const int32_t* sample_mesh = nullptr,
+                                    const BatchMeshDev* meshes = nullptr) {
   int64_t blocks = (c + 127) / 128;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   ProfScope ps("first_hits", s);
   if (dim == 2)
-    k_first_hits<2><<<(unsigned)blocks, 128, 0, s>>>(G, starts, pt_stride, i0, c, fh);
+    k_first_hits<2><<<(unsigned)blocks, 128, 0, s>>>(G, starts, pt_stride, i0, c, fh, sample_mesh, meshes);
   else
-    k_first_hits<3><<<(unsigned)blocks, 128, 0, s>>>(G, starts, pt_stride, i0, c, fh);
+    k_first_hits<3><<<(unsigned)blocks, 128, 0, s>>>(G, starts, pt_stride, i0, c, fh, sample_mesh, meshes);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -822,7 +838,9 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
                                                  const double* __restrict__ mom_u, const double* __restrict__ mom_q,
                                                  const float* __restrict__ z, const float* __restrict__ nrm,
                                                  double meas, double* __restrict__ u_hat,
-                                                 double* __restrict__ q_hat, float* __restrict__ packed) {
+                                                 double* __restrict__ q_hat, float* __restrict__ packed,
+                                                 const int32_t* __restrict__ sample_mesh,
+                                                 const BatchMeshDev* __restrict__ meshes) {
   constexpr int NM = Mono<D>::kN;
   constexpr int G = BVC_MULTI_GROUP;
   constexpr int S = 8 + 2 * G;
@@ -833,6 +851,11 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
   for (int m = 0; m < NM; ++m) {
     mu[m] = mom_u[i * NM + m];
     mq[m] = mom_q[i * NM + m];
+  }
+  if (sample_mesh != nullptr) {  // a batch: this sample's mesh's coefficients and measure
+    const int32_t msh = sample_mesh[i];
+    C += (int64_t)msh * K * NM;
+    meas = meshes[msh].measure;
   }
   const int groups = (K + G - 1) / G;
   const double ca = D == 2 ? meas / 6.283185307179586476925 : meas / 12.566370614359172953850;
@@ -869,16 +892,74 @@ static bool valid_multi(const bvc_multi_cache* c, int dim) {
          c->u_hat && c->dudn_hat && c->packed;
 }
 
-static bvc_status launch_project(const double* coeffs, bvc_multi_cache* c, cudaStream_t s) {
+static bvc_status launch_project(const double* coeffs, bvc_multi_cache* c, cudaStream_t s,
+                                 const int32_t* sample_mesh = nullptr, const BatchMeshDev* meshes = nullptr) {
   const unsigned grid = (unsigned)((c->n + 127) / 128);
   ProfScope ps("multi_project", s);
   if (c->dim == 2)
     k_project<2><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->bnd_measure, c->u_hat,
-                                      c->dudn_hat, c->packed);
+                                      c->dudn_hat, c->packed, sample_mesh, meshes);
   else
     k_project<3><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->bnd_measure, c->u_hat,
-                                      c->dudn_hat, c->packed);
+                                      c->dudn_hat, c->packed, sample_mesh, meshes);
   BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+// End-point walks of every start of a multi-RHS cache (one mesh, or a batch
+// when E.sample_mesh is set), in chunks that fit the workspace: first
+// closest-point queries, the walks, and the per-sample monomial moments.
+struct EndWalks {
+  DevGeometry G;
+  int dim;
+  bool counting;
+  int32_t W;
+  float eps;
+  int32_t max_steps;
+  uint64_t seed, wid_base;
+  const int32_t* sample_mesh;
+  const BatchMeshDev* meshes;
+};
+
+static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void* workspace, int64_t chunk,
+                                cudaStream_t s) {
+  const int D = E.dim;
+  const int64_t N = cache->n;
+  WalkParams P{};
+  P.G = E.G;
+  P.starts = cache->z;
+  P.nrm = cache->nrm;
+  P.pt_stride = N;
+  P.W = E.W;
+  P.eps = E.eps;
+  P.max_steps = E.max_steps;
+  P.seed = E.seed;
+  P.tag = 0;
+  P.counter = (unsigned long long*)workspace;
+  P.sample_mesh = E.sample_mesh;
+  P.meshes = E.meshes;
+  for (int64_t i0 = 0; i0 < N; i0 += chunk) {
+    const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
+    P.i0 = i0;
+    P.total = c * (int64_t)E.W;
+    P.wid0 = E.wid_base + (uint64_t)i0 * (uint64_t)E.W;
+    float* fh = ws_first(workspace);
+    P.rec = ws_records(workspace, c, D);
+    P.first = fh;
+    bvc_status st = launch_first_hits(D, E.G, P.starts, N, i0, c, fh, s, E.sample_mesh, E.meshes);
+    if (st != BVC_OK) return st;
+    st = launch_walk(D, false, kRecEnd, E.counting, P, s);
+    if (st != BVC_OK) return st;
+    int64_t blocks = (c * 32 + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    ProfScope ps("multi_moments", s);
+    if (D == 2)
+      k_moments<2><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, E.W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
+    else
+      k_moments<3><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, E.W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
+    BVC_LAUNCH_CHECK();
+  }
   return BVC_OK;
 }
 
@@ -912,39 +993,17 @@ extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs
   cache->bnd_measure = g->measure;
   bvc_status st = bvc_sample_boundary(g, N, opts->offset_l, opts->seed, cache->z, cache->nrm, nullptr, stream);
   if (st != BVC_OK) return st;
-  WalkParams P{};
-  P.G = g->dev;
-  P.starts = cache->z;
-  P.nrm = cache->nrm;
-  P.pt_stride = N;
-  P.W = W;
-  P.eps = (float)opts->eps;
-  P.max_steps = opts->max_steps;
-  P.seed = opts->seed;
-  P.tag = 0;
-  P.counter = (unsigned long long*)workspace;
-  for (int64_t i0 = 0; i0 < N; i0 += chunk) {
-    const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
-    P.i0 = i0;
-    P.total = c * (int64_t)W;
-    P.wid0 = opts->walk_id_base + (uint64_t)i0 * (uint64_t)W;
-    float* fh = ws_first(workspace);
-    P.rec = ws_records(workspace, c, D);
-    P.first = fh;
-    st = launch_first_hits(D, g->dev, P.starts, N, i0, c, fh, s);
-    if (st != BVC_OK) return st;
-    st = launch_walk(D, false, kRecEnd, g->counting != 0, P, s);
-    if (st != BVC_OK) return st;
-    int64_t blocks = (c * 32 + 255) / 256;
-    const int64_t cap = (int64_t)num_sms() * 16;
-    if (blocks > cap) blocks = cap;
-    ProfScope ps("multi_moments", s);
-    if (D == 2)
-      k_moments<2><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
-    else
-      k_moments<3><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
-    BVC_LAUNCH_CHECK();
-  }
+  EndWalks E{};
+  E.G = g->dev;
+  E.dim = D;
+  E.counting = g->counting != 0;
+  E.W = W;
+  E.eps = (float)opts->eps;
+  E.max_steps = opts->max_steps;
+  E.seed = opts->seed;
+  E.wid_base = opts->walk_id_base;
+  st = run_end_walks(E, cache, workspace, chunk, s);
+  if (st != BVC_OK) return st;
   return launch_project(coeffs, cache, s);
 }
 
@@ -952,6 +1011,59 @@ extern "C" bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_ca
   if (coeffs == nullptr || cache == nullptr || (cache->dim != 2 && cache->dim != 3) || !valid_multi(cache, cache->dim))
     return BVC_ERR_INVALID_ARG;
   return launch_project(coeffs, cache, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of meshes: every mesh's K1 into its sample range, then the
+// end-point walks of all meshes in one launch per workspace chunk over the
+// forest, the moments and one projection with per-mesh coefficients.
+static bool valid_batch_cache(const bvc_batch_s* b, const bvc_multi_cache* c) {
+  return b != nullptr && valid_multi(c, b->dim) && c->n == b->n_total && c->k == b->k;
+}
+
+extern "C" bvc_status bvc_batch_build_workspace_size(bvc_batch b, size_t* min_bytes, size_t* full_bytes) {
+  if (b == nullptr) return BVC_ERR_INVALID_ARG;
+  const size_t per = ws_per_start(b->dim, b->walks, b->dim);
+  if (min_bytes) *min_bytes = 2 * kWsHead + per;
+  if (full_bytes) *full_bytes = 2 * kWsHead + per * (size_t)b->n_total;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, uint64_t seed, bvc_multi_cache* cache,
+                                      void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  if (coeffs == nullptr || workspace == nullptr || !valid_batch_cache(b, cache)) return BVC_ERR_INVALID_ARG;
+  const size_t per = ws_per_start(b->dim, b->walks, b->dim);
+  int64_t chunk = ws_chunk(workspace_bytes, per);
+  if (chunk < 1) return BVC_ERR_WORKSPACE;
+  if (chunk > b->n_total) chunk = b->n_total;
+  cudaStream_t s = (cudaStream_t)stream;
+  cache->bnd_measure = 0.0;
+  for (int j = 0; j < b->count; ++j) {
+    const BatchMeshDev& m = b->mesh[j];
+    const bvc_status st = launch_sample_boundary(b->geoms[j], m.n_smp, b->offset_l[j], seed, cache->z + m.smp_off,
+                                                 cache->nrm + m.smp_off, nullptr, b->n_total, s);
+    if (st != BVC_OK) return st;
+  }
+  EndWalks E{};
+  E.G = b->forest;
+  E.dim = b->dim;
+  E.counting = false;
+  E.W = b->walks;
+  E.eps = b->mesh[0].eps;
+  E.max_steps = b->max_steps;
+  E.seed = seed;
+  E.wid_base = 0;
+  E.sample_mesh = b->sample_mesh;
+  E.meshes = b->table;
+  const bvc_status st = run_end_walks(E, cache, workspace, chunk, s);
+  if (st != BVC_OK) return st;
+  return launch_project(coeffs, cache, s, b->sample_mesh, b->table);
+}
+
+extern "C" bvc_status bvc_batch_project(bvc_batch b, const double* coeffs, bvc_multi_cache* cache,
+                                        bvc_stream stream) {
+  if (coeffs == nullptr || !valid_batch_cache(b, cache)) return BVC_ERR_INVALID_ARG;
+  return launch_project(coeffs, cache, (cudaStream_t)stream, b->sample_mesh, b->table);
 }
 
 // ---------------------------------------------------------------------------

@@ -142,3 +142,18 @@ def test_harmonic_polynomial_generator():
             lap = sum(wl.eval_terms(t, dim, x + h * e)[0] + wl.eval_terms(t, dim, x - h * e)[0] - 2 * f0
                       for e in np.eye(dim)) / h ** 2
             assert np.abs(lap).max() < 1e-4 * max(1.0, np.abs(f0).max())
+
+
+def test_batch_host_checks(lib):
+    lib.bvc_batch_create.restype = C.c_int
+    h = C.c_void_p()
+    assert lib.bvc_batch_create(None, 1, 4, 10, 1, None, C.byref(h)) == 1
+    assert lib.bvc_batch_create(None, 0, 4, 10, 1, None, None) == 1
+    for name, nargs in (("bvc_batch_destroy", 1), ("bvc_batch_get_info", 4), ("bvc_batch_build_workspace_size", 3),
+                        ("bvc_batch_build", 7), ("bvc_batch_project", 4), ("bvc_batch_evaluate", 5)):
+        fn = getattr(lib, name)
+        fn.restype = C.c_int
+        args = [None] * nargs
+        if name == "bvc_batch_build":
+            args = [None, None, C.c_uint64(0), None, None, C.c_size_t(0), None]
+        assert fn(*args) == 1, name
