@@ -10,8 +10,13 @@ value = interior points solved per second (device-resident inputs); e2e =
 the same through the C ABI with the evaluation points copied in from pinned
 host memory and u, grad u copied out every step.
 
+--workload batched: sixteen 3D meshes of uneven size x 64 harmonic
+polynomial right-hand sides each (32768 samples x 128 walks, 65536 points
+per mesh); one step = one replay of a CUDA graph holding the whole batched
+solve; value = points x right-hand sides per second.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload star|circle|sphere] [--no-cpu-baseline] [--no-fixed-rmse]
+                  [--workload star|circle|sphere|batched] [--no-cpu-baseline] [--no-fixed-rmse]
 
 Under torchrun every rank solves its own replica (its own seeds); timing is
 bracketed by a barrier and the max over ranks is reported.
@@ -47,6 +52,11 @@ BYTES_NODE = {2: 48, 3: 64}
 BYTES_PRIM = {2: 32, 3: 48}
 FLOPS_PAIR_BND = {2: 25, 3: 37}
 FLOPS_PAIR_SRC = {2: 9, 3: 13}
+# batched right-hand sides: per (point, sample) pair and group of 32
+# right-hand sides, the kernel terms plus 2 FMA per right-hand side
+FLOPS_PAIR_MULTI = {2: 9 + 4 * 32, 3: 16 + 4 * 32}
+METRIC_BATCHED = "batched interior pts x right-hand sides/s (1 GB300)"
+UNIT_BATCHED = "pts x RHS/s"
 
 
 # ------------------------------------------------------------------ helpers
@@ -390,6 +400,213 @@ def reference_arm(args, w):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ batched meshes
+def monomials3(p):
+    """[m][35] monomials of degree <= 4 in the library's POLY order (p: [m][3])."""
+    from paper_2302_11825_gb300 import workloads as wl
+    import torch
+    cols = [p[:, 0] ** i * p[:, 1] ** j * p[:, 2] ** k for (i, j, k) in wl.poly_exponents(3)]
+    return torch.stack(cols, 1)
+
+
+def bench_batched(args, rank, local, ws):
+    """Sixteen meshes x 64 right-hand sides: the whole batch (sampling, walks,
+    moments, projection, gather) is one CUDA graph replayed once per step,
+    with the step's seed in a device word."""
+    import torch
+    from paper_2302_11825_gb300 import bvc
+    from paper_2302_11825_gb300 import workloads as wl
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    rank, ws = init_dist("nccl")
+    w = wl.batched_laplace()
+    t0 = time.perf_counter()
+    geoms = [bvc.Geometry(m[1], m[2]) for m in w.meshes]
+    batch = bvc.Batch([(g, w.n_samples, l, e, w.n_points) for g, l, e in zip(geoms, w.offset_l, w.eps)],
+                      w.walks, MAX_STEPS, w.k)
+    geometry_build_s = time.perf_counter() - t0
+    C = torch.tensor(w.coeffs, dtype=torch.float64, device=device)
+    pts_h = np.concatenate(w.pts).T.copy()
+    P = torch.tensor(pts_h, dtype=torch.float32, device=device)
+    seed_t = torch.zeros(1, dtype=torch.int64, device=device)
+    cache = batch.cache(device)
+    wsb = bvc.workspace(batch.workspace_size()[1])
+    u = torch.empty((w.k, batch.m_total), dtype=torch.float64, device=device)
+    M, K_rhs, n_meshes = batch.m_total, w.k, len(w.meshes)
+
+    # counting pass (same walks, node and primitive counters on)
+    batch.stats(reset=True)
+    batch.set_counting(True)
+    seed_t.fill_(rank_seed(rank, 0, 7))
+    batch.build(C, seed_t, cache, wsb)
+    torch.cuda.synchronize()
+    cstats = batch.stats(reset=True)
+    batch.set_counting(False)
+
+    # one eager, profiled step: the per-kernel breakdown
+    bvc.profile_begin()
+    batch.build(C, seed_t, cache, wsb)
+    batch.evaluate(cache, P, u)
+    prof = bvc.profile_end()
+    torch.cuda.synchronize()
+
+    # capture the whole step once
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        batch.build(C, seed_t, cache, wsb)
+        batch.evaluate(cache, P, u)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.build(C, seed_t, cache, wsb)
+        batch.evaluate(cache, P, u)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    for k in range(args.warmup):
+        seed_t.fill_(rank_seed(rank, k, 0))
+        graph.replay()
+    torch.cuda.synchronize()
+    batch.stats(reset=True)
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            seed_t.fill_(rank_seed(rank, k, 1_000_000))
+            evs[k][0].record()
+            graph.replay()
+            evs[k][1].record()
+        torch.cuda.synchronize()
+    barrier()
+    t_local = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    t_max = max_over_ranks(t_local, device)
+    clocks = clk.summary()
+    run_stats = batch.stats(reset=True)
+
+    # accuracy of the last step against the exact solutions (u = g_k)
+    rel = []
+    po = batch.point_offsets
+    for j in range(n_meshes):
+        ph = monomials3(P[:, po[j]:po[j + 1]].double().T)
+        ex = C[j] @ ph.T
+        err = u[:, po[j]:po[j + 1]] - ex
+        rel.append((err.square().mean(1).sqrt() / ex.square().mean(1).sqrt()).median().item())
+
+    # end to end through the public API with host buffers: points and
+    # coefficients in, every right-hand side's u out
+    P_h = torch.from_numpy(pts_h).pin_memory()
+    C_h = C.cpu().pin_memory()
+    u_h = torch.empty((w.k, M), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        P.copy_(P_h, non_blocking=True)
+        C.copy_(C_h, non_blocking=True)
+        batch.build(C, rank_seed(rank, k, 2_000_000), cache, wsb)
+        batch.evaluate(cache, P, u)
+        u_h.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, device)
+    assert np.all(np.isfinite(u_h[:, :1000].numpy()))
+
+    Kst = args.steps
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    total_ms = sum(v[1] for v in prof.values())
+    kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    n_walks = batch.n_total * w.walks
+    walk_b = cstats["nodes"] * BYTES_NODE[3] + cstats["prims"] * BYTES_PRIM[3] + n_walks * (2 * 3 * 4 + 4 * 4)
+    walk_ms = prof["walk"][1] + prof.get("first_hits", (0, 0.0))[1]
+    groups = (w.k + 31) // 32
+    pairs = sum(w.n_points * w.n_samples for _ in range(n_meshes))
+    gather_flops = pairs * groups * FLOPS_PAIR_MULTI[3]
+    g_ms = prof["gather_multi"][1]
+    walk_roof = {"bound": "hbm", "achieved": walk_b / (walk_ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]),
+                 "unit": "GB/s", "kernel": "walk", "traffic": profile_traffic("walk", w.name),
+                 "peak_source": f"{peak_src} (hbm_gbs)"}
+    walk_roof["frac"] = walk_roof["achieved"] / walk_roof["peak"]
+    gather_roof = {"bound": "alu", "achieved": gather_flops / (g_ms / 1e3) / 1e12, "peak": fp32_peak,
+                   "unit": "TFLOP/s", "kernel": "gather_multi", "traffic": profile_traffic("gather_multi", w.name),
+                   "peak_source": f"FP32 FMA peak = {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max} MHz"}
+    gather_roof["frac"] = gather_roof["achieved"] / fp32_peak
+    dominant = walk_roof if walk_ms >= g_ms else gather_roof
+    units = M * K_rhs
+    value = units * Kst * ws / t_max
+    out = {
+        "metric": METRIC_BATCHED, "value": value, "unit": UNIT_BATCHED, "n_gpus": ws, "steps": Kst,
+        "warmup": args.warmup, "ms_per_step": t_max / Kst * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "meshes": n_meshes,
+                   "triangles": [int(m[2].shape[0]) for m in w.meshes], "samples_per_mesh": w.n_samples,
+                   "walks_per_sample": w.walks, "points_per_mesh": w.n_points, "rhs_per_mesh": w.k,
+                   "graph": "one CUDA graph replay per step (seed in a device word)",
+                   "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}",
+                   "sums": "fp64"},
+        "roofline": dominant, "rooflines_all": {"walk": walk_roof, "gather_multi": gather_roof},
+        "kernels_eager_step": kernels,
+        "eager_step_ms": total_ms,
+        "walk_nodes_per_step": cstats["nodes"] / max(cstats["steps"], 1),
+        "walk_prims_per_step": cstats["prims"] / max(cstats["steps"], 1),
+        "wos_steps_per_s": run_stats["steps"] / max(walk_ms * Kst / 1e3, 1e-12),
+        "median_rel_rmse_vs_exact_per_mesh": rel,
+        "e2e": {"value": units * e2e_steps * ws / t_e2e, "unit": UNIT_BATCHED,
+                "h2d_bytes_per_step": int(P.numel() * 4 + C.numel() * 8),
+                "d2h_bytes_per_step": int(u.numel() * 8), "steps": e2e_steps},
+        "gpu_launches": int(sum(v[0] for v in prof.values())) * Kst,
+        "clocks": clocks, "geometry_build_s": geometry_build_s, "walk_caps": run_stats["capped"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = batched_oracle_rate(w)
+    if rank == 0:
+        print(json.dumps(out))
+    import torch.distributed as td
+    if td.is_initialized():
+        td.destroy_process_group()
+    return 0
+
+
+def batched_oracle_rate(w, budget_s: float = 20.0):
+    """The oracle as it stands has one right-hand side per solve: it is timed
+    on walks from 256 samples of the first mesh and a gather of 128 points
+    against one full-size mesh cache, and extrapolated to k solves per mesh."""
+    import oracle
+    V, F = w.meshes[0][1], w.meshes[0][2]
+    bvh = oracle.BVH(V, F)
+    z, _, _ = oracle.sample_boundary(V, F, 256, w.offset_l[0], 0)
+    g = [(1, w.coeffs[0, 0])]
+    ns = 16
+    while True:
+        t0 = time.perf_counter()
+        oracle.walks(bvh, g, [], z[:ns].astype(np.float32), w.walks, w.eps[0], MAX_STEPS, 0, 0, 0)
+        tw = time.perf_counter() - t0
+        if tw > budget_s / 3 or ns >= 256:
+            break
+        ns = min(256, ns * 4)
+    walk_rate = ns * w.walks / tw
+    N = w.n_samples
+    rng = np.random.default_rng(1)
+    zc = rng.standard_normal((N, 3)) * 0.5
+    nc = rng.standard_normal((N, 3))
+    nc /= np.linalg.norm(nc, axis=1, keepdims=True)
+    mp = 128
+    t0 = time.perf_counter()
+    oracle.gather(zc, nc, rng.standard_normal(N), rng.standard_normal(N), 1.0, w.pts[0][:mp].astype(np.float64))
+    pair_rate = mp * N / (time.perf_counter() - t0)
+    n_m = len(w.meshes)
+    t_step = w.k * n_m * (N * w.walks / walk_rate + w.n_points * N / pair_rate)
+    return {"value": n_m * w.n_points * w.k / t_step, "unit": UNIT_BATCHED, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{ns} samples x {w.walks} walks of mesh 0; {mp} points x {N} samples; "
+                                        f"extrapolated to {w.k} single-RHS solves of each of {n_m} meshes",
+            "walks_per_s": walk_rate, "pairs_per_s": pair_rate}
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -397,7 +614,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="star", choices=["star", "circle", "sphere"])
+    ap.add_argument("--workload", default="star", choices=["star", "circle", "sphere", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed-rmse", action="store_true")
     args = ap.parse_args()
@@ -407,10 +624,27 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
+        if args.workload == "batched":
+            from paper_2302_11825_gb300 import workloads as wl
+            wb = wl.batched_laplace()
+            rates = [batched_oracle_rate(wb, budget_s=6.0) for _ in range(args.warmup + args.steps)][args.warmup:]
+            val = statistics.mean(r["value"] for r in rates)
+            cb = dict(rates[-1], value=val)
+            print(json.dumps({"metric": METRIC_BATCHED, "value": val, "unit": UNIT_BATCHED, "n_gpus": 0,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": wb.k * len(wb.meshes) * wb.n_points / val * 1e3,
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                              "data": "synthetic", "impl": "reference", "config": {"workload": wb.name},
+                              "cpu_baseline": cb,
+                              "e2e": {"value": val, "unit": UNIT_BATCHED, "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}))
+            return 0
         w = make_workload(args.workload)
         print(json.dumps(reference_arm(args, w)))
         return 0
 
+    if args.workload == "batched":
+        return bench_batched(args, rank, local, ws)
     import torch
     from paper_2302_11825_gb300 import bvc
     torch.cuda.set_device(local)

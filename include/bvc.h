@@ -27,9 +27,10 @@
  *    bit-reproducible for a given seed and launch-independent.
  *  - The functions g and f are sums of closed-form terms (bvc_function);
  *    they stand in for the paper's callbacks (Sec. 4 "Setup").
- *  - Nothing here allocates device memory except bvc_geometry_create, which
- *    owns the BVH until bvc_geometry_destroy.  Scratch memory is passed in
- *    as a workspace; each *_workspace_size call says how much is needed.
+ *  - Nothing here allocates device memory except bvc_geometry_create and
+ *    bvc_batch_create, which own their BVHs until bvc_geometry_destroy /
+ *    bvc_batch_destroy.  Scratch memory is passed in as a workspace; each
+ *    *_workspace_size call says how much is needed.
  */
 #ifndef BVC_H_
 #define BVC_H_
@@ -360,13 +361,18 @@ typedef struct {
 bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t count, int32_t walks, int32_t max_steps,
                             int32_t k, bvc_stream stream, bvc_batch* out);
 bvc_status bvc_batch_destroy(bvc_batch b);
+/* Walk counters of the forest, as bvc_geometry_stats / _set_counting. */
+bvc_status bvc_batch_set_counting(bvc_batch b, int32_t on);
+bvc_status bvc_batch_stats(bvc_batch b, uint64_t out[8], int32_t reset, bvc_stream stream);
 /* n_total, m_total: sums of n_samples and n_points. */
 bvc_status bvc_batch_get_info(bvc_batch b, int32_t* dim, int64_t* n_total, int64_t* m_total);
 bvc_status bvc_batch_build_workspace_size(bvc_batch b, size_t* min_bytes, size_t* full_bytes);
 /* coeffs: device double[count][k][bvc_poly_terms(dim)]; cache: a
  * bvc_multi_cache with n = n_total and k = the batch's k (its bnd_measure
- * is left 0: each mesh's measure is held by the batch). */
-bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, uint64_t seed, bvc_multi_cache* cache,
+ * is left 0: each mesh's measure is held by the batch).  seed: a DEVICE
+ * uint64 read by the kernels when they run, so a captured graph replays
+ * with whatever seed the word holds at replay time. */
+bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, const uint64_t* seed, bvc_multi_cache* cache,
                            void* workspace, size_t workspace_bytes, bvc_stream stream);
 /* Re-project the stored moments onto new coefficients (no walks). */
 bvc_status bvc_batch_project(bvc_batch b, const double* coeffs, bvc_multi_cache* cache, bvc_stream stream);

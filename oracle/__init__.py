@@ -73,6 +73,8 @@ def _load():
                 "orc_boundary_measure": (f64, [C.c_int, P, P, i64]),
                 "orc_sample_boundary": (None, [C.c_int, P, P, i64, i64, f64, u64, P, P, P]),
                 "orc_walks": (None, [P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
+                "orc_walks_vg": (None, [P, P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
+                "orc_vertex_interp": (f64, [P, P, i64, P]),
                 "orc_reduce_walks": (None, [C.c_int, i64, i32, P, P, P, P, P]),
                 "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P]),
                 "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
@@ -228,9 +230,11 @@ def sphere_step(dim: int, R: float, u0: float, u1: float, u2: float):
 
 
 def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int, seed: int,
-          id_base: int = 0, tag: int = TAG_WALK, want_pend: bool = False):
+          id_base: int = 0, tag: int = TAG_WALK, want_pend: bool = False, g_vertex=None):
     """Sec. 3.1 / Eq. 7: W walks from each FP32 start point.
 
+    g_vertex: optional per-vertex values of g (then g_terms is ignored): g at
+    a boundary point is interpolated linearly on the closest element.
     Returns dict with per-walk U, grad[.., dim], steps, prim, scale[.., 2]
     (magnitudes of the terms forming U and the gradient, for error scaling)
     and, if asked, pend (final closest point)."""
@@ -242,14 +246,24 @@ def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int
     steps, prim = np.zeros(T, np.int32), np.zeros(T, np.int32)
     pend = np.zeros((T, dim)) if want_pend else None
     scale = np.zeros((T, 2))
-    g = encode_function(g_terms)
+    g = encode_function(g_terms if g_vertex is None else [])
     f = encode_function(f_terms)
-    lib.orc_walks(bvh.h, _p(g), _p(f), _p(starts), n, int(W), float(eps), int(max_steps), int(seed),
-                  int(id_base), int(tag), _p(U), _p(grad), _p(steps), _p(prim), _p(pend), _p(scale))
+    gv = None if g_vertex is None else _f64(g_vertex)
+    lib.orc_walks_vg(bvh.h, _p(g), _p(gv), _p(f), _p(starts), n, int(W), float(eps), int(max_steps), int(seed),
+                     int(id_base), int(tag), _p(U), _p(grad), _p(steps), _p(prim), _p(pend), _p(scale))
     out = {"U": U, "grad": grad, "steps": steps, "prim": prim, "scale": scale}
     if want_pend:
         out["pend"] = pend
     return out
+
+
+def vertex_interp(bvh: BVH, gv, elem, pts):
+    """g from vertex values at points lying on the given elements."""
+    lib = _load()
+    gv = _f64(gv)
+    pts = _f64(pts)
+    return np.array([lib.orc_vertex_interp(bvh.h, _p(gv), int(e), _p(np.ascontiguousarray(p)))
+                     for e, p in zip(elem, pts)])
 
 
 def reduce_walks(U, grad, nrm, W: int):

@@ -721,7 +721,45 @@ typedef struct {
   int max_steps;
   uint64_t seed;
   uint32_t tag;
+  const double* gv; /* vertex values of g, or NULL for the closed form g */
 } walk_ctx_t;
+
+/* Boundary data given by values at the mesh vertices: g at a point p of   */
+/* element e is the linear interpolation of its vertex values -- on a       */
+/* segment by the projection parameter t = (p-a).(b-a)/|b-a|^2 clamped to   */
+/* [0,1], on a triangle by the barycentric coordinates of p (p on the       */
+/* triangle's plane; Ericson, Real-Time Collision Detection, Sec. 3.4).     */
+double orc_vertex_interp(const void* bvh, const double* gv, int64_t e, const double* p) {
+  const mesh_t* m = &((const obvh_t*)bvh)->m;
+  const int32_t* f = m->F + e * m->dim;
+  if (m->dim == 2) {
+    const double* a = m->V + 2 * (int64_t)f[0];
+    const double* b = m->V + 2 * (int64_t)f[1];
+    const double abx = b[0] - a[0], aby = b[1] - a[1];
+    double t = ((p[0] - a[0]) * abx + (p[1] - a[1]) * aby) / (abx * abx + aby * aby);
+    t = fmin(fmax(t, 0.0), 1.0);
+    return (1.0 - t) * gv[f[0]] + t * gv[f[1]];
+  }
+  const double* a = m->V + 3 * (int64_t)f[0];
+  const double* b = m->V + 3 * (int64_t)f[1];
+  const double* c = m->V + 3 * (int64_t)f[2];
+  double v0[3], v1[3], v2[3];
+  for (int i = 0; i < 3; ++i) {
+    v0[i] = b[i] - a[i];
+    v1[i] = c[i] - a[i];
+    v2[i] = p[i] - a[i];
+  }
+  const double d00 = dot3d(v0, v0), d01 = dot3d(v0, v1), d11 = dot3d(v1, v1);
+  const double d20 = dot3d(v2, v0), d21 = dot3d(v2, v1);
+  const double den = d00 * d11 - d01 * d01;
+  const double bv = (d11 * d20 - d01 * d21) / den;
+  const double bw = (d00 * d21 - d01 * d20) / den;
+  return (1.0 - bv - bw) * gv[f[0]] + bv * gv[f[1]] + bw * gv[f[2]];
+}
+
+static double g_at(const walk_ctx_t* w, const double* p, int64_t e) {
+  return w->gv ? orc_vertex_interp(w->bvh, w->gv, e, p) : orc_fn_eval(w->g, w->bvh->m.dim, p);
+}
 
 /* One sphere step: direction w from (u0,u1) and, for radius R, the source  */
 /* point radius rho = R u2 with its weights w_u and the scalar w_g such     */
@@ -756,7 +794,7 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
   for (;;) {
     const double d = sqrt(bvh_closest(w->bvh, x, pbar, &prim));
     ++k;
-    if (k == 1) cv = orc_fn_eval(w->g, dim, pbar);
+    if (k == 1) cv = g_at(w, pbar, prim);
     if (d < w->eps || k >= w->max_steps) break;
     const double R = d;
     double u[4];
@@ -780,7 +818,7 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
     }
     for (int a = 0; a < dim; ++a) x[a] += R * om[a];
   }
-  const double gend = orc_fn_eval(w->g, dim, pbar);
+  const double gend = g_at(w, pbar, prim);
   const double U = gend + usrc;
   *U_out = U;
   /* magnitudes of the terms that form U and the gradient (test scaling only) */
@@ -803,10 +841,10 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
 /* W walks from each of n start points; walk j of start i has id            */
 /* id_base + i*W + j.  Outputs are per walk: U[n*W], grad[n*W*dim],         */
 /* steps[n*W], prim[n*W], pend[n*W*dim] (pend may be NULL).                  */
-void orc_walks(void* bvh, const double* g, const double* f, const float* starts, int64_t n, int32_t W, double eps,
-               int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
-               int32_t* steps, int32_t* prim, double* pend, double* scale) {
-  walk_ctx_t w = {(const obvh_t*)bvh, g, f, eps, max_steps, seed, tag};
+void orc_walks_vg(void* bvh, const double* g, const double* gv, const double* f, const float* starts, int64_t n,
+                  int32_t W, double eps, int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U,
+                  double* grad, int32_t* steps, int32_t* prim, double* pend, double* scale) {
+  walk_ctx_t w = {(const obvh_t*)bvh, g, f, eps, max_steps, seed, tag, gv};
   const int dim = w.bvh->m.dim;
   const int64_t total = n * (int64_t)W;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -817,6 +855,13 @@ void orc_walks(void* bvh, const double* g, const double* f, const float* starts,
     walk_one(&w, x0, id_base + (uint64_t)t, &U[t], &grad[t * dim], &steps[t], &prim[t],
              pend ? &pend[t * dim] : NULL, scale ? &scale[2 * t] : NULL);
   }
+}
+
+/* The same with closed-form boundary data g (no vertex values).           */
+void orc_walks(void* bvh, const double* g, const double* f, const float* starts, int64_t n, int32_t W, double eps,
+               int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
+               int32_t* steps, int32_t* prim, double* pend, double* scale) {
+  orc_walks_vg(bvh, g, NULL, f, starts, n, W, eps, max_steps, seed, id_base, tag, U, grad, steps, prim, pend, scale);
 }
 
 /* Per-sample means over the W walks of each start (Alg. 1: the pointwise   */

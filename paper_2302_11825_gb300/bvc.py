@@ -124,7 +124,9 @@ def _declare(lib):
         "bvc_batch_destroy": (S, [P]),
         "bvc_batch_get_info": (S, [P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "bvc_batch_build_workspace_size": (S, [P, C.POINTER(sz), C.POINTER(sz)]),
-        "bvc_batch_build": (S, [P, P, u64, C.POINTER(MultiCacheStruct), P, sz, P]),
+        "bvc_batch_build": (S, [P, P, P, C.POINTER(MultiCacheStruct), P, sz, P]),
+        "bvc_batch_set_counting": (S, [P, i32]),
+        "bvc_batch_stats": (S, [P, C.POINTER(C.c_uint64), i32, P]),
         "bvc_batch_project": (S, [P, P, C.POINTER(MultiCacheStruct), P]),
         "bvc_batch_evaluate": (S, [P, C.POINTER(MultiCacheStruct), P, P, P]),
         "bvc_profile_begin": (S, []),
@@ -576,16 +578,37 @@ class Batch:
     def cache(self, device="cuda") -> MultiCache:
         return MultiCache(self.dim, self.n_total, self.k, device)
 
-    def build(self, coeffs: torch.Tensor, seed: int, cache: MultiCache, ws: torch.Tensor = None, stream=None):
-        """coeffs: CUDA float64 [meshes][k][poly_terms(dim)]."""
+    def build(self, coeffs: torch.Tensor, seed, cache: MultiCache, ws: torch.Tensor = None, stream=None):
+        """coeffs: CUDA float64 [meshes][k][poly_terms(dim)].  seed: an int,
+        or a CUDA int64 tensor of one element read when the kernels run (a
+        captured graph then replays with the value it holds)."""
         _dev(coeffs, torch.float64)
         if tuple(coeffs.shape) != (len(self.geoms), self.k, poly_terms(self.dim)):
             raise ValueError("coefficients must be [meshes][k][poly_terms(dim)]")
+        if isinstance(seed, torch.Tensor):
+            _dev(seed, torch.int64)
+            if seed.numel() != 1:
+                raise ValueError("seed tensor must hold one element")
+            seed_t = seed
+        else:
+            if not hasattr(self, "_seed"):
+                self._seed = torch.zeros(1, dtype=torch.int64, device=coeffs.device)
+            self._seed.fill_(int(seed))
+            seed_t = self._seed
         if ws is None:
             ws = workspace(self.workspace_size()[1])
-        _check(lib().bvc_batch_build(self.h, _ptr(coeffs), int(seed), C.byref(cache.struct), _ptr(ws), ws.numel(),
-                                     _stream(stream)), "bvc_batch_build")
+        _check(lib().bvc_batch_build(self.h, _ptr(coeffs), _ptr(seed_t), C.byref(cache.struct), _ptr(ws),
+                                     ws.numel(), _stream(stream)), "bvc_batch_build")
         return cache
+
+    def set_counting(self, on: bool):
+        _check(lib().bvc_batch_set_counting(self.h, 1 if on else 0), "bvc_batch_set_counting")
+
+    def stats(self, reset=False, stream=None):
+        out = (C.c_uint64 * 8)()
+        st = lib().bvc_batch_stats(self.h, out, 1 if reset else 0, _stream(stream))
+        _check(st, "bvc_batch_stats", allow=(OK, WARN_WALK_CAP))
+        return {"steps": out[0], "capped": out[1], "flags": out[2], "nodes": out[4], "prims": out[5]}
 
     def project(self, coeffs: torch.Tensor, cache: MultiCache, stream=None):
         _dev(coeffs, torch.float64)

@@ -163,6 +163,25 @@ extern "C" bvc_status bvc_batch_destroy(bvc_batch b) {
   return e == cudaSuccess ? BVC_OK : BVC_ERR_CUDA;
 }
 
+extern "C" bvc_status bvc_batch_set_counting(bvc_batch b, int32_t on) {
+  if (b == nullptr) return BVC_ERR_INVALID_ARG;
+  b->counting = on ? 1 : 0;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_batch_stats(bvc_batch b, uint64_t out[8], int32_t reset, bvc_stream stream) {
+  if (b == nullptr || out == nullptr) return BVC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h[8];
+  BVC_CUDA_TRY(cudaMemcpyAsync(h, b->forest.stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  if (reset) BVC_CUDA_TRY(cudaMemsetAsync(b->forest.stats, 0, sizeof(h), s));
+  BVC_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < 8; ++i) out[i] = h[i];
+  if (h[kStatFlags] & kFlagTimeout) return BVC_ERR_TIMEOUT;
+  if (h[kStatCapped]) return BVC_WARN_WALK_CAP;
+  return BVC_OK;
+}
+
 extern "C" bvc_status bvc_batch_get_info(bvc_batch b, int32_t* dim, int64_t* n_total, int64_t* m_total) {
   if (b == nullptr) return BVC_ERR_INVALID_ARG;
   if (dim) *dim = b->dim;

@@ -656,6 +656,11 @@ namespace bvc {
 
 constexpr int kMG = BVC_MULTI_GROUP;
 constexpr int kMTile = 32;
+// FP32 partial sums cover kMFlush tiles (128 samples) before they are added
+// to the FP64 sums: GB300's FP64 pipe runs at 1/64 of the FP32 rate, and one
+// FP64 add per right-hand side every 32 samples would occupy it almost as
+// long as the FP32 work itself.
+constexpr int kMFlush = 4;
 constexpr int kMStride = 8 + 2 * kMG;  // floats per packed sample row
 
 // One mesh (meshes == null): m points [D][m] against n samples.  A batch:
@@ -724,8 +729,10 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
       return;
     }
     const int cnt = (int)min64(kMTile, n_smp - it * kMTile);
+    if (it % kMFlush == 0) {
 #pragma unroll
-    for (int q = 0; q < kMG; ++q) acc[q] = 0.0f;
+      for (int q = 0; q < kMG; ++q) acc[q] = 0.0f;
+    }
     const float4* T = reinterpret_cast<const float4*>(tile[b]);
     for (int s = 0; s < cnt; ++s) {
       const float4* row = T + s * (kMStride / 4);
@@ -752,8 +759,10 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
         acc[4 * q + 3] = fmaf(b4.w, k2, fmaf(a4.w, k1, acc[4 * q + 3]));
       }
     }
+    if (it % kMFlush == kMFlush - 1 || it == nt - 1) {
 #pragma unroll
-    for (int q = 0; q < kMG; ++q) acc64[q] += (double)acc[q];
+      for (int q = 0; q < kMG; ++q) acc64[q] += (double)acc[q];
+    }
     __syncthreads();
     if (threadIdx.x == 0 && it + 2 < nt) {
       fence_proxy_async();

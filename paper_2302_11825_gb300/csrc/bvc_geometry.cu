@@ -65,10 +65,11 @@ __global__ void __launch_bounds__(128) k_query_closest(DevGeometry G, const floa
 template <int D>
 __global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t n, double l, uint64_t seed,
                                                          float* __restrict__ z, float* __restrict__ nrm,
-                                                         int32_t* __restrict__ elem, int64_t stride) {
+                                                         int32_t* __restrict__ elem, int64_t stride,
+                                                         const uint64_t* __restrict__ seed_dev) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const U4 r = philox_draw(seed, (uint64_t)i, 0u, 1u);
+  const U4 r = philox_draw(seed_dev ? *seed_dev : seed, (uint64_t)i, 0u, 1u);
   const double u0 = u01d(r.x), u1 = u01d(r.y), u2 = u01d(r.z);
   const int64_t np = G.n_prims;
   const double total = G.cdf[np];
@@ -303,14 +304,14 @@ namespace bvc {
 // K1 into planes of `stride` floats (a batch writes each mesh's samples into
 // its range of the batch's sample planes).
 bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
-                                  int32_t* elem, int64_t stride, cudaStream_t s) {
+                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev) {
   if (n == 0) return BVC_OK;
   const int grid = (int)((n + 255) / 256);
   ProfScope ps("sample_boundary", s);
   if (g->dim == 2)
-    k_sample_boundary<2><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride);
+    k_sample_boundary<2><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev);
   else
-    k_sample_boundary<3><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride);
+    k_sample_boundary<3><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -320,5 +321,5 @@ extern "C" bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, u
                                           int32_t* elem, bvc_stream stream) {
   if (g == nullptr || n < 0 || (n > 0 && (z == nullptr || nrm == nullptr)) || !std::isfinite(l))
     return BVC_ERR_INVALID_ARG;
-  return launch_sample_boundary(g, n, l, seed, z, nrm, elem, n, (cudaStream_t)stream);
+  return launch_sample_boundary(g, n, l, seed, z, nrm, elem, n, (cudaStream_t)stream, nullptr);
 }

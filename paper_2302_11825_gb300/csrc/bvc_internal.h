@@ -62,6 +62,7 @@ constexpr unsigned long long kFlagTimeout = 1ull;
 
 struct bvc_batch_s {
   int32_t dim, count, walks, max_steps, k;
+  int32_t counting;
   int64_t n_total, m_total, blocks_total;
   std::vector<bvc::BatchMeshDev> mesh;  // host copy of the table
   std::vector<double> offset_l;
@@ -89,8 +90,10 @@ namespace bvc {
 // Host helpers (bvc_common.cu)
 bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);
 int num_sms();
+// seed_dev: when non-null, the seed is read from this device word at run
+// time (a captured CUDA graph replays with the seed it holds then).
 bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
-                                  int32_t* elem, int64_t stride, cudaStream_t s);
+                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev);
 int max_blocks_per_sm(const void* kernel, int block, size_t smem);
 
 // Kernel timing: while bvc_profile_begin .. bvc_profile_end is active, every

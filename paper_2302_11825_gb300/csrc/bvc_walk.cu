@@ -64,6 +64,8 @@ struct WalkParams {
   // meshes' roots and shells; null for one mesh (root 0, shell eps).
   const int32_t* sample_mesh;
   const BatchMeshDev* meshes;
+  // kRecEnd walks: when non-null the seed is read from this device word.
+  const uint64_t* seed_dev;
 };
 
 // The first query of each start of a launch, once per start.
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
           phase = kIdle;
         } else {
           const float R = d;
-          const U4 r = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
+          const uint64_t seed = (REC == kRecEnd && P.seed_dev != nullptr) ? __ldg(P.seed_dev) : P.seed;
+          const U4 r = philox_draw(seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
           const float u0 = u01f(r.x);
           float om[D];
           if (D == 2) {
@@ -919,6 +922,7 @@ struct EndWalks {
   uint64_t seed, wid_base;
   const int32_t* sample_mesh;
   const BatchMeshDev* meshes;
+  const uint64_t* seed_dev;
 };
 
 static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void* workspace, int64_t chunk,
@@ -938,6 +942,7 @@ static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void*
   P.counter = (unsigned long long*)workspace;
   P.sample_mesh = E.sample_mesh;
   P.meshes = E.meshes;
+  P.seed_dev = E.seed_dev;
   for (int64_t i0 = 0; i0 < N; i0 += chunk) {
     const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
     P.i0 = i0;
@@ -1029,9 +1034,10 @@ extern "C" bvc_status bvc_batch_build_workspace_size(bvc_batch b, size_t* min_by
   return BVC_OK;
 }
 
-extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, uint64_t seed, bvc_multi_cache* cache,
+extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, const uint64_t* seed, bvc_multi_cache* cache,
                                       void* workspace, size_t workspace_bytes, bvc_stream stream) {
-  if (coeffs == nullptr || workspace == nullptr || !valid_batch_cache(b, cache)) return BVC_ERR_INVALID_ARG;
+  if (coeffs == nullptr || seed == nullptr || workspace == nullptr || !valid_batch_cache(b, cache))
+    return BVC_ERR_INVALID_ARG;
   const size_t per = ws_per_start(b->dim, b->walks, b->dim);
   int64_t chunk = ws_chunk(workspace_bytes, per);
   if (chunk < 1) return BVC_ERR_WORKSPACE;
@@ -1040,18 +1046,19 @@ extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, uint64_
   cache->bnd_measure = 0.0;
   for (int j = 0; j < b->count; ++j) {
     const BatchMeshDev& m = b->mesh[j];
-    const bvc_status st = launch_sample_boundary(b->geoms[j], m.n_smp, b->offset_l[j], seed, cache->z + m.smp_off,
-                                                 cache->nrm + m.smp_off, nullptr, b->n_total, s);
+    const bvc_status st = launch_sample_boundary(b->geoms[j], m.n_smp, b->offset_l[j], 0, cache->z + m.smp_off,
+                                                 cache->nrm + m.smp_off, nullptr, b->n_total, s, seed);
     if (st != BVC_OK) return st;
   }
   EndWalks E{};
   E.G = b->forest;
   E.dim = b->dim;
-  E.counting = false;
+  E.counting = b->counting != 0;
   E.W = b->walks;
   E.eps = b->mesh[0].eps;
   E.max_steps = b->max_steps;
-  E.seed = seed;
+  E.seed = 0;
+  E.seed_dev = seed;
   E.wid_base = 0;
   E.sample_mesh = b->sample_mesh;
   E.meshes = b->table;

@@ -479,3 +479,34 @@ def random_points_in(shape, n: int, seed: int) -> np.ndarray:
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     r = rng.uniform(size=n) ** (1.0 / 3.0) * 0.98
     return (c[None, :] + d * r[:, None] * a[None, :]).astype(np.float32)
+
+
+@dataclass
+class BatchedWorkload:
+    """Independent 3D Laplace problems on meshes of uneven size, each with k
+    random harmonic polynomial Dirichlet data (their own exact solutions)."""
+    name: str
+    meshes: list            # (name, V, F, shape) per mesh
+    n_samples: int          # boundary samples per mesh
+    walks: int
+    n_points: int           # evaluation points per mesh
+    k: int                  # right-hand sides per mesh
+    coeffs: np.ndarray      # [meshes][k][35] monomial coefficients
+    pts: list               # [n_points][3] float32 per mesh
+    eps: list               # shell per mesh: 1e-3 x bbox diagonal
+    offset_l: list          # 5 eps
+
+
+def batched_laplace(n_meshes: int = 16, n_samples: int = 32768, walks: int = 128, n_points: int = 65536,
+                    k: int = 64, seed: int = 0) -> BatchedWorkload:
+    """16 perturbed icospheres, ellipsoids and unions of two disjoint
+    ellipsoids (20k to 330k triangles) x 64 harmonic polynomials of degree
+    <= 4; 32k boundary samples x 128 walks and 64k uniform interior points
+    per mesh.  The walk count is not fixed by the batched configuration: it
+    takes the 128 of the single 3D configuration."""
+    meshes = batched_meshes(n_meshes, seed)
+    coeffs = np.stack([random_harmonic_polys(3, k, seed=1000 + seed + j) for j in range(n_meshes)])
+    pts = [random_points_in(m[3], n_points, seed=2000 + seed + j) for j, m in enumerate(meshes)]
+    eps = [1e-3 * bbox_diagonal(m[1]) for m in meshes]
+    return BatchedWorkload(f"batched{n_meshes}_laplace_k{k}", meshes, n_samples, walks, n_points, k, coeffs, pts,
+                           eps, [5.0 * e for e in eps])

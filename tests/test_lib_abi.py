@@ -150,10 +150,11 @@ def test_batch_host_checks(lib):
     assert lib.bvc_batch_create(None, 1, 4, 10, 1, None, C.byref(h)) == 1
     assert lib.bvc_batch_create(None, 0, 4, 10, 1, None, None) == 1
     for name, nargs in (("bvc_batch_destroy", 1), ("bvc_batch_get_info", 4), ("bvc_batch_build_workspace_size", 3),
-                        ("bvc_batch_build", 7), ("bvc_batch_project", 4), ("bvc_batch_evaluate", 5)):
+                        ("bvc_batch_build", 7), ("bvc_batch_project", 4), ("bvc_batch_evaluate", 5),
+                        ("bvc_batch_set_counting", 2), ("bvc_batch_stats", 4)):
         fn = getattr(lib, name)
         fn.restype = C.c_int
         args = [None] * nargs
         if name == "bvc_batch_build":
-            args = [None, None, C.c_uint64(0), None, None, C.c_size_t(0), None]
+            args = [None, None, None, None, None, C.c_size_t(0), None]
         assert fn(*args) == 1, name
