@@ -290,6 +290,49 @@ bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_funct
  * out).  Synchronises the device; reset != 0 clears it. */
 bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
 
+/* ------------------------------------------------------ differentiation */
+/* Gradients of a loss L of the values u(x) that bvc_evaluate gives (Eq. 3)
+ * with respect to the boundary data and the source.  The parameters are
+ *   - g as values at the mesh vertices (device float[n_verts]), interpolated
+ *     linearly on the element holding a walk's closest point (segment:
+ *     projection parameter; triangle: barycentric coordinates), and
+ *   - the amplitudes A_k of f when f is one BVC_FN_GAUSS or
+ *     BVC_FN_GAUSS_LAPLACIAN term of at most 8 bumps (f = sum_k A_k psi_k).
+ * With fixed seeds the walks' paths depend on neither, and every estimate
+ * (U, n.grad per walk; u^, du/dn^ per sample; the source weights c; u(x)) is
+ * linear in both, so the gradient is exact for the estimator: the adjoint
+ * of the gather gives dL/du^, dL/d(du/dn^) and dL/dc per sample
+ * (bvc_evaluate_adjoint), and the adjoint of the cache build replays each
+ * walk from its Philox stream and adds its weights to the vertices of the
+ * elements where it ends and starts and to the amplitudes
+ * (bvc_cache_adjoint).  Gradient sums are FP64; vertex gradients are
+ * accumulated with FP64 atomics (order-dependent in the last bits). */
+
+/* bvc_cache_build with g given by vertex values (device float[n_verts]). */
+bvc_status bvc_cache_build_vg(bvc_geometry g, const float* g_vertex, const bvc_function* ffn,
+                              const bvc_cache_opts* opts, bvc_cache* cache, void* workspace, size_t workspace_bytes,
+                              bvc_stream stream);
+bvc_status bvc_evaluate_adjoint_workspace_size(int64_t m, size_t* bytes);
+/* lam: device double[m], dL/du at the points pts (device [dim][m]) of one
+ * bvc_evaluate of this cache (one cache per evaluation state, so u = sums /
+ * (n, n_src_cand)).  Writes adj_u, adj_q (device double[n]) and, if
+ * adj_src is non-NULL and the cache has source candidates, adj_src (device
+ * double[n_src_cand], zero past the kept ones). */
+bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* pts, int64_t m, const double* lam,
+                                double* adj_u, double* adj_q, double* adj_src, void* workspace,
+                                size_t workspace_bytes, bvc_stream stream);
+bvc_status bvc_cache_adjoint_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+                                            size_t* full_bytes);
+/* Adds dL/dg_vertex into grad_gv (device double[n_verts]) and dL/dA into
+ * grad_amp (device double[8], used when f has a term) for the cache built by
+ * bvc_cache_build_vg with the same geometry, f, opts (seed, ids) -- its
+ * samples z, n are read from `cache`.  adj_src may be NULL (no source
+ * cache).  BVC_ERR_UNSUPPORTED if f is not of the differentiable form. */
+bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache_opts* opts,
+                             const bvc_cache* cache, const double* adj_u, const double* adj_q, const double* adj_src,
+                             double* grad_gv, double* grad_amp, void* workspace, size_t workspace_bytes,
+                             bvc_stream stream);
+
 /* ---------------------------------------------- many right-hand sides */
 /* Batching of right-hand sides for the Laplace equation (f = 0): K
  * Dirichlet data g_k = sum_m C[k][m] phi_m over the BVC_FN_POLY monomials

@@ -105,6 +105,13 @@ def _declare(lib):
         "bvc_cache_build_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz), C.POINTER(sz)]),
         "bvc_cache_build": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(CacheOpts),
                                 C.POINTER(CacheStruct), P, sz, P]),
+        "bvc_cache_build_vg": (S, [P, P, C.POINTER(Function), C.POINTER(CacheOpts), C.POINTER(CacheStruct), P, sz,
+                                   P]),
+        "bvc_evaluate_adjoint_workspace_size": (S, [i64, C.POINTER(sz)]),
+        "bvc_evaluate_adjoint": (S, [C.POINTER(CacheStruct), P, i64, P, P, P, P, P, sz, P]),
+        "bvc_cache_adjoint_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz), C.POINTER(sz)]),
+        "bvc_cache_adjoint": (S, [P, C.POINTER(Function), C.POINTER(CacheOpts), C.POINTER(CacheStruct), P, P, P, P,
+                                  P, P, sz, P]),
         "bvc_evaluate_workspace_size": (S, [C.POINTER(CacheStruct), C.POINTER(EvalStateStruct), C.POINTER(sz)]),
         "bvc_evaluate": (S, [C.POINTER(CacheStruct), C.POINTER(EvalStateStruct), P, sz, P]),
         "bvc_get_solution": (S, [C.POINTER(EvalStateStruct), P, P, P]),
@@ -434,6 +441,124 @@ def evaluate(cache: Cache, state: EvalState, ws: torch.Tensor = None, stream=Non
         ws = workspace(evaluate_workspace_size(cache, state))
     _check(lib().bvc_evaluate(C.byref(cache.struct), C.byref(state.struct), _ptr(ws), ws.numel(), _stream(stream)),
            "bvc_evaluate")
+
+
+# ---------------------------------------------------------------- differentiation
+def cache_build_vg(geom: Geometry, g_vertex: torch.Tensor, f_terms, opts: CacheOpts, cache: Cache,
+                   ws: torch.Tensor = None, stream=None):
+    """bvc_cache_build_vg: g from vertex values (CUDA float32 [n_verts])."""
+    _dev(g_vertex, torch.float32)
+    if ws is None:
+        ws = workspace(cache_build_workspace_size(geom, opts)[1])
+    f = make_function(f_terms)
+    _check(lib().bvc_cache_build_vg(geom.h, _ptr(g_vertex), C.byref(f), C.byref(opts), C.byref(cache.struct),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "bvc_cache_build_vg")
+    return cache
+
+
+def evaluate_adjoint(cache: Cache, pts: torch.Tensor, lam: torch.Tensor, stream=None):
+    """dL/du^, dL/d(du/dn^) per boundary sample and dL/dc per source
+    candidate from lam = dL/du at the points (CUDA float64 [m])."""
+    _dev(pts, torch.float32)
+    _dev(lam, torch.float64)
+    m = pts.shape[1]
+    nb = C.c_size_t()
+    _check(lib().bvc_evaluate_adjoint_workspace_size(m, C.byref(nb)), "bvc_evaluate_adjoint_workspace_size")
+    ws = workspace(nb.value)
+    dev = pts.device
+    adj_u = torch.empty(cache.n, dtype=torch.float64, device=dev)
+    adj_q = torch.empty(cache.n, dtype=torch.float64, device=dev)
+    adj_s = torch.zeros(max(cache.n_src_cand, 1), dtype=torch.float64, device=dev) if cache.n_src_cand else None
+    _check(lib().bvc_evaluate_adjoint(C.byref(cache.struct), _ptr(pts), m, _ptr(lam), _ptr(adj_u), _ptr(adj_q),
+                                      _ptr(adj_s), _ptr(ws), ws.numel(), _stream(stream)), "bvc_evaluate_adjoint")
+    return adj_u, adj_q, adj_s
+
+
+def cache_adjoint(geom: Geometry, f_terms, opts: CacheOpts, cache: Cache, adj_u, adj_q, adj_s, grad_gv: torch.Tensor,
+                  grad_amp: torch.Tensor, ws: torch.Tensor = None, stream=None):
+    """Adds dL/dg_vertex and dL/dA (FP64) by replaying the cache walks."""
+    _dev(grad_gv, torch.float64)
+    _dev(grad_amp, torch.float64)
+    if grad_amp.numel() < 8:
+        raise ValueError("grad_amp must hold 8 entries")
+    if ws is None:
+        mn, full = C.c_size_t(), C.c_size_t()
+        _check(lib().bvc_cache_adjoint_workspace_size(geom.h, C.byref(opts), C.byref(mn), C.byref(full)),
+               "bvc_cache_adjoint_workspace_size")
+        ws = workspace(full.value)
+    f = make_function(f_terms)
+    _check(lib().bvc_cache_adjoint(geom.h, C.byref(f), C.byref(opts), C.byref(cache.struct), _ptr(adj_u),
+                                   _ptr(adj_q), _ptr(adj_s), _ptr(grad_gv), _ptr(grad_amp), _ptr(ws), ws.numel(),
+                                   _stream(stream)), "bvc_cache_adjoint")
+
+
+def bump_terms(kind: int, sigma: float, centres, amps) -> list:
+    """One GAUSS / GAUSS_LAPLACIAN term [s, A_1, c_1, A_2, c_2, ...]."""
+    co = [float(sigma)]
+    for a, c in zip(amps, centres):
+        co.append(float(a))
+        co.extend(float(v) for v in c)
+    return [(kind, co)]
+
+
+class _Solve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, g_vertex, amps, solver):
+        cache = solver._forward(g_vertex, amps)
+        ctx.solver, ctx.cache = solver, cache
+        ctx.amps = amps.detach().cpu().numpy()
+        return solver._u
+
+    @staticmethod
+    def backward(ctx, lam):
+        s = ctx.solver
+        gg, ga = s._backward(ctx.cache, ctx.amps, lam.contiguous().double())
+        return gg, ga[:len(ctx.amps)], None
+
+
+class DiffSolver:
+    """u at fixed interior points as a differentiable function of the vertex
+    values of g and the bump amplitudes of f, with fixed seeds (BVC forward:
+    bvc_cache_build_vg + bvc_evaluate; backward: bvc_evaluate_adjoint +
+    bvc_cache_adjoint).  bumps: (kind, sigma, centres [nb][dim]) or None."""
+
+    def __init__(self, geom: Geometry, pts: torch.Tensor, n_samples: int, walks: int, offset_l: float, eps: float,
+                 seed: int, bumps=None, src_grid=(0, 0), max_steps: int = 1 << 14):
+        self.geom, self.pts = geom, pts
+        self.dim = geom.dim
+        self.bumps = bumps
+        self.opts = cache_opts(n_samples, walks, offset_l, eps, seed, max_steps=max_steps,
+                               src_grid=src_grid if bumps else (0, 0))
+        self.n_src = self.opts.src_grid[0] * self.opts.src_grid[1]
+        self.ws = workspace(cache_build_workspace_size(geom, self.opts)[1])
+        self.n_verts = geom.info().n_verts
+
+    def _f_terms(self, amps):
+        if not self.bumps:
+            return []
+        kind, sigma, centres = self.bumps
+        return bump_terms(kind, sigma, centres, amps)
+
+    def _forward(self, g_vertex, amps):
+        cache = Cache(self.dim, self.opts.n_samples, n_src_cand=self.n_src)
+        f = self._f_terms(amps.detach().cpu().numpy() if amps is not None else [])
+        cache_build_vg(self.geom, g_vertex.detach().float().contiguous(), f, self.opts, cache, self.ws)
+        st = EvalState(self.pts, grad=False)
+        evaluate(cache, st)
+        self._u, _ = get_solution(st)
+        return cache
+
+    def _backward(self, cache, amps, lam):
+        adj_u, adj_q, adj_s = evaluate_adjoint(cache, self.pts, lam)
+        gg = torch.zeros(self.n_verts, dtype=torch.float64, device=lam.device)
+        ga = torch.zeros(8, dtype=torch.float64, device=lam.device)
+        cache_adjoint(self.geom, self._f_terms(amps), self.opts, cache, adj_u, adj_q, adj_s, gg, ga)
+        return gg, ga
+
+    def __call__(self, g_vertex: torch.Tensor, amps: torch.Tensor = None):
+        if amps is None:
+            amps = torch.zeros(0, dtype=torch.float64, device=g_vertex.device)
+        return _Solve.apply(g_vertex, amps, self)
 
 
 def get_solution(state: EvalState, u=None, grad=None, stream=None):

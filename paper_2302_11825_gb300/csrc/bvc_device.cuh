@@ -138,6 +138,84 @@ __device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) 
   return v;
 }
 
+// Boundary data from vertex values (the differentiable parameterisation of
+// g): at a point p of element e (caller numbering), g is the linear
+// interpolation of the element's vertex values -- segment: projection
+// parameter t = (p-a).(b-a)/|b-a|^2 clamped to [0,1]; triangle: barycentric
+// coordinates of p.  Returns the vertex ids and their weights.
+template <int D>
+__device__ __forceinline__ void vertex_weights(const DevGeometry& G, int32_t e, const float* p, int32_t* vid,
+                                               float* w) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) vid[a] = __ldg(&G.idx[(int64_t)e * D + a]);
+  if (D == 2) {
+    const float ax = __ldg(&G.verts[2 * (int64_t)vid[0]]), ay = __ldg(&G.verts[2 * (int64_t)vid[0] + 1]);
+    const float abx = __ldg(&G.verts[2 * (int64_t)vid[1]]) - ax, aby = __ldg(&G.verts[2 * (int64_t)vid[1] + 1]) - ay;
+    float t = fmaf(p[1] - ay, aby, (p[0] - ax) * abx) / fmaf(aby, aby, abx * abx);
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    w[0] = 1.0f - t;
+    w[D - 1] = t;
+  } else {
+    float v0[3], v1[3], v2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float o = __ldg(&G.verts[3 * (int64_t)vid[0] + a]);
+      v0[a] = __ldg(&G.verts[3 * (int64_t)vid[1 % D] + a]) - o;
+      v1[a] = __ldg(&G.verts[3 * (int64_t)vid[2 % D] + a]) - o;
+      v2[a] = p[a % D] - o;
+    }
+    const float d00 = fmaf(v0[2], v0[2], fmaf(v0[1], v0[1], v0[0] * v0[0]));
+    const float d01 = fmaf(v0[2], v1[2], fmaf(v0[1], v1[1], v0[0] * v1[0]));
+    const float d11 = fmaf(v1[2], v1[2], fmaf(v1[1], v1[1], v1[0] * v1[0]));
+    const float d20 = fmaf(v2[2], v0[2], fmaf(v2[1], v0[1], v2[0] * v0[0]));
+    const float d21 = fmaf(v2[2], v1[2], fmaf(v2[1], v1[1], v2[0] * v1[0]));
+    const float inv = 1.0f / fmaf(d00, d11, -d01 * d01);
+    const float bv = fmaf(d11, d20, -d01 * d21) * inv, bw = fmaf(d00, d21, -d01 * d20) * inv;
+    w[0] = 1.0f - bv - bw;
+    w[1 % D] = bv;
+    w[2 % D] = bw;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ float vertex_g(const DevGeometry& G, const float* __restrict__ gv, int32_t e,
+                                          const float* p) {
+  int32_t vid[D];
+  float w[D];
+  vertex_weights<D>(G, e, p, vid, w);
+  float v = 0.0f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) v = fmaf(w[a], __ldg(&gv[vid[a]]), v);
+  return v;
+}
+
+// Shape functions of the bumps of a one-term GAUSS or GAUSS_LAPLACIAN
+// source (f = sum_k A_k psi_k): psi_k(y) for k < kMaxBumps.
+constexpr int kMaxBumps = 8;
+template <int D>
+__device__ __forceinline__ void bump_shapes(const DevFunction& fn, const float* y, float* psi) {
+  const float* c = fn.c + fn.off[0];
+  const bool lap = fn.kind[0] == BVC_FN_GAUSS_LAPLACIAN;
+  const int head = lap ? 3 : 1;
+  const float neg = c[0], q4 = lap ? c[1] : 0.0f, qd = lap ? c[2] : 0.0f;
+#pragma unroll
+  for (int k = 0; k < kMaxBumps; ++k) {
+    const int o = head + k * (1 + D);
+    float v = 0.0f;
+    if (o + D < fn.nc[0]) {
+      float r2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float d = y[a] - c[o + 1 + a];
+        r2 = fmaf(d, d, r2);
+      }
+      v = __expf(r2 * neg);
+      if (lap) v *= fmaf(r2, q4, qd);
+    }
+    psi[k] = v;
+  }
+}
+
 // ------------------------------------------- canonical closest-point distance
 // S = (a.x, a.y, ab.x, ab.y), inv = 1/|ab|^2.
 __device__ __forceinline__ float seg_d2(const float4 S, float inv, float px, float py) {

@@ -781,6 +781,131 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
   }
 }
 
+// ---------------------------------------------------------------- adjoint
+// Eq. 3 transposed: with lam(x) = dL/du(x) at the evaluation points,
+//   boundary sample i:  S1_i = sum_x lam(x) K1(x, z_i),  S2_i = sum_x lam(x) K2(x, z_i)
+//   source sample j:    S_j  = sum_x lam(x) G'(x, y_j)
+// with the gather's kernels (2D K1 = n.d / r^2, K2 = lg2 r^2; 3D K1 = n.d /
+// r^3, K2 = 1/r; G' = lg2 r^2 (2D), 1/r (3D)); the host scales them into
+// dL/du^, dL/d(du/dn^) and dL/dc.  Points, packed (x, lam) as float4, are
+// staged in shared memory by bulk copies, double-buffered; each thread owns
+// kAS samples.  FP32 sums per tile of kATile points, FP64 across tiles.
+constexpr int kATile = 128;
+constexpr int kAS = 4;
+
+template <int D, bool SRC>
+__global__ void __launch_bounds__(256) k_gather_adj(const float4* __restrict__ pl, int64_t m,
+                                                   const float* __restrict__ zs, const float* __restrict__ ns,
+                                                   int64_t stride, const int64_t* __restrict__ n_dev, int64_t n_fix,
+                                                   double s1, double s2, double* __restrict__ out1,
+                                                   double* __restrict__ out2) {
+  __shared__ __align__(128) float4 tile[2][kATile];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int64_t n = n_dev ? *n_dev : n_fix;
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * kAS;
+  if (base >= n) return;  // whole block idle (uniform)
+  float zc[kAS][3], nc[kAS][3];
+  bool live[kAS];
+#pragma unroll
+  for (int q = 0; q < kAS; ++q) {
+    const int64_t i = base + (int64_t)q * blockDim.x + threadIdx.x;
+    live[q] = i < n;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      zc[q][a] = (a < D && live[q]) ? zs[a * stride + i] : 0.0f;
+      nc[q][a] = (!SRC && a < D && live[q]) ? ns[a * stride + i] : 0.0f;
+    }
+  }
+  double A1[kAS], A2[kAS];
+#pragma unroll
+  for (int q = 0; q < kAS; ++q) A1[q] = A2[q] = 0.0;
+  const int64_t nt = (m + kATile - 1) / kATile;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2 && b < nt; ++b) {
+      const uint32_t bytes = (uint32_t)min64(kATile, m - (int64_t)b * kATile) * 16u;
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_g2s(&tile[b][0], pl + (int64_t)b * kATile, bytes, &bar[b]);
+    }
+  }
+  for (int64_t it = 0; it < nt; ++it) {
+    const int b = (int)(it & 1);
+    const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&g_gather_status, 1ull);
+        for (int64_t k2 = it; k2 < it + 2 && k2 < nt; ++k2)
+          (void)mbar_wait_bounded(&bar[k2 & 1], (uint32_t)((k2 >> 1) & 1));
+      }
+      return;
+    }
+    const int cnt = (int)min64(kATile, m - it * kATile);
+    float a1[kAS], a2[kAS];
+#pragma unroll
+    for (int q = 0; q < kAS; ++q) a1[q] = a2[q] = 0.0f;
+    for (int e = 0; e < cnt; ++e) {
+      const float4 P = tile[b][e];  // (x, y, z, lam)
+#pragma unroll
+      for (int q = 0; q < kAS; ++q) {
+        const float dx = zc[q][0] - P.x, dy = zc[q][1] - P.y, dz = D == 3 ? zc[q][2] - P.z : 0.0f;
+        const float r2 = D == 3 ? fmaf(dz, dz, fmaf(dy, dy, dx * dx)) : fmaf(dy, dy, dx * dx);
+        if (D == 2) {
+          const float l2 = lg2_approx(r2);
+          if (SRC) {
+            a1[q] = fmaf(P.w, l2, a1[q]);
+          } else {
+            const float k1 = fmaf(nc[q][1], dy, nc[q][0] * dx) * rcp_approx(r2);
+            a1[q] = fmaf(P.w, k1, a1[q]);
+            a2[q] = fmaf(P.w, l2, a2[q]);
+          }
+        } else {
+          const float ir = rsqrt_approx(r2);
+          if (SRC) {
+            a1[q] = fmaf(P.w, ir, a1[q]);
+          } else {
+            const float k1 = fmaf(nc[q][2], dz, fmaf(nc[q][1], dy, nc[q][0] * dx)) * (ir * ir * ir);
+            a1[q] = fmaf(P.w, k1, a1[q]);
+            a2[q] = fmaf(P.w, ir, a2[q]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kAS; ++q) {
+      A1[q] += (double)a1[q];
+      A2[q] += (double)a2[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && it + 2 < nt) {
+      fence_proxy_async();
+      const int64_t st = (it + 2) * kATile;
+      const uint32_t bytes = (uint32_t)min64(kATile, m - st) * 16u;
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_g2s(&tile[b][0], pl + st, bytes, &bar[b]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kAS; ++q) {
+    if (!live[q]) continue;
+    const int64_t i = base + (int64_t)q * blockDim.x + threadIdx.x;
+    out1[i] = A1[q] * s1;
+    if (!SRC) out2[i] = A2[q] * s2;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_pack_adj_pts(const float* __restrict__ x, int64_t m,
+                                                     const double* __restrict__ lam, float4* __restrict__ out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  out[p] = make_float4(x[p], x[m + p], D == 3 ? x[2 * m + p] : 0.0f, (float)lam[p]);
+}
+
 }  // namespace bvc
 
 extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
@@ -820,5 +945,70 @@ extern "C" bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cac
     k_gather_multi<3><<<grid, 256, 0, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u, b->table,
                                            b->count);
   BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_evaluate_adjoint_workspace_size(int64_t m, size_t* bytes) {
+  if (m < 0 || bytes == nullptr) return BVC_ERR_INVALID_ARG;
+  *bytes = 256 + (size_t)m * 16;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* pts, int64_t m, const double* lam,
+                                           double* adj_u, double* adj_q, double* adj_src, void* workspace,
+                                           size_t workspace_bytes, bvc_stream stream) {
+  if (cache == nullptr || (cache->dim != 2 && cache->dim != 3) || cache->n < 1 || cache->z == nullptr ||
+      cache->nrm == nullptr || adj_u == nullptr || adj_q == nullptr || m < 0 ||
+      (m > 0 && (pts == nullptr || lam == nullptr || workspace == nullptr)))
+    return BVC_ERR_INVALID_ARG;
+  const bool src = adj_src != nullptr && cache->n_src_cand > 0;
+  if (src && (cache->src_y == nullptr || cache->n_src_dev == nullptr)) return BVC_ERR_INVALID_ARG;
+  if (workspace_bytes < 256 + (size_t)m * 16) return BVC_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int D = cache->dim;
+  if (m == 0) {
+    BVC_CUDA_TRY(cudaMemsetAsync(adj_u, 0, (size_t)cache->n * 8, s));
+    BVC_CUDA_TRY(cudaMemsetAsync(adj_q, 0, (size_t)cache->n * 8, s));
+    if (src) BVC_CUDA_TRY(cudaMemsetAsync(adj_src, 0, (size_t)cache->n_src_cand * 8, s));
+    return BVC_OK;
+  }
+  float4* pl = (float4*)workspace;
+  {
+    ProfScope ps("adjoint_pack", s);
+    if (D == 2)
+      k_pack_adj_pts<2><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pts, m, lam, pl);
+    else
+      k_pack_adj_pts<3><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pts, m, lam, pl);
+    BVC_LAUNCH_CHECK();
+  }
+  const double N = (double)cache->n;
+  const double ca = D == 2 ? cache->bnd_measure / 6.283185307179586476925 : cache->bnd_measure / 12.566370614359172953850;
+  const double cb = D == 2 ? -ca * 0.34657359027997265471 : ca;
+  {
+    ProfScope ps("adjoint_gather_boundary", s);
+    const unsigned grid = (unsigned)((cache->n + 256 * kAS - 1) / (256 * kAS));
+    if (D == 2)
+      k_gather_adj<2, false><<<grid, 256, 0, s>>>(pl, m, cache->z, cache->nrm, cache->n, nullptr, cache->n, ca / N,
+                                                  cb / N, adj_u, adj_q);
+    else
+      k_gather_adj<3, false><<<grid, 256, 0, s>>>(pl, m, cache->z, cache->nrm, cache->n, nullptr, cache->n, ca / N,
+                                                  cb / N, adj_u, adj_q);
+    BVC_LAUNCH_CHECK();
+  }
+  if (src) {
+    const int64_t nc = cache->n_src_cand;
+    BVC_CUDA_TRY(cudaMemsetAsync(adj_src, 0, (size_t)nc * 8, s));
+    // source term: u += (1/ncand) sum_j G(x, y_j) c_j, G = lg2(r^2) ln2/(4 pi) (2D), -1/(4 pi r) (3D)
+    const double cs = D == 2 ? 0.34657359027997265471 / 6.283185307179586476925 : -1.0 / 12.566370614359172953850;
+    ProfScope ps("adjoint_gather_source", s);
+    const unsigned grid = (unsigned)((nc + 256 * kAS - 1) / (256 * kAS));
+    if (D == 2)
+      k_gather_adj<2, true><<<grid, 256, 0, s>>>(pl, m, cache->src_y, nullptr, nc, cache->n_src_dev, nc,
+                                                 cs / (double)nc, 0.0, adj_src, nullptr);
+    else
+      k_gather_adj<3, true><<<grid, 256, 0, s>>>(pl, m, cache->src_y, nullptr, nc, cache->n_src_dev, nc,
+                                                 cs / (double)nc, 0.0, adj_src, nullptr);
+    BVC_LAUNCH_CHECK();
+  }
   return BVC_OK;
 }

@@ -90,6 +90,9 @@ namespace bvc {
 // Host helpers (bvc_common.cu)
 bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);
 int num_sms();
+// dL/dA of the source cache's bump amplitudes from dL/dc of its samples.
+bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache* cache, const double* adj,
+                              double* grad_amp, cudaStream_t s);
 // seed_dev: when non-null, the seed is read from this device word at run
 // time (a captured CUDA graph replays with the seed it holds then).
 bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,

@@ -117,9 +117,54 @@ __global__ void __launch_bounds__(kSrcBlock) k_src_scatter(const SrcParams S) {
   }
 }
 
+// dL/dA_k += sum_j dL/dc_j |box| psi_k(y_j) over the kept candidates (c_j =
+// f(y_j) |box|): FP64 per thread, fixed-order warp sums, one atomic per warp.
+__global__ void __launch_bounds__(256) k_src_adjoint(DevFunction f, const float* __restrict__ src_y, int64_t ncand,
+                                                    const int64_t* __restrict__ n_src, double box,
+                                                    const double* __restrict__ adj, double* __restrict__ grad_amp) {
+  double acc[kMaxBumps];
+#pragma unroll
+  for (int b = 0; b < kMaxBumps; ++b) acc[b] = 0.0;
+  const int64_t nk = *n_src;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x) {
+    const float y[2] = {src_y[j], src_y[ncand + j]};
+    float psi[kMaxBumps];
+    bump_shapes<2>(f, y, psi);
+    const double a = adj[j] * box;
+#pragma unroll
+    for (int b = 0; b < kMaxBumps; ++b) acc[b] += a * (double)psi[b];
+  }
+#pragma unroll
+  for (int b = 0; b < kMaxBumps; ++b) {
+    double v = acc[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&grad_amp[b], v);
+  }
+}
+
 }  // namespace bvc
 
 using namespace bvc;
+
+namespace bvc {
+bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache* cache, const double* adj,
+                              double* grad_amp, cudaStream_t s) {
+  if (g->dim != 2) return BVC_ERR_UNSUPPORTED;
+  DevFunction f;
+  if (!make_dev_function(ffn, 2, &f)) return BVC_ERR_INVALID_ARG;
+  const double ext0 = (double)g->hi[0] - (double)g->lo[0], ext1 = (double)g->hi[1] - (double)g->lo[1];
+  int64_t blocks = (cache->n_src_cand + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  ProfScope ps("adjoint_source", s);
+  k_src_adjoint<<<(unsigned)blocks, 256, 0, s>>>(f, cache->src_y, cache->n_src_cand, cache->n_src_dev, ext0 * ext1,
+                                                 adj, grad_amp);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+}  // namespace bvc
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 

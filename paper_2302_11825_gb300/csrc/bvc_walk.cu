@@ -66,6 +66,15 @@ struct WalkParams {
   const BatchMeshDev* meshes;
   // kRecEnd walks: when non-null the seed is read from this device word.
   const uint64_t* seed_dev;
+  // Boundary data from vertex values (device float[n_verts]) instead of g.
+  const float* gv;
+  // kRecAdj walks: adjoint weights dL/du^ and dL/d(du/dn^) of every start
+  // (indexed like the starts) and the accumulated gradients with respect to
+  // the vertex values of g and the bump amplitudes of f.
+  const double* adj_u;
+  const double* adj_q;
+  double* grad_gv;
+  double* grad_amp;
 };
 
 // The first query of each start of a launch, once per start.
@@ -103,10 +112,18 @@ constexpr int kStep = 2;   // query done: termination test, sphere sample, sourc
 //            rec[D total + t] = (D / R0)(n . w0) (0 if the walk stopped at
 //            its start); for f = 0 a walk's path does not depend on g, and
 //            U = g(end), n . grad = rec[D] (g(end) - g(closest point of start)).
-constexpr int kRecGn = 0, kRecGrad = 1, kRecEnd = 2;
+//   kRecAdj  the adjoint replay of a kRecGn walk (same path, same draws):
+//            with cu = dL/du^ / W and cq = dL/d(du/dn^) / W of its start,
+//            U and n . grad are linear in the vertex values of g and the
+//            bump amplitudes A of f, so the walk adds
+//              (cu + cq (D/R0)(n . w0)) x (interpolation weights at the end)
+//            to dL/dg_vertex, the source terms' derivatives to dL/dA, and
+//            writes rec[t] = -cq (D/R0)(n . w0), the weight of the control
+//            variate g(closest point of the start), reduced per start later.
+constexpr int kRecGn = 0, kRecGrad = 1, kRecEnd = 2, kRecAdj = 3;
 
 template <int D, bool HAS_F, int REC, bool CNT>
-__global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const WalkParams P) {
+__global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB(D)) k_walk(const WalkParams P) {
   // Traversal stacks: node links and box distances, the latter in FP16
   // rounded down (a smaller stored distance can only cost an extra visit,
   // never prune a box that must be visited).
@@ -132,6 +149,11 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
   // the walk's tree and shell (per mesh in a batch)
   int root = 0;
   float eps = P.eps;
+  // adjoint replay: the start's weights, n . w0, FP64 amplitude gradients
+  float cu = 0.0f, cq = 0.0f, nw0 = 0.0f;
+  double gA[REC == kRecAdj && HAS_F ? kMaxBumps : 1];
+#pragma unroll
+  for (int b = 0; b < (REC == kRecAdj && HAS_F ? kMaxBumps : 1); ++b) gA[b] = 0.0;
   // query state
   int cur = 0, sp = 0;
   float thr = kInf;
@@ -190,6 +212,10 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
           const BatchMeshDev* M = P.meshes + P.sample_mesh[i];
           root = M->root;
           eps = M->eps;
+        }
+        if (REC == kRecAdj) {
+          cu = (float)(P.adj_u[i] / (double)P.W);
+          cq = (float)(P.adj_q[i] / (double)P.W);
         }
         k = 0;
         R0 = usrc = wf0 = wg0 = cv = 0.0f;
@@ -289,7 +315,8 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
 #pragma unroll
         for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
         const float d = sqrtf(h.d2);
-        if (REC != kRecEnd && k == 1) cv = eval_fn<D, true>(P.g, pbar);
+        if ((REC == kRecGn || REC == kRecGrad) && k == 1)
+          cv = P.gv ? vertex_g<D>(G, P.gv, h.id, pbar) : eval_fn<D, true>(P.g, pbar);
         if (d < eps || k >= P.max_steps) {
           if (REC == kRecEnd) {
 #pragma unroll
@@ -298,8 +325,17 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
 #pragma unroll
             for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn2);
             P.rec[D * P.total + t] = k > 1 ? ((float)D / R0) * nn2 : 0.0f;
+          } else if (REC == kRecAdj) {
+            const float s0 = k > 1 ? cq * ((float)D / R0) * nw0 : 0.0f;
+            int32_t vid[D];
+            float wv[D];
+            vertex_weights<D>(G, h.id, pbar, vid, wv);
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(&P.grad_gv[vid[a]], (double)((cu + s0) * wv[a]));
+            P.rec[t] = -s0;
           } else {
-            const float U = (k == 1 ? cv : eval_fn<D, true>(P.g, pbar)) + usrc;
+            const float gend = P.gv ? vertex_g<D>(G, P.gv, h.id, pbar) : eval_fn<D, true>(P.g, pbar);
+            const float U = (k == 1 ? cv : gend) + usrc;
             const float sc = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
             P.rec[t] = U;
             if (REC == kRecGn) {
@@ -338,7 +374,34 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
             om[1] = st * sn;
             om[D - 1] = zc;
           }
-          if (HAS_F) {
+          if (REC == kRecAdj && k == 1) {
+            float nn2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], om[a], nn2);
+            nw0 = nn2;
+          }
+          if (HAS_F && REC == kRecAdj) {
+            // d/dA_k of the source terms: U gains w_u psi_k(y) at every step;
+            // n.grad gains (D/R0)(n.w0) w_u psi_k(y) at steps after the first
+            // and (n.w0) w_g psi_k(y0) at the first (w_g = -R (1 - (rho/R)^D))
+            const float u2 = u01f(r.z);
+            const float rho = R * u2;
+            float y[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
+            const float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho);
+            float coef;
+            if (k == 1) {
+              const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
+              coef = fmaf(cq * nw0, -R * (1.0f - q), cu * wu);
+            } else {
+              coef = fmaf(cq * nw0, (float)D / R0, cu) * wu;
+            }
+            float psi[kMaxBumps];
+            bump_shapes<D>(P.f, y, psi);
+#pragma unroll
+            for (int b = 0; b < (REC == kRecAdj && HAS_F ? kMaxBumps : 1); ++b) gA[b] += (double)(coef * psi[b]);
+          } else if (HAS_F) {
             const float u2 = u01f(r.z);
             const float rho = R * u2;
             float y[D];
@@ -374,6 +437,15 @@ __global__ void __launch_bounds__(kWalkBlock, BVC_WALK_MINB(D)) k_walk(const Wal
     if (CNT) {
       my_nodes += __shfl_xor_sync(FULL, my_nodes, o);
       my_prims += __shfl_xor_sync(FULL, my_prims, o);
+    }
+  }
+  if (REC == kRecAdj && HAS_F) {
+#pragma unroll
+    for (int b = 0; b < (REC == kRecAdj && HAS_F ? kMaxBumps : 1); ++b) {
+      double v = gA[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+      if (lane == 0 && v != 0.0) atomicAdd(&P.grad_amp[b], v);
     }
   }
   if (lane == 0) {
@@ -427,6 +499,10 @@ static const void* walk_kernel(bool cnt) {
 // rec: kRecGn / kRecGrad / kRecEnd (the last only without a source term).
 static const void* pick_walk(int dim, bool has_f, int rec, bool cnt) {
   if (rec == kRecEnd) return dim == 2 ? walk_kernel<2, false, kRecEnd>(cnt) : walk_kernel<3, false, kRecEnd>(cnt);
+  if (rec == kRecAdj) {
+    if (dim == 2) return has_f ? (const void*)k_walk<2, true, kRecAdj, false> : (const void*)k_walk<2, false, kRecAdj, false>;
+    return has_f ? (const void*)k_walk<3, true, kRecAdj, false> : (const void*)k_walk<3, false, kRecAdj, false>;
+  }
   const bool gn = rec == kRecGn;
   if (dim == 2) {
     if (has_f) return gn ? walk_kernel<2, true, kRecGn>(cnt) : walk_kernel<2, true, kRecGrad>(cnt);
@@ -560,9 +636,9 @@ extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_c
   return BVC_OK;
 }
 
-extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
-                                      const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
-                                      size_t workspace_bytes, bvc_stream stream) {
+static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const float* gv, const bvc_function* ffn,
+                              const bvc_cache_opts* opts, bvc_cache* cache, void* workspace, size_t workspace_bytes,
+                              bvc_stream stream) {
   if (g == nullptr || opts == nullptr || cache == nullptr) return BVC_ERR_INVALID_ARG;
   const int D = g->dim;
   const int64_t N = opts->n_samples;
@@ -575,6 +651,7 @@ extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, c
   if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
   WalkParams P{};
   P.G = g->dev;
+  P.gv = gv;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
   const size_t per_sample = ws_per_start(D, W, 1);
   int64_t chunk = ws_chunk(workspace_bytes, per_sample);
@@ -622,6 +699,133 @@ extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, c
     if (st != BVC_OK) return st;
   }
   return bvc_cache_pack(cache, stream);
+}
+
+extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                      const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
+                                      size_t workspace_bytes, bvc_stream stream) {
+  return cache_build(g, gfn, nullptr, ffn, opts, cache, workspace, workspace_bytes, stream);
+}
+
+extern "C" bvc_status bvc_cache_build_vg(bvc_geometry g, const float* g_vertex, const bvc_function* ffn,
+                                         const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
+                                         size_t workspace_bytes, bvc_stream stream) {
+  if (g_vertex == nullptr) return BVC_ERR_INVALID_ARG;
+  return cache_build(g, nullptr, g_vertex, ffn, opts, cache, workspace, workspace_bytes, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the cache build (K2 transposed).  The estimator is linear in
+// the vertex values of g and the bump amplitudes of f and the walk paths do
+// not depend on either, so the walks are replayed from their Philox streams
+// with the adjoint weights of their starts (kRecAdj), and the control
+// variate's weights are summed per start and spread over the vertices of the
+// element holding the start's first closest point.
+__global__ void __launch_bounds__(256) k_adj_cv(const float* __restrict__ rec, int64_t c, int32_t W,
+                                               const float* __restrict__ starts, int64_t pt_stride, int64_t i0,
+                                               const float* __restrict__ fh, DevGeometry G, int dim,
+                                               double* __restrict__ grad_gv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < c; r += nwarps) {
+    double s = 0.0;
+    for (int j = lane; j < W; j += 32) s += (double)rec[r * W + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && s != 0.0) {
+      const int32_t e = __float_as_int(fh[(1 + dim) * c + r]);
+      float p[3];
+      for (int a = 0; a < dim; ++a) p[a] = starts[a * pt_stride + i0 + r] - fh[(1 + a) * c + r];
+      int32_t vid[3];
+      float w[3];
+      if (dim == 2)
+        vertex_weights<2>(G, e, p, vid, w);
+      else
+        vertex_weights<3>(G, e, p, vid, w);
+      for (int a = 0; a < dim; ++a) atomicAdd(&grad_gv[vid[a]], s * (double)w[a]);
+    }
+  }
+}
+
+// The differentiable source: no term, or one GAUSS / GAUSS_LAPLACIAN term of
+// at most kMaxBumps bumps whose amplitudes are the parameters.
+static bool diff_source_ok(const bvc_function* ffn, int dim) {
+  if (ffn == nullptr || ffn->n_terms == 0) return true;
+  if (ffn->n_terms != 1) return false;
+  const bvc_term& t = ffn->terms[0];
+  if (t.kind != BVC_FN_GAUSS && t.kind != BVC_FN_GAUSS_LAPLACIAN) return false;
+  return t.n_coeffs >= 1 && (t.n_coeffs - 1) % (1 + dim) == 0 && (t.n_coeffs - 1) / (1 + dim) <= kMaxBumps;
+}
+
+extern "C" bvc_status bvc_cache_adjoint_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+                                                       size_t* full_bytes) {
+  if (g == nullptr || opts == nullptr || opts->n_samples < 1 || opts->walks_per_sample < 1) return BVC_ERR_INVALID_ARG;
+  const size_t per = ws_per_start(g->dim, opts->walks_per_sample, 0);
+  if (min_bytes) *min_bytes = 2 * kWsHead + per;
+  if (full_bytes) *full_bytes = 2 * kWsHead + per * (size_t)opts->n_samples;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache_opts* opts,
+                                        const bvc_cache* cache, const double* adj_u, const double* adj_q,
+                                        const double* adj_src, double* grad_gv, double* grad_amp, void* workspace,
+                                        size_t workspace_bytes, bvc_stream stream) {
+  if (g == nullptr || opts == nullptr || cache == nullptr || adj_u == nullptr || adj_q == nullptr ||
+      grad_gv == nullptr || workspace == nullptr)
+    return BVC_ERR_INVALID_ARG;
+  const int D = g->dim;
+  const int64_t N = opts->n_samples;
+  const int32_t W = opts->walks_per_sample;
+  if (cache->dim != D || cache->n != N || cache->z == nullptr || cache->nrm == nullptr ||
+      !valid_walk_args((float)opts->eps, opts->max_steps, W))
+    return BVC_ERR_INVALID_ARG;
+  if (!diff_source_ok(ffn, D)) return BVC_ERR_UNSUPPORTED;
+  const bool has_f = ffn != nullptr && ffn->n_terms > 0;
+  if (has_f && grad_amp == nullptr) return BVC_ERR_INVALID_ARG;
+  WalkParams P{};
+  P.G = g->dev;
+  if (!make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
+  const size_t per = ws_per_start(D, W, 0);
+  int64_t chunk = ws_chunk(workspace_bytes, per);
+  if (chunk < 1) return BVC_ERR_WORKSPACE;
+  if (chunk > N) chunk = N;
+  cudaStream_t s = (cudaStream_t)stream;
+  P.starts = cache->z;
+  P.nrm = cache->nrm;
+  P.pt_stride = N;
+  P.W = W;
+  P.eps = (float)opts->eps;
+  P.max_steps = opts->max_steps;
+  P.seed = opts->seed;
+  P.tag = 0;
+  P.counter = (unsigned long long*)workspace;
+  P.adj_u = adj_u;
+  P.adj_q = adj_q;
+  P.grad_gv = grad_gv;
+  P.grad_amp = grad_amp;
+  for (int64_t i0 = 0; i0 < N; i0 += chunk) {
+    const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
+    P.i0 = i0;
+    P.total = c * (int64_t)W;
+    P.wid0 = opts->walk_id_base + (uint64_t)i0 * (uint64_t)W;
+    float* fh = ws_first(workspace);
+    P.rec = ws_records(workspace, c, D);
+    P.first = fh;
+    bvc_status st = launch_first_hits(D, g->dev, P.starts, N, i0, c, fh, s);
+    if (st != BVC_OK) return st;
+    st = launch_walk(D, has_f, kRecAdj, false, P, s);
+    if (st != BVC_OK) return st;
+    int64_t blocks = (c * 32 + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    ProfScope ps("adjoint_cv", s);
+    k_adj_cv<<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, W, P.starts, N, i0, fh, g->dev, D, grad_gv);
+    BVC_LAUNCH_CHECK();
+  }
+  if (has_f && cache->n_src_cand > 0 && adj_src != nullptr)
+    return bvc_source_adjoint(g, ffn, cache, adj_src, grad_amp, stream);
+  return BVC_OK;
 }
 
 extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,

@@ -9,11 +9,11 @@ import numpy as np
 import oracle
 
 
-def oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid=None, max_steps=1 << 14, bvh=None):
+def oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid=None, max_steps=1 << 14, bvh=None, g_vertex=None):
     bvh = bvh or oracle.BVH(V, F)
     z, n, e = oracle.sample_boundary(V, F, N, l, seed)
     z32, n32 = z.astype(np.float32), n.astype(np.float32)
-    out = oracle.walks(bvh, g, f, z32, W, eps, max_steps, seed, id_base=0, tag=oracle.TAG_WALK)
+    out = oracle.walks(bvh, g, f, z32, W, eps, max_steps, seed, id_base=0, tag=oracle.TAG_WALK, g_vertex=g_vertex)
     u_hat, q_hat = oracle.reduce_walks(out["U"], out["grad"], n32, W)
     cache = {"z": z32, "n": n32, "u_hat": u_hat, "q_hat": q_hat, "elem": e,
              "measure": oracle.boundary_measure(V, F), "walks": out, "N": N,
@@ -35,6 +35,6 @@ def oracle_evaluate(cache, pts):
     return u, grad
 
 
-def oracle_bvc(V, F, g, f, N, W, l, eps, pts, seed, src_grid=None, max_steps=1 << 14, bvh=None):
-    cache = oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid, max_steps, bvh)
+def oracle_bvc(V, F, g, f, N, W, l, eps, pts, seed, src_grid=None, max_steps=1 << 14, bvh=None, g_vertex=None):
+    cache = oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid, max_steps, bvh, g_vertex)
     return oracle_evaluate(cache, pts)
