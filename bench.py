@@ -222,6 +222,9 @@ class Solver:
                                    src_grid=w.src_grid if n_src else (0, 0))
         self.cache = bvc.Cache(w.dim, w.n_samples, n_src_cand=n_src)
         self.ws_cache = bvc.workspace(bvc.cache_build_workspace_size(self.geom, self.opts)[1])
+        # walk launch shape from the library's autotuner (setup, not timed)
+        self.walk_shape = bvc.tune_walks(self.geom, w.g, w.f, self.opts)
+        self.geom.stats(reset=True)
         self.far = bvc.EvalState(self.far_pts)
         self.near = bvc.EvalState(self.near_pts)
         self.ws_eval = bvc.workspace(bvc.evaluate_workspace_size(self.cache, self.far))
@@ -778,7 +781,9 @@ def main():
                    "eval_points": int(M), "eval_far": int(s.m_far), "eval_near_pointwise": int(s.m_near),
                    "near_walks": w.walks, "eps": w.eps, "offset_l": w.offset_l,
                    "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}",
-                   "sums": "fp64"},
+                   "sums": "fp64",
+                   "walk_shape": {"blocks_per_sm": s.walk_shape[0], "chunk": s.walk_shape[1],
+                                  "tuned_ms": s.walk_shape[2]}},
         "roofline": roofline,
         "kernels": kernels, "rooflines_all": extra,
         "wos_steps_per_s": (run_stats["steps"]) / max(walk_ms_total * K / 1e3, 1e-12),

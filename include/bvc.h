@@ -290,6 +290,24 @@ bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_funct
  * out).  Synchronises the device; reset != 0 clears it. */
 bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
 
+/* ------------------------------------------------------- walk autotuner */
+/* The walk kernel is persistent: a grid of (blocks per SM) x (SMs) blocks
+ * pulls walks from a counter, a warp taking `chunk` walks at a time.  A
+ * walk's result depends only on its id, so the shape changes speed, never
+ * results.  bvc_tune_walks times the cache walks of min(N, 16384) boundary
+ * samples of the given problem for every shape with blocks per SM from the
+ * kernel's maximum occupancy down to half of it and chunks of 64, 128, 256
+ * (best of two launches each, CUDA events on `stream`; synchronous, so not
+ * for stream capture), keeps the fastest in the geometry for all later walk
+ * launches on it, and returns it in shape[2] = {blocks per SM, chunk} and
+ * its time in best_ms.  The tuning walks add to the geometry's status
+ * block.  bvc_geometry_set_walk_shape sets a shape by hand (0 = default). */
+bvc_status bvc_tune_walks_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* bytes);
+bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                          const bvc_cache_opts* opts, void* workspace, size_t workspace_bytes, bvc_stream stream,
+                          int32_t shape[2], float* best_ms);
+bvc_status bvc_geometry_set_walk_shape(bvc_geometry g, int32_t blocks_per_sm, int32_t chunk);
+
 /* ------------------------------------------------------ differentiation */
 /* Gradients of a loss L of the values u(x) that bvc_evaluate gives (Eq. 3)
  * with respect to the boundary data and the source.  The parameters are

@@ -136,6 +136,10 @@ def _declare(lib):
         "bvc_batch_stats": (S, [P, C.POINTER(C.c_uint64), i32, P]),
         "bvc_batch_project": (S, [P, P, C.POINTER(MultiCacheStruct), P]),
         "bvc_batch_evaluate": (S, [P, C.POINTER(MultiCacheStruct), P, P, P]),
+        "bvc_tune_walks_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz)]),
+        "bvc_tune_walks": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(CacheOpts), P, sz, P,
+                               C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+        "bvc_geometry_set_walk_shape": (S, [P, i32, i32]),
         "bvc_profile_begin": (S, []),
         "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
         "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
@@ -441,6 +445,25 @@ def evaluate(cache: Cache, state: EvalState, ws: torch.Tensor = None, stream=Non
         ws = workspace(evaluate_workspace_size(cache, state))
     _check(lib().bvc_evaluate(C.byref(cache.struct), C.byref(state.struct), _ptr(ws), ws.numel(), _stream(stream)),
            "bvc_evaluate")
+
+
+# ---------------------------------------------------------------- walk autotuner
+def tune_walks(geom: Geometry, g_terms, f_terms, opts: CacheOpts, stream=None):
+    """bvc_tune_walks: returns (blocks per SM, chunk, best ms) and keeps the
+    shape in the geometry."""
+    b = C.c_size_t()
+    _check(lib().bvc_tune_walks_workspace_size(geom.h, C.byref(opts), C.byref(b)), "bvc_tune_walks_workspace_size")
+    ws = workspace(b.value)
+    g, f = make_function(g_terms), make_function(f_terms)
+    shape = (C.c_int32 * 2)()
+    ms = C.c_float()
+    _check(lib().bvc_tune_walks(geom.h, C.byref(g), C.byref(f), C.byref(opts), _ptr(ws), ws.numel(),
+                                _stream(stream), shape, C.byref(ms)), "bvc_tune_walks")
+    return int(shape[0]), int(shape[1]), float(ms.value)
+
+
+def set_walk_shape(geom: Geometry, blocks_per_sm: int, chunk: int):
+    _check(lib().bvc_geometry_set_walk_shape(geom.h, int(blocks_per_sm), int(chunk)), "bvc_geometry_set_walk_shape")
 
 
 # ---------------------------------------------------------------- differentiation

@@ -82,6 +82,9 @@ struct bvc_geometry_s {
   void* arena;            // one device allocation holding everything below
   size_t arena_bytes;
   int32_t counting;       // walks count node fetches and primitive tests
+  // Walk launch shape picked by bvc_tune_walks (0 = defaults): resident
+  // blocks per SM of the persistent grid and walks per warp refill.
+  int32_t tune_blocks_per_sm, tune_chunk;
   bvc::DevGeometry dev;
 };
 

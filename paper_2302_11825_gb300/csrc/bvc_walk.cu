@@ -36,7 +36,7 @@ namespace bvc {
 #endif
 constexpr int kWalkBlock = 128;
 constexpr int kStack = 24;  // the BVH builder bounds the depth by 24
-constexpr int64_t kChunk = 128;
+constexpr int64_t kChunk = 128;  // default walks per warp refill
 
 struct WalkParams {
   DevGeometry G;
@@ -75,6 +75,9 @@ struct WalkParams {
   const double* adj_q;
   double* grad_gv;
   double* grad_amp;
+  // launch shape: walks per warp refill (set by launch_walk)
+  int64_t chunk;
+  int32_t blocks_per_sm;  // 0 = as many as fit
 };
 
 // The first query of each start of a launch, once per start.
@@ -191,14 +194,14 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
     while (need != 0u && more) {
       if (q_next >= q_end) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)kChunk);
+        if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)P.chunk);
         base = __shfl_sync(FULL, base, 0);
         if ((int64_t)base >= P.total) {
           more = false;
           break;
         }
         q_next = (int64_t)base;
-        q_end = min64((int64_t)base + kChunk, P.total);
+        q_end = min64((int64_t)base + P.chunk, P.total);
       }
       const int avail = (int)min64(q_end - q_next, (int64_t)__popc(need));
       const int rank = __popc(need & ((1u << lane) - 1u));
@@ -512,10 +515,14 @@ static const void* pick_walk(int dim, bool has_f, int rec, bool cnt) {
   return gn ? walk_kernel<3, false, kRecGn>(cnt) : walk_kernel<3, false, kRecGrad>(cnt);
 }
 
-static bvc_status launch_walk(int dim, bool has_f, int rec, bool cnt, const WalkParams& P, cudaStream_t s) {
+static bvc_status launch_walk(int dim, bool has_f, int rec, bool cnt, const WalkParams& P0, cudaStream_t s) {
+  WalkParams P = P0;
+  if (P.chunk < 1) P.chunk = kChunk;
   const void* kern = pick_walk(dim, has_f, rec, cnt);
   const int64_t want = (P.total + 31) / 32;
-  int grid = num_sms() * max_blocks_per_sm(kern, kWalkBlock, 0);
+  int bps = max_blocks_per_sm(kern, kWalkBlock, 0);
+  if (P.blocks_per_sm > 0 && P.blocks_per_sm < bps) bps = P.blocks_per_sm;
+  int grid = num_sms() * bps;
   const int64_t need_blocks = (want + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
   if (need_blocks < grid) grid = (int)(need_blocks > 0 ? need_blocks : 1);
   BVC_CUDA_TRY(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
@@ -570,6 +577,8 @@ extern "C" bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bv
   if (starts == nullptr || rec == nullptr) return BVC_ERR_INVALID_ARG;
   WalkParams P{};
   P.G = g->dev;
+  P.chunk = g->tune_chunk;
+  P.blocks_per_sm = g->tune_blocks_per_sm;
   if (!make_dev_function(gfn, g->dim, &P.g) || !make_dev_function(ffn, g->dim, &P.f)) return BVC_ERR_INVALID_ARG;
   P.starts = starts;
   P.nrm = nrm;
@@ -651,6 +660,8 @@ static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const flo
   if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
   WalkParams P{};
   P.G = g->dev;
+  P.chunk = g->tune_chunk;
+  P.blocks_per_sm = g->tune_blocks_per_sm;
   P.gv = gv;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
   const size_t per_sample = ws_per_start(D, W, 1);
@@ -785,6 +796,8 @@ extern "C" bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn,
   if (has_f && grad_amp == nullptr) return BVC_ERR_INVALID_ARG;
   WalkParams P{};
   P.G = g->dev;
+  P.chunk = g->tune_chunk;
+  P.blocks_per_sm = g->tune_blocks_per_sm;
   if (!make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
   const size_t per = ws_per_start(D, W, 0);
   int64_t chunk = ws_chunk(workspace_bytes, per);
@@ -828,6 +841,121 @@ extern "C" bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn,
   return BVC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Walk launch autotuner.  A walk's result depends only on its id, never on
+// which thread runs it, so the persistent grid's occupancy and the refill
+// chunk change speed only.  bvc_tune_walks samples min(N, 16384) boundary
+// points of the caller's problem, and times the cache walks of those points
+// (CUDA events on the caller's stream, best of two launches) for resident
+// blocks per SM from the maximum down to half of it and refill chunks of
+// 64, 128 and 256 walks; the fastest shape is kept in the geometry.
+static constexpr int64_t kTuneSamples = 16384;
+
+static int64_t tune_samples(const bvc_cache_opts* o) {
+  return o->n_samples < kTuneSamples ? o->n_samples : kTuneSamples;
+}
+
+extern "C" bvc_status bvc_tune_walks_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* bytes) {
+  if (g == nullptr || opts == nullptr || bytes == nullptr || opts->n_samples < 1 || opts->walks_per_sample < 1)
+    return BVC_ERR_INVALID_ARG;
+  const int64_t n = tune_samples(opts);
+  const size_t pts = (((size_t)n * 2 * g->dim * sizeof(float)) + 255) & ~size_t(255);
+  *bytes = pts + 2 * kWsHead + ws_per_start(g->dim, opts->walks_per_sample, 1) * (size_t)n;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_geometry_set_walk_shape(bvc_geometry g, int32_t blocks_per_sm, int32_t chunk) {
+  if (g == nullptr || blocks_per_sm < 0 || chunk < 0 || chunk > (1 << 20)) return BVC_ERR_INVALID_ARG;
+  g->tune_blocks_per_sm = blocks_per_sm;
+  g->tune_chunk = chunk;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                     const bvc_cache_opts* opts, void* workspace, size_t workspace_bytes,
+                                     bvc_stream stream, int32_t shape[2], float* best_ms) {
+  size_t need = 0;
+  bvc_status st = bvc_tune_walks_workspace_size(g, opts, &need);
+  if (st != BVC_OK) return st;
+  if (workspace == nullptr || !valid_walk_args((float)opts->eps, opts->max_steps, opts->walks_per_sample))
+    return BVC_ERR_INVALID_ARG;
+  if (workspace_bytes < need) return BVC_ERR_WORKSPACE;
+  const int D = g->dim;
+  const int64_t n = tune_samples(opts);
+  const int32_t W = opts->walks_per_sample;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* z = (float*)workspace;
+  float* nrm = z + (size_t)D * n;
+  void* ws = (char*)workspace + ((((size_t)n * 2 * D * sizeof(float)) + 255) & ~size_t(255));
+  st = launch_sample_boundary(g, n, opts->offset_l, opts->seed, z, nrm, nullptr, n, s, nullptr);
+  if (st != BVC_OK) return st;
+  WalkParams P{};
+  P.G = g->dev;
+  if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
+  P.starts = z;
+  P.nrm = nrm;
+  P.pt_stride = n;
+  P.i0 = 0;
+  P.W = W;
+  P.total = n * (int64_t)W;
+  P.wid0 = opts->walk_id_base;
+  P.eps = (float)opts->eps;
+  P.max_steps = opts->max_steps;
+  P.seed = opts->seed;
+  P.tag = 0;
+  P.counter = (unsigned long long*)ws;
+  float* fh = ws_first(ws);
+  P.rec = ws_records(ws, n, D);
+  P.first = fh;
+  st = launch_first_hits(D, g->dev, z, n, 0, n, fh, s);
+  if (st != BVC_OK) return st;
+  const bool has_f = P.f.n_terms > 0;
+  const int maxb = max_blocks_per_sm(pick_walk(D, has_f, kRecGn, false), kWalkBlock, 0);
+  cudaEvent_t e0, e1;
+  BVC_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return BVC_ERR_CUDA;
+  }
+  float best = 3.0e38f;
+  int best_b = 0, best_c = 0;
+  const int chunks[3] = {64, 128, 256};
+  st = BVC_OK;
+  for (int b = maxb; b >= (maxb + 1) / 2 && st == BVC_OK; --b)
+    for (int ci = 0; ci < 3 && st == BVC_OK; ++ci) {
+      P.blocks_per_sm = b;
+      P.chunk = chunks[ci];
+      float t = 3.0e38f;
+      for (int rep = 0; rep < 2 && st == BVC_OK; ++rep) {
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = BVC_ERR_CUDA;
+        if (st == BVC_OK) st = launch_walk(D, has_f, kRecGn, false, P, s);
+        if (st == BVC_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+          st = BVC_ERR_CUDA;
+        float ms = 0.0f;
+        if (st == BVC_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < t) t = ms;
+      }
+      if (st == BVC_OK && t < best) {
+        best = t;
+        best_b = b;
+        best_c = chunks[ci];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != BVC_OK) {
+    (void)cudaGetLastError();
+    return st;
+  }
+  g->tune_blocks_per_sm = best_b;
+  g->tune_chunk = best_c;
+  if (shape) {
+    shape[0] = best_b;
+    shape[1] = best_c;
+  }
+  if (best_ms) *best_ms = best;
+  return BVC_OK;
+}
+
 extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
                                                   size_t* full_bytes) {
   if ((dim != 2 && dim != 3) || m < 0 || walks < 1) return BVC_ERR_INVALID_ARG;
@@ -852,6 +980,8 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
   const int D = g->dim;
   WalkParams P{};
   P.G = g->dev;
+  P.chunk = g->tune_chunk;
+  P.blocks_per_sm = g->tune_blocks_per_sm;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (m > 0) {
