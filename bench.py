@@ -10,6 +10,10 @@ value = interior points solved per second (device-resident inputs); e2e =
 the same through the C ABI with the evaluation points copied in from pinned
 host memory and u, grad u copied out every step.
 
+--workload inverse: one gradient step (forward solve at 100k observation
+points, adjoint gather, adjoint walk replay, Adam update) of the inverse
+problem on a box minus five overlapping ellipsoids (about 410k triangles).
+
 --workload batched: sixteen 3D meshes of uneven size x 64 harmonic
 polynomial right-hand sides each (32768 samples x 128 walks, 65536 points
 per mesh); one step = one replay of a CUDA graph holding the whole batched
@@ -610,6 +614,189 @@ def batched_oracle_rate(w, budget_s: float = 20.0):
             "walks_per_s": walk_rate, "pairs_per_s": pair_rate}
 
 
+# ------------------------------------------------------------------ inverse problem
+FLOPS_WINDING_PAIR = 60  # solid angle of one triangle at one point, atan2 counted as ~20
+
+
+def bench_inverse(args, rank, local, ws):
+    """Differentiable inverse problem: each step is one gradient of the
+    data misfit with respect to the 256 RBF coefficients of g and the 8
+    bump amplitudes of f (forward BVC solve at 100k observation points,
+    adjoint gather, adjoint walk replay) followed by an Adam update."""
+    import torch
+    from paper_2302_11825_gb300 import bvc
+    from paper_2302_11825_gb300 import workloads as wl
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    rank, ws = init_dist("nccl")
+    w = wl.inverse_problem(seed=rank)
+    t0 = time.perf_counter()
+    geom = bvc.Geometry(w.V, w.F)
+    torch.cuda.synchronize()
+    geometry_build_s = time.perf_counter() - t0
+    Vt = torch.tensor(w.V, dtype=torch.float64, device=device)
+    Ct = torch.tensor(w.rbf_centres, dtype=torch.float64, device=device)
+    Phi = torch.exp(-torch.cdist(Vt, Ct).square() / (2 * w.rbf_sigma ** 2))  # [n_verts][256]
+    bumps = (wl.GAUSS, w.bump_sigma, w.bump_centres)
+    P = bvc.soa(w.obs_pts)
+    M = P.shape[1]
+    solver = bvc.DiffSolver(geom, P, w.n_samples, w.walks, w.offset_l, w.eps, 1, bumps=bumps, src_grid=w.src_grid)
+    truth = bvc.DiffSolver(geom, P, w.n_samples, w.walks, w.offset_l, w.eps, 777, bumps=bumps, src_grid=w.src_grid)
+    c_true = torch.tensor(w.c_true, dtype=torch.float64, device=device)
+    a_true = torch.tensor(w.a_true, dtype=torch.float64, device=device)
+    with torch.no_grad():
+        u_true = truth(Phi @ c_true, a_true)
+        gen = torch.Generator(device=device).manual_seed(5)
+        obs = u_true + 0.01 * u_true.std() * torch.randn(M, generator=gen, device=device, dtype=torch.float64)
+    c = torch.zeros(256, dtype=torch.float64, device=device, requires_grad=True)
+    a = torch.zeros(8, dtype=torch.float64, device=device, requires_grad=True)
+    opt = torch.optim.Adam([c, a], lr=0.2)
+
+    def loss_of(cc, aa):
+        u = solver(Phi @ cc, aa)
+        return 0.5 * (u - obs).square().mean()
+
+    def step():
+        opt.zero_grad()
+        L = loss_of(c, a)
+        L.backward()
+        opt.step()
+        return L
+
+    # central differences at eps = 1e-3 along a random direction (fixed seeds)
+    gen2 = torch.Generator(device=device).manual_seed(6)
+    dc = torch.randn(256, generator=gen2, device=device, dtype=torch.float64)
+    da = torch.randn(8, generator=gen2, device=device, dtype=torch.float64)
+    c0 = torch.randn(256, generator=gen2, device=device, dtype=torch.float64)
+    a0 = torch.randn(8, generator=gen2, device=device, dtype=torch.float64) * 5
+    cc, aa = c0.clone().requires_grad_(True), a0.clone().requires_grad_(True)
+    loss_of(cc, aa).backward()
+    ad = float((cc.grad * dc).sum() + (aa.grad * da).sum())
+    with torch.no_grad():
+        h = 1e-3
+        fd = float((loss_of(c0 + h * dc, a0 + h * da) - loss_of(c0 - h * dc, a0 - h * da)) / (2 * h))
+
+    # counted forward: node fetches and primitive tests of the cache walks
+    geom.stats(reset=True)
+    geom.set_counting(True)
+    with torch.no_grad():
+        loss_of(c, a)
+    torch.cuda.synchronize()
+    cstats = geom.stats(reset=True)
+    geom.set_counting(False)
+
+    losses = []
+    for k in range(args.warmup):
+        losses.append(float(step()))
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        bvc.profile_begin()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record()
+            L = step()
+            evs[k][1].record()
+            losses.append(float(L))
+        prof = bvc.profile_end()
+        torch.cuda.synchronize()
+    barrier()
+    t_local = sum(x.elapsed_time(y) for x, y in evs) / 1e3
+    t_max = max_over_ranks(t_local, device)
+    Kst = args.steps
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    total_ms = sum(v[1] for v in prof.values())
+    kernels = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1), "share": v[1] / total_ms}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    n_walks = w.n_samples * w.walks
+    walk_b = walk_bytes(cstats, 3, n_walks)
+    ncand = w.src_grid[0] * w.src_grid[1] * w.src_grid[2]
+    roofs = {}
+    for kname in ("walk",):
+        if kname in prof:
+            avg = kernels[kname]["avg_ms"]
+            a_gbs = walk_b / (avg / 1e3) / 1e9
+            roofs[kname] = {"bound": "hbm", "achieved": a_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                            "frac": a_gbs / float(peaks["hbm_gbs"]), "kernel": kname,
+                            "traffic": profile_traffic(kname, w.name),
+                            "note": "forward and adjoint replay walks visit the same nodes; bytes from the "
+                                    "counted forward"}
+    if "source_classify" in prof:
+        avg = kernels["source_classify"]["avg_ms"]
+        fl = ncand * w.F.shape[0] * FLOPS_WINDING_PAIR / (avg / 1e3) / 1e12
+        roofs["source_classify"] = {"bound": "alu", "achieved": fl, "peak": fp32_peak, "unit": "TFLOP/s",
+                                    "frac": fl / fp32_peak, "kernel": "source_classify",
+                                    "traffic": profile_traffic("source_classify", w.name)}
+    dominant = max(roofs, key=lambda k: kernels[k]["share"]) if roofs else None
+    out = {
+        "metric": "inverse problem: gradient steps/s (forward + adjoint, 1 GB300)", "value": Kst * ws / t_max,
+        "unit": "gradient steps/s", "n_gpus": ws, "steps": Kst, "warmup": args.warmup,
+        "ms_per_step": t_max / Kst * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "triangles": int(w.F.shape[0]), "vertices": int(w.V.shape[0]),
+                   "rbf_coefficients": 256, "bump_amplitudes": 8, "observations": int(M),
+                   "n_samples": w.n_samples, "walks_per_sample": w.walks, "src_grid": list(w.src_grid),
+                   "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
+        "roofline": roofs.get(dominant), "rooflines_all": roofs, "kernels": kernels,
+        "fd_check": {"eps": 1e-3, "fd": fd, "adjoint": ad, "rel_err": abs(fd - ad) / max(abs(fd), 1e-300)},
+        "loss_first": losses[0], "loss_last": losses[-1],
+        "observation_pts_per_s": M * Kst * ws / t_max,
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "clocks": clk.summary(), "geometry_build_s": geometry_build_s,
+        "walk_nodes_per_step": cstats["nodes"] / max(cstats["steps"], 1),
+        "walk_prims_per_step": cstats["prims"] / max(cstats["steps"], 1),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_cpu, info = inverse_oracle_step_s(w)
+        out["cpu_baseline"] = dict(info, value=1.0 / t_cpu, unit="gradient steps/s", kind="oracle")
+    if rank == 0:
+        print(json.dumps(out))
+    import torch.distributed as td
+    if td.is_initialized():
+        td.destroy_process_group()
+    return 0
+
+
+def inverse_oracle_step_s(w, budget_s: float = 20.0):
+    """The oracle timed on bounded samples of one gradient step of the inverse
+    problem: walks from 64 samples, a gather of 64 points against the full
+    cache, winding numbers of 128 source candidates; a step is the forward
+    solve plus its adjoint (the same walks replayed and the transposed
+    gather), extrapolated as twice the forward's work."""
+    import oracle
+    bvh = oracle.BVH(w.V, w.F)
+    z, _, _ = oracle.sample_boundary(w.V, w.F, 64, w.offset_l, 0)
+    f = [(2, [w.bump_sigma] + [v for a, cc in zip(w.a_true, w.bump_centres) for v in [a, *cc]])]
+    t0 = time.perf_counter()
+    oracle.walks(bvh, [], f, z.astype(np.float32), w.walks, w.eps, MAX_STEPS, 0, 0, 0,
+                 g_vertex=np.zeros(w.V.shape[0]))
+    walk_rate = 64 * w.walks / (time.perf_counter() - t0)
+    N = w.n_samples
+    rng = np.random.default_rng(1)
+    zc = rng.standard_normal((N, 3)) * 0.5
+    nc = rng.standard_normal((N, 3))
+    nc /= np.linalg.norm(nc, axis=1, keepdims=True)
+    t0 = time.perf_counter()
+    oracle.gather(zc, nc, rng.standard_normal(N), rng.standard_normal(N), 1.0, w.obs_pts[:64].astype(np.float64))
+    pair_rate = 64 * N / (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    oracle.winding3d(w.V, w.F, rng.uniform(-1, 1, (16, 3)))
+    wind_rate = 16 / (time.perf_counter() - t0)
+    ncand = w.src_grid[0] * w.src_grid[1] * w.src_grid[2]
+    M = w.obs_pts.shape[0]
+    t_fwd = N * w.walks / walk_rate + M * (N + 0.8 * ncand) / pair_rate + ncand / wind_rate
+    info = {"cores": oracle.num_threads(),
+            "sample": f"64 samples x {w.walks} walks; 64 points x {N} samples; winding numbers of 16 points; "
+                      f"extrapolated to forward + adjoint (2 x forward)",
+            "walks_per_s": walk_rate, "pairs_per_s": pair_rate, "winding_points_per_s": wind_rate}
+    return 2.0 * t_fwd, info
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -617,7 +804,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="star", choices=["star", "circle", "sphere", "batched"])
+    ap.add_argument("--workload", default="star", choices=["star", "circle", "sphere", "batched", "inverse"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed-rmse", action="store_true")
     args = ap.parse_args()
@@ -626,6 +813,21 @@ def main():
 
     if args.impl == "reference":
         if rank != 0:
+            return 0
+        if args.workload == "inverse":
+            from paper_2302_11825_gb300 import workloads as wl
+            wi = wl.inverse_problem()
+            ts = [inverse_oracle_step_s(wi, budget_s=6.0) for _ in range(args.warmup + args.steps)][args.warmup:]
+            t = statistics.mean(x[0] for x in ts)
+            info = ts[-1][1]
+            print(json.dumps({"metric": "inverse problem: gradient steps/s (forward + adjoint, 1 GB300)",
+                              "value": 1.0 / t, "unit": "gradient steps/s", "n_gpus": 0, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                              "impl": "reference", "config": {"workload": wi.name},
+                              "cpu_baseline": dict(info, value=1.0 / t, unit="gradient steps/s", kind="oracle"),
+                              "e2e": {"value": 1.0 / t, "unit": "gradient steps/s", "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}))
             return 0
         if args.workload == "batched":
             from paper_2302_11825_gb300 import workloads as wl
@@ -648,6 +850,8 @@ def main():
 
     if args.workload == "batched":
         return bench_batched(args, rank, local, ws)
+    if args.workload == "inverse":
+        return bench_inverse(args, rank, local, ws)
     import torch
     from paper_2302_11825_gb300 import bvc
     torch.cuda.set_device(local)

@@ -203,16 +203,21 @@ typedef struct {
 } bvc_cache;
 
 /* K4 -- source samples (Alg. 1 "y ~ p^R", Sec. 4 "Sampling"): a jittered
- * grid[0] x grid[1] grid of candidates over the boundary's bounding box;
- * candidate c draws Philox(id = c, word2 = 0, tag = 2) for its position in
- * its cell; it is kept when the canonical FP32 crossing test puts it inside
- * the polygon.  With p = 1/|box| on the box times the indicator of Omega,
- * a kept sample carries c = f(y) |box| and the estimator divides by the
- * candidate count.  Kept samples are stored in candidate order.  2D only
- * (BVC_ERR_UNSUPPORTED in 3D).  Requires cache->n_src_cand = grid[0]*grid[1].
- * Workspace: bvc_sample_source_workspace_size. */
+ * grid[0] x grid[1] (x grid[2] in 3D) grid of candidates over the
+ * boundary's bounding box; candidate c (cell c mod G0, (c / G0) mod G1,
+ * c / (G0 G1)) draws Philox(id = c, word2 = 0, tag = 2) for its position in
+ * its cell.  2D: kept when the canonical FP32 crossing test puts it inside
+ * the polygon.  3D: kept when the generalized winding number of the mesh
+ * (the sum of its triangles' signed solid angles over 4 pi, FP32) is above
+ * 1/2 -- 1 inside a closed outward-wound surface, so holes are wound
+ * inward; overlapping shells are counted with their orientation, not
+ * repaired.  With p = 1/|box| on the box times the indicator of Omega, a
+ * kept sample carries c = f(y) |box| and the estimator divides by the
+ * candidate count.  Kept samples are stored in candidate order.  Requires
+ * cache->n_src_cand = the grid's cell count.  Workspace:
+ * bvc_sample_source_workspace_size. */
 bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes);
-bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[2], uint64_t seed,
+bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[3], uint64_t seed,
                              bvc_cache* cache, void* workspace, size_t workspace_bytes, bvc_stream stream);
 
 /* Pack z, nrm, u_hat, dudn_hat (and the kept source samples) into the
@@ -228,7 +233,8 @@ typedef struct {
   double eps;               /* epsilon shell width */
   uint64_t seed;
   uint64_t walk_id_base;    /* first walk id: distinct caches of one seed use disjoint ranges */
-  int32_t src_grid[2];      /* source candidate grid, {0,0} = no source cache */
+  int32_t src_grid[3];      /* source candidate grid (2D: [0] x [1], [2] unused; 3D: all three),
+                               all 0 = no source cache */
 } bvc_cache_opts;
 
 /* The whole cache: K1 -> K2 (chunked through the workspace) -> K3 -> K4 -> pack.

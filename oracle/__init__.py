@@ -75,6 +75,8 @@ def _load():
                 "orc_walks": (None, [P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_walks_vg": (None, [P, P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_vertex_interp": (f64, [P, P, i64, P]),
+                "orc_winding3d": (f64, [P, P, i64, P]),
+                "orc_sample_source3d": (i64, [P, i64, P, i64, i32, i32, i32, u64, P, P, P, P]),
                 "orc_reduce_walks": (None, [C.c_int, i64, i32, P, P, P, P, P]),
                 "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P]),
                 "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
@@ -277,6 +279,31 @@ def reduce_walks(U, grad, nrm, W: int):
     q_hat = np.zeros(n) if nrm is not None else None
     lib.orc_reduce_walks(dim, n, int(W), _p(U), _p(grad), _p(nrm_a), _p(u_hat), _p(q_hat))
     return u_hat, q_hat
+
+
+def winding3d(V, F, pts):
+    """Generalized winding number of a triangle mesh at each point."""
+    lib = _load()
+    V, F = _f32(V), np.ascontiguousarray(F, dtype=np.int32)
+    return np.array([lib.orc_winding3d(_p(V), _p(F), F.shape[0], _p(np.ascontiguousarray(p, dtype=np.float64)))
+                     for p in np.atleast_2d(pts)])
+
+
+def sample_source3d(V, F, grid, seed: int, f_terms, want_winding=False):
+    """Sec. 4 Sampling in 3D: jittered grid over the bounding box, kept where
+    the winding number exceeds 1/2.  Returns (y [kept][3], c [kept], ncand)
+    and, if asked, every candidate's winding number."""
+    lib = _load()
+    V, F = _f32(V), np.ascontiguousarray(F, dtype=np.int32)
+    ncand = int(grid[0]) * int(grid[1]) * int(grid[2])
+    y = np.zeros((ncand, 3), np.float32)
+    c = np.zeros(ncand)
+    wn = np.zeros(ncand) if want_winding else None
+    f = encode_function(f_terms)
+    k = lib.orc_sample_source3d(_p(V), V.shape[0], _p(F), F.shape[0], int(grid[0]), int(grid[1]), int(grid[2]),
+                                int(seed), _p(f), _p(y), _p(c), _p(wn))
+    out = (y[:k], c[:k], ncand)
+    return out + (wn,) if want_winding else out
 
 
 def sample_source2d(V, F, grid, seed: int, f_terms):

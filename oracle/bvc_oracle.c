@@ -923,6 +923,85 @@ int64_t orc_sample_source2d(const float* V, int64_t nv, const int32_t* F, int64_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Generalized winding number of a triangle mesh at p (Jacobson, Kavan and  */
+/* Sorkine-Hornung, SIGGRAPH 2013): the sum of the signed solid angles of   */
+/* its triangles seen from p over 4 pi.  The solid angle of triangle        */
+/* (a, b, c) relative to p is 2 atan2(A . (B x C), |A||B||C| + (A.B)|C|     */
+/* + (A.C)|B| + (B.C)|A|) with A = a - p, ... (Van Oosterom and Strackee,   */
+/* IEEE TBME 1983).  It is 1 inside a closed outward-wound surface, 0       */
+/* outside, and counts nested or overlapping shells with their orientation, */
+/* which is how an unrepaired self-intersecting boundary is classified.     */
+/* ------------------------------------------------------------------------ */
+double orc_winding3d(const float* V, const int32_t* F, int64_t np, const double* p) {
+  double w = 0.0;
+  for (int64_t e = 0; e < np; ++e) {
+    double A[3], B[3], Cc[3];
+    for (int a = 0; a < 3; ++a) {
+      A[a] = (double)V[3 * (int64_t)F[3 * e] + a] - p[a];
+      B[a] = (double)V[3 * (int64_t)F[3 * e + 1] + a] - p[a];
+      Cc[a] = (double)V[3 * (int64_t)F[3 * e + 2] + a] - p[a];
+    }
+    const double la = sqrt(dot3d(A, A)), lb = sqrt(dot3d(B, B)), lc = sqrt(dot3d(Cc, Cc));
+    const double bxc[3] = {B[1] * Cc[2] - B[2] * Cc[1], B[2] * Cc[0] - B[0] * Cc[2], B[0] * Cc[1] - B[1] * Cc[0]};
+    const double num = dot3d(A, bxc);
+    const double den = la * lb * lc + dot3d(A, B) * lc + dot3d(A, Cc) * lb + dot3d(B, Cc) * la;
+    w += 2.0 * atan2(num, den);
+  }
+  return w / (4.0 * ORC_PI);
+}
+
+/* Source samples in 3D (Sec. 4 "Sampling"): a jittered grid of G0 x G1 x  */
+/* G2 cells over the bounding box; candidate c (cell c0 = c mod G0,         */
+/* c1 = (c / G0) mod G1, c2 = c / (G0 G1)) draws (u0,u1,u2) from Philox      */
+/* (id = c, word2 = 0, tag = 2) and is kept when the winding number is      */
+/* above 1/2.  Weight f(y) |box|; the estimator divides by G0 G1 G2.         */
+/* winding_out (may be NULL) receives every candidate's winding number.     */
+int64_t orc_sample_source3d(const float* V, int64_t nv, const int32_t* F, int64_t np, int32_t G0, int32_t G1,
+                            int32_t G2, uint64_t seed, const double* f, float* y_out, double* c_out,
+                            double* winding_out) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < nv; ++i)
+    for (int a = 0; a < 3; ++a) {
+      if (V[3 * i + a] < lo[a]) lo[a] = V[3 * i + a];
+      if (V[3 * i + a] > hi[a]) hi[a] = V[3 * i + a];
+    }
+  const double ext[3] = {(double)hi[0] - lo[0], (double)hi[1] - lo[1], (double)hi[2] - lo[2]};
+  const int32_t G[3] = {G0, G1, G2};
+  const double vol = ext[0] * ext[1] * ext[2];
+  const int64_t ncand = (int64_t)G0 * G1 * G2;
+  float* yc = (float*)malloc((size_t)ncand * 3 * sizeof(float));
+  uint8_t* keep = (uint8_t*)malloc((size_t)ncand);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t c = 0; c < ncand; ++c) {
+    double u[4];
+    draw(seed, (uint64_t)c, 0u, 2u, u);
+    const int64_t ci[3] = {c % G0, (c / G0) % G1, c / ((int64_t)G0 * G1)};
+    double y[3];
+    for (int a = 0; a < 3; ++a) {
+      yc[3 * c + a] = (float)((double)lo[a] + ((double)ci[a] + u[a]) * (ext[a] / G[a]));
+      y[a] = yc[3 * c + a];
+    }
+    const double w = orc_winding3d(V, F, np, y);
+    if (winding_out) winding_out[c] = w;
+    keep[c] = w > 0.5;
+  }
+  int64_t kept = 0;
+  for (int64_t c = 0; c < ncand; ++c) {
+    if (!keep[c]) continue;
+    double y[3];
+    for (int a = 0; a < 3; ++a) {
+      y_out[3 * kept + a] = yc[3 * c + a];
+      y[a] = yc[3 * c + a];
+    }
+    c_out[kept] = orc_fn_eval(f, 3, y) * vol;
+    ++kept;
+  }
+  free(yc);
+  free(keep);
+  return kept;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The gather: Eq. 3-6 and the splat loops of Alg. 1, as a direct double    */
 /* loop.  For every evaluation point x and boundary sample (z, n, u^, q^):  */
 /*   u_bnd    += (dG/dn(x,z) u^ - G(x,z) q^) / p,        p = 1/|dOmega|      */

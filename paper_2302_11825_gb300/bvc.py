@@ -59,7 +59,7 @@ class CacheStruct(C.Structure):
 class CacheOpts(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("walks_per_sample", C.c_int32), ("max_steps", C.c_int32),
                 ("offset_l", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64),
-                ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 2)]
+                ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 3)]
 
 
 class MultiCacheStruct(C.Structure):
@@ -361,11 +361,18 @@ class Cache:
         self.bnd_measure = float(self.struct.bnd_measure)
 
 
+def n_candidates(dim: int, src_grid) -> int:
+    """Source candidates of a grid: G0 x G1 (2D) or G0 x G1 x G2 (3D)."""
+    g = list(src_grid) + [0] * (3 - len(src_grid))
+    return int(g[0]) * int(g[1]) * (int(g[2]) if dim == 3 else 1)
+
+
 def cache_opts(n_samples, walks, offset_l, eps, seed, max_steps=1 << 14, walk_id_base=0, src_grid=(0, 0)):
     o = CacheOpts()
     o.n_samples, o.walks_per_sample, o.max_steps = int(n_samples), int(walks), int(max_steps)
     o.offset_l, o.eps, o.seed, o.walk_id_base = float(offset_l), float(eps), int(seed), int(walk_id_base)
     o.src_grid[0], o.src_grid[1] = int(src_grid[0]), int(src_grid[1])
+    o.src_grid[2] = int(src_grid[2]) if len(src_grid) > 2 else 0
     return o
 
 
@@ -397,7 +404,7 @@ def sample_source(geom: Geometry, f_terms, grid, seed: int, cache: Cache, ws: to
     if ws is None:
         ws = workspace(need.value)
     f = make_function(f_terms)
-    gr = (C.c_int32 * 2)(int(grid[0]), int(grid[1]))
+    gr = (C.c_int32 * 3)(int(grid[0]), int(grid[1]), int(grid[2]) if len(grid) > 2 else 0)
     _check(lib().bvc_sample_source(geom.h, C.byref(f), gr, int(seed), C.byref(cache.struct), _ptr(ws), ws.numel(),
                                    _stream(stream)), "bvc_sample_source")
 
@@ -552,7 +559,7 @@ class DiffSolver:
         self.bumps = bumps
         self.opts = cache_opts(n_samples, walks, offset_l, eps, seed, max_steps=max_steps,
                                src_grid=src_grid if bumps else (0, 0))
-        self.n_src = self.opts.src_grid[0] * self.opts.src_grid[1]
+        self.n_src = n_candidates(self.dim, self.opts.src_grid)
         self.ws = workspace(cache_build_workspace_size(geom, self.opts)[1])
         self.n_verts = geom.info().n_verts
 

@@ -1,6 +1,7 @@
 // bvc_source.cu -- source samples (K4): jittered candidates over the
-// bounding box, kept by the canonical FP32 crossing test, compacted in
-// candidate order by a deterministic block scan.
+// bounding box, kept by the canonical FP32 crossing test (2D) or a winding
+// number above 1/2 (3D), compacted in candidate order by a deterministic
+// block scan.
 #include <cmath>
 
 #include "bvc_device.cuh"
@@ -14,15 +15,15 @@ constexpr int kSegTile = 1024;
 struct SrcParams {
   DevGeometry G;
   DevFunction f;
-  int32_t G0, G1;
+  int32_t G0, G1, G2;
   uint64_t seed;
-  double lo0, lo1, h0, h1, box;
+  double lo0, lo1, lo2, h0, h1, h2, box;
   int64_t ncand;
-  float* yc;          // [2][ncand] candidate positions (workspace)
+  float* yc;          // [dim][ncand] candidate positions (workspace)
   uint8_t* flag;      // [ncand] (workspace)
   int64_t* bcount;    // [nblocks] (workspace)
   int64_t* boff;      // [nblocks] (workspace)
-  float* src_y;       // [2][ncand]
+  float* src_y;       // [dim][ncand]
   double* src_c;      // [ncand]
   int64_t* n_src;     // [1]
   int64_t nblocks;
@@ -96,7 +97,65 @@ __global__ void __launch_bounds__(1024) k_src_scan(const SrcParams S) {
   }
 }
 
+// 3D: candidate position as in 2D, kept when the generalized winding number
+// of the triangle mesh (Jacobson et al. 2013) is above 1/2: the sum over the
+// triangles, staged through shared memory, of their signed solid angles
+// 2 atan2(A.(BxC), |A||B||C| + (A.B)|C| + (A.C)|B| + (B.C)|A|) (Van Oosterom
+// and Strackee 1983) over 4 pi.  It is 1 inside a closed outward-wound
+// surface and counts overlapping or nested shells with their orientation
+// (an unrepaired self-intersecting boundary is classified the same way).
+constexpr int kTriTile = 256;
+__global__ void __launch_bounds__(kSrcBlock) k_src_classify3d(const SrcParams S) {
+  __shared__ float4 tri[3][kTriTile];
+  const int64_t c = blockIdx.x * (int64_t)kSrcBlock + threadIdx.x;
+  float p[3] = {0.0f, 0.0f, 0.0f};
+  if (c < S.ncand) {
+    const U4 r = philox_draw(S.seed, (uint64_t)c, 0u, 2u);
+    const int64_t ci[3] = {c % S.G0, (c / S.G0) % S.G1, c / ((int64_t)S.G0 * S.G1)};
+    const double lo[3] = {S.lo0, S.lo1, S.lo2}, h[3] = {S.h0, S.h1, S.h2};
+    const double u[3] = {u01d(r.x), u01d(r.y), u01d(r.z)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      p[a] = __double2float_rn(__dadd_rn(lo[a], __dmul_rn(__dadd_rn((double)ci[a], u[a]), h[a])));
+      S.yc[a * S.ncand + c] = p[a];
+    }
+  }
+  float wsum = 0.0f;
+  const int64_t np = S.G.n_prims;
+  for (int64_t base = 0; base < np; base += kTriTile) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kTriTile && base + q < np; q += kSrcBlock) {
+      const int32_t* f = S.G.idx + 3 * (base + q);
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+        tri[v][q] = make_float4(S.G.verts[3 * f[v]], S.G.verts[3 * f[v] + 1], S.G.verts[3 * f[v] + 2], 0.0f);
+    }
+    __syncthreads();
+    const int cnt = (int)min64(kTriTile, np - base);
+    for (int q = 0; q < cnt; ++q) {
+      const float4 ta = tri[0][q], tb = tri[1][q], tc = tri[2][q];
+      const float ax = ta.x - p[0], ay = ta.y - p[1], az = ta.z - p[2];
+      const float bx = tb.x - p[0], by = tb.y - p[1], bz = tb.z - p[2];
+      const float cx = tc.x - p[0], cy = tc.y - p[1], cz = tc.z - p[2];
+      const float la = sqrtf(fmaf(az, az, fmaf(ay, ay, ax * ax)));
+      const float lb = sqrtf(fmaf(bz, bz, fmaf(by, by, bx * bx)));
+      const float lc = sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
+      const float num = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+      const float ab = fmaf(az, bz, fmaf(ay, by, ax * bx)), ac = fmaf(az, cz, fmaf(ay, cy, ax * cx));
+      const float bc = fmaf(bz, cz, fmaf(by, cy, bx * cx));
+      const float den = fmaf(bc, la, fmaf(ac, lb, fmaf(ab, lc, la * lb * lc)));
+      wsum += atan2f(num, den);
+    }
+  }
+  // winding = 2 sum / (4 pi) > 1/2  <=>  sum > pi / 2
+  const int keep = (c < S.ncand) ? (wsum > 1.57079632679489662f) : 0;
+  if (c < S.ncand) S.flag[c] = (uint8_t)keep;
+  const int cnt = __syncthreads_count(keep);
+  if (threadIdx.x == 0) S.bcount[blockIdx.x] = cnt;
+}
+
 // Stable scatter of kept candidates; weight f(y) |box| (p = 1/|box| on the box).
+template <int D>
 __global__ void __launch_bounds__(kSrcBlock) k_src_scatter(const SrcParams S) {
   __shared__ int wsum[kSrcBlock / 32];
   const int64_t c = blockIdx.x * (int64_t)kSrcBlock + threadIdx.x;
@@ -110,15 +169,19 @@ __global__ void __launch_bounds__(kSrcBlock) k_src_scatter(const SrcParams S) {
   before += __popc(bal & ((1u << lane) - 1u));
   if (keep) {
     const int64_t j = S.boff[blockIdx.x] + before;
-    float y[2] = {S.yc[c], S.yc[S.ncand + c]};
-    S.src_y[j] = y[0];
-    S.src_y[S.ncand + j] = y[1];
-    S.src_c[j] = (double)eval_fn<2>(S.f, y) * S.box;
+    float y[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      y[a] = S.yc[a * S.ncand + c];
+      S.src_y[a * S.ncand + j] = y[a];
+    }
+    S.src_c[j] = (double)eval_fn<D>(S.f, y) * S.box;
   }
 }
 
 // dL/dA_k += sum_j dL/dc_j |box| psi_k(y_j) over the kept candidates (c_j =
 // f(y_j) |box|): FP64 per thread, fixed-order warp sums, one atomic per warp.
+template <int D>
 __global__ void __launch_bounds__(256) k_src_adjoint(DevFunction f, const float* __restrict__ src_y, int64_t ncand,
                                                     const int64_t* __restrict__ n_src, double box,
                                                     const double* __restrict__ adj, double* __restrict__ grad_amp) {
@@ -127,9 +190,11 @@ __global__ void __launch_bounds__(256) k_src_adjoint(DevFunction f, const float*
   for (int b = 0; b < kMaxBumps; ++b) acc[b] = 0.0;
   const int64_t nk = *n_src;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x) {
-    const float y[2] = {src_y[j], src_y[ncand + j]};
+    float y[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) y[a] = src_y[a * ncand + j];
     float psi[kMaxBumps];
-    bump_shapes<2>(f, y, psi);
+    bump_shapes<D>(f, y, psi);
     const double a = adj[j] * box;
 #pragma unroll
     for (int b = 0; b < kMaxBumps; ++b) acc[b] += a * (double)psi[b];
@@ -150,17 +215,21 @@ using namespace bvc;
 namespace bvc {
 bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache* cache, const double* adj,
                               double* grad_amp, cudaStream_t s) {
-  if (g->dim != 2) return BVC_ERR_UNSUPPORTED;
   DevFunction f;
-  if (!make_dev_function(ffn, 2, &f)) return BVC_ERR_INVALID_ARG;
-  const double ext0 = (double)g->hi[0] - (double)g->lo[0], ext1 = (double)g->hi[1] - (double)g->lo[1];
+  if (!make_dev_function(ffn, g->dim, &f)) return BVC_ERR_INVALID_ARG;
+  double box = 1.0;
+  for (int a = 0; a < g->dim; ++a) box *= (double)g->hi[a] - (double)g->lo[a];
   int64_t blocks = (cache->n_src_cand + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   ProfScope ps("adjoint_source", s);
-  k_src_adjoint<<<(unsigned)blocks, 256, 0, s>>>(f, cache->src_y, cache->n_src_cand, cache->n_src_dev, ext0 * ext1,
-                                                 adj, grad_amp);
+  if (g->dim == 2)
+    k_src_adjoint<2><<<(unsigned)blocks, 256, 0, s>>>(f, cache->src_y, cache->n_src_cand, cache->n_src_dev, box, adj,
+                                                      grad_amp);
+  else
+    k_src_adjoint<3><<<(unsigned)blocks, 256, 0, s>>>(f, cache->src_y, cache->n_src_cand, cache->n_src_dev, box, adj,
+                                                      grad_amp);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -171,39 +240,43 @@ static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 extern "C" bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes) {
   if (n_cand < 0 || bytes == nullptr) return BVC_ERR_INVALID_ARG;
   const int64_t nb = (n_cand + kSrcBlock - 1) / kSrcBlock;
-  *bytes = al256((size_t)n_cand * 2 * sizeof(float)) + al256((size_t)n_cand) + 2 * al256((size_t)nb * 8);
+  *bytes = al256((size_t)n_cand * 3 * sizeof(float)) + al256((size_t)n_cand) + 2 * al256((size_t)nb * 8);
   return BVC_OK;
 }
 
-extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[2], uint64_t seed,
+extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[3], uint64_t seed,
                                         bvc_cache* cache, void* workspace, size_t workspace_bytes,
                                         bvc_stream stream) {
   if (g == nullptr || grid == nullptr || cache == nullptr) return BVC_ERR_INVALID_ARG;
-  if (g->dim != 2) return BVC_ERR_UNSUPPORTED;
-  const int64_t ncand = (int64_t)grid[0] * grid[1];
-  if (grid[0] < 1 || grid[1] < 1 || ncand != cache->n_src_cand || cache->src_y == nullptr ||
-      cache->src_c == nullptr || cache->n_src_dev == nullptr || workspace == nullptr)
+  const int D = g->dim;
+  const int64_t ncand = (int64_t)grid[0] * grid[1] * (D == 3 ? grid[2] : 1);
+  if (grid[0] < 1 || grid[1] < 1 || (D == 3 && grid[2] < 1) || ncand != cache->n_src_cand ||
+      cache->src_y == nullptr || cache->src_c == nullptr || cache->n_src_dev == nullptr || workspace == nullptr)
     return BVC_ERR_INVALID_ARG;
   size_t need = 0;
   bvc_sample_source_workspace_size(ncand, &need);
   if (workspace_bytes < need) return BVC_ERR_WORKSPACE;
   SrcParams S{};
   S.G = g->dev;
-  if (!make_dev_function(ffn, 2, &S.f)) return BVC_ERR_INVALID_ARG;
+  if (!make_dev_function(ffn, D, &S.f)) return BVC_ERR_INVALID_ARG;
   S.G0 = grid[0];
   S.G1 = grid[1];
+  S.G2 = D == 3 ? grid[2] : 1;
   S.seed = seed;
   S.lo0 = g->lo[0];
   S.lo1 = g->lo[1];
+  S.lo2 = g->lo[2];
   const double ext0 = (double)g->hi[0] - (double)g->lo[0], ext1 = (double)g->hi[1] - (double)g->lo[1];
+  const double ext2 = D == 3 ? (double)g->hi[2] - (double)g->lo[2] : 1.0;
   S.h0 = ext0 / grid[0];
   S.h1 = ext1 / grid[1];
-  S.box = ext0 * ext1;
+  S.h2 = ext2 / S.G2;
+  S.box = ext0 * ext1 * ext2;
   S.ncand = ncand;
   S.nblocks = (ncand + kSrcBlock - 1) / kSrcBlock;
   char* w = (char*)workspace;
   S.yc = (float*)w;
-  w += al256((size_t)ncand * 2 * sizeof(float));
+  w += al256((size_t)ncand * 3 * sizeof(float));
   S.flag = (uint8_t*)w;
   w += al256((size_t)ncand);
   S.bcount = (int64_t*)w;
@@ -215,7 +288,10 @@ extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn,
   cudaStream_t s = (cudaStream_t)stream;
   {
     ProfScope ps("source_classify", s);
-    k_src_classify<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+    if (D == 2)
+      k_src_classify<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+    else
+      k_src_classify3d<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
   }
   {
     ProfScope ps("source_scan", s);
@@ -223,7 +299,10 @@ extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn,
   }
   {
     ProfScope ps("source_scatter", s);
-    k_src_scatter<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+    if (D == 2)
+      k_src_scatter<2><<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+    else
+      k_src_scatter<3><<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
   }
   BVC_LAUNCH_CHECK();
   return BVC_OK;

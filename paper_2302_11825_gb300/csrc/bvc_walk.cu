@@ -560,6 +560,11 @@ static bvc_status launch_reduce(const ReduceParams& R, cudaStream_t s) {
   return BVC_OK;
 }
 
+// Source candidates of a cache build: G0 x G1 (2D) or G0 x G1 x G2 (3D).
+static int64_t src_candidates(const bvc_cache_opts* o, int dim) {
+  return (int64_t)o->src_grid[0] * o->src_grid[1] * (dim == 3 ? o->src_grid[2] : 1);
+}
+
 static bool valid_walk_args(float eps, int32_t max_steps, int32_t walks) {
   return std::isfinite(eps) && eps > 0.0f && max_steps >= 1 && walks >= 1;
 }
@@ -637,7 +642,7 @@ extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_c
     return BVC_ERR_INVALID_ARG;
   const size_t per_sample = ws_per_start(g->dim, opts->walks_per_sample, 1);
   size_t src = 0;
-  const int64_t ncand = (int64_t)opts->src_grid[0] * opts->src_grid[1];
+  const int64_t ncand = src_candidates(opts, g->dim);
   if (ncand > 0) bvc_sample_source_workspace_size(ncand, &src);
   const size_t mn = 2 * kWsHead + per_sample, full = 2 * kWsHead + per_sample * (size_t)opts->n_samples;
   if (min_bytes) *min_bytes = mn > src ? mn : src;
@@ -656,7 +661,7 @@ static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const flo
       !(opts->offset_l > 0.0) || cache->z == nullptr || cache->nrm == nullptr || cache->u_hat == nullptr ||
       cache->dudn_hat == nullptr || cache->packed == nullptr || workspace == nullptr)
     return BVC_ERR_INVALID_ARG;
-  const int64_t ncand = (int64_t)opts->src_grid[0] * opts->src_grid[1];
+  const int64_t ncand = src_candidates(opts, D);
   if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
   WalkParams P{};
   P.G = g->dev;
@@ -1323,7 +1328,7 @@ extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs
   if (!valid_multi(cache, D) || cache->n != N || !valid_walk_args((float)opts->eps, opts->max_steps, W) ||
       !(opts->offset_l > 0.0))
     return BVC_ERR_INVALID_ARG;
-  if (opts->src_grid[0] * opts->src_grid[1] != 0) return BVC_ERR_UNSUPPORTED;  // f = 0 only
+  if (src_candidates(opts, D) != 0) return BVC_ERR_UNSUPPORTED;  // f = 0 only
   const size_t per = ws_per_start(D, W, D);
   int64_t chunk = ws_chunk(workspace_bytes, per);
   if (chunk < 1) return BVC_ERR_WORKSPACE;

@@ -510,3 +510,123 @@ def batched_laplace(n_meshes: int = 16, n_samples: int = 32768, walks: int = 128
     eps = [1e-3 * bbox_diagonal(m[1]) for m in meshes]
     return BatchedWorkload(f"batched{n_meshes}_laplace_k{k}", meshes, n_samples, walks, n_points, k, coeffs, pts,
                            eps, [5.0 * e for e in eps])
+
+
+# ---------------------------------------------------------------- box with obstacles
+def box_surface(lo, hi, cells_per_unit: int):
+    """Surface of an axis-aligned box as a triangle grid, wound outward."""
+    lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+    n = [max(1, int(round((hi[a] - lo[a]) * cells_per_unit))) for a in range(3)]
+    V, F = [], []
+    for axis in range(3):
+        u, v = [(1, 2), (2, 0), (0, 1)][axis]
+        for side, val in ((0, lo[axis]), (1, hi[axis])):
+            nu, nv = n[u], n[v]
+            base = sum(len(x) for x in V)
+            grid = np.zeros(((nu + 1) * (nv + 1), 3))
+            iu, iv = np.meshgrid(np.arange(nu + 1), np.arange(nv + 1), indexing="ij")
+            grid[:, axis] = val
+            grid[:, u] = lo[u] + iu.ravel() * (hi[u] - lo[u]) / nu
+            grid[:, v] = lo[v] + iv.ravel() * (hi[v] - lo[v]) / nv
+            V.append(grid)
+            for i in range(nu):
+                for j in range(nv):
+                    a = base + i * (nv + 1) + j
+                    b, c, d = a + (nv + 1), a + (nv + 1) + 1, a + 1
+                    # (u, v, axis) is right-handed: u x v = +axis
+                    tri = [(a, b, c), (a, c, d)] if side == 1 else [(a, c, b), (a, d, c)]
+                    F.extend(tri)
+    V = np.concatenate(V)
+    # merge duplicated edge vertices
+    key = np.round(V * 1e6).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    return V[first].astype(np.float32), inv.ravel()[np.asarray(F)].astype(np.int32)
+
+
+def box_with_obstacles(lo=(-2.0, -1.0, -1.0), hi=(2.0, 1.0, 1.0), n_box: int = 8, ellipsoids=(), subdiv: int = 4,
+                       seed: int = 0, amp: float = 0.0):
+    """The boundary of a box minus a union of ellipsoids: the box wound
+    outward, each ellipsoid (an icosphere scaled by its semi-axes, optionally
+    radially perturbed) wound inward.  Overlapping ellipsoids are left as
+    they are (a self-intersecting boundary, no repair)."""
+    Vb, Fb = box_surface(lo, hi, n_box)
+    Vs, Fs = [Vb], [Fb]
+    off = Vb.shape[0]
+    for k, (c, ax) in enumerate(ellipsoids):
+        Ve, Fe = perturbed_ellipsoid(subdiv, ax, seed + k, amp=amp, centre=c) if amp > 0 else (None, None)
+        if Ve is None:
+            Vi, Fi = icosphere(subdiv)
+            Ve = (Vi * np.asarray(ax)[None, :] + np.asarray(c)[None, :]).astype(np.float32)
+            Fe = Fi
+        Vs.append(Ve)
+        Fs.append(Fe[:, ::-1] + off)
+        off += Ve.shape[0]
+    return np.concatenate(Vs).astype(np.float32), np.concatenate(Fs).astype(np.int32)
+
+
+@dataclass
+class InverseWorkload:
+    """Differentiable inverse problem: Delta u = f in a box minus a union of
+    overlapping ellipsoids, u = g on its (self-intersecting, unrepaired)
+    boundary; g at the mesh vertices = Phi c with Gaussian radial basis
+    functions (rbf_centres, rbf_sigma), f = sum_k A_k Gaussian bumps."""
+    name: str
+    V: np.ndarray
+    F: np.ndarray
+    ellipsoids: list
+    rbf_centres: np.ndarray
+    rbf_sigma: float
+    bump_centres: np.ndarray
+    bump_sigma: float
+    c_true: np.ndarray
+    a_true: np.ndarray
+    obs_pts: np.ndarray
+    n_samples: int
+    walks: int
+    eps: float
+    offset_l: float
+    src_grid: tuple
+
+
+def in_domain_box_obstacles(p, lo, hi, ellipsoids, margin: float) -> np.ndarray:
+    """Points inside the box and outside every ellipsoid, at least `margin`
+    (box walls) or a relative margin (ellipsoids) away from the boundary."""
+    p = np.asarray(p, dtype=np.float64)
+    ok = np.all((p > np.asarray(lo) + margin) & (p < np.asarray(hi) - margin), axis=1)
+    for c, ax in ellipsoids:
+        r = np.sqrt(np.sum(((p - np.asarray(c)) / np.asarray(ax)) ** 2, axis=1))
+        ok &= r > 1.0 + margin / min(ax)
+    return ok
+
+
+def inverse_problem(n_obs: int = 100000, n_samples: int = 65536, walks: int = 64, subdiv: int = 6,
+                    n_rbf: int = 256, seed: int = 0) -> InverseWorkload:
+    """Box [-2,2] x [-1,1]^2 with an obstacle of 5 overlapping ellipsoids
+    (icospheres of subdivision 6, 81920 triangles each: about 410k
+    triangles); g = Phi c with 256 Gaussian RBFs centred at seeded boundary
+    vertices; 8 Gaussian source bumps; 100k seeded interior observation
+    points; 65536 samples x 64 walks and a 64 x 32 x 32 source grid (the
+    configuration fixes neither).  eps = 1e-3 x bbox diagonal, l = 5 eps."""
+    rng = np.random.default_rng(seed)
+    lo, hi = (-2.0, -1.0, -1.0), (2.0, 1.0, 1.0)
+    ell = []
+    for k in range(5):
+        c = (-0.8 + 0.4 * k + rng.uniform(-0.05, 0.05), rng.uniform(-0.15, 0.15), rng.uniform(-0.15, 0.15))
+        ax = tuple(rng.uniform(0.3, 0.45, 3))
+        ell.append((c, ax))
+    V, F = box_with_obstacles(lo, hi, n_box=8, ellipsoids=ell, subdiv=subdiv)
+    rbf_c = V[rng.choice(V.shape[0], n_rbf, replace=False)].astype(np.float64)
+    bc = []
+    while len(bc) < 8:
+        q = rng.uniform(lo, hi, (64, 3))
+        q = q[in_domain_box_obstacles(q, lo, hi, ell, 0.3)]
+        bc.extend(q[: 8 - len(bc)])
+    obs = []
+    while sum(len(o) for o in obs) < n_obs:
+        q = rng.uniform(lo, hi, (2 * n_obs, 3))
+        obs.append(q[in_domain_box_obstacles(q, lo, hi, ell, 0.05)])
+    obs = np.concatenate(obs)[:n_obs].astype(np.float32)
+    eps = 1e-3 * bbox_diagonal(V)
+    return InverseWorkload(f"inverse_box5ellipsoids_{F.shape[0] // 1000}k", V, F, ell, rbf_c, 0.4,
+                           np.asarray(bc), 0.15, rng.standard_normal(n_rbf), rng.uniform(-10, 10, 8), obs,
+                           n_samples, walks, eps, 5 * eps, (64, 32, 32))

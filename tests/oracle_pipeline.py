@@ -19,7 +19,10 @@ def oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid=None, max_steps=1 << 1
              "measure": oracle.boundary_measure(V, F), "walks": out, "N": N,
              "y": None, "c": None, "n_src": 0}
     if f and src_grid is not None:
-        y, c, ncand = oracle.sample_source2d(V, F, src_grid, seed, f)
+        if V.shape[1] == 2:
+            y, c, ncand = oracle.sample_source2d(V, F, src_grid, seed, f)
+        else:
+            y, c, ncand = oracle.sample_source3d(V, F, src_grid, seed, f)
         cache.update(y=y, c=c, n_src=ncand)
     return cache
 
