@@ -650,7 +650,7 @@ def bench_inverse(args, rank, local, ws):
         obs = u_true + 0.01 * u_true.std() * torch.randn(M, generator=gen, device=device, dtype=torch.float64)
     c = torch.zeros(256, dtype=torch.float64, device=device, requires_grad=True)
     a = torch.zeros(8, dtype=torch.float64, device=device, requires_grad=True)
-    opt = torch.optim.Adam([c, a], lr=0.2)
+    opt = torch.optim.Adam([c, a], lr=0.05)
 
     def loss_of(cc, aa):
         u = solver(Phi @ cc, aa)
@@ -687,7 +687,7 @@ def bench_inverse(args, rank, local, ws):
 
     losses = []
     for k in range(args.warmup):
-        losses.append(float(step()))
+        losses.append(float(step().detach()))
     torch.cuda.synchronize()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -700,7 +700,7 @@ def bench_inverse(args, rank, local, ws):
             evs[k][0].record()
             L = step()
             evs[k][1].record()
-            losses.append(float(L))
+            losses.append(float(L.detach()))
         prof = bvc.profile_end()
         torch.cuda.synchronize()
     barrier()

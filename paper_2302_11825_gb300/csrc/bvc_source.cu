@@ -2,6 +2,7 @@
 // bounding box, kept by the canonical FP32 crossing test (2D) or a winding
 // number above 1/2 (3D), compacted in candidate order by a deterministic
 // block scan.
+#include <algorithm>
 #include <cmath>
 
 #include "bvc_device.cuh"
@@ -23,6 +24,8 @@ struct SrcParams {
   uint8_t* flag;      // [ncand] (workspace)
   int64_t* bcount;    // [nblocks] (workspace)
   int64_t* boff;      // [nblocks] (workspace)
+  float* theta;       // [slices][ncand] 3D partial angle sums (workspace)
+  int32_t slices;     // 3D: triangle slices per candidate
   float* src_y;       // [dim][ncand]
   double* src_c;      // [ncand]
   int64_t* n_src;     // [1]
@@ -98,16 +101,29 @@ __global__ void __launch_bounds__(1024) k_src_scan(const SrcParams S) {
 }
 
 // 3D: candidate position as in 2D, kept when the generalized winding number
-// of the triangle mesh (Jacobson et al. 2013) is above 1/2: the sum over the
-// triangles, staged through shared memory, of their signed solid angles
-// 2 atan2(A.(BxC), |A||B||C| + (A.B)|C| + (A.C)|B| + (B.C)|A|) (Van Oosterom
-// and Strackee 1983) over 4 pi.  It is 1 inside a closed outward-wound
-// surface and counts overlapping or nested shells with their orientation
-// (an unrepaired self-intersecting boundary is classified the same way).
+// of the triangle mesh (Jacobson et al. 2013) is above 1/2.  Each triangle
+// subtends the solid angle 2 theta, theta = arg(den + i num) with
+// num = A.(BxC), den = |A||B||C| + (A.B)|C| + (A.C)|B| + (B.C)|A| (Van
+// Oosterom and Strackee 1983), so w = sum theta / (2 pi).  Rather than one
+// arctangent per triangle, the kernel multiplies the complex numbers
+// (den + i num) -- scaled to unit size -- into a running product and counts
+// the product's crossings of the negative real axis (each factor turns it
+// by |theta| < pi, counter-clockwise when num > 0); then
+// sum theta = 2 pi crossings + arg(product), one arctangent per candidate.
+// Triangles are staged through shared memory.  It is 1 inside a closed
+// outward-wound surface and counts overlapping or nested shells with their
+// orientation (an unrepaired self-intersecting boundary is classified the
+// same way).
+// The triangles are split into S.slices contiguous ranges (blockIdx.y), so
+// that enough blocks run for the latency of each thread's serial product to
+// be hidden; every slice writes its partial angle sum and k_src_flag3d adds
+// the slices in a fixed order.
 constexpr int kTriTile = 256;
+constexpr int kMaxSlices = 16;
 __global__ void __launch_bounds__(kSrcBlock) k_src_classify3d(const SrcParams S) {
   __shared__ float4 tri[3][kTriTile];
   const int64_t c = blockIdx.x * (int64_t)kSrcBlock + threadIdx.x;
+  const int slice = blockIdx.y;
   float p[3] = {0.0f, 0.0f, 0.0f};
   if (c < S.ncand) {
     const U4 r = philox_draw(S.seed, (uint64_t)c, 0u, 2u);
@@ -117,12 +133,14 @@ __global__ void __launch_bounds__(kSrcBlock) k_src_classify3d(const SrcParams S)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       p[a] = __double2float_rn(__dadd_rn(lo[a], __dmul_rn(__dadd_rn((double)ci[a], u[a]), h[a])));
-      S.yc[a * S.ncand + c] = p[a];
+      if (slice == 0) S.yc[a * S.ncand + c] = p[a];
     }
   }
-  float wsum = 0.0f;
-  const int64_t np = S.G.n_prims;
-  for (int64_t base = 0; base < np; base += kTriTile) {
+  float zr = 1.0f, zi = 0.0f;
+  int crossings = 0;
+  const int64_t per = (S.G.n_prims + S.slices - 1) / S.slices;
+  const int64_t t0 = slice * per, np = min64(S.G.n_prims, t0 + per);
+  for (int64_t base = t0; base < np; base += kTriTile) {
     __syncthreads();
     for (int q = threadIdx.x; q < kTriTile && base + q < np; q += kSrcBlock) {
       const int32_t* f = S.G.idx + 3 * (base + q);
@@ -137,19 +155,49 @@ __global__ void __launch_bounds__(kSrcBlock) k_src_classify3d(const SrcParams S)
       const float ax = ta.x - p[0], ay = ta.y - p[1], az = ta.z - p[2];
       const float bx = tb.x - p[0], by = tb.y - p[1], bz = tb.z - p[2];
       const float cx = tc.x - p[0], cy = tc.y - p[1], cz = tc.z - p[2];
-      const float la = sqrtf(fmaf(az, az, fmaf(ay, ay, ax * ax)));
-      const float lb = sqrtf(fmaf(bz, bz, fmaf(by, by, bx * bx)));
-      const float lc = sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
+      const float a2 = fmaf(az, az, fmaf(ay, ay, ax * ax));
+      const float b2 = fmaf(bz, bz, fmaf(by, by, bx * bx));
+      const float c2 = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
+      const float la = a2 * rsqrtf(a2), lb = b2 * rsqrtf(b2), lc = c2 * rsqrtf(c2);
       const float num = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
       const float ab = fmaf(az, bz, fmaf(ay, by, ax * bx)), ac = fmaf(az, cz, fmaf(ay, cy, ax * cx));
       const float bc = fmaf(bz, cz, fmaf(by, cy, bx * cx));
       const float den = fmaf(bc, la, fmaf(ac, lb, fmaf(ab, lc, la * lb * lc)));
-      wsum += atan2f(num, den);
+      const float m = fmaxf(fabsf(num), fabsf(den));
+      if (!(m > 0.0f) || !(m < 3.0e38f)) continue;  // degenerate (the point on the triangle's edges)
+      const float sc = __frcp_rn(m);
+      const float wr = den * sc, wi = num * sc;
+      const float nr = fmaf(zr, wr, -zi * wi), ni = fmaf(zr, wi, zi * wr);
+      crossings += (zi >= 0.0f && ni < 0.0f && num > 0.0f) ? 1 : 0;
+      crossings -= (zi < 0.0f && ni >= 0.0f && num < 0.0f) ? 1 : 0;
+      // |w| is in [1, sqrt 2]: renormalise the product every 16 factors
+      if ((q & 15) == 15) {
+        const float t = rsqrtf(fmaf(ni, ni, nr * nr));
+        zr = nr * t;
+        zi = ni * t;
+      } else {
+        zr = nr;
+        zi = ni;
+      }
     }
+    const float t = rsqrtf(fmaf(zi, zi, zr * zr));
+    zr *= t;
+    zi *= t;
   }
-  // winding = 2 sum / (4 pi) > 1/2  <=>  sum > pi / 2
-  const int keep = (c < S.ncand) ? (wsum > 1.57079632679489662f) : 0;
-  if (c < S.ncand) S.flag[c] = (uint8_t)keep;
+  // this slice's sum of theta = 2 pi crossings + arg(product)
+  if (c < S.ncand) S.theta[(int64_t)slice * S.ncand + c] = 6.28318530717958648f * (float)crossings + atan2f(zi, zr);
+}
+
+// w = sum theta / (2 pi) > 1/2; slices added in order.
+__global__ void __launch_bounds__(kSrcBlock) k_src_flag3d(const SrcParams S) {
+  const int64_t c = blockIdx.x * (int64_t)kSrcBlock + threadIdx.x;
+  int keep = 0;
+  if (c < S.ncand) {
+    float th = 0.0f;
+    for (int q = 0; q < S.slices; ++q) th += S.theta[(int64_t)q * S.ncand + c];
+    keep = th > 3.14159265358979324f;
+    S.flag[c] = (uint8_t)keep;
+  }
   const int cnt = __syncthreads_count(keep);
   if (threadIdx.x == 0) S.bcount[blockIdx.x] = cnt;
 }
@@ -240,7 +288,8 @@ static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 extern "C" bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes) {
   if (n_cand < 0 || bytes == nullptr) return BVC_ERR_INVALID_ARG;
   const int64_t nb = (n_cand + kSrcBlock - 1) / kSrcBlock;
-  *bytes = al256((size_t)n_cand * 3 * sizeof(float)) + al256((size_t)n_cand) + 2 * al256((size_t)nb * 8);
+  *bytes = al256((size_t)n_cand * 3 * sizeof(float)) + al256((size_t)n_cand) + 2 * al256((size_t)nb * 8) +
+           al256((size_t)n_cand * kMaxSlices * sizeof(float));
   return BVC_OK;
 }
 
@@ -282,16 +331,25 @@ extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn,
   S.bcount = (int64_t*)w;
   w += al256((size_t)S.nblocks * 8);
   S.boff = (int64_t*)w;
+  w += al256((size_t)S.nblocks * 8);
+  S.theta = (float*)w;
+  if (D == 3) {  // about 8 blocks per SM, at least one tile of triangles per slice
+    const int64_t want = ((int64_t)num_sms() * 8 + S.nblocks - 1) / S.nblocks;
+    const int64_t tiles = (g->n_prims + kTriTile - 1) / kTriTile;
+    S.slices = (int32_t)std::max<int64_t>(1, std::min<int64_t>({want, tiles, (int64_t)kMaxSlices}));
+  }
   S.src_y = cache->src_y;
   S.src_c = cache->src_c;
   S.n_src = cache->n_src_dev;
   cudaStream_t s = (cudaStream_t)stream;
   {
     ProfScope ps("source_classify", s);
-    if (D == 2)
+    if (D == 2) {
       k_src_classify<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
-    else
-      k_src_classify3d<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+    } else {
+      k_src_classify3d<<<dim3((unsigned)S.nblocks, (unsigned)S.slices), kSrcBlock, 0, s>>>(S);
+      k_src_flag3d<<<(unsigned)S.nblocks, kSrcBlock, 0, s>>>(S);
+    }
   }
   {
     ProfScope ps("source_scan", s);
