@@ -76,6 +76,12 @@ def _load():
                 "orc_walks_vg": (None, [P, P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_vertex_interp": (f64, [P, P, i64, P]),
                 "orc_winding3d": (f64, [P, P, i64, P]),
+                "orc_bessel_i": (f64, [C.c_int, f64]),
+                "orc_bessel_k": (f64, [C.c_int, f64]),
+                "orc_green_sigma": (None, [C.c_int, f64, P, P, P, P]),
+                "orc_screened_factors": (None, [C.c_int, f64, P, P]),
+                "orc_walks_sigma": (None, [P, P, P, P, f64, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
+                "orc_gather_sigma": (None, [C.c_int, f64, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
                 "orc_sample_source3d": (i64, [P, i64, P, i64, i32, i32, i32, u64, P, P, P, P]),
                 "orc_reduce_walks": (None, [C.c_int, i64, i32, P, P, P, P, P]),
                 "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P]),
@@ -152,6 +158,29 @@ def green(dim: int, x, y, ny) -> np.ndarray:
     out = np.zeros(2 + 2 * dim)
     lib.orc_green(dim, _p(_f64(x)), _p(_f64(y)), _p(_f64(ny)), _p(out))
     return out
+
+
+def green_sigma(dim: int, sigma: float, x, y, ny) -> np.ndarray:
+    """Screened App. A Green's function and derivatives (layout as green)."""
+    lib = _load()
+    out = np.zeros(2 + 2 * dim)
+    lib.orc_green_sigma(dim, float(np.sqrt(sigma)), _p(_f64(x)), _p(_f64(y)), _p(_f64(ny)), _p(out))
+    return out
+
+
+def bessel_i(n: int, t: float) -> float:
+    return _load().orc_bessel_i(int(n), float(t))
+
+
+def bessel_k(n: int, t: float) -> float:
+    return _load().orc_bessel_k(int(n), float(t))
+
+
+def screened_factors(dim: int, t: float):
+    """(C, Qg) of a ball with t = R sqrt(sigma)."""
+    C_, Q_ = C.c_double(), C.c_double()
+    _load().orc_screened_factors(int(dim), float(t), C.byref(C_), C.byref(Q_))
+    return C_.value, Q_.value
 
 
 # ---------------------------------------------------------------- geometry
@@ -232,11 +261,12 @@ def sphere_step(dim: int, R: float, u0: float, u1: float, u2: float):
 
 
 def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int, seed: int,
-          id_base: int = 0, tag: int = TAG_WALK, want_pend: bool = False, g_vertex=None):
+          id_base: int = 0, tag: int = TAG_WALK, want_pend: bool = False, g_vertex=None, sigma: float = 0.0):
     """Sec. 3.1 / Eq. 7: W walks from each FP32 start point.
 
     g_vertex: optional per-vertex values of g (then g_terms is ignored): g at
     a boundary point is interpolated linearly on the closest element.
+    sigma > 0: the screened equation (Delta - sigma) u = 0 (f must be zero).
     Returns dict with per-walk U, grad[.., dim], steps, prim, scale[.., 2]
     (magnitudes of the terms forming U and the gradient, for error scaling)
     and, if asked, pend (final closest point)."""
@@ -251,8 +281,9 @@ def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int
     g = encode_function(g_terms if g_vertex is None else [])
     f = encode_function(f_terms)
     gv = None if g_vertex is None else _f64(g_vertex)
-    lib.orc_walks_vg(bvh.h, _p(g), _p(gv), _p(f), _p(starts), n, int(W), float(eps), int(max_steps), int(seed),
-                     int(id_base), int(tag), _p(U), _p(grad), _p(steps), _p(prim), _p(pend), _p(scale))
+    lib.orc_walks_sigma(bvh.h, _p(g), _p(gv), _p(f), float(np.sqrt(sigma)), _p(starts), n, int(W), float(eps),
+                        int(max_steps), int(seed), int(id_base), int(tag), _p(U), _p(grad), _p(steps), _p(prim),
+                        _p(pend), _p(scale))
     out = {"U": U, "grad": grad, "steps": steps, "prim": prim, "scale": scale}
     if want_pend:
         out["pend"] = pend
@@ -320,8 +351,9 @@ def sample_source2d(V, F, grid, seed: int, f_terms):
     return y[:kept].copy(), c[:kept].copy(), G0 * G1
 
 
-def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs: bool = False):
+def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs: bool = False, sigma: float = 0.0):
     """Eq. 3-6 / Alg. 1 splat: FP64 running sums (u_bnd, u_src, g_bnd, g_src).
+    sigma > 0: with the screened Green's functions of App. A.
 
     With want_abs, also the per-point sums of |term| (for error scaling):
     array [M, 2 + 2 dim] = [u_bnd, g_bnd(dim), u_src, g_src(dim)]."""
@@ -337,8 +369,8 @@ def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs:
     ub, us = np.zeros(M), np.zeros(M)
     gb, gs = np.zeros((M, dim)), np.zeros((M, dim))
     ab = np.zeros((M, 2 + 2 * dim)) if want_abs else None
-    lib.orc_gather(dim, N, _p(z), _p(nz), _p(u_hat), _p(q_hat), float(bnd_measure), y.shape[0], _p(y), _p(c),
-                   M, _p(x), _p(ub), _p(us), _p(gb), _p(gs), _p(ab))
+    lib.orc_gather_sigma(dim, float(np.sqrt(sigma)), N, _p(z), _p(nz), _p(u_hat), _p(q_hat), float(bnd_measure),
+                         y.shape[0], _p(y), _p(c), M, _p(x), _p(ub), _p(us), _p(gb), _p(gs), _p(ab))
     if want_abs:
         return ub, us, gb, gs, ab
     return ub, us, gb, gs

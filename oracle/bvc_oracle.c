@@ -93,6 +93,8 @@ static void draw(uint64_t seed, uint64_t id, uint32_t word2, uint32_t tag, doubl
 /*          sum A_k (|x-c_k|^2/s^4 - dim/s^2) exp(-|x-c_k|^2/(2 s^2)).       */
 /*   kind 4 EXP_TRIG (3D): [A, alpha, beta, gamma]:                           */
 /*          A exp(alpha z) cos(beta x) sin(gamma y).                          */
+/*   kind 5 EXP_COS: [A, alpha, beta]: A exp(alpha x_last) cos(beta x_0)      */
+/*          (x_last = y in 2D, z in 3D); Laplacian = (alpha^2 - beta^2) value. */
 /* ------------------------------------------------------------------------ */
 static double ipow(double x, int e) {
   double r = 1.0;
@@ -141,6 +143,7 @@ double orc_fn_eval(const double* spec, int dim, const double* x) {
       case 2: v += gauss_eval(dim, c, nc, x, 0); break;
       case 3: v += gauss_eval(dim, c, nc, x, 1); break;
       case 4: v += c[0] * exp(c[1] * x[2]) * cos(c[2] * x[0]) * sin(c[3] * x[1]); break;
+      case 5: v += c[0] * exp(c[1] * x[dim - 1]) * cos(c[2] * x[0]); break;
       default: break;
     }
     p += 2 + nc;
@@ -174,6 +177,142 @@ void orc_green(int dim, const double* x, const double* y, const double* ny, doub
     for (int a = 0; a < 3; ++a) out[1 + a] = -d[a] / (4.0 * ORC_PI * r3);
     out[4] = nd / (4.0 * ORC_PI * r3);
     for (int a = 0; a < 3; ++a) out[5 + a] = 3.0 * nd * d[a] / (4.0 * ORC_PI * r5) - ny[a] / (4.0 * ORC_PI * r3);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Modified Bessel functions (screened Poisson, App. A), FP64.               */
+/* I_n(t), n = 0, 1: the power series sum_k (t/2)^(2k+n) / (k! (k+n)!)     */
+/* (DLMF 10.25.2), all terms positive, for t <= 50; above, the integral     */
+/* (1/pi) int_0^pi exp(t cos s) cos(n s) ds (DLMF 10.32.3) by the           */
+/* trapezoidal rule, exact to rounding for this periodic analytic integrand. */
+/* K_n(t): for t <= 2 the series DLMF 10.31.1/10.31.2 with digamma values   */
+/* psi(k+1) = -gamma + H_k; above, int_0^inf exp(-t cosh s) cosh(n s) ds    */
+/* (DLMF 10.32.9) by the trapezoidal rule with step 1/16, which converges   */
+/* exponentially for this analytic, double-exponentially decaying integrand. */
+/* ------------------------------------------------------------------------ */
+#define ORC_EULER_GAMMA 0.57721566490153286061
+double orc_bessel_i(int n, double t) {
+  if (t <= 50.0) {
+    const double q = 0.25 * t * t;
+    double term = n == 0 ? 1.0 : 0.5 * t, sum = term;
+    for (int k = 1; k < 300; ++k) {
+      term *= q / ((double)k * (double)(k + n));
+      sum += term;
+      if (term < 1e-18 * sum) break;
+    }
+    return sum;
+  }
+  const int m = 512;
+  double sum = 0.0;
+  for (int j = 0; j <= m; ++j) {
+    const double sj = ORC_PI * j / m;
+    const double w = (j == 0 || j == m) ? 0.5 : 1.0;
+    sum += w * exp(t * cos(sj)) * cos(n * sj);
+  }
+  return sum / m;
+}
+
+double orc_bessel_k(int n, double t) {
+  if (t <= 2.0) {
+    const double q = 0.25 * t * t, lg = log(0.5 * t);
+    double term = 1.0, h = 0.0, sum = 0.0;
+    if (n == 0) {
+      for (int k = 0; k < 200; ++k) {
+        if (k > 0) {
+          term *= q / ((double)k * (double)k);
+          h += 1.0 / k;
+        }
+        sum += term * (h - ORC_EULER_GAMMA);
+        if (k > 2 && term < 1e-20) break;
+      }
+      return -lg * orc_bessel_i(0, t) + sum;
+    }
+    /* n = 1: 1/t + ln(t/2) I_1(t) - (t/4) sum_k (psi(k+1) + psi(k+2)) q^k / (k! (k+1)!) */
+    double h1 = 1.0; /* H_(k+1) */
+    for (int k = 0; k < 200; ++k) {
+      if (k > 0) {
+        term *= q / ((double)k * (double)(k + 1));
+        h += 1.0 / k;
+        h1 += 1.0 / (k + 1);
+      }
+      sum += term * ((h - ORC_EULER_GAMMA) + (h1 - ORC_EULER_GAMMA));
+      if (k > 2 && term < 1e-20) break;
+    }
+    return 1.0 / t + lg * orc_bessel_i(1, t) - 0.25 * t * sum;
+  }
+  const double hstep = 1.0 / 16.0;
+  double sum = 0.5 * exp(-t);
+  for (int j = 1; j < 100000; ++j) {
+    const double sj = j * hstep;
+    const double v = exp(-t * cosh(sj)) * cosh(n * sj);
+    sum += v;
+    if (v < 1e-300 || v < 1e-20 * sum) break;
+  }
+  return sum * hstep;
+}
+
+/* Screened Poisson (Delta - sigma) Green's functions, App. A, with k =     */
+/* sqrt(sigma): G = -K0(kr)/(2 pi) (2D), -exp(-kr)/(4 pi r) (3D) -- the    */
+/* signs that make the printed gradients (Q times the Laplace gradients)    */
+/* their derivatives and (Delta - sigma) G = +delta -- so that Eq. 2 keeps  */
+/* its form.  Q = kr K1(kr) (2D), exp(-kr)(kr + 1) (3D); grad_x Q =          */
+/* k^2 K0(kr) d (2D), k^2 exp(-kr) d (3D).  out as orc_green.               */
+void orc_green_sigma(int dim, double k, const double* x, const double* y, const double* ny, double* out) {
+  if (!(k > 0.0)) {
+    orc_green(dim, x, y, ny, out);
+    return;
+  }
+  double d[3] = {0, 0, 0}, r2 = 0.0, nd = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    d[a] = y[a] - x[a];
+    r2 += d[a] * d[a];
+    nd += ny[a] * d[a];
+  }
+  const double r = sqrt(r2), t = k * r;
+  double G0[8];
+  orc_green(dim, x, y, ny, G0);
+  double Q, gq, Gs;
+  if (dim == 2) {
+    const double k0 = orc_bessel_k(0, t);
+    Q = t * orc_bessel_k(1, t);
+    gq = k * k * k0;
+    Gs = -k0 / (2.0 * ORC_PI);
+  } else {
+    const double e = exp(-t);
+    Q = e * (t + 1.0);
+    gq = k * k * e;
+    Gs = -e / (4.0 * ORC_PI * r);
+  }
+  out[0] = Gs;
+  for (int a = 0; a < dim; ++a) out[1 + a] = Q * G0[1 + a];
+  out[1 + dim] = Q * G0[1 + dim];
+  for (int a = 0; a < dim; ++a) out[2 + dim + a] = Q * G0[2 + dim + a] + G0[1 + dim] * gq * d[a];
+}
+
+/* The walk's screened factors for a ball of radius R (t = R sqrt(sigma)):   */
+/* the mean over the sphere of a solution of (Delta - sigma) u = 0 is       */
+/* u(centre) / C(t), so u(x) = C(t) avg u with C = t / sinh t (3D),          */
+/* 1 / I0(t) (2D); its dipole moment gives grad u(x) = (d/R) Qg(t) avg[u nu]  */
+/* with Qg = t^3 / (3 (t cosh t - sinh t)) (3D), t / (2 I1(t)) (2D)           */
+/* (from the regular solutions i_l, I_m of the expansion about the centre). */
+void orc_screened_factors(int dim, double t, double* C, double* Qg) {
+  if (!(t > 0.0)) {
+    *C = 1.0;
+    *Qg = 1.0;
+    return;
+  }
+  if (dim == 2) {
+    *C = 1.0 / orc_bessel_i(0, t);
+    *Qg = t / (2.0 * orc_bessel_i(1, t));
+  } else {
+    *C = t < 1e-4 ? 1.0 / (1.0 + t * t / 6.0) : t / sinh(t);
+    if (t < 0.5) {
+      const double t2 = t * t;
+      *Qg = 1.0 / (1.0 + t2 / 10.0 + t2 * t2 / 280.0 + t2 * t2 * t2 / 15120.0 + t2 * t2 * t2 * t2 / 1330560.0);
+    } else {
+      *Qg = t * t * t / (3.0 * (t * cosh(t) - sinh(t)));
+    }
   }
 }
 
@@ -722,6 +861,7 @@ typedef struct {
   uint64_t seed;
   uint32_t tag;
   const double* gv; /* vertex values of g, or NULL for the closed form g */
+  double sqs;       /* sqrt(sigma) of the screened equation, 0 for Poisson */
 } walk_ctx_t;
 
 /* Boundary data given by values at the mesh vertices: g at a point p of   */
@@ -789,6 +929,9 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
   double x[3] = {0, 0, 0}, pbar[3] = {0, 0, 0}, nu[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) x[a] = x0[a];
   double usrc = 0.0, uabs = 0.0, wf0 = 0.0, wg0 = 0.0, R0 = 0.0, cv = 0.0;
+  /* screened: throughput = product of the steps' factors C; the first     */
+  /* step's C and gradient factor Qg (Sec. 3.1 with the screened ball)      */
+  double thr = 1.0, C0 = 1.0, Qg0 = 1.0;
   int k = 0;
   int64_t prim = -1;
   for (;;) {
@@ -797,6 +940,15 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
     if (k == 1) cv = g_at(w, pbar, prim);
     if (d < w->eps || k >= w->max_steps) break;
     const double R = d;
+    if (w->sqs > 0.0) {
+      double Cs, Qs;
+      orc_screened_factors(dim, w->sqs * R, &Cs, &Qs);
+      thr *= Cs;
+      if (k == 1) {
+        C0 = Cs;
+        Qg0 = Qs;
+      }
+    }
     double u[4];
     draw(w->seed, wid, (uint32_t)(k - 1), w->tag, u);
     double om[3] = {0, 0, 0}, rho, wu, wg;
@@ -819,7 +971,7 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
     for (int a = 0; a < dim; ++a) x[a] += R * om[a];
   }
   const double gend = g_at(w, pbar, prim);
-  const double U = gend + usrc;
+  const double U = (k == 1 ? gend : thr * gend) + usrc;
   *U_out = U;
   /* magnitudes of the terms that form U and the gradient (test scaling only) */
   if (scale_out) {
@@ -829,7 +981,9 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
   if (k == 1) {
     for (int a = 0; a < dim; ++a) grad_out[a] = 0.0;
   } else {
-    const double s = ((double)dim / R0) * (U - wf0 - cv) + wg0;
+    /* screened (f = 0): U / C0 estimates u at the first sphere point */
+    const double s = w->sqs > 0.0 ? ((double)dim / R0) * Qg0 * (U / C0 - cv)
+                                  : ((double)dim / R0) * (U - wf0 - cv) + wg0;
     for (int a = 0; a < dim; ++a) grad_out[a] = s * nu[a];
   }
   *steps_out = k;
@@ -841,10 +995,10 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
 /* W walks from each of n start points; walk j of start i has id            */
 /* id_base + i*W + j.  Outputs are per walk: U[n*W], grad[n*W*dim],         */
 /* steps[n*W], prim[n*W], pend[n*W*dim] (pend may be NULL).                  */
-void orc_walks_vg(void* bvh, const double* g, const double* gv, const double* f, const float* starts, int64_t n,
-                  int32_t W, double eps, int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U,
-                  double* grad, int32_t* steps, int32_t* prim, double* pend, double* scale) {
-  walk_ctx_t w = {(const obvh_t*)bvh, g, f, eps, max_steps, seed, tag, gv};
+void orc_walks_sigma(void* bvh, const double* g, const double* gv, const double* f, double sqs, const float* starts,
+                     int64_t n, int32_t W, double eps, int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag,
+                     double* U, double* grad, int32_t* steps, int32_t* prim, double* pend, double* scale) {
+  walk_ctx_t w = {(const obvh_t*)bvh, g, f, eps, max_steps, seed, tag, gv, sqs};
   const int dim = w.bvh->m.dim;
   const int64_t total = n * (int64_t)W;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -855,6 +1009,14 @@ void orc_walks_vg(void* bvh, const double* g, const double* gv, const double* f,
     walk_one(&w, x0, id_base + (uint64_t)t, &U[t], &grad[t * dim], &steps[t], &prim[t],
              pend ? &pend[t * dim] : NULL, scale ? &scale[2 * t] : NULL);
   }
+}
+
+/* Poisson (sigma = 0) walks, g in closed form or from vertex values.       */
+void orc_walks_vg(void* bvh, const double* g, const double* gv, const double* f, const float* starts, int64_t n,
+                  int32_t W, double eps, int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U,
+                  double* grad, int32_t* steps, int32_t* prim, double* pend, double* scale) {
+  orc_walks_sigma(bvh, g, gv, f, 0.0, starts, n, W, eps, max_steps, seed, id_base, tag, U, grad, steps, prim, pend,
+                  scale);
 }
 
 /* The same with closed-form boundary data g (no vertex values).           */
@@ -1010,9 +1172,9 @@ int64_t orc_sample_source3d(const float* V, int64_t nv, const int32_t* F, int64_
 /*   u_src    += G(x,y) c,    grad_src += dG/dx(x,y) c                       */
 /* Returns SUMS (Alg. 1 running sums); the caller divides by N and M.       */
 /* ------------------------------------------------------------------------ */
-void orc_gather(int dim, int64_t N, const double* z, const double* nz, const double* u_hat, const double* q_hat,
-                double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M, const double* x,
-                double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
+void orc_gather_sigma(int dim, double sqs, int64_t N, const double* z, const double* nz, const double* u_hat,
+                      const double* q_hat, double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M,
+                      const double* x, double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t k = 0; k < M; ++k) {
     double xk[3] = {0, 0, 0}, zz[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, G[8];
@@ -1025,7 +1187,7 @@ void orc_gather(int dim, int64_t N, const double* z, const double* nz, const dou
         zz[a] = z[i * dim + a];
         nn[a] = nz[i * dim + a];
       }
-      orc_green(dim, xk, zz, nn, G);
+      orc_green_sigma(dim, sqs, xk, zz, nn, G);
       const double dGdn = G[1 + dim];
       const double tu = (dGdn * u_hat[i] - G[0] * q_hat[i]) * bnd_measure;
       ub += tu;
@@ -1038,7 +1200,7 @@ void orc_gather(int dim, int64_t N, const double* z, const double* nz, const dou
     }
     for (int64_t j = 0; j < Ms; ++j) {
       for (int a = 0; a < dim; ++a) zz[a] = y[j * dim + a];
-      orc_green(dim, xk, zz, nn, G);
+      orc_green_sigma(dim, sqs, xk, zz, nn, G);
       us += G[0] * c[j];
       ab[1 + dim] += fabs(G[0] * c[j]);
       for (int a = 0; a < dim; ++a) {
@@ -1055,6 +1217,12 @@ void orc_gather(int dim, int64_t N, const double* z, const double* nz, const dou
       if (g_src) g_src[k * dim + a] = gs[a];
     }
   }
+}
+
+void orc_gather(int dim, int64_t N, const double* z, const double* nz, const double* u_hat, const double* q_hat,
+                double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M, const double* x,
+                double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
+  orc_gather_sigma(dim, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, Ms, y, c, M, x, u_bnd, u_src, g_bnd, g_src, abs_out);
 }
 
 int orc_num_threads(void) {
