@@ -68,10 +68,19 @@ typedef enum {
  *     sum_k A_k (|x - c_k|^2 / s^4 - dim / s^2) exp(-|x - c_k|^2 / (2 s^2)).
  *   BVC_FN_EXP_TRIG (3D): [A, alpha, beta, gamma] ->
  *     A exp(alpha z) cos(beta x) sin(gamma y).
+ *   BVC_FN_EXP_COS: [A, alpha, beta] -> A exp(alpha x_last) cos(beta x_0)
+ *     (x_last = y in 2D, z in 3D): a solution of Delta u = sigma u with
+ *     sigma = alpha^2 - beta^2.
  * The total coefficient count over all terms is at most BVC_MAX_COEFFS. */
 #define BVC_MAX_TERMS 4
 #define BVC_MAX_COEFFS 120
-typedef enum { BVC_FN_POLY = 1, BVC_FN_GAUSS = 2, BVC_FN_GAUSS_LAPLACIAN = 3, BVC_FN_EXP_TRIG = 4 } bvc_fn_kind;
+typedef enum {
+  BVC_FN_POLY = 1,
+  BVC_FN_GAUSS = 2,
+  BVC_FN_GAUSS_LAPLACIAN = 3,
+  BVC_FN_EXP_TRIG = 4,
+  BVC_FN_EXP_COS = 5
+} bvc_fn_kind;
 typedef struct {
   int32_t kind;
   int32_t n_coeffs;
@@ -200,6 +209,7 @@ typedef struct {
   double* src_c;        /* [n_src_cand] f(y) / p for kept points */
   float* src_packed;    /* [n_src_cand][8] gather tiles */
   int64_t* n_src_dev;   /* [1] number of kept source samples (written on device) */
+  double sigma;         /* screening coefficient of the cache (set by the build); 0 = Poisson */
 } bvc_cache;
 
 /* K4 -- source samples (Alg. 1 "y ~ p^R", Sec. 4 "Sampling"): a jittered
@@ -235,6 +245,10 @@ typedef struct {
   uint64_t walk_id_base;    /* first walk id: distinct caches of one seed use disjoint ranges */
   int32_t src_grid[3];      /* source candidate grid (2D: [0] x [1], [2] unused; 3D: all three),
                                all 0 = no source cache */
+  double sigma;             /* screened Poisson (Delta - sigma) u = 0 when > 0 (Eq. 1): f must be
+                               zero and there is no source cache; the walks weight each ball by its
+                               screened mean-value factor and the gather uses the screened Green's
+                               functions of App. A.  0 = Poisson. */
 } bvc_cache_opts;
 
 /* The whole cache: K1 -> K2 (chunked through the workspace) -> K3 -> K4 -> pack.
@@ -448,6 +462,17 @@ bvc_status bvc_batch_project(bvc_batch b, const double* coeffs, bvc_multi_cache*
  * over mesh j's samples only. */
 bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
                               bvc_stream stream);
+
+/* wos_estimate for the screened equation (Delta - sigma) u = 0 (sigma >= 0;
+ * f must be zero when sigma > 0, else BVC_ERR_UNSUPPORTED).  Each ball of
+ * radius R multiplies the walk's weight by its screened mean-value factor
+ * (R sqrt(sigma)) / sinh(R sqrt(sigma)) (3D) or 1 / I0(R sqrt(sigma)) (2D);
+ * the first ball's gradient uses (dim / R) Qg with Qg = t^3 / (3 (t cosh t
+ * - sinh t)) (3D) or t / (2 I1(t)) (2D), t = R sqrt(sigma).  sigma = 0 is
+ * wos_estimate. */
+bvc_status wos_estimate_sigma(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, double sigma,
+                              bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                              uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream);
 
 /* wos_estimate with no caller workspace and no allocation.  The paper has
  * no counterpart: this is an interface for callers that must not allocate

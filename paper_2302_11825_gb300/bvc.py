@@ -53,13 +53,14 @@ class CacheStruct(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("z", C.c_void_p), ("nrm", C.c_void_p),
                 ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p), ("packed", C.c_void_p),
                 ("bnd_measure", C.c_double), ("n_src_cand", C.c_int64), ("src_y", C.c_void_p),
-                ("src_c", C.c_void_p), ("src_packed", C.c_void_p), ("n_src_dev", C.c_void_p)]
+                ("src_c", C.c_void_p), ("src_packed", C.c_void_p), ("n_src_dev", C.c_void_p),
+                ("sigma", C.c_double)]
 
 
 class CacheOpts(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("walks_per_sample", C.c_int32), ("max_steps", C.c_int32),
                 ("offset_l", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64),
-                ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 3)]
+                ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 3), ("sigma", C.c_double)]
 
 
 class MultiCacheStruct(C.Structure):
@@ -119,6 +120,8 @@ def _declare(lib):
         "wos_estimate": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct), i32, f32, i32,
                              u64, u64, P, sz, P]),
         "bvc_eval_state_reset": (S, [C.POINTER(EvalStateStruct), P]),
+        "wos_estimate_sigma": (S, [P, C.POINTER(Function), C.POINTER(Function), f64, C.POINTER(EvalStateStruct), i32,
+                                   f32, i32, u64, u64, P, sz, P]),
         "wos_estimate_static_scratch": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct),
                                             i32, f32, i32, u64, u64, P]),
         "bvc_geometry_set_counting": (S, [P, i32]),
@@ -367,12 +370,14 @@ def n_candidates(dim: int, src_grid) -> int:
     return int(g[0]) * int(g[1]) * (int(g[2]) if dim == 3 else 1)
 
 
-def cache_opts(n_samples, walks, offset_l, eps, seed, max_steps=1 << 14, walk_id_base=0, src_grid=(0, 0)):
+def cache_opts(n_samples, walks, offset_l, eps, seed, max_steps=1 << 14, walk_id_base=0, src_grid=(0, 0),
+               sigma: float = 0.0):
     o = CacheOpts()
     o.n_samples, o.walks_per_sample, o.max_steps = int(n_samples), int(walks), int(max_steps)
     o.offset_l, o.eps, o.seed, o.walk_id_base = float(offset_l), float(eps), int(seed), int(walk_id_base)
     o.src_grid[0], o.src_grid[1] = int(src_grid[0]), int(src_grid[1])
     o.src_grid[2] = int(src_grid[2]) if len(src_grid) > 2 else 0
+    o.sigma = float(sigma)
     return o
 
 
@@ -611,12 +616,18 @@ def eval_state_reset(state: EvalState, stream=None):
 
 
 def wos_estimate(geom: Geometry, g_terms, f_terms, state: EvalState, walks: int, eps: float, max_steps: int,
-                 seed: int, id_base: int = 0, ws: torch.Tensor = None, stream=None):
+                 seed: int, id_base: int = 0, ws: torch.Tensor = None, stream=None, sigma: float = 0.0):
     """Pointwise walk on spheres: adds `walks` walks per point of `state` to
-    its running sums (finalise with get_solution)."""
+    its running sums (finalise with get_solution).  sigma > 0: the screened
+    equation (Delta - sigma) u = 0 (wos_estimate_sigma)."""
     if ws is None:
         ws = workspace(wos_workspace_size(state.dim, state.m, walks)[1])
     g, f = make_function(g_terms), make_function(f_terms)
+    if sigma:
+        _check(lib().wos_estimate_sigma(geom.h, C.byref(g), C.byref(f), float(sigma), C.byref(state.struct),
+                                        int(walks), float(eps), int(max_steps), int(seed), int(id_base), _ptr(ws),
+                                        ws.numel(), _stream(stream)), "wos_estimate_sigma")
+        return state
     _check(lib().wos_estimate(geom.h, C.byref(g), C.byref(f), C.byref(state.struct), int(walks), float(eps),
                               int(max_steps), int(seed), int(id_base), _ptr(ws), ws.numel(), _stream(stream)),
            "wos_estimate")

@@ -52,6 +52,11 @@ bool make_dev_function(const bvc_function* f, int dim, DevFunction* out) {
         if (used + nc > BVC_MAX_COEFFS) return false;
         for (int i = 0; i < 4; ++i) c[i] = (float)tm.coeffs[i];
         break;
+      case BVC_FN_EXP_COS:
+        if (nc != 3) return false;
+        if (used + nc > BVC_MAX_COEFFS) return false;
+        for (int i = 0; i < 3; ++i) c[i] = (float)tm.coeffs[i];
+        break;
       default:
         return false;
     }

@@ -131,6 +131,9 @@ __device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) 
       case BVC_FN_EXP_TRIG:
         if (D == 3) v = fmaf(c[0] * ex<D, FAST>(c[1] * x[D == 3 ? 2 : 0]), cosf(c[2] * x[0]) * sinf(c[3] * x[1]), v);
         break;
+      case BVC_FN_EXP_COS:
+        v = fmaf(c[0] * ex<D, FAST>(c[1] * x[D - 1]), cosf(c[2] * x[0]), v);
+        break;
       default:
         break;
     }
@@ -213,6 +216,91 @@ __device__ __forceinline__ void bump_shapes(const DevFunction& fn, const float* 
       if (lap) v *= fmaf(r2, q4, qd);
     }
     psi[k] = v;
+  }
+}
+
+// ------------------------------------------- screened Poisson (sigma > 0)
+// Modified Bessel functions in FP32 by the polynomial approximations of
+// Abramowitz and Stegun, Handbook of Mathematical Functions, 9.8.1-9.8.8
+// (absolute or relative error below 2.2e-7).  The large-argument forms are
+// returned with their exponential factored out, so that the walk's factors
+// and the gather's kernels never overflow:
+//   i0s(t) = sqrt(t) e^-t I0(t), i1s(t) = sqrt(t) e^-t I1(t)  (t >= 3.75)
+//   k0s(t) = sqrt(t) e^t K0(t),  k1s(t) = sqrt(t) e^t K1(t)   (t >= 2)
+__device__ __forceinline__ float bessel_i0_small(float t) {  // 9.8.1, |t| <= 3.75
+  const float y = (t / 3.75f) * (t / 3.75f);
+  return fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 0.0045813f, 0.0360768f), 0.2659732f), 1.2067492f),
+                                   3.0899424f), 3.5156229f), 1.0f);
+}
+__device__ __forceinline__ float bessel_i0s_large(float t) {  // 9.8.2, t >= 3.75
+  const float y = 3.75f / t;
+  return fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 0.00392377f, -0.01647633f), 0.02635537f),
+                                                                -0.02057706f), 0.00916281f), -0.00157565f),
+                                   0.00225319f), 0.01328592f), 0.39894228f);
+}
+__device__ __forceinline__ float bessel_i1_small(float t) {  // 9.8.3, |t| <= 3.75
+  const float y = (t / 3.75f) * (t / 3.75f);
+  return t * fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 0.00032411f, 0.00301532f), 0.02658733f), 0.15084934f),
+                                       0.51498869f), 0.87890594f), 0.5f);
+}
+__device__ __forceinline__ float bessel_i1s_large(float t) {  // 9.8.4, t >= 3.75
+  const float y = 3.75f / t;
+  return fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, -0.00420059f, 0.01787654f), -0.02895312f),
+                                                                0.02282967f), -0.01031555f), 0.00163801f),
+                                   -0.00362018f), -0.03988024f), 0.39894228f);
+}
+// K0, K1 for t <= 2 (9.8.5, 9.8.7) and the scaled forms for t >= 2 (9.8.6, 9.8.8).
+__device__ __forceinline__ float bessel_k0_small(float t) {
+  const float y = 0.25f * t * t;
+  const float p = fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 0.0000074f, 0.0001075f), 0.00262698f), 0.0348859f),
+                                       0.23069756f), 0.4227842f), -0.57721566f);
+  return fmaf(-__logf(0.5f * t), bessel_i0_small(t), p);
+}
+__device__ __forceinline__ float bessel_k0s_large(float t) {
+  const float y = 2.0f / t;
+  return fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 0.00053208f, -0.0025154f), 0.00587872f), -0.01062446f),
+                                   0.02189568f), -0.07832358f), 1.25331414f);
+}
+__device__ __forceinline__ float bessel_k1_small(float t) {  // returns K1(t)
+  const float y = 0.25f * t * t;
+  const float p = fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, -0.00004686f, -0.00110404f), -0.01919402f),
+                                                 -0.18156897f), -0.67278579f), 0.15443144f), 1.0f);
+  return fmaf(__logf(0.5f * t), bessel_i1_small(t), p / t);
+}
+__device__ __forceinline__ float bessel_k1s_large(float t) {
+  const float y = 2.0f / t;
+  return fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, -0.00068245f, 0.00325614f), -0.00780353f), 0.01504268f),
+                                   -0.0365562f), 0.23498619f), 1.25331414f);
+}
+
+// The walk's ball factors (t = R sqrt(sigma)): u(centre) = C avg_sphere u and
+// grad u(centre) = (D/R) Qg avg_sphere[u nu]:
+//   3D  C = t / sinh t,   Qg = t^3 / (3 (t cosh t - sinh t))   (series below 0.5)
+//   2D  C = 1 / I0(t),    Qg = t / (2 I1(t))
+template <int D>
+__device__ __forceinline__ void screened_factors(float t, float& C, float& Qg) {
+  if (D == 3) {
+    if (t < 0.5f) {
+      const float t2 = t * t;
+      C = 1.0f / fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 5040.0f, 1.0f / 120.0f), 1.0f / 6.0f), 1.0f);
+      Qg = 1.0f / fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 1330560.0f * t2 + 1.0f / 15120.0f, 1.0f / 280.0f), 1.0f / 10.0f),
+                       1.0f);
+    } else {
+      const float e = __expf(-t);            // sinh t = (1 - e^-2t) e^t / 2
+      const float e2 = e * e;
+      const float sh = 0.5f * (1.0f - e2), ch = 0.5f * (1.0f + e2);  // times e^t
+      C = t * 2.0f * e / (1.0f - e2);
+      Qg = t * t * t * e / (3.0f * fmaf(t, ch, -sh));
+    }
+  } else {
+    if (t <= 3.75f) {
+      C = 1.0f / bessel_i0_small(t);
+      Qg = t / (2.0f * bessel_i1_small(t));
+    } else {
+      const float sq = sqrtf(t) * __expf(-t);
+      C = sq / bessel_i0s_large(t);
+      Qg = t * sq / (2.0f * bessel_i1s_large(t));
+    }
   }
 }
 

@@ -28,6 +28,7 @@
 // fixed order, so results are deterministic.
 #include <cmath>
 
+#include "bvc_device.cuh"
 #include "bvc_internal.h"
 
 namespace bvc {
@@ -482,6 +483,133 @@ static size_t part_bytes(const Plan& P, int planes, int64_t m) {
   return P.n_splits > 1 ? (size_t)P.n_splits * planes * (size_t)m * sizeof(double) : 0;
 }
 
+// ---------------------------------------------------------------- screened
+// Screened Poisson gather (App. A, sigma > 0, k = sqrt(sigma)): per sample
+// the tile holds (z, A) and (n, B) with A = u^ |dOmega| / w, B = du/dn^
+// |dOmega| / w, w = 2 pi (2D) or 4 pi (3D); with d = z - x, t = k r, the
+// Green's functions G = -K0(t)/(2 pi) and -exp(-t)/(4 pi r) and
+// Q = t K1(t) or exp(-t)(t + 1):
+//   2D  u += A Q (n.d)/r^2 + B K0
+//       grad u += A [Q (2 (n.d) d / r^4 - n / r^2) + (n.d)/r^2 k^2 K0 d] + B Q d / r^2
+//   3D  u += A Q (n.d)/r^3 + B exp(-t)/r
+//       grad u += A [Q (3 (n.d) d / r^5 - n / r^3) + (n.d)/r^3 k^2 exp(-t) d] + B Q d / r^3
+// One point per thread, 128-sample tiles by bulk copy, FP32 per tile, FP64
+// across tiles; sums added into the evaluation state like bvc_evaluate's.
+constexpr int kSTile = 128;
+
+template <int D>
+__global__ void __launch_bounds__(256) k_pack_bnd_scr(const bvc_cache C) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= C.n) return;
+  const double w = D == 2 ? 6.283185307179586476925 : 12.566370614359172953850;
+  const double ca = C.bnd_measure / w;
+  float4* o = (float4*)C.packed + 2 * i;
+  o[0] = make_float4(C.z[i], C.z[C.n + i], D == 3 ? C.z[2 * C.n + i] : 0.0f, (float)(C.u_hat[i] * ca));
+  o[1] = make_float4(C.nrm[i], C.nrm[C.n + i], D == 3 ? C.nrm[2 * C.n + i] : 0.0f, (float)(C.dudn_hat[i] * ca));
+}
+
+template <int D, bool GRAD>
+__global__ void __launch_bounds__(256) k_gather_scr(const float* __restrict__ x, int64_t m, const float4* __restrict__ T,
+                                                   int64_t n, float k, double* __restrict__ u,
+                                                   double* __restrict__ grad) {
+  __shared__ __align__(128) float4 tile[2][2 * kSTile];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float pc[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pc[a] = (a < D && p < m) ? x[a * m + p] : 1.0e4f + (float)a;
+  double U = 0.0, Gd[3] = {0.0, 0.0, 0.0};
+  const float k2 = k * k;
+  const int64_t nt = (n + kSTile - 1) / kSTile;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2 && b < nt; ++b) {
+      const uint32_t bytes = (uint32_t)min64(kSTile, n - (int64_t)b * kSTile) * 32u;
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_g2s(&tile[b][0], T + 2 * (int64_t)b * kSTile, bytes, &bar[b]);
+    }
+  }
+  for (int64_t it = 0; it < nt; ++it) {
+    const int b = (int)(it & 1);
+    const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&g_gather_status, 1ull);
+        for (int64_t k3 = it; k3 < it + 2 && k3 < nt; ++k3)
+          (void)mbar_wait_bounded(&bar[k3 & 1], (uint32_t)((k3 >> 1) & 1));
+      }
+      return;
+    }
+    const int cnt = (int)min64(kSTile, n - it * kSTile);
+    float au = 0.0f, ag[3] = {0.0f, 0.0f, 0.0f};
+    for (int e = 0; e < cnt; ++e) {
+      const float4 zA = tile[b][2 * e], nB = tile[b][2 * e + 1];
+      const float dx = zA.x - pc[0], dy = zA.y - pc[1], dz = D == 3 ? zA.z - pc[2] : 0.0f;
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const float ir = rsqrtf(r2), r = r2 * ir, t = k * r;
+      const float nd = fmaf(nB.z, dz, fmaf(nB.y, dy, nB.x * dx));
+      float Q, kern, dq;  // Q; K0 or exp(-t)/r; the gradient factor of Q
+      float ik;           // 1/r^2 (2D) or 1/r^3 (3D)
+      if (D == 2) {
+        float k0, k1;
+        if (t <= 2.0f) {
+          k0 = bessel_k0_small(t);
+          k1 = bessel_k1_small(t);
+        } else {
+          const float e2 = __expf(-t) * rsqrtf(t);
+          k0 = bessel_k0s_large(t) * e2;
+          k1 = bessel_k1s_large(t) * e2;
+        }
+        Q = t * k1;
+        kern = k0;
+        dq = k2 * k0;
+        ik = ir * ir;
+      } else {
+        const float e3 = __expf(-t);
+        Q = e3 * (t + 1.0f);
+        kern = e3 * ir;
+        dq = k2 * e3;
+        ik = ir * ir * ir;
+      }
+      const float s1 = zA.w * Q * nd * ik;
+      au += fmaf(nB.w, kern, s1);
+      if (GRAD) {
+        // A [Q (D (n.d) d / r^(D+2) - n / r^D) + (n.d)/r^D dq d] + B Q d / r^D
+        const float c1 = zA.w * (Q * (float)D * nd * ik * ir * ir + nd * ik * dq) + nB.w * Q * ik;
+        const float c2 = -zA.w * Q * ik;
+        ag[0] = fmaf(c1, dx, fmaf(c2, nB.x, ag[0]));
+        ag[1] = fmaf(c1, dy, fmaf(c2, nB.y, ag[1]));
+        if (D == 3) ag[2] = fmaf(c1, dz, fmaf(c2, nB.z, ag[2]));
+      }
+    }
+    U += (double)au;
+    if (GRAD) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) Gd[a] += (double)ag[a];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && it + 2 < nt) {
+      fence_proxy_async();
+      const int64_t st = (it + 2) * kSTile;
+      const uint32_t bytes = (uint32_t)min64(kSTile, n - st) * 32u;
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_g2s(&tile[b][0], T + 2 * st, bytes, &bar[b]);
+    }
+  }
+  if (p < m) {
+    u[p] += U;
+    if (GRAD) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) grad[a * m + p] += Gd[a];
+    }
+  }
+}
+
 }  // namespace bvc
 
 using namespace bvc;
@@ -493,10 +621,16 @@ extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) 
     if (!cache->z || !cache->nrm || !cache->u_hat || !cache->dudn_hat || !cache->packed) return BVC_ERR_INVALID_ARG;
     const unsigned grid = (unsigned)((cache->n + 255) / 256);
     ProfScope ps("pack_boundary", s);
-    if (cache->dim == 2)
+    if (cache->sigma > 0.0) {
+      if (cache->dim == 2)
+        k_pack_bnd_scr<2><<<grid, 256, 0, s>>>(*cache);
+      else
+        k_pack_bnd_scr<3><<<grid, 256, 0, s>>>(*cache);
+    } else if (cache->dim == 2) {
       k_pack_bnd<2><<<grid, 256, 0, s>>>(*cache);
-    else
+    } else {
       k_pack_bnd<3><<<grid, 256, 0, s>>>(*cache);
+    }
   }
   if (cache->n_src_cand > 0) {
     if (!cache->src_y || !cache->src_c || !cache->src_packed || !cache->n_src_dev) return BVC_ERR_INVALID_ARG;
@@ -581,8 +715,29 @@ extern "C" bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state
       (cache->n_src_cand > 0 && (cache->src_packed == nullptr || cache->n_src_dev == nullptr)))
     return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (cache->sigma > 0.0 && cache->n_src_cand > 0) return BVC_ERR_UNSUPPORTED;  // screened: f = 0
   if (state->m > 0) {
-    if (cache->n > 0) {
+    if (cache->n > 0 && cache->sigma > 0.0) {
+      const unsigned grid = (unsigned)((state->m + 255) / 256);
+      const float k = (float)sqrt(cache->sigma);
+      ProfScope ps("gather_screened", s);
+      if (D == 2) {
+        if (grad)
+          k_gather_scr<2, true><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
+                                                     state->u_bnd, state->grad_bnd);
+        else
+          k_gather_scr<2, false><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
+                                                      state->u_bnd, nullptr);
+      } else {
+        if (grad)
+          k_gather_scr<3, true><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
+                                                     state->u_bnd, state->grad_bnd);
+        else
+          k_gather_scr<3, false><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
+                                                      state->u_bnd, nullptr);
+      }
+      BVC_LAUNCH_CHECK();
+    } else if (cache->n > 0) {
       bvc_status st = run_part(D, 0, grad, state->x, state->m, (const float4*)cache->packed, cache->n, nullptr,
                                state->u_bnd, state->grad_bnd, workspace, workspace_bytes, s);
       if (st != BVC_OK) return st;

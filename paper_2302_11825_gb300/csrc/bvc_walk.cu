@@ -75,6 +75,8 @@ struct WalkParams {
   const double* adj_q;
   double* grad_gv;
   double* grad_amp;
+  // screened Poisson: sqrt(sigma) (> 0 selects the screened kernel variant)
+  float sqs;
   // launch shape: walks per warp refill (set by launch_walk)
   int64_t chunk;
   int32_t blocks_per_sm;  // 0 = as many as fit
@@ -125,8 +127,14 @@ constexpr int kStep = 2;   // query done: termination test, sphere sample, sourc
 //            variate g(closest point of the start), reduced per start later.
 constexpr int kRecGn = 0, kRecGrad = 1, kRecEnd = 2, kRecAdj = 3;
 
-template <int D, bool HAS_F, int REC, bool CNT>
+// FM: 0 Laplace (f = 0), 1 Poisson with a source term, 2 screened Poisson
+// (sigma > 0, f = 0): every ball multiplies the walk's throughput by its
+// screened mean-value factor C (value) and the first ball's Qg scales the
+// gradient estimate (screened_factors).
+template <int D, int FM, int REC, bool CNT>
 __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB(D)) k_walk(const WalkParams P) {
+  constexpr bool HAS_F = FM == 1;
+  constexpr bool SCR = FM == 2;
   // Traversal stacks: node links and box distances, the latter in FP16
   // rounded down (a smaller stored distance can only cost an extra visit,
   // never prune a box that must be visited).
@@ -152,6 +160,8 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
   // the walk's tree and shell (per mesh in a batch)
   int root = 0;
   float eps = P.eps;
+  // screened: throughput and the first ball's factors
+  float wthr = 1.0f, C0 = 1.0f, Qg0 = 1.0f;
   // adjoint replay: the start's weights, n . w0, FP64 amplitude gradients
   float cu = 0.0f, cq = 0.0f, nw0 = 0.0f;
   double gA[REC == kRecAdj && HAS_F ? kMaxBumps : 1];
@@ -222,6 +232,7 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
         }
         k = 0;
         R0 = usrc = wf0 = wg0 = cv = 0.0f;
+        if (SCR) wthr = C0 = Qg0 = 1.0f;
         if (P.first) {
           const int64_t c = P.total / P.W;
           h.d2 = P.first[r];
@@ -338,8 +349,10 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
             P.rec[t] = -s0;
           } else {
             const float gend = P.gv ? vertex_g<D>(G, P.gv, h.id, pbar) : eval_fn<D, true>(P.g, pbar);
-            const float U = (k == 1 ? cv : gend) + usrc;
-            const float sc = k > 1 ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
+            const float U = (k == 1 ? cv : (SCR ? wthr * gend : gend)) + usrc;
+            // screened: U / C0 estimates u at the first sphere point
+            const float sc = k > 1 ? (SCR ? ((float)D / R0) * Qg0 * (U / C0 - cv) : ((float)D / R0) * (U - wf0 - cv) + wg0)
+                                   : 0.0f;
             P.rec[t] = U;
             if (REC == kRecGn) {
               float nn2 = 0.0f;
@@ -358,6 +371,15 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
           phase = kIdle;
         } else {
           const float R = d;
+          if (SCR) {
+            float Cs, Qs;
+            screened_factors<D>(P.sqs * R, Cs, Qs);
+            wthr *= Cs;
+            if (k == 1) {
+              C0 = Cs;
+              Qg0 = Qs;
+            }
+          }
           const uint64_t seed = (REC == kRecEnd && P.seed_dev != nullptr) ? __ldg(P.seed_dev) : P.seed;
           const U4 r = philox_draw(seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
           const float u0 = u01f(r.x);
@@ -494,31 +516,36 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceParams R) {
   }
 }
 
-template <int D, bool HAS_F, int REC>
+template <int D, int FM, int REC>
 static const void* walk_kernel(bool cnt) {
-  return cnt ? (const void*)k_walk<D, HAS_F, REC, true> : (const void*)k_walk<D, HAS_F, REC, false>;
+  return cnt ? (const void*)k_walk<D, FM, REC, true> : (const void*)k_walk<D, FM, REC, false>;
 }
 
-// rec: kRecGn / kRecGrad / kRecEnd (the last only without a source term).
-static const void* pick_walk(int dim, bool has_f, int rec, bool cnt) {
-  if (rec == kRecEnd) return dim == 2 ? walk_kernel<2, false, kRecEnd>(cnt) : walk_kernel<3, false, kRecEnd>(cnt);
+// rec: kRecGn / kRecGrad / kRecEnd (f = 0 only) / kRecAdj (no counting);
+// scr: screened Poisson (f = 0, kRecGn / kRecGrad).
+static const void* pick_walk(int dim, bool has_f, int rec, bool cnt, bool scr = false) {
+  if (rec == kRecEnd) return dim == 2 ? walk_kernel<2, 0, kRecEnd>(cnt) : walk_kernel<3, 0, kRecEnd>(cnt);
   if (rec == kRecAdj) {
-    if (dim == 2) return has_f ? (const void*)k_walk<2, true, kRecAdj, false> : (const void*)k_walk<2, false, kRecAdj, false>;
-    return has_f ? (const void*)k_walk<3, true, kRecAdj, false> : (const void*)k_walk<3, false, kRecAdj, false>;
+    if (dim == 2) return has_f ? (const void*)k_walk<2, 1, kRecAdj, false> : (const void*)k_walk<2, 0, kRecAdj, false>;
+    return has_f ? (const void*)k_walk<3, 1, kRecAdj, false> : (const void*)k_walk<3, 0, kRecAdj, false>;
   }
   const bool gn = rec == kRecGn;
-  if (dim == 2) {
-    if (has_f) return gn ? walk_kernel<2, true, kRecGn>(cnt) : walk_kernel<2, true, kRecGrad>(cnt);
-    return gn ? walk_kernel<2, false, kRecGn>(cnt) : walk_kernel<2, false, kRecGrad>(cnt);
+  if (scr) {
+    if (dim == 2) return gn ? walk_kernel<2, 2, kRecGn>(cnt) : walk_kernel<2, 2, kRecGrad>(cnt);
+    return gn ? walk_kernel<3, 2, kRecGn>(cnt) : walk_kernel<3, 2, kRecGrad>(cnt);
   }
-  if (has_f) return gn ? walk_kernel<3, true, kRecGn>(cnt) : walk_kernel<3, true, kRecGrad>(cnt);
-  return gn ? walk_kernel<3, false, kRecGn>(cnt) : walk_kernel<3, false, kRecGrad>(cnt);
+  if (dim == 2) {
+    if (has_f) return gn ? walk_kernel<2, 1, kRecGn>(cnt) : walk_kernel<2, 1, kRecGrad>(cnt);
+    return gn ? walk_kernel<2, 0, kRecGn>(cnt) : walk_kernel<2, 0, kRecGrad>(cnt);
+  }
+  if (has_f) return gn ? walk_kernel<3, 1, kRecGn>(cnt) : walk_kernel<3, 1, kRecGrad>(cnt);
+  return gn ? walk_kernel<3, 0, kRecGn>(cnt) : walk_kernel<3, 0, kRecGrad>(cnt);
 }
 
 static bvc_status launch_walk(int dim, bool has_f, int rec, bool cnt, const WalkParams& P0, cudaStream_t s) {
   WalkParams P = P0;
   if (P.chunk < 1) P.chunk = kChunk;
-  const void* kern = pick_walk(dim, has_f, rec, cnt);
+  const void* kern = pick_walk(dim, has_f, rec, cnt, P.sqs > 0.0f);
   const int64_t want = (P.total + 31) / 32;
   int bps = max_blocks_per_sm(kern, kWalkBlock, 0);
   if (P.blocks_per_sm > 0 && P.blocks_per_sm < bps) bps = P.blocks_per_sm;
@@ -663,11 +690,16 @@ static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const flo
     return BVC_ERR_INVALID_ARG;
   const int64_t ncand = src_candidates(opts, D);
   if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
+  if (!std::isfinite(opts->sigma) || opts->sigma < 0.0) return BVC_ERR_INVALID_ARG;
+  // screened Poisson: f = 0 and no source cache
+  if (opts->sigma > 0.0 && ((ffn != nullptr && ffn->n_terms > 0) || ncand > 0)) return BVC_ERR_UNSUPPORTED;
   WalkParams P{};
   P.G = g->dev;
   P.chunk = g->tune_chunk;
   P.blocks_per_sm = g->tune_blocks_per_sm;
   P.gv = gv;
+  P.sqs = (float)std::sqrt(opts->sigma);
+  cache->sigma = opts->sigma;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
   const size_t per_sample = ws_per_start(D, W, 1);
   int64_t chunk = ws_chunk(workspace_bytes, per_sample);
@@ -796,7 +828,7 @@ extern "C" bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn,
   if (cache->dim != D || cache->n != N || cache->z == nullptr || cache->nrm == nullptr ||
       !valid_walk_args((float)opts->eps, opts->max_steps, W))
     return BVC_ERR_INVALID_ARG;
-  if (!diff_source_ok(ffn, D)) return BVC_ERR_UNSUPPORTED;
+  if (!diff_source_ok(ffn, D) || cache->sigma != 0.0 || opts->sigma != 0.0) return BVC_ERR_UNSUPPORTED;
   const bool has_f = ffn != nullptr && ffn->n_terms > 0;
   if (has_f && grad_amp == nullptr) return BVC_ERR_INVALID_ARG;
   WalkParams P{};
@@ -974,12 +1006,14 @@ __global__ void k_add_walk_count(int64_t* counts, int64_t w) {
   if (threadIdx.x == 0 && blockIdx.x == 0) counts[0] += w;
 }
 
-extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
-                                   bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
-                                   uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream) {
+extern "C" bvc_status wos_estimate_sigma(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                         double sigma, bvc_eval_state* state, int32_t walks, float eps,
+                                         int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
+                                         size_t workspace_bytes, bvc_stream stream) {
   if (g == nullptr || state == nullptr || state->dim != g->dim || state->m < 0 || state->counts == nullptr ||
-      !valid_walk_args(eps, max_steps, walks))
+      !valid_walk_args(eps, max_steps, walks) || !std::isfinite(sigma) || sigma < 0.0)
     return BVC_ERR_INVALID_ARG;
+  if (sigma > 0.0 && ffn != nullptr && ffn->n_terms > 0) return BVC_ERR_UNSUPPORTED;  // screened: f = 0
   const int64_t m = state->m;
   if (m > 0 && (state->x == nullptr || state->u_bnd == nullptr || workspace == nullptr)) return BVC_ERR_INVALID_ARG;
   const int D = g->dim;
@@ -1002,6 +1036,7 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
     P.max_steps = max_steps;
     P.seed = seed;
     P.tag = 3;
+    P.sqs = (float)std::sqrt(sigma);
     P.counter = (unsigned long long*)workspace;
     const bool grad = state->grad_bnd != nullptr;
     for (int64_t i0 = 0; i0 < m; i0 += chunk) {
@@ -1036,6 +1071,13 @@ extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, cons
   }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
+}
+
+extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                   bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                                   uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return wos_estimate_sigma(g, gfn, ffn, 0.0, state, walks, eps, max_steps, seed, id_base, workspace,
+                            workspace_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -1328,7 +1370,7 @@ extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs
   if (!valid_multi(cache, D) || cache->n != N || !valid_walk_args((float)opts->eps, opts->max_steps, W) ||
       !(opts->offset_l > 0.0))
     return BVC_ERR_INVALID_ARG;
-  if (src_candidates(opts, D) != 0) return BVC_ERR_UNSUPPORTED;  // f = 0 only
+  if (src_candidates(opts, D) != 0 || opts->sigma != 0.0) return BVC_ERR_UNSUPPORTED;  // Laplace (f = 0) only
   const size_t per = ws_per_start(D, W, D);
   int64_t chunk = ws_chunk(workspace_bytes, per);
   if (chunk < 1) return BVC_ERR_WORKSPACE;

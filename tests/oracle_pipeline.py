@@ -9,15 +9,17 @@ import numpy as np
 import oracle
 
 
-def oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid=None, max_steps=1 << 14, bvh=None, g_vertex=None):
+def oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid=None, max_steps=1 << 14, bvh=None, g_vertex=None,
+                 sigma=0.0):
     bvh = bvh or oracle.BVH(V, F)
     z, n, e = oracle.sample_boundary(V, F, N, l, seed)
     z32, n32 = z.astype(np.float32), n.astype(np.float32)
-    out = oracle.walks(bvh, g, f, z32, W, eps, max_steps, seed, id_base=0, tag=oracle.TAG_WALK, g_vertex=g_vertex)
+    out = oracle.walks(bvh, g, f, z32, W, eps, max_steps, seed, id_base=0, tag=oracle.TAG_WALK, g_vertex=g_vertex,
+                       sigma=sigma)
     u_hat, q_hat = oracle.reduce_walks(out["U"], out["grad"], n32, W)
     cache = {"z": z32, "n": n32, "u_hat": u_hat, "q_hat": q_hat, "elem": e,
              "measure": oracle.boundary_measure(V, F), "walks": out, "N": N,
-             "y": None, "c": None, "n_src": 0}
+             "y": None, "c": None, "n_src": 0, "sigma": sigma}
     if f and src_grid is not None:
         if V.shape[1] == 2:
             y, c, ncand = oracle.sample_source2d(V, F, src_grid, seed, f)
@@ -29,7 +31,7 @@ def oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid=None, max_steps=1 << 1
 
 def oracle_evaluate(cache, pts):
     ub, us, gb, gs = oracle.gather(cache["z"], cache["n"], cache["u_hat"], cache["q_hat"], cache["measure"],
-                                   pts, cache["y"], cache["c"])
+                                   pts, cache["y"], cache["c"], sigma=cache.get("sigma", 0.0))
     u = ub / cache["N"]
     grad = gb / cache["N"]
     if cache["n_src"]:
@@ -38,6 +40,7 @@ def oracle_evaluate(cache, pts):
     return u, grad
 
 
-def oracle_bvc(V, F, g, f, N, W, l, eps, pts, seed, src_grid=None, max_steps=1 << 14, bvh=None, g_vertex=None):
-    cache = oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid, max_steps, bvh, g_vertex)
+def oracle_bvc(V, F, g, f, N, W, l, eps, pts, seed, src_grid=None, max_steps=1 << 14, bvh=None, g_vertex=None,
+               sigma=0.0):
+    cache = oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid, max_steps, bvh, g_vertex, sigma)
     return oracle_evaluate(cache, pts)

@@ -98,10 +98,13 @@ def test_source_samples_match_oracle():
     np.testing.assert_allclose(cache.src_c[:kept].cpu().numpy(), co, rtol=2e-6, atol=1e-6 * np.abs(co).max())
 
 
-def test_source_samples_unsupported_in_3d():
+def test_source_grid_in_3d_needs_three_entries():
+    # 3D source samples take a G0 x G1 x G2 grid; a 2-entry grid is rejected
     V, F = _mesh("sphere4")
     geom = bvc.Geometry(V, F)
     cache = bvc.Cache(3, 1, n_src_cand=16)
     with pytest.raises(bvc.BvcError) as e:
         bvc.sample_source(geom, [(wl.POLY, [1.0])], (4, 4), 0, cache)
-    assert e.value.status == bvc.ERR_UNSUPPORTED
+    assert e.value.status == bvc.ERR_INVALID_ARG
+    cache = bvc.Cache(3, 1, n_src_cand=64)
+    bvc.sample_source(geom, [(wl.POLY, [1.0])], (4, 4, 4), 0, cache)
