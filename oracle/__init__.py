@@ -77,6 +77,8 @@ def _load():
                 "orc_vertex_interp": (f64, [P, P, i64, P]),
                 "orc_winding3d": (f64, [P, P, i64, P]),
                 "orc_bessel_i": (f64, [C.c_int, f64]),
+                "orc_ray_hits": (C.c_int, [C.c_int, P, P, i64, f64, P, P, f64, P, P, P]),
+                "orc_clamp_correction": (i64, [P, P, P, f64, P, P, i64, f64, P, i64, f64, i32, i32, f64, i32, u64, P]),
                 "orc_bessel_k": (f64, [C.c_int, f64]),
                 "orc_green_sigma": (None, [C.c_int, f64, P, P, P, P]),
                 "orc_screened_factors": (None, [C.c_int, f64, P, P]),
@@ -297,6 +299,38 @@ def vertex_interp(bvh: BVH, gv, elem, pts):
     pts = _f64(pts)
     return np.array([lib.orc_vertex_interp(bvh.h, _p(gv), int(e), _p(np.ascontiguousarray(p)))
                      for e, p in zip(elem, pts)])
+
+
+MAX_HITS = 8
+
+
+def ray_hits(V, F, l: float, x, om, rmax: float):
+    """Crossings of the ray x + t om (0 < t <= rmax) with the mesh whose
+    elements are moved by -l n_e: (t, element, n.om), nearest first."""
+    lib = _load()
+    V, F = _f32(V), _i32(F)
+    t, nw = np.zeros(MAX_HITS), np.zeros(MAX_HITS)
+    e = np.zeros(MAX_HITS, np.int64)
+    k = lib.orc_ray_hits(V.shape[1], _p(V), _p(F), F.shape[0], float(l), _p(_f64(x)), _p(_f64(om)), float(rmax),
+                         _p(t), _p(e), _p(nw))
+    return t[:k], e[:k], nw[:k]
+
+
+def clamp_correction(bvh: BVH, g_terms, Vs, Fs, l: float, pts, c: float, n_dirs: int, W: int, eps: float,
+                     seed: int, max_steps: int = 1 << 14, g_vertex=None, sigma: float = 0.0):
+    """Sec. 3.3: the estimate of int [dG/dn - clamp_c(dG/dn)] u dz per point
+    (rays against the sample surface Vs, Fs moved by -l n_e; walks on bvh).
+    Returns (u_corr, number of contributing hits)."""
+    lib = _load()
+    pts = _f64(pts)
+    Vs, Fs = _f32(Vs), _i32(Fs)
+    out = np.zeros(pts.shape[0])
+    g = encode_function(g_terms if g_vertex is None else [])
+    gv = None if g_vertex is None else _f64(g_vertex)
+    n = lib.orc_clamp_correction(bvh.h, _p(g), _p(gv), float(np.sqrt(sigma)), _p(Vs), _p(Fs), Fs.shape[0], float(l),
+                                 _p(pts), pts.shape[0], float(c), int(n_dirs), int(W), float(eps), int(max_steps),
+                                 int(seed), _p(out))
+    return out, int(n)
 
 
 def reduce_walks(U, grad, nrm, W: int):

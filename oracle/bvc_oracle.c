@@ -1026,6 +1026,163 @@ void orc_walks(void* bvh, const double* g, const double* f, const float* starts,
   orc_walks_vg(bvh, g, NULL, f, starts, n, W, eps, max_steps, seed, id_base, tag, U, grad, steps, prim, pend, scale);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Clamped double-layer kernel and its bias correction (Sec. 3.3, Eq. 8-9). */
+/* The cache's u-term uses dG/dn clamped to [-c, c]; the remainder          */
+/*   int [dG/dn - clamp(dG/dn)] u dz                                        */
+/* is estimated per evaluation point x by importance sampling dG/dn dz,     */
+/* the signed solid angle: a direction w uniform on the circle / sphere     */
+/* (Philox id = point * n_dirs + j, word2 0, tag 4; 2D w = (cos 2 pi u0,    */
+/* sin 2 pi u0); 3D z = 1 - 2 u0, phi = 2 pi u1) and every crossing z of   */
+/* the ray x + t w (0 < t) with the sample surface contributes              */
+/*   sign(n.w) (1 - c / |dG/dn(x, z)|) u(z) / n_dirs   when |dG/dn| > c,     */
+/* |dG/dn| = |n.w| / (2 pi t) (2D), |n.w| / (4 pi t^2) (3D), so only t below */
+/* 1/(2 pi c) or (4 pi c)^(-1/2) can matter.  The sample surface is the     */
+/* mesh with each element moved by -l n_e (l = 0: the mesh itself).  u(z)   */
+/* is estimated by W walks from z (FP32-rounded) on the domain's geometry   */
+/* (tag 5, walk id = hit rank * W + j, hits ranked by point, direction and  */
+/* distance along the ray).                                                  */
+/* ------------------------------------------------------------------------ */
+#define ORC_MAX_HITS 8
+int orc_ray_hits(int dim, const float* V, const int32_t* F, int64_t np, double l, const double* x, const double* om,
+                 double rmax, double* t_out, int64_t* e_out, double* nw_out) {
+  int nh = 0;
+  for (int64_t e = 0; e < np; ++e) {
+    const int32_t* f = F + e * dim;
+    double n[3] = {0, 0, 0};
+    elem_measure_normal(dim, V, f, n);
+    double t = -1.0;
+    if (dim == 2) {
+      double a[2], b[2];
+      for (int k = 0; k < 2; ++k) {
+        a[k] = (double)V[2 * f[0] + k] - l * n[k];
+        b[k] = (double)V[2 * f[1] + k] - l * n[k];
+      }
+      const double ex = b[0] - a[0], ey = b[1] - a[1];
+      const double den = om[0] * ey - om[1] * ex;
+      if (fabs(den) < 1e-300) continue;
+      const double ax = a[0] - x[0], ay = a[1] - x[1];
+      const double tt = (ax * ey - ay * ex) / den;
+      const double ss = (ax * om[1] - ay * om[0]) / den;
+      if (ss < 0.0 || ss > 1.0) continue;
+      t = tt;
+    } else {
+      double a[3], b[3], c[3];
+      for (int k = 0; k < 3; ++k) {
+        a[k] = (double)V[3 * f[0] + k] - l * n[k];
+        b[k] = (double)V[3 * f[1] + k] - l * n[k];
+        c[k] = (double)V[3 * f[2] + k] - l * n[k];
+      }
+      /* Moller-Trumbore (J. Graphics Tools 2(1), 1997) */
+      double e1[3], e2[3], tv[3];
+      for (int k = 0; k < 3; ++k) {
+        e1[k] = b[k] - a[k];
+        e2[k] = c[k] - a[k];
+        tv[k] = x[k] - a[k];
+      }
+      const double pv[3] = {om[1] * e2[2] - om[2] * e2[1], om[2] * e2[0] - om[0] * e2[2],
+                            om[0] * e2[1] - om[1] * e2[0]};
+      const double det = dot3d(e1, pv);
+      if (fabs(det) < 1e-300) continue;
+      const double u = dot3d(tv, pv) / det;
+      if (u < 0.0 || u > 1.0) continue;
+      const double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2],
+                            tv[0] * e1[1] - tv[1] * e1[0]};
+      const double v = dot3d(om, qv) / det;
+      if (v < 0.0 || u + v > 1.0) continue;
+      t = dot3d(e2, qv) / det;
+    }
+    if (!(t > 0.0) || t > rmax) continue;
+    double nw = 0.0;
+    for (int k = 0; k < dim; ++k) nw += n[k] * om[k];
+    /* insert sorted by t (ties by element), keep the nearest ORC_MAX_HITS */
+    int pos = nh;
+    while (pos > 0 && (t_out[pos - 1] > t || (t_out[pos - 1] == t && e_out[pos - 1] > e))) --pos;
+    if (pos >= ORC_MAX_HITS) continue;
+    const int last = nh < ORC_MAX_HITS ? nh : ORC_MAX_HITS - 1;
+    for (int q = last; q > pos; --q) {
+      t_out[q] = t_out[q - 1];
+      e_out[q] = e_out[q - 1];
+      nw_out[q] = nw_out[q - 1];
+    }
+    t_out[pos] = t;
+    e_out[pos] = e;
+    nw_out[pos] = nw;
+    if (nh < ORC_MAX_HITS) ++nh;
+  }
+  return nh;
+}
+
+static void unit_direction(int dim, const double* u, double* om) {
+  if (dim == 2) {
+    om[0] = cos(2.0 * ORC_PI * u[0]);
+    om[1] = sin(2.0 * ORC_PI * u[0]);
+  } else {
+    const double zc = 1.0 - 2.0 * u[0], phi = 2.0 * ORC_PI * u[1];
+    const double s = sqrt(fmax(0.0, 1.0 - zc * zc));
+    om[0] = s * cos(phi);
+    om[1] = s * sin(phi);
+    om[2] = zc;
+  }
+}
+
+/* u_corr[m] (overwritten) and the number of contributing hits. */
+int64_t orc_clamp_correction(void* bvh, const double* g, const double* gv, double sqs, const float* Vs,
+                             const int32_t* Fs, int64_t nps, double l, const double* pts, int64_t m, double c,
+                             int32_t n_dirs, int32_t W, double eps, int32_t max_steps, uint64_t seed,
+                             double* u_corr) {
+  const obvh_t* B = (const obvh_t*)bvh;
+  const int dim = B->m.dim;
+  const double rmax = dim == 2 ? 1.0 / (2.0 * ORC_PI * c) : sqrt(1.0 / (4.0 * ORC_PI * c));
+  const int64_t slots = m * (int64_t)n_dirs * ORC_MAX_HITS;
+  double* hz = (double*)malloc((size_t)slots * 3 * sizeof(double));
+  double* hw = (double*)malloc((size_t)slots * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t q = 0; q < m * (int64_t)n_dirs; ++q) {
+    const int64_t p = q / n_dirs;
+    double u[4], om[3] = {0, 0, 0};
+    draw(seed, (uint64_t)q, 0u, 4u, u);
+    unit_direction(dim, u, om);
+    double t[ORC_MAX_HITS], nw[ORC_MAX_HITS];
+    int64_t e[ORC_MAX_HITS];
+    const int nh = orc_ray_hits(dim, Vs, Fs, nps, l, pts + p * dim, om, rmax, t, e, nw);
+    for (int k = 0; k < ORC_MAX_HITS; ++k) {
+      const int64_t sl = q * ORC_MAX_HITS + k;
+      hw[sl] = 0.0;
+      if (k >= nh) continue;
+      const double gn = dim == 2 ? fabs(nw[k]) / (2.0 * ORC_PI * t[k]) : fabs(nw[k]) / (4.0 * ORC_PI * t[k] * t[k]);
+      if (!(gn > c)) continue;
+      hw[sl] = (nw[k] > 0.0 ? 1.0 : -1.0) * (1.0 - c / gn) / n_dirs;
+      for (int a = 0; a < dim; ++a) hz[3 * sl + a] = (double)(float)(pts[p * dim + a] + t[k] * om[a]);
+    }
+  }
+  /* rank the contributing hits in slot order */
+  int64_t nhit = 0;
+  int64_t* rank = (int64_t*)malloc((size_t)slots * sizeof(int64_t));
+  for (int64_t sl = 0; sl < slots; ++sl) rank[sl] = hw[sl] != 0.0 ? nhit++ : -1;
+  for (int64_t p = 0; p < m; ++p) u_corr[p] = 0.0;
+  walk_ctx_t w = {B, g, NULL, eps, max_steps, seed, 5u, gv, sqs};
+  double* contrib = (double*)calloc((size_t)slots, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t sl = 0; sl < slots; ++sl) {
+    if (rank[sl] < 0) continue;
+    double sum = 0.0;
+    for (int32_t j = 0; j < W; ++j) {
+      double U, grad[3];
+      int32_t steps, prim;
+      walk_one(&w, hz + 3 * sl, (uint64_t)rank[sl] * W + j, &U, grad, &steps, &prim, NULL, NULL);
+      sum += U;
+    }
+    contrib[sl] = hw[sl] * sum / W;
+  }
+  for (int64_t sl = 0; sl < slots; ++sl) u_corr[sl / ((int64_t)n_dirs * ORC_MAX_HITS)] += contrib[sl];
+  free(contrib);
+  free(rank);
+  free(hz);
+  free(hw);
+  return nhit;
+}
+
 /* Per-sample means over the W walks of each start (Alg. 1: the pointwise   */
 /* estimates u^ and du/dn^ of a boundary sample).  du/dn^ = n . grad.        */
 void orc_reduce_walks(int dim, int64_t n, int32_t W, const double* U, const double* grad, const float* nrm,
