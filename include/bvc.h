@@ -210,6 +210,7 @@ typedef struct {
   float* src_packed;    /* [n_src_cand][8] gather tiles */
   int64_t* n_src_dev;   /* [1] number of kept source samples (written on device) */
   double sigma;         /* screening coefficient of the cache (set by the build); 0 = Poisson */
+  double clamp_c;       /* bound c of the clamped dG/dn in the u term (Sec. 3.3, set by the build); 0 = none */
 } bvc_cache;
 
 /* K4 -- source samples (Alg. 1 "y ~ p^R", Sec. 4 "Sampling"): a jittered
@@ -249,6 +250,8 @@ typedef struct {
                                zero and there is no source cache; the walks weight each ball by its
                                screened mean-value factor and the gather uses the screened Green's
                                functions of App. A.  0 = Poisson. */
+  double clamp_c;           /* > 0: the gather clamps dG/dn in the u term to [-c, c] (Sec. 3.3,
+                               Eq. 8-9); bvc_clamp_correction estimates the remainder.  0 = none. */
 } bvc_cache_opts;
 
 /* The whole cache: K1 -> K2 (chunked through the workspace) -> K3 -> K4 -> pack.
@@ -327,6 +330,39 @@ bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, const bvc_fun
                           const bvc_cache_opts* opts, void* workspace, size_t workspace_bytes, bvc_stream stream,
                           int32_t shape[2], float* best_ms);
 bvc_status bvc_geometry_set_walk_shape(bvc_geometry g, int32_t blocks_per_sm, int32_t chunk);
+
+/* ------------------------------------------- regions and clamped kernels */
+/* Region of interest (Sec. 3.2 "Boundary Specification"): the boundary
+ * samples lie on the region's own boundary (offset_l >= 0 from it, normals
+ * outward of the region), the walks run in the domain (its geometry), the
+ * source samples fill the region (its bounding box and inside test), and the
+ * gather then evaluates u and grad u at points inside the region (the
+ * estimate is 0 outside it).  region must lie inside the domain; both share
+ * a dimension.  Otherwise as bvc_cache_build. */
+bvc_status bvc_cache_build_region(bvc_geometry domain, bvc_geometry region, const bvc_function* gfn,
+                                  const bvc_function* ffn, const bvc_cache_opts* opts, bvc_cache* cache,
+                                  void* workspace, size_t workspace_bytes, bvc_stream stream);
+
+/* The remainder of the clamped double-layer kernel (Sec. 3.3, Eq. 8): for a
+ * cache built with opts.clamp_c = c (its gather uses dG/dn clamped to
+ * [-c, c] in the u term), u_corr[x] (device double[m], overwritten) is an
+ * unbiased estimate of int [dG/dn - clamp_c(dG/dn)] u dz over the sample
+ * surface -- `surface` with its elements moved by -offset_l n (the cache's
+ * geometry and offset, or a region and 0) -- so that get_solution + u_corr
+ * is unbiased.  n_dirs directions per point (Philox id = point * n_dirs + j,
+ * word2 0, tag 4) sample the signed solid angle; every crossing closer than
+ * 1/(2 pi c) (2D) or (4 pi c)^(-1/2) (3D) with |dG/dn| > c adds
+ * sign(n.w) (1 - c/|dG/dn|) u(z) / n_dirs, u(z) from `walks` walks on the
+ * domain (tag 5, ids rank * walks + j, crossings ranked by point, direction,
+ * distance; at most 8 per ray).  Synchronises `stream` once (the crossing
+ * count decides the walk launches); *n_hits receives that count. */
+bvc_status bvc_clamp_correction_workspace_size(int32_t dim, int64_t m, int32_t n_dirs, int32_t walks,
+                                               size_t* min_bytes);
+bvc_status bvc_clamp_correction(bvc_geometry domain, bvc_geometry surface, double offset_l, const bvc_function* gfn,
+                                const bvc_function* ffn, double sigma, double clamp_c, const float* pts, int64_t m,
+                                int32_t n_dirs, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                                double* u_corr, int64_t* n_hits, void* workspace, size_t workspace_bytes,
+                                bvc_stream stream);
 
 /* ------------------------------------------------------ differentiation */
 /* Gradients of a loss L of the values u(x) that bvc_evaluate gives (Eq. 3)

@@ -84,6 +84,8 @@ def _load():
                 "orc_screened_factors": (None, [C.c_int, f64, P, P]),
                 "orc_walks_sigma": (None, [P, P, P, P, f64, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_gather_sigma": (None, [C.c_int, f64, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
+                "orc_gather_full": (None, [C.c_int, f64, f64, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P,
+                                           P]),
                 "orc_sample_source3d": (i64, [P, i64, P, i64, i32, i32, i32, u64, P, P, P, P]),
                 "orc_reduce_walks": (None, [C.c_int, i64, i32, P, P, P, P, P]),
                 "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P]),
@@ -385,9 +387,11 @@ def sample_source2d(V, F, grid, seed: int, f_terms):
     return y[:kept].copy(), c[:kept].copy(), G0 * G1
 
 
-def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs: bool = False, sigma: float = 0.0):
+def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs: bool = False, sigma: float = 0.0,
+           clamp_c: float = 0.0):
     """Eq. 3-6 / Alg. 1 splat: FP64 running sums (u_bnd, u_src, g_bnd, g_src).
     sigma > 0: with the screened Green's functions of App. A.
+    clamp_c > 0: dG/dn of the u term clamped to [-c, c] (Sec. 3.3).
 
     With want_abs, also the per-point sums of |term| (for error scaling):
     array [M, 2 + 2 dim] = [u_bnd, g_bnd(dim), u_src, g_src(dim)]."""
@@ -403,8 +407,8 @@ def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs:
     ub, us = np.zeros(M), np.zeros(M)
     gb, gs = np.zeros((M, dim)), np.zeros((M, dim))
     ab = np.zeros((M, 2 + 2 * dim)) if want_abs else None
-    lib.orc_gather_sigma(dim, float(np.sqrt(sigma)), N, _p(z), _p(nz), _p(u_hat), _p(q_hat), float(bnd_measure),
-                         y.shape[0], _p(y), _p(c), M, _p(x), _p(ub), _p(us), _p(gb), _p(gs), _p(ab))
+    lib.orc_gather_full(dim, float(np.sqrt(sigma)), float(clamp_c), N, _p(z), _p(nz), _p(u_hat), _p(q_hat),
+                        float(bnd_measure), y.shape[0], _p(y), _p(c), M, _p(x), _p(ub), _p(us), _p(gb), _p(gs), _p(ab))
     if want_abs:
         return ub, us, gb, gs, ab
     return ub, us, gb, gs

@@ -1329,9 +1329,12 @@ int64_t orc_sample_source3d(const float* V, int64_t nv, const int32_t* F, int64_
 /*   u_src    += G(x,y) c,    grad_src += dG/dx(x,y) c                       */
 /* Returns SUMS (Alg. 1 running sums); the caller divides by N and M.       */
 /* ------------------------------------------------------------------------ */
-void orc_gather_sigma(int dim, double sqs, int64_t N, const double* z, const double* nz, const double* u_hat,
-                      const double* q_hat, double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M,
-                      const double* x, double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
+/* clamp_c > 0: dG/dn in the u term clamped to [-c, c] (Sec. 3.3, Eq. 9);  */
+/* the gradient terms are not clamped.                                       */
+void orc_gather_full(int dim, double sqs, double clamp_c, int64_t N, const double* z, const double* nz,
+                     const double* u_hat, const double* q_hat, double bnd_measure, int64_t Ms, const double* y,
+                     const double* c, int64_t M, const double* x, double* u_bnd, double* u_src, double* g_bnd,
+                     double* g_src, double* abs_out) {
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t k = 0; k < M; ++k) {
     double xk[3] = {0, 0, 0}, zz[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, G[8];
@@ -1345,7 +1348,7 @@ void orc_gather_sigma(int dim, double sqs, int64_t N, const double* z, const dou
         nn[a] = nz[i * dim + a];
       }
       orc_green_sigma(dim, sqs, xk, zz, nn, G);
-      const double dGdn = G[1 + dim];
+      const double dGdn = clamp_c > 0.0 ? fmax(-clamp_c, fmin(clamp_c, G[1 + dim])) : G[1 + dim];
       const double tu = (dGdn * u_hat[i] - G[0] * q_hat[i]) * bnd_measure;
       ub += tu;
       ab[0] += fabs(tu);
@@ -1376,10 +1379,18 @@ void orc_gather_sigma(int dim, double sqs, int64_t N, const double* z, const dou
   }
 }
 
+void orc_gather_sigma(int dim, double sqs, int64_t N, const double* z, const double* nz, const double* u_hat,
+                      const double* q_hat, double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M,
+                      const double* x, double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
+  orc_gather_full(dim, sqs, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, Ms, y, c, M, x, u_bnd, u_src, g_bnd, g_src,
+                  abs_out);
+}
+
 void orc_gather(int dim, int64_t N, const double* z, const double* nz, const double* u_hat, const double* q_hat,
                 double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M, const double* x,
                 double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
-  orc_gather_sigma(dim, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, Ms, y, c, M, x, u_bnd, u_src, g_bnd, g_src, abs_out);
+  orc_gather_full(dim, 0.0, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, Ms, y, c, M, x, u_bnd, u_src, g_bnd, g_src,
+                  abs_out);
 }
 
 int orc_num_threads(void) {

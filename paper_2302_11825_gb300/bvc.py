@@ -54,13 +54,14 @@ class CacheStruct(C.Structure):
                 ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p), ("packed", C.c_void_p),
                 ("bnd_measure", C.c_double), ("n_src_cand", C.c_int64), ("src_y", C.c_void_p),
                 ("src_c", C.c_void_p), ("src_packed", C.c_void_p), ("n_src_dev", C.c_void_p),
-                ("sigma", C.c_double)]
+                ("sigma", C.c_double), ("clamp_c", C.c_double)]
 
 
 class CacheOpts(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("walks_per_sample", C.c_int32), ("max_steps", C.c_int32),
                 ("offset_l", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64),
-                ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 3), ("sigma", C.c_double)]
+                ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 3), ("sigma", C.c_double),
+                ("clamp_c", C.c_double)]
 
 
 class MultiCacheStruct(C.Structure):
@@ -139,6 +140,11 @@ def _declare(lib):
         "bvc_batch_stats": (S, [P, C.POINTER(C.c_uint64), i32, P]),
         "bvc_batch_project": (S, [P, P, C.POINTER(MultiCacheStruct), P]),
         "bvc_batch_evaluate": (S, [P, C.POINTER(MultiCacheStruct), P, P, P]),
+        "bvc_cache_build_region": (S, [P, P, C.POINTER(Function), C.POINTER(Function), C.POINTER(CacheOpts),
+                                       C.POINTER(CacheStruct), P, sz, P]),
+        "bvc_clamp_correction_workspace_size": (S, [i32, i64, i32, i32, C.POINTER(sz)]),
+        "bvc_clamp_correction": (S, [P, P, f64, C.POINTER(Function), C.POINTER(Function), f64, f64, P, i64, i32, i32,
+                                     f32, i32, u64, P, C.POINTER(C.c_int64), P, sz, P]),
         "bvc_tune_walks_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz)]),
         "bvc_tune_walks": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(CacheOpts), P, sz, P,
                                C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
@@ -371,13 +377,14 @@ def n_candidates(dim: int, src_grid) -> int:
 
 
 def cache_opts(n_samples, walks, offset_l, eps, seed, max_steps=1 << 14, walk_id_base=0, src_grid=(0, 0),
-               sigma: float = 0.0):
+               sigma: float = 0.0, clamp_c: float = 0.0):
     o = CacheOpts()
     o.n_samples, o.walks_per_sample, o.max_steps = int(n_samples), int(walks), int(max_steps)
     o.offset_l, o.eps, o.seed, o.walk_id_base = float(offset_l), float(eps), int(seed), int(walk_id_base)
     o.src_grid[0], o.src_grid[1] = int(src_grid[0]), int(src_grid[1])
     o.src_grid[2] = int(src_grid[2]) if len(src_grid) > 2 else 0
     o.sigma = float(sigma)
+    o.clamp_c = float(clamp_c)
     return o
 
 
@@ -457,6 +464,41 @@ def evaluate(cache: Cache, state: EvalState, ws: torch.Tensor = None, stream=Non
         ws = workspace(evaluate_workspace_size(cache, state))
     _check(lib().bvc_evaluate(C.byref(cache.struct), C.byref(state.struct), _ptr(ws), ws.numel(), _stream(stream)),
            "bvc_evaluate")
+
+
+# ---------------------------------------------------------------- regions, clamping
+def cache_build_region(domain: Geometry, region: Geometry, g_terms, f_terms, opts: CacheOpts, cache: Cache,
+                       ws: torch.Tensor = None, stream=None):
+    """Sec. 3.2: samples on the region's boundary, walks in the domain."""
+    if ws is None:
+        ws = workspace(cache_build_workspace_size(domain, opts)[1])
+    g, f = make_function(g_terms), make_function(f_terms)
+    _check(lib().bvc_cache_build_region(domain.h, region.h, C.byref(g), C.byref(f), C.byref(opts),
+                                        C.byref(cache.struct), _ptr(ws), ws.numel(), _stream(stream)),
+           "bvc_cache_build_region")
+    return cache
+
+
+def clamp_correction(domain: Geometry, surface: Geometry, offset_l: float, g_terms, f_terms, clamp_c: float,
+                     pts: torch.Tensor, n_dirs: int, walks: int, eps: float, seed: int, max_steps: int = 1 << 14,
+                     sigma: float = 0.0, stream=None):
+    """Sec. 3.3: the remainder of the clamped double-layer term per point;
+    returns (u_corr float64 [m], number of crossings)."""
+    _dev(pts, torch.float32)
+    m = pts.shape[1]
+    b = C.c_size_t()
+    _check(lib().bvc_clamp_correction_workspace_size(domain.dim, m, int(n_dirs), int(walks), C.byref(b)),
+           "bvc_clamp_correction_workspace_size")
+    per = wos_workspace_size(domain.dim, 1, walks)[0]
+    ws = workspace(b.value + 4096 * per)
+    out = torch.empty(m, dtype=torch.float64, device=pts.device)
+    g, f = make_function(g_terms), make_function(f_terms)
+    nh = C.c_int64()
+    _check(lib().bvc_clamp_correction(domain.h, surface.h, float(offset_l), C.byref(g), C.byref(f), float(sigma),
+                                      float(clamp_c), _ptr(pts), m, int(n_dirs), int(walks), float(eps),
+                                      int(max_steps), int(seed), _ptr(out), C.byref(nh), _ptr(ws), ws.numel(),
+                                      _stream(stream)), "bvc_clamp_correction")
+    return out, int(nh.value)
 
 
 # ---------------------------------------------------------------- walk autotuner

@@ -495,6 +495,10 @@ static size_t part_bytes(const Plan& P, int planes, int64_t m) {
 //       grad u += A [Q (3 (n.d) d / r^5 - n / r^3) + (n.d)/r^3 k^2 exp(-t) d] + B Q d / r^3
 // One point per thread, 128-sample tiles by bulk copy, FP32 per tile, FP64
 // across tiles; sums added into the evaluation state like bvc_evaluate's.
+// The same kernel serves the Poisson boundary term (SCR false: Q = 1, the
+// K0 factor replaced by -ln r, exp(-t) by 1) when the u term's dG/dn is
+// clamped to [-c, c] (Sec. 3.3, Eq. 9; CLAMP, cw = c w): the gradient terms
+// stay unclamped.
 constexpr int kSTile = 128;
 
 template <int D>
@@ -508,9 +512,9 @@ __global__ void __launch_bounds__(256) k_pack_bnd_scr(const bvc_cache C) {
   o[1] = make_float4(C.nrm[i], C.nrm[C.n + i], D == 3 ? C.nrm[2 * C.n + i] : 0.0f, (float)(C.dudn_hat[i] * ca));
 }
 
-template <int D, bool GRAD>
+template <int D, bool GRAD, bool SCR, bool CLAMP>
 __global__ void __launch_bounds__(256) k_gather_scr(const float* __restrict__ x, int64_t m, const float4* __restrict__ T,
-                                                   int64_t n, float k, double* __restrict__ u,
+                                                   int64_t n, float k, float cw, double* __restrict__ u,
                                                    double* __restrict__ grad) {
   __shared__ __align__(128) float4 tile[2][2 * kSTile];
   __shared__ __align__(8) uint64_t bar[2];
@@ -555,7 +559,12 @@ __global__ void __launch_bounds__(256) k_gather_scr(const float* __restrict__ x,
       const float nd = fmaf(nB.z, dz, fmaf(nB.y, dy, nB.x * dx));
       float Q, kern, dq;  // Q; K0 or exp(-t)/r; the gradient factor of Q
       float ik;           // 1/r^2 (2D) or 1/r^3 (3D)
-      if (D == 2) {
+      if (!SCR) {
+        Q = 1.0f;
+        dq = 0.0f;
+        kern = D == 2 ? -0.5f * __logf(r2) : ir;
+        ik = D == 2 ? ir * ir : ir * ir * ir;
+      } else if (D == 2) {
         float k0, k1;
         if (t <= 2.0f) {
           k0 = bessel_k0_small(t);
@@ -576,7 +585,7 @@ __global__ void __launch_bounds__(256) k_gather_scr(const float* __restrict__ x,
         dq = k2 * e3;
         ik = ir * ir * ir;
       }
-      const float s1 = zA.w * Q * nd * ik;
+      const float s1 = CLAMP ? zA.w * fminf(fmaxf(Q * nd * ik, -cw), cw) : zA.w * Q * nd * ik;
       au += fmaf(nB.w, kern, s1);
       if (GRAD) {
         // A [Q (D (n.d) d / r^(D+2) - n / r^D) + (n.d)/r^D dq d] + B Q d / r^D
@@ -621,7 +630,7 @@ extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) 
     if (!cache->z || !cache->nrm || !cache->u_hat || !cache->dudn_hat || !cache->packed) return BVC_ERR_INVALID_ARG;
     const unsigned grid = (unsigned)((cache->n + 255) / 256);
     ProfScope ps("pack_boundary", s);
-    if (cache->sigma > 0.0) {
+    if (cache->sigma > 0.0 || cache->clamp_c > 0.0) {
       if (cache->dim == 2)
         k_pack_bnd_scr<2><<<grid, 256, 0, s>>>(*cache);
       else
@@ -717,25 +726,39 @@ extern "C" bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state
   cudaStream_t s = (cudaStream_t)stream;
   if (cache->sigma > 0.0 && cache->n_src_cand > 0) return BVC_ERR_UNSUPPORTED;  // screened: f = 0
   if (state->m > 0) {
-    if (cache->n > 0 && cache->sigma > 0.0) {
+    if (cache->n > 0 && (cache->sigma > 0.0 || cache->clamp_c > 0.0)) {
       const unsigned grid = (unsigned)((state->m + 255) / 256);
       const float k = (float)sqrt(cache->sigma);
-      ProfScope ps("gather_screened", s);
+      const float cw = (float)(cache->clamp_c * (D == 2 ? 6.283185307179586476925 : 12.566370614359172953850));
+      const bool scr = cache->sigma > 0.0, clamp = cache->clamp_c > 0.0;
+      const float4* T = (const float4*)cache->packed;
+      ProfScope ps(scr ? "gather_screened" : "gather_clamped", s);
+#define BVC_FLEX(DD, GG, SS, CC) \
+  k_gather_scr<DD, GG, SS, CC><<<grid, 256, 0, s>>>(state->x, state->m, T, cache->n, k, cw, state->u_bnd, \
+                                                    GG ? state->grad_bnd : nullptr)
+#define BVC_FLEX_D(DD) \
+  if (grad) {                                                  \
+    if (scr) {                                                 \
+      if (clamp) BVC_FLEX(DD, true, true, true);               \
+      else BVC_FLEX(DD, true, true, false);                    \
+    } else {                                                   \
+      BVC_FLEX(DD, true, false, true);                         \
+    }                                                          \
+  } else {                                                     \
+    if (scr) {                                                 \
+      if (clamp) BVC_FLEX(DD, false, true, true);              \
+      else BVC_FLEX(DD, false, true, false);                   \
+    } else {                                                   \
+      BVC_FLEX(DD, false, false, true);                        \
+    }                                                          \
+  }
       if (D == 2) {
-        if (grad)
-          k_gather_scr<2, true><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
-                                                     state->u_bnd, state->grad_bnd);
-        else
-          k_gather_scr<2, false><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
-                                                      state->u_bnd, nullptr);
+        BVC_FLEX_D(2)
       } else {
-        if (grad)
-          k_gather_scr<3, true><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
-                                                     state->u_bnd, state->grad_bnd);
-        else
-          k_gather_scr<3, false><<<grid, 256, 0, s>>>(state->x, state->m, (const float4*)cache->packed, cache->n, k,
-                                                      state->u_bnd, nullptr);
+        BVC_FLEX_D(3)
       }
+#undef BVC_FLEX_D
+#undef BVC_FLEX
       BVC_LAUNCH_CHECK();
     } else if (cache->n > 0) {
       bvc_status st = run_part(D, 0, grad, state->x, state->m, (const float4*)cache->packed, cache->n, nullptr,

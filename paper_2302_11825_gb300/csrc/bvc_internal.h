@@ -93,6 +93,14 @@ namespace bvc {
 // Host helpers (bvc_common.cu)
 bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);
 int num_sms();
+// Pointwise walks (kRecGrad records) from the starts [i0, i0 + c) of a
+// [dim][pt_stride] point set, walk ids wid0 + r * W + j, on geometry g; the
+// records' U plane is then at walk_records_u(ws, c, dim)[r * W + j].
+bvc_status walk_points_u(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, double sigma,
+                         const float* starts, int64_t pt_stride, int64_t i0, int64_t c, int32_t W, float eps,
+                         int32_t max_steps, uint64_t seed, uint32_t tag, uint64_t wid0, void* ws, size_t ws_bytes,
+                         cudaStream_t s);
+const float* walk_records_u(void* ws, int64_t c, int dim);
 // dL/dA of the source cache's bump amplitudes from dL/dc of its samples.
 bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache* cache, const double* adj,
                               double* grad_amp, cudaStream_t s);

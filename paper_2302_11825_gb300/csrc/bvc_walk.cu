@@ -677,20 +677,26 @@ extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_c
   return BVC_OK;
 }
 
-static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const float* gv, const bvc_function* ffn,
-                              const bvc_cache_opts* opts, bvc_cache* cache, void* workspace, size_t workspace_bytes,
-                              bvc_stream stream) {
-  if (g == nullptr || opts == nullptr || cache == nullptr) return BVC_ERR_INVALID_ARG;
+// g: the domain's geometry (walks); gs: the geometry the samples lie on and
+// the source samples fill -- g itself, or a region of interest inside the
+// domain (Sec. 3.2 "Boundary Specification"), whose samples may sit on its
+// boundary (offset 0).
+static bvc_status cache_build(bvc_geometry g, bvc_geometry gs, const bvc_function* gfn, const float* gv,
+                              const bvc_function* ffn, const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
+                              size_t workspace_bytes, bvc_stream stream) {
+  if (g == nullptr || gs == nullptr || opts == nullptr || cache == nullptr || gs->dim != g->dim)
+    return BVC_ERR_INVALID_ARG;
   const int D = g->dim;
   const int64_t N = opts->n_samples;
   const int32_t W = opts->walks_per_sample;
   if (cache->dim != D || cache->n != N || N < 1 || !valid_walk_args((float)opts->eps, opts->max_steps, W) ||
-      !(opts->offset_l > 0.0) || cache->z == nullptr || cache->nrm == nullptr || cache->u_hat == nullptr ||
+      !(gs == g ? opts->offset_l > 0.0 : opts->offset_l >= 0.0) || cache->z == nullptr || cache->nrm == nullptr || cache->u_hat == nullptr ||
       cache->dudn_hat == nullptr || cache->packed == nullptr || workspace == nullptr)
     return BVC_ERR_INVALID_ARG;
   const int64_t ncand = src_candidates(opts, D);
   if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
-  if (!std::isfinite(opts->sigma) || opts->sigma < 0.0) return BVC_ERR_INVALID_ARG;
+  if (!std::isfinite(opts->sigma) || opts->sigma < 0.0 || !std::isfinite(opts->clamp_c) || opts->clamp_c < 0.0)
+    return BVC_ERR_INVALID_ARG;
   // screened Poisson: f = 0 and no source cache
   if (opts->sigma > 0.0 && ((ffn != nullptr && ffn->n_terms > 0) || ncand > 0)) return BVC_ERR_UNSUPPORTED;
   WalkParams P{};
@@ -700,14 +706,15 @@ static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const flo
   P.gv = gv;
   P.sqs = (float)std::sqrt(opts->sigma);
   cache->sigma = opts->sigma;
+  cache->clamp_c = opts->clamp_c;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
   const size_t per_sample = ws_per_start(D, W, 1);
   int64_t chunk = ws_chunk(workspace_bytes, per_sample);
   if (chunk < 1) return BVC_ERR_WORKSPACE;
   if (chunk > N) chunk = N;
   cudaStream_t s = (cudaStream_t)stream;
-  cache->bnd_measure = g->measure;
-  bvc_status st = bvc_sample_boundary(g, N, opts->offset_l, opts->seed, cache->z, cache->nrm, nullptr, stream);
+  cache->bnd_measure = gs->measure;
+  bvc_status st = bvc_sample_boundary(gs, N, opts->offset_l, opts->seed, cache->z, cache->nrm, nullptr, stream);
   if (st != BVC_OK) return st;
   P.starts = cache->z;
   P.nrm = cache->nrm;
@@ -743,7 +750,7 @@ static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const flo
     if (st != BVC_OK) return st;
   }
   if (ncand > 0) {
-    st = bvc_sample_source(g, ffn, opts->src_grid, opts->seed, cache, workspace, workspace_bytes, stream);
+    st = bvc_sample_source(gs, ffn, opts->src_grid, opts->seed, cache, workspace, workspace_bytes, stream);
     if (st != BVC_OK) return st;
   }
   return bvc_cache_pack(cache, stream);
@@ -752,14 +759,20 @@ static bvc_status cache_build(bvc_geometry g, const bvc_function* gfn, const flo
 extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
                                       const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
                                       size_t workspace_bytes, bvc_stream stream) {
-  return cache_build(g, gfn, nullptr, ffn, opts, cache, workspace, workspace_bytes, stream);
+  return cache_build(g, g, gfn, nullptr, ffn, opts, cache, workspace, workspace_bytes, stream);
+}
+
+extern "C" bvc_status bvc_cache_build_region(bvc_geometry domain, bvc_geometry region, const bvc_function* gfn,
+                                             const bvc_function* ffn, const bvc_cache_opts* opts, bvc_cache* cache,
+                                             void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return cache_build(domain, region, gfn, nullptr, ffn, opts, cache, workspace, workspace_bytes, stream);
 }
 
 extern "C" bvc_status bvc_cache_build_vg(bvc_geometry g, const float* g_vertex, const bvc_function* ffn,
                                          const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
                                          size_t workspace_bytes, bvc_stream stream) {
   if (g_vertex == nullptr) return BVC_ERR_INVALID_ARG;
-  return cache_build(g, nullptr, g_vertex, ffn, opts, cache, workspace, workspace_bytes, stream);
+  return cache_build(g, g, nullptr, g_vertex, ffn, opts, cache, workspace, workspace_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -992,6 +1005,44 @@ extern "C" bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, co
   if (best_ms) *best_ms = best;
   return BVC_OK;
 }
+
+namespace bvc {
+bvc_status walk_points_u(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, double sigma,
+                         const float* starts, int64_t pt_stride, int64_t i0, int64_t c, int32_t W, float eps,
+                         int32_t max_steps, uint64_t seed, uint32_t tag, uint64_t wid0, void* ws, size_t ws_bytes,
+                         cudaStream_t s) {
+  const int D = g->dim;
+  if (!valid_walk_args(eps, max_steps, W) || !(sigma >= 0.0)) return BVC_ERR_INVALID_ARG;
+  if (ws_chunk(ws_bytes, ws_per_start(D, W, D)) < c) return BVC_ERR_WORKSPACE;
+  WalkParams P{};
+  P.G = g->dev;
+  P.chunk = g->tune_chunk;
+  P.blocks_per_sm = g->tune_blocks_per_sm;
+  if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
+  if (sigma > 0.0 && P.f.n_terms > 0) return BVC_ERR_UNSUPPORTED;
+  P.starts = starts;
+  P.nrm = nullptr;
+  P.pt_stride = pt_stride;
+  P.W = W;
+  P.eps = eps;
+  P.max_steps = max_steps;
+  P.seed = seed;
+  P.tag = tag;
+  P.sqs = (float)std::sqrt(sigma);
+  P.counter = (unsigned long long*)ws;
+  P.i0 = i0;
+  P.total = c * (int64_t)W;
+  P.wid0 = wid0;
+  float* fh = ws_first(ws);
+  P.rec = ws_records(ws, c, D);
+  P.first = fh;
+  bvc_status st = launch_first_hits(D, g->dev, starts, pt_stride, i0, c, fh, s);
+  if (st != BVC_OK) return st;
+  return launch_walk(D, P.f.n_terms > 0, kRecGrad, false, P, s);
+}
+
+const float* walk_records_u(void* ws, int64_t c, int dim) { return ws_records(ws, c, dim); }
+}  // namespace bvc
 
 extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
                                                   size_t* full_bytes) {
