@@ -252,6 +252,10 @@ typedef struct {
                                functions of App. A.  0 = Poisson. */
   double clamp_c;           /* > 0: the gather clamps dG/dn in the u term to [-c, c] (Sec. 3.3,
                                Eq. 8-9); bvc_clamp_correction estimates the remainder.  0 = none. */
+  int32_t reuse_sources;    /* != 0: cache->src_y and n_src_dev already hold the kept source
+                               candidates of this geometry, grid and seed (an earlier build); only
+                               their weights f(y) |box| are recomputed -- the same values a full
+                               build gives, without the inside tests. */
 } bvc_cache_opts;
 
 /* The whole cache: K1 -> K2 (chunked through the workspace) -> K3 -> K4 -> pack.

@@ -61,7 +61,7 @@ class CacheOpts(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("walks_per_sample", C.c_int32), ("max_steps", C.c_int32),
                 ("offset_l", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64),
                 ("walk_id_base", C.c_uint64), ("src_grid", C.c_int32 * 3), ("sigma", C.c_double),
-                ("clamp_c", C.c_double)]
+                ("clamp_c", C.c_double), ("reuse_sources", C.c_int32)]
 
 
 class MultiCacheStruct(C.Structure):
@@ -619,7 +619,16 @@ class DiffSolver:
     def _forward(self, g_vertex, amps):
         cache = Cache(self.dim, self.opts.n_samples, n_src_cand=self.n_src)
         f = self._f_terms(amps.detach().cpu().numpy() if amps is not None else [])
+        # the kept source candidates depend on the geometry, grid and seed
+        # only: classify them once and re-weight them on later solves
+        if self.n_src and getattr(self, "_src", None) is not None:
+            cache.src_y.copy_(self._src[0])
+            cache.n_src_dev.copy_(self._src[1])
+            self.opts.reuse_sources = 1
         cache_build_vg(self.geom, g_vertex.detach().float().contiguous(), f, self.opts, cache, self.ws)
+        self.opts.reuse_sources = 0
+        if self.n_src and getattr(self, "_src", None) is None:
+            self._src = (cache.src_y.clone(), cache.n_src_dev.clone())
         st = EvalState(self.pts, grad=False)
         evaluate(cache, st)
         self._u, _ = get_solution(st)

@@ -845,14 +845,26 @@ constexpr int kMStride = 8 + 2 * kMG;  // floats per packed sample row
 // block x belongs to the mesh whose gather blocks hold it; its points lie in
 // that mesh's range of the [D][m] point planes and its samples in that
 // mesh's range of the n sample rows of each group.
+//
+// 128 threads, two points each (a block covers 256 points): every sample's
+// 32 coefficient pairs, broadcast from shared memory, feed both points, which
+// halves the shared-memory reads per FMA.  The 64 FP32 partial sums of a
+// thread live in registers; the FP64 running sums in shared memory
+// (dynamic, kMSum64 bytes), column per thread.
+constexpr int kMThreads = 128;
+constexpr int kMSum64 = 2 * kMG * kMThreads * 8;
+
 template <int D>
-__global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict__ x, int64_t m,
-                                                         const float* __restrict__ packed, int64_t n, int32_t K,
-                                                         double* __restrict__ u, const BatchMeshDev* __restrict__ meshes,
-                                                         int32_t count) {
+__global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __restrict__ x, int64_t m,
+                                                               const float* __restrict__ packed, int64_t n, int32_t K,
+                                                               double* __restrict__ u,
+                                                               const BatchMeshDev* __restrict__ meshes,
+                                                               int32_t count) {
   __shared__ __align__(128) float tile[2][kMTile * kMStride];
   __shared__ __align__(8) uint64_t bar[2];
+  extern __shared__ double s64[];  // [2 * kMG][kMThreads]
   const int g = blockIdx.y;
+  const int tid = threadIdx.x;
   int64_t blk = blockIdx.x, pt_off = 0, n_pts = m, smp_off = 0, n_smp = n;
   if (meshes != nullptr) {
     int lo = 0, hi = count - 1;  // the last mesh whose first block is <= blockIdx.x
@@ -871,23 +883,24 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
     n_smp = M.n_smp;
   }
   const float* base = packed + ((int64_t)g * n + smp_off) * kMStride;
-  const int64_t pl = blk * blockDim.x + threadIdx.x;  // point within the mesh
-  const int64_t p = pt_off + pl;
-  float pc[3];
+  const int64_t pl0 = blk * (2 * kMThreads) + tid, pl1 = pl0 + kMThreads;  // points within the mesh
+  float pa[3], pb[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) pc[a] = (a < D && pl < n_pts) ? x[a * m + p] : 1.0e4f + (float)a;
-  float acc[kMG];
-  double acc64[kMG];
+  for (int a = 0; a < 3; ++a) {
+    pa[a] = (a < D && pl0 < n_pts) ? x[a * m + pt_off + pl0] : 1.0e4f + (float)a;
+    pb[a] = (a < D && pl1 < n_pts) ? x[a * m + pt_off + pl1] : 1.0e4f + (float)a;
+  }
+  float acc0[kMG], acc1[kMG];
 #pragma unroll
-  for (int q = 0; q < kMG; ++q) acc64[q] = 0.0;
+  for (int q = 0; q < 2 * kMG; ++q) s64[q * kMThreads + tid] = 0.0;
   const int64_t nt = (n_smp + kMTile - 1) / kMTile;
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     for (int b = 0; b < 2 && b < nt; ++b) {
       const int64_t st = (int64_t)b * kMTile;
       const uint32_t bytes = (uint32_t)min64(kMTile, n_smp - st) * kMStride * 4u;
@@ -899,7 +912,7 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
     const int b = (int)(it & 1);
     const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1));
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
+      if (tid == 0) {
         atomicOr(&g_gather_status, 1ull);
         for (int64_t k2 = it; k2 < it + 2 && k2 < nt; ++k2)
           (void)mbar_wait_bounded(&bar[k2 & 1], (uint32_t)((k2 >> 1) & 1));
@@ -909,40 +922,61 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
     const int cnt = (int)min64(kMTile, n_smp - it * kMTile);
     if (it % kMFlush == 0) {
 #pragma unroll
-      for (int q = 0; q < kMG; ++q) acc[q] = 0.0f;
+      for (int q = 0; q < kMG; ++q) acc0[q] = acc1[q] = 0.0f;
     }
     const float4* T = reinterpret_cast<const float4*>(tile[b]);
     for (int s = 0; s < cnt; ++s) {
       const float4* row = T + s * (kMStride / 4);
       const float4 zz = row[0], nn = row[1];
-      const float dx = zz.x - pc[0], dy = zz.y - pc[1], dz = zz.z - pc[2];
-      float k1, k2;
-      if (D == 2) {
-        const float r2 = fmaf(dy, dy, dx * dx);
-        const float inv = rcp_approx(r2);
-        k1 = fmaf(nn.y, dy, nn.x * dx) * inv;
-        k2 = lg2_approx(r2);
-      } else {
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float ir = rsqrt_approx(r2);
-        k1 = fmaf(nn.z, dz, fmaf(nn.y, dy, nn.x * dx)) * (ir * ir * ir);
-        k2 = ir;
+      float ka1, ka2, kb1, kb2;
+      {
+        const float dx = zz.x - pa[0], dy = zz.y - pa[1], dz = zz.z - pa[2];
+        if (D == 2) {
+          const float r2 = fmaf(dy, dy, dx * dx);
+          ka1 = fmaf(nn.y, dy, nn.x * dx) * rcp_approx(r2);
+          ka2 = lg2_approx(r2);
+        } else {
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          const float ir = rsqrt_approx(r2);
+          ka1 = fmaf(nn.z, dz, fmaf(nn.y, dy, nn.x * dx)) * (ir * ir * ir);
+          ka2 = ir;
+        }
+      }
+      {
+        const float dx = zz.x - pb[0], dy = zz.y - pb[1], dz = zz.z - pb[2];
+        if (D == 2) {
+          const float r2 = fmaf(dy, dy, dx * dx);
+          kb1 = fmaf(nn.y, dy, nn.x * dx) * rcp_approx(r2);
+          kb2 = lg2_approx(r2);
+        } else {
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          const float ir = rsqrt_approx(r2);
+          kb1 = fmaf(nn.z, dz, fmaf(nn.y, dy, nn.x * dx)) * (ir * ir * ir);
+          kb2 = ir;
+        }
       }
 #pragma unroll
       for (int q = 0; q < kMG / 4; ++q) {
         const float4 a4 = row[2 + q], b4 = row[2 + kMG / 4 + q];
-        acc[4 * q + 0] = fmaf(b4.x, k2, fmaf(a4.x, k1, acc[4 * q + 0]));
-        acc[4 * q + 1] = fmaf(b4.y, k2, fmaf(a4.y, k1, acc[4 * q + 1]));
-        acc[4 * q + 2] = fmaf(b4.z, k2, fmaf(a4.z, k1, acc[4 * q + 2]));
-        acc[4 * q + 3] = fmaf(b4.w, k2, fmaf(a4.w, k1, acc[4 * q + 3]));
+        acc0[4 * q + 0] = fmaf(b4.x, ka2, fmaf(a4.x, ka1, acc0[4 * q + 0]));
+        acc0[4 * q + 1] = fmaf(b4.y, ka2, fmaf(a4.y, ka1, acc0[4 * q + 1]));
+        acc0[4 * q + 2] = fmaf(b4.z, ka2, fmaf(a4.z, ka1, acc0[4 * q + 2]));
+        acc0[4 * q + 3] = fmaf(b4.w, ka2, fmaf(a4.w, ka1, acc0[4 * q + 3]));
+        acc1[4 * q + 0] = fmaf(b4.x, kb2, fmaf(a4.x, kb1, acc1[4 * q + 0]));
+        acc1[4 * q + 1] = fmaf(b4.y, kb2, fmaf(a4.y, kb1, acc1[4 * q + 1]));
+        acc1[4 * q + 2] = fmaf(b4.z, kb2, fmaf(a4.z, kb1, acc1[4 * q + 2]));
+        acc1[4 * q + 3] = fmaf(b4.w, kb2, fmaf(a4.w, kb1, acc1[4 * q + 3]));
       }
     }
     if (it % kMFlush == kMFlush - 1 || it == nt - 1) {
 #pragma unroll
-      for (int q = 0; q < kMG; ++q) acc64[q] += (double)acc[q];
+      for (int q = 0; q < kMG; ++q) {
+        s64[q * kMThreads + tid] += (double)acc0[q];
+        s64[(kMG + q) * kMThreads + tid] += (double)acc1[q];
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && it + 2 < nt) {
+    if (tid == 0 && it + 2 < nt) {
       fence_proxy_async();
       const int64_t st = (it + 2) * kMTile;
       const uint32_t bytes = (uint32_t)min64(kMTile, n_smp - st) * kMStride * 4u;
@@ -950,13 +984,28 @@ __global__ void __launch_bounds__(256, 2) k_gather_multi(const float* __restrict
       bulk_g2s(&tile[b][0], base + st * kMStride, bytes, &bar[b]);
     }
   }
-  if (pl < n_pts) {
-    const int kk = (K - g * kMG) < kMG ? (K - g * kMG) : kMG;
-    const double inv_n = 1.0 / (double)n_smp;
-#pragma unroll
-    for (int q = 0; q < kMG; ++q)
-      if (q < kk) u[(int64_t)(g * kMG + q) * m + p] = acc64[q] * inv_n;
+  const int kk = (K - g * kMG) < kMG ? (K - g * kMG) : kMG;
+  const double inv_n = 1.0 / (double)n_smp;
+  for (int h = 0; h < 2; ++h) {
+    const int64_t pl = h ? pl1 : pl0;
+    if (pl >= n_pts) continue;
+    for (int q = 0; q < kk; ++q) u[(int64_t)(g * kMG + q) * m + pt_off + pl] = s64[(h * kMG + q) * kMThreads + tid] * inv_n;
   }
+}
+
+// The dynamic shared memory of k_gather_multi exceeds the default 48 KB.
+template <int D>
+static bvc_status multi_gather_attr() {
+  static bool done = false;
+  if (!done) {
+    if (cudaFuncSetAttribute((const void*)k_gather_multi<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMSum64) !=
+        cudaSuccess) {
+      (void)cudaGetLastError();
+      return BVC_ERR_CUDA;
+    }
+    done = true;
+  }
+  return BVC_OK;
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -1097,10 +1146,12 @@ extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const flo
   const dim3 grid((unsigned)((m + 255) / 256), (unsigned)groups);
   cudaStream_t s = (cudaStream_t)stream;
   ProfScope ps("gather_multi", s);
+  const bvc_status at = cache->dim == 2 ? multi_gather_attr<2>() : multi_gather_attr<3>();
+  if (at != BVC_OK) return at;
   if (cache->dim == 2)
-    k_gather_multi<2><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
+    k_gather_multi<2><<<grid, kMThreads, kMSum64, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
   else
-    k_gather_multi<3><<<grid, 256, 0, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
+    k_gather_multi<3><<<grid, kMThreads, kMSum64, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -1116,12 +1167,14 @@ extern "C" bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cac
   const dim3 grid((unsigned)b->blocks_total, (unsigned)groups);
   cudaStream_t s = (cudaStream_t)stream;
   ProfScope ps("gather_multi", s);
+  const bvc_status at = b->dim == 2 ? multi_gather_attr<2>() : multi_gather_attr<3>();
+  if (at != BVC_OK) return at;
   if (b->dim == 2)
-    k_gather_multi<2><<<grid, 256, 0, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u, b->table,
-                                           b->count);
+    k_gather_multi<2><<<grid, kMThreads, kMSum64, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u,
+                                                       b->table, b->count);
   else
-    k_gather_multi<3><<<grid, 256, 0, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u, b->table,
-                                           b->count);
+    k_gather_multi<3><<<grid, kMThreads, kMSum64, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u,
+                                                       b->table, b->count);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }

@@ -101,6 +101,8 @@ bvc_status walk_points_u(bvc_geometry g, const bvc_function* gfn, const bvc_func
                          int32_t max_steps, uint64_t seed, uint32_t tag, uint64_t wid0, void* ws, size_t ws_bytes,
                          cudaStream_t s);
 const float* walk_records_u(void* ws, int64_t c, int dim);
+// Weights f(y)|box| of the kept source samples already in the cache.
+bvc_status bvc_source_reweight(bvc_geometry g, const bvc_function* ffn, bvc_cache* cache, cudaStream_t s);
 // dL/dA of the source cache's bump amplitudes from dL/dc of its samples.
 bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache* cache, const double* adj,
                               double* grad_amp, cudaStream_t s);

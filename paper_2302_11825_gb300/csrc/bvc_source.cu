@@ -256,11 +256,45 @@ __global__ void __launch_bounds__(256) k_src_adjoint(DevFunction f, const float*
   }
 }
 
+// Weights of already-kept candidates: c_j = f(y_j) |box| (as k_src_scatter).
+template <int D>
+__global__ void __launch_bounds__(256) k_src_reweight(DevFunction f, const float* __restrict__ src_y, int64_t ncand,
+                                                     const int64_t* __restrict__ n_src, double box,
+                                                     double* __restrict__ src_c) {
+  const int64_t nk = *n_src;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x) {
+    float y[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) y[a] = src_y[a * ncand + j];
+    src_c[j] = (double)eval_fn<D>(f, y) * box;
+  }
+}
+
 }  // namespace bvc
 
 using namespace bvc;
 
 namespace bvc {
+bvc_status bvc_source_reweight(bvc_geometry g, const bvc_function* ffn, bvc_cache* cache, cudaStream_t s) {
+  DevFunction f;
+  if (!make_dev_function(ffn, g->dim, &f)) return BVC_ERR_INVALID_ARG;
+  double box = 1.0;
+  for (int a = 0; a < g->dim; ++a) box *= (double)g->hi[a] - (double)g->lo[a];
+  int64_t blocks = (cache->n_src_cand + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  ProfScope ps("source_reweight", s);
+  if (g->dim == 2)
+    k_src_reweight<2><<<(unsigned)blocks, 256, 0, s>>>(f, cache->src_y, cache->n_src_cand, cache->n_src_dev, box,
+                                                       cache->src_c);
+  else
+    k_src_reweight<3><<<(unsigned)blocks, 256, 0, s>>>(f, cache->src_y, cache->n_src_cand, cache->n_src_dev, box,
+                                                       cache->src_c);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
 bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache* cache, const double* adj,
                               double* grad_amp, cudaStream_t s) {
   DevFunction f;

@@ -750,7 +750,9 @@ static bvc_status cache_build(bvc_geometry g, bvc_geometry gs, const bvc_functio
     if (st != BVC_OK) return st;
   }
   if (ncand > 0) {
-    st = bvc_sample_source(gs, ffn, opts->src_grid, opts->seed, cache, workspace, workspace_bytes, stream);
+    st = opts->reuse_sources ? bvc_source_reweight(gs, ffn, cache, s)
+                             : bvc_sample_source(gs, ffn, opts->src_grid, opts->seed, cache, workspace, workspace_bytes,
+                                                 stream);
     if (st != BVC_OK) return st;
   }
   return bvc_cache_pack(cache, stream);

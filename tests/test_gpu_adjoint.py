@@ -135,3 +135,21 @@ def test_adjoint_rejects_non_bump_sources():
     ga = torch.zeros(8, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
         bvc.cache_adjoint(geom, [(wl.POLY, [1.0])], opts, cache, z, z, None, gg, ga)
+
+
+def test_source_reuse_equals_fresh_build():
+    w = wl.star_poisson(n_samples=512, walks=4, grid=16, n_seg=2000, src_grid=(40, 40))
+    geom = bvc.Geometry(w.V, w.F)
+    opts = bvc.cache_opts(512, 4, w.offset_l, w.eps, 3, src_grid=(40, 40))
+    a = bvc.cache_build(geom, w.g, w.f, opts, bvc.Cache(2, 512, n_src_cand=1600))
+    f2 = [(wl.GAUSS, [0.08, 2.0, 0.1, 0.2, -1.0, -0.3, 0.1])]
+    fresh = bvc.cache_build(geom, w.g, f2, opts, bvc.Cache(2, 512, n_src_cand=1600))
+    reuse = bvc.Cache(2, 512, n_src_cand=1600)
+    reuse.src_y.copy_(a.src_y)
+    reuse.n_src_dev.copy_(a.n_src_dev)
+    opts.reuse_sources = 1
+    bvc.cache_build(geom, w.g, f2, opts, reuse)
+    torch.cuda.synchronize()
+    k = int(fresh.n_src_dev.item())
+    assert torch.equal(reuse.src_c[:k], fresh.src_c[:k]) and torch.equal(reuse.src_packed, fresh.src_packed)
+    assert torch.equal(reuse.u_hat, fresh.u_hat)
