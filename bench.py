@@ -165,10 +165,23 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def kernel_source_hash() -> str:
+# The source files that define each profiled kernel (its code, the device
+# helpers it inlines, and the data layout it reads).
+KERNEL_FILES = {
+    "walk": ["bvc_walk.cu", "bvc_device.cuh", "bvc_internal.h", "bvh_build.cpp"],
+    "gather_boundary": ["bvc_gather.cu", "bvc_device.cuh", "bvc_internal.h"],
+    "gather_source": ["bvc_gather.cu", "bvc_device.cuh", "bvc_internal.h"],
+    "gather_multi": ["bvc_gather.cu", "bvc_device.cuh", "bvc_internal.h", "bvc_walk.cu"],
+    "source_classify": ["bvc_source.cu", "bvc_device.cuh", "bvc_internal.h"],
+}
+
+
+def kernel_source_hash(kernel: str = None) -> str:
+    """SHA-256 prefix of the sources of one kernel (all of csrc/ if unknown)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_11825_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    files = KERNEL_FILES.get(kernel) or sorted(os.listdir(csrc))
+    for f in files:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -184,7 +197,7 @@ def profile_traffic(kernel: str, workload: str):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != kernel_source_hash():
+    if vals.get("kernel_source_hash") != kernel_source_hash(kernel):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_size"])

@@ -158,3 +158,21 @@ def test_batch_host_checks(lib):
         if name == "bvc_batch_build":
             args = [None, None, None, None, None, C.c_size_t(0), None]
         assert fn(*args) == 1, name
+
+
+def test_region_clamp_screened_host_checks(lib):
+    lib.bvc_cache_build_region.restype = C.c_int
+    assert lib.bvc_cache_build_region(None, None, None, None, None, None, None, C.c_size_t(0), None) == 1
+    lib.bvc_clamp_correction_workspace_size.restype = C.c_int
+    b = C.c_size_t()
+    assert lib.bvc_clamp_correction_workspace_size(2, C.c_int64(100), 4, 8, C.byref(b)) == 0 and b.value > 0
+    assert lib.bvc_clamp_correction_workspace_size(4, C.c_int64(100), 4, 8, C.byref(b)) == 1
+    lib.bvc_clamp_correction.restype = C.c_int
+    assert lib.bvc_clamp_correction(None, None, C.c_double(0.0), None, None, C.c_double(0.0), C.c_double(1.0), None,
+                                    C.c_int64(0), 1, 1, C.c_float(1e-3), 10, C.c_uint64(0), None, None, None,
+                                    C.c_size_t(0), None) == 1
+    lib.wos_estimate_sigma.restype = C.c_int
+    assert lib.wos_estimate_sigma(None, None, None, C.c_double(1.0), None, 1, C.c_float(1e-3), 10, C.c_uint64(0),
+                                  C.c_uint64(0), None, C.c_size_t(0), None) == 1
+    lib.bvc_tune_walks_workspace_size.restype = C.c_int
+    assert lib.bvc_tune_walks_workspace_size(None, None, None) == 1
