@@ -120,6 +120,13 @@ __global__ void __launch_bounds__(1024) k_src_scan(const SrcParams S) {
 // the slices in a fixed order.
 constexpr int kTriTile = 256;
 constexpr int kMaxSlices = 16;
+
+// Approximate reciprocal (MUFU.RCP): the factors are only rescaled by it.
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __global__ void __launch_bounds__(kSrcBlock) k_src_classify3d(const SrcParams S) {
   __shared__ float4 tri[3][kTriTile];
   const int64_t c = blockIdx.x * (int64_t)kSrcBlock + threadIdx.x;
@@ -150,39 +157,39 @@ __global__ void __launch_bounds__(kSrcBlock) k_src_classify3d(const SrcParams S)
     }
     __syncthreads();
     const int cnt = (int)min64(kTriTile, np - base);
-    for (int q = 0; q < cnt; ++q) {
-      const float4 ta = tri[0][q], tb = tri[1][q], tc = tri[2][q];
-      const float ax = ta.x - p[0], ay = ta.y - p[1], az = ta.z - p[2];
-      const float bx = tb.x - p[0], by = tb.y - p[1], bz = tb.z - p[2];
-      const float cx = tc.x - p[0], cy = tc.y - p[1], cz = tc.z - p[2];
-      const float a2 = fmaf(az, az, fmaf(ay, ay, ax * ax));
-      const float b2 = fmaf(bz, bz, fmaf(by, by, bx * bx));
-      const float c2 = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
-      const float la = a2 * rsqrtf(a2), lb = b2 * rsqrtf(b2), lc = c2 * rsqrtf(c2);
-      const float num = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
-      const float ab = fmaf(az, bz, fmaf(ay, by, ax * bx)), ac = fmaf(az, cz, fmaf(ay, cy, ax * cx));
-      const float bc = fmaf(bz, cz, fmaf(by, cy, bx * cx));
-      const float den = fmaf(bc, la, fmaf(ac, lb, fmaf(ab, lc, la * lb * lc)));
-      const float m = fmaxf(fabsf(num), fabsf(den));
-      if (!(m > 0.0f) || !(m < 3.0e38f)) continue;  // degenerate (the point on the triangle's edges)
-      const float sc = __frcp_rn(m);
-      const float wr = den * sc, wi = num * sc;
-      const float nr = fmaf(zr, wr, -zi * wi), ni = fmaf(zr, wi, zi * wr);
-      crossings += (zi >= 0.0f && ni < 0.0f && num > 0.0f) ? 1 : 0;
-      crossings -= (zi < 0.0f && ni >= 0.0f && num < 0.0f) ? 1 : 0;
-      // |w| is in [1, sqrt 2]: renormalise the product every 16 factors
-      if ((q & 15) == 15) {
-        const float t = rsqrtf(fmaf(ni, ni, nr * nr));
-        zr = nr * t;
-        zi = ni * t;
-      } else {
+    // blocks of 16 triangles, the product renormalised after each block
+    // (|factor| lies in [1, sqrt 2]); a degenerate factor (the point on a
+    // triangle's edge) is replaced by 1
+    for (int q0 = 0; q0 < cnt; q0 += 16) {
+#pragma unroll 4
+      for (int q = q0; q < q0 + 16; ++q) {
+        if (q >= cnt) break;
+        const float4 ta = tri[0][q], tb = tri[1][q], tc = tri[2][q];
+        const float ax = ta.x - p[0], ay = ta.y - p[1], az = ta.z - p[2];
+        const float bx = tb.x - p[0], by = tb.y - p[1], bz = tb.z - p[2];
+        const float cx = tc.x - p[0], cy = tc.y - p[1], cz = tc.z - p[2];
+        const float a2 = fmaf(az, az, fmaf(ay, ay, ax * ax));
+        const float b2 = fmaf(bz, bz, fmaf(by, by, bx * bx));
+        const float c2 = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
+        const float la = a2 * rsqrtf(a2), lb = b2 * rsqrtf(b2), lc = c2 * rsqrtf(c2);
+        const float num = fmaf(az, fmaf(bx, cy, -by * cx), fmaf(ay, fmaf(bz, cx, -bx * cz), ax * fmaf(by, cz, -bz * cy)));
+        const float ab = fmaf(az, bz, fmaf(ay, by, ax * bx)), ac = fmaf(az, cz, fmaf(ay, cy, ax * cx));
+        const float bc = fmaf(bz, cz, fmaf(by, cy, bx * cx));
+        const float den = fmaf(bc, la, fmaf(ac, lb, fmaf(ab, lc, la * lb * lc)));
+        const float mm = fmaxf(fabsf(num), fabsf(den));
+        const bool ok = mm > 0.0f && mm < 3.0e38f;
+        const float sc = ok ? rcp_fast(mm) : 0.0f;
+        const float wr = ok ? den * sc : 1.0f, wi = num * sc;
+        const float nr = fmaf(zr, wr, -zi * wi), ni = fmaf(zr, wi, zi * wr);
+        crossings += (zi >= 0.0f && ni < 0.0f && num > 0.0f) ? 1 : 0;
+        crossings -= (zi < 0.0f && ni >= 0.0f && num < 0.0f) ? 1 : 0;
         zr = nr;
         zi = ni;
       }
+      const float t = rsqrtf(fmaf(zi, zi, zr * zr));
+      zr *= t;
+      zi *= t;
     }
-    const float t = rsqrtf(fmaf(zi, zi, zr * zr));
-    zr *= t;
-    zi *= t;
   }
   // this slice's sum of theta = 2 pi crossings + arg(product)
   if (c < S.ncand) S.theta[(int64_t)slice * S.ncand + c] = 6.28318530717958648f * (float)crossings + atan2f(zi, zr);
