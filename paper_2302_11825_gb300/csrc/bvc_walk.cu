@@ -34,6 +34,10 @@ namespace bvc {
 #ifndef BVC_WALK_POLICY
 #define BVC_WALK_POLICY 0
 #endif
+// Warm-started closest-point queries (previous closest element first).
+#ifndef BVC_WALK_WARM
+#define BVC_WALK_WARM 1
+#endif
 constexpr int kWalkBlock = 128;
 constexpr int kStack = 24;  // the BVH builder bounds the depth by 24
 constexpr int64_t kChunk = 128;  // default walks per warp refill
@@ -177,7 +181,12 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
   for (int a = 0; a < D; ++a) h.df[a] = 0.0f;
   unsigned long long my_steps = 0, my_capped = 0, my_nodes = 0, my_prims = 0;
 
+  // A new query starts at the root; when the walk's previous closest element
+  // is known it is tested first at the new position, so the traversal
+  // starts with its distance as the pruning bound (the answer -- the
+  // smallest distance, ties to the lowest id -- does not depend on it).
   auto begin_query = [&]() {
+    const int32_t qp = h.q;
     phase = kQuery;
     cur = root;
     sp = 0;
@@ -185,6 +194,25 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
     h.d2 = kInf;
     h.id = 0x7fffffff;
     h.q = -1;
+    if (BVC_WALK_WARM && qp >= 0) {
+      float d2;
+      if (D == 2) {
+        const float4 S = __ldg(&G.prims[2 * qp]), T = __ldg(&G.prims[2 * qp + 1]);
+        d2 = seg_d2(S, T.x, x[0], x[D - 1]);
+        h.id = __float_as_int(T.y);
+      } else {
+        const float4 A = __ldg(&G.prims[3 * qp]), B = __ldg(&G.prims[3 * qp + 1]), Cq = __ldg(&G.prims[3 * qp + 2]);
+        float df[3];
+        d2 = tri_closest(A, B, Cq, x, df);
+#pragma unroll
+        for (int a = 0; a < D; ++a) h.df[a] = df[D == 3 ? a : 0];
+        h.id = __float_as_int(A.w);
+      }
+      h.d2 = d2;
+      h.q = qp;
+      const float sr = sqrtf(d2) + G.tau;
+      thr = sr * sr;
+    }
   };
   // Next stacked item still within reach, else the query is complete.
   auto pop = [&]() {
@@ -242,6 +270,7 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
           h.q = -1;  // closest-point vector already final
           phase = kStep;
         } else {
+          h.q = -1;  // no previous element for a new walk
           begin_query();
         }
       }
