@@ -92,6 +92,15 @@ def _load():
                 "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
                 "orc_sphere_step": (None, [C.c_int, f64, f64, f64, f64, P, P, P, P]),
                 "orc_num_threads": (C.c_int, []),
+                "orc_sample_boundary_mixed": (None, [C.c_int, P, P, i64, i64, f64, u64, P, P, P, P]),
+                "orc_fn_grad": (None, [P, C.c_int, P, P]),
+                "orc_neumann_eval": (f64, [P, P, C.c_int, P, P]),
+                "orc_wost_create": (P, [C.c_int, P, i64, P, i64, P]),
+                "orc_wost_free": (None, [P]),
+                "orc_wost_counts": (i64, [P, P]),
+                "orc_wost_walks": (None, [P, P, P, P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P]),
+                "orc_wost_query": (None, [P, P, i64, P, P]),
+                "orc_wost_rays": (None, [P, P, P, P, i64, f64, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -412,3 +421,94 @@ def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs:
     if want_abs:
         return ub, us, gb, gs, ab
     return ub, us, gb, gs
+
+
+# ---------------------------------------------------------------- mixed boundaries
+def sample_boundary_mixed(V, F, N: int, l: float, seed: int, neumann):
+    """Sec. 3.2 for a mixed boundary: samples on Dirichlet elements moved by
+    -l n, samples on Neumann elements left on the boundary."""
+    lib = _load()
+    V, F = _f32(V), _i32(F)
+    dim = V.shape[1]
+    nf = np.ascontiguousarray(neumann, dtype=np.uint8)
+    z, n, e = np.zeros((N, dim)), np.zeros((N, dim)), np.zeros(N, np.int32)
+    lib.orc_sample_boundary_mixed(dim, _p(V), _p(F), F.shape[0], N, float(l), int(seed), _p(nf), _p(z), _p(n), _p(e))
+    return z, n, e
+
+
+def fn_grad(terms, dim: int, x) -> np.ndarray:
+    """Gradient of a problem function at points x[n, dim]."""
+    lib = _load()
+    spec = encode_function(terms)
+    x = _f64(np.atleast_2d(x))
+    out = np.zeros((x.shape[0], dim))
+    for i in range(x.shape[0]):
+        lib.orc_fn_grad(_p(spec), dim, _p(x[i]), _p(out[i]))
+    return out
+
+
+def neumann_eval(h_value, h_potential, dim: int, z, n) -> np.ndarray:
+    """Neumann data h(z) = h_value(z) + n . grad h_potential(z)."""
+    lib = _load()
+    hv, hp = encode_function(h_value), encode_function(h_potential)
+    z, n = _f64(np.atleast_2d(z)), _f64(np.atleast_2d(n))
+    return np.array([lib.orc_neumann_eval(_p(hv), _p(hp), dim, _p(z[i]), _p(n[i])) for i in range(z.shape[0])])
+
+
+class Wost:
+    """Walk on stars (Sec. 3.1) on a boundary whose elements are flagged
+    Neumann (1) or Dirichlet (0): the oracle's brute-force silhouette and ray
+    queries and its walks."""
+
+    def __init__(self, V, F, neumann):
+        self._lib = _load()
+        self.V, self.F = _f32(V), _i32(F)
+        self.dim = self.V.shape[1]
+        self.neumann = np.ascontiguousarray(neumann, dtype=np.uint8)
+        self.h = self._lib.orc_wost_create(self.dim, _p(self.V), self.V.shape[0], _p(self.F), self.F.shape[0],
+                                           _p(self.neumann))
+
+    def counts(self):
+        """(Dirichlet elements, Neumann elements, silhouette candidates)."""
+        out = np.zeros(3, np.int64)
+        self._lib.orc_wost_counts(self.h, _p(out))
+        return tuple(int(v) for v in out)
+
+    def query(self, pts):
+        """Distances to the Dirichlet part and to the closest silhouette."""
+        pts = _f64(pts)
+        n = pts.shape[0]
+        dd, ds = np.zeros(n), np.zeros(n)
+        self._lib.orc_wost_query(self.h, _p(pts), n, _p(dd), _p(ds))
+        return dd, ds
+
+    def rays(self, org, dirs, tmax: float, skip=None):
+        """First crossing (t, element) of each ray with the Neumann part."""
+        org, dirs = _f64(org), _f64(dirs)
+        n = org.shape[0]
+        sk = None if skip is None else _i32(skip)
+        t, e = np.zeros(n), np.zeros(n, np.int32)
+        self._lib.orc_wost_rays(self.h, _p(org), _p(dirs), _p(sk), n, float(tmax), _p(t), _p(e))
+        return t, e
+
+    def walks(self, g_terms, h_value, h_potential, f_terms, starts, start_elem, W: int, eps: float,
+              max_steps: int, seed: int, id_base: int = 0, tag: int = TAG_WALK):
+        """W walks from each FP32 start; start_elem[i] >= 0 puts start i on
+        that Neumann element.  Returns per-walk U, grad[.., dim], steps and
+        the Dirichlet element of the end."""
+        starts = _f32(starts)
+        n, dim = starts.shape
+        T = n * W
+        U, grad = np.zeros(T), np.zeros((T, dim))
+        steps, prim = np.zeros(T, np.int32), np.zeros(T, np.int32)
+        se = None if start_elem is None else _i32(start_elem)
+        g, hv, hp, f = (encode_function(t) for t in (g_terms, h_value, h_potential, f_terms))
+        self._lib.orc_wost_walks(self.h, _p(g), _p(hv), _p(hp), _p(f), _p(starts), _p(se), n, int(W), float(eps),
+                                 int(max_steps), int(seed), int(id_base), int(tag), _p(U), _p(grad), _p(steps),
+                                 _p(prim))
+        return {"U": U, "grad": grad, "steps": steps, "prim": prim}
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._lib.orc_wost_free(self.h)
+            self.h = None

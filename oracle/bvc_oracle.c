@@ -153,6 +153,79 @@ double orc_fn_eval(const double* spec, int dim, const double* x) {
 
 static int fn_is_zero(const double* spec) { return spec == NULL || (int)spec[0] == 0; }
 
+/* Gradient of a problem function, term by term by the rules of calculus     */
+/* (the Neumann data of a mixed problem is given as h = n . grad phi).      */
+static double dpow(double x, int e) { return e == 0 ? 0.0 : e * ipow(x, e - 1); }
+
+void orc_fn_grad(const double* spec, int dim, const double* x, double* grad) {
+  for (int a = 0; a < dim; ++a) grad[a] = 0.0;
+  const int nt = (int)spec[0];
+  const double* p = spec + 1;
+  for (int t = 0; t < nt; ++t) {
+    const int kind = (int)p[0], nc = (int)p[1];
+    const double* c = p + 2;
+    if (kind == 1) {
+      int idx = 0;
+      for (int tt = 0; tt <= 4 && idx < nc; ++tt) {
+        if (dim == 2) {
+          for (int i = tt; i >= 0 && idx < nc; --i, ++idx) {
+            const int j = tt - i;
+            grad[0] += c[idx] * dpow(x[0], i) * ipow(x[1], j);
+            grad[1] += c[idx] * ipow(x[0], i) * dpow(x[1], j);
+          }
+        } else {
+          for (int i = tt; i >= 0 && idx < nc; --i)
+            for (int j = tt - i; j >= 0 && idx < nc; --j, ++idx) {
+              const int k = tt - i - j;
+              grad[0] += c[idx] * dpow(x[0], i) * ipow(x[1], j) * ipow(x[2], k);
+              grad[1] += c[idx] * ipow(x[0], i) * dpow(x[1], j) * ipow(x[2], k);
+              grad[2] += c[idx] * ipow(x[0], i) * ipow(x[1], j) * dpow(x[2], k);
+            }
+        }
+      }
+    } else if (kind == 2 || kind == 3) {
+      /* GAUSS: A e(r2), e = exp(-r2/(2 s^2)), grad = -A e d / s^2 (d = x - c); */
+      /* GAUSS_LAPLACIAN: A q e with q = r2/s^4 - dim/s^2,                       */
+      /* grad = A e d (2/s^4 - q/s^2)                                            */
+      const double sg = c[0];
+      const int per = 1 + dim;
+      for (int k = 0; 1 + (k + 1) * per <= nc; ++k) {
+        const double* b = c + 1 + k * per;
+        double d[3] = {0, 0, 0}, r2 = 0.0;
+        for (int a = 0; a < dim; ++a) {
+          d[a] = x[a] - b[1 + a];
+          r2 += d[a] * d[a];
+        }
+        const double e = exp(-r2 / (2.0 * sg * sg));
+        const double s2 = sg * sg, s4 = s2 * s2;
+        const double fac = kind == 2 ? -b[0] * e / s2 : b[0] * e * (2.0 / s4 - (r2 / s4 - dim / s2) / s2);
+        for (int a = 0; a < dim; ++a) grad[a] += fac * d[a];
+      }
+    } else if (kind == 4 && dim == 3) {
+      const double e = c[0] * exp(c[1] * x[2]);
+      grad[0] += -c[2] * e * sin(c[2] * x[0]) * sin(c[3] * x[1]);
+      grad[1] += c[3] * e * cos(c[2] * x[0]) * cos(c[3] * x[1]);
+      grad[2] += c[1] * e * cos(c[2] * x[0]) * sin(c[3] * x[1]);
+    } else if (kind == 5) {
+      const double e = c[0] * exp(c[1] * x[dim - 1]);
+      grad[0] += -c[2] * e * sin(c[2] * x[0]);
+      grad[dim - 1] += c[1] * e * cos(c[2] * x[0]);
+    }
+    p += 2 + nc;
+  }
+}
+
+/* Neumann data h(z) = hv(z) + n . grad hp(z) (either part may be empty).  */
+double orc_neumann_eval(const double* hv, const double* hp, int dim, const double* z, const double* n) {
+  double v = fn_is_zero(hv) ? 0.0 : orc_fn_eval(hv, dim, z);
+  if (!fn_is_zero(hp)) {
+    double g[3];
+    orc_fn_grad(hp, dim, z, g);
+    for (int a = 0; a < dim; ++a) v += n[a] * g[a];
+  }
+  return v;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Free-space Green's function of the Laplacian and its derivatives, App. A. */
 /* d = y - x, r = |d|.  out = [G, dG/dx (dim), dG/dn_y, d2G/dx dn_y (dim)].  */
@@ -333,6 +406,23 @@ static double seg_closest64(const double* a, const double* b, const double* p, d
 }
 
 static double dot3d(const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; }
+
+/* The same for a segment in 3D (an edge of a triangle mesh). */
+static double seg3_closest64(const double* a, const double* b, const double* p, double* c) {
+  double ab[3], ap[3];
+  for (int k = 0; k < 3; ++k) {
+    ab[k] = b[k] - a[k];
+    ap[k] = p[k] - a[k];
+  }
+  const double num = dot3d(ap, ab), den = dot3d(ab, ab);
+  const double t = num <= 0.0 ? 0.0 : (num >= den ? 1.0 : num / den);
+  double s = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    c[k] = a[k] + t * ab[k];
+    s += (p[k] - c[k]) * (p[k] - c[k]);
+  }
+  return s;
+}
 
 static double tri_closest64(const double* a, const double* b, const double* cc, const double* p, double* c) {
   double ab[3], ac[3], ap[3], bp[3], cp[3];
@@ -779,8 +869,10 @@ double orc_boundary_measure(int dim, const float* V, const int32_t* F, int64_t n
 /* element's CDF interval as the arclength parameter, 3D places the point   */
 /* uniformly on the triangle from (u1,u2) (barycentrics 1-sqrt(u1),         */
 /* sqrt(u1)(1-u2), sqrt(u1)u2).  z = p - l n.                               */
-void orc_sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l, uint64_t seed,
-                         double* z, double* nrm, int32_t* elem) {
+/* With zero_l non-NULL, samples on elements e with zero_l[e] != 0 (the     */
+/* Neumann part of a mixed boundary, Sec. 3.2) stay on the boundary.        */
+static void sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l,
+                            uint64_t seed, const uint8_t* zero_l, double* z, double* nrm, int32_t* elem) {
   double* cdf = (double*)malloc(sizeof(double) * (np + 1));
   double n[3];
   cdf[0] = 0.0;
@@ -820,13 +912,24 @@ void orc_sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, 
         p[a] = v0 + b1 * (v1 - v0) + b2 * (v2 - v0);
       }
     }
+    const double le = (zero_l && zero_l[e]) ? 0.0 : l;
     for (int a = 0; a < dim; ++a) {
-      z[i * dim + a] = p[a] - l * n[a];
+      z[i * dim + a] = p[a] - le * n[a];
       nrm[i * dim + a] = n[a];
     }
     elem[i] = (int32_t)e;
   }
   free(cdf);
+}
+
+void orc_sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l, uint64_t seed,
+                         double* z, double* nrm, int32_t* elem) {
+  sample_boundary(dim, V, F, np, N, l, seed, NULL, z, nrm, elem);
+}
+
+void orc_sample_boundary_mixed(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l,
+                               uint64_t seed, const uint8_t* neumann, double* z, double* nrm, int32_t* elem) {
+  sample_boundary(dim, V, F, np, N, l, seed, neumann, z, nrm, elem);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1399,4 +1502,545 @@ int orc_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Walk on stars (Sec. 3.1; Fig. "WoS vs WoSt") for a mixed boundary:       */
+/* Laplace(u) = f in Omega, u = g on the Dirichlet part, du/dn = h on the   */
+/* Neumann part (Eq. 1 with sigma = 0).                                     */
+/*                                                                          */
+/* Step at x: d_D = distance to the Dirichlet part; the walk stops when     */
+/* d_D < eps and returns g at the closest Dirichlet point.  Otherwise the   */
+/* star radius is R = max(min(d_D, d_sil), eps), d_sil the distance to the  */
+/* closest silhouette point of the Neumann part seen from x, so that every  */
+/* ray from x crosses the Neumann part at most once inside B(x, R).  A      */
+/* direction w is drawn uniformly (on the inward hemisphere when x lies on  */
+/* the Neumann part); the ray x + t w, 0 < t <= R, is intersected with the  */
+/* Neumann part; the walk moves to the first hit (and is then on the        */
+/* boundary with that element's normal) or to x + R w.  With the ball's    */
+/* Green's function of -Laplacian, G^B(t) = ln(R/t)/(2 pi) (2D),            */
+/* (1/t - 1/R)/(4 pi) (3D), Green's second identity on the star region     */
+/*   a(x) u(x) = int_{dSt} u dG^B/dn  -  int_St G^B f  +  int_{dSt_N} G^B h  */
+/* (a = 1 inside, 1/2 on a smooth boundary point; the first integral is    */
+/* the solid angle measure / |S|) gives per step, with r = min(t_hit, R):   */
+/*   source  y = x + rho w, rho = r u2:                                      */
+/*           w_u = -r rho ln(R/rho) (2D),  -r rho (1 - rho/R) (3D)           */
+/*   Neumann term: a point z on the Neumann part inside B(x, R), chosen by  */
+/*           measure among the Neumann elements that reach into the ball    */
+/*           (total measure A) and uniformly on the element, adds           */
+/*           (1/a) G^B(|z - x|) h(z) A when z is inside the ball and seen   */
+/*           from x (no Neumann crossing between, elements within 1e-4 of   */
+/*           parallel to the sight line not counting), else nothing;        */
+/*           a = 1/2 on the boundary.  Draws: Philox (walk id, step - 1, tag + 8):   */
+/*           u0 picks the element (cumulative measure in element order),    */
+/*           u1, u2 the point (as the boundary sampler places points).      */
+/*   U = g(end) + sum w_u f(y) + sum of the Neumann terms.                   */
+/* A walk that starts inside the domain takes its first step in the ball of */
+/* radius d_all (distance to the whole boundary, no Neumann part inside)    */
+/* and estimates the gradient there as the walk on spheres does (Eq. 7);   */
+/* when d_all < eps the first step is a star step and the gradient is 0.    */
+/* Draws: Philox (id = walk id, word2 = step - 1, tag), w from (u0, u1) as  */
+/* on the sphere and flipped to -w when it points out of an on-boundary x,  */
+/* rho from u2.                                                              */
+/*                                                                          */
+/* Silhouettes: a Neumann vertex (2D) or edge (3D) shared by two Neumann    */
+/* elements with outward normals n0, n1; with a = (vertex or the edge's     */
+/* first vertex) - x and d_k = n_k . a, treated as zero when |d_k| <= tau,  */
+/* it is a silhouette when exactly one d_k is zero or both are non-zero     */
+/* with opposite signs.  Vertices or edges with one or more than two        */
+/* Neumann elements and no Dirichlet element are always silhouettes; those  */
+/* touching a Dirichlet element are skipped (never closer than d_D).        */
+/* tau = 2^-18 x the bounding-box diagonal.  All queries are brute force.   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int dim;
+  int64_t np, nv;
+  double* V;          /* [nv][dim] */
+  int32_t* F;         /* [np][dim] */
+  uint8_t* neu;       /* [np] */
+  double* nrm;        /* [np][dim] outward normals */
+  double* meas;       /* [np] element measures */
+  void* all;          /* BVH of the whole boundary */
+  void* dir;          /* BVH of the Dirichlet elements */
+  int64_t* dir_ids;   /* Dirichlet BVH element -> whole element */
+  int64_t n_neu;
+  int64_t* neu_ids;   /* Neumann elements (whole numbering, increasing) */
+  int64_t n_sil;
+  double* sil;        /* per candidate: 2D [v(2) n0(2) n1(2) always], 3D [a(3) b(3) n0(3) n1(3) always] */
+  double tau;
+} wost_t;
+
+static int sil_stride(int dim) { return dim == 2 ? 7 : 13; }
+
+typedef struct {
+  int32_t lo, hi, e;
+} edge_ref_t;
+
+static int cmp_edge(const void* x, const void* y) {
+  const edge_ref_t* a = (const edge_ref_t*)x;
+  const edge_ref_t* b = (const edge_ref_t*)y;
+  if (a->lo != b->lo) return a->lo < b->lo ? -1 : 1;
+  if (a->hi != b->hi) return a->hi < b->hi ? -1 : 1;
+  return (a->e > b->e) - (a->e < b->e);
+}
+
+void* orc_wost_create(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const uint8_t* neu) {
+  wost_t* w = (wost_t*)calloc(1, sizeof(wost_t));
+  w->dim = dim;
+  w->np = np;
+  w->nv = nv;
+  w->V = (double*)malloc(sizeof(double) * nv * dim);
+  for (int64_t i = 0; i < nv * dim; ++i) w->V[i] = V[i];
+  w->F = (int32_t*)malloc(sizeof(int32_t) * np * dim);
+  memcpy(w->F, F, sizeof(int32_t) * np * dim);
+  w->neu = (uint8_t*)malloc((size_t)np);
+  memcpy(w->neu, neu, (size_t)np);
+  w->nrm = (double*)malloc(sizeof(double) * np * dim);
+  w->meas = (double*)malloc(sizeof(double) * np);
+  for (int64_t e = 0; e < np; ++e) w->meas[e] = elem_measure_normal(dim, V, F + e * dim, w->nrm + e * dim);
+  w->all = orc_bvh_create(dim, V, nv, F, np);
+  int64_t nd = 0;
+  for (int64_t e = 0; e < np; ++e) nd += neu[e] ? 0 : 1;
+  int32_t* FD = (int32_t*)malloc(sizeof(int32_t) * (nd > 0 ? nd : 1) * dim);
+  w->dir_ids = (int64_t*)malloc(sizeof(int64_t) * (nd > 0 ? nd : 1));
+  w->neu_ids = (int64_t*)malloc(sizeof(int64_t) * (np - nd > 0 ? np - nd : 1));
+  int64_t q = 0;
+  for (int64_t e = 0; e < np; ++e) {
+    if (neu[e]) {
+      w->neu_ids[w->n_neu++] = e;
+    } else {
+      memcpy(FD + q * dim, F + e * dim, sizeof(int32_t) * dim);
+      w->dir_ids[q++] = e;
+    }
+  }
+  w->dir = orc_bvh_create(dim, V, nv, FD, nd);
+  free(FD);
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < nv; ++i)
+    for (int a = 0; a < dim; ++a) {
+      if (V[i * dim + a] < lo[a]) lo[a] = V[i * dim + a];
+      if (V[i * dim + a] > hi[a]) hi[a] = V[i * dim + a];
+    }
+  double diag = 0.0;
+  for (int a = 0; a < dim; ++a) diag += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+  w->tau = ldexp(1.0, -18) * (diag > 0.0 ? sqrt(diag) : 1.0);
+  /* silhouette candidates from the elements around each vertex (2D) or    */
+  /* edge (3D)                                                              */
+  const int ss = sil_stride(dim);
+  if (dim == 2) {
+    int64_t* cnt_n = (int64_t*)calloc((size_t)nv, sizeof(int64_t));
+    int64_t* cnt_d = (int64_t*)calloc((size_t)nv, sizeof(int64_t));
+    int64_t* first = (int64_t*)malloc(sizeof(int64_t) * nv);
+    int64_t* second = (int64_t*)malloc(sizeof(int64_t) * nv);
+    for (int64_t v = 0; v < nv; ++v) first[v] = second[v] = -1;
+    for (int64_t e = 0; e < np; ++e)
+      for (int k = 0; k < 2; ++k) {
+        const int32_t v = F[2 * e + k];
+        if (!neu[e]) {
+          ++cnt_d[v];
+        } else {
+          if (cnt_n[v] == 0) first[v] = e;
+          if (cnt_n[v] == 1) second[v] = e;
+          ++cnt_n[v];
+        }
+      }
+    w->sil = (double*)malloc(sizeof(double) * ss * (nv > 0 ? nv : 1));
+    for (int64_t v = 0; v < nv; ++v) {
+      if (cnt_n[v] == 0 || cnt_d[v] > 0) continue;
+      double* c = w->sil + w->n_sil * ss;
+      c[0] = w->V[2 * v];
+      c[1] = w->V[2 * v + 1];
+      if (cnt_n[v] == 2) {
+        for (int a = 0; a < 2; ++a) {
+          c[2 + a] = w->nrm[2 * first[v] + a];
+          c[4 + a] = w->nrm[2 * second[v] + a];
+        }
+        c[6] = 0.0;
+      } else {
+        for (int a = 0; a < 4; ++a) c[2 + a] = 0.0;
+        c[6] = 1.0;
+      }
+      ++w->n_sil;
+    }
+    free(cnt_n);
+    free(cnt_d);
+    free(first);
+    free(second);
+  } else {
+    edge_ref_t* ed = (edge_ref_t*)malloc(sizeof(edge_ref_t) * 3 * (np > 0 ? np : 1));
+    for (int64_t e = 0; e < np; ++e)
+      for (int k = 0; k < 3; ++k) {
+        const int32_t a = F[3 * e + k], b = F[3 * e + (k + 1) % 3];
+        ed[3 * e + k].lo = a < b ? a : b;
+        ed[3 * e + k].hi = a < b ? b : a;
+        ed[3 * e + k].e = (int32_t)e;
+      }
+    qsort(ed, (size_t)(3 * np), sizeof(edge_ref_t), cmp_edge);
+    w->sil = (double*)malloc(sizeof(double) * ss * (3 * np > 0 ? 3 * np : 1));
+    for (int64_t i = 0; i < 3 * np;) {
+      int64_t j = i;
+      int n_n = 0, n_d = 0;
+      int32_t en[2] = {-1, -1};
+      while (j < 3 * np && ed[j].lo == ed[i].lo && ed[j].hi == ed[i].hi) {
+        if (neu[ed[j].e]) {
+          if (n_n < 2) en[n_n] = ed[j].e;
+          ++n_n;
+        } else {
+          ++n_d;
+        }
+        ++j;
+      }
+      if (n_n > 0 && n_d == 0) {
+        double* c = w->sil + w->n_sil * ss;
+        for (int a = 0; a < 3; ++a) {
+          c[a] = w->V[3 * (int64_t)ed[i].lo + a];
+          c[3 + a] = w->V[3 * (int64_t)ed[i].hi + a];
+        }
+        if (n_n == 2) {
+          for (int a = 0; a < 3; ++a) {
+            c[6 + a] = w->nrm[3 * (int64_t)en[0] + a];
+            c[9 + a] = w->nrm[3 * (int64_t)en[1] + a];
+          }
+          c[12] = 0.0;
+        } else {
+          for (int a = 0; a < 6; ++a) c[6 + a] = 0.0;
+          c[12] = 1.0;
+        }
+        ++w->n_sil;
+      }
+      i = j;
+    }
+    free(ed);
+  }
+  return w;
+}
+
+void orc_wost_free(void* h) {
+  wost_t* w = (wost_t*)h;
+  if (!w) return;
+  orc_bvh_free(w->all);
+  orc_bvh_free(w->dir);
+  free(w->V);
+  free(w->F);
+  free(w->neu);
+  free(w->nrm);
+  free(w->meas);
+  free(w->dir_ids);
+  free(w->neu_ids);
+  free(w->sil);
+  free(w);
+}
+
+int64_t orc_wost_counts(void* h, int64_t* out) {
+  const wost_t* w = (const wost_t*)h;
+  out[0] = w->np - w->n_neu;
+  out[1] = w->n_neu;
+  out[2] = w->n_sil;
+  return w->n_sil;
+}
+
+/* Distance from x to the closest silhouette point (INFINITY if none). */
+static double wost_sil_dist(const wost_t* w, const double* x) {
+  const int dim = w->dim, ss = sil_stride(dim);
+  double best = INFINITY;
+  for (int64_t i = 0; i < w->n_sil; ++i) {
+    const double* c = w->sil + i * ss;
+    double a[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) a[k] = c[k] - x[k];
+    const int always = c[dim == 2 ? 6 : 12] != 0.0;
+    int is_sil = always;
+    if (!always) {
+      const double* n0 = c + (dim == 2 ? 2 : 6);
+      const double* n1 = c + (dim == 2 ? 4 : 9);
+      double d0 = 0.0, d1 = 0.0;
+      for (int k = 0; k < dim; ++k) {
+        d0 += n0[k] * a[k];
+        d1 += n1[k] * a[k];
+      }
+      const int z0 = fabs(d0) <= w->tau, z1 = fabs(d1) <= w->tau;
+      is_sil = (z0 != z1) || (!z0 && !z1 && ((d0 > 0.0) != (d1 > 0.0)));
+    }
+    if (!is_sil) continue;
+    double d2;
+    if (dim == 2) {
+      d2 = a[0] * a[0] + a[1] * a[1];
+    } else {
+      double cp[3];
+      const double b[3] = {c[3], c[4], c[5]};
+      d2 = seg3_closest64(c, b, x, cp);
+    }
+    if (d2 < best) best = d2;
+  }
+  return sqrt(best);
+}
+
+/* First crossing of the ray x + t w, 0 < t <= tmax, with the Neumann part,  */
+/* skipping element `skip` (whole numbering, -1 for none); ties go to the    */
+/* lowest element.  Returns the element (or -1) and sets *t_out.             */
+static int ray_elem(const wost_t* w, int64_t e, const double* x, const double* om, double* t_out) {
+  const int dim = w->dim;
+  const int32_t* f = w->F + e * dim;
+  double t;
+  if (dim == 2) {
+    const double* a = w->V + 2 * (int64_t)f[0];
+    const double* b = w->V + 2 * (int64_t)f[1];
+    const double abx = b[0] - a[0], aby = b[1] - a[1];
+    const double den = om[0] * aby - om[1] * abx;
+    if (den == 0.0) return 0;
+    const double qx = a[0] - x[0], qy = a[1] - x[1];
+    const double s = (qx * om[1] - qy * om[0]) / den;
+    if (s < 0.0 || s > 1.0) return 0;
+    t = (qx * aby - qy * abx) / den;
+  } else {
+    /* Moller-Trumbore (J. Graphics Tools 2(1), 1997) */
+    const double* a = w->V + 3 * (int64_t)f[0];
+    const double* b = w->V + 3 * (int64_t)f[1];
+    const double* c = w->V + 3 * (int64_t)f[2];
+    double e1[3], e2[3], P[3], T[3], Q[3];
+    for (int k = 0; k < 3; ++k) {
+      e1[k] = b[k] - a[k];
+      e2[k] = c[k] - a[k];
+      T[k] = x[k] - a[k];
+    }
+    P[0] = om[1] * e2[2] - om[2] * e2[1];
+    P[1] = om[2] * e2[0] - om[0] * e2[2];
+    P[2] = om[0] * e2[1] - om[1] * e2[0];
+    const double det = dot3d(e1, P);
+    if (det == 0.0) return 0;
+    const double u = dot3d(T, P) / det;
+    if (u < 0.0 || u > 1.0) return 0;
+    Q[0] = T[1] * e1[2] - T[2] * e1[1];
+    Q[1] = T[2] * e1[0] - T[0] * e1[2];
+    Q[2] = T[0] * e1[1] - T[1] * e1[0];
+    const double v = dot3d(om, Q) / det;
+    if (v < 0.0 || u + v > 1.0) return 0;
+    t = dot3d(e2, Q) / det;
+  }
+  *t_out = t;
+  return t > 0.0;
+}
+
+static int64_t wost_ray(const wost_t* w, const double* x, const double* om, double tmax, int64_t skip,
+                        double* t_out) {
+  double best = INFINITY;
+  int64_t be = -1;
+  for (int64_t q = 0; q < w->n_neu; ++q) {
+    const int64_t e = w->neu_ids[q];
+    double t;
+    if (e == skip || !ray_elem(w, e, x, om, &t)) continue;
+    if (t <= tmax && (t < best || (t == best && e < be))) {
+      best = t;
+      be = e;
+    }
+  }
+  *t_out = best;
+  return be;
+}
+
+typedef struct {
+  const wost_t* w;
+  const double *g, *hv, *hp, *f;
+  double eps;
+  int max_steps;
+  uint64_t seed;
+  uint32_t tag;
+} wost_ctx_t;
+
+/* The Neumann term of one star step (see above). */
+static double wost_neumann_term(const wost_ctx_t* c, const double* x, int on_n, int64_t self, double R, uint64_t wid,
+                                uint32_t step) {
+  const wost_t* w = c->w;
+  const int dim = w->dim;
+  double total = 0.0;
+  for (int64_t q = 0; q < w->n_neu; ++q) {
+    const int64_t e = w->neu_ids[q];
+    double cp[3];
+    if (prim_closest64(&((const obvh_t*)w->all)->m, e, x, cp) < R * R) total += w->meas[e];
+  }
+  if (!(total > 0.0)) return 0.0;
+  double u[4];
+  draw(c->seed, wid, step, c->tag + 8u, u);
+  const double target = u[0] * total;
+  double run = 0.0;
+  int64_t pick = -1;
+  for (int64_t q = 0; q < w->n_neu; ++q) {
+    const int64_t e = w->neu_ids[q];
+    double cp[3];
+    if (prim_closest64(&((const obvh_t*)w->all)->m, e, x, cp) < R * R) {
+      run += w->meas[e];
+      pick = e;
+      if (run > target) break;
+    }
+  }
+  /* a uniform point on the element */
+  const int32_t* f = w->F + pick * dim;
+  double z[3] = {0, 0, 0};
+  if (dim == 2) {
+    for (int a = 0; a < 2; ++a) z[a] = w->V[2 * f[0] + a] + u[1] * (w->V[2 * f[1] + a] - w->V[2 * f[0] + a]);
+  } else {
+    const double sq = sqrt(u[1]), b1 = sq * (1.0 - u[2]), b2 = sq * u[2];
+    for (int a = 0; a < 3; ++a) {
+      const double v0 = w->V[3 * f[0] + a];
+      z[a] = v0 + b1 * (w->V[3 * f[1] + a] - v0) + b2 * (w->V[3 * f[2] + a] - v0);
+    }
+  }
+  double r2 = 0.0, dir[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) {
+    dir[a] = z[a] - x[a];
+    r2 += dir[a] * dir[a];
+  }
+  const double r = sqrt(r2);
+  if (!(r < R) || !(r > 0.0)) return 0.0;
+  for (int a = 0; a < dim; ++a) dir[a] /= r;
+  /* seen from x: no Neumann crossing strictly before z (z's own element and */
+  /* the element under x excluded)                                           */
+  for (int64_t q = 0; q < w->n_neu; ++q) {
+    const int64_t e = w->neu_ids[q];
+    if (e == pick || (on_n && e == self)) continue;
+    double th, cs = 0.0;
+    for (int a = 0; a < dim; ++a) cs += w->nrm[e * dim + a] * dir[a];
+    if (fabs(cs) < 1e-4) continue; /* grazing elements do not occlude */
+    if (ray_elem(w, e, x, dir, &th) && th < r * (1.0 - 1e-9)) return 0.0;
+  }
+  const double gb = dim == 2 ? log(R / r) / (2.0 * ORC_PI) : (1.0 / r - 1.0 / R) / (4.0 * ORC_PI);
+  const double inv_a = on_n ? 2.0 : 1.0;
+  return inv_a * gb * orc_neumann_eval(c->hv, c->hp, dim, z, w->nrm + pick * dim) * total;
+}
+
+static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uint64_t wid, double* U_out,
+                          double* grad_out, int32_t* steps_out, int32_t* prim_out) {
+  const wost_t* w = c->w;
+  const int dim = w->dim;
+  const int has_f = !fn_is_zero(c->f), has_h = !fn_is_zero(c->hv) || !fn_is_zero(c->hp);
+  double x[3] = {0, 0, 0}, pbar[3] = {0, 0, 0}, nu[3] = {0, 0, 0}, nx[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) x[a] = x0[a];
+  int on_n = e0 >= 0;
+  int64_t self = e0;
+  if (on_n)
+    for (int a = 0; a < dim; ++a) nx[a] = w->nrm[e0 * dim + a];
+  double acc = 0.0, wf0 = 0.0, wg0 = 0.0, R0 = 0.0, cv = 0.0;
+  int k = 0;
+  int64_t prim = -1;
+  for (;;) {
+    const double dD = sqrt(bvh_closest((const obvh_t*)w->dir, x, pbar, &prim));
+    ++k;
+    if (k == 1) cv = orc_fn_eval(c->g, dim, pbar);
+    if (dD < c->eps || k >= c->max_steps) break;
+    double u[4];
+    draw(c->seed, wid, (uint32_t)(k - 1), c->tag, u);
+    double om[3] = {0, 0, 0}, rho, wu, wg;
+    if (k == 1 && !on_n) {
+      double cp[3];
+      int64_t ea;
+      const double dA = sqrt(bvh_closest((const obvh_t*)w->all, x, cp, &ea));
+      if (dA >= c->eps) {
+        /* the gradient ball: B(x, d_all) holds no boundary */
+        const double R = dA;
+        orc_sphere_step(dim, R, u[0], u[1], u[2], om, &rho, &wu, &wg);
+        if (has_f) {
+          double y[3] = {0, 0, 0};
+          for (int a = 0; a < dim; ++a) y[a] = x[a] + rho * om[a];
+          const double fy = orc_fn_eval(c->f, dim, y);
+          acc += wu * fy;
+          wf0 = wu * fy;
+          wg0 = wg * fy;
+        }
+        R0 = R;
+        for (int a = 0; a < dim; ++a) {
+          nu[a] = om[a];
+          x[a] += R * om[a];
+        }
+        continue;
+      }
+    }
+    /* star step */
+    orc_sphere_step(dim, 1.0, u[0], u[1], u[2], om, &rho, &wu, &wg);
+    if (on_n) {
+      double s = 0.0;
+      for (int a = 0; a < dim; ++a) s += nx[a] * om[a];
+      if (s > 0.0)
+        for (int a = 0; a < dim; ++a) om[a] = -om[a];
+    }
+    const double dS = wost_sil_dist(w, x);
+    double R = dD < dS ? dD : dS;
+    if (R < c->eps) R = c->eps;
+    double th;
+    const int64_t eh = wost_ray(w, x, om, R, on_n ? self : -1, &th);
+    const double r = eh >= 0 ? th : R;
+    if (has_f) {
+      const double rr = r * u[2];
+      double y[3] = {0, 0, 0};
+      for (int a = 0; a < dim; ++a) y[a] = x[a] + rr * om[a];
+      const double wsrc = dim == 2 ? -r * rr * log(R / rr) : -r * rr * (1.0 - rr / R);
+      acc += wsrc * orc_fn_eval(c->f, dim, y);
+    }
+    if (has_h) acc += wost_neumann_term(c, x, on_n, self, R, wid, (uint32_t)(k - 1));
+    if (eh >= 0) {
+      for (int a = 0; a < dim; ++a) {
+        x[a] += th * om[a];
+        nx[a] = w->nrm[eh * dim + a];
+      }
+      on_n = 1;
+      self = eh;
+    } else {
+      for (int a = 0; a < dim; ++a) x[a] += R * om[a];
+      on_n = 0;
+      self = -1;
+    }
+  }
+  const double U = orc_fn_eval(c->g, dim, pbar) + acc;
+  *U_out = U;
+  const double s = R0 > 0.0 ? ((double)dim / R0) * (U - wf0 - cv) + wg0 : 0.0;
+  for (int a = 0; a < dim; ++a) grad_out[a] = s * nu[a];
+  *steps_out = k;
+  *prim_out = prim >= 0 ? (int32_t)w->dir_ids[prim] : -1;
+}
+
+/* W walks from each of n starts (start_elem[i] >= 0: the start lies on that */
+/* Neumann element; -1: inside).  Walk j of start i has id                   */
+/* id_base + i*W + j; outputs per walk: U, grad[dim], steps, the Dirichlet   */
+/* element of the end (whole numbering).                                      */
+void orc_wost_walks(void* h, const double* g, const double* hv, const double* hp, const double* f,
+                    const float* starts, const int32_t* start_elem, int64_t n, int32_t W, double eps,
+                    int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
+                    int32_t* steps, int32_t* prim) {
+  const wost_t* w = (const wost_t*)h;
+  const wost_ctx_t c = {w, g, hv, hp, f, eps, max_steps, seed, tag};
+  const int dim = w->dim;
+  const int64_t total = n * (int64_t)W;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t t = 0; t < total; ++t) {
+    const int64_t i = t / W;
+    double x0[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) x0[a] = starts[i * dim + a];
+    wost_walk_one(&c, x0, start_elem ? start_elem[i] : -1, id_base + (uint64_t)t, &U[t], &grad[t * dim], &steps[t],
+                  &prim[t]);
+  }
+}
+
+/* Queries for the tests: distances to the Dirichlet part and to the closest */
+/* silhouette, and the first Neumann crossing of rays.                        */
+void orc_wost_query(void* h, const double* pts, int64_t n, double* d_dir, double* d_sil) {
+  const wost_t* w = (const wost_t*)h;
+  const int dim = w->dim;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    double cp[3];
+    int64_t e;
+    d_dir[i] = sqrt(bvh_closest((const obvh_t*)w->dir, pts + i * dim, cp, &e));
+    d_sil[i] = wost_sil_dist(w, pts + i * dim);
+  }
+}
+
+void orc_wost_rays(void* h, const double* org, const double* dir, const int32_t* skip, int64_t n, double tmax,
+                   double* t_out, int32_t* e_out) {
+  const wost_t* w = (const wost_t*)h;
+  const int dim = w->dim;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    double t;
+    const int64_t e = wost_ray(w, org + i * dim, dir + i * dim, tmax, skip ? skip[i] : -1, &t);
+    t_out[i] = t;
+    e_out[i] = (int32_t)e;
+  }
 }

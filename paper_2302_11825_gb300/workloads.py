@@ -630,3 +630,101 @@ def inverse_problem(n_obs: int = 100000, n_samples: int = 65536, walks: int = 64
     return InverseWorkload(f"inverse_box5ellipsoids_{F.shape[0] // 1000}k", V, F, ell, rbf_c, 0.4,
                            np.asarray(bc), 0.15, rng.standard_normal(n_rbf), rng.uniform(-10, 10, 8), obs,
                            n_samples, walks, eps, 5 * eps, (64, 32, 32))
+
+
+# ---------------------------------------------------------------- mixed boundaries
+def rect_polygon(lo, hi, n_per_unit: int):
+    """Counter-clockwise polygon of an axis-aligned rectangle with sides cut
+    into segments of length ~1/n_per_unit.  Returns V, F and each element's
+    side: 0 bottom (y = lo), 1 right (x = hi), 2 top, 3 left."""
+    (x0, y0), (x1, y1) = lo, hi
+    corners = [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+    V, side = [], []
+    for s in range(4):
+        a, b = np.asarray(corners[s], float), np.asarray(corners[(s + 1) % 4], float)
+        n = max(1, int(round(np.linalg.norm(b - a) * n_per_unit)))
+        for k in range(n):
+            V.append(a + (b - a) * k / n)
+            side.append(s)
+    V = np.asarray(V, dtype=np.float32)
+    n = V.shape[0]
+    F = np.stack([np.arange(n), (np.arange(n) + 1) % n], 1).astype(np.int32)
+    return V, F, np.asarray(side, np.int32)
+
+
+def l_shape_polygon(n_per_unit: int):
+    """[-1,1]^2 without the quadrant (0,1] x (0,1], counter-clockwise; the
+    corner (0,0) is reflex.  Returns V, F."""
+    corners = [(-1.0, -1.0), (1.0, -1.0), (1.0, 0.0), (0.0, 0.0), (0.0, 1.0), (-1.0, 1.0)]
+    V = []
+    for s in range(len(corners)):
+        a, b = np.asarray(corners[s], float), np.asarray(corners[(s + 1) % len(corners)], float)
+        n = max(1, int(round(np.linalg.norm(b - a) * n_per_unit)))
+        for k in range(n):
+            V.append(a + (b - a) * k / n)
+    V = np.asarray(V, dtype=np.float32)
+    n = V.shape[0]
+    F = np.stack([np.arange(n), (np.arange(n) + 1) % n], 1).astype(np.int32)
+    return V, F
+
+
+def element_midpoints(V, F) -> np.ndarray:
+    return V[F].astype(np.float64).mean(1)
+
+
+@dataclass
+class MixedWorkload:
+    """A mixed Dirichlet / Neumann problem (Eq. 1, sigma = 0): g on the
+    Dirichlet part, h = value + n . grad(potential) on the Neumann part."""
+    name: str
+    dim: int
+    V: np.ndarray
+    F: np.ndarray
+    neumann: np.ndarray
+    g: list
+    h_value: list
+    h_potential: list
+    f: list
+    n_samples: int
+    walks: int
+    offset_l: float
+    eps: float
+    eval_pts: np.ndarray
+    src_grid: tuple = (0, 0)
+    exact: list | None = None
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+
+def star_mixed(n_samples: int = 65536, walks: int = 64, grid: int = 1024, n_seg: int = 20000,
+               src_grid=(256, 256), seed: int = 0, n_bumps: int = 8, sigma: float = 0.05) -> MixedWorkload:
+    """A Neumann-dominated 2D mixed problem on the 20k-segment star of
+    ``star_poisson``: elements whose midpoint angle t has sin(7 t) < 0.5
+    (the valleys and flanks, about 2/3 of the boundary, with reflex vertices)
+    are Neumann, the lobe tips Dirichlet.  Manufactured solution
+    u* = x^2 - y^2 + 8 Gaussian bumps (sigma 0.05, amplitudes U[-10,10]):
+    g = u*, h = n . grad u*, f = Laplacian(u*).  65536 samples x 64 walks,
+    256^2 source candidates, the 1024^2 grid clipped to the domain;
+    eps = 1e-3 x bbox diagonal, l = 5 eps."""
+    base = star_poisson(n_samples=n_samples, walks=walks, grid=grid, n_seg=n_seg, src_grid=src_grid, seed=seed,
+                        manufactured=True, n_bumps=n_bumps, sigma=sigma)
+    mid = element_midpoints(base.V, base.F)
+    th = np.arctan2(mid[:, 1], mid[:, 0])
+    neu = (np.sin(7.0 * th) < 0.5).astype(np.uint8)
+    return MixedWorkload("star_mixed_20kseg", 2, base.V, base.F, neu, base.g, [], base.g, base.f, n_samples, walks,
+                         base.offset_l, base.eps, base.eval_pts, src_grid=base.src_grid, exact=base.exact,
+                         seed=seed, meta=dict(base.meta))
+
+
+def box_mixed_3d(cells_per_unit: int = 4, n_samples: int = 4096, walks: int = 64, seed: int = 0) -> MixedWorkload:
+    """Unit cube, Dirichlet on the faces x = 0 and x = 1, Neumann on the
+    other four; harmonic u* = x^2 - y^2 + 0.5 x z: g = u*, h = n . grad u*."""
+    V, F = box_surface((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), cells_per_unit)
+    mid = element_midpoints(V, F)
+    neu = ((mid[:, 0] > 1e-6) & (mid[:, 0] < 1.0 - 1e-6)).astype(np.uint8)
+    u = [(POLY, poly3d_coeffs({(2, 0, 0): 1.0, (0, 2, 0): -1.0, (1, 0, 1): 0.5}))]
+    rng = np.random.default_rng(seed)
+    pts = rng.uniform(0.1, 0.9, (512, 3)).astype(np.float32)
+    eps = 1e-3 * bbox_diagonal(V)
+    return MixedWorkload("box_mixed_3d", 3, V, F, neu, u, [], u, [], n_samples, walks, 5 * eps, eps, pts, exact=u,
+                         seed=seed)

@@ -1,0 +1,217 @@
+"""Pins of the oracle's walk on stars (Sec. 3.1, Fig. "WoS vs WoSt") for
+mixed Dirichlet / Neumann boundaries, and of its mixed cache (Sec. 3.2):
+reduction to walk on spheres, closed-form solutions with Neumann data and
+sources in 2D and 3D (inside and on the boundary), the star-shape property
+behind the silhouette radius, an independent ray caster, finite differences
+of the Neumann data, and the whole mixed boundary-value cache."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_11825_gb300 import workloads as wl
+
+P = wl.POLY
+
+
+def _z(U, W, exact):
+    U = U.reshape(-1, W)
+    se = U.std(1) / np.sqrt(W)
+    return (U.mean(1) - exact) / se, U.mean(1) - exact
+
+
+def _square():
+    V, F, side = wl.rect_polygon((0.0, 0.0), (1.0, 1.0), 16)
+    return V, F, side, (side % 2 == 0).astype(np.uint8)  # bottom and top Neumann
+
+
+def test_all_dirichlet_reduces_to_walk_on_spheres():
+    # with no Neumann element every star is the ball of the walk on spheres
+    for V, F, starts, g, f in [
+        (*wl.star_polygon(256, 0), 0.6 * wl.star_polygon(64, 0)[0][::3],
+         [(P, wl.poly2d_coeffs({(2, 0): 1.0, (0, 2): -1.0}))], [(P, [2.0])]),
+        (*wl.perturbed_icosphere(2, 0)[:2], 0.5 * wl.icosphere(1)[0][::5],
+         [(P, wl.poly3d_coeffs({(1, 1, 0): 1.0}))], [(P, [1.0])]),
+    ]:
+        starts = np.asarray(starts, np.float32)
+        w = oracle.Wost(V, F, np.zeros(F.shape[0]))
+        a = w.walks(g, [], [], f, starts, None, 8, 1e-3, 4096, 5)
+        b = oracle.walks(oracle.BVH(V, F), g, f, starts, 8, 1e-3, 4096, 5)
+        np.testing.assert_array_equal(a["steps"], b["steps"])
+        np.testing.assert_allclose(a["U"], b["U"], rtol=1e-9, atol=1e-11)
+        np.testing.assert_allclose(a["grad"], b["grad"], rtol=1e-8, atol=1e-9)
+
+
+def test_silhouette_candidates_counted():
+    V, F, side, neu = _square()
+    # 32 Dirichlet, 32 Neumann segments; 15 flat vertices inside each Neumann side
+    assert oracle.Wost(V, F, neu).counts() == (32, 32, 30)
+    b = wl.box_mixed_3d()
+    # 4 Neumann faces of 32 triangles: 40 interior edges each + 16 on the cube edges between them
+    assert oracle.Wost(b.V, b.F, b.neumann).counts() == (64, 128, 176)
+
+
+@pytest.mark.parametrize("case", ["harmonic", "source"])
+def test_square_closed_form_inside(case):
+    V, F, side, neu = _square()
+    w = oracle.Wost(V, F, neu)
+    if case == "harmonic":
+        u = [(P, wl.poly2d_coeffs({(2, 0): 1.0, (0, 2): -1.0, (1, 1): 0.3, (0, 1): 0.2}))]
+        f = []
+    else:
+        u = [(P, wl.poly2d_coeffs({(2, 0): 1.0, (0, 2): 1.0, (0, 1): 0.3}))]
+        f = [(P, [4.0])]
+    pts = np.random.default_rng(1).uniform(0.15, 0.85, (8, 2)).astype(np.float32)
+    W = 4000
+    o = w.walks(u, [], u, f, pts, None, W, 1e-4, 1 << 16, 31)
+    ex, gex = wl.eval_terms(u, 2, pts.astype(np.float64))
+    z, d = _z(o["U"], W, ex)
+    assert np.all(np.abs(z) < 4.5), (z, d)
+    # the gradient of the first (ball) step, Eq. 7
+    G = o["grad"].reshape(-1, W, 2)
+    zg = (G.mean(1) - gex) / (G.std(1) / np.sqrt(W))
+    assert np.all(np.abs(zg) < 4.5), zg
+
+
+def test_square_closed_form_on_the_neumann_boundary():
+    # starts on Neumann elements: inward hemisphere, a = 1/2
+    V, F, side, neu = _square()
+    w = oracle.Wost(V, F, neu)
+    u = [(P, wl.poly2d_coeffs({(2, 0): 1.0, (0, 2): 1.0, (0, 1): 0.3}))]
+    top = np.where(side == 2)[0][3:9]
+    bottom = np.where(side == 0)[0][5:8]
+    el = np.concatenate([top, bottom]).astype(np.int32)
+    z = V[F[el]].astype(np.float64).mean(1).astype(np.float32)
+    W = 4000
+    o = w.walks(u, [], u, [(P, [4.0])], z, el, W, 1e-4, 1 << 16, 32)
+    ex, _ = wl.eval_terms(u, 2, z.astype(np.float64))
+    zs, d = _z(o["U"], W, ex)
+    assert np.all(np.abs(zs) < 4.5), (zs, d)
+    assert np.all(o["grad"] == 0.0)  # no gradient ball on the boundary
+
+
+def test_l_shape_reflex_neumann_corner_closed_form():
+    # Neumann everywhere but the side x = -1: walks pass the reflex corner
+    V, F = wl.l_shape_polygon(8)
+    mid = wl.element_midpoints(V, F)
+    w = oracle.Wost(V, F, (mid[:, 0] > -1 + 1e-6).astype(np.uint8))
+    u = [(P, wl.poly2d_coeffs({(2, 0): 1.0, (0, 2): -1.0, (1, 1): 0.5}))]
+    pts = np.array([[-0.5, -0.5], [0.3, -0.2], [-0.2, 0.3], [0.1, -0.05], [-0.05, 0.1], [0.6, -0.6]], np.float32)
+    W = 6000
+    o = w.walks(u, [], u, [], pts, None, W, 1e-4, 1 << 16, 33)
+    z, d = _z(o["U"], W, wl.eval_terms(u, 2, pts.astype(np.float64))[0])
+    assert np.all(np.abs(z) < 4.5), (z, d)
+
+
+@pytest.mark.parametrize("case", ["harmonic", "source"])
+def test_cube_closed_form(case):
+    b = wl.box_mixed_3d()
+    w = oracle.Wost(b.V, b.F, b.neumann)
+    if case == "harmonic":
+        u, f = b.g, []
+    else:
+        u = [(P, wl.poly3d_coeffs({(2, 0, 0): 1.0, (0, 2, 0): 1.0, (0, 0, 2): 1.0, (0, 1, 0): 0.3}))]
+        f = [(P, [6.0])]
+    pts = b.eval_pts[:6]
+    W = 2000
+    o = w.walks(u, [], u, f, pts, None, W, 1e-4, 1 << 16, 34)
+    z, d = _z(o["U"], W, wl.eval_terms(u, 3, pts.astype(np.float64))[0])
+    assert np.all(np.abs(z) < 4.5), (z, d)
+
+
+def test_star_radius_sees_each_neumann_crossing_once():
+    # R = min(d_D, d_sil): inside B(x, R) no ray from x crosses the Neumann
+    # part twice (on the L-shape, the exterior notch cannot span the ball
+    # without its reflex corner inside it)
+    V, F = wl.l_shape_polygon(8)
+    mid = wl.element_midpoints(V, F)
+    neu = (mid[:, 0] > -1 + 1e-6).astype(np.uint8)
+    w = oracle.Wost(V, F, neu)
+    rng = np.random.default_rng(5)
+    p = rng.uniform(-0.98, 0.98, (400, 2))
+    p = p[~((p[:, 0] > 0.0) & (p[:, 1] > 0.0))][:120]
+    dd, ds = w.query(p)
+    R = np.minimum(dd, ds)
+    assert np.median(R) > 0.05
+    Fn = F[neu == 1]
+    th = 2.0 * np.pi * (np.arange(128) + 0.5) / 128
+    for x, r in zip(p, R):
+        for t in th:
+            tt, _, _ = oracle.ray_hits(V, Fn, 0.0, x, np.array([np.cos(t), np.sin(t)]), r * (1.0 - 1e-9))
+            assert tt.size <= 1
+    # without the silhouette bound (R = d_D) some ray does cross twice
+    twice = 0
+    for x, r in zip(p, dd):
+        for t in th[::4]:
+            tt, _, _ = oracle.ray_hits(V, Fn, 0.0, x, np.array([np.cos(t), np.sin(t)]), r * (1.0 - 1e-9))
+            twice += tt.size > 1
+    assert twice > 0
+
+
+def test_first_crossing_matches_an_independent_ray_caster():
+    V, F = wl.l_shape_polygon(8)
+    mid = wl.element_midpoints(V, F)
+    neu = (mid[:, 0] > -1 + 1e-6).astype(np.uint8)
+    w = oracle.Wost(V, F, neu)
+    Fn = F[neu == 1]
+    ids = np.where(neu == 1)[0]
+    rng = np.random.default_rng(6)
+    org = rng.uniform(-0.95, 0.95, (300, 2))
+    org = org[~((org[:, 0] > 0.0) & (org[:, 1] > 0.0))]
+    ang = rng.uniform(0, 2 * np.pi, org.shape[0])
+    dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
+    t, e = w.rays(org, dirs, 10.0)
+    for i in range(org.shape[0]):
+        tt, ee, _ = oracle.ray_hits(V, Fn, 0.0, org[i], dirs[i], 10.0)
+        if tt.size == 0:
+            assert e[i] == -1
+        else:
+            assert e[i] == ids[ee[0]]
+            assert abs(t[i] - tt[0]) <= 1e-12 * max(1.0, tt[0])
+
+
+def test_neumann_data_is_the_normal_derivative():
+    rng = np.random.default_rng(7)
+    for dim, terms in [
+        (2, [(P, wl.poly2d_coeffs({(2, 0): 1.0, (1, 1): -0.7, (0, 3): 0.2, (1, 0): 0.4})),
+             (wl.GAUSS, wl.gauss_coeffs(0.3, [1.5, -2.0], [[0.1, 0.2], [-0.3, 0.4]])),
+             (wl.GAUSS_LAPLACIAN, wl.gauss_coeffs(0.4, [0.7], [[0.0, -0.2]]))]),
+        (3, [(P, wl.poly3d_coeffs({(1, 1, 1): 1.0, (0, 0, 3): -0.5, (2, 0, 0): 0.3})),
+             (wl.EXP_TRIG, [1.2, 0.5, 0.3, 0.4]), (5, [0.8, 0.6, 1.1])]),
+    ]:
+        z = rng.uniform(-0.5, 0.5, (20, dim))
+        n = rng.standard_normal((20, dim))
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        h = oracle.neumann_eval([(P, [0.25])], terms, dim, z, n)
+        d = 1e-5
+        fd = (oracle.fn_eval(terms, dim, z + d * n) - oracle.fn_eval(terms, dim, z - d * n)) / (2 * d)
+        np.testing.assert_allclose(h, 0.25 + fd, rtol=1e-7, atol=1e-7)
+
+
+def mixed_pipeline(V, F, neu, u, f, N, W, l, eps, seed, pts):
+    """The mixed cache (Sec. 3.2) with the oracle: samples on the Neumann
+    part keep offset 0 and carry du/dn = h; Dirichlet samples move by -l n
+    and carry walk estimates of u and du/dn; Eq. 3 at the points."""
+    dim = V.shape[1]
+    w = oracle.Wost(V, F, neu)
+    z, n, e = oracle.sample_boundary_mixed(V, F, N, l, seed, neu)
+    on_n = neu[e] == 1
+    se = np.where(on_n, e, -1).astype(np.int32)
+    o = w.walks(u, [], u, f, z.astype(np.float32), se, W, eps, 1 << 16, seed)
+    u_hat = o["U"].reshape(N, W).mean(1)
+    q_walk = np.einsum("iwd,id->i", o["grad"].reshape(N, W, dim), n) / W
+    h = oracle.neumann_eval([], u, dim, z.astype(np.float32).astype(np.float64), n.astype(np.float32)
+                            .astype(np.float64))
+    q_hat = np.where(on_n, h, q_walk)
+    ub, _, gb, _ = oracle.gather(z.astype(np.float32), n.astype(np.float32), u_hat, q_hat,
+                                 oracle.boundary_measure(V, F), pts)
+    return ub / N, gb / N, (z, n, e, u_hat, q_hat)
+
+
+def test_mixed_cache_square_closed_form():
+    V, F, side, neu = _square()
+    u = [(P, wl.poly2d_coeffs({(2, 0): 1.0, (0, 2): -1.0, (1, 1): 0.3, (0, 1): 0.2}))]
+    pts = wl.grid_points((0.1, 0.1), (0.9, 0.9), 12)
+    uh, gh, _ = mixed_pipeline(V, F, neu, u, [], 4096, 64, 5e-3, 1e-3, 9, pts)
+    ex, gex = wl.eval_terms(u, 2, pts)
+    rmse = np.sqrt(np.mean((uh - ex) ** 2))
+    assert rmse < 0.02 * (ex.max() - ex.min()), rmse
