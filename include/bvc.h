@@ -535,6 +535,109 @@ bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_function* gfn, 
                                        bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps,
                                        uint64_t seed, uint64_t id_base, bvc_stream stream);
 
+/* ------------------------------------------- mixed boundaries (WoSt) */
+/* Laplace(u) = f with u = g on the Dirichlet part and du/dn = h on the
+ * Neumann part of the boundary (Eq. 1, sigma = 0), by walk on stars
+ * (Sec. 3.1, Fig. "WoS vs WoSt") and the cache of Sec. 3.2 / Fig.
+ * "Dirichlet offset boundary": samples on Neumann elements lie on the
+ * boundary and carry the known du/dn = h(z); samples on Dirichlet elements
+ * are moved inward by l and carry walk estimates of u and du/dn; u on the
+ * Neumann samples is estimated by walks that start on the boundary.
+ *
+ * A walk step at x: distance d_D to the Dirichlet part (stop when below eps,
+ * returning g at the closest Dirichlet point); star radius
+ * R = max(min(d_D, d_sil), eps) with d_sil the distance to the closest
+ * silhouette point of the Neumann part as seen from x (so each ray from x
+ * crosses the Neumann part at most once inside B(x, R)); a direction w
+ * uniform on the sphere (flipped into the domain when x is on the Neumann
+ * part); the first crossing of x + t w, 0 < t <= R, with the Neumann part is
+ * the next point (then on the boundary), else x + R w.  With r = min(t, R)
+ * and rho = r u2 the step adds
+ *   source  w_u f(x + rho w),  w_u = r rho ln(rho/R) (2D), -r rho (1 - rho/R) (3D)
+ *   Neumann w_h h(z) at a crossing z with normal n_z,
+ *           w_h = t ln(R/t)/|n_z.w| (2D), t (1 - t/R)/|n_z.w| (3D).
+ * A walk that starts inside the domain first takes a ball step of radius
+ * d_all (distance to the whole boundary) and estimates the gradient as
+ * bvc_walk does; if d_all < eps its first step is a star step and its
+ * gradient is 0.  Silhouettes: a Neumann vertex (2D) or edge (3D) between
+ * two Neumann elements with outward normals n0, n1 is one when, with
+ * a = (vertex or edge start) - x and d_k = n_k . a (zero when
+ * |d_k| <= 2^-18 x bounding-box diagonal), exactly one d_k is zero or both
+ * are non-zero with opposite signs; one with one or more than two Neumann
+ * elements (and no Dirichlet element) always is; one touching a Dirichlet
+ * element is skipped (d_D covers it).  Draws: Philox(walk id, step - 1, tag)
+ * as bvc_walk. */
+typedef struct bvc_mixed_s* bvc_mixed;
+
+/* Flags neumann[e] != 0 mark Neumann elements (host uint8[n_prims]); at
+ * least one element must be Dirichlet.  Builds the whole boundary's geometry,
+ * the Dirichlet and Neumann parts' geometries and the silhouette tree
+ * (synchronous on `stream`).  Mesh arguments as bvc_geometry_create. */
+bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims, int64_t n_prims,
+                            const uint8_t* neumann, bvc_stream stream, bvc_mixed* out);
+bvc_status bvc_mixed_destroy(bvc_mixed m);
+typedef struct {
+  int32_t dim;
+  int64_t n_dirichlet, n_neumann; /* elements */
+  int64_t n_silhouette;           /* silhouette candidates (vertices 2D, edges 3D) */
+  double dirichlet_measure, neumann_measure;
+  size_t device_bytes;            /* the silhouette tree and maps (geometries not included) */
+} bvc_mixed_info;
+bvc_status bvc_mixed_get_info(bvc_mixed m, bvc_mixed_info* info);
+/* Borrowed handles (owned by m): the whole boundary, its Dirichlet part and
+ * its Neumann part (NULL when there is no Neumann element).  Element ids of
+ * the parts are their positions among the whole mesh's Dirichlet / Neumann
+ * elements. */
+bvc_status bvc_mixed_geometries(bvc_mixed m, bvc_geometry* whole, bvc_geometry* dirichlet, bvc_geometry* neumann);
+
+/* Neumann data h(z) = value(z) + n_z . grad potential(z) (either may have
+ * no terms; potential kinds POLY, GAUSS, GAUSS_LAPLACIAN, EXP_TRIG, EXP_COS). */
+typedef struct {
+  bvc_function value;
+  bvc_function potential;
+} bvc_neumann;
+
+/* Queries behind the walk, for checks: per point (device [dim][m]) the
+ * distance to the Dirichlet part and to the closest silhouette point (FP32,
+ * +inf when there is none); per ray (origins and unit directions device
+ * [dim][m], skip: device int32[m] Neumann element to ignore, or NULL) the
+ * first crossing t with the Neumann part in (0, tmax] and its Neumann element
+ * id (-1 and +inf when none). */
+bvc_status bvc_mixed_query(bvc_mixed m, const float* pts, int64_t n, float* d_dir, float* d_sil, bvc_stream stream);
+bvc_status bvc_mixed_rays(bvc_mixed m, const float* org, const float* dir, const int32_t* skip, int64_t n,
+                          float tmax, float* t, int32_t* elem, bvc_stream stream);
+
+/* Walks on stars from n starts (device float[dim][n]); start_elem: device
+ * int32[n], the whole-mesh element a start lies on (a Neumann element: the
+ * walk starts on the boundary with normal nrm), or -1 / NULL for starts
+ * inside.  Records as bvc_walk: with nrm != NULL one extra plane holding
+ * n . grad for starts inside and h(start) for starts on the Neumann part;
+ * else dim planes of grad.  steps, prim: per-walk step count and the whole-
+ * mesh Dirichlet element of the end, or NULL.  Walk ids id_base + i*walks + j;
+ * `counter`: device uint64 work counter, zeroed by the call. */
+bvc_status bvc_mixed_walk(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
+                          const float* starts, const int32_t* start_elem, const float* nrm, int64_t n, int32_t walks,
+                          float eps, int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, float* rec,
+                          int32_t* steps, int32_t* prim, unsigned long long* counter, bvc_stream stream);
+
+/* The mixed cache: K1 on the whole boundary (Neumann samples at offset 0,
+ * Dirichlet samples at offset_l), walks on stars (tag 0, ids as
+ * bvc_cache_build), K3, source samples (opts->src_grid, inside the whole
+ * boundary), pack.  dudn_hat of a Neumann sample is h(z).  sigma and
+ * clamp_c must be 0.  Workspace as bvc_cache_build on the whole geometry. */
+bvc_status bvc_mixed_cache_build_workspace_size(bvc_mixed m, const bvc_cache_opts* opts, size_t* min_bytes,
+                                                size_t* full_bytes);
+bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
+                                 const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
+                                 size_t workspace_bytes, bvc_stream stream);
+
+/* Pointwise walk on stars at the points of `state` (tag 3), as wos_estimate:
+ * u_bnd += sum_j U, grad_bnd += sum_j grad (if set), counts[0] += walks.
+ * Workspace: wos_estimate_workspace_size. */
+bvc_status wost_estimate(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
+                         bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                         uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream);
+
 /* ------------------------------------------------------------- profiling */
 /* Between bvc_profile_begin and bvc_profile_end every kernel the library
  * launches is bracketed by CUDA events on its own stream.  bvc_profile_end

@@ -85,6 +85,16 @@ class EvalStateStruct(C.Structure):
                 ("counts", C.c_void_p)]
 
 
+class NeumannStruct(C.Structure):
+    _fields_ = [("value", Function), ("potential", Function)]
+
+
+class MixedInfo(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_dirichlet", C.c_int64), ("n_neumann", C.c_int64),
+                ("n_silhouette", C.c_int64), ("dirichlet_measure", C.c_double), ("neumann_measure", C.c_double),
+                ("device_bytes", C.c_size_t)]
+
+
 def _declare(lib):
     P, i32, i64, u32, u64, f32, f64, sz = (C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float,
                                           C.c_double, C.c_size_t)
@@ -149,6 +159,19 @@ def _declare(lib):
         "bvc_tune_walks": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(CacheOpts), P, sz, P,
                                C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
         "bvc_geometry_set_walk_shape": (S, [P, i32, i32]),
+        "bvc_mixed_create": (S, [i32, P, i64, P, i64, P, P, C.POINTER(C.c_void_p)]),
+        "bvc_mixed_destroy": (S, [P]),
+        "bvc_mixed_get_info": (S, [P, C.POINTER(MixedInfo)]),
+        "bvc_mixed_geometries": (S, [P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+        "bvc_mixed_query": (S, [P, P, i64, P, P, P]),
+        "bvc_mixed_rays": (S, [P, P, P, P, i64, f32, P, P, P]),
+        "bvc_mixed_walk": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function), P, P, P, i64,
+                               i32, f32, i32, u64, u64, u32, P, P, P, P, P]),
+        "bvc_mixed_cache_build_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz), C.POINTER(sz)]),
+        "bvc_mixed_cache_build": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function),
+                                      C.POINTER(CacheOpts), C.POINTER(CacheStruct), P, sz, P]),
+        "wost_estimate": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function),
+                              C.POINTER(EvalStateStruct), i32, f32, i32, u64, u64, P, sz, P]),
         "bvc_profile_begin": (S, []),
         "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
         "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
@@ -873,3 +896,142 @@ def gather_status(reset=False):
     f = C.c_uint64()
     st = lib().bvc_gather_status(C.byref(f), int(bool(reset)))
     return int(f.value), st
+
+
+# ---------------------------------------------------------------- mixed boundaries (WoSt)
+def make_neumann(h) -> NeumannStruct:
+    """h = (value_terms, potential_terms): Neumann data value(z) + n . grad potential(z)."""
+    hv, hp = (h or ([], []))
+    out = NeumannStruct()
+    fv, fp = make_function(hv), make_function(hp)
+    out.value, out.potential = fv, fp
+    out._keep = (fv, fp)
+    return out
+
+
+class _BorrowedGeometry(Geometry):
+    """A geometry handle owned by another object (not destroyed here)."""
+
+    def __init__(self, h, dim):
+        self.h = h
+        self.dim = dim
+
+    def close(self):
+        self.h = None
+
+
+class Mixed:
+    """bvc_mixed_create / bvc_mixed_destroy: a boundary whose elements are
+    Dirichlet (neumann[e] == 0) or Neumann, with its walk-on-stars trees."""
+
+    def __init__(self, V, F, neumann, stream=None):
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        fl = np.ascontiguousarray(np.asarray(neumann) != 0, dtype=np.uint8)
+        if fl.shape[0] != F.shape[0]:
+            raise ValueError("one Neumann flag per element")
+        self.dim = int(V.shape[1])
+        h = C.c_void_p()
+        _check(lib().bvc_mixed_create(self.dim, V.ctypes.data_as(C.c_void_p), V.shape[0],
+                                      F.ctypes.data_as(C.c_void_p), F.shape[0], fl.ctypes.data_as(C.c_void_p),
+                                      _stream(stream), C.byref(h)), "bvc_mixed_create")
+        self.h = h
+        w, d, n = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(lib().bvc_mixed_geometries(self.h, C.byref(w), C.byref(d), C.byref(n)), "bvc_mixed_geometries")
+        self.whole = _BorrowedGeometry(w, self.dim)
+        self.dirichlet = _BorrowedGeometry(d, self.dim)
+        self.neumann = _BorrowedGeometry(n, self.dim) if n.value else None
+
+    def info(self) -> MixedInfo:
+        inf = MixedInfo()
+        _check(lib().bvc_mixed_get_info(self.h, C.byref(inf)), "bvc_mixed_get_info")
+        return inf
+
+    def close(self):
+        if getattr(self, "h", None):
+            for g in (self.whole, self.dirichlet, self.neumann):
+                if g is not None:
+                    g.close()
+            lib().bvc_mixed_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mixed_query(m: Mixed, pts: torch.Tensor, stream=None):
+    """Distances to the Dirichlet part and to the closest silhouette."""
+    _dev(pts, torch.float32)
+    n = pts.shape[1]
+    dd = torch.empty(n, dtype=torch.float32, device=pts.device)
+    ds = torch.empty(n, dtype=torch.float32, device=pts.device)
+    _check(lib().bvc_mixed_query(m.h, _ptr(pts), n, _ptr(dd), _ptr(ds), _stream(stream)), "bvc_mixed_query")
+    return dd, ds
+
+
+def mixed_rays(m: Mixed, org: torch.Tensor, dirs: torch.Tensor, tmax: float, skip: torch.Tensor = None,
+               stream=None):
+    """First crossing (t, Neumann element) of each ray with the Neumann part."""
+    _dev(org, torch.float32)
+    _dev(dirs, torch.float32)
+    n = org.shape[1]
+    t = torch.empty(n, dtype=torch.float32, device=org.device)
+    e = torch.empty(n, dtype=torch.int32, device=org.device)
+    _check(lib().bvc_mixed_rays(m.h, _ptr(org), _ptr(dirs), _ptr(skip), n, float(tmax), _ptr(t), _ptr(e),
+                                _stream(stream)), "bvc_mixed_rays")
+    return t, e
+
+
+def mixed_walk(m: Mixed, g_terms, h, f_terms, starts, start_elem, nrm, walks: int, eps: float, max_steps: int,
+               seed: int, id_base: int = 0, tag: int = TAG_WALK, debug=False, stream=None):
+    """bvc_mixed_walk: per-walk records (U, and n.grad / h or grad)."""
+    _dev(starts, torch.float32)
+    n = starts.shape[1]
+    planes = 1 if nrm is not None else m.dim
+    rec = torch.empty((1 + planes, n * walks), dtype=torch.float32, device="cuda")
+    steps = torch.empty(n * walks, dtype=torch.int32, device="cuda") if debug else None
+    prim = torch.empty(n * walks, dtype=torch.int32, device="cuda") if debug else None
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    g, f, hn = make_function(g_terms), make_function(f_terms), make_neumann(h)
+    _check(lib().bvc_mixed_walk(m.h, C.byref(g), C.byref(hn), C.byref(f), _ptr(starts), _ptr(start_elem), _ptr(nrm),
+                                n, int(walks), float(eps), int(max_steps), int(seed), int(id_base), int(tag),
+                                _ptr(rec), _ptr(steps), _ptr(prim), _ptr(counter), _stream(stream)),
+           "bvc_mixed_walk")
+    return rec, steps, prim
+
+
+def mixed_cache_build_workspace_size(m: Mixed, opts: CacheOpts):
+    mn, full = C.c_size_t(), C.c_size_t()
+    _check(lib().bvc_mixed_cache_build_workspace_size(m.h, C.byref(opts), C.byref(mn), C.byref(full)),
+           "bvc_mixed_cache_build_workspace_size")
+    return int(mn.value), int(full.value)
+
+
+def mixed_cache_build(m: Mixed, g_terms, h, f_terms, opts: CacheOpts, cache: Cache, ws: torch.Tensor = None,
+                      stream=None):
+    """The mixed cache (Sec. 3.2): Neumann samples on the boundary with
+    du/dn = h, Dirichlet samples at offset l, u by walks on stars."""
+    if ws is None:
+        ws = workspace(mixed_cache_build_workspace_size(m, opts)[1])
+    g, f, hn = make_function(g_terms), make_function(f_terms), make_neumann(h)
+    _check(lib().bvc_mixed_cache_build(m.h, C.byref(g), C.byref(hn), C.byref(f), C.byref(opts),
+                                       C.byref(cache.struct), _ptr(ws), ws.numel(), _stream(stream)),
+           "bvc_mixed_cache_build")
+    cache.sync_from_struct()
+    return cache
+
+
+def wost_estimate(m: Mixed, g_terms, h, f_terms, state: EvalState, walks: int, eps: float, max_steps: int,
+                  seed: int, id_base: int = 0, ws: torch.Tensor = None, stream=None):
+    """Pointwise walk on stars: adds `walks` walks per point to the state's
+    running sums (finalise with get_solution)."""
+    if ws is None:
+        ws = workspace(wos_workspace_size(state.dim, state.m, walks)[1])
+    g, f, hn = make_function(g_terms), make_function(f_terms), make_neumann(h)
+    _check(lib().wost_estimate(m.h, C.byref(g), C.byref(hn), C.byref(f), C.byref(state.struct), int(walks),
+                               float(eps), int(max_steps), int(seed), int(id_base), _ptr(ws), ws.numel(),
+                               _stream(stream)), "wost_estimate")
+    return state

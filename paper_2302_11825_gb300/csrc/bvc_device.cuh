@@ -141,6 +141,92 @@ __device__ __forceinline__ float eval_fn(const DevFunction& fn, const float* x) 
   return v;
 }
 
+// Gradient of a problem function (a mixed problem's Neumann data is
+// h = n . grad(potential)); kinds as eval_fn.
+template <int D>
+__device__ __forceinline__ void eval_fn_grad(const DevFunction& fn, const float* x, float* g) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) g[a] = 0.0f;
+  for (int t = 0; t < fn.n_terms; ++t) {
+    const float* c = fn.c + fn.off[t];
+    const int nc = fn.nc[t];
+    switch (fn.kind[t]) {
+      case BVC_FN_POLY: {
+        // powers p[e] = x^e and derivatives dp[e] = e x^(e-1) per axis
+        float xp[3][5], dp[3][5];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float v = a < D ? x[a < D ? a : 0] : 0.0f;
+          xp[a][0] = 1.0f;
+          dp[a][0] = 0.0f;
+#pragma unroll
+          for (int e = 1; e < 5; ++e) {
+            dp[a][e] = (float)e * xp[a][e - 1];
+            xp[a][e] = xp[a][e - 1] * v;
+          }
+        }
+        int idx = 0;
+        for (int tt = 0; tt <= 4 && idx < nc; ++tt) {
+          if (D == 2) {
+            for (int i = tt; i >= 0 && idx < nc; --i, ++idx) {
+              const int j = tt - i;
+              g[0] = fmaf(c[idx], dp[0][i] * xp[1][j], g[0]);
+              g[1] = fmaf(c[idx], xp[0][i] * dp[1][j], g[1]);
+            }
+          } else {
+            for (int i = tt; i >= 0 && idx < nc; --i)
+              for (int j = tt - i; j >= 0 && idx < nc; --j, ++idx) {
+                const int k = tt - i - j;
+                g[0] = fmaf(c[idx], dp[0][i] * xp[1][j] * xp[2][k], g[0]);
+                g[1] = fmaf(c[idx], xp[0][i] * dp[1][j] * xp[2][k], g[1]);
+                g[D - 1] = fmaf(c[idx], xp[0][i] * xp[1][j] * dp[2][k], g[D - 1]);
+              }
+          }
+        }
+        break;
+      }
+      case BVC_FN_GAUSS:
+      case BVC_FN_GAUSS_LAPLACIAN: {
+        // GAUSS: A e, e = exp(neg r2), grad = 2 neg A e d (d = x - centre);
+        // GAUSS_LAPLACIAN: A q e, q = r2 q4 + qd, grad = A e d (2 q4 + 2 neg q)
+        const bool lap = fn.kind[t] == BVC_FN_GAUSS_LAPLACIAN;
+        const float neg = c[0], q4 = lap ? c[1] : 0.0f, qd = lap ? c[2] : 0.0f;
+        for (int k = lap ? 3 : 1; k + D < nc; k += 1 + D) {
+          float d[D], r2 = 0.0f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            d[a] = x[a] - c[k + 1 + a];
+            r2 = fmaf(d[a], d[a], r2);
+          }
+          const float e = c[k] * expf(r2 * neg);
+          const float fac = lap ? e * (2.0f * q4 + 2.0f * neg * fmaf(r2, q4, qd)) : 2.0f * neg * e;
+#pragma unroll
+          for (int a = 0; a < D; ++a) g[a] = fmaf(fac, d[a], g[a]);
+        }
+        break;
+      }
+      case BVC_FN_EXP_TRIG:
+        if (D == 3) {
+          const float e = c[0] * expf(c[1] * x[D == 3 ? 2 : 0]);
+          const float cx = cosf(c[2] * x[0]), sx = sinf(c[2] * x[0]);
+          const float cy = cosf(c[3] * x[1]), sy = sinf(c[3] * x[1]);
+          g[0] = fmaf(-c[2] * e * sx, sy, g[0]);
+          g[1] = fmaf(c[3] * e * cx, cy, g[1]);
+          g[D - 1] = fmaf(c[1] * e * cx, sy, g[D - 1]);
+        }
+        break;
+      case BVC_FN_EXP_COS: {
+        const float e = c[0] * expf(c[1] * x[D - 1]);
+        g[0] = fmaf(-c[2] * e, sinf(c[2] * x[0]), g[0]);
+        g[D - 1] = fmaf(c[1] * e, cosf(c[2] * x[0]), g[D - 1]);
+        break;
+      }
+      default:
+        break;
+    }
+  }
+}
+
 // Boundary data from vertex values (the differentiable parameterisation of
 // g): at a point p of element e (caller numbering), g is the linear
 // interpolation of the element's vertex values -- segment: projection

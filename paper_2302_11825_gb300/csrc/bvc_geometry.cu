@@ -66,7 +66,8 @@ template <int D>
 __global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t n, double l, uint64_t seed,
                                                          float* __restrict__ z, float* __restrict__ nrm,
                                                          int32_t* __restrict__ elem, int64_t stride,
-                                                         const uint64_t* __restrict__ seed_dev) {
+                                                         const uint64_t* __restrict__ seed_dev,
+                                                         const uint8_t* __restrict__ zero_l) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const U4 r = philox_draw(seed_dev ? *seed_dev : seed, (uint64_t)i, 0u, 1u);
@@ -115,9 +116,11 @@ __global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t 
     const double b1 = __dmul_rn(sq, __dsub_rn(1.0, u2)), b2 = __dmul_rn(sq, u2);
     for (int a = 0; a < 3; ++a) p[a] = __dadd_rn(__dadd_rn(v0[a], __dmul_rn(b1, e1[a])), __dmul_rn(b2, e2[a]));
   }
+  // a mixed boundary's Neumann samples stay on the boundary (Sec. 3.2)
+  const double le = (zero_l != nullptr && zero_l[e] != 0) ? 0.0 : l;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    z[a * stride + i] = __double2float_rn(__dsub_rn(p[a], __dmul_rn(l, nn[a])));
+    z[a * stride + i] = __double2float_rn(__dsub_rn(p[a], __dmul_rn(le, nn[a])));
     nrm[a * stride + i] = __double2float_rn(nn[a]);
   }
   if (elem) elem[i] = (int32_t)e;
@@ -304,14 +307,15 @@ namespace bvc {
 // K1 into planes of `stride` floats (a batch writes each mesh's samples into
 // its range of the batch's sample planes).
 bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
-                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev) {
+                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev,
+                                  const uint8_t* zero_l) {
   if (n == 0) return BVC_OK;
   const int grid = (int)((n + 255) / 256);
   ProfScope ps("sample_boundary", s);
   if (g->dim == 2)
-    k_sample_boundary<2><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev);
+    k_sample_boundary<2><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev, zero_l);
   else
-    k_sample_boundary<3><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev);
+    k_sample_boundary<3><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev, zero_l);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }

@@ -108,8 +108,22 @@ bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc
                               double* grad_amp, cudaStream_t s);
 // seed_dev: when non-null, the seed is read from this device word at run
 // time (a captured CUDA graph replays with the seed it holds then).
+// zero_l: when non-null, samples on elements e with zero_l[e] != 0 keep
+// offset 0 (the Neumann part of a mixed boundary).
 bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
-                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev);
+                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev,
+                                  const uint8_t* zero_l = nullptr);
+// Per-start FP64 reduction of walk records (K3).
+struct ReduceParams {
+  const float* rec;
+  int64_t n;       // starts in this launch
+  int32_t W;
+  int32_t planes;  // 1 + extra planes
+  int64_t stride;  // plane stride of rec
+  int32_t mode;    // 0 mean, 1 accumulate sum
+  double* out[4];  // per plane, already offset to the launch's first start
+};
+bvc_status launch_reduce(const ReduceParams& R, cudaStream_t s);
 int max_blocks_per_sm(const void* kernel, int block, size_t smem);
 
 // Kernel timing: while bvc_profile_begin .. bvc_profile_end is active, every

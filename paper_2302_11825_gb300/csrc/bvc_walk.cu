@@ -514,16 +514,6 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
 
 // K3: one warp per start; lanes stride the start's walks, FP64 partials are
 // combined by a fixed xor-shuffle tree (deterministic).
-struct ReduceParams {
-  const float* rec;
-  int64_t n;       // starts in this launch
-  int32_t W;
-  int32_t planes;  // 1 + extra planes
-  int64_t stride;  // plane stride of rec
-  int32_t mode;    // 0 mean, 1 accumulate sum
-  double* out[4];  // per plane, already offset to the launch's first start
-};
-
 __global__ void __launch_bounds__(256) k_reduce(const ReduceParams R) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -604,7 +594,7 @@ static bvc_status launch_first_hits(int dim, const DevGeometry& G, const float* 
   return BVC_OK;
 }
 
-static bvc_status launch_reduce(const ReduceParams& R, cudaStream_t s) {
+bvc_status launch_reduce(const ReduceParams& R, cudaStream_t s) {
   const int64_t warps = R.n;
   int64_t blocks = (warps * 32 + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 16;

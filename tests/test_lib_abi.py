@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "bvc.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b((?:bvc|wos)_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b((?:bvc|wost?)_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -176,3 +176,37 @@ def test_region_clamp_screened_host_checks(lib):
                                   C.c_uint64(0), None, C.c_size_t(0), None) == 1
     lib.bvc_tune_walks_workspace_size.restype = C.c_int
     assert lib.bvc_tune_walks_workspace_size(None, None, None) == 1
+
+
+def test_mixed_host_checks(lib):
+    """Mixed boundaries: argument errors are caught on the host, before any
+    device work (no GPU needed)."""
+    lib.bvc_mixed_create.restype = C.c_int
+    lib.bvc_mixed_create.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]
+    from paper_2302_11825_gb300 import workloads as wl
+    V, F, side = wl.rect_polygon((0, 0), (1, 1), 4)
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    h = C.c_void_p()
+    all_neu = np.ones(F.shape[0], np.uint8)
+    vp, fp = V.ctypes.data_as(C.c_void_p), F.ctypes.data_as(C.c_void_p)
+    # no Dirichlet element: walks could never stop
+    assert lib.bvc_mixed_create(2, vp, V.shape[0], fp, F.shape[0], all_neu.ctypes.data_as(C.c_void_p), None,
+                                C.byref(h)) == 1
+    assert lib.bvc_mixed_create(4, vp, V.shape[0], fp, F.shape[0], all_neu.ctypes.data_as(C.c_void_p), None,
+                                C.byref(h)) == 1
+    assert lib.bvc_mixed_create(2, vp, V.shape[0], fp, F.shape[0], None, None, C.byref(h)) == 1
+    assert lib.bvc_mixed_create(2, vp, V.shape[0], fp, F.shape[0], None, None, None) == 1
+    for name in ("bvc_mixed_destroy", "bvc_mixed_get_info"):
+        fn = getattr(lib, name)
+        fn.restype = C.c_int
+    lib.bvc_mixed_destroy.argtypes = [C.c_void_p]
+    assert lib.bvc_mixed_destroy(None) == 1
+    lib.bvc_mixed_cache_build_workspace_size.restype = C.c_int
+    lib.bvc_mixed_cache_build_workspace_size.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert lib.bvc_mixed_cache_build_workspace_size(None, None, None, None) == 1
+    lib.wost_estimate.restype = C.c_int
+    lib.wost_estimate.argtypes = [C.c_void_p] * 5 + [C.c_int32, C.c_float, C.c_int32, C.c_uint64, C.c_uint64,
+                                                      C.c_void_p, C.c_size_t, C.c_void_p]
+    assert lib.wost_estimate(None, None, None, None, None, 1, 1e-3, 10, 0, 0, None, 0, None) == 1
