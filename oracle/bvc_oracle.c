@@ -1534,6 +1534,8 @@ int orc_num_threads(void) {
 /*           a = 1/2 on the boundary.  Draws: Philox (walk id, step - 1, tag + 8):   */
 /*           u0 picks the element (cumulative measure in element order),    */
 /*           u1, u2 the point (as the boundary sampler places points).      */
+/*           For an x on the Neumann part the element under x is left out  */
+/*           of this choice and sampled around x instead (wost_own_term).   */
 /*   U = g(end) + sum w_u f(y) + sum of the Neumann terms.                   */
 /* A walk that starts inside the domain takes its first step in the ball of */
 /* radius d_all (distance to the whole boundary, no Neumann part inside)    */
@@ -1568,6 +1570,7 @@ typedef struct {
   int64_t n_sil;
   double* sil;        /* per candidate: 2D [v(2) n0(2) n1(2) always], 3D [a(3) b(3) n0(3) n1(3) always] */
   double tau;
+  double diag;        /* bounding-box diagonal */
 } wost_t;
 
 static int sil_stride(int dim) { return dim == 2 ? 7 : 13; }
@@ -1624,6 +1627,7 @@ void* orc_wost_create(int dim, const float* V, int64_t nv, const int32_t* F, int
   double diag = 0.0;
   for (int a = 0; a < dim; ++a) diag += (hi[a] - lo[a]) * (hi[a] - lo[a]);
   w->tau = ldexp(1.0, -18) * (diag > 0.0 ? sqrt(diag) : 1.0);
+  w->diag = sqrt(diag);
   /* silhouette candidates from the elements around each vertex (2D) or    */
   /* edge (3D)                                                              */
   const int ss = sil_stride(dim);
@@ -1779,6 +1783,7 @@ static double wost_sil_dist(const wost_t* w, const double* x) {
 /* lowest element.  Returns the element (or -1) and sets *t_out.             */
 static int ray_elem(const wost_t* w, int64_t e, const double* x, const double* om, double* t_out) {
   const int dim = w->dim;
+  *t_out = -INFINITY;
   const int32_t* f = w->F + e * dim;
   double t;
   if (dim == 2) {
@@ -1819,15 +1824,29 @@ static int ray_elem(const wost_t* w, int64_t e, const double* x, const double* o
   *t_out = t;
   return t > 0.0;
 }
+/* (ray_elem sets *t_out whenever the line meets the element; it returns 1 */
+/* only for t > 0.)                                                         */
 
+/* Only elements the ray leaves the domain through (n . w > 0) count: a ray */
+/* from inside meets such a front face first, and a walker on an edge       */
+/* between two Neumann elements is not stopped by the one it moves away     */
+/* from.  Crossings with t in (-tau, 0] count as crossings at t = 0: that   */
+/* walker, looking out through the other element, does not pass it.        */
 static int64_t wost_ray(const wost_t* w, const double* x, const double* om, double tmax, int64_t skip,
                         double* t_out) {
   double best = INFINITY;
   int64_t be = -1;
   for (int64_t q = 0; q < w->n_neu; ++q) {
     const int64_t e = w->neu_ids[q];
-    double t;
-    if (e == skip || !ray_elem(w, e, x, om, &t)) continue;
+    double t, cs = 0.0;
+    if (e == skip) continue;
+    for (int a = 0; a < w->dim; ++a) cs += w->nrm[e * w->dim + a] * om[a];
+    if (!(cs > 0.0)) continue;
+    const int hit = ray_elem(w, e, x, om, &t);
+    if (!hit) {
+      if (!(t > -w->tau && t <= 0.0)) continue;
+      t = 0.0;
+    }
     if (t <= tmax && (t < best || (t == best && e < be))) {
       best = t;
       be = e;
@@ -1884,6 +1903,8 @@ static double wost_neumann_term(const wost_ctx_t* c, const double* x, int on_n, 
       z[a] = v0 + b1 * (w->V[3 * f[1] + a] - v0) + b2 * (w->V[3 * f[2] + a] - v0);
     }
   }
+  /* the element under an on-boundary x is covered by wost_own_term */
+  if (on_n && pick == self) return 0.0;
   double r2 = 0.0, dir[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) {
     dir[a] = z[a] - x[a];
@@ -1907,6 +1928,73 @@ static double wost_neumann_term(const wost_ctx_t* c, const double* x, int on_n, 
   return inv_a * gb * orc_neumann_eval(c->hv, c->hp, dim, z, w->nrm + pick * dim) * total;
 }
 
+/* The Neumann term over the element under an on-boundary x, sampled      */
+/* around x inside the element, where G^B is singular (a uniform point     */
+/* would give the 3D term infinite variance): 2D a side (u0 < 1/2: towards */
+/* b) and rho = u1 rho_max, rho_max = min(R, distance to that end); 3D a   */
+/* direction theta = 2 pi u0 in the element's plane (e1 = (b - a)/|b - a|,  */
+/* e2 = n x e1) and rho = u1 rho_max, rho_max = min(R, distance to the     */
+/* triangle's border along it).  1/pdf = 2 rho_max (2D), 2 pi rho rho_max   */
+/* (3D); the term is (1/a) G^B(rho) h(z) / pdf with a = 1/2.  Draws:       */
+/* Philox (walk id, step - 1, tag + 12).                                    */
+static double wost_own_term(const wost_ctx_t* c, const double* x, int64_t self, double R, uint64_t wid,
+                            uint32_t step) {
+  const wost_t* w = c->w;
+  const int dim = w->dim;
+  double u[4];
+  draw(c->seed, wid, step, c->tag + 12u, u);
+  const int32_t* f = w->F + self * dim;
+  const double* n = w->nrm + self * dim;
+  double z[3] = {0, 0, 0}, rmax, rho;
+  if (dim == 2) {
+    const double* a = w->V + 2 * (int64_t)f[0];
+    const double* b = w->V + 2 * (int64_t)f[1];
+    const double len = sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]));
+    const double t[2] = {(b[0] - a[0]) / len, (b[1] - a[1]) / len};
+    double sx = (x[0] - a[0]) * t[0] + (x[1] - a[1]) * t[1];
+    sx = fmin(fmax(sx, 0.0), len);
+    const double sgn = u[0] < 0.5 ? 1.0 : -1.0;
+    rmax = fmin(R, sgn > 0.0 ? len - sx : sx);
+    if (!(rmax > 0.0)) return 0.0;
+    rho = u[1] * rmax;
+    for (int k = 0; k < 2; ++k) z[k] = x[k] + sgn * rho * t[k];
+    return 2.0 * (log(R / rho) / (2.0 * ORC_PI)) * orc_neumann_eval(c->hv, c->hp, dim, z, n) * 2.0 * rmax;
+  }
+  const double* P[3] = {w->V + 3 * (int64_t)f[0], w->V + 3 * (int64_t)f[1], w->V + 3 * (int64_t)f[2]};
+  double e1[3], e2[3], d[3];
+  double l1 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = P[1][k] - P[0][k];
+    l1 += e1[k] * e1[k];
+  }
+  l1 = sqrt(l1);
+  for (int k = 0; k < 3; ++k) e1[k] /= l1;
+  e2[0] = n[1] * e1[2] - n[2] * e1[1];
+  e2[1] = n[2] * e1[0] - n[0] * e1[2];
+  e2[2] = n[0] * e1[1] - n[1] * e1[0];
+  const double th = 2.0 * ORC_PI * u[0];
+  for (int k = 0; k < 3; ++k) d[k] = cos(th) * e1[k] + sin(th) * e2[k];
+  rmax = R;
+  for (int j = 0; j < 3; ++j) {
+    const double* p = P[j];
+    const double* q = P[(j + 1) % 3];
+    const double pq[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
+    /* in-plane normal of the edge pointing into the triangle */
+    const double m[3] = {n[1] * pq[2] - n[2] * pq[1], n[2] * pq[0] - n[0] * pq[2], n[0] * pq[1] - n[1] * pq[0]};
+    const double dm = dot3d(d, m);
+    if (dm < 0.0) {
+      const double xp[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+      const double lim = dot3d(xp, m) / -dm;
+      if (lim < rmax) rmax = lim;
+    }
+  }
+  if (!(rmax > 0.0)) return 0.0;
+  rho = u[1] * rmax;
+  for (int k = 0; k < 3; ++k) z[k] = x[k] + rho * d[k];
+  return 2.0 * ((1.0 / rho - 1.0 / R) / (4.0 * ORC_PI)) * orc_neumann_eval(c->hv, c->hp, dim, z, n) *
+         (2.0 * ORC_PI * rho * rmax);
+}
+
 static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uint64_t wid, double* U_out,
                           double* grad_out, int32_t* steps_out, int32_t* prim_out) {
   const wost_t* w = c->w;
@@ -1924,6 +2012,7 @@ static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uin
   for (;;) {
     const double dD = sqrt(bvh_closest((const obvh_t*)w->dir, x, pbar, &prim));
     ++k;
+    if (!(dD <= 4.0 * w->diag)) break; /* escaped through a rounding gap: capped */
     if (k == 1) cv = orc_fn_eval(c->g, dim, pbar);
     if (dD < c->eps || k >= c->max_steps) break;
     double u[4];
@@ -1967,14 +2056,17 @@ static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uin
     double th;
     const int64_t eh = wost_ray(w, x, om, R, on_n ? self : -1, &th);
     const double r = eh >= 0 ? th : R;
-    if (has_f) {
+    if (has_f && r > 0.0) { /* a crossing at t = 0 leaves no segment */
       const double rr = r * u[2];
       double y[3] = {0, 0, 0};
       for (int a = 0; a < dim; ++a) y[a] = x[a] + rr * om[a];
       const double wsrc = dim == 2 ? -r * rr * log(R / rr) : -r * rr * (1.0 - rr / R);
       acc += wsrc * orc_fn_eval(c->f, dim, y);
     }
-    if (has_h) acc += wost_neumann_term(c, x, on_n, self, R, wid, (uint32_t)(k - 1));
+    if (has_h) {
+      acc += wost_neumann_term(c, x, on_n, self, R, wid, (uint32_t)(k - 1));
+      if (on_n) acc += wost_own_term(c, x, self, R, wid, (uint32_t)(k - 1));
+    }
     if (eh >= 0) {
       for (int a = 0; a < dim; ++a) {
         x[a] += th * om[a];

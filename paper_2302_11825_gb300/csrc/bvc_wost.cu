@@ -50,6 +50,7 @@ struct bvc_mixed_s {
   const int32_t* neu_local;  // whole element -> Neumann element or -1
   const uint8_t* flags;      // whole element: 1 Neumann
   const float2* nmeas;       // Neumann tree: (left, right) subtree measures per node
+  const int32_t* neu_q;      // Neumann element -> tree position
 };
 
 namespace bvc {
@@ -81,6 +82,8 @@ struct WostParams {
   const int32_t* neu_local;
   const int32_t* dir_ids;
   const float2* nmeas;  // Neumann tree: subtree measures of each node's children
+  const int32_t* neu_q;  // Neumann element -> its position in the Neumann tree's primitive order
+  float escape;         // 4 x bounding-box diagonal: a walk farther from the Dirichlet part has escaped
   unsigned long long* stats;
   unsigned long long* counter;
 };
@@ -89,10 +92,11 @@ struct WostParams {
 // Closest silhouette point of the Neumann part seen from x, if nearer than
 // sqrt(best2): returns min(best2, its squared distance).
 template <int D>
-__device__ float sil_closest(const DevSil& S, const float* x, float best2, int* snode, float* sdist) {
+__device__ float sil_closest(const DevSil& S, const float* x, float best2, int* snode, float* sdist, TravCount& tcn) {
   if (S.n == 0) return best2;
   int sp = 0, node = 0;
   for (int guard = 0; guard < (1 << 22); ++guard) {
+    ++tcn.nodes;
     int32_t ch[2];
     float dc[2];
     if (D == 2) {
@@ -117,6 +121,7 @@ __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* 
       if (go[k] && ch[k] < 0) {
         const int32_t enc = ~ch[k];
         const int32_t first = enc >> 4, count = enc & 15;
+        tcn.prims += (uint32_t)count;
         for (int32_t q = first; q < first + count; ++q) {
           float ax, ay, az = 0.0f, d0, d1, d2;
           bool always;
@@ -181,10 +186,10 @@ __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* 
 }
 
 // Entry parameter of the ray o + t w into a box (inv = 1/w with zero
-// components replaced by +-1e20), or +inf when it misses within [0, tmax].
+// components replaced by +-1e20), or +inf when it misses within [tmin, tmax].
 __device__ __forceinline__ float slab(const float* lo, const float* hi, const float* o, const float* inv, int D,
-                                      float tmax) {
-  float tn = 0.0f, tf = tmax;
+                                      float tmin, float tmax) {
+  float tn = tmin, tf = tmax;
   for (int a = 0; a < D; ++a) {
     const float t0 = (lo[a] - o[a]) * inv[a], t1 = (hi[a] - o[a]) * inv[a];
     tn = fmaxf(tn, fminf(t0, t1));
@@ -201,9 +206,15 @@ __device__ __forceinline__ float slab(const float* lo, const float* hi, const fl
 // not crossings -- a walker on a flat wall looks along it, and a rounded
 // near-parallel test there would report a crossing anywhere along the wall.
 constexpr float kGraze = 1e-4f;
+// Walk rays (VIS false) only cross elements they leave the domain through
+// (n . w > 0): a ray from inside meets a front face first, and a walker on an
+// edge between two Neumann elements must not be stopped by the element it
+// moves away from.  tmin (<= 0): crossings with t in (tmin, 0] count as
+// crossings at t = 0 -- that walker, looking out through the other element,
+// must not pass it.
 template <int D, bool VIS = false>
 __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, float tmax, int skip, int skip2,
-                         float& t_out, float* n, int* snode, float* sdist) {
+                         float tmin, float& t_out, float* n, int* snode, float* sdist, TravCount& tcn) {
   float inv[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -214,14 +225,15 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
   int bid = 0x7fffffff, bq = -1;
   int sp = 0, node = 0;
   for (int guard = 0; guard < (1 << 22); ++guard) {
+    ++tcn.nodes;
     int32_t ch[2];
     float tc[2];
     if (D == 2) {
       const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
       const float4 C = __ldg(&G.nodes[3 * node + 2]);
       const float llo[2] = {L.x, L.y}, lhi[2] = {L.z, L.w}, rlo[2] = {R.x, R.y}, rhi[2] = {R.z, R.w};
-      tc[0] = slab(llo, lhi, o, inv, 2, best);
-      tc[1] = slab(rlo, rhi, o, inv, 2, best);
+      tc[0] = slab(llo, lhi, o, inv, 2, tmin, best);
+      tc[1] = slab(rlo, rhi, o, inv, 2, tmin, best);
       ch[0] = __float_as_int(C.x);
       ch[1] = __float_as_int(C.y);
     } else {
@@ -229,8 +241,8 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
       const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
       const float llo[3] = {a.x, a.y, a.z}, lhi[3] = {a.w, b.x, b.y}, rlo[3] = {b.z, b.w, c.x},
                   rhi[3] = {c.y, c.z, c.w};
-      tc[0] = slab(llo, lhi, o, inv, 3, best);
-      tc[1] = slab(rlo, rhi, o, inv, 3, best);
+      tc[0] = slab(llo, lhi, o, inv, 3, tmin, best);
+      tc[1] = slab(rlo, rhi, o, inv, 3, tmin, best);
       ch[0] = __float_as_int(e.x);
       ch[1] = __float_as_int(e.y);
     }
@@ -241,6 +253,7 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
       if (go[k] && ch[k] < 0) {
         const int32_t enc = ~ch[k];
         const int32_t first = enc >> 4, count = enc & 15;
+        tcn.prims += (uint32_t)count;
         for (int32_t q = first; q < first + count; ++q) {
           float tt;
           int id;
@@ -250,6 +263,8 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
             const float den = fmaf(w[0], Sg.w, -w[1] * Sg.z);
             if (id == skip || id == skip2 || den == 0.0f) continue;
             if (VIS && fabsf(den) * sqrtf(T.x) < kGraze) continue;
+            // walk rays leave the domain through front faces only (n . w > 0)
+            if (!VIS && !(den > 0.0f)) continue;
             const float qx = Sg.x - o[0], qy = Sg.y - o[1];
             const float s = fmaf(qx, w[1], -qy * w[0]) / den;
             if (!(s >= -kRayInfl && s <= 1.0f + kRayInfl)) continue;
@@ -264,6 +279,8 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
             const float Pz = fmaf(w[0], Cc.y, -w[1] * Cc.x);
             const float det = fmaf(B.z, Pz, fmaf(B.y, Py, B.x * Px));
             if (det == 0.0f) continue;
+            // walk rays leave the domain through front faces only: det = -(n . w) |ab x ac|
+            if (!VIS && !(det < 0.0f)) continue;
             if (VIS) {
               const float cx = fmaf(B.y, Cc.z, -B.z * Cc.y), cy = fmaf(B.z, Cc.x, -B.x * Cc.z);
               const float cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
@@ -280,7 +297,8 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
             if (!(v >= -kRayInfl && u + v <= 1.0f + kRayInfl)) continue;
             tt = fmaf(Cc.z, Qz, fmaf(Cc.y, Qy, Cc.x * Qx)) * idet;
           }
-          if (tt > 0.0f && (tt < best || (tt == best && id < bid))) {
+          tt = tt > 0.0f ? tt : (tt > tmin ? 0.0f : -1.0f);
+          if (tt >= 0.0f && (tt < best || (tt == best && id < bid))) {
             best = tt;
             bid = id;
             bq = q;
@@ -345,12 +363,13 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
 // z, w the point.  Returns false when no subtree reaches into the ball.
 template <int D>
 __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ nm, const float* x, float R,
-                               const U4 r, float* z, float* nz, int& id, float& ipdf) {
+                               const U4 r, float* z, float* nz, int& id, float& ipdf, TravCount& tcn) {
   double u = ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6) + 0.5) * (1.0 / 9007199254740992.0);
   double pdf = 1.0;
   const float R2 = R * R;
   int node = 0;
   for (int depth = 0; depth < 64; ++depth) {
+    ++tcn.nodes;
     int32_t ch[2];
     float dc[2];
     if (D == 2) {
@@ -397,6 +416,7 @@ __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ 
       const float cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
       return 0.5f * sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
     };
+    tcn.prims += (uint32_t)count;
     float tot = 0.0f;
     for (int32_t q = first; q < first + count; ++q) tot += elem_measure(q);
     if (!(tot > 0.0f)) return false;
@@ -439,6 +459,76 @@ __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ 
   return false;
 }
 
+// The Neumann term over the element under an on-boundary x (Neumann id
+// self at tree position q), sampled around x inside the element, where G^B
+// is singular: 2D a side (u0 < 1/2: towards b) and rho = u1 rho_max with
+// rho_max = min(R, distance to that end); 3D a direction theta = 2 pi u0 in
+// the element's plane (e1 = ab / |ab|, e2 = n x e1) and rho = u1 rho_max,
+// rho_max = min(R, distance to the triangle's border along it).  Returns the
+// point, the element normal and 1/pdf (2 rho_max in 2D, 2 pi rho rho_max in
+// 3D), or false when x is not inside the element.
+template <int D>
+__device__ bool sample_own(const DevGeometry& G, int q, const float* x, float R, float u0, float u1, float* z,
+                           float* nz, float& rho, float& ipdf) {
+  if (D == 2) {
+    const float4 S = __ldg(&G.prims[2 * q]), T = __ldg(&G.prims[2 * q + 1]);
+    const float il = sqrtf(T.x), len = 1.0f / il;
+    const float tx = S.z * il, ty = S.w * il;
+    float sx = fmaf(x[D - 1] - S.y, ty, (x[0] - S.x) * tx);
+    sx = fminf(fmaxf(sx, 0.0f), len);
+    const float sg = u0 < 0.5f ? 1.0f : -1.0f;
+    const float rmax = fminf(R, sg > 0.0f ? len - sx : sx);
+    if (!(rmax > 0.0f)) return false;
+    rho = u1 * rmax;
+    z[0] = fmaf(sg * rho, tx, x[0]);
+    z[D - 1] = fmaf(sg * rho, ty, x[D - 1]);
+    nz[0] = ty;
+    nz[D - 1] = -tx;
+    ipdf = 2.0f * rmax;
+    return true;
+  } else {
+    const float4 A = __ldg(&G.prims[3 * q]), B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
+    float n[3] = {fmaf(B.y, Cc.z, -B.z * Cc.y), fmaf(B.z, Cc.x, -B.x * Cc.z), fmaf(B.x, Cc.y, -B.y * Cc.x)};
+    const float inn = rsqrtf(fmaf(n[2], n[2], fmaf(n[1], n[1], n[0] * n[0])));
+    const float il1 = rsqrtf(fmaf(B.z, B.z, fmaf(B.y, B.y, B.x * B.x)));
+    float e1[3] = {B.x * il1, B.y * il1, B.z * il1};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n[k] *= inn;
+    const float e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
+    float sn, cs;
+    sincospif(2.0f * u0, &sn, &cs);
+    float d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = fmaf(cs, e1[k], sn * e2[k]);
+    // vertices relative to x, and the in-plane inward normals of the edges
+    const float P[3][3] = {{A.x - x[0], A.y - x[1], A.z - x[D - 1]},
+                           {A.x + B.x - x[0], A.y + B.y - x[1], A.z + B.z - x[D - 1]},
+                           {A.x + Cc.x - x[0], A.y + Cc.y - x[1], A.z + Cc.z - x[D - 1]}};
+    float rmax = R;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int jn = j == 2 ? 0 : j + 1;
+      const float pq[3] = {P[jn][0] - P[j][0], P[jn][1] - P[j][1], P[jn][2] - P[j][2]};
+      const float m[3] = {n[1] * pq[2] - n[2] * pq[1], n[2] * pq[0] - n[0] * pq[2], n[0] * pq[1] - n[1] * pq[0]};
+      const float dm = fmaf(d[2], m[2], fmaf(d[1], m[1], d[0] * m[0]));
+      if (dm < 0.0f) {
+        // (x - p) . m over -(d . m), with x - p = -P[j]
+        const float lim = -fmaf(P[j][2], m[2], fmaf(P[j][1], m[1], P[j][0] * m[0])) / -dm;
+        rmax = fminf(rmax, lim);
+      }
+    }
+    if (!(rmax > 0.0f)) return false;
+    rho = u1 * rmax;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      z[k < D ? k : 0] = fmaf(rho, d[k], x[k < D ? k : 0]);
+      nz[k < D ? k : 0] = n[k];
+    }
+    ipdf = 2.0f * kPiF * rho * rmax;
+    return true;
+  }
+}
+
 template <int D>
 __device__ __forceinline__ float neumann_h(const DevFunction& hv, const DevFunction& hp, const float* z,
                                            const float* n) {
@@ -467,7 +557,7 @@ __global__ void __launch_bounds__(128) k_mixed_query(DevGeometry Gd, DevSil S, c
     bvh_closest<D>(Gd, p, h, snode + threadIdx.x, sdist + threadIdx.x, kWostBlock, tc);
     if (d_dir) d_dir[i] = sqrtf(h.d2);
     if (d_sil) d_sil[i] = sqrtf(sil_closest<D>(S, p, __int_as_float(0x7f800000), snode + threadIdx.x,
-                                               sdist + threadIdx.x));
+                                               sdist + threadIdx.x, tc));
   }
 }
 
@@ -487,8 +577,11 @@ __global__ void __launch_bounds__(128) k_mixed_rays(DevGeometry Gn, int32_t has_
     }
     float t = __int_as_float(0x7f800000);
     int e = -1;
-    if (has_neu)
-      e = ray_first<D>(Gn, o, w, tmax, skip ? skip[i] : -1, -1, t, n, snode + threadIdx.x, sdist + threadIdx.x);
+    if (has_neu) {
+      TravCount tc{0, 0};
+      e = ray_first<D>(Gn, o, w, tmax, skip ? skip[i] : -1, -1, -Gn.tau, t, n, snode + threadIdx.x,
+                       sdist + threadIdx.x, tc);
+    }
     t_out[i] = t;
     e_out[i] = e;
   }
@@ -505,6 +598,7 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   unsigned long long my_steps = 0, my_capped = 0;
+  TravCount tc{0, 0};  // node fetches and primitive tests of every query
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(P.counter, 32ull);
@@ -523,7 +617,7 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
       int self = -1;
       if (P.start_elem != nullptr && P.has_neu) {
         const int32_t e0 = P.start_elem[i];
-        if (e0 >= 0) {
+        if (e0 >= 0 && e0 < P.Ga.n_prims) {
           const int32_t nl = P.neu_local[e0];
           if (nl >= 0) {
             on_n = true;
@@ -539,12 +633,12 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
       Hit<D> h;
       bool reached = false;
       for (;;) {
-        TravCount tc{0, 0};
-        bvh_closest<D>(P.Gd, x, h, sn, sd, kWostBlock, tc);
+        bvh_closest<D, true>(P.Gd, x, h, sn, sd, kWostBlock, tc);
 #pragma unroll
         for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
         const float dD = sqrtf(h.d2);
         ++k;
+        if (!(dD <= P.escape)) break;  // left the domain through a rounding gap: capped
         if (k == 1) cv = eval_fn<D, true>(P.g, pbar);  // control variate of the gradient
         if (dD < P.eps) {
           reached = true;
@@ -571,7 +665,7 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
         }
         if (k == 1 && !on_n) {
           Hit<D> ha;
-          bvh_closest<D>(P.Ga, x, ha, sn, sd, kWostBlock, tc);
+          bvh_closest<D, true>(P.Ga, x, ha, sn, sd, kWostBlock, tc);
           const float dA = sqrtf(ha.d2);
           if (dA >= P.eps) {
             // the gradient ball B(x, d_all): no boundary inside
@@ -610,12 +704,12 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
         int eh = -1;
         float th = 0.0f, nh[D];
         if (P.has_neu) {
-          R = sqrtf(sil_closest<D>(P.S, x, h.d2, sn, sd));
+          R = sqrtf(sil_closest<D>(P.S, x, h.d2, sn, sd, tc));
           R = fmaxf(R, P.eps);
-          eh = ray_first<D>(P.Gn, x, om, R, on_n ? self : -1, -1, th, nh, sn, sd);
+          eh = ray_first<D>(P.Gn, x, om, R, on_n ? self : -1, -1, -P.Gn.tau, th, nh, sn, sd, tc);
         }
         const float rl = eh >= 0 ? th : R;
-        if (HAS_F) {
+        if (HAS_F && rl > 0.0f) {  // a crossing at t = 0 leaves no segment
           const float rho = rl * u2;
           float y[D];
 #pragma unroll
@@ -623,12 +717,13 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
           const float wu = D == 2 ? rl * rho * __logf(rho / R) : -rl * rho * (1.0f - rho / R);
           acc = fmaf(wu, eval_fn<D, true>(P.f, y), acc);
         }
-        if (HAS_H) {
+        if (HAS_H && P.has_neu) {
           // area-sampled Neumann term over the part inside B(x, R)
           const U4 r2 = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag + 8u);
           float z[D], nz[D], ipdf;
           int ez;
-          if (sample_neumann<D>(P.Gn, P.nmeas, x, R, r2, z, nz, ez, ipdf)) {
+          // the element under an on-boundary x: sampled around x below
+          if (sample_neumann<D>(P.Gn, P.nmeas, x, R, r2, z, nz, ez, ipdf, tc) && !(on_n && ez == self)) {
             float dz[D], r2z = 0.0f;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -641,12 +736,21 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
 #pragma unroll
               for (int a = 0; a < D; ++a) dz[a] *= ir;
               float tv, nv[D];
-              const int ev = ray_first<D, true>(P.Gn, x, dz, rz * (1.0f - 1e-5f), on_n ? self : -1, ez, tv, nv, sn, sd);
+              const int ev =
+                  ray_first<D, true>(P.Gn, x, dz, rz * (1.0f - 1e-5f), on_n ? self : -1, ez, 0.0f, tv, nv, sn, sd, tc);
               if (ev < 0) {
                 // G^B of -Laplacian: ln(R/r)/(2 pi) (2D), (1/r - 1/R)/(4 pi) (3D)
                 const float gb = D == 2 ? __logf(R * ir) * (0.5f / kPiF) : (ir - 1.0f / R) * (0.25f / kPiF);
                 acc = fmaf((on_n ? 2.0f : 1.0f) * gb * ipdf, neumann_h<D>(P.hv, P.hp, z, nz), acc);
               }
+            }
+          }
+          if (on_n) {
+            const U4 r3 = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag + 12u);
+            float rho;
+            if (sample_own<D>(P.Gn, P.neu_q[self], x, R, u01f(r3.x), u01f(r3.y), z, nz, rho, ipdf)) {
+              const float gb = D == 2 ? __logf(R / rho) * (0.5f / kPiF) : (1.0f / rho - 1.0f / R) * (0.25f / kPiF);
+              acc = fmaf(2.0f * gb * ipdf, neumann_h<D>(P.hv, P.hp, z, nz), acc);
             }
           }
         }
@@ -698,14 +802,19 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
       if (!reached) ++my_capped;
     }
   }
+  unsigned long long my_nodes = tc.nodes, my_prims = tc.prims;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     my_steps += __shfl_xor_sync(FULL, my_steps, o);
     my_capped += __shfl_xor_sync(FULL, my_capped, o);
+    my_nodes += __shfl_xor_sync(FULL, my_nodes, o);
+    my_prims += __shfl_xor_sync(FULL, my_prims, o);
   }
   if (lane == 0) {
     if (my_steps) atomicAdd(&P.stats[kStatSteps], my_steps);
     if (my_capped) atomicAdd(&P.stats[kStatCapped], my_capped);
+    if (my_nodes) atomicAdd(&P.stats[kStatNodes], my_nodes);
+    if (my_prims) atomicAdd(&P.stats[kStatPrims], my_prims);
   }
 }
 
@@ -830,6 +939,12 @@ static bool fill_params(bvc_mixed m, const bvc_function* gfn, const bvc_neumann*
   P.neu_local = m->neu_local;
   P.dir_ids = m->dir_ids;
   P.nmeas = m->nmeas;
+  P.neu_q = m->neu_q;
+  {
+    double d2 = 0.0;
+    for (int a = 0; a < m->dim; ++a) d2 += ((double)m->whole->hi[a] - m->whole->lo[a]) * (m->whole->hi[a] - m->whole->lo[a]);
+    P.escape = (float)(4.0 * std::sqrt(d2));
+  }
   P.stats = m->whole->dev.stats;
   const int D = m->dim;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return false;
@@ -889,10 +1004,13 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   // subtree measures of the Neumann tree (the same deterministic build as
   // the Neumann geometry's), for the area sampling of the Neumann term
   std::vector<float2> nmeas;
+  std::vector<int32_t> nq;
   if (nn > 0) {
     std::vector<float4> nnodes, nprims;
     std::vector<int32_t> nids;
     const int64_t nnod = build_bvh(dim, verts, fn.data(), nn, nnodes, nprims, nids);
+    nq.assign(nn, 0);
+    for (int64_t q = 0; q < nn; ++q) nq[nids[q]] = (int32_t)q;
     const int per = dim == 2 ? 3 : 4;
     std::vector<double> em(nn);
     for (int64_t q = 0; q < nn; ++q) {
@@ -961,8 +1079,8 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   m->n_sil_nodes = ns > 0 ? (int64_t)snodes.size() / (dim == 2 ? 3 : 4) : 0;
   const size_t b_nodes = al256(snodes.size() * sizeof(float4)), b_prims = al256(sprims.size() * sizeof(float4));
   const size_t b_dir = al256((size_t)nd * 4), b_loc = al256((size_t)n_prims * 4), b_flag = al256((size_t)n_prims);
-  const size_t b_nm = al256(nmeas.size() * sizeof(float2));
-  m->arena_bytes = b_nodes + b_prims + b_dir + b_loc + b_flag + b_nm;
+  const size_t b_nm = al256(nmeas.size() * sizeof(float2)), b_nq = al256(nq.size() * 4);
+  m->arena_bytes = b_nodes + b_prims + b_dir + b_loc + b_flag + b_nm + b_nq;
   if (cudaMalloc(&m->arena, m->arena_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     m->arena = nullptr;
@@ -975,6 +1093,7 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   m->neu_local = (const int32_t*)(base += b_dir);
   m->flags = (const uint8_t*)(base += b_loc);
   m->nmeas = (const float2*)(base += b_flag);
+  m->neu_q = (const int32_t*)(base += b_nm);
   m->sil.n = ns;
   m->sil.tau = m->whole->dev.tau;
   cudaStream_t s = (cudaStream_t)stream;
@@ -995,6 +1114,8 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   if (!nmeas.empty())
     ok = ok && cudaMemcpyAsync((void*)m->nmeas, nmeas.data(), nmeas.size() * sizeof(float2), cudaMemcpyHostToDevice,
                                s) == cudaSuccess;
+  if (!nq.empty())
+    ok = ok && cudaMemcpyAsync((void*)m->neu_q, nq.data(), nq.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2302_11825_gb300 import workloads as wl
+from tests.oracle_pipeline import mixed_pipeline
 
 P = wl.POLY
 
@@ -185,26 +186,6 @@ def test_neumann_data_is_the_normal_derivative():
         d = 1e-5
         fd = (oracle.fn_eval(terms, dim, z + d * n) - oracle.fn_eval(terms, dim, z - d * n)) / (2 * d)
         np.testing.assert_allclose(h, 0.25 + fd, rtol=1e-7, atol=1e-7)
-
-
-def mixed_pipeline(V, F, neu, u, f, N, W, l, eps, seed, pts):
-    """The mixed cache (Sec. 3.2) with the oracle: samples on the Neumann
-    part keep offset 0 and carry du/dn = h; Dirichlet samples move by -l n
-    and carry walk estimates of u and du/dn; Eq. 3 at the points."""
-    dim = V.shape[1]
-    w = oracle.Wost(V, F, neu)
-    z, n, e = oracle.sample_boundary_mixed(V, F, N, l, seed, neu)
-    on_n = neu[e] == 1
-    se = np.where(on_n, e, -1).astype(np.int32)
-    o = w.walks(u, [], u, f, z.astype(np.float32), se, W, eps, 1 << 16, seed)
-    u_hat = o["U"].reshape(N, W).mean(1)
-    q_walk = np.einsum("iwd,id->i", o["grad"].reshape(N, W, dim), n) / W
-    h = oracle.neumann_eval([], u, dim, z.astype(np.float32).astype(np.float64), n.astype(np.float32)
-                            .astype(np.float64))
-    q_hat = np.where(on_n, h, q_walk)
-    ub, _, gb, _ = oracle.gather(z.astype(np.float32), n.astype(np.float32), u_hat, q_hat,
-                                 oracle.boundary_measure(V, F), pts)
-    return ub / N, gb / N, (z, n, e, u_hat, q_hat)
 
 
 def test_mixed_cache_square_closed_form():
