@@ -32,9 +32,43 @@ int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::ve
 struct DevSil {
   const float4* nodes;
   const float4* prims;
+  // per node, per child: a cone (axis.xyz, half-angle) holding the normals of
+  // every candidate below (half-angle pi: some candidate is unconditional)
+  const float4* cones;
   int64_t n;
   float tau;  // |n_k . a| <= tau counts as zero
 };
+
+// True when no candidate inside the box [lo, hi] under a normal cone can be a
+// silhouette seen from x: with psi the angle between the cone axis and the
+// direction to the box centre, phi the half-angle the box's bounding sphere
+// subtends and theta the cone's half-angle, every n . (p - x) has one sign
+// and magnitude above tau when psi + theta + phi < pi/2 (all positive) or
+// psi - theta - phi > pi/2 (all negative) (triangle inequality on angles).
+template <int D>
+__device__ __forceinline__ bool cone_prunes(const float4 cone, const float* lo, const float* hi, const float* x,
+                                            float tau) {
+  if (!(cone.w < 1.5707f)) return false;
+  float d[3] = {0.0f, 0.0f, 0.0f}, rb2 = 0.0f, dd = 0.0f, ad = 0.0f;
+  const float ax[3] = {cone.x, cone.y, cone.z};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const float h = 0.5f * (hi[a] - lo[a]);
+    d[a] = 0.5f * (hi[a] + lo[a]) - x[a];
+    rb2 = fmaf(h, h, rb2);
+    dd = fmaf(d[a], d[a], dd);
+    ad = fmaf(ax[a], d[a], ad);
+  }
+  const float dist = sqrtf(dd), rb = sqrtf(rb2);
+  if (!(dist > rb)) return false;
+  const float phi = asinf(rb / dist);
+  const float psi = acosf(fminf(fmaxf(ad / dist, -1.0f), 1.0f));
+  const float dmin = dist - rb;
+  const float s1 = psi + cone.w + phi, s2 = psi - cone.w - phi;
+  if (s1 < 1.5707f && cosf(s1) * dmin > tau) return true;
+  if (s2 > 1.5709f && -cosf(s2) * dmin > tau) return true;
+  return false;
+}
 
 }  // namespace bvc
 
@@ -98,7 +132,7 @@ __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* 
   for (int guard = 0; guard < (1 << 22); ++guard) {
     ++tcn.nodes;
     int32_t ch[2];
-    float dc[2];
+    float dc[2], blo[2][3], bhi[2][3];
     if (D == 2) {
       const float4 L = __ldg(&S.nodes[3 * node]), R = __ldg(&S.nodes[3 * node + 1]);
       const float4 C = __ldg(&S.nodes[3 * node + 2]);
@@ -106,6 +140,8 @@ __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* 
       dc[1] = box_d2_2(R.x, R.y, R.z, R.w, x);
       ch[0] = __float_as_int(C.x);
       ch[1] = __float_as_int(C.y);
+      blo[0][0] = L.x, blo[0][1] = L.y, bhi[0][0] = L.z, bhi[0][1] = L.w;
+      blo[1][0] = R.x, blo[1][1] = R.y, bhi[1][0] = R.z, bhi[1][1] = R.w;
     } else {
       const float4 a = __ldg(&S.nodes[4 * node]), b = __ldg(&S.nodes[4 * node + 1]);
       const float4 c = __ldg(&S.nodes[4 * node + 2]), e = __ldg(&S.nodes[4 * node + 3]);
@@ -113,11 +149,13 @@ __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* 
       dc[1] = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, x);
       ch[0] = __float_as_int(e.x);
       ch[1] = __float_as_int(e.y);
+      blo[0][0] = a.x, blo[0][1] = a.y, blo[0][2] = a.z, bhi[0][0] = a.w, bhi[0][1] = b.x, bhi[0][2] = b.y;
+      blo[1][0] = b.z, blo[1][1] = b.w, blo[1][2] = c.x, bhi[1][0] = c.y, bhi[1][1] = c.z, bhi[1][2] = c.w;
     }
     bool go[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      go[k] = dc[k] < best2;
+      go[k] = dc[k] < best2 && !cone_prunes<D>(__ldg(&S.cones[2 * node + k]), blo[k], bhi[k], x, S.tau);
       if (go[k] && ch[k] < 0) {
         const int32_t enc = ~ch[k];
         const int32_t first = enc >> 4, count = enc & 15;
@@ -588,7 +626,9 @@ __global__ void __launch_bounds__(128) k_mixed_rays(DevGeometry Gn, int32_t has_
 }
 
 // ------------------------------------------------------------ the walk
-// One walk per lane; warps take 32 walks at a time from a work counter.
+// One walk per lane, advanced one step per loop iteration; a lane whose walk
+// ends takes the next walk at once (the warp's idle lanes share one atomic
+// on the work counter), so long walks do not idle the rest of the warp.
 template <int D, bool HAS_F, bool HAS_H, int REC>
 __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
   __shared__ int snode[kWStack * kWostBlock];
@@ -599,104 +639,130 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
   const int lane = threadIdx.x & 31;
   unsigned long long my_steps = 0, my_capped = 0;
   TravCount tc{0, 0};  // node fetches and primitive tests of every query
+  bool active = false, more = true;
+  // walk state
+  int64_t t = 0, i = 0;
+  float x[D], nx[D], nu[D], pbar[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) x[a] = nx[a] = nu[a] = pbar[a] = 0.0f;
+  bool on_n = false, start_on_n = false;
+  int self = -1, k = 0;
+  float acc = 0.0f, wf0 = 0.0f, wg0 = 0.0f, R0 = 0.0f, cv = 0.0f;
+  Hit<D> h;
   for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(P.counter, 32ull);
-    base = __shfl_sync(FULL, base, 0);
-    if ((int64_t)base >= P.total) break;
-    const int64_t t = (int64_t)base + lane;
-    if (t < P.total) {
-      const int64_t r = t / P.W, i = P.i0 + r;
-      float x[D], nx[D], nu[D], pbar[D];
+    // ---- idle lanes take the next walks
+    const unsigned need = __ballot_sync(FULL, !active);
+    if (need != 0u && more) {
+      const unsigned nneed = (unsigned)__popc(need);
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)nneed);
+      base = __shfl_sync(FULL, base, 0);
+      if ((int64_t)(base + nneed) >= P.total) more = false;
+      if (!active) {
+        const int64_t tt = (int64_t)base + __popc(need & ((1u << lane) - 1u));
+        if (tt < P.total) {
+          active = true;
+          t = tt;
+          i = P.i0 + t / P.W;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        x[a] = P.starts[a * P.pt_stride + i];
-        nx[a] = nu[a] = pbar[a] = 0.0f;
+          for (int a = 0; a < D; ++a) {
+            x[a] = P.starts[a * P.pt_stride + i];
+            nx[a] = nu[a] = 0.0f;
+          }
+          on_n = false;
+          self = -1;
+          if (P.start_elem != nullptr && P.has_neu) {
+            const int32_t e0 = P.start_elem[i];
+            if (e0 >= 0 && e0 < P.Ga.n_prims) {
+              const int32_t nl = P.neu_local[e0];
+              if (nl >= 0) {
+                on_n = true;
+                self = nl;
+#pragma unroll
+                for (int a = 0; a < D; ++a) nx[a] = P.nrm[a * P.pt_stride + i];
+              }
+            }
+          }
+          start_on_n = on_n;
+          acc = wf0 = wg0 = R0 = cv = 0.0f;
+          k = 0;
+        }
       }
-      bool on_n = false;
-      int self = -1;
-      if (P.start_elem != nullptr && P.has_neu) {
-        const int32_t e0 = P.start_elem[i];
-        if (e0 >= 0 && e0 < P.Ga.n_prims) {
-          const int32_t nl = P.neu_local[e0];
-          if (nl >= 0) {
-            on_n = true;
-            self = nl;
+    }
+    if (__ballot_sync(FULL, active) == 0u) break;
+    if (!active) continue;
+    // ---- one step of this lane's walk
+    bvh_closest<D, true>(P.Gd, x, h, sn, sd, kWostBlock, tc);
 #pragma unroll
-            for (int a = 0; a < D; ++a) nx[a] = P.nrm[a * P.pt_stride + i];
+    for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
+    const float dD = sqrtf(h.d2);
+    ++k;
+    bool done = false, reached = false;
+    if (!(dD <= P.escape)) {
+      done = true;  // left the domain through a rounding gap: capped
+    } else {
+      if (k == 1) cv = eval_fn<D, true>(P.g, pbar);  // control variate of the gradient
+      if (dD < P.eps) {
+        done = reached = true;
+      } else if (k >= P.max_steps) {
+        done = true;
+      }
+    }
+    if (!done) {
+      const U4 rr = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
+      const float u0 = u01f(rr.x), u2 = u01f(rr.z);
+      float om[D];
+      if (D == 2) {
+        float sn2, cs;
+        sincospif(2.0f * u0, &sn2, &cs);
+        om[0] = cs;
+        om[D - 1] = sn2;
+      } else {
+        const float u1 = u01f(rr.y);
+        const float zc = 1.0f - 2.0f * u0;
+        const float st = 2.0f * sqrtf(u0 * (1.0f - u0));
+        float sn2, cs;
+        sincospif(2.0f * u1, &sn2, &cs);
+        om[0] = st * cs;
+        om[1] = st * sn2;
+        om[D - 1] = zc;
+      }
+      bool ball = false;
+      if (k == 1 && !on_n) {
+        Hit<D> ha;
+        bvh_closest<D, true>(P.Ga, x, ha, sn, sd, kWostBlock, tc);
+        const float dA = sqrtf(ha.d2);
+        if (dA >= P.eps) {
+          // the gradient ball B(x, d_all): no boundary inside
+          ball = true;
+          const float R = dA;
+          if (HAS_F) {
+            const float rho = R * u2;
+            float y[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
+            const float fy = eval_fn<D, true>(P.f, y);
+            const float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho);
+            acc = fmaf(wu, fy, acc);
+            wf0 = wu * fy;
+            const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
+            wg0 = -R * (1.0f - q) * fy;
+          }
+          R0 = R;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            nu[a] = om[a];
+            x[a] = fmaf(R, om[a], x[a]);
           }
         }
       }
-      const bool start_on_n = on_n;
-      float acc = 0.0f, wf0 = 0.0f, wg0 = 0.0f, R0 = 0.0f, cv = 0.0f;
-      int k = 0;
-      Hit<D> h;
-      bool reached = false;
-      for (;;) {
-        bvh_closest<D, true>(P.Gd, x, h, sn, sd, kWostBlock, tc);
-#pragma unroll
-        for (int a = 0; a < D; ++a) pbar[a] = x[a] - h.df[a];
-        const float dD = sqrtf(h.d2);
-        ++k;
-        if (!(dD <= P.escape)) break;  // left the domain through a rounding gap: capped
-        if (k == 1) cv = eval_fn<D, true>(P.g, pbar);  // control variate of the gradient
-        if (dD < P.eps) {
-          reached = true;
-          break;
-        }
-        if (k >= P.max_steps) break;
-        const U4 rr = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag);
-        const float u0 = u01f(rr.x), u2 = u01f(rr.z);
-        float om[D];
-        if (D == 2) {
-          float sn2, cs;
-          sincospif(2.0f * u0, &sn2, &cs);
-          om[0] = cs;
-          om[D - 1] = sn2;
-        } else {
-          const float u1 = u01f(rr.y);
-          const float zc = 1.0f - 2.0f * u0;
-          const float st = 2.0f * sqrtf(u0 * (1.0f - u0));
-          float sn2, cs;
-          sincospif(2.0f * u1, &sn2, &cs);
-          om[0] = st * cs;
-          om[1] = st * sn2;
-          om[D - 1] = zc;
-        }
-        if (k == 1 && !on_n) {
-          Hit<D> ha;
-          bvh_closest<D, true>(P.Ga, x, ha, sn, sd, kWostBlock, tc);
-          const float dA = sqrtf(ha.d2);
-          if (dA >= P.eps) {
-            // the gradient ball B(x, d_all): no boundary inside
-            const float R = dA;
-            if (HAS_F) {
-              const float rho = R * u2;
-              float y[D];
-#pragma unroll
-              for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
-              const float fy = eval_fn<D, true>(P.f, y);
-              const float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho);
-              acc = fmaf(wu, fy, acc);
-              wf0 = wu * fy;
-              const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
-              wg0 = -R * (1.0f - q) * fy;
-            }
-            R0 = R;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-              nu[a] = om[a];
-              x[a] = fmaf(R, om[a], x[a]);
-            }
-            continue;
-          }
-        }
+      if (!ball) {
         // star step
         if (on_n) {
-          float s = 0.0f;
+          float sdot = 0.0f;
 #pragma unroll
-          for (int a = 0; a < D; ++a) s = fmaf(nx[a], om[a], s);
-          if (s > 0.0f)
+          for (int a = 0; a < D; ++a) sdot = fmaf(nx[a], om[a], sdot);
+          if (sdot > 0.0f)
 #pragma unroll
             for (int a = 0; a < D; ++a) om[a] = -om[a];
         }
@@ -755,12 +821,9 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
           }
         }
         if (eh >= 0) {
-          float z[D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) z[a] = fmaf(th, om[a], x[a]);
 #pragma unroll
           for (int a = 0; a < D; ++a) {
-            x[a] = z[a];
+            x[a] = fmaf(th, om[a], x[a]);
             nx[a] = nh[a];
           }
           on_n = true;
@@ -772,35 +835,38 @@ __global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
           self = -1;
         }
       }
-      const float U = eval_fn<D, true>(P.g, pbar) + acc;
-      const float sc = R0 > 0.0f ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
-      P.rec[t] = U;
-      if (REC == kRecGnW) {
-        float v;
-        if (start_on_n) {
-          float z0[D], n0[D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            z0[a] = P.starts[a * P.pt_stride + i];
-            n0[a] = P.nrm[a * P.pt_stride + i];
-          }
-          v = neumann_h<D>(P.hv, P.hp, z0, n0);
-        } else {
-          float nn2 = 0.0f;
-#pragma unroll
-          for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn2);
-          v = sc * nn2;
-        }
-        P.rec[P.total + t] = v;
-      } else {
-#pragma unroll
-        for (int a = 0; a < D; ++a) P.rec[(1 + a) * P.total + t] = sc * nu[a];
-      }
-      if (P.steps) P.steps[t] = k;
-      if (P.prim) P.prim[t] = h.id >= 0 && h.id < 0x7fffffff ? P.dir_ids[h.id] : -1;
-      my_steps += (unsigned long long)k;
-      if (!reached) ++my_capped;
+      continue;
     }
+    // ---- the walk ended: its records
+    const float U = eval_fn<D, true>(P.g, pbar) + acc;
+    const float sc = R0 > 0.0f ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
+    P.rec[t] = U;
+    if (REC == kRecGnW) {
+      float v;
+      if (start_on_n) {
+        float z0[D], n0[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          z0[a] = P.starts[a * P.pt_stride + i];
+          n0[a] = P.nrm[a * P.pt_stride + i];
+        }
+        v = neumann_h<D>(P.hv, P.hp, z0, n0);
+      } else {
+        float nn2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn2);
+        v = sc * nn2;
+      }
+      P.rec[P.total + t] = v;
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a) P.rec[(1 + a) * P.total + t] = sc * nu[a];
+    }
+    if (P.steps) P.steps[t] = k;
+    if (P.prim) P.prim[t] = h.id >= 0 && h.id < 0x7fffffff ? P.dir_ids[h.id] : -1;
+    my_steps += (unsigned long long)k;
+    if (!reached) ++my_capped;
+    active = false;
   }
   unsigned long long my_nodes = tc.nodes, my_prims = tc.prims;
 #pragma unroll
@@ -927,6 +993,43 @@ static std::vector<SilCand> silhouette_candidates(int dim, int64_t n_verts, cons
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Normal cones of the silhouette tree: a cone (unit axis, half-angle)
+// holding a set of unit normals; half-angles from pi/2 up are useless for
+// pruning and stored as "full" (pi).
+struct Cone {
+  double a[3];
+  double th;
+};
+static const double kFullCone = 3.14159265358979323846;
+
+static Cone cone_merge(const Cone& c1, const Cone& c2) {
+  if (c1.th >= kFullCone) return c1;
+  if (c2.th >= kFullCone) return c2;
+  double ca = c1.a[0] * c2.a[0] + c1.a[1] * c2.a[1] + c1.a[2] * c2.a[2];
+  ca = std::min(1.0, std::max(-1.0, ca));
+  const double al = std::acos(ca);
+  if (al + c2.th <= c1.th) return c1;
+  if (al + c1.th <= c2.th) return c2;
+  Cone r;
+  r.th = 0.5 * (al + c1.th + c2.th);
+  if (r.th >= 0.5 * kFullCone - 1e-6) {
+    r.a[0] = r.a[1] = r.a[2] = 0.0;
+    r.th = kFullCone;
+    return r;
+  }
+  // rotate c1's axis towards c2's by th - th1 (spherical interpolation)
+  const double t = (r.th - c1.th) / al, sa = std::sin(al);
+  const double w1 = std::sin((1.0 - t) * al) / sa, w2 = std::sin(t * al) / sa;
+  double nn = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    r.a[k] = w1 * c1.a[k] + w2 * c2.a[k];
+    nn += r.a[k] * r.a[k];
+  }
+  nn = std::sqrt(nn);
+  for (int k = 0; k < 3; ++k) r.a[k] /= nn;
+  return r;
+}
 
 static bool fill_params(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
                         WostParams& P) {
@@ -1077,10 +1180,49 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   }
   m->n_sil = ns;
   m->n_sil_nodes = ns > 0 ? (int64_t)snodes.size() / (dim == 2 ? 3 : 4) : 0;
+  // per node and child, the cone of the normals of the candidates below
+  std::vector<float4> scones((size_t)m->n_sil_nodes * 2, make_float4(0, 0, 0, (float)kFullCone));
+  if (ns > 0) {
+    const int per = dim == 2 ? 3 : 4;
+    auto cand_cone = [&](int64_t q) {
+      const SilCand& c = cand[ids[q]];
+      Cone r{{0, 0, 0}, kFullCone};
+      if (c.always) return r;
+      double n0[3] = {0, 0, 0}, n1[3] = {0, 0, 0};
+      elem_normal(dim, verts, prims + (int64_t)c.e0 * dim, n0);
+      elem_normal(dim, verts, prims + (int64_t)c.e1 * dim, n1);
+      Cone c0{{n0[0], n0[1], n0[2]}, 0.0}, c1{{n1[0], n1[1], n1[2]}, 0.0};
+      return cone_merge(c0, c1);
+    };
+    std::vector<Cone> sub(m->n_sil_nodes);
+    for (int64_t i = m->n_sil_nodes - 1; i >= 0; --i) {
+      const float4 cc = snodes[i * per + per - 1];
+      int32_t ch[2];
+      std::memcpy(&ch[0], &cc.x, 4);
+      std::memcpy(&ch[1], &cc.y, 4);
+      Cone k2[2];
+      for (int k = 0; k < 2; ++k) {
+        if (ch[k] >= 0) {
+          k2[k] = sub[ch[k]];
+        } else {
+          const int32_t enc = ~ch[k];
+          const int32_t first = enc >> 4, count = enc & 15;
+          Cone r{{0, 0, 0}, -1.0};
+          for (int32_t q = first; q < first + count; ++q) r = r.th < 0.0 ? cand_cone(q) : cone_merge(r, cand_cone(q));
+          k2[k] = r.th < 0.0 ? Cone{{0, 0, 0}, 0.0} : r;
+        }
+        // a little slack for the FP32 normals and axis
+        scones[2 * i + k] = make_float4((float)k2[k].a[0], (float)k2[k].a[1], (float)k2[k].a[2],
+                                        k2[k].th >= kFullCone ? (float)kFullCone : (float)(k2[k].th + 1e-4));
+      }
+      sub[i] = cone_merge(k2[0], k2[1]);
+    }
+  }
   const size_t b_nodes = al256(snodes.size() * sizeof(float4)), b_prims = al256(sprims.size() * sizeof(float4));
   const size_t b_dir = al256((size_t)nd * 4), b_loc = al256((size_t)n_prims * 4), b_flag = al256((size_t)n_prims);
   const size_t b_nm = al256(nmeas.size() * sizeof(float2)), b_nq = al256(nq.size() * 4);
-  m->arena_bytes = b_nodes + b_prims + b_dir + b_loc + b_flag + b_nm + b_nq;
+  const size_t b_cone = al256(scones.size() * sizeof(float4));
+  m->arena_bytes = b_nodes + b_prims + b_dir + b_loc + b_flag + b_nm + b_nq + b_cone;
   if (cudaMalloc(&m->arena, m->arena_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     m->arena = nullptr;
@@ -1094,6 +1236,7 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   m->flags = (const uint8_t*)(base += b_loc);
   m->nmeas = (const float2*)(base += b_flag);
   m->neu_q = (const int32_t*)(base += b_nm);
+  m->sil.cones = (const float4*)(base += b_nq);
   m->sil.n = ns;
   m->sil.tau = m->whole->dev.tau;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1116,6 +1259,9 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
                                s) == cudaSuccess;
   if (!nq.empty())
     ok = ok && cudaMemcpyAsync((void*)m->neu_q, nq.data(), nq.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  if (!scones.empty())
+    ok = ok && cudaMemcpyAsync((void*)m->sil.cones, scones.data(), scones.size() * sizeof(float4),
+                               cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();
