@@ -173,6 +173,7 @@ KERNEL_FILES = {
     "gather_source": ["bvc_gather.cu", "bvc_device.cuh", "bvc_internal.h"],
     "gather_multi": ["bvc_gather.cu", "bvc_device.cuh", "bvc_internal.h", "bvc_walk.cu"],
     "source_classify": ["bvc_source.cu", "bvc_device.cuh", "bvc_internal.h"],
+    "wost_walk": ["bvc_wost.cu", "bvc_device.cuh", "bvc_internal.h", "bvh_build.cpp"],
 }
 
 
@@ -1013,7 +1014,7 @@ def bench_mixed(args, rank, local, ws):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     rank, ws = init_dist("nccl")
-    w = wl.star_mixed(seed=0)
+    w = wl.star_mixed(seed=0, n_samples=args.samples or 65536)
     s = MixedSolver(w, device)
     M = s.m_far + s.m_near
     dim = w.dim
@@ -1137,6 +1138,8 @@ def main():
                     choices=["star", "circle", "sphere", "batched", "inverse", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed-rmse", action="store_true")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="mixed workload only: boundary samples (default: the workload's 65536)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, local, ws = dist_env()

@@ -397,13 +397,24 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
 // in the leaf an element by its measure, on the element a uniform point
 // (2D a + s ab; 3D barycentrics (1 - sqrt u1, sqrt u1 (1 - u2), sqrt u1 u2)).
 // Every Neumann point inside the ball has positive density; ipdf = 1/pdf(z).
-// Draw words: x, y a 53-bit uniform for the descent (rescaled per choice),
-// z, w the point.  Returns false when no subtree reaches into the ball.
+// Draw words: x, y seed one uniform per level of the descent (and the leaf's
+// element choice) through an integer hash, z, w place the point.  Returns
+// false when no subtree reaches into the ball.
 template <int D>
 __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ nm, const float* x, float R,
                                const U4 r, float* z, float* nz, int& id, float& ipdf, TravCount& tcn) {
-  double u = ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6) + 0.5) * (1.0 / 9007199254740992.0);
-  double pdf = 1.0;
+  // a fresh uniform per level: an integer hash of (r.x, r.y, level)
+  // (xor-shift-multiply rounds, constants of C. Wellons' "lowbias32")
+  auto level_u = [&](uint32_t lv) {
+    uint32_t v = r.x ^ (r.y + 0x9e3779b9u * (lv + 1u));
+    v ^= v >> 16;
+    v *= 0x7feb352du;
+    v ^= v >> 15;
+    v *= 0x846ca68bu;
+    v ^= v >> 16;
+    return u01f(v);
+  };
+  float pdf = 1.0f;
   const float R2 = R * R;
   int node = 0;
   for (int depth = 0; depth < 64; ++depth) {
@@ -426,20 +437,11 @@ __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ 
       ch[1] = __float_as_int(e.y);
     }
     const float2 m = __ldg(&nm[node]);
-    const double w0 = dc[0] < R2 ? (double)m.x : 0.0, w1 = dc[1] < R2 ? (double)m.y : 0.0;
-    if (!(w0 + w1 > 0.0)) return false;
-    const double p0 = w0 / (w0 + w1);
-    int pick;
-    if (u < p0) {
-      pick = 0;
-      u = u / p0;
-      pdf *= p0;
-    } else {
-      pick = 1;
-      u = (u - p0) / (1.0 - p0);
-      pdf *= 1.0 - p0;
-    }
-    u = fmin(fmax(u, 0.0), 0.99999999999999989);
+    const float w0 = dc[0] < R2 ? m.x : 0.0f, w1 = dc[1] < R2 ? m.y : 0.0f;
+    if (!(w0 + w1 > 0.0f)) return false;
+    const float p0 = w0 / (w0 + w1);
+    const int pick = level_u((uint32_t)depth) < p0 ? 0 : 1;
+    pdf *= pick == 0 ? p0 : 1.0f - p0;
     if (ch[pick] >= 0) {
       node = ch[pick];
       continue;
@@ -458,7 +460,7 @@ __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ 
     float tot = 0.0f;
     for (int32_t q = first; q < first + count; ++q) tot += elem_measure(q);
     if (!(tot > 0.0f)) return false;
-    const float target = (float)u * tot;
+    const float target = level_u(63u) * tot;
     float run = 0.0f;
     int32_t qs = first + count - 1;
     for (int32_t q = first; q < first + count; ++q) {
@@ -469,7 +471,7 @@ __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ 
       }
     }
     // pdf(z) = (descent probability) x (m_e / tot) x (1 / m_e)
-    ipdf = (float)((double)tot / pdf);
+    ipdf = tot / pdf;
     const float s1 = u01f(r.z), s2 = u01f(r.w);
     if (D == 2) {
       const float4 S = __ldg(&G.prims[2 * qs]), T = __ldg(&G.prims[2 * qs + 1]);
@@ -629,8 +631,13 @@ __global__ void __launch_bounds__(128) k_mixed_rays(DevGeometry Gn, int32_t has_
 // One walk per lane, advanced one step per loop iteration; a lane whose walk
 // ends takes the next walk at once (the warp's idle lanes share one atomic
 // on the work counter), so long walks do not idle the rest of the warp.
+// Resident blocks per SM the walk-on-stars kernel is compiled for (measured
+// best on GB300 for the 20k-segment mixed star: 4).
+#ifndef BVC_WOST_MINB
+#define BVC_WOST_MINB 4
+#endif
 template <int D, bool HAS_F, bool HAS_H, int REC>
-__global__ void __launch_bounds__(kWostBlock) k_wost(const WostParams P) {
+__global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostParams P) {
   __shared__ int snode[kWStack * kWostBlock];
   __shared__ float sdist[kWStack * kWostBlock];
   int* const sn = snode + threadIdx.x;
