@@ -32,8 +32,8 @@ int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::ve
 struct DevSil {
   const float4* nodes;
   const float4* prims;
-  // per node, per child: a cone (axis.xyz, half-angle) holding the normals of
-  // every candidate below (half-angle pi: some candidate is unconditional)
+  // per node, per child: a cone (axis.xyz, cos half-angle) holding the normals
+  // of every candidate below (cos <= 0: no bound, e.g. an unconditional one)
   const float4* cones;
   int64_t n;
   float tau;  // |n_k . a| <= tau counts as zero
@@ -45,10 +45,12 @@ struct DevSil {
 // subtends and theta the cone's half-angle, every n . (p - x) has one sign
 // and magnitude above tau when psi + theta + phi < pi/2 (all positive) or
 // psi - theta - phi > pi/2 (all negative) (triangle inequality on angles).
+// The cone is (axis, cos theta), cos theta <= 0 meaning no bound; the angle
+// sums are formed with the addition formulas (no inverse trigonometry).
 template <int D>
 __device__ __forceinline__ bool cone_prunes(const float4 cone, const float* lo, const float* hi, const float* x,
                                             float tau) {
-  if (!(cone.w < 1.5707f)) return false;
+  if (!(cone.w > 0.0f)) return false;
   float d[3] = {0.0f, 0.0f, 0.0f}, rb2 = 0.0f, dd = 0.0f, ad = 0.0f;
   const float ax[3] = {cone.x, cone.y, cone.z};
 #pragma unroll
@@ -59,14 +61,19 @@ __device__ __forceinline__ bool cone_prunes(const float4 cone, const float* lo, 
     dd = fmaf(d[a], d[a], dd);
     ad = fmaf(ax[a], d[a], ad);
   }
-  const float dist = sqrtf(dd), rb = sqrtf(rb2);
-  if (!(dist > rb)) return false;
-  const float phi = asinf(rb / dist);
-  const float psi = acosf(fminf(fmaxf(ad / dist, -1.0f), 1.0f));
-  const float dmin = dist - rb;
-  const float s1 = psi + cone.w + phi, s2 = psi - cone.w - phi;
-  if (s1 < 1.5707f && cosf(s1) * dmin > tau) return true;
-  if (s2 > 1.5709f && -cosf(s2) * dmin > tau) return true;
+  if (!(dd > rb2)) return false;
+  const float idist = rsqrtf(dd), dist = dd * idist;
+  const float sphi = sqrtf(rb2) * idist, cphi = sqrtf(fmaxf(1.0f - sphi * sphi, 0.0f));
+  const float cth = cone.w, sth = sqrtf(fmaxf(1.0f - cth * cth, 0.0f));
+  // alpha = theta + phi
+  const float ca = cth * cphi - sth * sphi, sa = sth * cphi + cth * sphi;
+  if (!(ca > 0.0f)) return false;  // theta + phi >= pi/2: the cone spans too much
+  const float cpsi = fminf(fmaxf(ad * idist, -1.0f), 1.0f), spsi = sqrtf(fmaxf(1.0f - cpsi * cpsi, 0.0f));
+  const float dmin = dist - sqrtf(rb2);
+  // psi + alpha < pi/2  <=>  cos psi > sin alpha; margin cos(psi + alpha)
+  if (cpsi > sa && (cpsi * ca - spsi * sa) * dmin > tau) return true;
+  // psi - alpha > pi/2  <=>  cos psi < -sin alpha; margin -cos(psi - alpha)
+  if (cpsi < -sa && -(cpsi * ca + spsi * sa) * dmin > tau) return true;
   return false;
 }
 
@@ -1188,7 +1195,7 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   m->n_sil = ns;
   m->n_sil_nodes = ns > 0 ? (int64_t)snodes.size() / (dim == 2 ? 3 : 4) : 0;
   // per node and child, the cone of the normals of the candidates below
-  std::vector<float4> scones((size_t)m->n_sil_nodes * 2, make_float4(0, 0, 0, (float)kFullCone));
+  std::vector<float4> scones((size_t)m->n_sil_nodes * 2, make_float4(0, 0, 0, -1.0f));
   if (ns > 0) {
     const int per = dim == 2 ? 3 : 4;
     auto cand_cone = [&](int64_t q) {
@@ -1218,9 +1225,11 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
           for (int32_t q = first; q < first + count; ++q) r = r.th < 0.0 ? cand_cone(q) : cone_merge(r, cand_cone(q));
           k2[k] = r.th < 0.0 ? Cone{{0, 0, 0}, 0.0} : r;
         }
-        // a little slack for the FP32 normals and axis
+        // (axis, cos theta) with a little slack for the FP32 normals and axis;
+        // cos theta <= 0: no bound
+        const double th = k2[k].th + 1e-4;
         scones[2 * i + k] = make_float4((float)k2[k].a[0], (float)k2[k].a[1], (float)k2[k].a[2],
-                                        k2[k].th >= kFullCone ? (float)kFullCone : (float)(k2[k].th + 1e-4));
+                                        th >= 0.5 * kFullCone ? -1.0f : (float)std::cos(th));
       }
       sub[i] = cone_merge(k2[0], k2[1]);
     }
