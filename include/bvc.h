@@ -562,8 +562,8 @@ bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_function* gfn, 
  * gradient is 0.  Silhouettes: a Neumann vertex (2D) or edge (3D) between
  * two Neumann elements with outward normals n0, n1 is one when, with
  * a = (vertex or edge start) - x and d_k = n_k . a (zero when
- * |d_k| <= 2^-18 x bounding-box diagonal), exactly one d_k is zero or both
- * are non-zero with opposite signs; one with one or more than two Neumann
+ * |d_k| <= 2^-18 x bounding-box diagonal), one d_k is zero and the other
+ * negative, or both are non-zero with opposite signs; one with one or more than two Neumann
  * elements (and no Dirichlet element) always is; one touching a Dirichlet
  * element is skipped (d_D covers it).  Draws: Philox(walk id, step - 1, tag)
  * as bvc_walk. */

@@ -1548,8 +1548,9 @@ int orc_num_threads(void) {
 /* Silhouettes: a Neumann vertex (2D) or edge (3D) shared by two Neumann    */
 /* elements with outward normals n0, n1; with a = (vertex or the edge's     */
 /* first vertex) - x and d_k = n_k . a, treated as zero when |d_k| <= tau,  */
-/* it is a silhouette when exactly one d_k is zero or both are non-zero     */
-/* with opposite signs.  Vertices or edges with one or more than two        */
+/* it is a silhouette when one d_k is zero and the other negative (the      */
+/* element seen edge-on, its neighbour facing away: a reflex vertex or      */
+/* edge) or both are non-zero with opposite signs.  Vertices or edges with one or more than two        */
 /* Neumann elements and no Dirichlet element are always silhouettes; those  */
 /* touching a Dirichlet element are skipped (never closer than d_D).        */
 /* tau = 2^-18 x the bounding-box diagonal.  All queries are brute force.   */
@@ -1762,7 +1763,8 @@ static double wost_sil_dist(const wost_t* w, const double* x) {
         d1 += n1[k] * a[k];
       }
       const int z0 = fabs(d0) <= w->tau, z1 = fabs(d1) <= w->tau;
-      is_sil = (z0 != z1) || (!z0 && !z1 && ((d0 > 0.0) != (d1 > 0.0)));
+      /* one element edge-on (zero): a silhouette when the other faces away */
+      is_sil = (z0 && !z1 && d1 < 0.0) || (z1 && !z0 && d0 < 0.0) || (!z0 && !z1 && ((d0 > 0.0) != (d1 > 0.0)));
     }
     if (!is_sil) continue;
     double d2;

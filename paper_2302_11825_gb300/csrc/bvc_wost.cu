@@ -195,7 +195,9 @@ __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* 
             d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
           }
           const bool z0 = fabsf(d0) <= S.tau, z1 = fabsf(d1) <= S.tau;
-          const bool sil = always || (z0 != z1) || (!z0 && !z1 && ((d0 > 0.0f) != (d1 > 0.0f)));
+          // one element edge-on (zero): a silhouette when the other faces away
+          const bool sil = always || (z0 && !z1 && d1 < 0.0f) || (z1 && !z0 && d0 < 0.0f) ||
+                           (!z0 && !z1 && ((d0 > 0.0f) != (d1 > 0.0f)));
           if (sil && d2 < best2) best2 = d2;
         }
         go[k] = false;

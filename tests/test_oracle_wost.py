@@ -148,6 +148,36 @@ def test_star_radius_sees_each_neumann_crossing_once():
     assert twice > 0
 
 
+def test_star_radius_from_the_neumann_boundary():
+    # walkers on a Neumann element (inward hemisphere): no ray crosses the rest
+    # of the Neumann part twice inside B(x, min(d_D, d_sil)), and on the flat
+    # sides away from corners the radius is not pinned to the element size
+    V, F = wl.l_shape_polygon(16)
+    mid = wl.element_midpoints(V, F)
+    neu = (mid[:, 0] > -1 + 1e-6).astype(np.uint8)
+    w = oracle.Wost(V, F, neu)
+    rng = np.random.default_rng(8)
+    ids = np.where(neu == 1)[0]
+    els = rng.choice(ids, 60, replace=False)
+    lam = rng.uniform(0.1, 0.9, els.size)
+    x = V[F[els, 0]] + lam[:, None] * (V[F[els, 1]] - V[F[els, 0]])
+    n = np.stack([V[F[els, 1], 1] - V[F[els, 0], 1], V[F[els, 0], 0] - V[F[els, 1], 0]], 1).astype(np.float64)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    dd, ds = w.query(x.astype(np.float64))
+    R = np.minimum(dd, ds)
+    seg = 1.0 / 16
+    assert np.median(R) > 2.0 * seg
+    th = 2.0 * np.pi * (np.arange(96) + 0.5) / 96
+    for k in range(els.size):
+        Fn = F[(neu == 1) & (np.arange(F.shape[0]) != els[k])]
+        for t in th:
+            om = np.array([np.cos(t), np.sin(t)])
+            if om @ n[k] >= 0.0:
+                continue
+            tt, _, _ = oracle.ray_hits(V, Fn, 0.0, x[k], om, R[k] * (1.0 - 1e-9))
+            assert tt.size <= 1
+
+
 def test_first_crossing_matches_an_independent_ray_caster():
     V, F = wl.l_shape_polygon(8)
     mid = wl.element_midpoints(V, F)
