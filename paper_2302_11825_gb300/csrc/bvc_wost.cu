@@ -130,105 +130,114 @@ struct WostParams {
 };
 
 // -------------------------------------------------------------- queries
+// Each query is a traversal written as "visit one node" (state: node, stack
+// depth sp, the running best) plus a loop over it.  Stacks live in shared
+// memory, entry e of a lane at [e * kWostBlock].
+
+// Closest silhouette: one node.  best2 is lowered to the squared distance of
+// any nearer silhouette; children are skipped by distance or by their cone.
+template <int D>
+__device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float& best2, int& node, int& sp,
+                                          int* snode, float* sdist, TravCount& tcn) {
+  ++tcn.nodes;
+  int32_t ch[2];
+  float dc[2], blo[2][3], bhi[2][3];
+  if (D == 2) {
+    const float4 L = __ldg(&S.nodes[3 * node]), R = __ldg(&S.nodes[3 * node + 1]);
+    const float4 C = __ldg(&S.nodes[3 * node + 2]);
+    dc[0] = box_d2_2(L.x, L.y, L.z, L.w, x);
+    dc[1] = box_d2_2(R.x, R.y, R.z, R.w, x);
+    ch[0] = __float_as_int(C.x);
+    ch[1] = __float_as_int(C.y);
+    blo[0][0] = L.x, blo[0][1] = L.y, bhi[0][0] = L.z, bhi[0][1] = L.w;
+    blo[1][0] = R.x, blo[1][1] = R.y, bhi[1][0] = R.z, bhi[1][1] = R.w;
+  } else {
+    const float4 a = __ldg(&S.nodes[4 * node]), b = __ldg(&S.nodes[4 * node + 1]);
+    const float4 c = __ldg(&S.nodes[4 * node + 2]), e = __ldg(&S.nodes[4 * node + 3]);
+    dc[0] = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, x);
+    dc[1] = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, x);
+    ch[0] = __float_as_int(e.x);
+    ch[1] = __float_as_int(e.y);
+    blo[0][0] = a.x, blo[0][1] = a.y, blo[0][2] = a.z, bhi[0][0] = a.w, bhi[0][1] = b.x, bhi[0][2] = b.y;
+    blo[1][0] = b.z, blo[1][1] = b.w, blo[1][2] = c.x, bhi[1][0] = c.y, bhi[1][1] = c.z, bhi[1][2] = c.w;
+  }
+  bool go[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    go[k] = dc[k] < best2 && !cone_prunes<D>(__ldg(&S.cones[2 * node + k]), blo[k], bhi[k], x, S.tau);
+    if (go[k] && ch[k] < 0) {
+      const int32_t enc = ~ch[k];
+      const int32_t first = enc >> 4, count = enc & 15;
+      tcn.prims += (uint32_t)count;
+      for (int32_t q = first; q < first + count; ++q) {
+        float ax, ay, az = 0.0f, d0, d1, d2;
+        bool always;
+        if (D == 2) {
+          const float4 A = __ldg(&S.prims[2 * q]), B = __ldg(&S.prims[2 * q + 1]);
+          ax = A.x - x[0];
+          ay = A.y - x[1];
+          d0 = fmaf(A.w, ay, A.z * ax);
+          d1 = fmaf(B.y, ay, B.x * ax);
+          always = B.z != 0.0f;
+          d2 = fmaf(ay, ay, ax * ax);
+        } else {
+          const float4 A = __ldg(&S.prims[4 * q]), B = __ldg(&S.prims[4 * q + 1]);
+          const float4 N0 = __ldg(&S.prims[4 * q + 2]), N1 = __ldg(&S.prims[4 * q + 3]);
+          ax = A.x - x[0];
+          ay = A.y - x[1];
+          az = A.z - x[D - 1];
+          d0 = fmaf(N0.z, az, fmaf(N0.y, ay, N0.x * ax));
+          d1 = fmaf(N1.z, az, fmaf(N1.y, ay, N1.x * ax));
+          always = A.w != 0.0f;
+          // distance to the edge a + s ab, s in [0, 1]
+          const float px = -ax, py = -ay, pz = -az;
+          float s = fmaf(B.z, pz, fmaf(B.y, py, B.x * px)) * B.w;
+          s = fminf(fmaxf(s, 0.0f), 1.0f);
+          const float ex = fmaf(-s, B.x, px), ey = fmaf(-s, B.y, py), ez = fmaf(-s, B.z, pz);
+          d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        }
+        const bool z0 = fabsf(d0) <= S.tau, z1 = fabsf(d1) <= S.tau;
+        // one element edge-on (zero): a silhouette when the other faces away
+        const bool sil = always || (z0 && !z1 && d1 < 0.0f) || (z1 && !z0 && d0 < 0.0f) ||
+                         (!z0 && !z1 && ((d0 > 0.0f) != (d1 > 0.0f)));
+        if (sil && d2 < best2) best2 = d2;
+      }
+      go[k] = false;
+    }
+  }
+  // re-test against the bound a leaf may have lowered
+  go[0] = go[0] && dc[0] < best2;
+  go[1] = go[1] && dc[1] < best2;
+  if (go[0] && go[1]) {
+    const int nearer = dc[1] < dc[0] ? 1 : 0;
+    snode[sp * kWostBlock] = ch[1 - nearer];
+    sdist[sp * kWostBlock] = dc[1 - nearer];
+    ++sp;
+    node = ch[nearer];
+    return false;
+  }
+  if (go[0] || go[1]) {
+    node = go[0] ? ch[0] : ch[1];
+    return false;
+  }
+  while (sp > 0) {
+    --sp;
+    if (sdist[sp * kWostBlock] < best2) {
+      node = snode[sp * kWostBlock];
+      return false;
+    }
+  }
+  return true;
+}
+
 // Closest silhouette point of the Neumann part seen from x, if nearer than
 // sqrt(best2): returns min(best2, its squared distance).
 template <int D>
 __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* snode, float* sdist, TravCount& tcn) {
   if (S.n == 0) return best2;
   int sp = 0, node = 0;
-  for (int guard = 0; guard < (1 << 22); ++guard) {
-    ++tcn.nodes;
-    int32_t ch[2];
-    float dc[2], blo[2][3], bhi[2][3];
-    if (D == 2) {
-      const float4 L = __ldg(&S.nodes[3 * node]), R = __ldg(&S.nodes[3 * node + 1]);
-      const float4 C = __ldg(&S.nodes[3 * node + 2]);
-      dc[0] = box_d2_2(L.x, L.y, L.z, L.w, x);
-      dc[1] = box_d2_2(R.x, R.y, R.z, R.w, x);
-      ch[0] = __float_as_int(C.x);
-      ch[1] = __float_as_int(C.y);
-      blo[0][0] = L.x, blo[0][1] = L.y, bhi[0][0] = L.z, bhi[0][1] = L.w;
-      blo[1][0] = R.x, blo[1][1] = R.y, bhi[1][0] = R.z, bhi[1][1] = R.w;
-    } else {
-      const float4 a = __ldg(&S.nodes[4 * node]), b = __ldg(&S.nodes[4 * node + 1]);
-      const float4 c = __ldg(&S.nodes[4 * node + 2]), e = __ldg(&S.nodes[4 * node + 3]);
-      dc[0] = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, x);
-      dc[1] = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, x);
-      ch[0] = __float_as_int(e.x);
-      ch[1] = __float_as_int(e.y);
-      blo[0][0] = a.x, blo[0][1] = a.y, blo[0][2] = a.z, bhi[0][0] = a.w, bhi[0][1] = b.x, bhi[0][2] = b.y;
-      blo[1][0] = b.z, blo[1][1] = b.w, blo[1][2] = c.x, bhi[1][0] = c.y, bhi[1][1] = c.z, bhi[1][2] = c.w;
-    }
-    bool go[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      go[k] = dc[k] < best2 && !cone_prunes<D>(__ldg(&S.cones[2 * node + k]), blo[k], bhi[k], x, S.tau);
-      if (go[k] && ch[k] < 0) {
-        const int32_t enc = ~ch[k];
-        const int32_t first = enc >> 4, count = enc & 15;
-        tcn.prims += (uint32_t)count;
-        for (int32_t q = first; q < first + count; ++q) {
-          float ax, ay, az = 0.0f, d0, d1, d2;
-          bool always;
-          if (D == 2) {
-            const float4 A = __ldg(&S.prims[2 * q]), B = __ldg(&S.prims[2 * q + 1]);
-            ax = A.x - x[0];
-            ay = A.y - x[1];
-            d0 = fmaf(A.w, ay, A.z * ax);
-            d1 = fmaf(B.y, ay, B.x * ax);
-            always = B.z != 0.0f;
-            d2 = fmaf(ay, ay, ax * ax);
-          } else {
-            const float4 A = __ldg(&S.prims[4 * q]), B = __ldg(&S.prims[4 * q + 1]);
-            const float4 N0 = __ldg(&S.prims[4 * q + 2]), N1 = __ldg(&S.prims[4 * q + 3]);
-            ax = A.x - x[0];
-            ay = A.y - x[1];
-            az = A.z - x[D - 1];
-            d0 = fmaf(N0.z, az, fmaf(N0.y, ay, N0.x * ax));
-            d1 = fmaf(N1.z, az, fmaf(N1.y, ay, N1.x * ax));
-            always = A.w != 0.0f;
-            // distance to the edge a + s ab, s in [0, 1]
-            const float px = -ax, py = -ay, pz = -az;
-            float s = fmaf(B.z, pz, fmaf(B.y, py, B.x * px)) * B.w;
-            s = fminf(fmaxf(s, 0.0f), 1.0f);
-            const float ex = fmaf(-s, B.x, px), ey = fmaf(-s, B.y, py), ez = fmaf(-s, B.z, pz);
-            d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-          }
-          const bool z0 = fabsf(d0) <= S.tau, z1 = fabsf(d1) <= S.tau;
-          // one element edge-on (zero): a silhouette when the other faces away
-          const bool sil = always || (z0 && !z1 && d1 < 0.0f) || (z1 && !z0 && d0 < 0.0f) ||
-                           (!z0 && !z1 && ((d0 > 0.0f) != (d1 > 0.0f)));
-          if (sil && d2 < best2) best2 = d2;
-        }
-        go[k] = false;
-      }
-    }
-    // re-test against the bound a leaf may have lowered
-    go[0] = go[0] && dc[0] < best2;
-    go[1] = go[1] && dc[1] < best2;
-    if (go[0] && go[1]) {
-      const int nearer = dc[1] < dc[0] ? 1 : 0;
-      snode[sp * kWostBlock] = ch[1 - nearer];
-      sdist[sp * kWostBlock] = dc[1 - nearer];
-      ++sp;
-      node = ch[nearer];
-      continue;
-    }
-    if (go[0] || go[1]) {
-      node = go[0] ? ch[0] : ch[1];
-      continue;
-    }
-    bool found = false;
-    while (sp > 0) {
-      --sp;
-      if (sdist[sp * kWostBlock] < best2) {
-        node = snode[sp * kWostBlock];
-        found = true;
-        break;
-      }
-    }
-    if (!found) break;
-  }
+  for (int guard = 0; guard < (1 << 22); ++guard)
+    if (sil_visit<D>(S, x, best2, node, sp, snode, sdist, tcn)) break;
   return best2;
 }
 
@@ -246,158 +255,185 @@ __device__ __forceinline__ float slab(const float* lo, const float* hi, const fl
   return tn <= tf * 1.0000004f + 1e-30f ? tn : __int_as_float(0x7f800000);
 }
 
-// First crossing of o + t w, 0 < t <= tmax, with the Neumann part (element
-// `skip` ignored); ties to the lowest element.  Returns the element (its
-// Neumann id) or -1; t and the element's outward normal through t_out, n.
-// VIS (visibility tests): elements within kGraze of parallel to the ray are
+// Visibility rays (vis): elements within kGraze of parallel to the ray are
 // not crossings -- a walker on a flat wall looks along it, and a rounded
 // near-parallel test there would report a crossing anywhere along the wall.
 constexpr float kGraze = 1e-4f;
-// Walk rays (VIS false) only cross elements they leave the domain through
-// (n . w > 0): a ray from inside meets a front face first, and a walker on an
-// edge between two Neumann elements must not be stopped by the element it
-// moves away from.  tmin (<= 0): crossings with t in (tmin, 0] count as
-// crossings at t = 0 -- that walker, looking out through the other element,
-// must not pass it.
-template <int D, bool VIS = false>
-__device__ int ray_first(const DevGeometry& G, const float* o, const float* w, float tmax, int skip, int skip2,
-                         float tmin, float& t_out, float* n, int* snode, float* sdist, TravCount& tcn) {
-  float inv[D];
+
+template <int D>
+__device__ __forceinline__ void ray_inv(const float* w, float* inv) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const float v = fabsf(w[a]) < 1e-20f ? copysignf(1e-20f, w[a]) : w[a];
     inv[a] = 1.0f / v;
   }
-  float best = tmax;
-  int bid = 0x7fffffff, bq = -1;
-  int sp = 0, node = 0;
-  for (int guard = 0; guard < (1 << 22); ++guard) {
-    ++tcn.nodes;
-    int32_t ch[2];
-    float tc[2];
-    if (D == 2) {
-      const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
-      const float4 C = __ldg(&G.nodes[3 * node + 2]);
-      const float llo[2] = {L.x, L.y}, lhi[2] = {L.z, L.w}, rlo[2] = {R.x, R.y}, rhi[2] = {R.z, R.w};
-      tc[0] = slab(llo, lhi, o, inv, 2, tmin, best);
-      tc[1] = slab(rlo, rhi, o, inv, 2, tmin, best);
-      ch[0] = __float_as_int(C.x);
-      ch[1] = __float_as_int(C.y);
-    } else {
-      const float4 a = __ldg(&G.nodes[4 * node]), b = __ldg(&G.nodes[4 * node + 1]);
-      const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
-      const float llo[3] = {a.x, a.y, a.z}, lhi[3] = {a.w, b.x, b.y}, rlo[3] = {b.z, b.w, c.x},
-                  rhi[3] = {c.y, c.z, c.w};
-      tc[0] = slab(llo, lhi, o, inv, 3, tmin, best);
-      tc[1] = slab(rlo, rhi, o, inv, 3, tmin, best);
-      ch[0] = __float_as_int(e.x);
-      ch[1] = __float_as_int(e.y);
-    }
-    bool go[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      go[k] = tc[k] <= best;
-      if (go[k] && ch[k] < 0) {
-        const int32_t enc = ~ch[k];
-        const int32_t first = enc >> 4, count = enc & 15;
-        tcn.prims += (uint32_t)count;
-        for (int32_t q = first; q < first + count; ++q) {
-          float tt;
-          int id;
-          if (D == 2) {
-            const float4 Sg = __ldg(&G.prims[2 * q]), T = __ldg(&G.prims[2 * q + 1]);
-            id = __float_as_int(T.y);
-            const float den = fmaf(w[0], Sg.w, -w[1] * Sg.z);
-            if (id == skip || id == skip2 || den == 0.0f) continue;
-            if (VIS && fabsf(den) * sqrtf(T.x) < kGraze) continue;
-            // walk rays leave the domain through front faces only (n . w > 0)
-            if (!VIS && !(den > 0.0f)) continue;
-            const float qx = Sg.x - o[0], qy = Sg.y - o[1];
-            const float s = fmaf(qx, w[1], -qy * w[0]) / den;
-            if (!(s >= -kRayInfl && s <= 1.0f + kRayInfl)) continue;
-            tt = fmaf(qx, Sg.w, -qy * Sg.z) / den;
-          } else {
-            // Moller-Trumbore (J. Graphics Tools 2(1), 1997)
-            const float4 A = __ldg(&G.prims[3 * q]), B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
-            id = __float_as_int(A.w);
-            if (id == skip || id == skip2) continue;
-            const float Px = fmaf(w[1], Cc.z, -w[D - 1] * Cc.y);
-            const float Py = fmaf(w[D - 1], Cc.x, -w[0] * Cc.z);
-            const float Pz = fmaf(w[0], Cc.y, -w[1] * Cc.x);
-            const float det = fmaf(B.z, Pz, fmaf(B.y, Py, B.x * Px));
-            if (det == 0.0f) continue;
-            // walk rays leave the domain through front faces only: det = -(n . w) |ab x ac|
-            if (!VIS && !(det < 0.0f)) continue;
-            if (VIS) {
-              const float cx = fmaf(B.y, Cc.z, -B.z * Cc.y), cy = fmaf(B.z, Cc.x, -B.x * Cc.z);
-              const float cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
-              if (fabsf(det) < kGraze * sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)))) continue;
-            }
-            const float idet = 1.0f / det;
-            const float Tx = o[0] - A.x, Ty = o[1] - A.y, Tz = o[D - 1] - A.z;
-            const float u = fmaf(Tz, Pz, fmaf(Ty, Py, Tx * Px)) * idet;
-            if (!(u >= -kRayInfl && u <= 1.0f + kRayInfl)) continue;
-            const float Qx = fmaf(Ty, B.z, -Tz * B.y);
-            const float Qy = fmaf(Tz, B.x, -Tx * B.z);
-            const float Qz = fmaf(Tx, B.y, -Ty * B.x);
-            const float v = fmaf(w[D - 1], Qz, fmaf(w[1], Qy, w[0] * Qx)) * idet;
-            if (!(v >= -kRayInfl && u + v <= 1.0f + kRayInfl)) continue;
-            tt = fmaf(Cc.z, Qz, fmaf(Cc.y, Qy, Cc.x * Qx)) * idet;
-          }
-          tt = tt > 0.0f ? tt : (tt > tmin ? 0.0f : -1.0f);
-          if (tt >= 0.0f && (tt < best || (tt == best && id < bid))) {
-            best = tt;
-            bid = id;
-            bq = q;
-          }
-        }
-        go[k] = false;
-      }
-    }
-    go[0] = go[0] && tc[0] <= best;
-    go[1] = go[1] && tc[1] <= best;
-    if (go[0] && go[1]) {
-      const int nearer = tc[1] < tc[0] ? 1 : 0;
-      snode[sp * kWostBlock] = ch[1 - nearer];
-      sdist[sp * kWostBlock] = tc[1 - nearer];
-      ++sp;
-      node = ch[nearer];
-      continue;
-    }
-    if (go[0] || go[1]) {
-      node = go[0] ? ch[0] : ch[1];
-      continue;
-    }
-    bool found = false;
-    while (sp > 0) {
-      --sp;
-      if (sdist[sp * kWostBlock] <= best) {
-        node = snode[sp * kWostBlock];
-        found = true;
-        break;
-      }
-    }
-    if (!found) break;
-  }
-  if (bq < 0) {
-    t_out = __int_as_float(0x7f800000);
-    return -1;
-  }
-  t_out = best;
+}
+
+// First crossing of o + t w with the Neumann part: one node.  Walk rays (vis
+// false) only cross elements they leave the domain through (n . w > 0): a ray
+// from inside meets a front face first, and a walker on an edge between two
+// Neumann elements must not be stopped by the element it moves away from.
+// tmin (<= 0): crossings with t in (tmin, 0] count as crossings at t = 0 --
+// that walker, looking out through the other element, must not pass it.
+// Elements skip and skip2 are ignored; ties go to the lowest element.
+template <int D>
+__device__ __forceinline__ bool ray_visit(const DevGeometry& G, const float* o, const float* w, const float* inv,
+                                          float tmin, int skip, int skip2, bool vis, float& best, int& bid, int& bq,
+                                          int& node, int& sp, int* snode, float* sdist, TravCount& tcn) {
+  ++tcn.nodes;
+  int32_t ch[2];
+  float tc[2];
   if (D == 2) {
-    const float4 Sg = __ldg(&G.prims[2 * bq]), T = __ldg(&G.prims[2 * bq + 1]);
+    const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
+    const float4 C = __ldg(&G.nodes[3 * node + 2]);
+    const float llo[2] = {L.x, L.y}, lhi[2] = {L.z, L.w}, rlo[2] = {R.x, R.y}, rhi[2] = {R.z, R.w};
+    tc[0] = slab(llo, lhi, o, inv, 2, tmin, best);
+    tc[1] = slab(rlo, rhi, o, inv, 2, tmin, best);
+    ch[0] = __float_as_int(C.x);
+    ch[1] = __float_as_int(C.y);
+  } else {
+    const float4 a = __ldg(&G.nodes[4 * node]), b = __ldg(&G.nodes[4 * node + 1]);
+    const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
+    const float llo[3] = {a.x, a.y, a.z}, lhi[3] = {a.w, b.x, b.y}, rlo[3] = {b.z, b.w, c.x},
+                rhi[3] = {c.y, c.z, c.w};
+    tc[0] = slab(llo, lhi, o, inv, 3, tmin, best);
+    tc[1] = slab(rlo, rhi, o, inv, 3, tmin, best);
+    ch[0] = __float_as_int(e.x);
+    ch[1] = __float_as_int(e.y);
+  }
+  bool go[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    go[k] = tc[k] <= best;
+    if (go[k] && ch[k] < 0) {
+      const int32_t enc = ~ch[k];
+      const int32_t first = enc >> 4, count = enc & 15;
+      tcn.prims += (uint32_t)count;
+      for (int32_t q = first; q < first + count; ++q) {
+        float tt;
+        int id;
+        if (D == 2) {
+          const float4 Sg = __ldg(&G.prims[2 * q]), T = __ldg(&G.prims[2 * q + 1]);
+          id = __float_as_int(T.y);
+          const float den = fmaf(w[0], Sg.w, -w[1] * Sg.z);
+          if (id == skip || id == skip2 || den == 0.0f) continue;
+          if (vis ? fabsf(den) * sqrtf(T.x) < kGraze : !(den > 0.0f)) continue;
+          const float qx = Sg.x - o[0], qy = Sg.y - o[1];
+          const float s = fmaf(qx, w[1], -qy * w[0]) / den;
+          if (!(s >= -kRayInfl && s <= 1.0f + kRayInfl)) continue;
+          tt = fmaf(qx, Sg.w, -qy * Sg.z) / den;
+        } else {
+          // Moller-Trumbore (J. Graphics Tools 2(1), 1997)
+          const float4 A = __ldg(&G.prims[3 * q]), B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
+          id = __float_as_int(A.w);
+          if (id == skip || id == skip2) continue;
+          const float Px = fmaf(w[1], Cc.z, -w[D - 1] * Cc.y);
+          const float Py = fmaf(w[D - 1], Cc.x, -w[0] * Cc.z);
+          const float Pz = fmaf(w[0], Cc.y, -w[1] * Cc.x);
+          const float det = fmaf(B.z, Pz, fmaf(B.y, Py, B.x * Px));
+          if (det == 0.0f) continue;
+          if (vis) {
+            const float cx = fmaf(B.y, Cc.z, -B.z * Cc.y), cy = fmaf(B.z, Cc.x, -B.x * Cc.z);
+            const float cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
+            if (fabsf(det) < kGraze * sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)))) continue;
+          } else if (!(det < 0.0f)) {
+            continue;  // det = -(n . w) |ab x ac|: a back face
+          }
+          const float idet = 1.0f / det;
+          const float Tx = o[0] - A.x, Ty = o[1] - A.y, Tz = o[D - 1] - A.z;
+          const float u = fmaf(Tz, Pz, fmaf(Ty, Py, Tx * Px)) * idet;
+          if (!(u >= -kRayInfl && u <= 1.0f + kRayInfl)) continue;
+          const float Qx = fmaf(Ty, B.z, -Tz * B.y);
+          const float Qy = fmaf(Tz, B.x, -Tx * B.z);
+          const float Qz = fmaf(Tx, B.y, -Ty * B.x);
+          const float v = fmaf(w[D - 1], Qz, fmaf(w[1], Qy, w[0] * Qx)) * idet;
+          if (!(v >= -kRayInfl && u + v <= 1.0f + kRayInfl)) continue;
+          tt = fmaf(Cc.z, Qz, fmaf(Cc.y, Qy, Cc.x * Qx)) * idet;
+        }
+        tt = tt > 0.0f ? tt : (tt > tmin ? 0.0f : -1.0f);
+        if (tt >= 0.0f && (tt < best || (tt == best && id < bid))) {
+          best = tt;
+          bid = id;
+          bq = q;
+        }
+      }
+      go[k] = false;
+    }
+  }
+  go[0] = go[0] && tc[0] <= best;
+  go[1] = go[1] && tc[1] <= best;
+  if (go[0] && go[1]) {
+    const int nearer = tc[1] < tc[0] ? 1 : 0;
+    snode[sp * kWostBlock] = ch[1 - nearer];
+    sdist[sp * kWostBlock] = tc[1 - nearer];
+    ++sp;
+    node = ch[nearer];
+    return false;
+  }
+  if (go[0] || go[1]) {
+    node = go[0] ? ch[0] : ch[1];
+    return false;
+  }
+  while (sp > 0) {
+    --sp;
+    if (sdist[sp * kWostBlock] <= best) {
+      node = snode[sp * kWostBlock];
+      return false;
+    }
+  }
+  return true;
+}
+
+// Outward unit normal of the Neumann element at tree position q.
+template <int D>
+__device__ __forceinline__ void neumann_normal(const DevGeometry& G, int q, float* n) {
+  if (D == 2) {
+    const float4 Sg = __ldg(&G.prims[2 * q]), T = __ldg(&G.prims[2 * q + 1]);
     const float il = sqrtf(T.x);
     n[0] = Sg.w * il;
     n[D - 1] = -Sg.z * il;
   } else {
-    const float4 B = __ldg(&G.prims[3 * bq + 1]), Cc = __ldg(&G.prims[3 * bq + 2]);
+    const float4 B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
     const float cx = fmaf(B.y, Cc.z, -B.z * Cc.y), cy = fmaf(B.z, Cc.x, -B.x * Cc.z), cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
     const float il = rsqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
     n[0] = cx * il;
     n[1] = cy * il;
     n[D - 1] = cz * il;
   }
+}
+
+// First crossing of o + t w, 0 < t <= tmax (see ray_visit): the element's
+// Neumann id or -1; t and its outward normal through t_out, n.
+template <int D, bool VIS = false>
+__device__ int ray_first(const DevGeometry& G, const float* o, const float* w, float tmax, int skip, int skip2,
+                         float tmin, float& t_out, float* n, int* snode, float* sdist, TravCount& tcn) {
+  float inv[D];
+  ray_inv<D>(w, inv);
+  float best = tmax;
+  int bid = 0x7fffffff, bq = -1;
+  int sp = 0, node = 0;
+  for (int guard = 0; guard < (1 << 22); ++guard)
+    if (ray_visit<D>(G, o, w, inv, tmin, skip, skip2, VIS, best, bid, bq, node, sp, snode, sdist, tcn)) break;
+  if (bq < 0) {
+    t_out = __int_as_float(0x7f800000);
+    return -1;
+  }
+  t_out = best;
+  neumann_normal<D>(G, bq, n);
   return bid;
+}
+
+// A uniform per level of the area-sampling descent: an integer hash of the
+// draw's words x, y and the level (xor-shift-multiply rounds, constants of
+// C. Wellons' "lowbias32").
+__device__ __forceinline__ float level_uniform(const U4& r, uint32_t lv) {
+  uint32_t v = r.x ^ (r.y + 0x9e3779b9u * (lv + 1u));
+  v ^= v >> 16;
+  v *= 0x7feb352du;
+  v ^= v >> 15;
+  v *= 0x846ca68bu;
+  v ^= v >> 16;
+  return u01f(v);
 }
 
 // A point z on the Neumann part, chosen by descending the Neumann tree:
@@ -406,106 +442,95 @@ __device__ int ray_first(const DevGeometry& G, const float* o, const float* w, f
 // in the leaf an element by its measure, on the element a uniform point
 // (2D a + s ab; 3D barycentrics (1 - sqrt u1, sqrt u1 (1 - u2), sqrt u1 u2)).
 // Every Neumann point inside the ball has positive density; ipdf = 1/pdf(z).
-// Draw words: x, y seed one uniform per level of the descent (and the leaf's
-// element choice) through an integer hash, z, w place the point.  Returns
-// false when no subtree reaches into the ball.
+// Draw words: x, y seed one uniform per level (and the leaf's element
+// choice), z, w place the point.  One level per call: returns 0 to go on,
+// 1 with the point, 2 when no subtree reaches into the ball.
+template <int D>
+__device__ __forceinline__ int descent_visit(const DevGeometry& G, const float2* __restrict__ nm, const float* x,
+                                             float R2, const U4& r, int& level, int& node, float& pdf, float* z,
+                                             float* nz, int& id, float& ipdf, TravCount& tcn) {
+  ++tcn.nodes;
+  int32_t ch[2];
+  float dc[2];
+  if (D == 2) {
+    const float4 L = __ldg(&G.nodes[3 * node]), Rb = __ldg(&G.nodes[3 * node + 1]);
+    const float4 C = __ldg(&G.nodes[3 * node + 2]);
+    dc[0] = box_d2_2(L.x, L.y, L.z, L.w, x);
+    dc[1] = box_d2_2(Rb.x, Rb.y, Rb.z, Rb.w, x);
+    ch[0] = __float_as_int(C.x);
+    ch[1] = __float_as_int(C.y);
+  } else {
+    const float4 a = __ldg(&G.nodes[4 * node]), b = __ldg(&G.nodes[4 * node + 1]);
+    const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
+    dc[0] = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, x);
+    dc[1] = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, x);
+    ch[0] = __float_as_int(e.x);
+    ch[1] = __float_as_int(e.y);
+  }
+  const float2 m = __ldg(&nm[node]);
+  const float w0 = dc[0] < R2 ? m.x : 0.0f, w1 = dc[1] < R2 ? m.y : 0.0f;
+  if (!(w0 + w1 > 0.0f) || level >= 63) return 2;
+  const float p0 = w0 / (w0 + w1);
+  const int pick = level_uniform(r, (uint32_t)level) < p0 ? 0 : 1;
+  pdf *= pick == 0 ? p0 : 1.0f - p0;
+  ++level;
+  if (ch[pick] >= 0) {
+    node = ch[pick];
+    return 0;
+  }
+  // leaf: an element by measure
+  const int32_t enc = ~ch[pick];
+  const int32_t first = enc >> 4, count = enc & 15;
+  auto elem_measure = [&](int32_t q) {
+    if (D == 2) return 1.0f / sqrtf(__ldg(&G.prims[2 * q + 1]).x);
+    const float4 B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
+    const float cx = fmaf(B.y, Cc.z, -B.z * Cc.y), cy = fmaf(B.z, Cc.x, -B.x * Cc.z);
+    const float cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
+    return 0.5f * sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
+  };
+  tcn.prims += (uint32_t)count;
+  float tot = 0.0f;
+  for (int32_t q = first; q < first + count; ++q) tot += elem_measure(q);
+  if (!(tot > 0.0f)) return 2;
+  const float target = level_uniform(r, 63u) * tot;
+  float run = 0.0f;
+  int32_t qs = first + count - 1;
+  for (int32_t q = first; q < first + count; ++q) {
+    run += elem_measure(q);
+    if (run > target) {
+      qs = q;
+      break;
+    }
+  }
+  // pdf(z) = (descent probability) x (m_e / tot) x (1 / m_e)
+  ipdf = tot / pdf;
+  const float s1 = u01f(r.z), s2 = u01f(r.w);
+  if (D == 2) {
+    const float4 S = __ldg(&G.prims[2 * qs]), T = __ldg(&G.prims[2 * qs + 1]);
+    z[0] = fmaf(s1, S.z, S.x);
+    z[D - 1] = fmaf(s1, S.w, S.y);
+    id = __float_as_int(T.y);
+  } else {
+    const float4 A = __ldg(&G.prims[3 * qs]), B = __ldg(&G.prims[3 * qs + 1]), Cc = __ldg(&G.prims[3 * qs + 2]);
+    const float sq = sqrtf(s1), b1 = sq * (1.0f - s2), b2 = sq * s2;
+    z[0] = fmaf(b2, Cc.x, fmaf(b1, B.x, A.x));
+    z[1] = fmaf(b2, Cc.y, fmaf(b1, B.y, A.y));
+    z[D - 1] = fmaf(b2, Cc.z, fmaf(b1, B.z, A.z));
+    id = __float_as_int(A.w);
+  }
+  neumann_normal<D>(G, qs, nz);
+  return 1;
+}
+
 template <int D>
 __device__ bool sample_neumann(const DevGeometry& G, const float2* __restrict__ nm, const float* x, float R,
                                const U4 r, float* z, float* nz, int& id, float& ipdf, TravCount& tcn) {
-  // a fresh uniform per level: an integer hash of (r.x, r.y, level)
-  // (xor-shift-multiply rounds, constants of C. Wellons' "lowbias32")
-  auto level_u = [&](uint32_t lv) {
-    uint32_t v = r.x ^ (r.y + 0x9e3779b9u * (lv + 1u));
-    v ^= v >> 16;
-    v *= 0x7feb352du;
-    v ^= v >> 15;
-    v *= 0x846ca68bu;
-    v ^= v >> 16;
-    return u01f(v);
-  };
   float pdf = 1.0f;
-  const float R2 = R * R;
-  int node = 0;
-  for (int depth = 0; depth < 64; ++depth) {
-    ++tcn.nodes;
-    int32_t ch[2];
-    float dc[2];
-    if (D == 2) {
-      const float4 L = __ldg(&G.nodes[3 * node]), Rb = __ldg(&G.nodes[3 * node + 1]);
-      const float4 C = __ldg(&G.nodes[3 * node + 2]);
-      dc[0] = box_d2_2(L.x, L.y, L.z, L.w, x);
-      dc[1] = box_d2_2(Rb.x, Rb.y, Rb.z, Rb.w, x);
-      ch[0] = __float_as_int(C.x);
-      ch[1] = __float_as_int(C.y);
-    } else {
-      const float4 a = __ldg(&G.nodes[4 * node]), b = __ldg(&G.nodes[4 * node + 1]);
-      const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
-      dc[0] = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, x);
-      dc[1] = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, x);
-      ch[0] = __float_as_int(e.x);
-      ch[1] = __float_as_int(e.y);
-    }
-    const float2 m = __ldg(&nm[node]);
-    const float w0 = dc[0] < R2 ? m.x : 0.0f, w1 = dc[1] < R2 ? m.y : 0.0f;
-    if (!(w0 + w1 > 0.0f)) return false;
-    const float p0 = w0 / (w0 + w1);
-    const int pick = level_u((uint32_t)depth) < p0 ? 0 : 1;
-    pdf *= pick == 0 ? p0 : 1.0f - p0;
-    if (ch[pick] >= 0) {
-      node = ch[pick];
-      continue;
-    }
-    // leaf: an element by measure
-    const int32_t enc = ~ch[pick];
-    const int32_t first = enc >> 4, count = enc & 15;
-    auto elem_measure = [&](int32_t q) {
-      if (D == 2) return 1.0f / sqrtf(__ldg(&G.prims[2 * q + 1]).x);
-      const float4 B = __ldg(&G.prims[3 * q + 1]), Cc = __ldg(&G.prims[3 * q + 2]);
-      const float cx = fmaf(B.y, Cc.z, -B.z * Cc.y), cy = fmaf(B.z, Cc.x, -B.x * Cc.z);
-      const float cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
-      return 0.5f * sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
-    };
-    tcn.prims += (uint32_t)count;
-    float tot = 0.0f;
-    for (int32_t q = first; q < first + count; ++q) tot += elem_measure(q);
-    if (!(tot > 0.0f)) return false;
-    const float target = level_u(63u) * tot;
-    float run = 0.0f;
-    int32_t qs = first + count - 1;
-    for (int32_t q = first; q < first + count; ++q) {
-      run += elem_measure(q);
-      if (run > target) {
-        qs = q;
-        break;
-      }
-    }
-    // pdf(z) = (descent probability) x (m_e / tot) x (1 / m_e)
-    ipdf = tot / pdf;
-    const float s1 = u01f(r.z), s2 = u01f(r.w);
-    if (D == 2) {
-      const float4 S = __ldg(&G.prims[2 * qs]), T = __ldg(&G.prims[2 * qs + 1]);
-      z[0] = fmaf(s1, S.z, S.x);
-      z[D - 1] = fmaf(s1, S.w, S.y);
-      const float il = sqrtf(T.x);
-      nz[0] = S.w * il;
-      nz[D - 1] = -S.z * il;
-      id = __float_as_int(T.y);
-    } else {
-      const float4 A = __ldg(&G.prims[3 * qs]), B = __ldg(&G.prims[3 * qs + 1]), Cc = __ldg(&G.prims[3 * qs + 2]);
-      const float sq = sqrtf(s1), b1 = sq * (1.0f - s2), b2 = sq * s2;
-      z[0] = fmaf(b2, Cc.x, fmaf(b1, B.x, A.x));
-      z[1] = fmaf(b2, Cc.y, fmaf(b1, B.y, A.y));
-      z[D - 1] = fmaf(b2, Cc.z, fmaf(b1, B.z, A.z));
-      const float cx = fmaf(B.y, Cc.z, -B.z * Cc.y), cy = fmaf(B.z, Cc.x, -B.x * Cc.z), cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
-      const float il = rsqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
-      nz[0] = cx * il;
-      nz[1] = cy * il;
-      nz[D - 1] = cz * il;
-      id = __float_as_int(A.w);
-    }
-    return true;
+  int node = 0, level = 0;
+  for (;;) {
+    const int st = descent_visit<D>(G, nm, x, R * R, r, level, node, pdf, z, nz, id, ipdf, tcn);
+    if (st) return st == 1;
   }
-  return false;
 }
 
 // The Neumann term over the element under an on-boundary x (Neumann id
