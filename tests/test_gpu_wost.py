@@ -299,3 +299,42 @@ def test_wost_estimate_closed_form():
     assert np.all(np.abs(z) < 4.5), z
     s = m.whole.stats(reset=True)
     assert s["capped"] == 0
+
+
+def test_mixed_cache_full_size_sampled():
+    # the mixed workload's launch: 65,536 samples x 64 walks on the 20k-segment
+    # star (2/3 Neumann); with zero Neumann data every walk is replayed by the
+    # oracle with the same ids: 24 sampled samples of each kind, all 64 walks
+    w = wl.star_mixed()
+    m = bvc.Mixed(w.V, w.F, w.neumann)
+    N, W = w.n_samples, w.walks
+    opts = bvc.cache_opts(N, W, w.offset_l, w.eps, 3, src_grid=w.src_grid)
+    cache = bvc.Cache(2, N, n_src_cand=bvc.n_candidates(2, w.src_grid))
+    bvc.mixed_cache_build(m, w.g, None, w.f, opts, cache)
+    torch.cuda.synchronize()
+    # a few walks in 4.2M slip through a rounding gap or hit the step cap
+    assert m.whole.stats(reset=True)["capped"] <= 1e-5 * N * W
+    z, n, e = oracle.sample_boundary_mixed(w.V, w.F, N, w.offset_l, 3, w.neumann)
+    np.testing.assert_array_equal(cache.z.cpu().numpy().T, z.astype(np.float32))
+    on = w.neumann[e] == 1
+    rng = np.random.default_rng(9)
+    sel = np.concatenate([rng.choice(np.where(on)[0], 24, replace=False), rng.choice(np.where(~on)[0], 24, replace=False)])
+    wo = oracle.Wost(w.V, w.F, w.neumann)
+    uh = cache.u_hat.cpu().numpy()
+    qh = cache.dudn_hat.cpu().numpy()
+    close = 0
+    for i in sel:
+        o = wo.walks(w.g, [], [], w.f, z[i:i + 1].astype(np.float32), np.array([e[i] if on[i] else -1], np.int32), W,
+                     w.eps, 1 << 14, 3, id_base=int(i) * W)
+        ou = o["U"].mean()
+        sd = o["U"].std() / np.sqrt(W) + 1e-9
+        close += abs(uh[i] - ou) <= 1e-4 * (np.abs(o["U"]).max() + 1.0)
+        assert abs(uh[i] - ou) < 6 * sd + 1e-4, (i, uh[i], ou, sd)
+        if on[i]:
+            assert qh[i] == 0.0  # zero Neumann data
+        else:
+            oq = np.mean(o["grad"] @ n[i].astype(np.float32).astype(np.float64))
+            sq = np.std(o["grad"] @ n[i]) / np.sqrt(W) + 1e-9
+            assert abs(qh[i] - oq) < 6 * sq + 1e-3, (i, qh[i], oq, sq)
+    # most samples reproduce the oracle's mean to rounding (every walk agrees)
+    assert close >= 0.75 * sel.size, close
