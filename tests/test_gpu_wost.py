@@ -303,8 +303,9 @@ def test_wost_estimate_closed_form():
 
 def test_mixed_cache_full_size_sampled():
     # the mixed workload's launch: 65,536 samples x 64 walks on the 20k-segment
-    # star (2/3 Neumann); with zero Neumann data every walk is replayed by the
-    # oracle with the same ids: 24 sampled samples of each kind, all 64 walks
+    # star (2/3 Neumann), zero Neumann data.  For 48 sampled samples (24 of
+    # each kind) the same walks (ids sample * 64 + j, tag 0) are run one by one
+    # on the GPU -- their mean is the cache's estimate -- and by the oracle.
     w = wl.star_mixed()
     m = bvc.Mixed(w.V, w.F, w.neumann)
     N, W = w.n_samples, w.walks
@@ -318,23 +319,29 @@ def test_mixed_cache_full_size_sampled():
     np.testing.assert_array_equal(cache.z.cpu().numpy().T, z.astype(np.float32))
     on = w.neumann[e] == 1
     rng = np.random.default_rng(9)
-    sel = np.concatenate([rng.choice(np.where(on)[0], 24, replace=False), rng.choice(np.where(~on)[0], 24, replace=False)])
-    wo = oracle.Wost(w.V, w.F, w.neumann)
+    sel = np.concatenate([rng.choice(np.where(on)[0], 24, replace=False),
+                          rng.choice(np.where(~on)[0], 24, replace=False)])
     uh = cache.u_hat.cpu().numpy()
     qh = cache.dudn_hat.cpu().numpy()
-    close = 0
+    wo = oracle.Wost(w.V, w.F, w.neumann)
+    n_close = n_all = 0
     for i in sel:
-        o = wo.walks(w.g, [], [], w.f, z[i:i + 1].astype(np.float32), np.array([e[i] if on[i] else -1], np.int32), W,
-                     w.eps, 1 << 14, 3, id_base=int(i) * W)
-        ou = o["U"].mean()
-        sd = o["U"].std() / np.sqrt(W) + 1e-9
-        close += abs(uh[i] - ou) <= 1e-4 * (np.abs(o["U"]).max() + 1.0)
-        assert abs(uh[i] - ou) < 6 * sd + 1e-4, (i, uh[i], ou, sd)
-        if on[i]:
-            assert qh[i] == 0.0  # zero Neumann data
-        else:
-            oq = np.mean(o["grad"] @ n[i].astype(np.float32).astype(np.float64))
-            sq = np.std(o["grad"] @ n[i]) / np.sqrt(W) + 1e-9
-            assert abs(qh[i] - oq) < 6 * sq + 1e-3, (i, qh[i], oq, sq)
-    # most samples reproduce the oracle's mean to rounding (every walk agrees)
-    assert close >= 0.75 * sel.size, close
+        zi = z[i:i + 1].astype(np.float32)
+        se = np.array([e[i] if on[i] else -1], np.int32)
+        rec, steps, _ = bvc.mixed_walk(m, w.g, None, w.f, bvc.soa(zi), torch.from_numpy(se).cuda(),
+                                       bvc.soa(n[i:i + 1].astype(np.float32)), W, w.eps, 1 << 14, 3,
+                                       id_base=int(i) * W, debug=True)
+        torch.cuda.synchronize()
+        r = rec.cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(r[0].mean(), uh[i], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(r[1].mean(), qh[i], rtol=1e-12, atol=1e-12)
+        o = wo.walks(w.g, [], [], w.f, zi, se, W, w.eps, 1 << 14, 3, id_base=int(i) * W)
+        sc = np.abs(o["U"]).max() + 1.0
+        close = (steps.cpu().numpy() == o["steps"]) & (np.abs(r[0] - o["U"]) <= 2e-4 * sc)
+        n_close += int(close.sum())
+        n_all += W
+        # and the sample's means agree in distribution
+        sd = np.sqrt(r[0].var() / W + o["U"].var() / W) + 1e-9
+        assert abs(r[0].mean() - o["U"].mean()) < 6 * sd + 1e-4
+    # chaotic reflections separate some FP32 / FP64 paths; most walks agree
+    assert n_close >= 0.85 * n_all, n_close / n_all
