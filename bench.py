@@ -310,12 +310,17 @@ def fixed_rmse_comparison(device, w_lit):
     if w.exact is None:
         return None
     s = Solver(w, device)
-    s.step(7)
-    torch.cuda.synchronize()
     ex_far, _ = wl.eval_terms(w.exact, w.dim, s.far_pts.cpu().numpy().T.astype(np.float64))
     ex_near, _ = wl.eval_terms(w.exact, w.dim, s.near_pts.cpu().numpy().T.astype(np.float64))
-    err = np.concatenate([s.u_far.cpu().numpy() - ex_far, s.u_near.cpu().numpy() - ex_near])
-    tau = float(np.sqrt(np.mean(err ** 2)))
+    # the cache's error is shared by all points of a solve (correlated), so
+    # tau is the RMSE over four independent solves
+    mse = []
+    for seed in (7, 8, 9, 10):
+        s.step(seed)
+        torch.cuda.synchronize()
+        err = np.concatenate([s.u_far.cpu().numpy() - ex_far, s.u_near.cpu().numpy() - ex_near])
+        mse.append(float(np.mean(err ** 2)))
+    tau = float(np.sqrt(np.mean(mse)))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for k in range(3):
@@ -376,11 +381,14 @@ def fixed_rmse_comparison(device, w_lit):
             n2 = int(np.ceil(w.n_samples * fac / 1024.0) * 1024)
             g2 = tuple(int(np.ceil(gd * fac ** (1.0 / w.dim))) for gd in w.src_grid)
             s2 = Solver(replace(w, n_samples=n2, src_grid=g2), device)
-            s2.step(7)
-            torch.cuda.synchronize()
             x2f, _ = wl.eval_terms(w.exact, w.dim, s2.far_pts.cpu().numpy().T.astype(np.float64))
             x2n, _ = wl.eval_terms(w.exact, w.dim, s2.near_pts.cpu().numpy().T.astype(np.float64))
-            e2 = np.concatenate([s2.u_far.cpu().numpy() - x2f, s2.u_near.cpu().numpy() - x2n])
+            e2 = []
+            for seed in (7, 8, 9, 10):
+                s2.step(seed)
+                torch.cuda.synchronize()
+                e2.append(np.concatenate([s2.u_far.cpu().numpy() - x2f, s2.u_near.cpu().numpy() - x2n]))
+            e2 = np.concatenate(e2)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for q in range(2):
@@ -929,13 +937,17 @@ def mixed_fixed_rmse(device, s):
     from paper_2302_11825_gb300 import bvc
     from paper_2302_11825_gb300 import workloads as wl
     w = s.w
-    s.step(7)
-    torch.cuda.synchronize()
     fp = s.far_pts.cpu().numpy().T.astype(np.float64)
     npt = s.near_pts.cpu().numpy().T.astype(np.float64)
     ex = np.concatenate([wl.eval_terms(w.exact, w.dim, fp)[0], wl.eval_terms(w.exact, w.dim, npt)[0]])
-    err = np.concatenate([s.u_far.cpu().numpy(), s.u_near.cpu().numpy()]) - ex
-    tau = float(np.sqrt(np.mean(err ** 2)))
+    # RMSE over four independent solves (the cache's error is shared by all points)
+    mse = []
+    for seed in (7, 8, 9, 10):
+        s.step(seed)
+        torch.cuda.synchronize()
+        err = np.concatenate([s.u_far.cpu().numpy(), s.u_near.cpu().numpy()]) - ex
+        mse.append(float(np.mean(err ** 2)))
+    tau = float(np.sqrt(np.mean(mse)))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for k in range(3):
