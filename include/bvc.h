@@ -314,8 +314,14 @@ bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_funct
                         void* workspace, size_t workspace_bytes, bvc_stream stream);
 
 /* Gather device status word (bit 0: a bounded wait for a tile copy ran
- * out).  Synchronises the device; reset != 0 clears it. */
+ * out; bit 1: the self-test's wait ran out).  Synchronises the device;
+ * reset != 0 clears it. */
 bvc_status bvc_gather_status(uint64_t* flags, int32_t reset);
+/* Failure-path self-test: one warp waits on a barrier that nothing completes,
+ * with the gathers' bounded wait cut to limit_ns (0..2e9); the wait gives up,
+ * sets bit 1 of the status word and the kernel returns (the context stays
+ * usable). */
+bvc_status bvc_wait_selftest(int64_t limit_ns, bvc_stream stream);
 
 /* ------------------------------------------------------- walk autotuner */
 /* The walk kernel is persistent: a grid of (blocks per SM) x (SMs) blocks

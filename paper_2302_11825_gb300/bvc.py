@@ -175,6 +175,7 @@ def _declare(lib):
         "bvc_profile_begin": (S, []),
         "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
         "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
+        "bvc_wait_selftest": (S, [i64, P]),
         "bvc_status_string": (C.c_char_p, [S]),
         "bvc_version": (i32, []),
     }
@@ -1035,3 +1036,8 @@ def wost_estimate(m: Mixed, g_terms, h, f_terms, state: EvalState, walks: int, e
                                float(eps), int(max_steps), int(seed), int(id_base), _ptr(ws), ws.numel(),
                                _stream(stream)), "wost_estimate")
     return state
+
+
+def wait_selftest(limit_ns: int = 1_000_000, stream=None):
+    """Runs the bounded-wait self-test (a wait that nothing completes)."""
+    _check(lib().bvc_wait_selftest(int(limit_ns), _stream(stream)), "bvc_wait_selftest")

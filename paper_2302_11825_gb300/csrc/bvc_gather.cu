@@ -80,15 +80,19 @@ __device__ __forceinline__ uint64_t global_timer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait: gives up after ~2 s or 2^26 polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+// Bounded wait: gives up after limit_ns or 2^26 polls.
+__device__ __forceinline__ bool mbar_wait_bounded_ns(uint64_t* bar, uint32_t phase, uint64_t limit_ns) {
   if (mbar_try_wait(bar, phase)) return true;
   const uint64_t t0 = global_timer();
   for (int it = 0; it < (1 << 26); ++it) {
     if (mbar_try_wait(bar, phase)) return true;
-    if ((it & 255) == 0 && global_timer() - t0 > 2000000000ull) break;
+    if ((it & 255) == 0 && global_timer() - t0 > limit_ns) break;
   }
   return false;
+}
+// The gathers' wait for a tile copy: ~2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  return mbar_wait_bounded_ns(bar, phase, 2000000000ull);
 }
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
@@ -808,6 +812,27 @@ extern "C" bvc_status bvc_get_solution(const bvc_eval_state* state, double* u, d
     k_get_solution<2><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(*state, u, grad);
   else
     k_get_solution<3><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(*state, u, grad);
+  BVC_LAUNCH_CHECK();
+  return BVC_OK;
+}
+
+// Self-test of the bounded wait: one warp waits on a barrier that nothing
+// completes; the wait gives up after limit_ns and the status word records it
+// (bit 1), as a stalled tile copy would (bit 0).
+__global__ void k_wait_selftest(uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const bool ok = mbar_wait_bounded_ns(&bar, 0u, limit_ns);
+  if (!ok && threadIdx.x == 0) atomicOr(&g_gather_status, 2ull);
+}
+
+extern "C" bvc_status bvc_wait_selftest(int64_t limit_ns, bvc_stream stream) {
+  if (limit_ns < 0 || limit_ns > 2000000000ll) return BVC_ERR_INVALID_ARG;
+  k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_ns);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }

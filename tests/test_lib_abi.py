@@ -210,3 +210,10 @@ def test_mixed_host_checks(lib):
     lib.wost_estimate.argtypes = [C.c_void_p] * 5 + [C.c_int32, C.c_float, C.c_int32, C.c_uint64, C.c_uint64,
                                                       C.c_void_p, C.c_size_t, C.c_void_p]
     assert lib.wost_estimate(None, None, None, None, None, 1, 1e-3, 10, 0, 0, None, 0, None) == 1
+
+
+def test_wait_selftest_rejects_bad_limits(lib):
+    lib.bvc_wait_selftest.restype = C.c_int
+    lib.bvc_wait_selftest.argtypes = [C.c_int64, C.c_void_p]
+    assert lib.bvc_wait_selftest(-1, None) == 1
+    assert lib.bvc_wait_selftest(3_000_000_000, None) == 1
