@@ -310,17 +310,27 @@ def fixed_rmse_comparison(device, w_lit):
     if w.exact is None:
         return None
     s = Solver(w, device)
-    ex_far, _ = wl.eval_terms(w.exact, w.dim, s.far_pts.cpu().numpy().T.astype(np.float64))
+    ex_far, gx_far = wl.eval_terms(w.exact, w.dim, s.far_pts.cpu().numpy().T.astype(np.float64))
     ex_near, _ = wl.eval_terms(w.exact, w.dim, s.near_pts.cpu().numpy().T.astype(np.float64))
     # the cache's error is shared by all points of a solve (correlated), so
-    # tau is the RMSE over four independent solves
-    mse = []
+    # tau is the RMSE over four independent solves; the gradient error of the
+    # gathered points (Eq. 5-6) is reported beside it
+    # the gradient kernel is singular like 1/r^2 at the sample surface, so the
+    # gradient error is reported for all gathered points and for those at
+    # least 4 l from the boundary
+    d2f, _, _ = bvc.query_closest(s.geom, s.far_pts)
+    deep_far = np.sqrt(d2f.cpu().numpy()) >= 4.0 * w.offset_l
+    mse, gmse, gmse_deep = [], [], []
     for seed in (7, 8, 9, 10):
         s.step(seed)
         torch.cuda.synchronize()
         err = np.concatenate([s.u_far.cpu().numpy() - ex_far, s.u_near.cpu().numpy() - ex_near])
         mse.append(float(np.mean(err ** 2)))
+        ge = np.sum((s.g_far.cpu().numpy().T - gx_far) ** 2, 1)
+        gmse.append(float(np.mean(ge)))
+        gmse_deep.append(float(np.mean(ge[deep_far])))
     tau = float(np.sqrt(np.mean(mse)))
+    bvc_grad = (float(np.sqrt(np.mean(gmse))), float(np.sqrt(np.mean(gmse_deep))))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for k in range(3):
@@ -331,10 +341,15 @@ def fixed_rmse_comparison(device, w_lit):
     # pointwise walk on spheres on a random subset of interior points
     rng = np.random.default_rng(3)
     allp = np.concatenate([s.far_pts.cpu().numpy().T, s.near_pts.cpu().numpy().T])
-    sub = allp[rng.choice(allp.shape[0], min(8192, allp.shape[0]), replace=False)]
-    ex_sub, _ = wl.eval_terms(w.exact, w.dim, sub.astype(np.float64))
+    pick = rng.choice(allp.shape[0], min(8192, allp.shape[0]), replace=False)
+    sub = allp[pick]
+    sub_far = pick < s.m_far  # the gathered points, for the gradient comparison
+    ex_sub, gx_sub = wl.eval_terms(w.exact, w.dim, sub.astype(np.float64))
+    d2s, _, _ = bvc.query_closest(s.geom, bvc.soa(sub))
+    sub_deep = sub_far & (np.sqrt(d2s.cpu().numpy()) >= 4.0 * w.offset_l)
+    last_grad = [float("nan"), float("nan")]
     pts = bvc.soa(sub)
-    st = bvc.EvalState(pts, grad=False)
+    st = bvc.EvalState(pts, grad=True)
 
     def wos_rmse(k, seed):
         bvc.eval_state_reset(st)
@@ -342,9 +357,12 @@ def fixed_rmse_comparison(device, w_lit):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         bvc.wos_estimate(s.geom, w.g, w.f, st, k, w.eps, MAX_STEPS, seed, 0, ws)
-        u, _ = bvc.get_solution(st)
+        u, gr = bvc.get_solution(st)
         e1.record()
         torch.cuda.synchronize()
+        gerr = np.sum((gr.cpu().numpy().T - gx_sub) ** 2, 1)
+        last_grad[0] = float(np.sqrt(np.mean(gerr[sub_far])))
+        last_grad[1] = float(np.sqrt(np.mean(gerr[sub_deep])))
         return float(np.sqrt(np.mean((u.cpu().numpy() - ex_sub) ** 2))), e0.elapsed_time(e1) / 1e3
 
     kmax = 1 << 18
@@ -362,7 +380,14 @@ def fixed_rmse_comparison(device, w_lit):
     k, r, wos_rate = wos_at(tau)
     out = {"variant": w.name, "tau_rmse": tau, "bvc_pts_per_s": bvc_rate, "wos_walks_per_point": k,
            "wos_rmse": r, "wos_pts_per_s": wos_rate, "bvc_over_wos": bvc_rate / wos_rate,
-           "wos_subset_points": int(st.m)}
+           "wos_subset_points": int(st.m),
+           # gradient error at those sizes (points farther than l): BVC (Eq. 5-6)
+           # and pointwise WoS with k walks per point
+           "grad_rmse": {"bvc": bvc_grad[0], "wos": last_grad[0], "bvc_beyond_4l": bvc_grad[1],
+                         "wos_beyond_4l": last_grad[1], "wos_walks_per_point": k,
+                         # WoS at the BVC's time per point: k / ratio walks, the
+                         # error of independent walks growing as sqrt(ratio)
+                         "wos_beyond_4l_equal_time": last_grad[1] * float(np.sqrt(bvc_rate / wos_rate))}}
     # the same at tau = 1e-2 and 3e-3 of the range of u: where the target is
     # below the configured cache's RMSE, the boundary and source caches grow
     # by the squared ratio (RMSE ~ N^-1/2, M^-1/2; capped at 16x) and the
@@ -939,15 +964,23 @@ def mixed_fixed_rmse(device, s):
     w = s.w
     fp = s.far_pts.cpu().numpy().T.astype(np.float64)
     npt = s.near_pts.cpu().numpy().T.astype(np.float64)
-    ex = np.concatenate([wl.eval_terms(w.exact, w.dim, fp)[0], wl.eval_terms(w.exact, w.dim, npt)[0]])
-    # RMSE over four independent solves (the cache's error is shared by all points)
-    mse = []
+    exf, gxf = wl.eval_terms(w.exact, w.dim, fp)
+    ex = np.concatenate([exf, wl.eval_terms(w.exact, w.dim, npt)[0]])
+    # RMSE over four independent solves (the cache's error is shared by all
+    # points); the gradient error of the gathered points beside it
+    d2f, _, _ = bvc.query_closest(s.m.whole, s.far_pts)
+    deep_far = np.sqrt(d2f.cpu().numpy()) >= 4.0 * w.offset_l
+    mse, gmse, gmse_deep = [], [], []
     for seed in (7, 8, 9, 10):
         s.step(seed)
         torch.cuda.synchronize()
         err = np.concatenate([s.u_far.cpu().numpy(), s.u_near.cpu().numpy()]) - ex
         mse.append(float(np.mean(err ** 2)))
+        ge = np.sum((s.g_far.cpu().numpy().T - gxf) ** 2, 1)
+        gmse.append(float(np.mean(ge)))
+        gmse_deep.append(float(np.mean(ge[deep_far])))
     tau = float(np.sqrt(np.mean(mse)))
+    bvc_grad = (float(np.sqrt(np.mean(gmse))), float(np.sqrt(np.mean(gmse_deep))))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for k in range(3):
@@ -957,9 +990,14 @@ def mixed_fixed_rmse(device, s):
     bvc_rate = (s.m_far + s.m_near) * 3 / (e0.elapsed_time(e1) / 1e3)
     rng = np.random.default_rng(3)
     allp = np.concatenate([fp, npt]).astype(np.float32)
-    sub = allp[rng.choice(allp.shape[0], min(4096, allp.shape[0]), replace=False)]
-    ex_sub = wl.eval_terms(w.exact, w.dim, sub.astype(np.float64))[0]
-    st = bvc.EvalState(bvc.soa(sub), grad=False)
+    pick = rng.choice(allp.shape[0], min(4096, allp.shape[0]), replace=False)
+    sub = allp[pick]
+    sub_far = pick < s.m_far
+    ex_sub, gx_sub = wl.eval_terms(w.exact, w.dim, sub.astype(np.float64))
+    d2s, _, _ = bvc.query_closest(s.m.whole, bvc.soa(sub))
+    sub_deep = sub_far & (np.sqrt(d2s.cpu().numpy()) >= 4.0 * w.offset_l)
+    st = bvc.EvalState(bvc.soa(sub), grad=True)
+    last_grad = [float("nan"), float("nan")]
 
     def rmse(k, seed):
         bvc.eval_state_reset(st)
@@ -967,9 +1005,12 @@ def mixed_fixed_rmse(device, s):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         bvc.wost_estimate(s.m, w.g, s.h, w.f, st, k, w.eps, MAX_STEPS, seed, 0, ws_)
-        u, _ = bvc.get_solution(st)
+        u, gr = bvc.get_solution(st)
         b.record()
         torch.cuda.synchronize()
+        gerr = np.sum((gr.cpu().numpy().T - gx_sub) ** 2, 1)
+        last_grad[0] = float(np.sqrt(np.mean(gerr[sub_far])))
+        last_grad[1] = float(np.sqrt(np.mean(gerr[sub_deep])))
         return float(np.sqrt(np.mean((u.cpu().numpy() - ex_sub) ** 2))), a.elapsed_time(b) / 1e3
 
     kmax = 1 << 16
@@ -979,6 +1020,7 @@ def mixed_fixed_rmse(device, s):
     while r > tau and k < kmax:
         k = min(kmax, int(k * 1.25) + 1)
         r, t = rmse(k, 13)
+    grad_at_k, k_run = list(last_grad), k
     rate = st.m / t
     capped = bool(k >= kmax and r > tau)
     if capped:
@@ -987,7 +1029,10 @@ def mixed_fixed_rmse(device, s):
         k = int(np.ceil(kx))
     return {"variant": w.name, "tau_rmse": tau, "range_u": float(ex.max() - ex.min()), "bvc_pts_per_s": bvc_rate,
             "wost_walks_per_point": k, "wost_rmse": r, "wost_pts_per_s": rate, "bvc_over_wost": bvc_rate / rate,
-            "wost_extrapolated": capped, "wost_subset_points": int(st.m)}
+            "wost_extrapolated": capped, "wost_subset_points": int(st.m),
+            "grad_rmse": {"bvc": bvc_grad[0], "wost": grad_at_k[0], "bvc_beyond_4l": bvc_grad[1],
+                          "wost_beyond_4l": grad_at_k[1], "wost_walks_per_point": k_run,
+                          "wost_beyond_4l_equal_time": grad_at_k[1] * float(np.sqrt(bvc_rate / rate))}}
 
 
 def mixed_oracle_step_s(w, budget_s: float = 20.0):
