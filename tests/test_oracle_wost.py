@@ -119,6 +119,22 @@ def test_cube_closed_form(case):
     assert np.all(np.abs(z) < 4.5), (z, d)
 
 
+def test_cube_closed_form_on_the_neumann_faces():
+    # starts on Neumann triangles (inward hemisphere, the element under the
+    # walker sampled around it): u at the start within 4.5 SE
+    b = wl.box_mixed_3d()
+    w = oracle.Wost(b.V, b.F, b.neumann)
+    u = [(P, wl.poly3d_coeffs({(2, 0, 0): 1.0, (0, 2, 0): 1.0, (0, 0, 2): 1.0, (0, 1, 0): 0.3}))]
+    rng = np.random.default_rng(12)
+    els = rng.choice(np.where(b.neumann == 1)[0], 6, replace=False).astype(np.int32)
+    bary = rng.dirichlet([2.0, 2.0, 2.0], els.size)
+    z = np.einsum("ik,ikd->id", bary, b.V[b.F[els]].astype(np.float64)).astype(np.float32)
+    W = 3000
+    o = w.walks(u, [], u, [(P, [6.0])], z, els, W, 1e-4, 1 << 16, 35)
+    zs, d = _z(o["U"], W, wl.eval_terms(u, 3, z.astype(np.float64))[0])
+    assert np.all(np.abs(zs) < 4.5), (zs, d)
+
+
 def test_star_radius_sees_each_neumann_crossing_once():
     # R = min(d_D, d_sil): inside B(x, R) no ray from x crosses the Neumann
     # part twice (on the L-shape, the exterior notch cannot span the ball
