@@ -206,6 +206,16 @@ def profile_traffic(kernel: str, workload: str):
         return None
 
 
+def optional_part(fn):
+    """Runs an optional part of the report (fixed-RMSE comparison, CPU
+    baseline): a failure there is recorded in the JSON line instead of
+    losing the timed result."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 # ------------------------------------------------------------------ workloads
 def make_workload(name: str):
     from paper_2302_11825_gb300 import workloads as wl
@@ -666,7 +676,7 @@ def bench_batched(args, rank, local, ws):
         "clocks": clocks, "geometry_build_s": geometry_build_s, "walk_caps": run_stats["capped"],
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = batched_oracle_rate(w)
+        out["cpu_baseline"] = optional_part(lambda: batched_oracle_rate(w))
     if rank == 0:
         print(json.dumps(out))
     import torch.distributed as td
@@ -848,8 +858,10 @@ def bench_inverse(args, rank, local, ws):
         "walk_prims_per_step": cstats["prims"] / max(cstats["steps"], 1),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_cpu, info = inverse_oracle_step_s(w)
-        out["cpu_baseline"] = dict(info, value=1.0 / t_cpu, unit="gradient steps/s", kind="oracle")
+        def cpu():
+            t_cpu, info = inverse_oracle_step_s(w)
+            return dict(info, value=1.0 / t_cpu, unit="gradient steps/s", kind="oracle")
+        out["cpu_baseline"] = optional_part(cpu)
     if rank == 0:
         print(json.dumps(out))
     import torch.distributed as td
@@ -1172,10 +1184,12 @@ def bench_mixed(args, rank, local, ws):
         "walk_caps": run_stats["capped"],
     }
     if rank == 0 and ws == 1 and not args.no_fixed_rmse:
-        out["fixed_rmse"] = mixed_fixed_rmse(device, s)
+        out["fixed_rmse"] = optional_part(lambda: mixed_fixed_rmse(device, s))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_cpu, info = mixed_oracle_step_s(w)
-        out["cpu_baseline"] = dict(info, value=M / t_cpu, unit=UNIT, kind="oracle")
+        def cpu():
+            t_cpu, info = mixed_oracle_step_s(w)
+            return dict(info, value=M / t_cpu, unit=UNIT, kind="oracle")
+        out["cpu_baseline"] = optional_part(cpu)
     if rank == 0:
         print(json.dumps(out))
     import torch.distributed as td
@@ -1406,13 +1420,15 @@ def main():
         "walk_caps": run_stats["capped"],
     }
     if rank == 0 and ws == 1 and not args.no_fixed_rmse:
-        out["fixed_rmse"] = fixed_rmse_comparison(device, w)
+        out["fixed_rmse"] = optional_part(lambda: fixed_rmse_comparison(device, w))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_cpu, info = oracle_sample_rates(w)
-        out["cpu_baseline"] = {"value": M / t_cpu, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
-                               "sample": f"{info['walk_sample']}; {info['gather_sample']}; source test on 1024 "
-                                         f"candidates; extrapolated to one full step",
-                               "walks_per_s": info["walks_per_s"], "pairs_per_s": info["pairs_per_s"]}
+        def cpu():
+            t_cpu, info = oracle_sample_rates(w)
+            return {"value": M / t_cpu, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
+                    "sample": f"{info['walk_sample']}; {info['gather_sample']}; source test on 1024 "
+                              f"candidates; extrapolated to one full step",
+                    "walks_per_s": info["walks_per_s"], "pairs_per_s": info["pairs_per_s"]}
+        out["cpu_baseline"] = optional_part(cpu)
     if rank == 0:
         print(json.dumps(out))
     import torch.distributed as td
