@@ -1049,12 +1049,12 @@ def mixed_fixed_rmse(device, s):
 
 def mixed_oracle_step_s(w, budget_s: float = 20.0):
     """The oracle timed on bounded samples of one mixed step: walks on stars
-    from 32 cache samples (both kinds), a gather of 64 points against the
-    full cache, extrapolated to the step."""
+    from 32 cache samples in 2D, 8 in 3D (both kinds), a gather of 64 points
+    against the full cache, extrapolated to the step."""
     import oracle
     wo = oracle.Wost(w.V, w.F, w.neumann)
     z, n, e = oracle.sample_boundary_mixed(w.V, w.F, 4096, w.offset_l, 0, w.neumann)
-    sel = np.arange(0, 4096, 128)
+    sel = np.arange(0, 4096, 128 if w.dim == 2 else 512)
     se = np.where(w.neumann[e[sel]] == 1, e[sel], -1).astype(np.int32)
     t0 = time.perf_counter()
     wo.walks(w.g, w.h_value, w.h_potential, w.f, z[sel].astype(np.float32), se, w.walks, w.eps, MAX_STEPS, 0)
@@ -1076,6 +1076,15 @@ def mixed_oracle_step_s(w, budget_s: float = 20.0):
     return t_step, info
 
 
+def mixed_workload(name: str, samples: int = 0):
+    """`mixed`: the 2D star (2/3 Neumann, with sources); `mixed3d`: the 3D
+    channel with an ellipsoidal obstacle (96% Neumann, harmonic)."""
+    from paper_2302_11825_gb300 import workloads as wl
+    if name == "mixed3d":
+        return wl.tunnel_mixed_3d(seed=0, n_samples=samples or 65536)
+    return wl.star_mixed(seed=0, n_samples=samples or 65536)
+
+
 def bench_mixed(args, rank, local, ws):
     import torch
     from paper_2302_11825_gb300 import bvc
@@ -1083,7 +1092,7 @@ def bench_mixed(args, rank, local, ws):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     rank, ws = init_dist("nccl")
-    w = wl.star_mixed(seed=0, n_samples=args.samples or 65536)
+    w = mixed_workload(args.workload, args.samples)
     s = MixedSolver(w, device)
     M = s.m_far + s.m_near
     dim = w.dim
@@ -1206,7 +1215,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="star",
-                    choices=["star", "circle", "sphere", "batched", "inverse", "mixed"])
+                    choices=["star", "circle", "sphere", "batched", "inverse", "mixed", "mixed3d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed-rmse", action="store_true")
     ap.add_argument("--samples", type=int, default=0,
@@ -1233,9 +1242,8 @@ def main():
                               "e2e": {"value": 1.0 / t, "unit": "gradient steps/s", "h2d_bytes_per_step": 0,
                                       "d2h_bytes_per_step": 0}}))
             return 0
-        if args.workload == "mixed":
-            from paper_2302_11825_gb300 import workloads as wl
-            wm = wl.star_mixed()
+        if args.workload in ("mixed", "mixed3d"):
+            wm = mixed_workload(args.workload)
             ts = [mixed_oracle_step_s(wm, budget_s=6.0) for _ in range(args.warmup + args.steps)][args.warmup:]
             t = statistics.mean(x[0] for x in ts)
             M = wm.eval_pts.shape[0]
@@ -1270,7 +1278,7 @@ def main():
         return bench_batched(args, rank, local, ws)
     if args.workload == "inverse":
         return bench_inverse(args, rank, local, ws)
-    if args.workload == "mixed":
+    if args.workload in ("mixed", "mixed3d"):
         return bench_mixed(args, rank, local, ws)
     import torch
     from paper_2302_11825_gb300 import bvc

@@ -728,3 +728,29 @@ def box_mixed_3d(cells_per_unit: int = 4, n_samples: int = 4096, walks: int = 64
     eps = 1e-3 * bbox_diagonal(V)
     return MixedWorkload("box_mixed_3d", 3, V, F, neu, u, [], u, [], n_samples, walks, 5 * eps, eps, pts, exact=u,
                          seed=seed)
+
+
+def tunnel_mixed_3d(n_samples: int = 65536, walks: int = 32, n_points: int = 200000, n_box: int = 8,
+                    subdiv: int = 5, seed: int = 0) -> MixedWorkload:
+    """A 3D mixed channel problem (a wind-tunnel-like setting): the box [-2,2] x [-1,1]^2 with an ellipsoidal obstacle
+    (semi-axes 0.5, 0.35, 0.35 at the origin, icosphere subdivision 5: 20,480
+    triangles, wound inward); Dirichlet on the inlet and outlet faces x = -2,
+    2, Neumann on the four walls and the obstacle.  Manufactured harmonic
+    u* = x + 0.3 x y + 0.2 (y^2 - z^2): g = u*, h = n . grad u*.  65,536
+    samples x 32 walks; 200,000 uniform points in the domain at least 0.02
+    from the boundary.  eps = 1e-3 x bbox diagonal, l = 5 eps."""
+    lo, hi = (-2.0, -1.0, -1.0), (2.0, 1.0, 1.0)
+    ax = (0.5, 0.35, 0.35)
+    V, F = box_with_obstacles(lo, hi, n_box=n_box, ellipsoids=[((0.0, 0.0, 0.0), ax)], subdiv=subdiv)
+    mid = element_midpoints(V, F)
+    neu = ~((np.abs(mid[:, 0] - lo[0]) < 1e-6) | (np.abs(mid[:, 0] - hi[0]) < 1e-6))
+    u = [(POLY, poly3d_coeffs({(1, 0, 0): 1.0, (1, 1, 0): 0.3, (0, 2, 0): 0.2, (0, 0, 2): -0.2}))]
+    rng = np.random.default_rng(seed)
+    pts = []
+    while sum(len(q) for q in pts) < n_points:
+        q = rng.uniform(lo, hi, (2 * n_points, 3))
+        pts.append(q[in_domain_box_obstacles(q, lo, hi, [((0.0, 0.0, 0.0), ax)], 0.02)])
+    pts = np.concatenate(pts)[:n_points].astype(np.float32)
+    eps = 1e-3 * bbox_diagonal(V)
+    return MixedWorkload("tunnel_mixed_3d", 3, V, F, neu.astype(np.uint8), u, [], u, [], n_samples, walks, 5 * eps,
+                         eps, pts, exact=u, seed=seed)

@@ -49,12 +49,24 @@ CASES = {
     "lshape": lambda: (*_lshape(), "l"),
     "star": lambda: (*_star_valleys(), "star"),
     "cube": lambda: (wl.box_mixed_3d().V, wl.box_mixed_3d().F, wl.box_mixed_3d().neumann, "cube"),
+    "tunnel": lambda: (*_tunnel_small(), "tunnel"),
 }
+
+
+def _tunnel_small():
+    t = wl.tunnel_mixed_3d(n_points=16, n_box=4, subdiv=3)
+    return t.V, t.F, t.neumann
 
 
 def _pts(case, V, n, seed):
     if case == "cube":
         return np.random.default_rng(seed).uniform(0.02, 0.98, (n, 3)).astype(np.float32)
+    if case == "tunnel":
+        rng = np.random.default_rng(seed)
+        q = rng.uniform((-2.0, -1.0, -1.0), (2.0, 1.0, 1.0), (8 * n, 3))
+        q = q[wl.in_domain_box_obstacles(q, (-2.0, -1.0, -1.0), (2.0, 1.0, 1.0),
+                                         [((0.0, 0.0, 0.0), (0.5, 0.35, 0.35))], 0.01)]
+        return q[:n].astype(np.float32)
     if case == "star":
         return _inside_points(V, n, seed, -1.3, 1.3, "star")
     return _inside_points(V, n, seed)
@@ -131,14 +143,16 @@ def test_walks_match_oracle_per_walk(case, src):
     W = 32
     rec, steps, prim, o = _walk_parity(V, F, neu, g, ([], []), f, starts, None, None, W, 2e-3, 11)
     same = steps == o["steps"]
-    assert same.mean() >= 0.97, same.mean()
-    # reflections off concave Neumann walls amplify the FP32 / FP64 rounding
-    # difference of the path (the star's valleys); most walks still agree
-    # to rounding, and the rest agree in distribution
+    # reflections off concave Neumann walls (the star's valleys) and off the
+    # convex obstacle (the tunnel) amplify the FP32 / FP64 rounding
+    # difference of the path; most walks still agree to rounding, and the
+    # rest agree in distribution
+    chaotic = case in ("star", "tunnel")
+    assert same.mean() >= (0.97 if not chaotic else 0.9), same.mean()
     sc = np.abs(o["U"]).max() + 1e-9
     du = np.abs(rec[0] - o["U"])
     close = same & (du < 2e-4 * sc)
-    assert close.mean() >= (0.97 if case != "star" else 0.85), close.mean()
+    assert close.mean() >= (0.97 if not chaotic else 0.85), close.mean()
     # ends at a vertex shared by two Dirichlet elements may pick either
     assert (prim[close] == o["prim"][close]).mean() >= 0.99
     for a in range(dim):
@@ -274,6 +288,20 @@ def test_mixed_cache_cube_closed_form():
     m, cache, fp, uf, npts, un = _mixed_solve(b)
     ex = wl.eval_terms(b.g, 3, fp.astype(np.float64))[0]
     assert np.sqrt(np.mean((uf - ex) ** 2)) < 0.03 * (ex.max() - ex.min())
+
+
+def test_mixed_cache_tunnel_closed_form():
+    # the 3D channel with an ellipsoidal obstacle (20,480 triangles, 96%
+    # Neumann) at the bench's sample count and half its walks
+    t = wl.tunnel_mixed_3d(n_samples=65536, walks=16, n_points=4000)
+    m, cache, fp, uf, npts, un = _mixed_solve(t)
+    assert m.whole.stats(reset=True)["capped"] <= 1e-5 * t.n_samples * t.walks
+    ex = wl.eval_terms(t.g, 3, fp.astype(np.float64))[0]
+    assert np.all(np.isfinite(uf))
+    assert np.sqrt(np.mean((uf - ex) ** 2)) < 0.03 * (ex.max() - ex.min())
+    if un is not None:
+        exn = wl.eval_terms(t.g, 3, npts.astype(np.float64))[0]
+        assert np.sqrt(np.mean((un - exn) ** 2)) < 0.03 * (ex.max() - ex.min())
 
 
 def test_wost_estimate_closed_form():
