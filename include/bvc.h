@@ -586,6 +586,8 @@ typedef struct {
   int32_t dim;
   int64_t n_dirichlet, n_neumann; /* elements */
   int64_t n_silhouette;           /* silhouette candidates (vertices 2D, edges 3D) */
+  int64_t n_silhouette_tree;      /* those in the silhouette tree: all but the flat ones (two elements
+                                     with equal normals, which are never silhouettes) */
   double dirichlet_measure, neumann_measure;
   size_t device_bytes;            /* the silhouette tree and maps (geometries not included) */
 } bvc_mixed_info;

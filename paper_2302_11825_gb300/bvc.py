@@ -91,7 +91,8 @@ class NeumannStruct(C.Structure):
 
 class MixedInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_dirichlet", C.c_int64), ("n_neumann", C.c_int64),
-                ("n_silhouette", C.c_int64), ("dirichlet_measure", C.c_double), ("neumann_measure", C.c_double),
+                ("n_silhouette", C.c_int64), ("n_silhouette_tree", C.c_int64),
+                ("dirichlet_measure", C.c_double), ("neumann_measure", C.c_double),
                 ("device_bytes", C.c_size_t)]
 
 

@@ -1033,6 +1033,21 @@ static std::vector<SilCand> silhouette_candidates(int dim, int64_t n_verts, cons
   return out;
 }
 
+// A candidate whose two elements lie in one line / plane (unit normals equal
+// to within 2^-23, FP32 resolution) has no dihedral angle: every point has
+// the same signed distance to both, so the silhouette rule never holds for
+// it.  Such candidates (the inside of a flat wall) stay out of the tree: a
+// walker on the wall could otherwise prune none of them by its cone.
+static bool flat_candidate(int dim, const float* verts, const int32_t* prims, const SilCand& c) {
+  if (c.always || c.e0 < 0 || c.e1 < 0) return false;
+  double n0[3] = {0, 0, 0}, n1[3] = {0, 0, 0};
+  elem_normal(dim, verts, prims + (int64_t)c.e0 * dim, n0);
+  elem_normal(dim, verts, prims + (int64_t)c.e1 * dim, n1);
+  double d2 = 0.0;
+  for (int a = 0; a < dim; ++a) d2 += (n0[a] - n1[a]) * (n0[a] - n1[a]);
+  return d2 <= 0x1p-46;
+}
+
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Normal cones of the silhouette tree: a cone (unit axis, half-angle)
@@ -1186,7 +1201,11 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
     }
   }
   // silhouette candidates and their tree
-  const std::vector<SilCand> cand = silhouette_candidates(dim, n_verts, prims, n_prims, neumann);
+  std::vector<SilCand> cand = silhouette_candidates(dim, n_verts, prims, n_prims, neumann);
+  m->n_sil = (int64_t)cand.size();
+  cand.erase(std::remove_if(cand.begin(), cand.end(),
+                            [&](const SilCand& c) { return flat_candidate(dim, verts, prims, c); }),
+             cand.end());
   const int64_t ns = (int64_t)cand.size();
   std::vector<float4> snodes, sprims_unused, sprims;
   std::vector<int32_t> ids;
@@ -1219,7 +1238,6 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
       }
     }
   }
-  m->n_sil = ns;
   m->n_sil_nodes = ns > 0 ? (int64_t)snodes.size() / (dim == 2 ? 3 : 4) : 0;
   // per node and child, the cone of the normals of the candidates below
   std::vector<float4> scones((size_t)m->n_sil_nodes * 2, make_float4(0, 0, 0, -1.0f));
@@ -1331,6 +1349,7 @@ extern "C" bvc_status bvc_mixed_get_info(bvc_mixed m, bvc_mixed_info* info) {
   info->n_dirichlet = m->n_dir;
   info->n_neumann = m->n_neu;
   info->n_silhouette = m->n_sil;
+  info->n_silhouette_tree = m->sil.n;
   info->dirichlet_measure = m->dir_measure;
   info->neumann_measure = m->neu_measure;
   info->device_bytes = m->arena_bytes;

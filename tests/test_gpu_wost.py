@@ -72,6 +72,26 @@ def _pts(case, V, n, seed):
     return _inside_points(V, n, seed)
 
 
+def _flat_candidates(V, F, neu):
+    """Silhouette candidates (vertices / edges whose elements are all
+    Neumann) with exactly two elements of equal unit normal (to 2^-23)."""
+    V = V.astype(np.float64)
+    if V.shape[1] == 3:
+        n = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+        keys = [[(min(f[k], f[(k + 1) % 3]), max(f[k], f[(k + 1) % 3])) for k in range(3)] for f in F]
+    else:
+        d = V[F[:, 1]] - V[F[:, 0]]
+        n = np.stack([d[:, 1], -d[:, 0]], 1)
+        keys = [[(v, v) for v in f] for f in F]
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    adj = {}
+    for e, ks in enumerate(keys):
+        for k in ks:
+            adj.setdefault(k, []).append(e)
+    return sum(1 for es in adj.values() if len(es) == 2 and neu[es[0]] and neu[es[1]]
+               and np.sum((n[es[0]] - n[es[1]]) ** 2) <= 2.0 ** -46)
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_queries_match_oracle(case):
     V, F, neu, _ = CASES[case]()
@@ -79,6 +99,8 @@ def test_queries_match_oracle(case):
     w = oracle.Wost(V, F, neu)
     inf = m.info()
     assert (inf.n_dirichlet, inf.n_neumann, inf.n_silhouette) == w.counts()
+    # flat candidates are never silhouettes and stay out of the tree
+    assert inf.n_silhouette_tree == inf.n_silhouette - _flat_candidates(V, F, neu)
     pts = _pts(case, V, 3000, 1)
     dd, ds = bvc.mixed_query(m, bvc.soa(pts))
     torch.cuda.synchronize()
