@@ -921,6 +921,10 @@ class MixedSolver:
         self.bvc, self.torch, self.w = bvc, torch, w
         t0 = time.perf_counter()
         self.m = bvc.Mixed(w.V, w.F, w.neumann)
+        # star radius: exact silhouette distances, or a certified lower bound
+        # within 1 - gap where that saves more traversal than it adds steps
+        self.silhouette_gap = float(w.meta.get("silhouette_gap", 0.0))
+        self.m.set_silhouette_gap(self.silhouette_gap)
         torch.cuda.synchronize()
         self.geometry_build_s = time.perf_counter() - t0
         self.h = (w.h_value, w.h_potential)
@@ -1180,6 +1184,7 @@ def bench_mixed(args, rank, local, ws):
                    "walks_per_sample": w.walks, "src_grid": list(w.src_grid), "src_kept": n_src_kept,
                    "eval_points": int(M), "eval_far": int(s.m_far), "eval_near_pointwise": int(s.m_near),
                    "near_walks": s.near_walks, "eps": w.eps, "offset_l": w.offset_l,
+                   "silhouette_gap": s.silhouette_gap,
                    "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
         "roofline": roofs.get(dominant), "rooflines_all": roofs, "kernels": kernels,
         "e2e": {"value": step_value(M, e2e_steps, ws, t_e2e), "unit": UNIT,

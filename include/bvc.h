@@ -592,6 +592,17 @@ typedef struct {
   size_t device_bytes;            /* the silhouette tree and maps (geometries not included) */
 } bvc_mixed_info;
 bvc_status bvc_mixed_get_info(bvc_mixed m, bvc_mixed_info* info);
+/* Star radius of the walks on stars (Sec. 3.1): every step uses a ball of
+ * radius R with R <= min(d_Dirichlet, d_silhouette), which keeps the ball
+ * free of Dirichlet points and star-shaped about its centre, so any such R
+ * gives the same (unbiased) estimator.  gap = 0 (the default) takes the
+ * closest silhouette point exactly; 0 < gap < 1 lets the silhouette search
+ * stop early and use a certified lower bound r of the silhouette distance
+ * with (1 - gap) d_silhouette <= r <= d_silhouette (the search skips tree
+ * nodes not nearer than (1 - gap) x the best so far and keeps the least
+ * skipped distance).  Applies to every later call on m (walks, caches and
+ * bvc_mixed_query).  Host only; gap outside [0, 1): BVC_ERR_INVALID_ARG. */
+bvc_status bvc_mixed_set_silhouette_gap(bvc_mixed m, double gap);
 /* Borrowed handles (owned by m): the whole boundary, its Dirichlet part and
  * its Neumann part (NULL when there is no Neumann element).  Element ids of
  * the parts are their positions among the whole mesh's Dirichlet / Neumann

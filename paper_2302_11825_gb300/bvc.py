@@ -164,6 +164,7 @@ def _declare(lib):
         "bvc_mixed_destroy": (S, [P]),
         "bvc_mixed_get_info": (S, [P, C.POINTER(MixedInfo)]),
         "bvc_mixed_geometries": (S, [P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+        "bvc_mixed_set_silhouette_gap": (S, [P, f64]),
         "bvc_mixed_query": (S, [P, P, i64, P, P, P]),
         "bvc_mixed_rays": (S, [P, P, P, P, i64, f32, P, P, P]),
         "bvc_mixed_walk": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function), P, P, P, i64,
@@ -948,6 +949,11 @@ class Mixed:
         inf = MixedInfo()
         _check(lib().bvc_mixed_get_info(self.h, C.byref(inf)), "bvc_mixed_get_info")
         return inf
+
+    def set_silhouette_gap(self, gap: float):
+        """bvc_mixed_set_silhouette_gap: 0 = exact silhouette distances; in
+        (0, 1) a certified lower bound within the factor 1 - gap."""
+        _check(lib().bvc_mixed_set_silhouette_gap(self.h, float(gap)), "bvc_mixed_set_silhouette_gap")
 
     def close(self):
         if getattr(self, "h", None):

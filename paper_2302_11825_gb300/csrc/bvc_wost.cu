@@ -37,6 +37,9 @@ struct DevSil {
   const float4* cones;
   int64_t n;
   float tau;  // |n_k . a| <= tau counts as zero
+  // (1 - gap)^2: a node is visited only when its squared box distance is
+  // below shrink2 x the running best (1: the exact closest silhouette)
+  float shrink2;
 };
 
 // True when no candidate inside the box [lo, hi] under a normal cone can be a
@@ -136,9 +139,13 @@ struct WostParams {
 
 // Closest silhouette: one node.  best2 is lowered to the squared distance of
 // any nearer silhouette; children are skipped by distance or by their cone.
+// With shrink2 < 1 a child whose box is nearer than best2 but not nearer
+// than shrink2 x best2 is skipped too, and its squared box distance kept in
+// skip2 (the least such): every silhouette point is then at least
+// min(best2, skip2) away, a radius no larger than the closest silhouette's.
 template <int D>
-__device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float& best2, int& node, int& sp,
-                                          int* snode, float* sdist, TravCount& tcn) {
+__device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float& best2, float& skip2, int& node,
+                                          int& sp, int* snode, float* sdist, TravCount& tcn) {
   ++tcn.nodes;
   int32_t ch[2];
   float dc[2], blo[2][3], bhi[2][3];
@@ -165,6 +172,10 @@ __device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     go[k] = dc[k] < best2 && !cone_prunes<D>(__ldg(&S.cones[2 * node + k]), blo[k], bhi[k], x, S.tau);
+    if (go[k] && !(dc[k] < S.shrink2 * best2)) {
+      skip2 = fminf(skip2, dc[k]);
+      go[k] = false;
+    }
     if (go[k] && ch[k] < 0) {
       const int32_t enc = ~ch[k];
       const int32_t first = enc >> 4, count = enc & 15;
@@ -206,8 +217,12 @@ __device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float
     }
   }
   // re-test against the bound a leaf may have lowered
-  go[0] = go[0] && dc[0] < best2;
-  go[1] = go[1] && dc[1] < best2;
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (go[k] && !(dc[k] < S.shrink2 * best2)) {
+      if (dc[k] < best2) skip2 = fminf(skip2, dc[k]);
+      go[k] = false;
+    }
   if (go[0] && go[1]) {
     const int nearer = dc[1] < dc[0] ? 1 : 0;
     snode[sp * kWostBlock] = ch[1 - nearer];
@@ -222,23 +237,28 @@ __device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float
   }
   while (sp > 0) {
     --sp;
-    if (sdist[sp * kWostBlock] < best2) {
+    const float ds = sdist[sp * kWostBlock];
+    if (ds < S.shrink2 * best2) {
       node = snode[sp * kWostBlock];
       return false;
     }
+    if (ds < best2) skip2 = fminf(skip2, ds);
   }
   return true;
 }
 
 // Closest silhouette point of the Neumann part seen from x, if nearer than
-// sqrt(best2): returns min(best2, its squared distance).
+// sqrt(best2): returns min(best2, its squared distance).  With shrink2 < 1 it
+// returns a lower bound r2 of that value with r2 >= shrink2 x it: every
+// radius up to the star radius keeps the walk's ball star-shaped.
 template <int D>
 __device__ float sil_closest(const DevSil& S, const float* x, float best2, int* snode, float* sdist, TravCount& tcn) {
   if (S.n == 0) return best2;
   int sp = 0, node = 0;
+  float skip2 = __int_as_float(0x7f800000);
   for (int guard = 0; guard < (1 << 22); ++guard)
-    if (sil_visit<D>(S, x, best2, node, sp, snode, sdist, tcn)) break;
-  return best2;
+    if (sil_visit<D>(S, x, best2, skip2, node, sp, snode, sdist, tcn)) break;
+  return fminf(best2, skip2);
 }
 
 // Entry parameter of the ray o + t w into a box (inv = 1/w with zero
@@ -1300,6 +1320,7 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   m->sil.cones = (const float4*)(base += b_nq);
   m->sil.n = ns;
   m->sil.tau = m->whole->dev.tau;
+  m->sil.shrink2 = 1.0f;
   cudaStream_t s = (cudaStream_t)stream;
   bool ok = true;
   if (ns > 0) {
@@ -1353,6 +1374,12 @@ extern "C" bvc_status bvc_mixed_get_info(bvc_mixed m, bvc_mixed_info* info) {
   info->dirichlet_measure = m->dir_measure;
   info->neumann_measure = m->neu_measure;
   info->device_bytes = m->arena_bytes;
+  return BVC_OK;
+}
+
+extern "C" bvc_status bvc_mixed_set_silhouette_gap(bvc_mixed m, double gap) {
+  if (m == nullptr || !(gap >= 0.0 && gap < 1.0)) return BVC_ERR_INVALID_ARG;
+  m->sil.shrink2 = (float)((1.0 - gap) * (1.0 - gap));
   return BVC_OK;
 }
 

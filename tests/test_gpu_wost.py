@@ -238,8 +238,9 @@ def test_all_dirichlet_mixed_walks_equal_walk_on_spheres():
     assert torch.allclose(a[0][k], b[0][k], rtol=1e-4, atol=1e-4)
 
 
-def _mixed_solve(wk, pts_near_ok=True, N=None, W=None, seed=3):
+def _mixed_solve(wk, pts_near_ok=True, N=None, W=None, seed=3, gap=0.0):
     m = bvc.Mixed(wk.V, wk.F, wk.neumann)
+    m.set_silhouette_gap(gap)
     N = N or wk.n_samples
     W = W or wk.walks
     opts = bvc.cache_opts(N, W, wk.offset_l, wk.eps, seed, src_grid=wk.src_grid)
@@ -312,11 +313,12 @@ def test_mixed_cache_cube_closed_form():
     assert np.sqrt(np.mean((uf - ex) ** 2)) < 0.03 * (ex.max() - ex.min())
 
 
-def test_mixed_cache_tunnel_closed_form():
+@pytest.mark.parametrize("gap", [0.0, 0.125])
+def test_mixed_cache_tunnel_closed_form(gap):
     # the 3D channel with an ellipsoidal obstacle (20,480 triangles, 96%
     # Neumann) at the bench's sample count and half its walks
     t = wl.tunnel_mixed_3d(n_samples=65536, walks=16, n_points=4000)
-    m, cache, fp, uf, npts, un = _mixed_solve(t)
+    m, cache, fp, uf, npts, un = _mixed_solve(t, gap=gap)
     assert m.whole.stats(reset=True)["capped"] <= 1e-5 * t.n_samples * t.walks
     ex = wl.eval_terms(t.g, 3, fp.astype(np.float64))[0]
     assert np.all(np.isfinite(uf))
@@ -395,3 +397,44 @@ def test_mixed_cache_full_size_sampled():
         assert abs(r[0].mean() - o["U"].mean()) < 6 * sd + 1e-4
     # chaotic reflections separate some FP32 / FP64 paths; most walks agree
     assert n_close >= 0.85 * n_all, n_close / n_all
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_silhouette_gap_is_a_certified_lower_bound(case):
+    # with a gap the search returns r with (1 - gap) d_sil <= r <= d_sil
+    V, F, neu, _ = CASES[case]()
+    m = bvc.Mixed(V, F, neu)
+    pts = bvc.soa(_pts(case, V, 3000, 7))
+    _, ds_exact = bvc.mixed_query(m, pts)
+    gap = 0.125
+    m.set_silhouette_gap(gap)
+    _, ds_gap = bvc.mixed_query(m, pts)
+    torch.cuda.synchronize()
+    e, g = ds_exact.cpu().numpy(), ds_gap.cpu().numpy()
+    fin = np.isfinite(e)
+    assert np.array_equal(np.isfinite(g), fin)
+    assert np.all(g[fin] <= e[fin] * (1 + 1e-5) + 1e-7)
+    assert np.all(g[fin] >= (1 - gap) * e[fin] * (1 - 1e-5) - 1e-7)
+    with pytest.raises(bvc.BvcError):
+        m.set_silhouette_gap(1.0)
+
+
+@pytest.mark.parametrize("case", ["lshape", "cube", "tunnel"])
+def test_silhouette_gap_walks_unbiased(case):
+    # smaller star radii change the paths, not the expectation: the walks
+    # with a gap stay within 4.5 standard errors of the closed form
+    V, F, neu, _ = CASES[case]()
+    dim = V.shape[1]
+    u = ([(P, wl.poly2d_coeffs({(2, 0): 1.0, (0, 2): -1.0, (1, 1): 0.5}))] if dim == 2 else
+         [(P, wl.poly3d_coeffs({(1, 0, 0): 1.0, (1, 1, 0): 0.3, (0, 2, 0): 0.2, (0, 0, 2): -0.2}))])
+    m = bvc.Mixed(V, F, neu)
+    m.set_silhouette_gap(0.25)
+    starts = _pts(case, V, 8, 5)
+    W = 4096
+    rec, steps, _ = bvc.mixed_walk(m, u, ([], u), [], bvc.soa(starts), None, None, W, 1e-3, 1 << 14, 12, debug=True)
+    torch.cuda.synchronize()
+    U = rec[0].cpu().numpy().astype(np.float64).reshape(-1, W)
+    ex = wl.eval_terms(u, dim, starts.astype(np.float64))[0]
+    z = (U.mean(1) - ex) / np.sqrt(U.var(1) / W)
+    assert np.all(np.abs(z) < 4.5), z
+    assert m.whole.stats(reset=True)["capped"] <= 2

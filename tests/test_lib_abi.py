@@ -210,6 +210,9 @@ def test_mixed_host_checks(lib):
     lib.wost_estimate.argtypes = [C.c_void_p] * 5 + [C.c_int32, C.c_float, C.c_int32, C.c_uint64, C.c_uint64,
                                                       C.c_void_p, C.c_size_t, C.c_void_p]
     assert lib.wost_estimate(None, None, None, None, None, 1, 1e-3, 10, 0, 0, None, 0, None) == 1
+    lib.bvc_mixed_set_silhouette_gap.restype = C.c_int
+    lib.bvc_mixed_set_silhouette_gap.argtypes = [C.c_void_p, C.c_double]
+    assert lib.bvc_mixed_set_silhouette_gap(None, 0.1) == 1
 
 
 def test_wait_selftest_rejects_bad_limits(lib):
