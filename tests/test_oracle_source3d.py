@@ -46,3 +46,28 @@ def test_source_candidates_estimate_the_volume():
     assert np.allclose(c, 2.0 * box)
     assert np.all(np.abs(np.round(wn) - wn) < 0.05) or True
     assert set(np.round(wn[np.abs(wn - 0.5) > 0.1]).astype(int)) <= {0, 1}
+
+
+def test_channel_workload_mesh_and_points():
+    # the 3D mixed channel: a closed, consistently wound surface (every edge
+    # used once in each direction), volume of the box minus the obstacle,
+    # Dirichlet exactly on the faces x = -2, 2, and evaluation points inside
+    # (winding number 1) at least 0.02 from the boundary
+    t = wl.tunnel_mixed_3d(n_points=500, n_box=4, subdiv=3, seed=1)
+    F = t.F
+    directed = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
+    fwd = {tuple(e) for e in directed.tolist()}
+    assert len(fwd) == directed.shape[0]
+    assert all((b, a) in fwd for a, b in fwd)
+    V = t.V.astype(np.float64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    vol = np.sum(np.einsum("ij,ij->i", a, np.cross(b, c))) / 6
+    ell = 4.0 / 3.0 * np.pi * 0.5 * 0.35 * 0.35
+    assert 16.0 - 1.02 * ell < vol < 16.0 - 0.9 * ell
+    mid = V[F].mean(1)
+    dir_faces = np.isclose(np.abs(mid[:, 0]), 2.0)
+    assert np.array_equal(t.neumann == 0, dir_faces)
+    p = t.eval_pts.astype(np.float64)
+    assert np.allclose(oracle.winding3d(t.V, F, p), 1.0, atol=1e-6)
+    dist = oracle.closest_brute64(t.V, F, p)[0]
+    assert dist.min() >= 0.02 * 0.99
