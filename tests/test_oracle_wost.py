@@ -297,3 +297,38 @@ def test_channel_closed_form():
     o = w.walks(u, [], u, [], pts, None, W, 1e-3, 1 << 16, 36)
     z, d = _z(o["U"], W, wl.eval_terms(u, 3, pts.astype(np.float64))[0])
     assert np.all(np.abs(z) < 4.5), (z, d)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mixed_boundary_samples(dim):
+    # Sec. 3.2 on a mixed boundary: samples on Neumann elements lie on their
+    # element, samples on Dirichlet elements sit l inside along -n; the share
+    # of Neumann samples is the Neumann share of the boundary measure
+    # (stratified: within a few samples)
+    if dim == 2:
+        V, F, side, neu = _square()
+    else:
+        b = wl.box_mixed_3d()
+        V, F, neu = b.V, b.F, b.neumann
+    N, l = 3000, 0.01
+    z, n, e = oracle.sample_boundary_mixed(V, F, N, l, 4, neu)
+    assert np.allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-12)
+    on = neu[e] == 1
+    p = z + np.where(on, 0.0, l)[:, None] * n
+    for i in range(N):
+        d = oracle.closest_brute64(V, F[e[i]:e[i] + 1], p[i:i + 1])[0][0]
+        assert d < 1e-6
+    V64 = V.astype(np.float64)
+    if dim == 2:
+        meas = np.linalg.norm(V64[F[:, 1]] - V64[F[:, 0]], axis=1)
+    else:
+        meas = 0.5 * np.linalg.norm(np.cross(V64[F[:, 1]] - V64[F[:, 0]], V64[F[:, 2]] - V64[F[:, 0]]), axis=1)
+    share = meas[neu == 1].sum() / meas.sum()
+    assert abs(on.sum() - share * N) <= 3
+    # a Dirichlet sample is l from its own element, and inside the domain
+    for i in np.where(~on)[0][::7]:
+        d = oracle.closest_brute64(V, F[e[i]:e[i] + 1], z[i:i + 1])[0][0]
+        assert abs(d - l) < 1e-7
+    inside = (oracle.inside2d_f32(V, F, z[~on]).astype(bool) if dim == 2 else
+              np.isclose(oracle.winding3d(V, F, z[~on]), 1.0, atol=1e-6))
+    assert np.all(inside)
