@@ -1187,6 +1187,9 @@ def bench_mixed(args, rank, local, ws):
                    "silhouette_gap": s.silhouette_gap,
                    "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
         "roofline": roofs.get(dominant), "rooflines_all": roofs, "kernels": kernels,
+        "kernels_note": "each launch timed by events on its own stream; the pointwise walks near the Dirichlet "
+                        "part and their reduction run on a second stream beside the cache build, so their "
+                        "times include waiting for SMs",
         "e2e": {"value": step_value(M, e2e_steps, ws, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(M * dim * 4), "d2h_bytes_per_step": int(M * (1 + dim) * 8),
                 "steps": e2e_steps},
