@@ -31,6 +31,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -104,6 +105,37 @@ def step_value(points: int, steps: int, world: int, t_max: float) -> float:
 def rank_seed(rank: int, k: int, base: int) -> int:
     """Disjoint Philox seeds per rank and step (replicas are independent)."""
     return base + 10_000 * rank + k
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def single_core(fn):
+    """Runs fn with the oracle's parallel loops on one thread."""
+    import oracle
+    n = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        return fn()
+    finally:
+        oracle.set_num_threads(n)
 
 
 def measured_peaks():
@@ -486,8 +518,19 @@ def oracle_sample_rates(w, budget_s: float = 20.0):
     M = w.eval_pts.shape[0]
     kept_src = 0.45 * n_src_cand
     t_step = (N * w.walks) / walk_rate + M * (N + kept_src) / pair_rate + src_s
+
+    def one_core():
+        t0 = time.perf_counter()
+        oracle.walks(bvh, w.g, w.f, z[:16].astype(np.float32), w.walks, w.eps, MAX_STEPS, 0, 0, 0)
+        t1 = time.perf_counter()
+        oracle.gather(zc, nc, rng.standard_normal(N), rng.standard_normal(N), 1.0, w.eval_pts[:8])
+        t2 = time.perf_counter()
+        return {"walks_per_s": 16 * w.walks / (t1 - t0), "pairs_per_s": 8 * N / (t2 - t1),
+                "sample": f"16 samples x {w.walks} walks; 8 points x {N} samples"}
+
     info = {"walks_per_s": walk_rate, "pairs_per_s": pair_rate, "walk_sample": f"{ns} samples x {w.walks} walks",
-            "gather_sample": f"{mp} points x {N} samples", "source_s": src_s, "threads": oracle.num_threads()}
+            "gather_sample": f"{mp} points x {N} samples", "source_s": src_s, "threads": oracle.num_threads(),
+            "single_core": single_core(one_core), "cpu_model": cpu_model()}
     return t_step, info
 
 
@@ -1074,7 +1117,20 @@ def mixed_oracle_step_s(w, budget_s: float = 20.0):
     M = w.eval_pts.shape[0]
     n_src = w.src_grid[0] * w.src_grid[1] if w.f else 0
     t_step = N * w.walks / walk_rate + M * (N + 0.45 * n_src) / pair_rate
+
+    def one_core():
+        t0 = time.perf_counter()
+        wo.walks(w.g, w.h_value, w.h_potential, w.f, z[sel[:2]].astype(np.float32), se[:2], w.walks, w.eps,
+                 MAX_STEPS, 0)
+        t1 = time.perf_counter()
+        oracle.gather(zc, nc, rng.standard_normal(N), rng.standard_normal(N), 1.0,
+                      w.eval_pts[:8].astype(np.float64))
+        t2 = time.perf_counter()
+        return {"walks_per_s": 2 * w.walks / (t1 - t0), "pairs_per_s": 8 * N / (t2 - t1),
+                "sample": f"2 samples x {w.walks} walks on stars; 8 points x {N} samples"}
+
     info = {"cores": oracle.num_threads(), "walks_per_s": walk_rate, "pairs_per_s": pair_rate,
+            "single_core": single_core(one_core), "cpu_model": cpu_model(),
             "sample": f"{sel.size} samples x {w.walks} walks on stars; 64 points x {N} samples; "
                       f"extrapolated to one full step"}
     return t_step, info
@@ -1443,7 +1499,8 @@ def main():
             return {"value": M / t_cpu, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
                     "sample": f"{info['walk_sample']}; {info['gather_sample']}; source test on 1024 "
                               f"candidates; extrapolated to one full step",
-                    "walks_per_s": info["walks_per_s"], "pairs_per_s": info["pairs_per_s"]}
+                    "walks_per_s": info["walks_per_s"], "pairs_per_s": info["pairs_per_s"],
+                    "single_core": info["single_core"], "cpu_model": info["cpu_model"]}
         out["cpu_baseline"] = optional_part(cpu)
     if rank == 0:
         print(json.dumps(out))

@@ -92,6 +92,7 @@ def _load():
                 "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
                 "orc_sphere_step": (None, [C.c_int, f64, f64, f64, f64, P, P, P, P]),
                 "orc_num_threads": (C.c_int, []),
+                "orc_set_num_threads": (None, [C.c_int]),
                 "orc_sample_boundary_mixed": (None, [C.c_int, P, P, i64, i64, f64, u64, P, P, P, P]),
                 "orc_fn_grad": (None, [P, C.c_int, P, P]),
                 "orc_neumann_eval": (f64, [P, P, C.c_int, P, P]),
@@ -128,6 +129,11 @@ def _i32(a):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later parallel loops."""
+    _load().orc_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- Philox

@@ -1504,6 +1504,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of later parallel loops (timing the oracle on one core). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Walk on stars (Sec. 3.1; Fig. "WoS vs WoSt") for a mixed boundary:       */
 /* Laplace(u) = f in Omega, u = g on the Dirichlet part, du/dn = h on the   */
