@@ -4,6 +4,7 @@ summaries (taken only on matching kernel sources), the optional report parts
 and the mixed workload switch."""
 import os
 import sys
+from pathlib import Path
 
 import pytest
 
@@ -12,8 +13,8 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_clock_summary_median_and_reasons(tmp_path):
-    p = tmp_path / "clocks.csv"
+def test_clock_summary_median_and_reasons(work_dir):
+    p = Path(work_dir) / "clocks.csv"
     p.write_text("0, 2070, 2070, 400.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
                  "0, 1980, 2070, 610.0, 0x4, Not Active, Not Active, Not Active, Active\n"
                  "0, 2040, 2070, 590.2, 0x0, Not Active, Not Active, Not Active, Not Active\n"
@@ -33,7 +34,8 @@ def test_clock_summary_without_samples():
     assert c.summary()["reasons"] == ["unavailable"]
 
 
-def test_profile_traffic_needs_matching_sources(tmp_path, monkeypatch):
+def test_profile_traffic_needs_matching_sources(work_dir, monkeypatch):
+    tmp_path = Path(work_dir)
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     csrc = tmp_path / "paper_2302_11825_gb300" / "csrc"
