@@ -220,3 +220,22 @@ def test_wait_selftest_rejects_bad_limits(lib):
     lib.bvc_wait_selftest.argtypes = [C.c_int64, C.c_void_p]
     assert lib.bvc_wait_selftest(-1, None) == 1
     assert lib.bvc_wait_selftest(3_000_000_000, None) == 1
+
+
+def test_header_is_plain_c_and_links(work_dir):
+    """include/bvc.h compiles as C11 with -pedantic -Werror, and a C program
+    linked against the library gets the declared host-side behaviour."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    from paper_2302_11825_gb300 import build as b
+    lib_path = b.build()
+    exe = os.path.join(work_dir, "abi_c_check")
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "host", "abi_c_check.c"),
+                        "-o", exe, lib_path, "-Wl,-rpath," + os.path.dirname(lib_path)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.stdout, r.stderr[-2000:])
