@@ -113,6 +113,26 @@ def test_product_does_not_use_the_oracle():
                 assert "liboracle" not in text and "bvc_oracle" not in text, f
 
 
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the CUDA library (and no way to build it) every call raises:
+    there is no CPU fallback."""
+    from paper_2302_11825_gb300 import bvc
+    from paper_2302_11825_gb300 import build as b
+
+    def no_toolkit(*a, **k):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libbvc.so")
+
+    monkeypatch.setattr(bvc, "_lib", None)
+    monkeypatch.setattr(b, "LIB", os.path.join(ROOT, "tests", "_tmp", "missing", "libbvc.so"))
+    monkeypatch.setattr(b, "build", no_toolkit)
+    with pytest.raises(RuntimeError, match="CUDA toolkit"):
+        bvc.lib()
+    V = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]], np.float32)
+    F = np.array([[0, 1], [1, 2], [2, 0]], np.int32)
+    with pytest.raises(RuntimeError, match="CUDA toolkit"):
+        bvc.Geometry(V, F)
+
+
 def test_multi_rhs_host_checks(lib):
     lib.bvc_poly_terms.restype = C.c_int32
     assert [lib.bvc_poly_terms(d) for d in (1, 2, 3, 4)] == [0, 15, 35, 0]
