@@ -138,6 +138,14 @@ def single_core(fn):
         oracle.set_num_threads(n)
 
 
+def device_info(local: int) -> dict:
+    """The GPU the line was measured on."""
+    import torch
+    p = torch.cuda.get_device_properties(local)
+    return {"name": p.name, "sm_count": p.multi_processor_count, "cc": f"{p.major}.{p.minor}",
+            "memory_gib": round(p.total_memory / 2 ** 30, 1), "torch": torch.__version__, "cuda": torch.version.cuda}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -721,7 +729,7 @@ def bench_batched(args, rank, local, ws):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = optional_part(lambda: batched_oracle_rate(w))
     if rank == 0:
-        print(json.dumps(out))
+        print(json.dumps(dict(out, device=optional_part(lambda: device_info(local)))))
     import torch.distributed as td
     if td.is_initialized():
         td.destroy_process_group()
@@ -906,7 +914,7 @@ def bench_inverse(args, rank, local, ws):
             return dict(info, value=1.0 / t_cpu, unit="gradient steps/s", kind="oracle")
         out["cpu_baseline"] = optional_part(cpu)
     if rank == 0:
-        print(json.dumps(out))
+        print(json.dumps(dict(out, device=optional_part(lambda: device_info(local)))))
     import torch.distributed as td
     if td.is_initialized():
         td.destroy_process_group()
@@ -1264,7 +1272,7 @@ def bench_mixed(args, rank, local, ws):
             return dict(info, value=M / t_cpu, unit=UNIT, kind="oracle")
         out["cpu_baseline"] = optional_part(cpu)
     if rank == 0:
-        print(json.dumps(out))
+        print(json.dumps(dict(out, device=optional_part(lambda: device_info(local)))))
     import torch.distributed as td
     if td.is_initialized():
         td.destroy_process_group()
@@ -1503,7 +1511,7 @@ def main():
                     "single_core": info["single_core"], "cpu_model": info["cpu_model"]}
         out["cpu_baseline"] = optional_part(cpu)
     if rank == 0:
-        print(json.dumps(out))
+        print(json.dumps(dict(out, device=optional_part(lambda: device_info(local)))))
     import torch.distributed as td
     if td.is_initialized():
         td.destroy_process_group()

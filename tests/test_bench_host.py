@@ -74,3 +74,9 @@ def test_mixed_workload_switch(name, expect):
     assert w.name == expect and w.n_samples == 1024
     gap = w.meta.get("silhouette_gap", 0.0)
     assert (gap > 0.0) == (name == "mixed3d")
+
+
+def test_device_info_never_breaks_the_line():
+    # on a GPU: name, SM count, compute capability; without one: an error entry
+    d = bench.optional_part(lambda: bench.device_info(0))
+    assert isinstance(d, dict) and ("name" in d or "error" in d)
