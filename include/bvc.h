@@ -27,9 +27,10 @@
  *    bit-reproducible for a given seed and launch-independent.
  *  - The functions g and f are sums of closed-form terms (bvc_function);
  *    they stand in for the paper's callbacks (Sec. 4 "Setup").
- *  - Nothing here allocates device memory except bvc_geometry_create and
- *    bvc_batch_create, which own their BVHs until bvc_geometry_destroy /
- *    bvc_batch_destroy.  Scratch memory is passed in as a workspace; each
+ *  - Nothing here allocates device memory except bvc_geometry_create,
+ *    bvc_batch_create and bvc_mixed_create, which own their trees until
+ *    bvc_geometry_destroy / bvc_batch_destroy / bvc_mixed_destroy; a failed
+ *    allocation returns BVC_ERR_OOM and leaves *out NULL.  Scratch memory is passed in as a workspace; each
  *    *_workspace_size call says how much is needed.
  */
 #ifndef BVC_H_

@@ -133,6 +133,34 @@ def test_missing_library_fails_loudly(monkeypatch):
         bvc.Geometry(V, F)
 
 
+def test_device_allocation_failure_is_an_error(lib):
+    """On a machine without a GPU every device allocation fails: the creating
+    calls return an error and leave the handle NULL (no crash, no leak of a
+    half-built handle)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: allocations succeed")
+    from paper_2302_11825_gb300 import workloads as wl
+    V, F = wl.circle_polygon(64)
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    vp, fp = V.ctypes.data_as(C.c_void_p), F.ctypes.data_as(C.c_void_p)
+    lib.bvc_geometry_create.restype = C.c_int
+    lib.bvc_geometry_create.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.POINTER(C.c_void_p)]
+    h = C.c_void_p(1)
+    st = lib.bvc_geometry_create(2, vp, V.shape[0], fp, F.shape[0], None, C.byref(h))
+    assert st not in (0, 1) and h.value is None
+    lib.bvc_mixed_create.restype = C.c_int
+    lib.bvc_mixed_create.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                     C.c_void_p, C.POINTER(C.c_void_p)]
+    neu = np.zeros(F.shape[0], np.uint8)
+    neu[:10] = 1
+    h = C.c_void_p(1)
+    st = lib.bvc_mixed_create(2, vp, V.shape[0], fp, F.shape[0], neu.ctypes.data_as(C.c_void_p), None, C.byref(h))
+    assert st not in (0, 1) and h.value is None
+
+
 def test_multi_rhs_host_checks(lib):
     lib.bvc_poly_terms.restype = C.c_int32
     assert [lib.bvc_poly_terms(d) for d in (1, 2, 3, 4)] == [0, 15, 35, 0]
