@@ -136,3 +136,19 @@ def test_walks_deterministic_and_capped():
     assert not np.array_equal(a["U"], c["U"])
     d = oracle.walks(bvh, g, [], x, 64, 1e-4, 3, seed=5)
     assert d["steps"].max() <= 3
+
+
+def test_reduce_walks_is_the_per_sample_mean():
+    # Alg. 1: u^ and du/dn^ of sample i are the means over its W walks of U
+    # and of grad . n_i (n_i as stored, FP32)
+    rng = np.random.default_rng(4)
+    n, W, dim = 37, 9, 3
+    U = rng.standard_normal(n * W)
+    grad = rng.standard_normal((n * W, dim))
+    nrm = rng.standard_normal((n, dim)).astype(np.float32)
+    uh, qh = oracle.reduce_walks(U, grad, nrm, W)
+    np.testing.assert_allclose(uh, U.reshape(n, W).mean(1), rtol=1e-13, atol=1e-15)
+    q = np.einsum("iwd,id->iw", grad.reshape(n, W, dim), nrm.astype(np.float64)).mean(1)
+    np.testing.assert_allclose(qh, q, rtol=1e-12, atol=1e-14)
+    uh2, qh2 = oracle.reduce_walks(U, grad, None, W)
+    assert qh2 is None and np.array_equal(uh2, uh)
