@@ -14,7 +14,11 @@ Parity status: every function here is pinned by tests in ``tests/`` against
 closed forms, a deterministic Green's-identity quadrature, brute force, the
 mean-value property or published known answers, except as noted:
   (none: ``sample_source2d`` is pinned by the exact polygon area and the
-  closed-form Newtonian potential of a disk, see tests/test_oracle_sampling.py)
+  closed-form Newtonian potential of a disk, see tests/test_oracle_sampling.py;
+  the offset boundary of Sec. 3.2 (``offset_disp``, ``offset_vertices``, the
+  samplers) by Green's representation formula over the moved mesh, crossing
+  signs of rays, distances to the elements' lines and the offset region's
+  area, see tests/test_oracle_offset.py)
 """
 from __future__ import annotations
 
@@ -71,29 +75,31 @@ def _load():
                 "orc_bvh_free": (None, [P]),
                 "orc_bvh_closest": (None, [P, P, i64, P, P, P]),
                 "orc_boundary_measure": (f64, [C.c_int, P, P, i64]),
-                "orc_sample_boundary": (None, [C.c_int, P, P, i64, i64, f64, u64, P, P, P]),
+                "orc_sample_boundary": (None, [C.c_int, P, i64, P, i64, i64, f64, u64, P, P, P, P]),
+                "orc_offset_disp": (f64, [C.c_int, P, i64, P, i64, P, P]),
+                "orc_offset_vertices": (None, [C.c_int, P, i64, P, f64, P]),
                 "orc_walks": (None, [P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_walks_vg": (None, [P, P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_vertex_interp": (f64, [P, P, i64, P]),
                 "orc_winding3d": (f64, [P, P, i64, P]),
                 "orc_bessel_i": (f64, [C.c_int, f64]),
-                "orc_ray_hits": (C.c_int, [C.c_int, P, P, i64, f64, P, P, f64, P, P, P]),
+                "orc_ray_hits": (C.c_int, [C.c_int, P, P, i64, f64, P, P, P, f64, P, P, P]),
                 "orc_clamp_correction": (i64, [P, P, P, f64, P, P, i64, f64, P, i64, f64, i32, i32, f64, i32, u64, P]),
                 "orc_bessel_k": (f64, [C.c_int, f64]),
                 "orc_green_sigma": (None, [C.c_int, f64, P, P, P, P]),
                 "orc_screened_factors": (None, [C.c_int, f64, P, P]),
                 "orc_walks_sigma": (None, [P, P, P, P, f64, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_gather_sigma": (None, [C.c_int, f64, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
-                "orc_gather_full": (None, [C.c_int, f64, f64, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P,
-                                           P]),
-                "orc_sample_source3d": (i64, [P, i64, P, i64, i32, i32, i32, u64, P, P, P, P]),
+                "orc_gather_full": (None, [C.c_int, f64, f64, i64, P, P, P, P, f64, P, i64, P, P, i64, P, P, P, P,
+                                           P, P]),
+                "orc_sample_source3d": (i64, [P, i64, P, i64, i32, i32, i32, u64, P, P, P, P, P]),
                 "orc_reduce_walks": (None, [C.c_int, i64, i32, P, P, P, P, P]),
-                "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P]),
+                "orc_sample_source2d": (i64, [P, i64, P, i64, i32, i32, u64, P, P, P, P]),
                 "orc_gather": (None, [C.c_int, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
                 "orc_sphere_step": (None, [C.c_int, f64, f64, f64, f64, P, P, P, P]),
                 "orc_num_threads": (C.c_int, []),
                 "orc_set_num_threads": (None, [C.c_int]),
-                "orc_sample_boundary_mixed": (None, [C.c_int, P, P, i64, i64, f64, u64, P, P, P, P]),
+                "orc_sample_boundary_mixed": (None, [C.c_int, P, i64, P, i64, i64, f64, u64, P, P, P, P, P]),
                 "orc_fn_grad": (None, [P, C.c_int, P, P]),
                 "orc_neumann_eval": (f64, [P, P, C.c_int, P, P]),
                 "orc_wost_create": (P, [C.c_int, P, i64, P, i64, P]),
@@ -259,14 +265,40 @@ def boundary_measure(V, F) -> float:
     return float(_load().orc_boundary_measure(V.shape[1], _p(V), _p(F), F.shape[0]))
 
 
-def sample_boundary(V, F, N: int, l: float, seed: int):
-    """Sec. 4 Sampling + Sec. 3.2 offset: (z[N,dim], n[N,dim], element[N]) in FP64."""
+def offset_disp(V, F, fixed=None):
+    """Sec. 3.2: per-vertex inward displacement directions m_v of the offset
+    boundary (the closed surface of the mesh with vertex v moved to
+    v - l m_v) and their largest length (the reach).  fixed: optional per-
+    element flags of elements that are not moved."""
     lib = _load()
     V, F = _f32(V), _i32(F)
     dim = V.shape[1]
-    z, n, e = np.zeros((N, dim)), np.zeros((N, dim)), np.zeros(N, np.int32)
-    lib.orc_sample_boundary(dim, _p(V), _p(F), F.shape[0], N, float(l), int(seed), _p(z), _p(n), _p(e))
-    return z, n, e
+    m = np.zeros((V.shape[0], dim))
+    fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+    reach = lib.orc_offset_disp(dim, _p(V), V.shape[0], _p(F), F.shape[0], _p(fx), _p(m))
+    return m, float(reach)
+
+
+def offset_vertices(V, F, l: float, fixed=None) -> np.ndarray:
+    """The offset boundary's vertices, fl32(V - l m) (Sec. 3.2)."""
+    lib = _load()
+    V = _f32(V)
+    m, _ = offset_disp(V, F, fixed)
+    out = np.zeros_like(V)
+    lib.orc_offset_vertices(V.shape[1], _p(V), V.shape[0], _p(m), float(l), _p(out))
+    return out
+
+
+def sample_boundary(V, F, N: int, l: float, seed: int):
+    """Sec. 4 Sampling + Sec. 3.2 offset boundary: (z[N,dim], n[N,dim],
+    element[N], jac[N]) in FP64; 1/p of sample i is |dOmega| jac[i]."""
+    lib = _load()
+    V, F = _f32(V), _i32(F)
+    dim = V.shape[1]
+    z, n, e, j = np.zeros((N, dim)), np.zeros((N, dim)), np.zeros(N, np.int32), np.zeros(N)
+    lib.orc_sample_boundary(dim, _p(V), V.shape[0], _p(F), F.shape[0], N, float(l), int(seed), _p(z), _p(n), _p(j),
+                            _p(e))
+    return z, n, e, j
 
 
 def sphere_step(dim: int, R: float, u0: float, u1: float, u2: float):
@@ -322,14 +354,16 @@ MAX_HITS = 8
 
 
 def ray_hits(V, F, l: float, x, om, rmax: float):
-    """Crossings of the ray x + t om (0 < t <= rmax) with the mesh whose
-    elements are moved by -l n_e: (t, element, n.om), nearest first."""
+    """Crossings of the ray x + t om (0 < t <= rmax) with the offset
+    boundary at l (the mesh with its vertices moved by -l m_v, Sec. 3.2):
+    (t, element, n.om), nearest first."""
     lib = _load()
     V, F = _f32(V), _i32(F)
+    m = offset_disp(V, F)[0] if l != 0.0 else None
     t, nw = np.zeros(MAX_HITS), np.zeros(MAX_HITS)
     e = np.zeros(MAX_HITS, np.int64)
-    k = lib.orc_ray_hits(V.shape[1], _p(V), _p(F), F.shape[0], float(l), _p(_f64(x)), _p(_f64(om)), float(rmax),
-                         _p(t), _p(e), _p(nw))
+    k = lib.orc_ray_hits(V.shape[1], _p(V), _p(F), F.shape[0], float(l), _p(m), _p(_f64(x)), _p(_f64(om)),
+                         float(rmax), _p(t), _p(e), _p(nw))
     return t[:k], e[:k], nw[:k]
 
 
@@ -371,40 +405,47 @@ def winding3d(V, F, pts):
                      for p in np.atleast_2d(pts)])
 
 
-def sample_source3d(V, F, grid, seed: int, f_terms, want_winding=False):
+def sample_source3d(V, F, grid, seed: int, f_terms, want_winding=False, l: float = 0.0):
     """Sec. 4 Sampling in 3D: jittered grid over the bounding box, kept where
-    the winding number exceeds 1/2.  Returns (y [kept][3], c [kept], ncand)
-    and, if asked, every candidate's winding number."""
+    the winding number of the offset boundary at l (Sec. 3.2; l = 0: the
+    mesh) exceeds 1/2.  Returns (y [kept][3], c [kept], ncand) and, if
+    asked, every candidate's winding number."""
     lib = _load()
     V, F = _f32(V), np.ascontiguousarray(F, dtype=np.int32)
+    Vin = offset_vertices(V, F, l) if l != 0.0 else None
     ncand = int(grid[0]) * int(grid[1]) * int(grid[2])
     y = np.zeros((ncand, 3), np.float32)
     c = np.zeros(ncand)
     wn = np.zeros(ncand) if want_winding else None
     f = encode_function(f_terms)
     k = lib.orc_sample_source3d(_p(V), V.shape[0], _p(F), F.shape[0], int(grid[0]), int(grid[1]), int(grid[2]),
-                                int(seed), _p(f), _p(y), _p(c), _p(wn))
+                                int(seed), _p(f), _p(Vin), _p(y), _p(c), _p(wn))
     out = (y[:k], c[:k], ncand)
     return out + (wn,) if want_winding else out
 
 
-def sample_source2d(V, F, grid, seed: int, f_terms):
-    """Sec. 4 Sampling: jittered grid over the bounding box, kept if inside.
+def sample_source2d(V, F, grid, seed: int, f_terms, l: float = 0.0):
+    """Sec. 4 Sampling: jittered grid over the bounding box, kept if inside
+    the offset boundary at l (Sec. 3.2; l = 0: the polygon itself).
 
     Returns (y[kept,2] FP32, c[kept] = f(y)|box| FP64, n_candidates)."""
     lib = _load()
     V, F = _f32(V), _i32(F)
+    Vin = offset_vertices(V, F, l) if l != 0.0 else None
     G0, G1 = int(grid[0]), int(grid[1])
     y = np.zeros((G0 * G1, 2), np.float32)
     c = np.zeros(G0 * G1)
     f = encode_function(f_terms)
-    kept = lib.orc_sample_source2d(_p(V), V.shape[0], _p(F), F.shape[0], G0, G1, int(seed), _p(f), _p(y), _p(c))
+    kept = lib.orc_sample_source2d(_p(V), V.shape[0], _p(F), F.shape[0], G0, G1, int(seed), _p(f), _p(Vin), _p(y),
+                                   _p(c))
     return y[:kept].copy(), c[:kept].copy(), G0 * G1
 
 
 def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs: bool = False, sigma: float = 0.0,
-           clamp_c: float = 0.0):
+           clamp_c: float = 0.0, jac=None):
     """Eq. 3-6 / Alg. 1 splat: FP64 running sums (u_bnd, u_src, g_bnd, g_src).
+    jac: per-sample measure ratios of the offset boundary (1/p = bnd_measure
+    jac[i]); None = 1.
     sigma > 0: with the screened Green's functions of App. A.
     clamp_c > 0: dG/dn of the u term clamped to [-c, c] (Sec. 3.3).
 
@@ -422,8 +463,10 @@ def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs:
     ub, us = np.zeros(M), np.zeros(M)
     gb, gs = np.zeros((M, dim)), np.zeros((M, dim))
     ab = np.zeros((M, 2 + 2 * dim)) if want_abs else None
+    jac = None if jac is None else _f64(jac)
     lib.orc_gather_full(dim, float(np.sqrt(sigma)), float(clamp_c), N, _p(z), _p(nz), _p(u_hat), _p(q_hat),
-                        float(bnd_measure), y.shape[0], _p(y), _p(c), M, _p(x), _p(ub), _p(us), _p(gb), _p(gs), _p(ab))
+                        float(bnd_measure), _p(jac), y.shape[0], _p(y), _p(c), M, _p(x), _p(ub), _p(us), _p(gb), _p(gs),
+                        _p(ab))
     if want_abs:
         return ub, us, gb, gs, ab
     return ub, us, gb, gs
@@ -431,15 +474,17 @@ def gather(z, nz, u_hat, q_hat, bnd_measure: float, x, y=None, c=None, want_abs:
 
 # ---------------------------------------------------------------- mixed boundaries
 def sample_boundary_mixed(V, F, N: int, l: float, seed: int, neumann):
-    """Sec. 3.2 for a mixed boundary: samples on Dirichlet elements moved by
-    -l n, samples on Neumann elements left on the boundary."""
+    """Sec. 3.2 for a mixed boundary: samples on the Dirichlet elements of
+    the offset boundary built from the Dirichlet elements alone, samples on
+    Neumann elements left on the boundary (jac 1).  Returns (z, n, e, jac)."""
     lib = _load()
     V, F = _f32(V), _i32(F)
     dim = V.shape[1]
     nf = np.ascontiguousarray(neumann, dtype=np.uint8)
-    z, n, e = np.zeros((N, dim)), np.zeros((N, dim)), np.zeros(N, np.int32)
-    lib.orc_sample_boundary_mixed(dim, _p(V), _p(F), F.shape[0], N, float(l), int(seed), _p(nf), _p(z), _p(n), _p(e))
-    return z, n, e
+    z, n, e, j = np.zeros((N, dim)), np.zeros((N, dim)), np.zeros(N, np.int32), np.zeros(N)
+    lib.orc_sample_boundary_mixed(dim, _p(V), V.shape[0], _p(F), F.shape[0], N, float(l), int(seed), _p(nf), _p(z),
+                                  _p(n), _p(j), _p(e))
+    return z, n, e, j
 
 
 def fn_grad(terms, dim: int, x) -> np.ndarray:

@@ -16,7 +16,8 @@
  *   - boundary estimator, source estimator, gradients ..... Eq. 3-6, Alg. 1
  *   - walk on spheres with the ball Green's function ...... Sec. 3.1, Eq. 7
  *   - boundary sampling by a CDF over element measures .... Sec. 4 "Sampling"
- *   - offset Dirichlet boundary (samples moved by -l n) ... Sec. 3.2
+ *   - offset Dirichlet boundary: the closed surface of the
+ *     mesh with its vertices moved inward (reading below) ... Sec. 3.2
  *   - stratified uniform source samples ................... Sec. 4 "Sampling"
  * Randomness: Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), written here from that definition.
@@ -863,16 +864,154 @@ double orc_boundary_measure(int dim, const float* V, const int32_t* F, int64_t n
   return s;
 }
 
+/* Measure and outward unit normal of an element given by FP64 vertex       */
+/* positions P[0..dim-1], in the same operation order as                    */
+/* elem_measure_normal (so P = the mesh's own vertices gives the same bits).*/
+static double pts_measure_normal(int dim, double P[3][3], double* nrm) {
+  if (dim == 2) {
+    const double dx = P[1][0] - P[0][0], dy = P[1][1] - P[0][1];
+    const double len = sqrt(dx * dx + dy * dy);
+    nrm[0] = dy / len;
+    nrm[1] = -dx / len;
+    return len;
+  }
+  double e1[3], e2[3], c[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = P[1][a] - P[0][a];
+    e2[a] = P[2][a] - P[0][a];
+  }
+  c[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  c[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  c[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  for (int a = 0; a < 3; ++a) nrm[a] = c[a] / len;
+  return 0.5 * len;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The offset Dirichlet boundary (Sec. 3.2, Fig. "Dirichlet offset          */
+/* boundary"): the cache's samples lie on the boundary of a CLOSED region   */
+/* inside Omega, about l from the boundary, and the BIE (Eq. 2) and the     */
+/* source samples refer to that region.  Reading: the region is bounded by  */
+/* the mesh with every vertex v moved to v - l m_v, m_v built from the unit */
+/* normals of the MOVED elements at v (all elements, or the Dirichlet ones  */
+/* of a mixed boundary, whose Neumann elements stay put):                   */
+/*   2D, k = 2 moved segments with normals na, nb, S = na + nb:             */
+/*       m = S / max(|S|^2 / 2, 1/4)                                        */
+/*     (|S|^2/2 = 1 + na.nb: the miter, both moved segments parallel to     */
+/*      theirs at distance exactly l, for turning angles up to 138.6 deg);  */
+/*   2D, any other k >= 1: m = S / |S|;                                     */
+/*   3D: N = sum over the moved triangles at v of theta_f n_f (theta_f the */
+/*       triangle's angle at v, n_f its unit normal: the angle-weighted     */
+/*       pseudonormal, independent of how flat parts are triangulated), N^  */
+/*       its direction, m = N^ / max(min_f n_f . N^, 1/4), so every moved   */
+/*       triangle's plane moves inward by at least l at v (a box corner     */
+/*       moves by (1,1,1) l: l from each of its three faces).               */
+/* A vertex with no moved element, or S = 0 / N = 0, keeps m = 0.           */
+/* fixed (may be NULL): fixed[e] != 0 marks an element that is not moved.   */
+/* Returns max_v |m_v| (the reach: the moved mesh lies within l x reach of  */
+/* the boundary).                                                            */
+/* ------------------------------------------------------------------------ */
+double orc_offset_disp(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const uint8_t* fixed,
+                       double* m) {
+  int32_t* cnt = (int32_t*)calloc((size_t)nv, sizeof(int32_t));
+  double* S = (double*)calloc((size_t)nv * dim, sizeof(double));
+  for (int64_t i = 0; i < nv * dim; ++i) m[i] = 0.0;
+  for (int64_t e = 0; e < np; ++e) {
+    if (fixed && fixed[e]) continue;
+    const int32_t* f = F + e * dim;
+    double n[3];
+    if (dim == 2) {
+      elem_measure_normal(2, V, f, n);
+      for (int k = 0; k < 2; ++k) {
+        S[2 * (int64_t)f[k]] += n[0];
+        S[2 * (int64_t)f[k] + 1] += n[1];
+        cnt[f[k]] += 1;
+      }
+    } else {
+      elem_measure_normal(3, V, f, n);
+      for (int k = 0; k < 3; ++k) {
+        /* angle at corner k between the edges to the other two corners */
+        double p[3], q[3];
+        for (int a = 0; a < 3; ++a) {
+          p[a] = (double)V[3 * f[(k + 1) % 3] + a] - (double)V[3 * f[k] + a];
+          q[a] = (double)V[3 * f[(k + 2) % 3] + a] - (double)V[3 * f[k] + a];
+        }
+        const double x[3] = {p[1] * q[2] - p[2] * q[1], p[2] * q[0] - p[0] * q[2], p[0] * q[1] - p[1] * q[0]};
+        const double th = atan2(sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]), p[0] * q[0] + p[1] * q[1] + p[2] * q[2]);
+        for (int a = 0; a < 3; ++a) S[3 * (int64_t)f[k] + a] += th * n[a];
+        cnt[f[k]] += 1;
+      }
+    }
+  }
+  if (dim == 2) {
+    for (int64_t v = 0; v < nv; ++v) {
+      const double s0 = S[2 * v], s1 = S[2 * v + 1];
+      const double q = s0 * s0 + s1 * s1;
+      if (cnt[v] == 0 || !(q > 0.0)) continue;
+      const double den = cnt[v] == 2 ? fmax(0.5 * q, 0.25) : sqrt(q);
+      m[2 * v] = s0 / den;
+      m[2 * v + 1] = s1 / den;
+    }
+  } else {
+    double* cmin = (double*)malloc(sizeof(double) * (size_t)nv);
+    for (int64_t v = 0; v < nv; ++v) {
+      cmin[v] = 2.0;
+      const double q = sqrt(S[3 * v] * S[3 * v] + S[3 * v + 1] * S[3 * v + 1] + S[3 * v + 2] * S[3 * v + 2]);
+      if (q > 0.0)
+        for (int a = 0; a < 3; ++a) S[3 * v + a] = S[3 * v + a] / q;
+      else
+        cnt[v] = 0;
+    }
+    for (int64_t e = 0; e < np; ++e) {
+      if (fixed && fixed[e]) continue;
+      const int32_t* f = F + e * 3;
+      double n[3];
+      elem_measure_normal(3, V, f, n);
+      for (int k = 0; k < 3; ++k) {
+        const double* Nv = S + 3 * (int64_t)f[k];
+        const double c = n[0] * Nv[0] + n[1] * Nv[1] + n[2] * Nv[2];
+        if (c < cmin[f[k]]) cmin[f[k]] = c;
+      }
+    }
+    for (int64_t v = 0; v < nv; ++v) {
+      if (cnt[v] == 0) continue;
+      const double den = fmax(cmin[v], 0.25);
+      for (int a = 0; a < 3; ++a) m[3 * v + a] = S[3 * v + a] / den;
+    }
+    free(cmin);
+  }
+  double reach = 0.0;
+  for (int64_t v = 0; v < nv; ++v) {
+    double q = 0.0;
+    for (int a = 0; a < dim; ++a) q += m[dim * v + a] * m[dim * v + a];
+    if (sqrt(q) > reach) reach = sqrt(q);
+  }
+  free(cnt);
+  free(S);
+  return reach;
+}
+
+/* The moved mesh's vertices rounded to FP32: V'[v] = fl32(V[v] - l m_v).   */
+void orc_offset_vertices(int dim, const float* V, int64_t nv, const double* m, double l, float* Vout) {
+  for (int64_t i = 0; i < nv * dim; ++i) Vout[i] = (float)((double)V[i] - l * m[i]);
+}
+
 /* N stratified boundary samples.  Sample i draws (u0,u1,u2) from Philox    */
 /* (id = i, word2 = 0, tag = 1); s = (i + u0)/N picks the element through   */
 /* the CDF of element measures; 2D reuses the position of s inside the      */
-/* element's CDF interval as the arclength parameter, 3D places the point   */
-/* uniformly on the triangle from (u1,u2) (barycentrics 1-sqrt(u1),         */
-/* sqrt(u1)(1-u2), sqrt(u1)u2).  z = p - l n.                               */
-/* With zero_l non-NULL, samples on elements e with zero_l[e] != 0 (the     */
-/* Neumann part of a mixed boundary, Sec. 3.2) stay on the boundary.        */
+/* element's CDF interval as the arclength parameter lam, 3D draws          */
+/* barycentrics (1-sqrt(u1), sqrt(u1)(1-u2), sqrt(u1)u2).  The sample sits  */
+/* at those coordinates on the MOVED element (vertices P_k = v_k - l m_k,   */
+/* see orc_offset_disp): an affine map of the element, so the point stays   */
+/* uniform on it.  Its density on the offset surface is                     */
+/* 1 / (|dOmega| jac) with jac = |moved element| / |element|, so 1/p =      */
+/* |dOmega| jac; nrm is the moved element's outward unit normal.            */
+/* With fixed non-NULL, elements e with fixed[e] != 0 (the Neumann part of  */
+/* a mixed boundary) are not moved (jac = 1).                               */
 static void sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l,
-                            uint64_t seed, const uint8_t* zero_l, double* z, double* nrm, int32_t* elem) {
+                            uint64_t seed, const uint8_t* fixed, const double* m, double* z, double* nrm,
+                            double* jac, int32_t* elem) {
   double* cdf = (double*)malloc(sizeof(double) * (np + 1));
   double n[3];
   cdf[0] = 0.0;
@@ -895,41 +1034,48 @@ static void sample_boundary(int dim, const float* V, const int32_t* F, int64_t n
     const int64_t e = lo;
     const int32_t* f = F + e * dim;
     const double meas = elem_measure_normal(dim, V, f, n);
+    const double le = (fixed && fixed[e]) ? 0.0 : l;
+    double P[3][3];
+    for (int k = 0; k < dim; ++k)
+      for (int a = 0; a < dim; ++a) P[k][a] = (double)V[dim * f[k] + a] - le * m[dim * f[k] + a];
+    double nm[3];
+    const double meas_m = pts_measure_normal(dim, P, nm);
     double p[3];
     if (dim == 2) {
       double lam = (t - cdf[e]) / meas;
       if (lam < 0.0) lam = 0.0;
       if (lam > 1.0) lam = 1.0;
-      for (int a = 0; a < 2; ++a) {
-        const double va = V[2 * f[0] + a], vb = V[2 * f[1] + a];
-        p[a] = va + lam * (vb - va);
-      }
+      for (int a = 0; a < 2; ++a) p[a] = P[0][a] + lam * (P[1][a] - P[0][a]);
     } else {
       const double sq = sqrt(u[1]);
       const double b1 = sq * (1.0 - u[2]), b2 = sq * u[2];
-      for (int a = 0; a < 3; ++a) {
-        const double v0 = V[3 * f[0] + a], v1 = V[3 * f[1] + a], v2 = V[3 * f[2] + a];
-        p[a] = v0 + b1 * (v1 - v0) + b2 * (v2 - v0);
-      }
+      for (int a = 0; a < 3; ++a) p[a] = P[0][a] + b1 * (P[1][a] - P[0][a]) + b2 * (P[2][a] - P[0][a]);
     }
-    const double le = (zero_l && zero_l[e]) ? 0.0 : l;
     for (int a = 0; a < dim; ++a) {
-      z[i * dim + a] = p[a] - le * n[a];
-      nrm[i * dim + a] = n[a];
+      z[i * dim + a] = p[a];
+      nrm[i * dim + a] = nm[a];
     }
+    jac[i] = meas_m / meas;
     elem[i] = (int32_t)e;
   }
   free(cdf);
 }
 
-void orc_sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l, uint64_t seed,
-                         double* z, double* nrm, int32_t* elem) {
-  sample_boundary(dim, V, F, np, N, l, seed, NULL, z, nrm, elem);
+void orc_sample_boundary(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, int64_t N, double l,
+                         uint64_t seed, double* z, double* nrm, double* jac, int32_t* elem) {
+  double* m = (double*)malloc(sizeof(double) * (size_t)nv * dim);
+  orc_offset_disp(dim, V, nv, F, np, NULL, m);
+  sample_boundary(dim, V, F, np, N, l, seed, NULL, m, z, nrm, jac, elem);
+  free(m);
 }
 
-void orc_sample_boundary_mixed(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l,
-                               uint64_t seed, const uint8_t* neumann, double* z, double* nrm, int32_t* elem) {
-  sample_boundary(dim, V, F, np, N, l, seed, neumann, z, nrm, elem);
+void orc_sample_boundary_mixed(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, int64_t N,
+                               double l, uint64_t seed, const uint8_t* neumann, double* z, double* nrm, double* jac,
+                               int32_t* elem) {
+  double* m = (double*)malloc(sizeof(double) * (size_t)nv * dim);
+  orc_offset_disp(dim, V, nv, F, np, neumann, m);
+  sample_boundary(dim, V, F, np, N, l, seed, neumann, m, z, nrm, jac, elem);
+  free(m);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1141,25 +1287,29 @@ void orc_walks(void* bvh, const double* g, const double* f, const float* starts,
 /*   sign(n.w) (1 - c / |dG/dn(x, z)|) u(z) / n_dirs   when |dG/dn| > c,     */
 /* |dG/dn| = |n.w| / (2 pi t) (2D), |n.w| / (4 pi t^2) (3D), so only t below */
 /* 1/(2 pi c) or (4 pi c)^(-1/2) can matter.  The sample surface is the     */
-/* mesh with each element moved by -l n_e (l = 0: the mesh itself).  u(z)   */
+/* mesh with each vertex moved by -l m_v (orc_offset_disp; l = 0: the mesh  */
+/* itself), the surface the cache's samples lie on.  u(z)                   */
 /* is estimated by W walks from z (FP32-rounded) on the domain's geometry   */
 /* (tag 5, walk id = hit rank * W + j, hits ranked by point, direction and  */
 /* distance along the ray).                                                  */
 /* ------------------------------------------------------------------------ */
 #define ORC_MAX_HITS 8
-int orc_ray_hits(int dim, const float* V, const int32_t* F, int64_t np, double l, const double* x, const double* om,
-                 double rmax, double* t_out, int64_t* e_out, double* nw_out) {
+int orc_ray_hits(int dim, const float* V, const int32_t* F, int64_t np, double l, const double* mdisp,
+                 const double* x, const double* om, double rmax, double* t_out, int64_t* e_out, double* nw_out) {
   int nh = 0;
   for (int64_t e = 0; e < np; ++e) {
     const int32_t* f = F + e * dim;
     double n[3] = {0, 0, 0};
-    elem_measure_normal(dim, V, f, n);
+    double P[3][3];
+    for (int k = 0; k < dim; ++k)
+      for (int a = 0; a < dim; ++a) P[k][a] = (double)V[dim * f[k] + a] - (mdisp ? l * mdisp[dim * f[k] + a] : 0.0);
+    pts_measure_normal(dim, P, n);
     double t = -1.0;
     if (dim == 2) {
       double a[2], b[2];
       for (int k = 0; k < 2; ++k) {
-        a[k] = (double)V[2 * f[0] + k] - l * n[k];
-        b[k] = (double)V[2 * f[1] + k] - l * n[k];
+        a[k] = P[0][k];
+        b[k] = P[1][k];
       }
       const double ex = b[0] - a[0], ey = b[1] - a[1];
       const double den = om[0] * ey - om[1] * ex;
@@ -1172,9 +1322,9 @@ int orc_ray_hits(int dim, const float* V, const int32_t* F, int64_t np, double l
     } else {
       double a[3], b[3], c[3];
       for (int k = 0; k < 3; ++k) {
-        a[k] = (double)V[3 * f[0] + k] - l * n[k];
-        b[k] = (double)V[3 * f[1] + k] - l * n[k];
-        c[k] = (double)V[3 * f[2] + k] - l * n[k];
+        a[k] = P[0][k];
+        b[k] = P[1][k];
+        c[k] = P[2][k];
       }
       /* Moller-Trumbore (J. Graphics Tools 2(1), 1997) */
       double e1[3], e2[3], tv[3];
@@ -1238,6 +1388,11 @@ int64_t orc_clamp_correction(void* bvh, const double* g, const double* gv, doubl
   const int dim = B->m.dim;
   const double rmax = dim == 2 ? 1.0 / (2.0 * ORC_PI * c) : sqrt(1.0 / (4.0 * ORC_PI * c));
   const int64_t slots = m * (int64_t)n_dirs * ORC_MAX_HITS;
+  int64_t nvs = 0;
+  for (int64_t i = 0; i < nps * dim; ++i)
+    if (Fs[i] + 1 > nvs) nvs = Fs[i] + 1;
+  double* mdisp = (double*)malloc(sizeof(double) * (size_t)nvs * dim);
+  orc_offset_disp(dim, Vs, nvs, Fs, nps, NULL, mdisp);
   double* hz = (double*)malloc((size_t)slots * 3 * sizeof(double));
   double* hw = (double*)malloc((size_t)slots * sizeof(double));
 #pragma omp parallel for schedule(dynamic, 4)
@@ -1248,7 +1403,7 @@ int64_t orc_clamp_correction(void* bvh, const double* g, const double* gv, doubl
     unit_direction(dim, u, om);
     double t[ORC_MAX_HITS], nw[ORC_MAX_HITS];
     int64_t e[ORC_MAX_HITS];
-    const int nh = orc_ray_hits(dim, Vs, Fs, nps, l, pts + p * dim, om, rmax, t, e, nw);
+    const int nh = orc_ray_hits(dim, Vs, Fs, nps, l, mdisp, pts + p * dim, om, rmax, t, e, nw);
     for (int k = 0; k < ORC_MAX_HITS; ++k) {
       const int64_t sl = q * ORC_MAX_HITS + k;
       hw[sl] = 0.0;
@@ -1283,6 +1438,7 @@ int64_t orc_clamp_correction(void* bvh, const double* g, const double* gv, doubl
   free(rank);
   free(hz);
   free(hw);
+  free(mdisp);
   return nhit;
 }
 
@@ -1313,10 +1469,13 @@ void orc_reduce_walks(int dim, int64_t n, int32_t W, const double* U, const doub
 /* FP32 crossing test puts it inside.  With p = 1/|box| on the box and the  */
 /* indicator of the domain, the weight of a kept sample is f(y) |box| and    */
 /* the source estimator divides by the number of candidates G0*G1.          */
-/* Kept samples are returned in candidate order.                            */
+/* Kept samples are returned in candidate order.  The region the BIE of the */
+/* cache refers to is the one inside the offset boundary (Sec. 3.2), so the */
+/* inside test takes the moved vertices Vin (orc_offset_vertices; NULL =   */
+/* V itself, offset 0); the box stays the boundary's own.                   */
 /* ------------------------------------------------------------------------ */
 int64_t orc_sample_source2d(const float* V, int64_t nv, const int32_t* F, int64_t np, int32_t G0, int32_t G1,
-                            uint64_t seed, const double* f, float* y_out, double* c_out) {
+                            uint64_t seed, const double* f, const float* Vin, float* y_out, double* c_out) {
   float lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
   for (int64_t i = 0; i < nv; ++i)
     for (int a = 0; a < 2; ++a) {
@@ -1334,7 +1493,7 @@ int64_t orc_sample_source2d(const float* V, int64_t nv, const int32_t* F, int64_
     const double y0 = (double)lo[0] + ((double)c0 + u[0]) * (ext0 / G0);
     const double y1 = (double)lo[1] + ((double)c1 + u[1]) * (ext1 / G1);
     const float fy0 = (float)y0, fy1 = (float)y1;
-    if (!inside2d_f32(V, F, np, fy0, fy1)) continue;
+    if (!inside2d_f32(Vin ? Vin : V, F, np, fy0, fy1)) continue;
     const double yy[2] = {fy0, fy1};
     y_out[2 * kept] = fy0;
     y_out[2 * kept + 1] = fy1;
@@ -1376,10 +1535,11 @@ double orc_winding3d(const float* V, const int32_t* F, int64_t np, const double*
 /* G2 cells over the bounding box; candidate c (cell c0 = c mod G0,         */
 /* c1 = (c / G0) mod G1, c2 = c / (G0 G1)) draws (u0,u1,u2) from Philox      */
 /* (id = c, word2 = 0, tag = 2) and is kept when the winding number is      */
-/* above 1/2.  Weight f(y) |box|; the estimator divides by G0 G1 G2.         */
+/* above 1/2 (winding number of the moved mesh Vin, as in 2D; NULL = V).   */
+/* Weight f(y) |box|; the estimator divides by G0 G1 G2.                    */
 /* winding_out (may be NULL) receives every candidate's winding number.     */
 int64_t orc_sample_source3d(const float* V, int64_t nv, const int32_t* F, int64_t np, int32_t G0, int32_t G1,
-                            int32_t G2, uint64_t seed, const double* f, float* y_out, double* c_out,
+                            int32_t G2, uint64_t seed, const double* f, const float* Vin, float* y_out, double* c_out,
                             double* winding_out) {
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t i = 0; i < nv; ++i)
@@ -1403,7 +1563,7 @@ int64_t orc_sample_source3d(const float* V, int64_t nv, const int32_t* F, int64_
       yc[3 * c + a] = (float)((double)lo[a] + ((double)ci[a] + u[a]) * (ext[a] / G[a]));
       y[a] = yc[3 * c + a];
     }
-    const double w = orc_winding3d(V, F, np, y);
+    const double w = orc_winding3d(Vin ? Vin : V, F, np, y);
     if (winding_out) winding_out[c] = w;
     keep[c] = w > 0.5;
   }
@@ -1431,11 +1591,14 @@ int64_t orc_sample_source3d(const float* V, int64_t nv, const int32_t* F, int64_
 /* and for every source sample (y, c = f(y)/p^Omega):                        */
 /*   u_src    += G(x,y) c,    grad_src += dG/dx(x,y) c                       */
 /* Returns SUMS (Alg. 1 running sums); the caller divides by N and M.       */
+/* jac (may be NULL = all 1): per boundary sample, 1/p = |dOmega| jac       */
+/* (samples on the offset boundary, see sample_boundary).                   */
 /* ------------------------------------------------------------------------ */
 /* clamp_c > 0: dG/dn in the u term clamped to [-c, c] (Sec. 3.3, Eq. 9);  */
 /* the gradient terms are not clamped.                                       */
 void orc_gather_full(int dim, double sqs, double clamp_c, int64_t N, const double* z, const double* nz,
-                     const double* u_hat, const double* q_hat, double bnd_measure, int64_t Ms, const double* y,
+                     const double* u_hat, const double* q_hat, double bnd_measure, const double* jac, int64_t Ms,
+                     const double* y,
                      const double* c, int64_t M, const double* x, double* u_bnd, double* u_src, double* g_bnd,
                      double* g_src, double* abs_out) {
 #pragma omp parallel for schedule(dynamic, 8)
@@ -1452,11 +1615,12 @@ void orc_gather_full(int dim, double sqs, double clamp_c, int64_t N, const doubl
       }
       orc_green_sigma(dim, sqs, xk, zz, nn, G);
       const double dGdn = clamp_c > 0.0 ? fmax(-clamp_c, fmin(clamp_c, G[1 + dim])) : G[1 + dim];
-      const double tu = (dGdn * u_hat[i] - G[0] * q_hat[i]) * bnd_measure;
+      const double ip = jac ? bnd_measure * jac[i] : bnd_measure; /* 1/p of sample i */
+      const double tu = (dGdn * u_hat[i] - G[0] * q_hat[i]) * ip;
       ub += tu;
       ab[0] += fabs(tu);
       for (int a = 0; a < dim; ++a) {
-        const double tg = (G[2 + dim + a] * u_hat[i] - G[1 + a] * q_hat[i]) * bnd_measure;
+        const double tg = (G[2 + dim + a] * u_hat[i] - G[1 + a] * q_hat[i]) * ip;
         gb[a] += tg;
         ab[1 + a] += fabs(tg);
       }
@@ -1485,15 +1649,15 @@ void orc_gather_full(int dim, double sqs, double clamp_c, int64_t N, const doubl
 void orc_gather_sigma(int dim, double sqs, int64_t N, const double* z, const double* nz, const double* u_hat,
                       const double* q_hat, double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M,
                       const double* x, double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
-  orc_gather_full(dim, sqs, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, Ms, y, c, M, x, u_bnd, u_src, g_bnd, g_src,
-                  abs_out);
+  orc_gather_full(dim, sqs, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, NULL, Ms, y, c, M, x, u_bnd, u_src, g_bnd,
+                  g_src, abs_out);
 }
 
 void orc_gather(int dim, int64_t N, const double* z, const double* nz, const double* u_hat, const double* q_hat,
                 double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M, const double* x,
                 double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out) {
-  orc_gather_full(dim, 0.0, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, Ms, y, c, M, x, u_bnd, u_src, g_bnd, g_src,
-                  abs_out);
+  orc_gather_full(dim, 0.0, 0.0, N, z, nz, u_hat, q_hat, bnd_measure, NULL, Ms, y, c, M, x, u_bnd, u_src, g_bnd,
+                  g_src, abs_out);
 }
 
 int orc_num_threads(void) {

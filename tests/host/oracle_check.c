@@ -3,7 +3,7 @@
  * (int32 dim, int64 n_verts, int64 n_prims, float32 V[n_verts*dim], int32
  * F[n_prims*dim], uint8 neumann[n_prims], int64 n_g, float64 g[n_g] (encoded
  * terms), int64 n_pts, float64 pts[n_pts*dim]) and runs the closest-point
- * BVH, boundary sampling, walks on spheres, the gather, the mixed-boundary
+ * BVH, the offset boundary and boundary sampling, walks on spheres, the gather, the mixed-boundary
  * queries and walks on stars, and (3D) the winding number, printing a few
  * sums.  Any sanitizer report fails the test. */
 #include <stdint.h>
@@ -14,14 +14,17 @@ void* orc_bvh_create(int dim, const float* V, int64_t nv, const int32_t* F, int6
 void orc_bvh_free(void* h);
 void orc_bvh_closest(void* h, const double* pts, int64_t n, double* dist, int32_t* prim, double* cp);
 double orc_boundary_measure(int dim, const float* V, const int32_t* F, int64_t np);
-void orc_sample_boundary(int dim, const float* V, const int32_t* F, int64_t np, int64_t N, double l, uint64_t seed,
-                         double* z, double* nrm, int32_t* elem);
+void orc_sample_boundary(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, int64_t N, double l,
+                         uint64_t seed, double* z, double* nrm, double* jac, int32_t* elem);
+double orc_offset_disp(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const uint8_t* fixed,
+                       double* m);
+void orc_gather_full(int dim, double sqs, double clamp_c, int64_t N, const double* z, const double* nz,
+                     const double* u_hat, const double* q_hat, double bnd_measure, const double* jac, int64_t Ms,
+                     const double* y, const double* c, int64_t M, const double* x, double* u_bnd, double* u_src,
+                     double* g_bnd, double* g_src, double* abs_out);
 void orc_walks(void* bvh, const double* g, const double* f, const float* starts, int64_t n, int32_t W, double eps,
                int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
                int32_t* steps, int32_t* prim, double* pend, double* scale);
-void orc_gather(int dim, int64_t N, const double* z, const double* nz, const double* u_hat, const double* q_hat,
-                double bnd_measure, int64_t Ms, const double* y, const double* c, int64_t M, const double* x,
-                double* u_bnd, double* u_src, double* g_bnd, double* g_src, double* abs_out);
 void* orc_wost_create(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const uint8_t* neu);
 void orc_wost_free(void* h);
 void orc_wost_query(void* h, const double* pts, int64_t n, double* d_dir, double* d_sil);
@@ -72,7 +75,11 @@ int main(int argc, char** argv) {
   double* z = (double*)calloc(N * dim, 8);
   double* nz = (double*)calloc(N * dim, 8);
   int32_t* el = (int32_t*)calloc(N, 4);
-  orc_sample_boundary(dim, V, F, np, N, 1e-3, 7, z, nz, el);
+  double* jac = (double*)calloc(N, 8);
+  orc_sample_boundary(dim, V, nv, F, np, N, 1e-3, 7, z, nz, jac, el);
+  /* the mixed boundary's offset (Dirichlet elements only) */
+  double* md = (double*)calloc(nv * dim, 8);
+  const double reach = orc_offset_disp(dim, V, nv, F, np, neu, md);
   float* zf = (float*)calloc(N * dim, 4);
   for (int64_t i = 0; i < N * dim; ++i) zf[i] = (float)z[i];
   double* U = (double*)calloc(N * W, 8);
@@ -94,8 +101,8 @@ int main(int argc, char** argv) {
   double* gb = (double*)calloc(npts * dim, 8);
   double* gs = (double*)calloc(npts * dim, 8);
   double* ab = (double*)calloc(npts * (2 + 2 * dim), 8);
-  orc_gather(dim, N, z, nz, uh, qh, orc_boundary_measure(dim, V, F, np), 0, NULL, NULL, npts, pts, ub, us, gb, gs,
-             ab);
+  orc_gather_full(dim, 0.0, 0.0, N, z, nz, uh, qh, orc_boundary_measure(dim, V, F, np), jac, 0, NULL, NULL, npts,
+                  pts, ub, us, gb, gs, ab);
   double s_u = 0.0;
   for (int64_t i = 0; i < npts; ++i) s_u += ub[i] / N;
 
@@ -117,10 +124,11 @@ int main(int argc, char** argv) {
   double s_wind = 0.0;
   if (dim == 3)
     for (int64_t i = 0; i < npts; ++i) s_wind += orc_winding3d(V, F, np, pts + i * dim);
-  printf("dist %.6g u %.6g wost %.6g winding %.6g\n", s_dist, s_u, s_w / W, s_wind);
+  printf("dist %.6g u %.6g wost %.6g winding %.6g reach %.6g\n", s_dist, s_u, s_w / W, s_wind, reach);
 
   orc_wost_free(w);
   orc_bvh_free(bvh);
+  free(jac), free(md);
   free(V), free(F), free(neu), free(g), free(pts), free(dist), free(prim), free(cp), free(z), free(nz), free(el);
   free(zf), free(U), free(grad), free(steps), free(wprim), free(pend), free(scale), free(uh), free(qh), free(ub);
   free(us), free(gb), free(gs), free(ab), free(dd), free(ds), free(pf), free(U2), free(g2), free(st2), free(pr2);

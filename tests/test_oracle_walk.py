@@ -114,7 +114,7 @@ def test_offset_inside_shell_gives_zero_normal_derivative():
     # Fig. "Ablations": l = 0.1 eps puts each ball inside the shell => du/dn^ = 0
     V, F = wl.circle_polygon(256)
     eps = 1e-3
-    z, n, e = oracle.sample_boundary(V, F, 64, 0.1 * eps, seed=1)
+    z, n, e, _ = oracle.sample_boundary(V, F, 64, 0.1 * eps, seed=1)
     g = [(wl.POLY, wl.poly2d_coeffs({(3, 0): 1.0, (1, 2): -3.0}))]
     out = oracle.walks(oracle.BVH(V, F), g, [], z.astype(np.float32), 4, eps, 1 << 14, seed=2)
     assert np.all(out["steps"] == 1)

@@ -311,7 +311,9 @@ def test_mixed_boundary_samples(dim):
         b = wl.box_mixed_3d()
         V, F, neu = b.V, b.F, b.neumann
     N, l = 3000, 0.01
-    z, n, e = oracle.sample_boundary_mixed(V, F, N, l, 4, neu)
+    z, n, e, jac = oracle.sample_boundary_mixed(V, F, N, l, 4, neu)
+    # flat Dirichlet sides: the offset boundary is their translate (jac 1)
+    np.testing.assert_allclose(jac, 1.0, rtol=1e-12)
     assert np.allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-12)
     on = neu[e] == 1
     p = z + np.where(on, 0.0, l)[:, None] * n
