@@ -47,14 +47,17 @@ if ROOT not in sys.path:
 METRIC = "interior pts/s at fixed RMSE (BVC vs pointwise WoS, 1 GB300); WoS steps/s; pairs/s"
 UNIT = "interior pts/s"
 L2_FLUSH_BYTES = 256 << 20
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MAX_STEPS = 1 << 14
 
-# Algorithmic work per unit: bytes per BVH node fetch and
-# per primitive test, per-walk input/output bytes, FP32 flops per pair.
+# Algorithmic work per unit: bytes per BVH node fetch (two child boxes and
+# links) and per primitive test (2D: a segment's two endpoints, 16 B; 3D:
+# three vertices, 48 B), per-walk input/output bytes, FP32 flops per pair.
 BYTES_NODE = {2: 48, 3: 64}
-BYTES_PRIM = {2: 32, 3: 48}
+BYTES_PRIM = {2: 16, 3: 48}
+# bytes the walk kernel actually loads per primitive test: the 2D record
+# also holds the edge vector, 1/|edge|^2 and the element id (two float4)
+FETCHED_PRIM = {2: 32, 3: 48}
 FLOPS_PAIR_BND = {2: 25, 3: 37}
 FLOPS_PAIR_SRC = {2: 9, 3: 13}
 # batched right-hand sides: per (point, sample) pair and group of 32
@@ -144,6 +147,12 @@ def device_info(local: int) -> dict:
     p = torch.cuda.get_device_properties(local)
     return {"name": p.name, "sm_count": p.multi_processor_count, "cc": f"{p.major}.{p.minor}",
             "memory_gib": round(p.total_memory / 2 ** 30, 1), "torch": torch.__version__, "cuda": torch.version.cuda}
+
+
+def sm_count(local: int) -> int:
+    """Streaming multiprocessors of this device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(local).multi_processor_count)
 
 
 def measured_peaks():
@@ -305,12 +314,15 @@ class Solver:
         # they run on a second stream, overlapping the cache build and gather
         self.side = torch.cuda.Stream(device=device)
 
-    def step(self, seed: int):
+    def step(self, seed: int, serial: bool = False):
+        """One solve.  serial: the pointwise walks run on the main stream
+        before the cache build (for per-kernel timing)."""
         bvc, w, torch = self.bvc, self.w, self.torch
         main = torch.cuda.current_stream()
         if self.m_near:
-            self.side.wait_stream(main)
-            with torch.cuda.stream(self.side):
+            if not serial:
+                self.side.wait_stream(main)
+            with torch.cuda.stream(main if serial else self.side):
                 bvc.eval_state_reset(self.near)
                 bvc.wos_estimate(self.geom, w.g, w.f, self.near, w.walks, w.eps, MAX_STEPS, seed, 0, self.ws_wos)
                 bvc.get_solution(self.near, self.u_near, self.g_near)
@@ -319,7 +331,7 @@ class Solver:
         bvc.cache_build(self.geom, w.g, w.f, self.opts, self.cache, self.ws_cache)
         bvc.evaluate(self.cache, self.far, self.ws_eval)
         bvc.get_solution(self.far, self.u_far, self.g_far)
-        if self.m_near:
+        if self.m_near and not serial:
             main.wait_stream(self.side)
 
     def counting_pass(self, seed: int):
@@ -341,13 +353,17 @@ class Solver:
         return cache_stats, near_stats
 
 
-def walk_bytes(stats, dim, n_walks):
-    return (stats["nodes"] * BYTES_NODE[dim] + stats["prims"] * BYTES_PRIM[dim]
+def walk_bytes(stats, dim, n_walks, prim_bytes=None):
+    """Bytes of a walk launch: node fetches x bytes per node + primitive
+    tests x bytes per primitive (algorithmic by default) + per-walk I/O."""
+    prim_bytes = BYTES_PRIM if prim_bytes is None else prim_bytes
+    return (stats["nodes"] * BYTES_NODE[dim] + stats["prims"] * prim_bytes[dim]
             + n_walks * (2 * dim * 4 + 8))
 
 
-def fixed_rmse_comparison(device, w_lit):
-    """Manufactured variant of the same workload (same geometry and sizes,
+def fixed_rmse_comparison(device, w_lit, solver=None):
+    """The workload itself when it has a closed-form solution (circle,
+    sphere), else its manufactured variant (star: same geometry and sizes,
     closed-form u): BVC RMSE tau at the configured sizes, then the number of
     pointwise walks per point that reaches RMSE <= tau, and both rates."""
     import torch
@@ -355,11 +371,12 @@ def fixed_rmse_comparison(device, w_lit):
     from paper_2302_11825_gb300 import workloads as wl
     if w_lit.name.startswith("star"):
         w = wl.star_poisson(manufactured=True)
+        solver = None
     else:
         w = w_lit
     if w.exact is None:
         return None
-    s = Solver(w, device)
+    s = solver if solver is not None else Solver(w, device)
     ex_far, gx_far = wl.eval_terms(w.exact, w.dim, s.far_pts.cpu().numpy().T.astype(np.float64))
     ex_near, _ = wl.eval_terms(w.exact, w.dim, s.near_pts.cpu().numpy().T.astype(np.float64))
     # the cache's error is shared by all points of a solve (correlated), so
@@ -452,7 +469,8 @@ def fixed_rmse_comparison(device, w_lit):
             lev.update(bvc_pts_per_s=bvc_rate, bvc_rmse=tau, bvc_n_samples=w.n_samples)
         else:
             from dataclasses import replace
-            fac = min(16.0, (tau / target) ** 2 * 1.1)
+            # (3D: at most 4x, to keep the benchmark within minutes)
+            fac = min(16.0 if w.dim == 2 else 4.0, (tau / target) ** 2 * 1.1)
             n2 = int(np.ceil(w.n_samples * fac / 1024.0) * 1024)
             g2 = tuple(int(np.ceil(gd * fac ** (1.0 / w.dim))) for gd in w.src_grid)
             s2 = Solver(replace(w, n_samples=n2, src_grid=g2), device)
@@ -472,15 +490,28 @@ def fixed_rmse_comparison(device, w_lit):
             torch.cuda.synchronize()
             lev.update(bvc_pts_per_s=(s2.m_far + s2.m_near) * 2 / (e0.elapsed_time(e1) / 1e3),
                        bvc_rmse=float(np.sqrt(np.mean(e2 ** 2))), bvc_n_samples=n2, bvc_src_grid=list(g2))
-        kk, rr, wr = wos_at(target)
-        capped = bool(kk >= kmax and rr > target)
-        if capped:
-            # variance ~ 1/k: the walks per point that would reach the target
-            kx = kk * (rr / target) ** 2
-            wr = wr * kk / kx
-            kk = int(np.ceil(kx))
-        lev.update(wos_walks_per_point=kk, wos_rmse=rr, wos_pts_per_s=wr,
-                   bvc_over_wos=lev["bvc_pts_per_s"] / wr, wos_extrapolated=capped)
+        def wos_level(tgt):
+            kk, rr, wr = wos_at(tgt)
+            capped = bool(kk >= kmax and rr > tgt)
+            if capped:
+                # variance ~ 1/k: the walks per point that would reach the target
+                kx = kk * (rr / tgt) ** 2
+                wr = wr * kk / kx
+                kk = int(np.ceil(kx))
+            return kk, rr, wr, capped
+
+        kk, rr, wr, capped = wos_level(target)
+        reached = lev["bvc_rmse"] <= target
+        lev.update(wos_walks_per_point=kk, wos_rmse=rr, wos_pts_per_s=wr, wos_extrapolated=capped,
+                   bvc_reached_tau=bool(reached),
+                   # an equal-RMSE speed-up only where the BVC reaches the target
+                   bvc_over_wos=lev["bvc_pts_per_s"] / wr if reached else None)
+        if not reached:
+            # the comparison at the error the BVC did reach
+            k2, r2, w2, c2 = wos_level(lev["bvc_rmse"])
+            lev["at_bvc_rmse"] = {"tau": lev["bvc_rmse"], "wos_walks_per_point": k2, "wos_rmse": r2,
+                                  "wos_pts_per_s": w2, "wos_extrapolated": c2,
+                                  "bvc_over_wos": lev["bvc_pts_per_s"] / w2}
         levels.append(lev)
     out["range_u"] = urange
     out["levels"] = levels
@@ -492,9 +523,8 @@ def oracle_sample_rates(w, budget_s: float = 20.0):
     """Times the FP64 oracle on bounded samples of the workload and
     extrapolates the time of one full step.  Returns (step seconds, info)."""
     import oracle
-    from tests.oracle_pipeline import oracle_cache  # noqa: F401  (same composition as the tests)
     bvh = oracle.BVH(w.V, w.F)
-    z, n, _ = oracle.sample_boundary(w.V, w.F, 4096, w.offset_l, 0)
+    z, n, _, _ = oracle.sample_boundary(w.V, w.F, 4096, w.offset_l, 0)
     # walks: grow the sample until ~budget/3
     ns = 64
     while True:
@@ -519,12 +549,13 @@ def oracle_sample_rates(w, budget_s: float = 20.0):
     # source candidates (2D): inside test on a sample of candidates
     src_s = 0.0
     n_src_cand = w.src_grid[0] * w.src_grid[1] if w.f else 0
+    kept_src = 0.0
     if n_src_cand:
         t0 = time.perf_counter()
-        oracle.sample_source2d(w.V, w.F, (64, 16), 0, w.f)
-        src_s = (time.perf_counter() - t0) * n_src_cand / (64 * 16)
+        ys, _, nc = oracle.sample_source2d(w.V, w.F, (64, 64), 0, w.f, l=w.offset_l)
+        src_s = (time.perf_counter() - t0) * n_src_cand / nc
+        kept_src = ys.shape[0] / nc * n_src_cand  # the oracle's own kept share
     M = w.eval_pts.shape[0]
-    kept_src = 0.45 * n_src_cand
     t_step = (N * w.walks) / walk_rate + M * (N + kept_src) / pair_rate + src_s
 
     def one_core():
@@ -681,7 +712,7 @@ def bench_batched(args, rank, local, ws):
     Kst = args.steps
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = sm_count(local) * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     total_ms = sum(v[1] for v in prof.values())
     kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -698,7 +729,7 @@ def bench_batched(args, rank, local, ws):
     walk_roof["frac"] = walk_roof["achieved"] / walk_roof["peak"]
     gather_roof = {"bound": "alu", "achieved": gather_flops / (g_ms / 1e3) / 1e12, "peak": fp32_peak,
                    "unit": "TFLOP/s", "kernel": "gather_multi", "traffic": profile_traffic("gather_multi", w.name),
-                   "peak_source": f"FP32 FMA peak = {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max} MHz"}
+                   "peak_source": f"FP32 FMA peak = {sm_count(local)} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max} MHz"}
     gather_roof["frac"] = gather_roof["achieved"] / fp32_peak
     dominant = walk_roof if walk_ms >= g_ms else gather_roof
     units = M * K_rhs
@@ -743,7 +774,7 @@ def batched_oracle_rate(w, budget_s: float = 20.0):
     import oracle
     V, F = w.meshes[0][1], w.meshes[0][2]
     bvh = oracle.BVH(V, F)
-    z, _, _ = oracle.sample_boundary(V, F, 256, w.offset_l[0], 0)
+    z, _, _, _ = oracle.sample_boundary(V, F, 256, w.offset_l[0], 0)
     g = [(1, w.coeffs[0, 0])]
     ns = 16
     while True:
@@ -866,7 +897,7 @@ def bench_inverse(args, rank, local, ws):
     Kst = args.steps
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = sm_count(local) * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     total_ms = sum(v[1] for v in prof.values())
     kernels = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1), "share": v[1] / total_ms}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -929,7 +960,7 @@ def inverse_oracle_step_s(w, budget_s: float = 20.0):
     gather), extrapolated as twice the forward's work."""
     import oracle
     bvh = oracle.BVH(w.V, w.F)
-    z, _, _ = oracle.sample_boundary(w.V, w.F, 64, w.offset_l, 0)
+    z, _, _, _ = oracle.sample_boundary(w.V, w.F, 64, w.offset_l, 0)
     f = [(2, [w.bump_sigma] + [v for a, cc in zip(w.a_true, w.bump_centres) for v in [a, *cc]])]
     t0 = time.perf_counter()
     oracle.walks(bvh, [], f, z.astype(np.float32), w.walks, w.eps, MAX_STEPS, 0, 0, 0,
@@ -1108,7 +1139,7 @@ def mixed_oracle_step_s(w, budget_s: float = 20.0):
     against the full cache, extrapolated to the step."""
     import oracle
     wo = oracle.Wost(w.V, w.F, w.neumann)
-    z, n, e = oracle.sample_boundary_mixed(w.V, w.F, 4096, w.offset_l, 0, w.neumann)
+    z, n, e, _ = oracle.sample_boundary_mixed(w.V, w.F, 4096, w.offset_l, 0, w.neumann)
     sel = np.arange(0, 4096, 128 if w.dim == 2 else 512)
     se = np.where(w.neumann[e[sel]] == 1, e[sel], -1).astype(np.int32)
     t0 = time.perf_counter()
@@ -1217,7 +1248,7 @@ def bench_mixed(args, rank, local, ws):
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = sm_count(local) * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     n_walks = w.n_samples * w.walks + s.m_near * s.near_walks
     walk_b = walk_bytes(cstats, dim, n_walks)
     n_src_kept = int(s.cache.n_src_dev.item()) if s.cache.n_src_cand else 0
@@ -1286,7 +1317,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="star",
+    ap.add_argument("--workload", default="sphere",
                     choices=["star", "circle", "sphere", "batched", "inverse", "mixed", "mixed3d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed-rmse", action="store_true")
@@ -1413,38 +1444,56 @@ def main():
     d2h = (s.m_far + s.m_near) * (1 + dim) * 8
     assert np.all(np.isfinite(u_far_h.numpy())) and np.all(np.isfinite(u_near_h.numpy()))
 
-    # ---- per-kernel breakdown and the roofline of the dominant kernel
+    # ---- per-kernel times and the roofline of the dominant kernel, from two
+    # more (untimed) steps with the pointwise walks serialised on the main
+    # stream, so that every launch's event time is its own work, not time
+    # spent waiting beside a launch on the other stream
     K = args.steps
-    total_ms = sum(v[1] for v in prof.values())
-    kernels = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1), "share": v[1] / total_ms}
-               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     launches = sum(v[0] for v in prof.values())
+    KS = 2
+    torch.cuda.synchronize()
+    bvc.profile_begin()
+    for k in range(KS):
+        flush.zero_()
+        s.step(rank_seed(rank, k, 3_000_000), serial=True)
+    sprof = bvc.profile_end()
+    torch.cuda.synchronize()
+    total_ms = sum(v[1] for v in sprof.values())
+    kernels = {k: {"launches": v[0] / KS, "avg_ms": v[1] / max(v[0], 1), "ms_per_step": v[1] / KS,
+                   "share": v[1] / total_ms}
+               for k, v in sorted(sprof.items(), key=lambda kv: -kv[1][1])}
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak_tflops = sm_count(local) * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     n_walks_cache = w.n_samples * w.walks
-    walk_cache_bytes = walk_bytes(cache_stats, dim, n_walks_cache)
     n_src_kept = int(s.cache.n_src_dev.item()) if s.cache.n_src_cand else 0
     pairs_bnd = s.m_far * w.n_samples
     pairs_src = s.m_far * n_src_kept
-    dominant = max(prof.items(), key=lambda kv: kv[1][1])[0]
-    gb_ms = prof.get("gather_boundary", (1, float("nan")))[1] / max(prof.get("gather_boundary", (1, 1))[0], 1)
-    gs_ms = prof.get("gather_source", (1, 0.0))[1] / max(prof.get("gather_source", (1, 1))[0], 1)
-    # walk time per step includes the once-per-start first queries
-    walk_ms_total = (prof.get("walk", (0, 0.0))[1] + prof.get("first_hits", (0, 0.0))[1]) / K
+    dominant = max(sprof.items(), key=lambda kv: kv[1][1])[0]
+    gb_ms = kernels.get("gather_boundary", {}).get("avg_ms", float("nan"))
+    gs_ms = kernels.get("gather_source", {}).get("avg_ms", 0.0)
+    # walk time per step: the cache walk and the pointwise walk launches
+    # (the once-per-start first queries are a separate, small kernel)
+    walk_ms_step = kernels.get("walk", {}).get("ms_per_step", float("nan"))
     steps_cache = cache_stats["steps"]
     steps_near = near_stats["steps"]
+    n_walks_near = s.m_near * w.walks
+    walk_alg = (walk_bytes(cache_stats, dim, n_walks_cache, BYTES_PRIM)
+                + walk_bytes(near_stats, dim, n_walks_near, BYTES_PRIM))
+    walk_fetch = (walk_bytes(cache_stats, dim, n_walks_cache, FETCHED_PRIM)
+                  + walk_bytes(near_stats, dim, n_walks_near, FETCHED_PRIM))
+    l2_bytes = int(torch.cuda.get_device_properties(local).L2_cache_size)
+    resident = s.geom.info().device_bytes < l2_bytes / 2
+    walk_gbs = walk_alg / (walk_ms_step / 1e3) / 1e9
     if dominant == "walk":
-        # average over the step's walk launches: algorithmic bytes of both / their time
-        bytes_step = walk_cache_bytes + walk_bytes(near_stats, dim, s.m_near * w.walks)
-        launches_per_step = prof["walk"][0] / K
-        achieved = bytes_step / launches_per_step / (kernels["walk"]["avg_ms"] / 1e3) / 1e9
         peak = float(peaks["hbm_gbs"])
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        roofline = {"bound": "hbm", "achieved": walk_gbs, "peak": peak, "unit": "GB/s", "frac": walk_gbs / peak,
                     "traffic": profile_traffic("walk", w.name), "kernel": "walk",
                     "peak_source": f"{peak_src} (hbm_gbs)",
-                    "note": "BVH and mesh are L2-resident; bytes are algorithmic (node fetches x bytes/node + "
-                            "primitive tests x bytes/primitive + per-walk I/O)"}
+                    "fetched_gbs": walk_fetch / (walk_ms_step / 1e3) / 1e9,
+                    "note": ("tree and mesh fit in half the L2; " if resident else "tree and mesh exceed half the "
+                             "L2; ") + "bytes are algorithmic (node fetches x 48/64 B + primitive tests x 16/48 B "
+                             "+ per-walk I/O) over the walk launches' own time"}
     else:
         kname = dominant
         if kname == "gather_boundary":
@@ -1455,25 +1504,26 @@ def main():
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak_tflops, "traffic": profile_traffic(kname, w.name),
                     "kernel": kname,
-                    "peak_source": f"FP32 FMA peak = {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max} MHz"}
+                    "peak_source": f"FP32 FMA peak = {sm_count(local)} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                   f"{sm_max} MHz"}
     # secondary rooflines, reported beside the main one
     extra = {}
-    if "gather_boundary" in prof:
+    if "gather_boundary" in sprof:
         a = pairs_bnd * FLOPS_PAIR_BND[dim] / (gb_ms / 1e3) / 1e12
         extra["gather_boundary"] = {"bound": "alu", "achieved_tflops": a, "frac_fp32_peak": a / fp32_peak_tflops,
                                     "pairs_per_launch": pairs_bnd, "avg_ms": gb_ms}
-    if "gather_source" in prof and pairs_src:
+    if "gather_source" in sprof and pairs_src:
         a = pairs_src * FLOPS_PAIR_SRC[dim] / (gs_ms / 1e3) / 1e12
         extra["gather_source"] = {"bound": "alu", "achieved_tflops": a, "frac_fp32_peak": a / fp32_peak_tflops,
                                   "pairs_per_launch": pairs_src, "avg_ms": gs_ms}
-    if "walk" in prof:
-        bytes_step = walk_cache_bytes + walk_bytes(near_stats, dim, s.m_near * w.walks)
-        a = bytes_step / (walk_ms_total / 1e3) / 1e9
-        extra["walk"] = {"bound": "hbm", "achieved_gbs": a, "frac_hbm_peak": a / float(peaks["hbm_gbs"]),
+    if "walk" in sprof:
+        extra["walk"] = {"bound": "hbm", "achieved_gbs": walk_gbs, "frac_hbm_peak": walk_gbs / float(peaks["hbm_gbs"]),
+                         "fetched_gbs": walk_fetch / (walk_ms_step / 1e3) / 1e9,
                          "steps_per_launch_cache": steps_cache, "steps_per_launch_near": steps_near,
                          "nodes_per_step": (cache_stats["nodes"] + near_stats["nodes"]) / max(steps_cache + steps_near, 1),
                          "prims_per_step": (cache_stats["prims"] + near_stats["prims"]) / max(steps_cache + steps_near, 1),
-                         "ms_per_step_total": walk_ms_total}
+                         "ms_per_step_total": walk_ms_step, "tree_bytes": int(s.geom.info().device_bytes),
+                         "l2_bytes": l2_bytes}
 
     value = step_value(M, K, ws, t_max)
     out = {
@@ -1490,8 +1540,8 @@ def main():
                                   "tuned_ms": s.walk_shape[2]}},
         "roofline": roofline,
         "kernels": kernels, "rooflines_all": extra,
-        "wos_steps_per_s": (run_stats["steps"]) / max(walk_ms_total * K / 1e3, 1e-12),
-        "pairs_per_s": (pairs_bnd + pairs_src) / ((gb_ms + gs_ms) / 1e3) if "gather_boundary" in prof else None,
+        "wos_steps_per_s": (steps_cache + steps_near) / max(walk_ms_step / 1e3, 1e-12),
+        "pairs_per_s": (pairs_bnd + pairs_src) / ((gb_ms + gs_ms) / 1e3) if "gather_boundary" in sprof else None,
         "e2e": {"value": step_value(M, e2e_steps, ws, t_e2e), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "gpu_launches": int(launches),
@@ -1500,7 +1550,7 @@ def main():
         "walk_caps": run_stats["capped"],
     }
     if rank == 0 and ws == 1 and not args.no_fixed_rmse:
-        out["fixed_rmse"] = optional_part(lambda: fixed_rmse_comparison(device, w))
+        out["fixed_rmse"] = optional_part(lambda: fixed_rmse_comparison(device, w, s))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         def cpu():
             t_cpu, info = oracle_sample_rates(w)

@@ -103,7 +103,9 @@ typedef struct {
  * (binned SAH) and copied to device memory the handle owns; the copy is
  * enqueued on `stream` and the call returns once it is complete.  The
  * handle also holds the element-measure CDF used by boundary sampling
- * (Sec. 4 "Sampling") and a small device status/statistics block. */
+ * (Sec. 4 "Sampling"), the per-vertex displacements of the offset boundary
+ * (Sec. 3.2, see bvc_sample_boundary) and a small device status/statistics
+ * block. */
 typedef struct bvc_geometry_s* bvc_geometry;
 
 bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
@@ -116,6 +118,7 @@ typedef struct {
   double boundary_measure; /* |dOmega|: total length (2D) or area (3D), FP64 sequential sum */
   float bbox_lo[3], bbox_hi[3];
   size_t device_bytes; /* device memory owned by the handle */
+  double offset_reach; /* max_v |m_v| >= 1: the offset boundary at l lies within l x reach of the boundary */
 } bvc_geometry_info;
 bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* info);
 
@@ -143,23 +146,36 @@ bvc_status bvc_geometry_set_counting(bvc_geometry g, int32_t on);
 bvc_status bvc_query_closest(bvc_geometry g, const float* pts, int64_t m, float* d2, int32_t* prim, float* cp,
                              bvc_stream stream);
 
-/* Flag evaluation points closer than `l` to the boundary (Sec. 3.2: such
- * points get pointwise walk-on-spheres estimates instead of the cache).
- * near: device uint8[m], 1 if distance < l. */
+/* Flag evaluation points that may lie outside the region bounded by the
+ * offset boundary at `l` (Sec. 3.2: such points get pointwise walk-on-
+ * spheres estimates instead of the cache): near: device uint8[m], 1 if the
+ * distance to the boundary is below l x offset_reach (bvc_geometry_info;
+ * every point of the strip between the boundary and the offset boundary is
+ * that close). */
 bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_t m, float l, uint8_t* near,
                              bvc_stream stream);
 
 /* ----------------------------------------------------- cache build steps */
 /* K1 -- boundary samples (Alg. 1 "b.z, b.n_z ~ p", Sec. 4 "Sampling",
- * Sec. 3.2 offset).  Sample i draws Philox(id = i, word2 = 0, tag = 1) ->
- * (u0, u1, u2); s = (i + u0)/n selects the element by the FP64 CDF of
- * element measures (stratified); in 2D the remainder of s inside the
- * element is the arclength position, in 3D (u1, u2) place the point
- * uniformly on the triangle (barycentrics 1 - sqrt(u1), sqrt(u1)(1 - u2),
- * sqrt(u1) u2).  Output z = p - l n (FP64 arithmetic, rounded to FP32),
- * n the outward unit normal of the element; p = 1/|dOmega|.
- * z, nrm: device float[dim][n]; elem: device int32[n] or NULL. */
-bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
+ * Sec. 3.2 offset boundary).  The offset boundary at l is the closed
+ * surface of the mesh with every vertex v moved to v - l m_v, the region it
+ * bounds being the one the cache's integral equation (Eq. 2) and source
+ * samples refer to: in 2D m_v is the miter of the vertex's two segments
+ * with normals na, nb, (na + nb) / max(1 + na.nb, 1/4), so each moved
+ * segment is parallel to its element at distance l (any other number k of
+ * segments: their normals' sum, normalised); in 3D m_v = N^ / max(min_f
+ * n_f . N^, 1/4) with N^ the angle-weighted vertex normal, so no incident
+ * face moves by less than l.  Sample i draws Philox(id = i, word2 = 0,
+ * tag = 1) -> (u0, u1, u2); s = (i + u0)/n selects the element by the FP64
+ * CDF of element measures (stratified); in 2D the remainder of s inside the
+ * element is the arclength fraction, in 3D (u1, u2) give the barycentrics
+ * 1 - sqrt(u1), sqrt(u1)(1 - u2), sqrt(u1) u2.  The sample is the point with
+ * those coordinates on the MOVED element (FP64, rounded to FP32), nrm the
+ * moved element's outward unit normal, and jac = |moved element| /
+ * |element|, so that 1/p = |dOmega| jac.  l = 0 gives points on the mesh
+ * and jac = 1.  z, nrm: device float[dim][n]; jac: device float[n];
+ * elem: device int32[n] or NULL. */
+bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm, float* jac,
                                int32_t* elem, bvc_stream stream);
 
 /* K2 / K6 -- walks on spheres (Sec. 3.1) from n start points, `walks` each;
@@ -201,6 +217,7 @@ typedef struct {
   int64_t n;            /* N boundary samples */
   float* z;             /* [dim][n] sample positions on the offset boundary */
   float* nrm;           /* [dim][n] unit outward normals */
+  float* jac;           /* [n] measure ratios of the samples' offset elements (1/p = bnd_measure jac) */
   double* u_hat;        /* [n] estimates of u */
   double* dudn_hat;     /* [n] estimates of du/dn */
   float* packed;        /* [n][20] gather tiles, written by bvc_cache_pack */
@@ -218,8 +235,10 @@ typedef struct {
  * grid[0] x grid[1] (x grid[2] in 3D) grid of candidates over the
  * boundary's bounding box; candidate c (cell c mod G0, (c / G0) mod G1,
  * c / (G0 G1)) draws Philox(id = c, word2 = 0, tag = 2) for its position in
- * its cell.  2D: kept when the canonical FP32 crossing test puts it inside
- * the polygon.  3D: kept when the generalized winding number of the mesh
+ * its cell.  The region is the one inside the offset boundary at offset_l
+ * (Sec. 3.2; its vertices fl32(v - offset_l m_v), see bvc_sample_boundary;
+ * 0 = the mesh itself).  2D: kept when the canonical FP32 crossing test puts
+ * it inside that polygon.  3D: kept when the generalized winding number of that mesh
  * (the sum of its triangles' signed solid angles over 4 pi, FP32) is above
  * 1/2 -- 1 inside a closed outward-wound surface, so holes are wound
  * inward; overlapping shells are counted with their orientation, not
@@ -230,18 +249,19 @@ typedef struct {
  * bvc_sample_source_workspace_size. */
 bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes);
 bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[3], uint64_t seed,
-                             bvc_cache* cache, void* workspace, size_t workspace_bytes, bvc_stream stream);
+                             double offset_l, bvc_cache* cache, void* workspace, size_t workspace_bytes,
+                             bvc_stream stream);
 
 /* Pack z, nrm, u_hat, dudn_hat (and the kept source samples) into the
- * gather's tile layout, folding 1/p and the Green's function constants of
- * App. A into the per-sample coefficients. */
+ * gather's tile layout, folding 1/p = bnd_measure jac and the Green's
+ * function constants of App. A into the per-sample coefficients. */
 bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream);
 
 typedef struct {
   int64_t n_samples;        /* N */
   int32_t walks_per_sample; /* nWalks of Alg. 1 */
   int32_t max_steps;        /* cap on closest-point queries per walk (e.g. 1 << 14) */
-  double offset_l;          /* Sec. 3.2 offset l > eps */
+  double offset_l;          /* Sec. 3.2 offset l > eps of the offset boundary (see bvc_sample_boundary) */
   double eps;               /* epsilon shell width */
   uint64_t seed;
   uint64_t walk_id_base;    /* first walk id: distinct caches of one seed use disjoint ranges */
@@ -259,7 +279,8 @@ typedef struct {
                                build gives, without the inside tests. */
 } bvc_cache_opts;
 
-/* The whole cache: K1 -> K2 (chunked through the workspace) -> K3 -> K4 -> pack.
+/* The whole cache: K1 -> K2 (chunked through the workspace) -> K3 -> K4 (in
+ * the region inside the offset boundary at opts->offset_l) -> pack.
  * cache->n must equal opts->n_samples; n_src_cand must equal the grid size.
  * Any workspace of at least bvc_cache_build_workspace_size(min) bytes works;
  * larger ones (up to `full`) run the walks in fewer chunks. */
@@ -358,8 +379,9 @@ bvc_status bvc_cache_build_region(bvc_geometry domain, bvc_geometry region, cons
  * cache built with opts.clamp_c = c (its gather uses dG/dn clamped to
  * [-c, c] in the u term), u_corr[x] (device double[m], overwritten) is an
  * unbiased estimate of int [dG/dn - clamp_c(dG/dn)] u dz over the sample
- * surface -- `surface` with its elements moved by -offset_l n (the cache's
- * geometry and offset, or a region and 0) -- so that get_solution + u_corr
+ * surface -- the offset boundary of `surface` at offset_l (its vertices
+ * moved by -offset_l m_v as in bvc_sample_boundary: the cache's geometry and
+ * offset, or a region and 0) -- so that get_solution + u_corr
  * is unbiased.  n_dirs directions per point (Philox id = point * n_dirs + j,
  * word2 0, tag 4) sample the signed solid angle; every crossing closer than
  * 1/(2 pi c) (2D) or (4 pi c)^(-1/2) (3D) with |dG/dn| > c adds
@@ -437,6 +459,7 @@ typedef struct {
   int32_t k;           /* right-hand sides */
   float* z;            /* [dim][n] */
   float* nrm;          /* [dim][n] */
+  float* jac;          /* [n] measure ratios (1/p = |dOmega| jac) */
   double* mom_u;       /* [n][bvc_poly_terms(dim)] means of phi_m at walk ends */
   double* mom_q;       /* [n][bvc_poly_terms(dim)] means of s (phi_m(end) - phi_m(p0)) */
   double* u_hat;       /* [k][n] */
@@ -534,7 +557,9 @@ bvc_status wos_estimate_sigma(bvc_geometry g, const bvc_function* gfn, const bvc
  * fit: walks > 1,398,057 (2D) or 1,048,542 (3D) returns BVC_ERR_WORKSPACE.
  * Arguments, results and state semantics are those of wos_estimate.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
+ * capture.  The address is kept for the lifetime of the device's context:
+ * after cudaDeviceReset (or any teardown of the primary context) it is
+ * stale, and this entry point must not be called again in that process.  All calls share the one array: calls that overlap on the GPU
  * (on different streams, or from several threads) race on it and must be
  * serialised by the caller.  The work counter in the array is cleared at
  * the start of every call. */
@@ -548,8 +573,11 @@ bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_function* gfn, 
  * (Sec. 3.1, Fig. "WoS vs WoSt") and the cache of Sec. 3.2 / Fig.
  * "Dirichlet offset boundary": samples on Neumann elements lie on the
  * boundary and carry the known du/dn = h(z); samples on Dirichlet elements
- * are moved inward by l and carry walk estimates of u and du/dn; u on the
- * Neumann samples is estimated by walks that start on the boundary.
+ * lie on the offset boundary built from the Dirichlet elements alone (as
+ * bvc_sample_boundary, with displacements from the Dirichlet elements at
+ * each vertex, so a vertex shared with a Neumann element moves along its
+ * Dirichlet element's normal) and carry walk estimates of u and du/dn; u on
+ * the Neumann samples is estimated by walks that start on the boundary.
  *
  * A walk step at x: distance d_D to the Dirichlet part (stop when below eps,
  * returning g at the closest Dirichlet point); star radius
@@ -641,9 +669,9 @@ bvc_status bvc_mixed_walk(bvc_mixed m, const bvc_function* gfn, const bvc_neuman
                           int32_t* steps, int32_t* prim, unsigned long long* counter, bvc_stream stream);
 
 /* The mixed cache: K1 on the whole boundary (Neumann samples at offset 0,
- * Dirichlet samples at offset_l), walks on stars (tag 0, ids as
- * bvc_cache_build), K3, source samples (opts->src_grid, inside the whole
- * boundary), pack.  dudn_hat of a Neumann sample is h(z).  sigma and
+ * Dirichlet samples on the Dirichlet offset boundary at offset_l), walks on
+ * stars (tag 0, ids as bvc_cache_build), K3, source samples (opts->src_grid,
+ * inside the whole boundary itself), pack.  dudn_hat of a Neumann sample is h(z).  sigma and
  * clamp_c must be 0.  Workspace as bvc_cache_build on the whole geometry. */
 bvc_status bvc_mixed_cache_build_workspace_size(bvc_mixed m, const bvc_cache_opts* opts, size_t* min_bytes,
                                                 size_t* full_bytes);

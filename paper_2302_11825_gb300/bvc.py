@@ -46,11 +46,11 @@ class Function(C.Structure):
 class GeometryInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_verts", C.c_int64), ("n_prims", C.c_int64), ("n_nodes", C.c_int64),
                 ("boundary_measure", C.c_double), ("bbox_lo", C.c_float * 3), ("bbox_hi", C.c_float * 3),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("offset_reach", C.c_double)]
 
 
 class CacheStruct(C.Structure):
-    _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("z", C.c_void_p), ("nrm", C.c_void_p),
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("z", C.c_void_p), ("nrm", C.c_void_p), ("jac", C.c_void_p),
                 ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p), ("packed", C.c_void_p),
                 ("bnd_measure", C.c_double), ("n_src_cand", C.c_int64), ("src_y", C.c_void_p),
                 ("src_c", C.c_void_p), ("src_packed", C.c_void_p), ("n_src_dev", C.c_void_p),
@@ -66,7 +66,7 @@ class CacheOpts(C.Structure):
 
 class MultiCacheStruct(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("k", C.c_int32), ("z", C.c_void_p), ("nrm", C.c_void_p),
-                ("mom_u", C.c_void_p), ("mom_q", C.c_void_p), ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p),
+                ("jac", C.c_void_p), ("mom_u", C.c_void_p), ("mom_q", C.c_void_p), ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p),
                 ("packed", C.c_void_p), ("bnd_measure", C.c_double)]
 
 
@@ -107,13 +107,13 @@ def _declare(lib):
         "bvc_geometry_stats": (S, [P, C.POINTER(C.c_uint64), i32, P]),
         "bvc_query_closest": (S, [P, P, i64, P, P, P, P]),
         "bvc_classify_near": (S, [P, P, i64, f32, P, P]),
-        "bvc_sample_boundary": (S, [P, i64, f64, u64, P, P, P, P]),
+        "bvc_sample_boundary": (S, [P, i64, f64, u64, P, P, P, P, P]),
         "bvc_walk": (S, [P, C.POINTER(Function), C.POINTER(Function), P, P, i64, i32, f32, i32, u64, u64, u32, P, P,
                          P, P]),
         "bvc_reduce_walks": (S, [P, i64, i32, i32, i32, P, P]),
         "bvc_sample_source_workspace_size": (S, [i64, C.POINTER(sz)]),
-        "bvc_sample_source": (S, [P, C.POINTER(Function), C.POINTER(C.c_int32), u64, C.POINTER(CacheStruct), P, sz,
-                                  P]),
+        "bvc_sample_source": (S, [P, C.POINTER(Function), C.POINTER(C.c_int32), u64, f64, C.POINTER(CacheStruct), P,
+                                  sz, P]),
         "bvc_cache_pack": (S, [C.POINTER(CacheStruct), P]),
         "bvc_cache_build_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz), C.POINTER(sz)]),
         "bvc_cache_build": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(CacheOpts),
@@ -321,12 +321,14 @@ def classify_near(geom: Geometry, pts: torch.Tensor, l: float, stream=None) -> t
 
 
 def sample_boundary(geom: Geometry, n: int, l: float, seed: int, want_elem=True, stream=None):
+    """K1: (z, nrm, elem, jac) on the offset boundary at l (1/p = |dOmega| jac)."""
     z = torch.empty((geom.dim, n), dtype=torch.float32, device="cuda")
     nrm = torch.empty_like(z)
+    jac = torch.empty(n, dtype=torch.float32, device="cuda")
     elem = torch.empty(n, dtype=torch.int32, device="cuda") if want_elem else None
-    _check(lib().bvc_sample_boundary(geom.h, n, float(l), int(seed), _ptr(z), _ptr(nrm), _ptr(elem),
+    _check(lib().bvc_sample_boundary(geom.h, n, float(l), int(seed), _ptr(z), _ptr(nrm), _ptr(jac), _ptr(elem),
                                      _stream(stream)), "bvc_sample_boundary")
-    return z, nrm, elem
+    return z, nrm, elem, jac
 
 
 def walk(geom: Geometry, g_terms, f_terms, starts, nrm, walks: int, eps: float, max_steps: int, seed: int,
@@ -366,6 +368,7 @@ class Cache:
         self.dim, self.n, self.n_src_cand = dim, n, n_src_cand
         self.z = torch.zeros((dim, n), dtype=torch.float32, device=device)
         self.nrm = torch.zeros((dim, n), dtype=torch.float32, device=device)
+        self.jac = torch.ones(n, dtype=torch.float32, device=device)
         self.u_hat = torch.zeros(n, dtype=torch.float64, device=device)
         self.dudn_hat = torch.zeros(n, dtype=torch.float64, device=device)
         self.packed = torch.zeros((n, 20), dtype=torch.float32, device=device)
@@ -382,6 +385,7 @@ class Cache:
         s.dim, s.n = self.dim, self.n
         s.z, s.nrm, s.u_hat, s.dudn_hat, s.packed = (_ptr(self.z), _ptr(self.nrm), _ptr(self.u_hat),
                                                      _ptr(self.dudn_hat), _ptr(self.packed))
+        s.jac = _ptr(self.jac)
         s.bnd_measure = float(self.bnd_measure)
         s.n_src_cand = self.n_src_cand
         s.src_y, s.src_c, s.src_packed, s.n_src_dev = (_ptr(self.src_y), _ptr(self.src_c), _ptr(self.src_packed),
@@ -436,15 +440,17 @@ def cache_build(geom: Geometry, g_terms, f_terms, opts: CacheOpts, cache: Cache,
     return cache
 
 
-def sample_source(geom: Geometry, f_terms, grid, seed: int, cache: Cache, ws: torch.Tensor = None, stream=None):
+def sample_source(geom: Geometry, f_terms, grid, seed: int, cache: Cache, ws: torch.Tensor = None, stream=None,
+                  l: float = 0.0):
+    """K4: source candidates kept inside the offset boundary at l (0: the mesh)."""
     need = C.c_size_t()
     _check(lib().bvc_sample_source_workspace_size(cache.n_src_cand, C.byref(need)), "workspace size")
     if ws is None:
         ws = workspace(need.value)
     f = make_function(f_terms)
     gr = (C.c_int32 * 3)(int(grid[0]), int(grid[1]), int(grid[2]) if len(grid) > 2 else 0)
-    _check(lib().bvc_sample_source(geom.h, C.byref(f), gr, int(seed), C.byref(cache.struct), _ptr(ws), ws.numel(),
-                                   _stream(stream)), "bvc_sample_source")
+    _check(lib().bvc_sample_source(geom.h, C.byref(f), gr, int(seed), float(l), C.byref(cache.struct), _ptr(ws),
+                                   ws.numel(), _stream(stream)), "bvc_sample_source")
 
 
 def cache_pack(cache: Cache, stream=None):
@@ -739,6 +745,7 @@ class MultiCache:
         groups = (k + MULTI_GROUP - 1) // MULTI_GROUP
         self.z = torch.zeros((dim, n), dtype=torch.float32, device=device)
         self.nrm = torch.zeros((dim, n), dtype=torch.float32, device=device)
+        self.jac = torch.ones(n, dtype=torch.float32, device=device)
         self.mom_u = torch.zeros((n, t), dtype=torch.float64, device=device)
         self.mom_q = torch.zeros((n, t), dtype=torch.float64, device=device)
         self.u_hat = torch.zeros((k, n), dtype=torch.float64, device=device)
@@ -747,6 +754,7 @@ class MultiCache:
         st = MultiCacheStruct()
         st.dim, st.n, st.k = dim, n, k
         st.z, st.nrm, st.mom_u, st.mom_q = _ptr(self.z), _ptr(self.nrm), _ptr(self.mom_u), _ptr(self.mom_q)
+        st.jac = _ptr(self.jac)
         st.u_hat, st.dudn_hat, st.packed = _ptr(self.u_hat), _ptr(self.dudn_hat), _ptr(self.packed)
         st.bnd_measure = 0.0
         self.struct = st

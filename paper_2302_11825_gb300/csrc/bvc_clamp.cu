@@ -6,10 +6,11 @@
 // crossing z of the ray x + t w with the sample surface gives the unbiased
 // term sign(n.w) (1 - c/|dG/dn(x, z)|) u(z) / n_dirs wherever |dG/dn| > c;
 // |dG/dn| = |n.w| / (2 pi t) (2D), |n.w| / (4 pi t^2) (3D), so rays stop at
-// t = 1/(2 pi c) or (4 pi c)^(-1/2).  The sample surface is a mesh whose
-// elements are moved by -l n_e (the cache's offset boundary; l = 0 for a
-// region's own boundary): the BVH's boxes are grown by l and each element is
-// tested at its moved position.  u at the crossings is estimated by walks on
+// t = 1/(2 pi c) or (4 pi c)^(-1/2).  The sample surface is the offset
+// boundary of a mesh at l (its vertices moved by -l m_v, Sec. 3.2: the
+// surface the cache's samples lie on; l = 0 for a region's own boundary):
+// the BVH's boxes are grown by l x max|m_v| and each element is tested at
+// its moved position.  u at the crossings is estimated by walks on
 // the domain (tag 5, walk id = crossing rank * walks + j, crossings ranked by
 // point, direction and distance); the crossings are compacted in that order
 // by a deterministic block scan.
@@ -27,7 +28,7 @@ constexpr int kRayStack = 48;
 
 struct RayParams {
   DevGeometry S;  // sample surface
-  float l;        // elements moved by -l n
+  float l;        // vertices moved by -l m_v
   const float* pts;
   int64_t m;
   int32_t n_dirs;
@@ -99,8 +100,8 @@ __global__ void __launch_bounds__(kRayBlock) k_rays(const RayParams R) {
         const float4 L = __ldg(&G.nodes[3 * node]), Rb = __ldg(&G.nodes[3 * node + 1]);
         const float4 Cc = __ldg(&G.nodes[3 * node + 2]);
         const float lo0[2] = {L.x, L.y}, hi0[2] = {L.z, L.w}, lo1[2] = {Rb.x, Rb.y}, hi1[2] = {Rb.z, Rb.w};
-        hit[0] = ray_box<2>(lo0, hi0, x, inv, R.l, R.rmax);
-        hit[1] = ray_box<2>(lo1, hi1, x, inv, R.l, R.rmax);
+        hit[0] = ray_box<2>(lo0, hi0, x, inv, R.l * G.reach, R.rmax);
+        hit[1] = ray_box<2>(lo1, hi1, x, inv, R.l * G.reach, R.rmax);
         ch[0] = __float_as_int(Cc.x);
         ch[1] = __float_as_int(Cc.y);
       } else {
@@ -108,8 +109,8 @@ __global__ void __launch_bounds__(kRayBlock) k_rays(const RayParams R) {
         const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
         const float lo0[3] = {a.x, a.y, a.z}, hi0[3] = {a.w, b.x, b.y};
         const float lo1[3] = {b.z, b.w, c.x}, hi1[3] = {c.y, c.z, c.w};
-        hit[0] = ray_box<3>(lo0, hi0, x, inv, R.l, R.rmax);
-        hit[1] = ray_box<3>(lo1, hi1, x, inv, R.l, R.rmax);
+        hit[0] = ray_box<3>(lo0, hi0, x, inv, R.l * G.reach, R.rmax);
+        hit[1] = ray_box<3>(lo1, hi1, x, inv, R.l * G.reach, R.rmax);
         ch[0] = __float_as_int(e.x);
         ch[1] = __float_as_int(e.y);
       }
@@ -124,10 +125,18 @@ __global__ void __launch_bounds__(kRayBlock) k_rays(const RayParams R) {
         for (int32_t pq = first; pq < first + count; ++pq) {
           float t = -1.0f, nw = 0.0f;
           if (D == 2) {
-            const float4 S = __ldg(&G.prims[2 * pq]);
+            float4 S = __ldg(&G.prims[2 * pq]);
+            if (R.l != 0.0f) {  // the moved segment: its vertices minus l m_v
+              const int32_t* f = G.idx + 2 * __float_as_int(__ldg(&G.prims[2 * pq + 1]).y);
+              const float a0 = G.verts[2 * f[0]] - R.l * (float)G.disp[2 * f[0]];
+              const float a1 = G.verts[2 * f[0] + 1] - R.l * (float)G.disp[2 * f[0] + 1];
+              const float b0 = G.verts[2 * f[1]] - R.l * (float)G.disp[2 * f[1]];
+              const float b1 = G.verts[2 * f[1] + 1] - R.l * (float)G.disp[2 * f[1] + 1];
+              S = make_float4(a0, a1, b0 - a0, b1 - a1);
+            }
             const float len = sqrtf(fmaf(S.w, S.w, S.z * S.z));
             const float nx = S.w / len, ny = -S.z / len;  // outward normal of a counter-clockwise polygon
-            const float ax = S.x - R.l * nx - x[0], ay = S.y - R.l * ny - x[1];
+            const float ax = S.x - x[0], ay = S.y - x[1];
             const float den = om[0] * S.w - om[D - 1] * S.z;
             if (den != 0.0f) {
               const float tt = (ax * S.w - ay * S.z) / den, ss = (ax * om[D - 1] - ay * om[0]) / den;
@@ -135,14 +144,25 @@ __global__ void __launch_bounds__(kRayBlock) k_rays(const RayParams R) {
             }
             nw = nx * om[0] + ny * om[D - 1];
           } else {
-            const float4 A = __ldg(&G.prims[3 * pq]), B = __ldg(&G.prims[3 * pq + 1]), Cq = __ldg(&G.prims[3 * pq + 2]);
+            float4 A = __ldg(&G.prims[3 * pq]), B = __ldg(&G.prims[3 * pq + 1]), Cq = __ldg(&G.prims[3 * pq + 2]);
+            if (R.l != 0.0f) {  // the moved triangle: its vertices minus l m_v
+              const int32_t* f = G.idx + 3 * __float_as_int(A.w);
+              float P[3][3];
+#pragma unroll
+              for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) P[k2][a] = G.verts[3 * f[k2] + a] - R.l * (float)G.disp[3 * f[k2] + a];
+              A = make_float4(P[0][0], P[0][1], P[0][2], A.w);
+              B = make_float4(P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2], 0.0f);
+              Cq = make_float4(P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2], 0.0f);
+            }
             const float e1[3] = {B.x, B.y, B.z}, e2[3] = {Cq.x, Cq.y, Cq.z};
             float n3[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
             const float nl = rsqrtf(fmaf(n3[2], n3[2], fmaf(n3[1], n3[1], n3[0] * n3[0])));
 #pragma unroll
             for (int a = 0; a < 3; ++a) n3[a] *= nl;
-            // Moller-Trumbore on the moved triangle
-            const float tv[3] = {x[0] - (A.x - R.l * n3[0]), x[1] - (A.y - R.l * n3[1]), x[D - 1] - (A.z - R.l * n3[2])};
+            // Moller-Trumbore on the (moved) triangle
+            const float tv[3] = {x[0] - A.x, x[1] - A.y, x[D - 1] - A.z};
             const float o3[3] = {om[0], om[1], om[D - 1]};
             const float pv[3] = {o3[1] * e2[2] - o3[2] * e2[1], o3[2] * e2[0] - o3[0] * e2[2],
                                  o3[0] * e2[1] - o3[1] * e2[0]};

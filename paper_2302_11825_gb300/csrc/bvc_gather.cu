@@ -386,9 +386,10 @@ __global__ void __launch_bounds__(256) k_pack_bnd(const bvc_cache C) {
   if (i >= C.n) return;
   const double two_pi = 6.283185307179586476925, four_pi = 12.566370614359172953850;
   float4* o = (float4*)C.packed + 5 * i;
+  const double ip = C.bnd_measure * (double)C.jac[i];  // 1/p of sample i
   if (D == 2) {
-    const double a = C.u_hat[i] * C.bnd_measure / two_pi;
-    const double b = C.dudn_hat[i] * C.bnd_measure / two_pi;
+    const double a = C.u_hat[i] * ip / two_pi;
+    const double b = C.dudn_hat[i] * ip / two_pi;
     const float zx = C.z[i], zy = C.z[C.n + i], nx = C.nrm[i], ny = C.nrm[C.n + i];
     const float fa = (float)a, fb = (float)b, a2 = (float)(2.0 * a), nbl = (float)(-b * 0.34657359027997265471);
     o[0] = make_float4(zx, zx, zy, zy);
@@ -397,8 +398,8 @@ __global__ void __launch_bounds__(256) k_pack_bnd(const bvc_cache C) {
     o[3] = make_float4(a2, a2, fb, fb);
     o[4] = make_float4(nbl, nbl, 0.0f, 0.0f);
   } else {
-    const double a = C.u_hat[i] * C.bnd_measure / four_pi;
-    const double b = C.dudn_hat[i] * C.bnd_measure / four_pi;
+    const double a = C.u_hat[i] * ip / four_pi;
+    const double b = C.dudn_hat[i] * ip / four_pi;
     const float zx = C.z[i], zy = C.z[C.n + i], zz = C.z[2 * C.n + i];
     const float nx = C.nrm[i], ny = C.nrm[C.n + i], nz = C.nrm[2 * C.n + i];
     const float fa = (float)a, fb = (float)b, a3 = (float)(3.0 * a);
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(256) k_pack_bnd_scr(const bvc_cache C) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= C.n) return;
   const double w = D == 2 ? 6.283185307179586476925 : 12.566370614359172953850;
-  const double ca = C.bnd_measure / w;
+  const double ca = C.bnd_measure * (double)C.jac[i] / w;
   float4* o = (float4*)C.packed + 2 * i;
   o[0] = make_float4(C.z[i], C.z[C.n + i], D == 3 ? C.z[2 * C.n + i] : 0.0f, (float)(C.u_hat[i] * ca));
   o[1] = make_float4(C.nrm[i], C.nrm[C.n + i], D == 3 ? C.nrm[2 * C.n + i] : 0.0f, (float)(C.dudn_hat[i] * ca));
@@ -631,7 +632,8 @@ extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) 
   if (cache == nullptr || (cache->dim != 2 && cache->dim != 3) || cache->n < 0) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (cache->n > 0) {
-    if (!cache->z || !cache->nrm || !cache->u_hat || !cache->dudn_hat || !cache->packed) return BVC_ERR_INVALID_ARG;
+    if (!cache->z || !cache->nrm || !cache->jac || !cache->u_hat || !cache->dudn_hat || !cache->packed)
+      return BVC_ERR_INVALID_ARG;
     const unsigned grid = (unsigned)((cache->n + 255) / 256);
     ProfScope ps("pack_boundary", s);
     if (cache->sigma > 0.0 || cache->clamp_c > 0.0) {
@@ -1048,9 +1050,9 @@ constexpr int kAS = 4;
 template <int D, bool SRC>
 __global__ void __launch_bounds__(256) k_gather_adj(const float4* __restrict__ pl, int64_t m,
                                                    const float* __restrict__ zs, const float* __restrict__ ns,
-                                                   int64_t stride, const int64_t* __restrict__ n_dev, int64_t n_fix,
-                                                   double s1, double s2, double* __restrict__ out1,
-                                                   double* __restrict__ out2) {
+                                                   const float* __restrict__ jw, int64_t stride,
+                                                   const int64_t* __restrict__ n_dev, int64_t n_fix, double s1,
+                                                   double s2, double* __restrict__ out1, double* __restrict__ out2) {
   __shared__ __align__(128) float4 tile[2][kATile];
   __shared__ __align__(8) uint64_t bar[2];
   const int64_t n = n_dev ? *n_dev : n_fix;
@@ -1145,8 +1147,9 @@ __global__ void __launch_bounds__(256) k_gather_adj(const float4* __restrict__ p
   for (int q = 0; q < kAS; ++q) {
     if (!live[q]) continue;
     const int64_t i = base + (int64_t)q * blockDim.x + threadIdx.x;
-    out1[i] = A1[q] * s1;
-    if (!SRC) out2[i] = A2[q] * s2;
+    const double wi = jw != nullptr ? (double)jw[i] : 1.0;  // per-sample 1/p factor
+    out1[i] = A1[q] * s1 * wi;
+    if (!SRC) out2[i] = A2[q] * s2 * wi;
   }
 }
 
@@ -1214,7 +1217,7 @@ extern "C" bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* 
                                            double* adj_u, double* adj_q, double* adj_src, void* workspace,
                                            size_t workspace_bytes, bvc_stream stream) {
   if (cache == nullptr || (cache->dim != 2 && cache->dim != 3) || cache->n < 1 || cache->z == nullptr ||
-      cache->nrm == nullptr || adj_u == nullptr || adj_q == nullptr || m < 0 ||
+      cache->nrm == nullptr || cache->jac == nullptr || adj_u == nullptr || adj_q == nullptr || m < 0 ||
       (m > 0 && (pts == nullptr || lam == nullptr || workspace == nullptr)))
     return BVC_ERR_INVALID_ARG;
   const bool src = adj_src != nullptr && cache->n_src_cand > 0;
@@ -1244,11 +1247,11 @@ extern "C" bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* 
     ProfScope ps("adjoint_gather_boundary", s);
     const unsigned grid = (unsigned)((cache->n + 256 * kAS - 1) / (256 * kAS));
     if (D == 2)
-      k_gather_adj<2, false><<<grid, 256, 0, s>>>(pl, m, cache->z, cache->nrm, cache->n, nullptr, cache->n, ca / N,
-                                                  cb / N, adj_u, adj_q);
+      k_gather_adj<2, false><<<grid, 256, 0, s>>>(pl, m, cache->z, cache->nrm, cache->jac, cache->n, nullptr, cache->n,
+                                                  ca / N, cb / N, adj_u, adj_q);
     else
-      k_gather_adj<3, false><<<grid, 256, 0, s>>>(pl, m, cache->z, cache->nrm, cache->n, nullptr, cache->n, ca / N,
-                                                  cb / N, adj_u, adj_q);
+      k_gather_adj<3, false><<<grid, 256, 0, s>>>(pl, m, cache->z, cache->nrm, cache->jac, cache->n, nullptr, cache->n,
+                                                  ca / N, cb / N, adj_u, adj_q);
     BVC_LAUNCH_CHECK();
   }
   if (src) {
@@ -1259,10 +1262,10 @@ extern "C" bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* 
     ProfScope ps("adjoint_gather_source", s);
     const unsigned grid = (unsigned)((nc + 256 * kAS - 1) / (256 * kAS));
     if (D == 2)
-      k_gather_adj<2, true><<<grid, 256, 0, s>>>(pl, m, cache->src_y, nullptr, nc, cache->n_src_dev, nc,
+      k_gather_adj<2, true><<<grid, 256, 0, s>>>(pl, m, cache->src_y, nullptr, nullptr, nc, cache->n_src_dev, nc,
                                                  cs / (double)nc, 0.0, adj_src, nullptr);
     else
-      k_gather_adj<3, true><<<grid, 256, 0, s>>>(pl, m, cache->src_y, nullptr, nc, cache->n_src_dev, nc,
+      k_gather_adj<3, true><<<grid, 256, 0, s>>>(pl, m, cache->src_y, nullptr, nullptr, nc, cache->n_src_dev, nc,
                                                  cs / (double)nc, 0.0, adj_src, nullptr);
     BVC_LAUNCH_CHECK();
   }

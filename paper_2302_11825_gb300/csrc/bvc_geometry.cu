@@ -33,6 +33,110 @@ static double elem_measure(int dim, const float* V, const int32_t* f) {
   return 0.5 * std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
 }
 
+// Outward unit normal of element f (FP64, the operation order of
+// elem_measure).
+static void elem_normal(int dim, const float* V, const int32_t* f, double* n) {
+  if (dim == 2) {
+    const double ax = V[2 * f[0]], ay = V[2 * f[0] + 1], bx = V[2 * f[1]], by = V[2 * f[1] + 1];
+    const double dx = bx - ax, dy = by - ay;
+    const double len = std::sqrt(dx * dx + dy * dy);
+    n[0] = dy / len;
+    n[1] = -dx / len;
+    return;
+  }
+  double e1[3], e2[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = (double)V[3 * f[1] + a] - (double)V[3 * f[0] + a];
+    e2[a] = (double)V[3 * f[2] + a] - (double)V[3 * f[0] + a];
+  }
+  const double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  const double len = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  for (int a = 0; a < 3; ++a) n[a] = c[a] / len;
+}
+
+// The offset boundary of Sec. 3.2 (the samples of the cache bound a closed
+// region about l inside the domain): vertex v moves to v - l m_v.  2D: for a
+// vertex between two moved segments, S = na + nb and m = S / max(|S|^2 / 2,
+// 1/4) -- |S|^2 / 2 = 1 + na.nb, the miter, which keeps both moved segments
+// parallel to theirs at distance l; for any other count, S / |S|.  3D: the
+// angle-weighted normal (each triangle's unit normal times its angle at v,
+// summed, normalised) N^, and m = N^ / max(min_f n_f . N^, 1/4), so every
+// moved triangle's plane moves inward by at least l at v.
+double offset_disp(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const uint8_t* fixed,
+                   double* m) {
+  std::vector<int32_t> cnt((size_t)nv, 0);
+  std::vector<double> S((size_t)nv * dim, 0.0);
+  for (int64_t i = 0; i < nv * dim; ++i) m[i] = 0.0;
+  for (int64_t e = 0; e < np; ++e) {
+    if (fixed != nullptr && fixed[e] != 0) continue;
+    const int32_t* f = F + e * dim;
+    double n[3];
+    elem_normal(dim, V, f, n);
+    if (dim == 2) {
+      for (int k = 0; k < 2; ++k) {
+        S[2 * (size_t)f[k]] += n[0];
+        S[2 * (size_t)f[k] + 1] += n[1];
+        cnt[f[k]] += 1;
+      }
+    } else {
+      for (int k = 0; k < 3; ++k) {
+        double p[3], q[3];
+        for (int a = 0; a < 3; ++a) {
+          p[a] = (double)V[3 * f[(k + 1) % 3] + a] - (double)V[3 * f[k] + a];
+          q[a] = (double)V[3 * f[(k + 2) % 3] + a] - (double)V[3 * f[k] + a];
+        }
+        const double x[3] = {p[1] * q[2] - p[2] * q[1], p[2] * q[0] - p[0] * q[2], p[0] * q[1] - p[1] * q[0]};
+        const double th =
+            std::atan2(std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]), p[0] * q[0] + p[1] * q[1] + p[2] * q[2]);
+        for (int a = 0; a < 3; ++a) S[3 * (size_t)f[k] + a] += th * n[a];
+        cnt[f[k]] += 1;
+      }
+    }
+  }
+  if (dim == 2) {
+    for (int64_t v = 0; v < nv; ++v) {
+      const double s0 = S[2 * v], s1 = S[2 * v + 1];
+      const double q = s0 * s0 + s1 * s1;
+      if (cnt[v] == 0 || !(q > 0.0)) continue;
+      const double den = cnt[v] == 2 ? std::fmax(0.5 * q, 0.25) : std::sqrt(q);
+      m[2 * v] = s0 / den;
+      m[2 * v + 1] = s1 / den;
+    }
+  } else {
+    std::vector<double> cmin((size_t)nv, 2.0);
+    for (int64_t v = 0; v < nv; ++v) {
+      const double q = std::sqrt(S[3 * v] * S[3 * v] + S[3 * v + 1] * S[3 * v + 1] + S[3 * v + 2] * S[3 * v + 2]);
+      if (q > 0.0)
+        for (int a = 0; a < 3; ++a) S[3 * v + a] = S[3 * v + a] / q;
+      else
+        cnt[v] = 0;
+    }
+    for (int64_t e = 0; e < np; ++e) {
+      if (fixed != nullptr && fixed[e] != 0) continue;
+      const int32_t* f = F + e * 3;
+      double n[3];
+      elem_normal(3, V, f, n);
+      for (int k = 0; k < 3; ++k) {
+        const double* Nv = S.data() + 3 * (size_t)f[k];
+        const double c = n[0] * Nv[0] + n[1] * Nv[1] + n[2] * Nv[2];
+        if (c < cmin[f[k]]) cmin[f[k]] = c;
+      }
+    }
+    for (int64_t v = 0; v < nv; ++v) {
+      if (cnt[v] == 0) continue;
+      const double den = std::fmax(cmin[v], 0.25);
+      for (int a = 0; a < 3; ++a) m[3 * v + a] = S[3 * v + a] / den;
+    }
+  }
+  double reach = 0.0;
+  for (int64_t v = 0; v < nv; ++v) {
+    double q = 0.0;
+    for (int a = 0; a < dim; ++a) q += m[dim * v + a] * m[dim * v + a];
+    if (std::sqrt(q) > reach) reach = std::sqrt(q);
+  }
+  return reach;
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // ---------------------------------------------------------------- kernels
@@ -59,15 +163,19 @@ __global__ void __launch_bounds__(128) k_query_closest(DevGeometry G, const floa
   }
 }
 
-// K1: stratified boundary samples through the FP64 measure CDF, offset by
-// -l n.  The FP64 operations use explicit round-to-nearest intrinsics (no
-// contraction), in the same order as the host's measure computation.
+// K1: stratified boundary samples through the FP64 measure CDF, placed on
+// the offset boundary (Sec. 3.2): the element's vertices moved by -l m_v
+// (disp), the sample at the same element coordinates on the moved element,
+// its normal the moved element's, jac = |moved element| / |element|.  The
+// FP64 operations use explicit round-to-nearest intrinsics (no contraction),
+// in the order of the host's measure computation.
 template <int D>
 __global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t n, double l, uint64_t seed,
                                                          float* __restrict__ z, float* __restrict__ nrm,
-                                                         int32_t* __restrict__ elem, int64_t stride,
-                                                         const uint64_t* __restrict__ seed_dev,
-                                                         const uint8_t* __restrict__ zero_l) {
+                                                         float* __restrict__ jac, int32_t* __restrict__ elem,
+                                                         int64_t stride, const uint64_t* __restrict__ seed_dev,
+                                                         const uint8_t* __restrict__ zero_l,
+                                                         const double* __restrict__ disp) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const U4 r = philox_draw(seed_dev ? *seed_dev : seed, (uint64_t)i, 0u, 1u);
@@ -86,43 +194,60 @@ __global__ void __launch_bounds__(256) k_sample_boundary(DevGeometry G, int64_t 
   }
   const int64_t e = lo;
   const int32_t* f = G.idx + e * D;
-  double p[3], nn[3];
+  // a mixed boundary's Neumann samples stay on the boundary (Sec. 3.2)
+  const double le = (zero_l != nullptr && zero_l[e] != 0) ? 0.0 : l;
+  double P[3][3];
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      P[k][a] = __dsub_rn((double)G.verts[D * f[k] + a], __dmul_rn(le, disp[D * (int64_t)f[k] + a]));
+  double p[3], nn[3], ratio;
   if (D == 2) {
     const double ax = G.verts[2 * f[0]], ay = G.verts[2 * f[0] + 1];
     const double bx = G.verts[2 * f[1]], by = G.verts[2 * f[1] + 1];
     const double dx = __dsub_rn(bx, ax), dy = __dsub_rn(by, ay);
     const double len = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-    nn[0] = __ddiv_rn(dy, len);
-    nn[1] = __ddiv_rn(-dx, len);
+    const double mx = __dsub_rn(P[1][0], P[0][0]), my = __dsub_rn(P[1][1], P[0][1]);
+    const double lm = __dsqrt_rn(__dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my)));
+    nn[0] = __ddiv_rn(my, lm);
+    nn[1] = __ddiv_rn(-mx, lm);
     double lam = __ddiv_rn(__dsub_rn(t, G.cdf[e]), len);
     lam = fmin(fmax(lam, 0.0), 1.0);
-    p[0] = __dadd_rn(ax, __dmul_rn(lam, dx));
-    p[1] = __dadd_rn(ay, __dmul_rn(lam, dy));
+    p[0] = __dadd_rn(P[0][0], __dmul_rn(lam, mx));
+    p[1] = __dadd_rn(P[0][1], __dmul_rn(lam, my));
+    ratio = __ddiv_rn(lm, len);
   } else {
-    double v0[3], e1[3], e2[3];
+    double e1[3], e2[3], m1[3], m2[3];
     for (int a = 0; a < 3; ++a) {
-      v0[a] = G.verts[3 * f[0] + a];
-      e1[a] = __dsub_rn((double)G.verts[3 * f[1] + a], v0[a]);
-      e2[a] = __dsub_rn((double)G.verts[3 * f[2] + a], v0[a]);
+      const double v0 = G.verts[3 * f[0] + a];
+      e1[a] = __dsub_rn((double)G.verts[3 * f[1] + a], v0);
+      e2[a] = __dsub_rn((double)G.verts[3 * f[2] + a], v0);
+      m1[a] = __dsub_rn(P[1][a], P[0][a]);
+      m2[a] = __dsub_rn(P[2][a], P[0][a]);
     }
     const double c0 = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
     const double c1 = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
     const double c2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
     const double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2)));
-    nn[0] = __ddiv_rn(c0, len);
-    nn[1] = __ddiv_rn(c1, len);
-    nn[2] = __ddiv_rn(c2, len);
+    const double d0 = __dsub_rn(__dmul_rn(m1[1], m2[2]), __dmul_rn(m1[2], m2[1]));
+    const double d1 = __dsub_rn(__dmul_rn(m1[2], m2[0]), __dmul_rn(m1[0], m2[2]));
+    const double d2 = __dsub_rn(__dmul_rn(m1[0], m2[1]), __dmul_rn(m1[1], m2[0]));
+    const double lm = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
+    nn[0] = __ddiv_rn(d0, lm);
+    nn[1] = __ddiv_rn(d1, lm);
+    nn[2] = __ddiv_rn(d2, lm);
     const double sq = __dsqrt_rn(u1);
     const double b1 = __dmul_rn(sq, __dsub_rn(1.0, u2)), b2 = __dmul_rn(sq, u2);
-    for (int a = 0; a < 3; ++a) p[a] = __dadd_rn(__dadd_rn(v0[a], __dmul_rn(b1, e1[a])), __dmul_rn(b2, e2[a]));
+    for (int a = 0; a < 3; ++a) p[a] = __dadd_rn(__dadd_rn(P[0][a], __dmul_rn(b1, m1[a])), __dmul_rn(b2, m2[a]));
+    ratio = __ddiv_rn(__dmul_rn(0.5, lm), __dmul_rn(0.5, len));
   }
-  // a mixed boundary's Neumann samples stay on the boundary (Sec. 3.2)
-  const double le = (zero_l != nullptr && zero_l[e] != 0) ? 0.0 : l;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    z[a * stride + i] = __double2float_rn(__dsub_rn(p[a], __dmul_rn(le, nn[a])));
+    z[a * stride + i] = __double2float_rn(p[a]);
     nrm[a * stride + i] = __double2float_rn(nn[a]);
   }
+  jac[i] = __double2float_rn(ratio);
   if (elem) elem[i] = (int32_t)e;
 }
 
@@ -163,6 +288,8 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   std::vector<float4> nodes, pr;
   std::vector<int32_t> ids;
   const int64_t n_nodes = build_bvh(dim, verts, prims, n_prims, nodes, pr, ids);
+  std::vector<double> disp((size_t)n_verts * dim);
+  const double reach = offset_disp(dim, verts, n_verts, prims, n_prims, nullptr, disp.data());
 
   bvc_geometry g = new bvc_geometry_s();
   g->dim = dim;
@@ -170,6 +297,7 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   g->n_prims = n_prims;
   g->n_nodes = n_nodes;
   g->measure = cdf[n_prims];
+  g->reach = reach;
   for (int a = 0; a < 3; ++a) {
     g->lo[a] = a < dim ? INFINITY : 0.0f;
     g->hi[a] = a < dim ? -INFINITY : 0.0f;
@@ -188,8 +316,9 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   const size_t b_cdf = align256(cdf.size() * sizeof(double));
   const size_t b_verts = align256((size_t)n_verts * dim * sizeof(float));
   const size_t b_idx = align256((size_t)n_prims * dim * sizeof(int32_t));
+  const size_t b_disp = align256(disp.size() * sizeof(double));
   const size_t b_stats = 256;
-  g->arena_bytes = b_nodes + b_prims + b_cdf + b_verts + b_idx + b_stats;
+  g->arena_bytes = b_nodes + b_prims + b_cdf + b_verts + b_idx + b_disp + b_stats;
   if (cudaMalloc(&g->arena, g->arena_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     delete g;
@@ -202,10 +331,12 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   d.cdf = (const double*)(base += b_prims);
   d.verts = (const float*)(base += b_cdf);
   d.idx = (const int32_t*)(base += b_verts);
-  d.stats = (unsigned long long*)(base += b_idx);
+  d.disp = (const double*)(base += b_idx);
+  d.stats = (unsigned long long*)(base += b_disp);
   d.n_prims = n_prims;
   d.n_verts = n_verts;
   d.tau = (float)(std::ldexp(1.0, -18) * (diag > 0 ? diag : 1.0));
+  d.reach = std::nextafter((float)reach, INFINITY);
   for (int a = 0; a < 3; ++a) {
     d.lo[a] = g->lo[a];
     d.hi[a] = g->hi[a];
@@ -220,6 +351,7 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
                 cudaSuccess &&
             cudaMemcpyAsync((void*)d.idx, prims, (size_t)n_prims * dim * 4, cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
+            cudaMemcpyAsync((void*)d.disp, disp.data(), disp.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
             cudaMemsetAsync(d.stats, 0, b_stats, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();
@@ -250,6 +382,7 @@ extern "C" bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* i
     info->bbox_hi[a] = g->hi[a];
   }
   info->device_bytes = g->arena_bytes;
+  info->offset_reach = g->reach;
   return BVC_OK;
 }
 
@@ -293,11 +426,14 @@ extern "C" bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_
   if (m == 0) return BVC_OK;
   const int grid = grid_for(m, 128);
   ProfScope ps("classify_near", (cudaStream_t)stream);
+  // every point of the strip between the boundary and the offset boundary
+  // at l lies within l x reach of the boundary
+  const float lr = l * g->dev.reach;
   if (g->dim == 2)
-    k_query_closest<2><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, nullptr, nullptr, nullptr, l * l,
+    k_query_closest<2><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, nullptr, nullptr, nullptr, lr * lr,
                                                               near);
   else
-    k_query_closest<3><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, nullptr, nullptr, nullptr, l * l,
+    k_query_closest<3><<<grid, 128, 0, (cudaStream_t)stream>>>(g->dev, pts, m, nullptr, nullptr, nullptr, lr * lr,
                                                               near);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
@@ -307,23 +443,24 @@ namespace bvc {
 // K1 into planes of `stride` floats (a batch writes each mesh's samples into
 // its range of the batch's sample planes).
 bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
-                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev,
-                                  const uint8_t* zero_l) {
+                                  float* jac, int32_t* elem, int64_t stride, cudaStream_t s,
+                                  const uint64_t* seed_dev, const uint8_t* zero_l, const double* disp) {
   if (n == 0) return BVC_OK;
   const int grid = (int)((n + 255) / 256);
+  const double* dp = disp != nullptr ? disp : g->dev.disp;
   ProfScope ps("sample_boundary", s);
   if (g->dim == 2)
-    k_sample_boundary<2><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev, zero_l);
+    k_sample_boundary<2><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, jac, elem, stride, seed_dev, zero_l, dp);
   else
-    k_sample_boundary<3><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, elem, stride, seed_dev, zero_l);
+    k_sample_boundary<3><<<grid, 256, 0, s>>>(g->dev, n, l, seed, z, nrm, jac, elem, stride, seed_dev, zero_l, dp);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
 }  // namespace bvc
 
 extern "C" bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
-                                          int32_t* elem, bvc_stream stream) {
-  if (g == nullptr || n < 0 || (n > 0 && (z == nullptr || nrm == nullptr)) || !std::isfinite(l))
+                                          float* jac, int32_t* elem, bvc_stream stream) {
+  if (g == nullptr || n < 0 || (n > 0 && (z == nullptr || nrm == nullptr || jac == nullptr)) || !std::isfinite(l))
     return BVC_ERR_INVALID_ARG;
-  return launch_sample_boundary(g, n, l, seed, z, nrm, elem, n, (cudaStream_t)stream, nullptr);
+  return launch_sample_boundary(g, n, l, seed, z, nrm, jac, elem, n, (cudaStream_t)stream, nullptr);
 }

@@ -38,9 +38,11 @@ struct DevGeometry {
   const double* cdf;      // [n_prims + 1] FP64 prefix sums of element measures (caller order)
   const float* verts;     // [n_verts][dim] caller's vertices
   const int32_t* idx;     // [n_prims][dim] caller's element indices
+  const double* disp;     // [n_verts][dim] offset-boundary displacements m_v (Sec. 3.2)
   unsigned long long* stats;  // [4] status block
   int64_t n_prims, n_verts;
   float tau;              // traversal slack, 2^-18 x bbox diagonal
+  float reach;            // max_v |m_v| (FP32, rounded up)
   float lo[3], hi[3];     // bbox
 };
 
@@ -78,6 +80,7 @@ struct bvc_geometry_s {
   int32_t dim;
   int64_t n_verts, n_prims, n_nodes;
   double measure;
+  double reach;           // max_v |m_v| of the offset boundary's displacements
   float lo[3], hi[3];
   void* arena;            // one device allocation holding everything below
   size_t arena_bytes;
@@ -89,6 +92,16 @@ struct bvc_geometry_s {
 };
 
 namespace bvc {
+
+// Offset boundary (Sec. 3.2): per-vertex displacements m_v [n_verts][dim] of
+// the closed surface v -> v - l m_v, from the unit normals of the elements
+// at v that are moved (fixed[e] != 0: element e is not moved; may be NULL).
+// 2D: k = 2 moved segments, S = na + nb: m = S / max(|S|^2 / 2, 1/4) (the
+// miter); other k >= 1: S / |S|.  3D: angle-weighted normal N^, m = N^ /
+// max(min_f n_f . N^, 1/4).  FP64 with a fixed operation order.  Returns
+// max_v |m_v|.  (bvc_geometry.cu)
+double offset_disp(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const uint8_t* fixed,
+                   double* m);
 
 // Host helpers (bvc_common.cu)
 bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);
@@ -109,10 +122,13 @@ bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc
 // seed_dev: when non-null, the seed is read from this device word at run
 // time (a captured CUDA graph replays with the seed it holds then).
 // zero_l: when non-null, samples on elements e with zero_l[e] != 0 keep
-// offset 0 (the Neumann part of a mixed boundary).
+// offset 0 (the Neumann part of a mixed boundary).  disp: displacement table
+// of the offset boundary (device double[n_verts][dim]); null = the
+// geometry's own.  jac: device float[n] (plane of one float per sample).
 bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
-                                  int32_t* elem, int64_t stride, cudaStream_t s, const uint64_t* seed_dev,
-                                  const uint8_t* zero_l = nullptr);
+                                  float* jac, int32_t* elem, int64_t stride, cudaStream_t s,
+                                  const uint64_t* seed_dev, const uint8_t* zero_l = nullptr,
+                                  const double* disp = nullptr);
 // Per-start FP64 reduction of walk records (K3).
 struct ReduceParams {
   const float* rec;

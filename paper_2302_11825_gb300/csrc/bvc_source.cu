@@ -1,7 +1,9 @@
 // bvc_source.cu -- source samples (K4): jittered candidates over the
 // bounding box, kept by the canonical FP32 crossing test (2D) or a winding
-// number above 1/2 (3D), compacted in candidate order by a deterministic
-// block scan.
+// number above 1/2 (3D) against the offset boundary (the mesh with its
+// vertices moved to fl32(v - l m_v), Sec. 3.2: the region the cache's
+// integral equation refers to), compacted in candidate order by a
+// deterministic block scan.
 #include <algorithm>
 #include <cmath>
 
@@ -15,6 +17,7 @@ constexpr int kSegTile = 1024;
 
 struct SrcParams {
   DevGeometry G;
+  double l;           // offset of the region's boundary (0: the mesh itself)
   DevFunction f;
   int32_t G0, G1, G2;
   uint64_t seed;
@@ -31,6 +34,11 @@ struct SrcParams {
   int64_t* n_src;     // [1]
   int64_t nblocks;
 };
+
+// Coordinate k of the offset boundary's vertex list: fl32(v - l m) in FP64.
+__device__ __forceinline__ float moved_vertex(const SrcParams& S, int64_t k) {
+  return S.l == 0.0 ? S.G.verts[k] : __double2float_rn(__dsub_rn((double)S.G.verts[k], __dmul_rn(S.l, S.G.disp[k])));
+}
 
 // Candidate position (FP64, rounded to FP32) and the crossing-number test
 // against every segment, staged through shared memory.
@@ -54,7 +62,8 @@ __global__ void __launch_bounds__(kSrcBlock) k_src_classify(const SrcParams S) {
     __syncthreads();
     for (int q = threadIdx.x; q < kSegTile && base + q < np; q += kSrcBlock) {
       const int32_t* f = S.G.idx + 2 * (base + q);
-      seg[q] = make_float4(S.G.verts[2 * f[0]], S.G.verts[2 * f[0] + 1], S.G.verts[2 * f[1]], S.G.verts[2 * f[1] + 1]);
+      seg[q] = make_float4(moved_vertex(S, 2 * f[0]), moved_vertex(S, 2 * f[0] + 1), moved_vertex(S, 2 * f[1]),
+                           moved_vertex(S, 2 * f[1] + 1));
     }
     __syncthreads();
     const int cnt = (int)min64(kSegTile, np - base);
@@ -153,7 +162,8 @@ __global__ void __launch_bounds__(kSrcBlock) k_src_classify3d(const SrcParams S)
       const int32_t* f = S.G.idx + 3 * (base + q);
 #pragma unroll
       for (int v = 0; v < 3; ++v)
-        tri[v][q] = make_float4(S.G.verts[3 * f[v]], S.G.verts[3 * f[v] + 1], S.G.verts[3 * f[v] + 2], 0.0f);
+        tri[v][q] = make_float4(moved_vertex(S, 3 * f[v]), moved_vertex(S, 3 * f[v] + 1),
+                                moved_vertex(S, 3 * f[v] + 2), 0.0f);
     }
     __syncthreads();
     const int cnt = (int)min64(kTriTile, np - base);
@@ -335,9 +345,10 @@ extern "C" bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* b
 }
 
 extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[3], uint64_t seed,
-                                        bvc_cache* cache, void* workspace, size_t workspace_bytes,
+                                        double offset_l, bvc_cache* cache, void* workspace, size_t workspace_bytes,
                                         bvc_stream stream) {
-  if (g == nullptr || grid == nullptr || cache == nullptr) return BVC_ERR_INVALID_ARG;
+  if (g == nullptr || grid == nullptr || cache == nullptr || !std::isfinite(offset_l) || offset_l < 0.0)
+    return BVC_ERR_INVALID_ARG;
   const int D = g->dim;
   const int64_t ncand = (int64_t)grid[0] * grid[1] * (D == 3 ? grid[2] : 1);
   if (grid[0] < 1 || grid[1] < 1 || (D == 3 && grid[2] < 1) || ncand != cache->n_src_cand ||
@@ -348,6 +359,7 @@ extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn,
   if (workspace_bytes < need) return BVC_ERR_WORKSPACE;
   SrcParams S{};
   S.G = g->dev;
+  S.l = offset_l;
   if (!make_dev_function(ffn, D, &S.f)) return BVC_ERR_INVALID_ARG;
   S.G0 = grid[0];
   S.G1 = grid[1];

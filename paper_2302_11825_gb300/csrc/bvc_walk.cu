@@ -709,7 +709,8 @@ static bvc_status cache_build(bvc_geometry g, bvc_geometry gs, const bvc_functio
   const int64_t N = opts->n_samples;
   const int32_t W = opts->walks_per_sample;
   if (cache->dim != D || cache->n != N || N < 1 || !valid_walk_args((float)opts->eps, opts->max_steps, W) ||
-      !(gs == g ? opts->offset_l > 0.0 : opts->offset_l >= 0.0) || cache->z == nullptr || cache->nrm == nullptr || cache->u_hat == nullptr ||
+      !(gs == g ? opts->offset_l > 0.0 : opts->offset_l >= 0.0) || cache->z == nullptr || cache->nrm == nullptr ||
+      cache->jac == nullptr || cache->u_hat == nullptr ||
       cache->dudn_hat == nullptr || cache->packed == nullptr || workspace == nullptr)
     return BVC_ERR_INVALID_ARG;
   const int64_t ncand = src_candidates(opts, D);
@@ -733,7 +734,8 @@ static bvc_status cache_build(bvc_geometry g, bvc_geometry gs, const bvc_functio
   if (chunk > N) chunk = N;
   cudaStream_t s = (cudaStream_t)stream;
   cache->bnd_measure = gs->measure;
-  bvc_status st = bvc_sample_boundary(gs, N, opts->offset_l, opts->seed, cache->z, cache->nrm, nullptr, stream);
+  bvc_status st =
+      bvc_sample_boundary(gs, N, opts->offset_l, opts->seed, cache->z, cache->nrm, cache->jac, nullptr, stream);
   if (st != BVC_OK) return st;
   P.starts = cache->z;
   P.nrm = cache->nrm;
@@ -770,8 +772,8 @@ static bvc_status cache_build(bvc_geometry g, bvc_geometry gs, const bvc_functio
   }
   if (ncand > 0) {
     st = opts->reuse_sources ? bvc_source_reweight(gs, ffn, cache, s)
-                             : bvc_sample_source(gs, ffn, opts->src_grid, opts->seed, cache, workspace, workspace_bytes,
-                                                 stream);
+                             : bvc_sample_source(gs, ffn, opts->src_grid, opts->seed, opts->offset_l, cache, workspace,
+                                                 workspace_bytes, stream);
     if (st != BVC_OK) return st;
   }
   return bvc_cache_pack(cache, stream);
@@ -930,7 +932,7 @@ extern "C" bvc_status bvc_tune_walks_workspace_size(bvc_geometry g, const bvc_ca
   if (g == nullptr || opts == nullptr || bytes == nullptr || opts->n_samples < 1 || opts->walks_per_sample < 1)
     return BVC_ERR_INVALID_ARG;
   const int64_t n = tune_samples(opts);
-  const size_t pts = (((size_t)n * 2 * g->dim * sizeof(float)) + 255) & ~size_t(255);
+  const size_t pts = (((size_t)n * (2 * g->dim + 1) * sizeof(float)) + 255) & ~size_t(255);
   *bytes = pts + 2 * kWsHead + ws_per_start(g->dim, opts->walks_per_sample, 1) * (size_t)n;
   return BVC_OK;
 }
@@ -957,8 +959,9 @@ extern "C" bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, co
   cudaStream_t s = (cudaStream_t)stream;
   float* z = (float*)workspace;
   float* nrm = z + (size_t)D * n;
-  void* ws = (char*)workspace + ((((size_t)n * 2 * D * sizeof(float)) + 255) & ~size_t(255));
-  st = launch_sample_boundary(g, n, opts->offset_l, opts->seed, z, nrm, nullptr, n, s, nullptr);
+  float* jac = nrm + (size_t)D * n;
+  void* ws = (char*)workspace + ((((size_t)n * (2 * D + 1) * sizeof(float)) + 255) & ~size_t(255));
+  st = launch_sample_boundary(g, n, opts->offset_l, opts->seed, z, nrm, jac, nullptr, n, s, nullptr);
   if (st != BVC_OK) return st;
   WalkParams P{};
   P.G = g->dev;
@@ -1287,13 +1290,15 @@ __global__ void __launch_bounds__(256) k_moments(const float* __restrict__ rec, 
 // Per sample: u^_k, du/dn^_k for every right-hand side (FP64) and the
 // gather tiles, grouped by BVC_MULTI_GROUP right-hand sides:
 // [group][sample][8 + 2 G] floats = z (4), n (4), a_k (G), b_k (G) with
-//   2D  a = u^ |dOmega|/(2 pi),  b = -du/dn^ |dOmega|/(2 pi) ln2/2   (u += a (n.d)/r^2 + b lg2 r^2)
-//   3D  a = u^ |dOmega|/(4 pi),  b = du/dn^ |dOmega|/(4 pi)          (u += a (n.d)/r^3 + b/r)
+// 1/p = |dOmega| jac (the sample's offset element, Sec. 3.2) and
+//   2D  a = u^ /(2 pi p),  b = -du/dn^ /(2 pi p) ln2/2   (u += a (n.d)/r^2 + b lg2 r^2)
+//   3D  a = u^ /(4 pi p),  b = du/dn^ /(4 pi p)          (u += a (n.d)/r^3 + b/r)
 template <int D>
 __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, int32_t K, int64_t n,
                                                  const double* __restrict__ mom_u, const double* __restrict__ mom_q,
                                                  const float* __restrict__ z, const float* __restrict__ nrm,
-                                                 double meas, double* __restrict__ u_hat,
+                                                 const float* __restrict__ jac, double meas,
+                                                 double* __restrict__ u_hat,
                                                  double* __restrict__ q_hat, float* __restrict__ packed,
                                                  const int32_t* __restrict__ sample_mesh,
                                                  const BatchMeshDev* __restrict__ meshes) {
@@ -1314,7 +1319,8 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
     meas = meshes[msh].measure;
   }
   const int groups = (K + G - 1) / G;
-  const double ca = D == 2 ? meas / 6.283185307179586476925 : meas / 12.566370614359172953850;
+  const double ip = meas * (double)jac[i];
+  const double ca = D == 2 ? ip / 6.283185307179586476925 : ip / 12.566370614359172953850;
   const double cb = D == 2 ? -ca * 0.34657359027997265471 : ca;
   for (int g = 0; g < groups; ++g) {
     float* row = packed + ((int64_t)g * n + i) * S;
@@ -1344,7 +1350,7 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
 }  // namespace bvc
 
 static bool valid_multi(const bvc_multi_cache* c, int dim) {
-  return c != nullptr && c->dim == dim && c->n >= 1 && c->k >= 1 && c->z && c->nrm && c->mom_u && c->mom_q &&
+  return c != nullptr && c->dim == dim && c->n >= 1 && c->k >= 1 && c->z && c->nrm && c->jac && c->mom_u && c->mom_q &&
          c->u_hat && c->dudn_hat && c->packed;
 }
 
@@ -1353,11 +1359,11 @@ static bvc_status launch_project(const double* coeffs, bvc_multi_cache* c, cudaS
   const unsigned grid = (unsigned)((c->n + 127) / 128);
   ProfScope ps("multi_project", s);
   if (c->dim == 2)
-    k_project<2><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->bnd_measure, c->u_hat,
-                                      c->dudn_hat, c->packed, sample_mesh, meshes);
+    k_project<2><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->jac, c->bnd_measure,
+                                      c->u_hat, c->dudn_hat, c->packed, sample_mesh, meshes);
   else
-    k_project<3><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->bnd_measure, c->u_hat,
-                                      c->dudn_hat, c->packed, sample_mesh, meshes);
+    k_project<3><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->jac, c->bnd_measure,
+                                      c->u_hat, c->dudn_hat, c->packed, sample_mesh, meshes);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -1449,7 +1455,8 @@ extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs
   if (chunk > N) chunk = N;
   cudaStream_t s = (cudaStream_t)stream;
   cache->bnd_measure = g->measure;
-  bvc_status st = bvc_sample_boundary(g, N, opts->offset_l, opts->seed, cache->z, cache->nrm, nullptr, stream);
+  bvc_status st =
+      bvc_sample_boundary(g, N, opts->offset_l, opts->seed, cache->z, cache->nrm, cache->jac, nullptr, stream);
   if (st != BVC_OK) return st;
   EndWalks E{};
   E.G = g->dev;
@@ -1499,8 +1506,9 @@ extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, const u
   cache->bnd_measure = 0.0;
   for (int j = 0; j < b->count; ++j) {
     const BatchMeshDev& m = b->mesh[j];
-    const bvc_status st = launch_sample_boundary(b->geoms[j], m.n_smp, b->offset_l[j], 0, cache->z + m.smp_off,
-                                                 cache->nrm + m.smp_off, nullptr, b->n_total, s, seed);
+    const bvc_status st =
+        launch_sample_boundary(b->geoms[j], m.n_smp, b->offset_l[j], 0, cache->z + m.smp_off, cache->nrm + m.smp_off,
+                               cache->jac + m.smp_off, nullptr, b->n_total, s, seed);
     if (st != BVC_OK) return st;
   }
   EndWalks E{};

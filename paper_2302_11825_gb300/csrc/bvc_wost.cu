@@ -93,6 +93,7 @@ struct bvc_mixed_s {
   const int32_t* dir_ids;    // Dirichlet element -> whole element
   const int32_t* neu_local;  // whole element -> Neumann element or -1
   const uint8_t* flags;      // whole element: 1 Neumann
+  const double* disp;        // [n_verts][dim] offset displacements from the Dirichlet elements (Sec. 3.2)
   const float2* nmeas;       // Neumann tree: (left, right) subtree measures per node
   const int32_t* neu_q;      // Neumann element -> tree position
 };
@@ -1303,7 +1304,15 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   const size_t b_dir = al256((size_t)nd * 4), b_loc = al256((size_t)n_prims * 4), b_flag = al256((size_t)n_prims);
   const size_t b_nm = al256(nmeas.size() * sizeof(float2)), b_nq = al256(nq.size() * 4);
   const size_t b_cone = al256(scones.size() * sizeof(float4));
-  m->arena_bytes = b_nodes + b_prims + b_dir + b_loc + b_flag + b_nm + b_nq + b_cone;
+  // the Dirichlet offset boundary: displacements from the Dirichlet
+  // elements alone (a vertex shared with a Neumann element moves along its
+  // Dirichlet element's normal; Neumann elements are not moved)
+  std::vector<uint8_t> fl(n_prims);
+  for (int64_t e = 0; e < n_prims; ++e) fl[e] = neumann[e] ? 1 : 0;
+  std::vector<double> dsp((size_t)n_verts * dim);
+  offset_disp(dim, verts, n_verts, prims, n_prims, fl.data(), dsp.data());
+  const size_t b_disp = al256(dsp.size() * sizeof(double));
+  m->arena_bytes = b_nodes + b_prims + b_dir + b_loc + b_flag + b_nm + b_nq + b_cone + b_disp;
   if (cudaMalloc(&m->arena, m->arena_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     m->arena = nullptr;
@@ -1318,6 +1327,7 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   m->nmeas = (const float2*)(base += b_flag);
   m->neu_q = (const int32_t*)(base += b_nm);
   m->sil.cones = (const float4*)(base += b_nq);
+  m->disp = (const double*)(base += b_cone);
   m->sil.n = ns;
   m->sil.tau = m->whole->dev.tau;
   m->sil.shrink2 = 1.0f;
@@ -1333,9 +1343,8 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
                  cudaSuccess;
   ok = ok && cudaMemcpyAsync((void*)m->neu_local, neu_local.data(), (size_t)n_prims * 4, cudaMemcpyHostToDevice,
                              s) == cudaSuccess;
-  std::vector<uint8_t> fl(n_prims);
-  for (int64_t e = 0; e < n_prims; ++e) fl[e] = neumann[e] ? 1 : 0;
   ok = ok && cudaMemcpyAsync((void*)m->flags, fl.data(), (size_t)n_prims, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync((void*)m->disp, dsp.data(), dsp.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
   if (!nmeas.empty())
     ok = ok && cudaMemcpyAsync((void*)m->nmeas, nmeas.data(), nmeas.size() * sizeof(float2), cudaMemcpyHostToDevice,
                                s) == cudaSuccess;
@@ -1487,7 +1496,8 @@ extern "C" bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn
   const int64_t N = opts->n_samples;
   const int32_t W = opts->walks_per_sample;
   if (cache->dim != D || cache->n != N || N < 1 || !valid_walk((float)opts->eps, opts->max_steps, W) ||
-      !(opts->offset_l > 0.0) || cache->z == nullptr || cache->nrm == nullptr || cache->u_hat == nullptr ||
+      !(opts->offset_l > 0.0) || cache->z == nullptr || cache->nrm == nullptr || cache->jac == nullptr ||
+      cache->u_hat == nullptr ||
       cache->dudn_hat == nullptr || cache->packed == nullptr || workspace == nullptr)
     return BVC_ERR_INVALID_ARG;
   if (opts->sigma != 0.0 || opts->clamp_c != 0.0) return BVC_ERR_UNSUPPORTED;
@@ -1505,8 +1515,8 @@ extern "C" bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn
   cache->clamp_c = 0.0;
   cache->bnd_measure = m->whole->measure;
   int32_t* elem = (int32_t*)((char*)workspace + 256);
-  bvc_status st = launch_sample_boundary(m->whole, N, opts->offset_l, opts->seed, cache->z, cache->nrm, elem, N, s,
-                                         nullptr, m->flags);
+  bvc_status st = launch_sample_boundary(m->whole, N, opts->offset_l, opts->seed, cache->z, cache->nrm, cache->jac,
+                                         elem, N, s, nullptr, m->flags, m->disp);
   if (st != BVC_OK) return st;
   P.starts = cache->z;
   P.start_elem = elem;
@@ -1540,7 +1550,7 @@ extern "C" bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn
   }
   if (ncand > 0) {
     st = opts->reuse_sources ? bvc_source_reweight(m->whole, ffn, cache, s)
-                             : bvc_sample_source(m->whole, ffn, opts->src_grid, opts->seed, cache, workspace,
+                             : bvc_sample_source(m->whole, ffn, opts->src_grid, opts->seed, 0.0, cache, workspace,
                                                  workspace_bytes, stream);
     if (st != BVC_OK) return st;
   }

@@ -17,12 +17,13 @@ TOL = 1e-5
 
 
 def _gpu_cache_from(c, dim, measure):
-    """Device cache holding exactly the oracle's z, n, u^, du/dn^ (and sources)."""
+    """Device cache holding exactly the oracle's z, n, jac, u^, du/dn^ (and sources)."""
     N = c["z"].shape[0]
     ncand = c["n_src"]
     cache = bvc.Cache(dim, N, n_src_cand=ncand)
     cache.z.copy_(torch.from_numpy(np.ascontiguousarray(c["z"].T)))
     cache.nrm.copy_(torch.from_numpy(np.ascontiguousarray(c["n"].T)))
+    cache.jac.copy_(torch.from_numpy(c["jac"].astype(np.float32)))
     cache.u_hat.copy_(torch.from_numpy(c["u_hat"]))
     cache.dudn_hat.copy_(torch.from_numpy(c["q_hat"]))
     if ncand:
@@ -40,7 +41,7 @@ def _compare(cache, c, pts, dim, label):
     bvc.evaluate(cache, st)
     torch.cuda.synchronize()
     ub, us, gb, gs, ab = oracle.gather(c["z"], c["n"], c["u_hat"], c["q_hat"], c["measure"], pts, c["y"], c["c"],
-                                       want_abs=True)
+                                       want_abs=True, jac=c["jac"])
     errs = {}
     errs["u_bnd"] = np.abs(st.u_bnd.cpu().numpy() - ub) / np.maximum(np.abs(ub), ab[:, 0])
     errs["g_bnd"] = np.abs(st.grad_bnd.cpu().numpy().T - gb) / np.maximum(np.abs(gb), ab[:, 1:1 + dim])
@@ -89,6 +90,7 @@ def test_gather_full_size_3d_sampled():
     d = rng.standard_normal((N, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     c = {"z": (d * 0.97).astype(np.float32), "n": d.astype(np.float32),
+         "jac": rng.uniform(0.9, 1.1, N).astype(np.float32).astype(np.float64),
          "u_hat": rng.standard_normal(N), "q_hat": rng.standard_normal(N), "measure": 4 * np.pi,
          "y": None, "c": None, "n_src": 0, "N": N}
     cache = _gpu_cache_from(c, 3, c["measure"])
@@ -97,7 +99,7 @@ def test_gather_full_size_3d_sampled():
     torch.cuda.synchronize()
     sel = rng.choice(w.eval_pts.shape[0], 48, replace=False)
     ub, _, gb, _, ab = oracle.gather(c["z"], c["n"], c["u_hat"], c["q_hat"], c["measure"], w.eval_pts[sel],
-                                     want_abs=True)
+                                     want_abs=True, jac=c["jac"])
     eu = np.abs(st.u_bnd.cpu().numpy()[sel] - ub) / np.maximum(np.abs(ub), ab[:, 0])
     eg = np.abs(st.grad_bnd.cpu().numpy().T[sel] - gb) / np.maximum(np.abs(gb), ab[:, 1:4])
     print(f"[gather full 3D] M={w.eval_pts.shape[0]} N={N} u={eu.max():.2e} g={eg.max():.2e}")
@@ -118,8 +120,8 @@ def test_progressive_accumulation_and_solution():
     u, grad = bvc.get_solution(st)
     torch.cuda.synchronize()
     assert st.counts.cpu().tolist() == [1024, 0]
-    ub1, _, gb1, _ = oracle.gather(c1["z"], c1["n"], c1["u_hat"], c1["q_hat"], c1["measure"], pts)
-    ub2, _, gb2, _ = oracle.gather(c2["z"], c2["n"], c2["u_hat"], c2["q_hat"], c2["measure"], pts)
+    ub1, _, gb1, _ = oracle.gather(c1["z"], c1["n"], c1["u_hat"], c1["q_hat"], c1["measure"], pts, jac=c1["jac"])
+    ub2, _, gb2, _ = oracle.gather(c2["z"], c2["n"], c2["u_hat"], c2["q_hat"], c2["measure"], pts, jac=c2["jac"])
     ref = (ub1 + ub2) / 1024
     np.testing.assert_allclose(u.cpu().numpy(), ref, rtol=1e-4, atol=1e-5)
     np.testing.assert_allclose(grad.cpu().numpy().T, (gb1 + gb2) / 1024, rtol=1e-4, atol=1e-4)

@@ -66,7 +66,13 @@ def test_classify_near_matches_distance():
     pts = _points(V, 4000, 2)
     near = bvc.classify_near(geom, bvc.soa(pts), 0.02).cpu().numpy()
     d2o, _ = oracle.closest_brute32(V, F, pts)
-    np.testing.assert_array_equal(near, (d2o < np.float32(0.02) * np.float32(0.02)).astype(np.uint8))
+    # near = closer than l x reach, the largest vertex displacement of the
+    # offset boundary (FP32, rounded up), so the whole strip between the
+    # boundary and the offset boundary is flagged
+    _, reach = oracle.offset_disp(V, F)
+    assert geom.info().offset_reach == reach
+    lr = np.float32(0.02) * np.nextafter(np.float32(reach), np.float32(np.inf))
+    np.testing.assert_array_equal(near, (d2o < lr * lr).astype(np.uint8))
 
 
 @pytest.mark.parametrize("mesh,n,l", [("circle", 1024, 1e-3), ("star20k", 1000, 0.019), ("sphere4", 3001, 0.01)])
@@ -74,14 +80,17 @@ def test_boundary_samples_match_oracle(mesh, n, l):
     V, F = _mesh(mesh)
     geom = bvc.Geometry(V, F)
     assert geom.boundary_measure == oracle.boundary_measure(V, F)
-    z, nrm, elem = bvc.sample_boundary(geom, n, l, seed=17)
-    zo, no, eo = oracle.sample_boundary(V, F, n, l, seed=17)
+    z, nrm, elem, jac = bvc.sample_boundary(geom, n, l, seed=17)
+    zo, no, eo, jo = oracle.sample_boundary(V, F, n, l, seed=17)
     np.testing.assert_array_equal(elem.cpu().numpy(), eo)
     np.testing.assert_array_equal(z.cpu().numpy().T, zo.astype(np.float32))
     np.testing.assert_array_equal(nrm.cpu().numpy().T, no.astype(np.float32))
+    np.testing.assert_array_equal(jac.cpu().numpy(), jo.astype(np.float32))
 
 
-def test_source_samples_match_oracle():
+@pytest.mark.parametrize("l", [0.0, 0.019])
+def test_source_samples_match_oracle(l):
+    # kept inside the offset boundary at l (the moved polygon, Sec. 3.2)
     V, F = _mesh("star20k")
     geom = bvc.Geometry(V, F)
     rng = np.random.default_rng(3)
@@ -89,9 +98,9 @@ def test_source_samples_match_oracle():
     f = [(wl.GAUSS, bumps)]
     grid = (96, 80)
     cache = bvc.Cache(2, 1, n_src_cand=grid[0] * grid[1])
-    bvc.sample_source(geom, f, grid, seed=5, cache=cache)
+    bvc.sample_source(geom, f, grid, seed=5, cache=cache, l=l)
     torch.cuda.synchronize()
-    yo, co, ncand = oracle.sample_source2d(V, F, grid, 5, f)
+    yo, co, ncand = oracle.sample_source2d(V, F, grid, 5, f, l=l)
     kept = int(cache.n_src_dev.item())
     assert kept == yo.shape[0]
     np.testing.assert_array_equal(cache.src_y[:, :kept].cpu().numpy().T, yo)

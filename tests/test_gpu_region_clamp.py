@@ -53,7 +53,7 @@ def test_region_cache_matches_oracle_and_closed_form():
     exact = _exact(pts)
     z = (us.mean(0) - exact) / (us.std(0, ddof=1) / np.sqrt(len(us)))
     # oracle: samples on the region, walks in the domain
-    zo, no, _ = oracle.sample_boundary(Vr, Fr, N, 0.0, 0)
+    zo, no, _, _ = oracle.sample_boundary(Vr, Fr, N, 0.0, 0)
     z32, n32 = zo.astype(np.float32), no.astype(np.float32)
     o = oracle.walks(oracle.BVH(Vd, Fd), G3, [], z32, W, eps, 1 << 14, 0, 0, oracle.TAG_WALK)
     uh, qh = oracle.reduce_walks(o["U"], o["grad"], n32, W)

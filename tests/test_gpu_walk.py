@@ -54,7 +54,7 @@ def _replay(V, F, g, f, starts, nrm, W, eps, seed, tag=0, max_steps=1 << 14, bvh
 
 def test_replay_circle_configuration():
     w = wl.circle_laplace()
-    z, n, _ = oracle.sample_boundary(w.V, w.F, w.n_samples, w.offset_l, seed=0)
+    z, n, _, _ = oracle.sample_boundary(w.V, w.F, w.n_samples, w.offset_l, seed=0)
     div, eu, eg, steps, o = _replay(w.V, w.F, w.g, w.f, z.astype(np.float32), n.astype(np.float32), w.walks,
                                     w.eps, 0, label="circle 1024x64")
     assert div < 0.01
@@ -63,7 +63,7 @@ def test_replay_circle_configuration():
 
 def test_replay_star_poisson_subset():
     w = wl.star_poisson(grid=16)
-    z, n, _ = oracle.sample_boundary(w.V, w.F, w.n_samples, w.offset_l, seed=1)
+    z, n, _, _ = oracle.sample_boundary(w.V, w.F, w.n_samples, w.offset_l, seed=1)
     sel = np.arange(0, w.n_samples, 128)  # 512 samples spread over the boundary
     div, eu, eg, _, _ = _replay(w.V, w.F, w.g, w.f, z[sel].astype(np.float32), n[sel].astype(np.float32), 32,
                                 w.eps, 1, label="star 512x32 with source")
@@ -74,7 +74,7 @@ def test_replay_star_poisson_subset():
 def test_replay_icosphere_full_mesh_subset():
     V, F, _ = wl.perturbed_icosphere(8, 0)
     eps = 1e-3 * wl.bbox_diagonal(V)
-    z, n, _ = oracle.sample_boundary(V, F, 262144, 5 * eps, seed=2)
+    z, n, _, _ = oracle.sample_boundary(V, F, 262144, 5 * eps, seed=2)
     sel = np.arange(0, 262144, 1024)
     g = [(wl.EXP_TRIG, [1.0, 0.5, 0.3, 0.4])]
     div, eu, eg, _, _ = _replay(V, F, g, [], z[sel].astype(np.float32), n[sel].astype(np.float32), 16, eps, 2,

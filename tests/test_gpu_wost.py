@@ -367,7 +367,7 @@ def test_mixed_cache_full_size_sampled():
     torch.cuda.synchronize()
     # a few walks in 4.2M slip through a rounding gap or hit the step cap
     assert m.whole.stats(reset=True)["capped"] <= 1e-5 * N * W
-    z, n, e = oracle.sample_boundary_mixed(w.V, w.F, N, w.offset_l, 3, w.neumann)
+    z, n, e, _ = oracle.sample_boundary_mixed(w.V, w.F, N, w.offset_l, 3, w.neumann)
     np.testing.assert_array_equal(cache.z.cpu().numpy().T, z.astype(np.float32))
     on = w.neumann[e] == 1
     rng = np.random.default_rng(9)
