@@ -51,9 +51,10 @@ FP32_LANES_PER_SM = 128
 MAX_STEPS = 1 << 14
 
 # Algorithmic work per unit: bytes per BVH node fetch (two child boxes and
-# links) and per primitive test (2D: a segment's two endpoints, 16 B; 3D:
-# three vertices, 48 B), per-walk input/output bytes, FP32 flops per pair.
-BYTES_NODE = {2: 48, 3: 64}
+# links, 48 / 64 B, and the two children's slabs, 32 / 48 B) and per
+# primitive test (2D: a segment's two endpoints, 16 B; 3D: three vertices,
+# 48 B), per-walk input/output bytes, FP32 flops per pair.
+BYTES_NODE = {2: 48 + 32, 3: 64 + 48}
 BYTES_PRIM = {2: 16, 3: 48}
 # bytes the walk kernel actually loads per primitive test: the 2D record
 # also holds the edge vector, 1/|edge|^2 and the element id (two float4)
@@ -266,15 +267,36 @@ def optional_part(fn):
 
 
 # ------------------------------------------------------------------ workloads
-def make_workload(name: str):
+def make_workload(name: str, samples: int = 0, points: int = 0):
+    """The benchmark workload; samples / points (0 = the configuration's)
+    shrink the cache and the evaluation set for bounded profiler captures,
+    keeping the geometry."""
+    from dataclasses import replace
     from paper_2302_11825_gb300 import workloads as wl
     if name == "star":
-        return wl.star_poisson()
-    if name == "circle":
-        return wl.circle_laplace()
-    if name == "sphere":
-        return wl.icosphere_laplace()
-    raise ValueError(name)
+        w = wl.star_poisson()
+    elif name == "circle":
+        w = wl.circle_laplace()
+    elif name == "sphere":
+        w = wl.icosphere_laplace()
+    else:
+        raise ValueError(name)
+    if samples:
+        w = replace(w, n_samples=int(samples))
+    if points and points < w.eval_pts.shape[0]:
+        pick = np.random.default_rng(11).choice(w.eval_pts.shape[0], int(points), replace=False)
+        w = replace(w, eval_pts=w.eval_pts[np.sort(pick)])
+    return w
+
+
+def near_band(dim: int) -> float:
+    """Width of the pointwise band in units of l: points closer to the
+    boundary than near_band x l get pointwise walk-on-spheres estimates
+    (Sec. 3.2 uses l).  In 3D the double-layer kernel of Eq. 3 grows like
+    1/r^2 next to the sample surface, and the points between l and 1.1 l
+    carry most of the gathered points' squared error, so the 3D workloads
+    use 2 l."""
+    return 1.0 if dim == 2 else 2.0
 
 
 class Solver:
@@ -289,7 +311,8 @@ class Solver:
         torch.cuda.synchronize()
         self.geometry_build_s = time.perf_counter() - t0
         pts = bvc.soa(w.eval_pts)
-        near = bvc.classify_near(self.geom, pts, w.offset_l).bool()
+        self.band = near_band(w.dim)
+        near = bvc.classify_near(self.geom, pts, self.band * w.offset_l).bool()
         torch.cuda.synchronize()
         self.far_pts = pts[:, ~near].contiguous()
         self.near_pts = pts[:, near].contiguous()
@@ -387,12 +410,15 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
     # least 4 l from the boundary
     d2f, _, _ = bvc.query_closest(s.geom, s.far_pts)
     deep_far = np.sqrt(d2f.cpu().numpy()) >= 4.0 * w.offset_l
-    mse, gmse, gmse_deep = [], [], []
+    mse, gmse, gmse_deep, mse_far, mse_near = [], [], [], [], []
     for seed in (7, 8, 9, 10):
         s.step(seed)
         torch.cuda.synchronize()
-        err = np.concatenate([s.u_far.cpu().numpy() - ex_far, s.u_near.cpu().numpy() - ex_near])
+        ef, en = s.u_far.cpu().numpy() - ex_far, s.u_near.cpu().numpy() - ex_near
+        err = np.concatenate([ef, en])
         mse.append(float(np.mean(err ** 2)))
+        mse_far.append(float(np.mean(ef ** 2)))
+        mse_near.append(float(np.mean(en ** 2)) if en.size else 0.0)
         ge = np.sum((s.g_far.cpu().numpy().T - gx_far) ** 2, 1)
         gmse.append(float(np.mean(ge)))
         gmse_deep.append(float(np.mean(ge[deep_far])))
@@ -437,7 +463,7 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
 
     def wos_at(target):
         """Pointwise walks per point reaching RMSE <= target, and the rate."""
-        k = int(min(kmax, max(64, np.ceil(64 * (r0 / target) ** 2))))
+        k = int(min(kmax, max(4, np.ceil(64 * (r0 / target) ** 2))))
         r, t = wos_rmse(k, 12)
         while r > target and k < kmax:
             k = min(kmax, int(k * 1.25) + 1)
@@ -445,7 +471,9 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
         return k, r, st.m / t
 
     k, r, wos_rate = wos_at(tau)
-    out = {"variant": w.name, "tau_rmse": tau, "bvc_pts_per_s": bvc_rate, "wos_walks_per_point": k,
+    out = {"variant": w.name, "tau_rmse": tau, "bvc_rmse_gathered": float(np.sqrt(np.mean(mse_far))),
+           "bvc_rmse_pointwise_band": float(np.sqrt(np.mean(mse_near))), "near_band_l": s.band,
+           "bvc_pts_per_s": bvc_rate, "wos_walks_per_point": k,
            "wos_rmse": r, "wos_pts_per_s": wos_rate, "bvc_over_wos": bvc_rate / wos_rate,
            "wos_subset_points": int(st.m),
            # gradient error at those sizes (points farther than l): BVC (Eq. 5-6)
@@ -1322,7 +1350,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed-rmse", action="store_true")
     ap.add_argument("--samples", type=int, default=0,
-                    help="mixed workload only: boundary samples (default: the workload's 65536)")
+                    help="boundary samples (default: the workload's); for bounded profiler captures")
+    ap.add_argument("--points", type=int, default=0,
+                    help="circle, star, sphere: evaluation points (default: all); for bounded profiler captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, local, ws = dist_env()
@@ -1388,7 +1418,7 @@ def main():
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     rank, ws = init_dist("nccl")
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.samples, args.points)
     s = Solver(w, device)
     M = s.m_far + s.m_near
     dim = w.dim
@@ -1533,7 +1563,7 @@ def main():
         "config": {"workload": w.name, "dim": dim, "n_prims": int(w.F.shape[0]), "n_samples": w.n_samples,
                    "walks_per_sample": w.walks, "src_candidates": int(s.cache.n_src_cand), "src_kept": n_src_kept,
                    "eval_points": int(M), "eval_far": int(s.m_far), "eval_near_pointwise": int(s.m_near),
-                   "near_walks": w.walks, "eps": w.eps, "offset_l": w.offset_l,
+                   "near_walks": w.walks, "eps": w.eps, "offset_l": w.offset_l, "near_band_l": s.band,
                    "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}",
                    "sums": "fp64",
                    "walk_shape": {"blocks_per_sm": s.walk_shape[0], "chunk": s.walk_shape[1],

@@ -100,8 +100,12 @@ typedef struct {
  * verts: host float[n_verts][dim] (row-major); prims: host int32[n_prims][dim].
  * Validation: finite vertices, indices in range, no zero-length or
  * zero-area element (BVC_ERR_DEGENERATE_MESH).  The BVH is built on the host
- * (binned SAH) and copied to device memory the handle owns; the copy is
- * enqueued on `stream` and the call returns once it is complete.  The
+ * (binned SAH) and copied to device memory the handle owns.  The allocation
+ * is stream-ordered (cudaMallocAsync on `stream`) and the copies are
+ * enqueued on `stream`, so the handle is ready for later work on that
+ * stream at once (other streams must first synchronise with it); the call
+ * does not wait for the device, and the caller's arrays are read during the
+ * call only.  bvc_geometry_destroy frees with cudaFree (which waits).  The
  * handle also holds the element-measure CDF used by boundary sampling
  * (Sec. 4 "Sampling"), the per-vertex displacements of the offset boundary
  * (Sec. 3.2, see bvc_sample_boundary) and a small device status/statistics
@@ -505,7 +509,7 @@ typedef struct {
   int64_t n_points;  /* evaluation points (>= 0) */
 } bvc_batch_mesh;
 
-/* Builds the forest (synchronous on `stream`).  All meshes must share one
+/* Builds the forest (stream-ordered on `stream`, as bvc_geometry_create).  All meshes must share one
  * dimension; count >= 1; walks, max_steps >= 1; k >= 1.  Samples of mesh j
  * occupy [sum_{i<j} n_samples_i, ...) of the batch's sample range and its
  * points [sum_{i<j} n_points_i, ...) of the point range. */
@@ -607,7 +611,7 @@ typedef struct bvc_mixed_s* bvc_mixed;
 /* Flags neumann[e] != 0 mark Neumann elements (host uint8[n_prims]); at
  * least one element must be Dirichlet.  Builds the whole boundary's geometry,
  * the Dirichlet and Neumann parts' geometries and the silhouette tree
- * (synchronous on `stream`).  Mesh arguments as bvc_geometry_create. */
+ * (stream-ordered on `stream`, as bvc_geometry_create).  Mesh arguments as bvc_geometry_create. */
 bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims, int64_t n_prims,
                             const uint8_t* neumann, bvc_stream stream, bvc_mixed* out);
 bvc_status bvc_mixed_destroy(bvc_mixed m);
@@ -702,6 +706,13 @@ bvc_status bvc_profile_end(bvc_kernel_time* out, int32_t max_out, int32_t* n_out
 
 /* ------------------------------------------------------------------ misc */
 const char* bvc_status_string(bvc_status s);
+/* The last status other than BVC_OK that any entry point returned on the
+ * calling thread (thread-local; every call returns its status directly as
+ * well), or BVC_OK if there was none since the previous bvc_last_error call;
+ * the call clears it.  Device-side conditions are read per handle
+ * (bvc_geometry_stats, bvc_batch_stats, bvc_gather_status) and also pass
+ * through here when those calls return them. */
+bvc_status bvc_last_error(void);
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t bvc_version(void);
 

@@ -49,7 +49,7 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 using namespace bvc;
 
-extern "C" bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t count, int32_t walks, int32_t max_steps,
+static bvc_status bvc_batch_create_impl(const bvc_batch_mesh* meshes, int32_t count, int32_t walks, int32_t max_steps,
                                        int32_t k, bvc_stream stream, bvc_batch* out) {
   if (out == nullptr) return BVC_ERR_INVALID_ARG;
   *out = nullptr;
@@ -88,6 +88,8 @@ extern "C" bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t cou
   if (n_prims >= (int64_t(1) << 27) || n_nodes >= (int64_t(1) << 31)) return BVC_ERR_UNSUPPORTED;
   const int per_node = dim == 2 ? 3 : 4, per_prim = dim == 2 ? 2 : 3;
   const size_t b_nodes = align256((size_t)n_nodes * per_node * sizeof(float4));
+  const int per_slab = dim == 2 ? 2 : 3;
+  const size_t b_slabs = align256((size_t)n_nodes * per_slab * sizeof(float4));
   const size_t b_prims = align256((size_t)n_prims * per_prim * sizeof(float4));
   const size_t b_stats = 256;
   const size_t b_mesh = align256((size_t)n_total * sizeof(int32_t));
@@ -104,8 +106,9 @@ extern "C" bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t cou
   b->mesh = tab;
   b->offset_l = offl;
   b->geoms = geoms;
-  b->arena_bytes = b_nodes + b_prims + b_stats + b_mesh + b_tab;
-  if (cudaMalloc(&b->arena, b->arena_bytes) != cudaSuccess) {
+  b->arena_bytes = b_nodes + b_slabs + b_prims + b_stats + b_mesh + b_tab;
+  // stream-ordered, like bvc_geometry_create: ready for work on `stream`
+  if (cudaMallocAsync(&b->arena, b->arena_bytes, (cudaStream_t)stream) != cudaSuccess) {
     (void)cudaGetLastError();
     delete b;
     return BVC_ERR_OOM;
@@ -114,7 +117,8 @@ extern "C" bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t cou
   DevGeometry& F = b->forest;
   F = DevGeometry{};
   F.nodes = (const float4*)base;
-  F.prims = (const float4*)(base += b_nodes);
+  F.slabs = (const float4*)(base += b_nodes);
+  F.prims = (const float4*)(base += b_slabs);
   F.stats = (unsigned long long*)(base += b_prims);
   b->sample_mesh = (int32_t*)(base += b_stats);
   b->table = (BatchMeshDev*)(base += b_mesh);
@@ -140,36 +144,48 @@ extern "C" bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t cou
     else
       k_rebase_nodes<3><<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(g->dev.nodes, nn, dn, tab[j].root,
                                                                       (int32_t)prim_off);
+    // slabs hold no links: copied as they are, node for node
     ok = cudaGetLastError() == cudaSuccess &&
+         cudaMemcpyAsync((float4*)F.slabs + (size_t)tab[j].root * per_slab, g->dev.slabs,
+                         (size_t)nn * per_slab * sizeof(float4), cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
          cudaMemcpyAsync((float4*)F.prims + (size_t)prim_off * per_prim, g->dev.prims,
                          (size_t)g->n_prims * per_prim * sizeof(float4), cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     prim_off += g->n_prims;
   }
-  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();
-    cudaFree(b->arena);
+    (void)cudaFreeAsync(b->arena, s);
     delete b;
     return BVC_ERR_CUDA;
   }
   *out = b;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_batch_create(const bvc_batch_mesh* meshes, int32_t count, int32_t walks, int32_t max_steps,
+                                       int32_t k, bvc_stream stream, bvc_batch* out) {
+  return bvc::note_status(bvc_batch_create_impl(meshes, count, walks, max_steps, k, stream, out));
+}
 
-extern "C" bvc_status bvc_batch_destroy(bvc_batch b) {
+static bvc_status bvc_batch_destroy_impl(bvc_batch b) {
   if (b == nullptr) return BVC_ERR_INVALID_ARG;
   const cudaError_t e = cudaFree(b->arena);
   delete b;
   return e == cudaSuccess ? BVC_OK : BVC_ERR_CUDA;
 }
+extern "C" bvc_status bvc_batch_destroy(bvc_batch b) {
+  return bvc::note_status(bvc_batch_destroy_impl(b));
+}
 
-extern "C" bvc_status bvc_batch_set_counting(bvc_batch b, int32_t on) {
+static bvc_status bvc_batch_set_counting_impl(bvc_batch b, int32_t on) {
   if (b == nullptr) return BVC_ERR_INVALID_ARG;
   b->counting = on ? 1 : 0;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_batch_set_counting(bvc_batch b, int32_t on) {
+  return bvc::note_status(bvc_batch_set_counting_impl(b, on));
+}
 
-extern "C" bvc_status bvc_batch_stats(bvc_batch b, uint64_t out[8], int32_t reset, bvc_stream stream) {
+static bvc_status bvc_batch_stats_impl(bvc_batch b, uint64_t out[8], int32_t reset, bvc_stream stream) {
   if (b == nullptr || out == nullptr) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long h[8];
@@ -181,11 +197,17 @@ extern "C" bvc_status bvc_batch_stats(bvc_batch b, uint64_t out[8], int32_t rese
   if (h[kStatCapped]) return BVC_WARN_WALK_CAP;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_batch_stats(bvc_batch b, uint64_t out[8], int32_t reset, bvc_stream stream) {
+  return bvc::note_status(bvc_batch_stats_impl(b, out, reset, stream));
+}
 
-extern "C" bvc_status bvc_batch_get_info(bvc_batch b, int32_t* dim, int64_t* n_total, int64_t* m_total) {
+static bvc_status bvc_batch_get_info_impl(bvc_batch b, int32_t* dim, int64_t* n_total, int64_t* m_total) {
   if (b == nullptr) return BVC_ERR_INVALID_ARG;
   if (dim) *dim = b->dim;
   if (n_total) *n_total = b->n_total;
   if (m_total) *m_total = b->m_total;
   return BVC_OK;
+}
+extern "C" bvc_status bvc_batch_get_info(bvc_batch b, int32_t* dim, int64_t* n_total, int64_t* m_total) {
+  return bvc::note_status(bvc_batch_get_info_impl(b, dim, n_total, m_total));
 }

@@ -343,7 +343,7 @@ CorrLayout corr_layout(int dim, int64_t m, int32_t n_dirs) {
 }
 }  // namespace
 
-extern "C" bvc_status bvc_clamp_correction_workspace_size(int32_t dim, int64_t m, int32_t n_dirs, int32_t walks,
+static bvc_status bvc_clamp_correction_workspace_size_impl(int32_t dim, int64_t m, int32_t n_dirs, int32_t walks,
                                                           size_t* min_bytes) {
   if ((dim != 2 && dim != 3) || m < 0 || n_dirs < 1 || walks < 1 || min_bytes == nullptr) return BVC_ERR_INVALID_ARG;
   size_t per = 0;
@@ -351,8 +351,12 @@ extern "C" bvc_status bvc_clamp_correction_workspace_size(int32_t dim, int64_t m
   *min_bytes = corr_layout(dim, m, n_dirs).total + per;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_clamp_correction_workspace_size(int32_t dim, int64_t m, int32_t n_dirs, int32_t walks,
+                                                          size_t* min_bytes) {
+  return bvc::note_status(bvc_clamp_correction_workspace_size_impl(dim, m, n_dirs, walks, min_bytes));
+}
 
-extern "C" bvc_status bvc_clamp_correction(bvc_geometry domain, bvc_geometry surface, double offset_l,
+static bvc_status bvc_clamp_correction_impl(bvc_geometry domain, bvc_geometry surface, double offset_l,
                                            const bvc_function* gfn, const bvc_function* ffn, double sigma,
                                            double clamp_c, const float* pts, int64_t m, int32_t n_dirs,
                                            int32_t walks, float eps, int32_t max_steps, uint64_t seed,
@@ -435,4 +439,12 @@ extern "C" bvc_status bvc_clamp_correction(bvc_geometry domain, bvc_geometry sur
     BVC_LAUNCH_CHECK();
   }
   return BVC_OK;
+}
+extern "C" bvc_status bvc_clamp_correction(bvc_geometry domain, bvc_geometry surface, double offset_l,
+                                           const bvc_function* gfn, const bvc_function* ffn, double sigma,
+                                           double clamp_c, const float* pts, int64_t m, int32_t n_dirs,
+                                           int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                                           double* u_corr, int64_t* n_hits, void* workspace, size_t workspace_bytes,
+                                           bvc_stream stream) {
+  return bvc::note_status(bvc_clamp_correction_impl(domain, surface, offset_l, gfn, ffn, sigma, clamp_c, pts, m, n_dirs, walks, eps, max_steps, seed, u_corr, n_hits, workspace, workspace_bytes, stream));
 }

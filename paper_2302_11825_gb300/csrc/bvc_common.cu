@@ -1,5 +1,6 @@
 // bvc_common.cu -- host helpers: problem-function conversion, device
 // properties, status strings.
+#include <nvtx3/nvToolsExt.h>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -113,6 +114,10 @@ Profiler& prof() {
 }  // namespace
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : slot_(-1), s_(s) {
+  // an NVTX range around every launch, named for its step (K1 sample_boundary,
+  // K2/K6 walk, K3 reduce_walks, K4 source_*, K5 gather_*, ...), for
+  // timeline tools; without a tool attached the call returns at once
+  nvtxRangePushA(name);
   Profiler& P = prof();
   std::lock_guard<std::mutex> g(P.mu);
   if (!P.on) return;
@@ -124,6 +129,7 @@ ProfScope::ProfScope(const char* name, cudaStream_t s) : slot_(-1), s_(s) {
 }
 
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   if (slot_ < 0) return;
   Profiler& P = prof();
   std::lock_guard<std::mutex> g(P.mu);
@@ -132,7 +138,7 @@ ProfScope::~ProfScope() {
 
 }  // namespace bvc
 
-extern "C" bvc_status bvc_profile_begin(void) {
+static bvc_status bvc_profile_begin_impl(void) {
   bvc::Profiler& P = bvc::prof();
   std::lock_guard<std::mutex> g(P.mu);
   for (auto& r : P.recs) {
@@ -143,8 +149,11 @@ extern "C" bvc_status bvc_profile_begin(void) {
   P.on = true;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_profile_begin(void) {
+  return bvc::note_status(bvc_profile_begin_impl());
+}
 
-extern "C" bvc_status bvc_profile_end(bvc_kernel_time* out, int32_t max_out, int32_t* n_out) {
+static bvc_status bvc_profile_end_impl(bvc_kernel_time* out, int32_t max_out, int32_t* n_out) {
   bvc::Profiler& P = bvc::prof();
   std::lock_guard<std::mutex> g(P.mu);
   P.on = false;
@@ -180,6 +189,9 @@ extern "C" bvc_status bvc_profile_end(bvc_kernel_time* out, int32_t max_out, int
   (void)cudaGetLastError();
   return st;
 }
+extern "C" bvc_status bvc_profile_end(bvc_kernel_time* out, int32_t max_out, int32_t* n_out) {
+  return bvc::note_status(bvc_profile_end_impl(out, max_out, n_out));
+}
 
 extern "C" const char* bvc_status_string(bvc_status s) {
   switch (s) {
@@ -197,3 +209,13 @@ extern "C" const char* bvc_status_string(bvc_status s) {
 }
 
 extern "C" int32_t bvc_version(void) { return 100; }
+
+namespace bvc {
+thread_local bvc_status g_last_status = BVC_OK;
+}
+
+extern "C" bvc_status bvc_last_error(void) {
+  const bvc_status s = bvc::g_last_status;
+  bvc::g_last_status = BVC_OK;
+  return s;
+}

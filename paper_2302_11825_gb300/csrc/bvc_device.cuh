@@ -502,6 +502,44 @@ __device__ __forceinline__ float box_d2_3(float lox, float loy, float loz, float
   return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 
+// Squared distance from p to the slab dmin <= n . x <= dmax (an unbounded
+// slab has n = 0 and gives 0).
+template <int D>
+__device__ __forceinline__ float slab_d2(float nx, float ny, float nz, float dmin, float dmax, const float* p) {
+  const float s = D == 2 ? fmaf(ny, p[1], nx * p[0]) : fmaf(nz, p[D - 1], fmaf(ny, p[1], nx * p[0]));
+  const float d = fmaxf(fmaxf(s - dmax, dmin - s), 0.0f);
+  return d * d;
+}
+
+// One node fetch: the children's links and lower bounds on the squared
+// distance from p to the elements below each child, max(box distance^2,
+// slab distance^2) (the slab of a smooth patch is much thinner than its
+// box).  Box distances are exact FP32 bounds; the slab distance's rounding
+// (a few ulp of |p|) is far below the traversal's slack tau, which the
+// pruning threshold already includes.
+template <int D>
+__device__ __forceinline__ void node_bounds(const DevGeometry& G, int node, const float* p, float& dl, float& dr,
+                                            int32_t& cl, int32_t& cr) {
+  if (D == 2) {
+    const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
+    const float4 C = __ldg(&G.nodes[3 * node + 2]);
+    const float4 SL = __ldg(&G.slabs[2 * node]), SR = __ldg(&G.slabs[2 * node + 1]);
+    dl = fmaxf(box_d2_2(L.x, L.y, L.z, L.w, p), slab_d2<2>(SL.x, SL.y, 0.0f, SL.z, SL.w, p));
+    dr = fmaxf(box_d2_2(R.x, R.y, R.z, R.w, p), slab_d2<2>(SR.x, SR.y, 0.0f, SR.z, SR.w, p));
+    cl = __float_as_int(C.x);
+    cr = __float_as_int(C.y);
+  } else {
+    const float4 a = __ldg(&G.nodes[4 * node]), b = __ldg(&G.nodes[4 * node + 1]);
+    const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
+    const float4 s0 = __ldg(&G.slabs[3 * node]), s1 = __ldg(&G.slabs[3 * node + 1]);
+    const float4 s2 = __ldg(&G.slabs[3 * node + 2]);
+    dl = fmaxf(box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, p), slab_d2<3>(s0.x, s0.y, s0.z, s0.w, s1.x, p));
+    dr = fmaxf(box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, p), slab_d2<3>(s1.y, s1.z, s1.w, s2.x, s2.y, p));
+    cl = __float_as_int(e.x);
+    cr = __float_as_int(e.y);
+  }
+}
+
 // Work counters of the counting variant (node fetches, primitive tests).
 struct TravCount {
   uint32_t nodes, prims;
@@ -568,21 +606,7 @@ __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p
     int32_t cl, cr;
     float dl, dr;
     if (CNT) ++tc.nodes;
-    if (D == 2) {
-      const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
-      const float4 C = __ldg(&G.nodes[3 * node + 2]);
-      dl = box_d2_2(L.x, L.y, L.z, L.w, p);
-      dr = box_d2_2(R.x, R.y, R.z, R.w, p);
-      cl = __float_as_int(C.x);
-      cr = __float_as_int(C.y);
-    } else {
-      const float4 a = __ldg(&G.nodes[4 * node]), b = __ldg(&G.nodes[4 * node + 1]);
-      const float4 c = __ldg(&G.nodes[4 * node + 2]), e = __ldg(&G.nodes[4 * node + 3]);
-      dl = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, p);
-      dr = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, p);
-      cl = __float_as_int(e.x);
-      cr = __float_as_int(e.y);
-    }
+    node_bounds<D>(G, node, p, dl, dr, cl, cr);
     if (dr < dl) {
       const int32_t tc = cl;
       cl = cr;

@@ -12,9 +12,11 @@
 //      a = u^ |dOmega| / (2 pi), b = du/dn^ |dOmega| / (2 pi)
 //      u    += a (n.d)/r^2 - b ln r
 //      grad += d (2a (n.d)/r^2 + b)/r^2 - a n / r^2            (d = z - x)
-//   3D boundary (20 floats): z, n, a, -a, 3a, b   (a, b with 4 pi)
-//      u    += a (n.d)/r^3 + b/r
-//      grad += d (3a (n.d)/r^2 + b)/r^3 - a n / r^3
+//   3D boundary (20 floats): z, A = a n, -A, b   (a, b with 4 pi)
+//      u    += (A.d)/r^3 + b/r
+//      grad += (d (3 (A.d)/r^2 + b) - A) / r^3
+//      (1/r from rsqrt and 1/r^2 from rcp, both on the SFU, so that the
+//      FMA pipe carries 20 paired instructions per two pairs)
 //   2D source (8 floats): y, c ln2/(4 pi), -c/(2 pi):  u += c/(2 pi) ln r,  grad -= c/(2 pi) d/r^2
 //   3D source (8 floats): y, -c/(4 pi):                u -= c/(4 pi)/r,     grad -= c/(4 pi) d/r^3
 // (G_2D = ln r/(2 pi), G_3D = -1/(4 pi r), the sign that makes Eq. 2 hold.)
@@ -39,10 +41,16 @@ constexpr int kTile = 128;  // samples per tile (FP32 partial-sum length)
 // (measured on GB300: boundary tiles are FMA/SFU-bound and gain from reuse
 // of each shared-memory sample across 6 points; source tiles are SFU-bound
 // and gain from occupancy).
-template <int KIND>
+#ifndef BVC_GATHER_PTS_BND
+#define BVC_GATHER_PTS_BND(D) 6
+#endif
+#ifndef BVC_GATHER_MINB_BND
+#define BVC_GATHER_MINB_BND(D) 2
+#endif
+template <int D, int KIND>
 struct GatherShape {
-  static constexpr int kPts = KIND == 0 ? 6 : 2;
-  static constexpr int kMinBlocks = KIND == 0 ? 2 : 4;
+  static constexpr int kPts = KIND == 0 ? BVC_GATHER_PTS_BND(D) : 2;
+  static constexpr int kMinBlocks = KIND == 0 ? BVC_GATHER_MINB_BND(D) : 4;
   static constexpr int kPtsPerCta = kGBlock * kPts;
 };
 
@@ -177,21 +185,20 @@ __device__ __forceinline__ void pair_bnd2(const ulonglong2* T, f2 px, f2 py, f2*
 template <bool GRAD>
 __device__ __forceinline__ void pair_bnd3(const ulonglong2* T, f2 px, f2 py, f2 pz, f2* acc) {
   const ulonglong2 t0 = T[0], t1 = T[1], t2 = T[2], t3 = T[3], t4 = T[4];
-  // t0 = (z.x, z.y), t1 = (z.z, n.x), t2 = (n.y, n.z), t3 = (a, -a), t4 = (3a, b)
+  // t0 = (z.x, z.y), t1 = (z.z, A.x), t2 = (A.y, A.z), t3 = (-A.x, -A.y), t4 = (-A.z, b)
   const f2 dx = add2(t0.x, px), dy = add2(t0.y, py), dz = add2(t1.x, pz);
   const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
   const f2 ir = rsqrt2(r2);
-  const f2 ir2 = mul2(ir, ir);
+  const f2 ir2 = rcp2(r2);
   const f2 ir3 = mul2(ir2, ir);
-  const f2 nd = fma2(t2.y, dz, fma2(t2.x, dy, mul2(t1.y, dx)));
-  acc[0] = fma2(mul2(t3.x, nd), ir3, acc[0]);
+  const f2 ad = fma2(t2.y, dz, fma2(t2.x, dy, mul2(t1.y, dx)));  // A.d
+  acc[0] = fma2(ad, ir3, acc[0]);
   acc[0] = fma2(t4.y, ir, acc[0]);
   if (GRAD) {
-    const f2 k = mul2(fma2(t4.x, mul2(nd, ir2), t4.y), ir3);
-    const f2 nai = mul2(t3.y, ir3);
-    acc[1] = fma2(nai, t1.y, fma2(k, dx, acc[1]));
-    acc[2] = fma2(nai, t2.x, fma2(k, dy, acc[2]));
-    acc[3] = fma2(nai, t2.y, fma2(k, dz, acc[3]));
+    const f2 t = fma2(ad, mul2(ir2, pk(3.0f, 3.0f)), t4.y);  // 3 (A.d)/r^2 + b
+    acc[1] = fma2(ir3, fma2(t, dx, t3.x), acc[1]);
+    acc[2] = fma2(ir3, fma2(t, dy, t3.y), acc[2]);
+    acc[3] = fma2(ir3, fma2(t, dz, t4.x), acc[3]);
   }
 }
 
@@ -239,9 +246,9 @@ struct GatherArgs {
 };
 
 template <int D, int KIND, bool GRAD>
-__global__ void __launch_bounds__(kGBlock, GatherShape<KIND>::kMinBlocks) k_gather(const GatherArgs A) {
-  constexpr int kGPts = GatherShape<KIND>::kPts;
-  constexpr int kPtsPerCta = GatherShape<KIND>::kPtsPerCta;
+__global__ void __launch_bounds__(kGBlock, GatherShape<D, KIND>::kMinBlocks) k_gather(const GatherArgs A) {
+  constexpr int kGPts = GatherShape<D, KIND>::kPts;
+  constexpr int kPtsPerCta = GatherShape<D, KIND>::kPtsPerCta;
   constexpr int SPF = KIND == 1 ? 2 : 5;
   constexpr int NA = GRAD ? 1 + D : 1;
   __shared__ __align__(128) float4 tile[2][kTile * SPF];
@@ -401,13 +408,13 @@ __global__ void __launch_bounds__(256) k_pack_bnd(const bvc_cache C) {
     const double a = C.u_hat[i] * ip / four_pi;
     const double b = C.dudn_hat[i] * ip / four_pi;
     const float zx = C.z[i], zy = C.z[C.n + i], zz = C.z[2 * C.n + i];
-    const float nx = C.nrm[i], ny = C.nrm[C.n + i], nz = C.nrm[2 * C.n + i];
-    const float fa = (float)a, fb = (float)b, a3 = (float)(3.0 * a);
+    const float ax = (float)(a * (double)C.nrm[i]), ay = (float)(a * (double)C.nrm[C.n + i]);
+    const float az = (float)(a * (double)C.nrm[2 * C.n + i]), fb = (float)b;
     o[0] = make_float4(zx, zx, zy, zy);
-    o[1] = make_float4(zz, zz, nx, nx);
-    o[2] = make_float4(ny, ny, nz, nz);
-    o[3] = make_float4(fa, fa, -fa, -fa);
-    o[4] = make_float4(a3, a3, fb, fb);
+    o[1] = make_float4(zz, zz, ax, ax);
+    o[2] = make_float4(ay, ay, az, az);
+    o[3] = make_float4(-ax, -ax, -ay, -ay);
+    o[4] = make_float4(-az, -az, fb, fb);
   }
 }
 
@@ -453,9 +460,10 @@ struct Plan {
   int64_t split_len;
 };
 
-static Plan plan_gather(int64_t m, int64_t n, int kind, const void* kern) {
+static Plan plan_gather(int D, int64_t m, int64_t n, int kind, const void* kern) {
   Plan P;
-  const int64_t per_cta = kind == 0 ? GatherShape<0>::kPtsPerCta : GatherShape<1>::kPtsPerCta;
+  const int64_t per_cta = kind == 0 ? (D == 2 ? GatherShape<2, 0>::kPtsPerCta : GatherShape<3, 0>::kPtsPerCta)
+                                    : GatherShape<2, 1>::kPtsPerCta;
   P.pblocks = (int32_t)((m + per_cta - 1) / per_cta);
   const int64_t tiles = (n + kTile - 1) / kTile;
   const int64_t conc = (int64_t)num_sms() * max_blocks_per_sm(kern, kGBlock, 0);
@@ -628,7 +636,7 @@ __global__ void __launch_bounds__(256) k_gather_scr(const float* __restrict__ x,
 
 using namespace bvc;
 
-extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) {
+static bvc_status bvc_cache_pack_impl(const bvc_cache* cache, bvc_stream stream) {
   if (cache == nullptr || (cache->dim != 2 && cache->dim != 3) || cache->n < 0) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (cache->n > 0) {
@@ -659,8 +667,11 @@ extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) 
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_cache_pack(const bvc_cache* cache, bvc_stream stream) {
+  return bvc::note_status(bvc_cache_pack_impl(cache, stream));
+}
 
-extern "C" bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const bvc_eval_state* state,
+static bvc_status bvc_evaluate_workspace_size_impl(const bvc_cache* cache, const bvc_eval_state* state,
                                                   size_t* bytes) {
   if (cache == nullptr || state == nullptr || bytes == nullptr || cache->dim != state->dim) return BVC_ERR_INVALID_ARG;
   const int D = cache->dim;
@@ -668,22 +679,26 @@ extern "C" bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const 
   const int planes = grad ? 1 + D : 1;
   size_t b = 0;
   if (cache->n > 0) {
-    const Plan P = plan_gather(state->m, cache->n, 0, pick(D, 0, grad));
+    const Plan P = plan_gather(D, state->m, cache->n, 0, pick(D, 0, grad));
     b = part_bytes(P, planes, state->m);
   }
   if (cache->n_src_cand > 0) {
-    const Plan P = plan_gather(state->m, cache->n_src_cand, 1, pick(D, 1, grad));
+    const Plan P = plan_gather(D, state->m, cache->n_src_cand, 1, pick(D, 1, grad));
     const size_t bs = part_bytes(P, planes, state->m);
     b = bs > b ? bs : b;
   }
   *bytes = b;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const bvc_eval_state* state,
+                                                  size_t* bytes) {
+  return bvc::note_status(bvc_evaluate_workspace_size_impl(cache, state, bytes));
+}
 
 static bvc_status run_part(int D, int kind, bool grad, const float* x, int64_t m, const float4* samples, int64_t n,
                            const int64_t* n_dev, double* u, double* g, void* ws, size_t ws_bytes, cudaStream_t s) {
   const void* kern = pick(D, kind, grad);
-  const Plan P = plan_gather(m, n, kind, kern);
+  const Plan P = plan_gather(D, m, n, kind, kern);
   const int planes = grad ? 1 + D : 1;
   GatherArgs A{};
   A.x = x;
@@ -716,7 +731,7 @@ static bvc_status run_part(int D, int kind, bool grad, const float* x, int64_t m
   return BVC_OK;
 }
 
-extern "C" bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state, void* workspace,
+static bvc_status bvc_evaluate_impl(const bvc_cache* cache, bvc_eval_state* state, void* workspace,
                                    size_t workspace_bytes, bvc_stream stream) {
   if (cache == nullptr || state == nullptr || cache->dim != state->dim || (cache->dim != 2 && cache->dim != 3) ||
       state->m < 0 || cache->n < 0 || state->counts == nullptr)
@@ -784,8 +799,12 @@ extern "C" bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state, void* workspace,
+                                   size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_evaluate_impl(cache, state, workspace, workspace_bytes, stream));
+}
 
-extern "C" bvc_status bvc_eval_state_reset(const bvc_eval_state* state, bvc_stream stream) {
+static bvc_status bvc_eval_state_reset_impl(const bvc_eval_state* state, bvc_stream stream) {
   if (state == nullptr || state->m < 0 || state->counts == nullptr || (state->dim != 2 && state->dim != 3))
     return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -800,8 +819,11 @@ extern "C" bvc_status bvc_eval_state_reset(const bvc_eval_state* state, bvc_stre
   BVC_CUDA_TRY(cudaMemsetAsync(state->counts, 0, 2 * sizeof(int64_t), s));
   return BVC_OK;
 }
+extern "C" bvc_status bvc_eval_state_reset(const bvc_eval_state* state, bvc_stream stream) {
+  return bvc::note_status(bvc_eval_state_reset_impl(state, stream));
+}
 
-extern "C" bvc_status bvc_get_solution(const bvc_eval_state* state, double* u, double* grad, bvc_stream stream) {
+static bvc_status bvc_get_solution_impl(const bvc_eval_state* state, double* u, double* grad, bvc_stream stream) {
   if (state == nullptr || u == nullptr || state->m < 0 || state->counts == nullptr ||
       (state->dim != 2 && state->dim != 3))
     return BVC_ERR_INVALID_ARG;
@@ -816,6 +838,9 @@ extern "C" bvc_status bvc_get_solution(const bvc_eval_state* state, double* u, d
     k_get_solution<3><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(*state, u, grad);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
+}
+extern "C" bvc_status bvc_get_solution(const bvc_eval_state* state, double* u, double* grad, bvc_stream stream) {
+  return bvc::note_status(bvc_get_solution_impl(state, u, grad, stream));
 }
 
 // Self-test of the bounded wait: one warp waits on a barrier that nothing
@@ -832,14 +857,17 @@ __global__ void k_wait_selftest(uint64_t limit_ns) {
   if (!ok && threadIdx.x == 0) atomicOr(&g_gather_status, 2ull);
 }
 
-extern "C" bvc_status bvc_wait_selftest(int64_t limit_ns, bvc_stream stream) {
+static bvc_status bvc_wait_selftest_impl(int64_t limit_ns, bvc_stream stream) {
   if (limit_ns < 0 || limit_ns > 2000000000ll) return BVC_ERR_INVALID_ARG;
   k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_ns);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_wait_selftest(int64_t limit_ns, bvc_stream stream) {
+  return bvc::note_status(bvc_wait_selftest_impl(limit_ns, stream));
+}
 
-extern "C" bvc_status bvc_gather_status(uint64_t* flags, int32_t reset) {
+static bvc_status bvc_gather_status_impl(uint64_t* flags, int32_t reset) {
   if (flags == nullptr) return BVC_ERR_INVALID_ARG;
   unsigned long long h = 0;
   BVC_CUDA_TRY(cudaMemcpyFromSymbol(&h, g_gather_status, sizeof(h)));
@@ -849,6 +877,9 @@ extern "C" bvc_status bvc_gather_status(uint64_t* flags, int32_t reset) {
   }
   *flags = h;
   return (h & 1ull) ? BVC_ERR_TIMEOUT : BVC_OK;
+}
+extern "C" bvc_status bvc_gather_status(uint64_t* flags, int32_t reset) {
+  return bvc::note_status(bvc_gather_status_impl(flags, reset));
 }
 
 // ---------------------------------------------------------------------------
@@ -1163,7 +1194,7 @@ __global__ void __launch_bounds__(256) k_pack_adj_pts(const float* __restrict__ 
 
 }  // namespace bvc
 
-extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
+static bvc_status bvc_evaluate_multi_impl(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
                                          bvc_stream stream) {
   if (cache == nullptr || (cache->dim != 2 && cache->dim != 3) || cache->n < 1 || cache->k < 1 ||
       cache->packed == nullptr || m < 0 || (m > 0 && (pts == nullptr || u == nullptr)))
@@ -1183,8 +1214,12 @@ extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const flo
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
+                                         bvc_stream stream) {
+  return bvc::note_status(bvc_evaluate_multi_impl(cache, pts, m, u, stream));
+}
 
-extern "C" bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
+static bvc_status bvc_batch_evaluate_impl(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
                                          bvc_stream stream) {
   if (b == nullptr || cache == nullptr || cache->dim != b->dim || cache->n != b->n_total || cache->k != b->k ||
       cache->packed == nullptr || (b->m_total > 0 && (pts == nullptr || u == nullptr)))
@@ -1206,14 +1241,21 @@ extern "C" bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cac
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
+                                         bvc_stream stream) {
+  return bvc::note_status(bvc_batch_evaluate_impl(b, cache, pts, u, stream));
+}
 
-extern "C" bvc_status bvc_evaluate_adjoint_workspace_size(int64_t m, size_t* bytes) {
+static bvc_status bvc_evaluate_adjoint_workspace_size_impl(int64_t m, size_t* bytes) {
   if (m < 0 || bytes == nullptr) return BVC_ERR_INVALID_ARG;
   *bytes = 256 + (size_t)m * 16;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_evaluate_adjoint_workspace_size(int64_t m, size_t* bytes) {
+  return bvc::note_status(bvc_evaluate_adjoint_workspace_size_impl(m, bytes));
+}
 
-extern "C" bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* pts, int64_t m, const double* lam,
+static bvc_status bvc_evaluate_adjoint_impl(const bvc_cache* cache, const float* pts, int64_t m, const double* lam,
                                            double* adj_u, double* adj_q, double* adj_src, void* workspace,
                                            size_t workspace_bytes, bvc_stream stream) {
   if (cache == nullptr || (cache->dim != 2 && cache->dim != 3) || cache->n < 1 || cache->z == nullptr ||
@@ -1270,4 +1312,9 @@ extern "C" bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* 
     BVC_LAUNCH_CHECK();
   }
   return BVC_OK;
+}
+extern "C" bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* pts, int64_t m, const double* lam,
+                                           double* adj_u, double* adj_q, double* adj_src, void* workspace,
+                                           size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_evaluate_adjoint_impl(cache, pts, m, lam, adj_u, adj_q, adj_src, workspace, workspace_bytes, stream));
 }

@@ -10,7 +10,8 @@
 namespace bvc {
 
 int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::vector<float4>& nodes_out,
-                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out);
+                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out,
+                  std::vector<float4>* slabs_out = nullptr);
 
 // Measure and outward unit normal of element e in FP64 (Sec. 4 "Sampling":
 // elements are chosen in proportion to their measure).  This exact sequence
@@ -261,7 +262,7 @@ static int grid_for(int64_t n, int block) {
 
 using namespace bvc;
 
-extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
+static bvc_status bvc_geometry_create_impl(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
                                           int64_t n_prims, bvc_stream stream, bvc_geometry* out) {
   if (out == nullptr) return BVC_ERR_INVALID_ARG;
   *out = nullptr;
@@ -285,9 +286,9 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
     }
     cdf[e + 1] = cdf[e] + m;
   }
-  std::vector<float4> nodes, pr;
+  std::vector<float4> nodes, pr, slabs;
   std::vector<int32_t> ids;
-  const int64_t n_nodes = build_bvh(dim, verts, prims, n_prims, nodes, pr, ids);
+  const int64_t n_nodes = build_bvh(dim, verts, prims, n_prims, nodes, pr, ids, &slabs);
   std::vector<double> disp((size_t)n_verts * dim);
   const double reach = offset_disp(dim, verts, n_verts, prims, n_prims, nullptr, disp.data());
 
@@ -312,14 +313,18 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   diag = std::sqrt(diag);
 
   const size_t b_nodes = align256(nodes.size() * sizeof(float4));
+  const size_t b_slabs = align256(slabs.size() * sizeof(float4));
   const size_t b_prims = align256(pr.size() * sizeof(float4));
   const size_t b_cdf = align256(cdf.size() * sizeof(double));
   const size_t b_verts = align256((size_t)n_verts * dim * sizeof(float));
   const size_t b_idx = align256((size_t)n_prims * dim * sizeof(int32_t));
   const size_t b_disp = align256(disp.size() * sizeof(double));
   const size_t b_stats = 256;
-  g->arena_bytes = b_nodes + b_prims + b_cdf + b_verts + b_idx + b_disp + b_stats;
-  if (cudaMalloc(&g->arena, g->arena_bytes) != cudaSuccess) {
+  g->arena_bytes = b_nodes + b_slabs + b_prims + b_cdf + b_verts + b_idx + b_disp + b_stats;
+  // stream-ordered: the arena and its contents are ready for later work on
+  // `stream` (other streams synchronise with it first); nothing here waits
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMallocAsync(&g->arena, g->arena_bytes, s) != cudaSuccess) {
     (void)cudaGetLastError();
     delete g;
     return BVC_ERR_OOM;
@@ -327,7 +332,8 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
   char* base = (char*)g->arena;
   DevGeometry& d = g->dev;
   d.nodes = (const float4*)base;
-  d.prims = (const float4*)(base += b_nodes);
+  d.slabs = (const float4*)(base += b_nodes);
+  d.prims = (const float4*)(base += b_slabs);
   d.cdf = (const double*)(base += b_prims);
   d.verts = (const float*)(base += b_cdf);
   d.idx = (const int32_t*)(base += b_verts);
@@ -341,36 +347,49 @@ extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64
     d.lo[a] = g->lo[a];
     d.hi[a] = g->hi[a];
   }
-  cudaStream_t s = (cudaStream_t)stream;
+  // the caller's arrays are copied into pageable vectors first: a copy from
+  // pageable memory is staged before cudaMemcpyAsync returns, so the call
+  // reads the caller's memory during the call only, pinned or not
+  const std::vector<float> vcopy(verts, verts + n_verts * dim);
+  const std::vector<int32_t> icopy(prims, prims + n_prims * dim);
   bool ok = cudaMemcpyAsync((void*)d.nodes, nodes.data(), nodes.size() * sizeof(float4), cudaMemcpyHostToDevice, s) ==
+                cudaSuccess &&
+            cudaMemcpyAsync((void*)d.slabs, slabs.data(), slabs.size() * sizeof(float4), cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
             cudaMemcpyAsync((void*)d.prims, pr.data(), pr.size() * sizeof(float4), cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
             cudaMemcpyAsync((void*)d.cdf, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync((void*)d.verts, verts, (size_t)n_verts * dim * 4, cudaMemcpyHostToDevice, s) ==
+            cudaMemcpyAsync((void*)d.verts, vcopy.data(), (size_t)n_verts * dim * 4, cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
-            cudaMemcpyAsync((void*)d.idx, prims, (size_t)n_prims * dim * 4, cudaMemcpyHostToDevice, s) ==
+            cudaMemcpyAsync((void*)d.idx, icopy.data(), (size_t)n_prims * dim * 4, cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
             cudaMemcpyAsync((void*)d.disp, disp.data(), disp.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemsetAsync(d.stats, 0, b_stats, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+            cudaMemsetAsync(d.stats, 0, b_stats, s) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();
-    cudaFree(g->arena);
+    (void)cudaFreeAsync(g->arena, s);
     delete g;
     return BVC_ERR_CUDA;
   }
   *out = g;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_geometry_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
+                                          int64_t n_prims, bvc_stream stream, bvc_geometry* out) {
+  return bvc::note_status(bvc_geometry_create_impl(dim, verts, n_verts, prims, n_prims, stream, out));
+}
 
-extern "C" bvc_status bvc_geometry_destroy(bvc_geometry g) {
+static bvc_status bvc_geometry_destroy_impl(bvc_geometry g) {
   if (g == nullptr) return BVC_ERR_INVALID_ARG;
   const cudaError_t e = cudaFree(g->arena);
   delete g;
   return e == cudaSuccess ? BVC_OK : BVC_ERR_CUDA;
 }
+extern "C" bvc_status bvc_geometry_destroy(bvc_geometry g) {
+  return bvc::note_status(bvc_geometry_destroy_impl(g));
+}
 
-extern "C" bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* info) {
+static bvc_status bvc_geometry_get_info_impl(bvc_geometry g, bvc_geometry_info* info) {
   if (g == nullptr || info == nullptr) return BVC_ERR_INVALID_ARG;
   info->dim = g->dim;
   info->n_verts = g->n_verts;
@@ -385,14 +404,20 @@ extern "C" bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* i
   info->offset_reach = g->reach;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* info) {
+  return bvc::note_status(bvc_geometry_get_info_impl(g, info));
+}
 
-extern "C" bvc_status bvc_geometry_set_counting(bvc_geometry g, int32_t on) {
+static bvc_status bvc_geometry_set_counting_impl(bvc_geometry g, int32_t on) {
   if (g == nullptr) return BVC_ERR_INVALID_ARG;
   g->counting = on ? 1 : 0;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_geometry_set_counting(bvc_geometry g, int32_t on) {
+  return bvc::note_status(bvc_geometry_set_counting_impl(g, on));
+}
 
-extern "C" bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[8], int32_t reset, bvc_stream stream) {
+static bvc_status bvc_geometry_stats_impl(bvc_geometry g, uint64_t out[8], int32_t reset, bvc_stream stream) {
   if (g == nullptr || out == nullptr) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long h[8];
@@ -404,8 +429,11 @@ extern "C" bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[8], int32_
   if (h[kStatCapped]) return BVC_WARN_WALK_CAP;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[8], int32_t reset, bvc_stream stream) {
+  return bvc::note_status(bvc_geometry_stats_impl(g, out, reset, stream));
+}
 
-extern "C" bvc_status bvc_query_closest(bvc_geometry g, const float* pts, int64_t m, float* d2, int32_t* prim,
+static bvc_status bvc_query_closest_impl(bvc_geometry g, const float* pts, int64_t m, float* d2, int32_t* prim,
                                         float* cp, bvc_stream stream) {
   if (g == nullptr || m < 0 || (m > 0 && pts == nullptr)) return BVC_ERR_INVALID_ARG;
   if (m == 0) return BVC_OK;
@@ -418,8 +446,12 @@ extern "C" bvc_status bvc_query_closest(bvc_geometry g, const float* pts, int64_
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_query_closest(bvc_geometry g, const float* pts, int64_t m, float* d2, int32_t* prim,
+                                        float* cp, bvc_stream stream) {
+  return bvc::note_status(bvc_query_closest_impl(g, pts, m, d2, prim, cp, stream));
+}
 
-extern "C" bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_t m, float l, uint8_t* near,
+static bvc_status bvc_classify_near_impl(bvc_geometry g, const float* pts, int64_t m, float l, uint8_t* near,
                                         bvc_stream stream) {
   if (g == nullptr || m < 0 || (m > 0 && (pts == nullptr || near == nullptr)) || !(l >= 0.0f))
     return BVC_ERR_INVALID_ARG;
@@ -437,6 +469,10 @@ extern "C" bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_
                                                               near);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
+}
+extern "C" bvc_status bvc_classify_near(bvc_geometry g, const float* pts, int64_t m, float l, uint8_t* near,
+                                        bvc_stream stream) {
+  return bvc::note_status(bvc_classify_near_impl(g, pts, m, l, near, stream));
 }
 
 namespace bvc {
@@ -458,9 +494,13 @@ bvc_status launch_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t 
 }
 }  // namespace bvc
 
-extern "C" bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
+static bvc_status bvc_sample_boundary_impl(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
                                           float* jac, int32_t* elem, bvc_stream stream) {
   if (g == nullptr || n < 0 || (n > 0 && (z == nullptr || nrm == nullptr || jac == nullptr)) || !std::isfinite(l))
     return BVC_ERR_INVALID_ARG;
   return launch_sample_boundary(g, n, l, seed, z, nrm, jac, elem, n, (cudaStream_t)stream, nullptr);
+}
+extern "C" bvc_status bvc_sample_boundary(bvc_geometry g, int64_t n, double l, uint64_t seed, float* z, float* nrm,
+                                          float* jac, int32_t* elem, bvc_stream stream) {
+  return bvc::note_status(bvc_sample_boundary_impl(g, n, l, seed, z, nrm, jac, elem, stream));
 }

@@ -30,10 +30,15 @@ struct DevFunction {
 //  nodes: 2D 3 float4 per node  [L.lo.x L.lo.y L.hi.x L.hi.y] [R ...] [cl cr - -]
 //         3D 4 float4 per node  [L.lo.xyz L.hi.x] [L.hi.yz R.lo.xy] [R.lo.z R.hi.xyz] [cl cr - -]
 //         child >= 0: internal node; child < 0: leaf, ~child = first << 4 | count.
+//  slabs: per node, both children's slabs (unit normal n, dmin <= n.x <= dmax
+//         over the elements below; n = 0 unbounded): 2D 2 float4
+//         [n0 dmin0 dmax0] [n1 dmin1 dmax1]; 3D 3 float4
+//         [n0 dmin0] [dmax0 n1] [dmin1 dmax1 - -] (see bvh_build.cpp).
 //  prims: BVH order; 2D two float4 (a, ab) (1/|ab|^2, id, -, -); 3D three
 //         float4 (a, id) (ab, -) (ac, -); id = caller's element index (int bits).
 struct DevGeometry {
   const float4* nodes;
+  const float4* slabs;
   const float4* prims;
   const double* cdf;      // [n_prims + 1] FP64 prefix sums of element measures (caller order)
   const float* verts;     // [n_verts][dim] caller's vertices
@@ -102,6 +107,15 @@ namespace bvc {
 // max_v |m_v|.  (bvc_geometry.cu)
 double offset_disp(int dim, const float* V, int64_t nv, const int32_t* F, int64_t np, const uint8_t* fixed,
                    double* m);
+
+// The last status other than BVC_OK that an entry point returned on this
+// thread (bvc_last_error); every extern "C" entry point passes its result
+// through note_status.  (bvc_common.cu)
+extern thread_local bvc_status g_last_status;
+inline bvc_status note_status(bvc_status s) {
+  if (s != BVC_OK) g_last_status = s;
+  return s;
+}
 
 // Host helpers (bvc_common.cu)
 bool make_dev_function(const bvc_function* f, int dim, DevFunction* out);

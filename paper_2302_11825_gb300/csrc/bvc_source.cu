@@ -336,15 +336,18 @@ bvc_status bvc_source_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
-extern "C" bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes) {
+static bvc_status bvc_sample_source_workspace_size_impl(int64_t n_cand, size_t* bytes) {
   if (n_cand < 0 || bytes == nullptr) return BVC_ERR_INVALID_ARG;
   const int64_t nb = (n_cand + kSrcBlock - 1) / kSrcBlock;
   *bytes = al256((size_t)n_cand * 3 * sizeof(float)) + al256((size_t)n_cand) + 2 * al256((size_t)nb * 8) +
            al256((size_t)n_cand * kMaxSlices * sizeof(float));
   return BVC_OK;
 }
+extern "C" bvc_status bvc_sample_source_workspace_size(int64_t n_cand, size_t* bytes) {
+  return bvc::note_status(bvc_sample_source_workspace_size_impl(n_cand, bytes));
+}
 
-extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[3], uint64_t seed,
+static bvc_status bvc_sample_source_impl(bvc_geometry g, const bvc_function* ffn, const int32_t grid[3], uint64_t seed,
                                         double offset_l, bvc_cache* cache, void* workspace, size_t workspace_bytes,
                                         bvc_stream stream) {
   if (g == nullptr || grid == nullptr || cache == nullptr || !std::isfinite(offset_l) || offset_l < 0.0)
@@ -417,4 +420,9 @@ extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn,
   }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
+}
+extern "C" bvc_status bvc_sample_source(bvc_geometry g, const bvc_function* ffn, const int32_t grid[3], uint64_t seed,
+                                        double offset_l, bvc_cache* cache, void* workspace, size_t workspace_bytes,
+                                        bvc_stream stream) {
+  return bvc::note_status(bvc_sample_source_impl(g, ffn, grid, seed, offset_l, cache, workspace, workspace_bytes, stream));
 }

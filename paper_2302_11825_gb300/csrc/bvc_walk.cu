@@ -304,21 +304,7 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
         if (CNT) ++my_nodes;
         int32_t cl, cr;
         float dl, dr;
-        if (D == 2) {
-          const float4 L = __ldg(&G.nodes[3 * cur]), R = __ldg(&G.nodes[3 * cur + 1]);
-          const float4 C = __ldg(&G.nodes[3 * cur + 2]);
-          dl = box_d2_2(L.x, L.y, L.z, L.w, x);
-          dr = box_d2_2(R.x, R.y, R.z, R.w, x);
-          cl = __float_as_int(C.x);
-          cr = __float_as_int(C.y);
-        } else {
-          const float4 a = __ldg(&G.nodes[4 * cur]), b = __ldg(&G.nodes[4 * cur + 1]);
-          const float4 c = __ldg(&G.nodes[4 * cur + 2]), e = __ldg(&G.nodes[4 * cur + 3]);
-          dl = box_d2_3(a.x, a.y, a.z, a.w, b.x, b.y, x);
-          dr = box_d2_3(b.z, b.w, c.x, c.y, c.z, c.w, x);
-          cl = __float_as_int(e.x);
-          cr = __float_as_int(e.y);
-        }
+        node_bounds<D>(G, cur, x, dl, dr, cl, cr);
         if (dr < dl) {
           const int32_t tc = cl;
           cl = cr;
@@ -619,7 +605,7 @@ static bool valid_walk_args(float eps, int32_t max_steps, int32_t walks) {
 
 using namespace bvc;
 
-extern "C" bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* starts,
+static bvc_status bvc_walk_impl(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* starts,
                                const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps,
                                uint64_t seed, uint64_t id_base, uint32_t tag, float* rec, int32_t* steps,
                                int32_t* prim, bvc_stream stream) {
@@ -650,8 +636,14 @@ extern "C" bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bv
   return launch_walk(g->dim, P.f.n_terms > 0, nrm != nullptr ? kRecGn : kRecGrad, g->counting != 0, P,
                      (cudaStream_t)stream);
 }
+extern "C" bvc_status bvc_walk(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, const float* starts,
+                               const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps,
+                               uint64_t seed, uint64_t id_base, uint32_t tag, float* rec, int32_t* steps,
+                               int32_t* prim, bvc_stream stream) {
+  return bvc::note_status(bvc_walk_impl(g, gfn, ffn, starts, nrm, n, walks, eps, max_steps, seed, id_base, tag, rec, steps, prim, stream));
+}
 
-extern "C" bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walks, int32_t planes, int32_t mode,
+static bvc_status bvc_reduce_walks_impl(const float* rec, int64_t n, int32_t walks, int32_t planes, int32_t mode,
                                        double* out, bvc_stream stream) {
   if (rec == nullptr || out == nullptr || n < 0 || walks < 1 || planes < 0 || planes > 3 || (mode != 0 && mode != 1))
     return BVC_ERR_INVALID_ARG;
@@ -665,6 +657,10 @@ extern "C" bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walk
   R.mode = mode;
   for (int p = 0; p < R.planes; ++p) R.out[p] = out + p * n;
   return launch_reduce(R, (cudaStream_t)stream);
+}
+extern "C" bvc_status bvc_reduce_walks(const float* rec, int64_t n, int32_t walks, int32_t planes, int32_t mode,
+                                       double* out, bvc_stream stream) {
+  return bvc::note_status(bvc_reduce_walks_impl(rec, n, walks, planes, mode, out, stream));
 }
 
 // Workspace layout for the chunked drivers: [0, 256) work counter, then the
@@ -682,7 +678,7 @@ static float* ws_records(void* ws, int64_t c, int dim) {
   return (float*)((char*)ws + off);
 }
 
-extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+static bvc_status bvc_cache_build_workspace_size_impl(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
                                                      size_t* full_bytes) {
   if (g == nullptr || opts == nullptr || opts->n_samples < 0 || opts->walks_per_sample < 1)
     return BVC_ERR_INVALID_ARG;
@@ -694,6 +690,10 @@ extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_c
   if (min_bytes) *min_bytes = mn > src ? mn : src;
   if (full_bytes) *full_bytes = full > src ? full : src;
   return BVC_OK;
+}
+extern "C" bvc_status bvc_cache_build_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+                                                     size_t* full_bytes) {
+  return bvc::note_status(bvc_cache_build_workspace_size_impl(g, opts, min_bytes, full_bytes));
 }
 
 // g: the domain's geometry (walks); gs: the geometry the samples lie on and
@@ -779,23 +779,38 @@ static bvc_status cache_build(bvc_geometry g, bvc_geometry gs, const bvc_functio
   return bvc_cache_pack(cache, stream);
 }
 
-extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+static bvc_status bvc_cache_build_impl(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
                                       const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
                                       size_t workspace_bytes, bvc_stream stream) {
   return cache_build(g, g, gfn, nullptr, ffn, opts, cache, workspace, workspace_bytes, stream);
 }
+extern "C" bvc_status bvc_cache_build(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                      const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
+                                      size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_cache_build_impl(g, gfn, ffn, opts, cache, workspace, workspace_bytes, stream));
+}
 
-extern "C" bvc_status bvc_cache_build_region(bvc_geometry domain, bvc_geometry region, const bvc_function* gfn,
+static bvc_status bvc_cache_build_region_impl(bvc_geometry domain, bvc_geometry region, const bvc_function* gfn,
                                              const bvc_function* ffn, const bvc_cache_opts* opts, bvc_cache* cache,
                                              void* workspace, size_t workspace_bytes, bvc_stream stream) {
   return cache_build(domain, region, gfn, nullptr, ffn, opts, cache, workspace, workspace_bytes, stream);
 }
+extern "C" bvc_status bvc_cache_build_region(bvc_geometry domain, bvc_geometry region, const bvc_function* gfn,
+                                             const bvc_function* ffn, const bvc_cache_opts* opts, bvc_cache* cache,
+                                             void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_cache_build_region_impl(domain, region, gfn, ffn, opts, cache, workspace, workspace_bytes, stream));
+}
 
-extern "C" bvc_status bvc_cache_build_vg(bvc_geometry g, const float* g_vertex, const bvc_function* ffn,
+static bvc_status bvc_cache_build_vg_impl(bvc_geometry g, const float* g_vertex, const bvc_function* ffn,
                                          const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
                                          size_t workspace_bytes, bvc_stream stream) {
   if (g_vertex == nullptr) return BVC_ERR_INVALID_ARG;
   return cache_build(g, g, nullptr, g_vertex, ffn, opts, cache, workspace, workspace_bytes, stream);
+}
+extern "C" bvc_status bvc_cache_build_vg(bvc_geometry g, const float* g_vertex, const bvc_function* ffn,
+                                         const bvc_cache_opts* opts, bvc_cache* cache, void* workspace,
+                                         size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_cache_build_vg_impl(g, g_vertex, ffn, opts, cache, workspace, workspace_bytes, stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -842,7 +857,7 @@ static bool diff_source_ok(const bvc_function* ffn, int dim) {
   return t.n_coeffs >= 1 && (t.n_coeffs - 1) % (1 + dim) == 0 && (t.n_coeffs - 1) / (1 + dim) <= kMaxBumps;
 }
 
-extern "C" bvc_status bvc_cache_adjoint_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+static bvc_status bvc_cache_adjoint_workspace_size_impl(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
                                                        size_t* full_bytes) {
   if (g == nullptr || opts == nullptr || opts->n_samples < 1 || opts->walks_per_sample < 1) return BVC_ERR_INVALID_ARG;
   const size_t per = ws_per_start(g->dim, opts->walks_per_sample, 0);
@@ -850,8 +865,12 @@ extern "C" bvc_status bvc_cache_adjoint_workspace_size(bvc_geometry g, const bvc
   if (full_bytes) *full_bytes = 2 * kWsHead + per * (size_t)opts->n_samples;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_cache_adjoint_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+                                                       size_t* full_bytes) {
+  return bvc::note_status(bvc_cache_adjoint_workspace_size_impl(g, opts, min_bytes, full_bytes));
+}
 
-extern "C" bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache_opts* opts,
+static bvc_status bvc_cache_adjoint_impl(bvc_geometry g, const bvc_function* ffn, const bvc_cache_opts* opts,
                                         const bvc_cache* cache, const double* adj_u, const double* adj_q,
                                         const double* adj_src, double* grad_gv, double* grad_amp, void* workspace,
                                         size_t workspace_bytes, bvc_stream stream) {
@@ -913,6 +932,12 @@ extern "C" bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn,
     return bvc_source_adjoint(g, ffn, cache, adj_src, grad_amp, stream);
   return BVC_OK;
 }
+extern "C" bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_cache_opts* opts,
+                                        const bvc_cache* cache, const double* adj_u, const double* adj_q,
+                                        const double* adj_src, double* grad_gv, double* grad_amp, void* workspace,
+                                        size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_cache_adjoint_impl(g, ffn, opts, cache, adj_u, adj_q, adj_src, grad_gv, grad_amp, workspace, workspace_bytes, stream));
+}
 
 // ---------------------------------------------------------------------------
 // Walk launch autotuner.  A walk's result depends only on its id, never on
@@ -928,7 +953,7 @@ static int64_t tune_samples(const bvc_cache_opts* o) {
   return o->n_samples < kTuneSamples ? o->n_samples : kTuneSamples;
 }
 
-extern "C" bvc_status bvc_tune_walks_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* bytes) {
+static bvc_status bvc_tune_walks_workspace_size_impl(bvc_geometry g, const bvc_cache_opts* opts, size_t* bytes) {
   if (g == nullptr || opts == nullptr || bytes == nullptr || opts->n_samples < 1 || opts->walks_per_sample < 1)
     return BVC_ERR_INVALID_ARG;
   const int64_t n = tune_samples(opts);
@@ -936,15 +961,21 @@ extern "C" bvc_status bvc_tune_walks_workspace_size(bvc_geometry g, const bvc_ca
   *bytes = pts + 2 * kWsHead + ws_per_start(g->dim, opts->walks_per_sample, 1) * (size_t)n;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_tune_walks_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* bytes) {
+  return bvc::note_status(bvc_tune_walks_workspace_size_impl(g, opts, bytes));
+}
 
-extern "C" bvc_status bvc_geometry_set_walk_shape(bvc_geometry g, int32_t blocks_per_sm, int32_t chunk) {
+static bvc_status bvc_geometry_set_walk_shape_impl(bvc_geometry g, int32_t blocks_per_sm, int32_t chunk) {
   if (g == nullptr || blocks_per_sm < 0 || chunk < 0 || chunk > (1 << 20)) return BVC_ERR_INVALID_ARG;
   g->tune_blocks_per_sm = blocks_per_sm;
   g->tune_chunk = chunk;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_geometry_set_walk_shape(bvc_geometry g, int32_t blocks_per_sm, int32_t chunk) {
+  return bvc::note_status(bvc_geometry_set_walk_shape_impl(g, blocks_per_sm, chunk));
+}
 
-extern "C" bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+static bvc_status bvc_tune_walks_impl(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
                                      const bvc_cache_opts* opts, void* workspace, size_t workspace_bytes,
                                      bvc_stream stream, int32_t shape[2], float* best_ms) {
   size_t need = 0;
@@ -1029,6 +1060,11 @@ extern "C" bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, co
   if (best_ms) *best_ms = best;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_tune_walks(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                     const bvc_cache_opts* opts, void* workspace, size_t workspace_bytes,
+                                     bvc_stream stream, int32_t shape[2], float* best_ms) {
+  return bvc::note_status(bvc_tune_walks_impl(g, gfn, ffn, opts, workspace, workspace_bytes, stream, shape, best_ms));
+}
 
 namespace bvc {
 bvc_status walk_points_u(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, double sigma,
@@ -1068,7 +1104,7 @@ bvc_status walk_points_u(bvc_geometry g, const bvc_function* gfn, const bvc_func
 const float* walk_records_u(void* ws, int64_t c, int dim) { return ws_records(ws, c, dim); }
 }  // namespace bvc
 
-extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
+static bvc_status wos_estimate_workspace_size_impl(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
                                                   size_t* full_bytes) {
   if ((dim != 2 && dim != 3) || m < 0 || walks < 1) return BVC_ERR_INVALID_ARG;
   const size_t per_pt = ws_per_start(dim, walks, dim);
@@ -1076,12 +1112,16 @@ extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_
   if (full_bytes) *full_bytes = 2 * kWsHead + per_pt * (size_t)m;
   return BVC_OK;
 }
+extern "C" bvc_status wos_estimate_workspace_size(int32_t dim, int64_t m, int32_t walks, size_t* min_bytes,
+                                                  size_t* full_bytes) {
+  return bvc::note_status(wos_estimate_workspace_size_impl(dim, m, walks, min_bytes, full_bytes));
+}
 
 __global__ void k_add_walk_count(int64_t* counts, int64_t w) {
   if (threadIdx.x == 0 && blockIdx.x == 0) counts[0] += w;
 }
 
-extern "C" bvc_status wos_estimate_sigma(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+static bvc_status wos_estimate_sigma_impl(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
                                          double sigma, bvc_eval_state* state, int32_t walks, float eps,
                                          int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
                                          size_t workspace_bytes, bvc_stream stream) {
@@ -1147,12 +1187,23 @@ extern "C" bvc_status wos_estimate_sigma(bvc_geometry g, const bvc_function* gfn
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status wos_estimate_sigma(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                         double sigma, bvc_eval_state* state, int32_t walks, float eps,
+                                         int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
+                                         size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(wos_estimate_sigma_impl(g, gfn, ffn, sigma, state, walks, eps, max_steps, seed, id_base, workspace, workspace_bytes, stream));
+}
 
-extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+static bvc_status wos_estimate_impl(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
                                    bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
                                    uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream) {
   return wos_estimate_sigma(g, gfn, ffn, 0.0, state, walks, eps, max_steps, seed, id_base, workspace,
                             workspace_bytes, stream);
+}
+extern "C" bvc_status wos_estimate(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                   bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
+                                   uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(wos_estimate_impl(g, gfn, ffn, state, walks, eps, max_steps, seed, id_base, workspace, workspace_bytes, stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -1429,7 +1480,7 @@ static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void*
 
 extern "C" int32_t bvc_poly_terms(int32_t dim) { return dim == 2 ? 15 : (dim == 3 ? 35 : 0); }
 
-extern "C" bvc_status bvc_multi_cache_build_workspace_size(bvc_geometry g, int64_t n, int32_t walks,
+static bvc_status bvc_multi_cache_build_workspace_size_impl(bvc_geometry g, int64_t n, int32_t walks,
                                                            size_t* min_bytes, size_t* full_bytes) {
   if (g == nullptr || n < 1 || walks < 1) return BVC_ERR_INVALID_ARG;
   const size_t per = ws_per_start(g->dim, walks, g->dim);
@@ -1437,8 +1488,12 @@ extern "C" bvc_status bvc_multi_cache_build_workspace_size(bvc_geometry g, int64
   if (full_bytes) *full_bytes = 2 * kWsHead + per * (size_t)n;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_multi_cache_build_workspace_size(bvc_geometry g, int64_t n, int32_t walks,
+                                                           size_t* min_bytes, size_t* full_bytes) {
+  return bvc::note_status(bvc_multi_cache_build_workspace_size_impl(g, n, walks, min_bytes, full_bytes));
+}
 
-extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs, const bvc_cache_opts* opts,
+static bvc_status bvc_multi_cache_build_impl(bvc_geometry g, const double* coeffs, const bvc_cache_opts* opts,
                                             bvc_multi_cache* cache, void* workspace, size_t workspace_bytes,
                                             bvc_stream stream) {
   if (g == nullptr || opts == nullptr || coeffs == nullptr || workspace == nullptr) return BVC_ERR_INVALID_ARG;
@@ -1471,11 +1526,19 @@ extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs
   if (st != BVC_OK) return st;
   return launch_project(coeffs, cache, s);
 }
+extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs, const bvc_cache_opts* opts,
+                                            bvc_multi_cache* cache, void* workspace, size_t workspace_bytes,
+                                            bvc_stream stream) {
+  return bvc::note_status(bvc_multi_cache_build_impl(g, coeffs, opts, cache, workspace, workspace_bytes, stream));
+}
 
-extern "C" bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_cache* cache, bvc_stream stream) {
+static bvc_status bvc_multi_cache_project_impl(const double* coeffs, bvc_multi_cache* cache, bvc_stream stream) {
   if (coeffs == nullptr || cache == nullptr || (cache->dim != 2 && cache->dim != 3) || !valid_multi(cache, cache->dim))
     return BVC_ERR_INVALID_ARG;
   return launch_project(coeffs, cache, (cudaStream_t)stream);
+}
+extern "C" bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_cache* cache, bvc_stream stream) {
+  return bvc::note_status(bvc_multi_cache_project_impl(coeffs, cache, stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -1486,15 +1549,18 @@ static bool valid_batch_cache(const bvc_batch_s* b, const bvc_multi_cache* c) {
   return b != nullptr && valid_multi(c, b->dim) && c->n == b->n_total && c->k == b->k;
 }
 
-extern "C" bvc_status bvc_batch_build_workspace_size(bvc_batch b, size_t* min_bytes, size_t* full_bytes) {
+static bvc_status bvc_batch_build_workspace_size_impl(bvc_batch b, size_t* min_bytes, size_t* full_bytes) {
   if (b == nullptr) return BVC_ERR_INVALID_ARG;
   const size_t per = ws_per_start(b->dim, b->walks, b->dim);
   if (min_bytes) *min_bytes = 2 * kWsHead + per;
   if (full_bytes) *full_bytes = 2 * kWsHead + per * (size_t)b->n_total;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_batch_build_workspace_size(bvc_batch b, size_t* min_bytes, size_t* full_bytes) {
+  return bvc::note_status(bvc_batch_build_workspace_size_impl(b, min_bytes, full_bytes));
+}
 
-extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, const uint64_t* seed, bvc_multi_cache* cache,
+static bvc_status bvc_batch_build_impl(bvc_batch b, const double* coeffs, const uint64_t* seed, bvc_multi_cache* cache,
                                       void* workspace, size_t workspace_bytes, bvc_stream stream) {
   if (coeffs == nullptr || seed == nullptr || workspace == nullptr || !valid_batch_cache(b, cache))
     return BVC_ERR_INVALID_ARG;
@@ -1527,11 +1593,19 @@ extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, const u
   if (st != BVC_OK) return st;
   return launch_project(coeffs, cache, s, b->sample_mesh, b->table);
 }
+extern "C" bvc_status bvc_batch_build(bvc_batch b, const double* coeffs, const uint64_t* seed, bvc_multi_cache* cache,
+                                      void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_batch_build_impl(b, coeffs, seed, cache, workspace, workspace_bytes, stream));
+}
 
-extern "C" bvc_status bvc_batch_project(bvc_batch b, const double* coeffs, bvc_multi_cache* cache,
+static bvc_status bvc_batch_project_impl(bvc_batch b, const double* coeffs, bvc_multi_cache* cache,
                                         bvc_stream stream) {
   if (coeffs == nullptr || !valid_batch_cache(b, cache)) return BVC_ERR_INVALID_ARG;
   return launch_project(coeffs, cache, (cudaStream_t)stream, b->sample_mesh, b->table);
+}
+extern "C" bvc_status bvc_batch_project(bvc_batch b, const double* coeffs, bvc_multi_cache* cache,
+                                        bvc_stream stream) {
+  return bvc::note_status(bvc_batch_project_impl(b, coeffs, cache, stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -1569,7 +1643,7 @@ bvc_status static_scratch_address(void** out) {
 }
 }  // namespace
 
-extern "C" bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+static bvc_status wos_estimate_static_scratch_impl(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
                                                   bvc_eval_state* state, int32_t walks, float eps,
                                                   int32_t max_steps, uint64_t seed, uint64_t id_base,
                                                   bvc_stream stream) {
@@ -1582,4 +1656,10 @@ extern "C" bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_func
   const bvc_status st = static_scratch_address(&scratch);
   if (st != BVC_OK) return st;
   return wos_estimate(g, gfn, ffn, state, walks, eps, max_steps, seed, id_base, scratch, kStaticScratchBytes, stream);
+}
+extern "C" bvc_status wos_estimate_static_scratch(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn,
+                                                  bvc_eval_state* state, int32_t walks, float eps,
+                                                  int32_t max_steps, uint64_t seed, uint64_t id_base,
+                                                  bvc_stream stream) {
+  return bvc::note_status(wos_estimate_static_scratch_impl(g, gfn, ffn, state, walks, eps, max_steps, seed, id_base, stream));
 }

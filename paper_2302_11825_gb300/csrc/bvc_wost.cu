@@ -23,7 +23,8 @@
 namespace bvc {
 
 int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::vector<float4>& nodes_out,
-                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out);
+                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out,
+                  std::vector<float4>* slabs_out = nullptr);
 
 // Silhouette candidates in BVH order.
 //  2D two float4:  (v.x, v.y, n0.x, n0.y) (n1.x, n1.y, always, -)
@@ -1142,7 +1143,7 @@ static bool valid_walk(float eps, int32_t max_steps, int32_t walks) {
 
 using namespace bvc;
 
-extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
+static bvc_status bvc_mixed_create_impl(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
                                        int64_t n_prims, const uint8_t* neumann, bvc_stream stream, bvc_mixed* out) {
   if (out == nullptr) return BVC_ERR_INVALID_ARG;
   *out = nullptr;
@@ -1313,7 +1314,7 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   offset_disp(dim, verts, n_verts, prims, n_prims, fl.data(), dsp.data());
   const size_t b_disp = al256(dsp.size() * sizeof(double));
   m->arena_bytes = b_nodes + b_prims + b_dir + b_loc + b_flag + b_nm + b_nq + b_cone + b_disp;
-  if (cudaMalloc(&m->arena, m->arena_bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&m->arena, m->arena_bytes, (cudaStream_t)stream) != cudaSuccess) {
     (void)cudaGetLastError();
     m->arena = nullptr;
     return fail(BVC_ERR_OOM);
@@ -1353,7 +1354,6 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   if (!scones.empty())
     ok = ok && cudaMemcpyAsync((void*)m->sil.cones, scones.data(), scones.size() * sizeof(float4),
                                cudaMemcpyHostToDevice, s) == cudaSuccess;
-  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();
     return fail(BVC_ERR_CUDA);
@@ -1361,8 +1361,12 @@ extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t 
   *out = m;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_mixed_create(int32_t dim, const float* verts, int64_t n_verts, const int32_t* prims,
+                                       int64_t n_prims, const uint8_t* neumann, bvc_stream stream, bvc_mixed* out) {
+  return bvc::note_status(bvc_mixed_create_impl(dim, verts, n_verts, prims, n_prims, neumann, stream, out));
+}
 
-extern "C" bvc_status bvc_mixed_destroy(bvc_mixed m) {
+static bvc_status bvc_mixed_destroy_impl(bvc_mixed m) {
   if (m == nullptr) return BVC_ERR_INVALID_ARG;
   bvc_status st = BVC_OK;
   if (bvc_geometry_destroy(m->whole) != BVC_OK) st = BVC_ERR_CUDA;
@@ -1372,8 +1376,11 @@ extern "C" bvc_status bvc_mixed_destroy(bvc_mixed m) {
   delete m;
   return st;
 }
+extern "C" bvc_status bvc_mixed_destroy(bvc_mixed m) {
+  return bvc::note_status(bvc_mixed_destroy_impl(m));
+}
 
-extern "C" bvc_status bvc_mixed_get_info(bvc_mixed m, bvc_mixed_info* info) {
+static bvc_status bvc_mixed_get_info_impl(bvc_mixed m, bvc_mixed_info* info) {
   if (m == nullptr || info == nullptr) return BVC_ERR_INVALID_ARG;
   info->dim = m->dim;
   info->n_dirichlet = m->n_dir;
@@ -1385,20 +1392,30 @@ extern "C" bvc_status bvc_mixed_get_info(bvc_mixed m, bvc_mixed_info* info) {
   info->device_bytes = m->arena_bytes;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_mixed_get_info(bvc_mixed m, bvc_mixed_info* info) {
+  return bvc::note_status(bvc_mixed_get_info_impl(m, info));
+}
 
-extern "C" bvc_status bvc_mixed_set_silhouette_gap(bvc_mixed m, double gap) {
+static bvc_status bvc_mixed_set_silhouette_gap_impl(bvc_mixed m, double gap) {
   if (m == nullptr || !(gap >= 0.0 && gap < 1.0)) return BVC_ERR_INVALID_ARG;
   m->sil.shrink2 = (float)((1.0 - gap) * (1.0 - gap));
   return BVC_OK;
 }
+extern "C" bvc_status bvc_mixed_set_silhouette_gap(bvc_mixed m, double gap) {
+  return bvc::note_status(bvc_mixed_set_silhouette_gap_impl(m, gap));
+}
 
-extern "C" bvc_status bvc_mixed_geometries(bvc_mixed m, bvc_geometry* whole, bvc_geometry* dirichlet,
+static bvc_status bvc_mixed_geometries_impl(bvc_mixed m, bvc_geometry* whole, bvc_geometry* dirichlet,
                                            bvc_geometry* neumann) {
   if (m == nullptr) return BVC_ERR_INVALID_ARG;
   if (whole) *whole = m->whole;
   if (dirichlet) *dirichlet = m->dir;
   if (neumann) *neumann = m->neu;
   return BVC_OK;
+}
+extern "C" bvc_status bvc_mixed_geometries(bvc_mixed m, bvc_geometry* whole, bvc_geometry* dirichlet,
+                                           bvc_geometry* neumann) {
+  return bvc::note_status(bvc_mixed_geometries_impl(m, whole, dirichlet, neumann));
 }
 
 static int small_grid(int64_t n) {
@@ -1408,7 +1425,7 @@ static int small_grid(int64_t n) {
   return (int)(g > 0 ? g : 1);
 }
 
-extern "C" bvc_status bvc_mixed_query(bvc_mixed m, const float* pts, int64_t n, float* d_dir, float* d_sil,
+static bvc_status bvc_mixed_query_impl(bvc_mixed m, const float* pts, int64_t n, float* d_dir, float* d_sil,
                                       bvc_stream stream) {
   if (m == nullptr || n < 0 || (n > 0 && pts == nullptr)) return BVC_ERR_INVALID_ARG;
   if (n == 0) return BVC_OK;
@@ -1421,8 +1438,12 @@ extern "C" bvc_status bvc_mixed_query(bvc_mixed m, const float* pts, int64_t n, 
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_mixed_query(bvc_mixed m, const float* pts, int64_t n, float* d_dir, float* d_sil,
+                                      bvc_stream stream) {
+  return bvc::note_status(bvc_mixed_query_impl(m, pts, n, d_dir, d_sil, stream));
+}
 
-extern "C" bvc_status bvc_mixed_rays(bvc_mixed m, const float* org, const float* dir, const int32_t* skip, int64_t n,
+static bvc_status bvc_mixed_rays_impl(bvc_mixed m, const float* org, const float* dir, const int32_t* skip, int64_t n,
                                      float tmax, float* t, int32_t* elem, bvc_stream stream) {
   if (m == nullptr || n < 0 || !(tmax > 0.0f) ||
       (n > 0 && (org == nullptr || dir == nullptr || t == nullptr || elem == nullptr)))
@@ -1438,8 +1459,12 @@ extern "C" bvc_status bvc_mixed_rays(bvc_mixed m, const float* org, const float*
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
+extern "C" bvc_status bvc_mixed_rays(bvc_mixed m, const float* org, const float* dir, const int32_t* skip, int64_t n,
+                                     float tmax, float* t, int32_t* elem, bvc_stream stream) {
+  return bvc::note_status(bvc_mixed_rays_impl(m, org, dir, skip, n, tmax, t, elem, stream));
+}
 
-extern "C" bvc_status bvc_mixed_walk(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+static bvc_status bvc_mixed_walk_impl(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
                                      const bvc_function* ffn, const float* starts, const int32_t* start_elem,
                                      const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps,
                                      uint64_t seed, uint64_t id_base, uint32_t tag, float* rec, int32_t* steps,
@@ -1468,12 +1493,19 @@ extern "C" bvc_status bvc_mixed_walk(bvc_mixed m, const bvc_function* gfn, const
   P.counter = counter;
   return launch_wost(m->dim, nrm != nullptr ? kRecGnW : kRecGradW, P, (cudaStream_t)stream);
 }
+extern "C" bvc_status bvc_mixed_walk(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+                                     const bvc_function* ffn, const float* starts, const int32_t* start_elem,
+                                     const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps,
+                                     uint64_t seed, uint64_t id_base, uint32_t tag, float* rec, int32_t* steps,
+                                     int32_t* prim, unsigned long long* counter, bvc_stream stream) {
+  return bvc::note_status(bvc_mixed_walk_impl(m, gfn, h, ffn, starts, start_elem, nrm, n, walks, eps, max_steps, seed, id_base, tag, rec, steps, prim, counter, stream));
+}
 
 // Workspace of the mixed cache: [0, 256) work counter, the samples' elements
 // (int32[N]), then the chunk's walk records (2 planes).
 static size_t mixed_head(int64_t N) { return 256 + al256((size_t)N * 4); }
 
-extern "C" bvc_status bvc_mixed_cache_build_workspace_size(bvc_mixed m, const bvc_cache_opts* opts, size_t* min_bytes,
+static bvc_status bvc_mixed_cache_build_workspace_size_impl(bvc_mixed m, const bvc_cache_opts* opts, size_t* min_bytes,
                                                            size_t* full_bytes) {
   if (m == nullptr || opts == nullptr || opts->n_samples < 0 || opts->walks_per_sample < 1)
     return BVC_ERR_INVALID_ARG;
@@ -1487,8 +1519,12 @@ extern "C" bvc_status bvc_mixed_cache_build_workspace_size(bvc_mixed m, const bv
   if (full_bytes) *full_bytes = full > src ? full : src;
   return BVC_OK;
 }
+extern "C" bvc_status bvc_mixed_cache_build_workspace_size(bvc_mixed m, const bvc_cache_opts* opts, size_t* min_bytes,
+                                                           size_t* full_bytes) {
+  return bvc::note_status(bvc_mixed_cache_build_workspace_size_impl(m, opts, min_bytes, full_bytes));
+}
 
-extern "C" bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+static bvc_status bvc_mixed_cache_build_impl(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
                                             const bvc_function* ffn, const bvc_cache_opts* opts, bvc_cache* cache,
                                             void* workspace, size_t workspace_bytes, bvc_stream stream) {
   if (m == nullptr || opts == nullptr || cache == nullptr) return BVC_ERR_INVALID_ARG;
@@ -1556,8 +1592,13 @@ extern "C" bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn
   }
   return bvc_cache_pack(cache, stream);
 }
+extern "C" bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+                                            const bvc_function* ffn, const bvc_cache_opts* opts, bvc_cache* cache,
+                                            void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(bvc_mixed_cache_build_impl(m, gfn, h, ffn, opts, cache, workspace, workspace_bytes, stream));
+}
 
-extern "C" bvc_status wost_estimate(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+static bvc_status wost_estimate_impl(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
                                     const bvc_function* ffn, bvc_eval_state* state, int32_t walks, float eps,
                                     int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
                                     size_t workspace_bytes, bvc_stream stream) {
@@ -1612,4 +1653,10 @@ extern "C" bvc_status wost_estimate(bvc_mixed m, const bvc_function* gfn, const 
   }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
+}
+extern "C" bvc_status wost_estimate(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+                                    const bvc_function* ffn, bvc_eval_state* state, int32_t walks, float eps,
+                                    int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
+                                    size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(wost_estimate_impl(m, gfn, h, ffn, state, walks, eps, max_steps, seed, id_base, workspace, workspace_bytes, stream));
 }

@@ -10,6 +10,17 @@
 // flattened in depth-first order (a parent precedes its children) with both
 // child boxes stored in the parent, so one node fetch (48 B in 2D, 64 B in
 // 3D, 16-byte vector loads) decides the visiting order of both children.
+//
+// Each child also gets a slab: the unit vector n of its elements' summed
+// (length- or area-weighted) outward normals and the interval [dmin, dmax]
+// of n . v over its vertices, rounded outward.  A point's distance to the
+// child's elements is at least max(box distance, distance to the slab), and
+// for a patch of a smooth surface the slab is far thinner than the box, so
+// closest-point queries near the surface visit fewer nodes.  A child whose
+// normals cancel (|sum n| < sum |n| / 2) gets an unbounded slab.  Slabs live
+// in a separate array, 2 float4 (2D) or 3 float4 (3D) per node:
+//   2D [n0.x n0.y dmin0 dmax0] [n1.x n1.y dmin1 dmax1]
+//   3D [n0.x n0.y n0.z dmin0] [dmax0 n1.x n1.y n1.z] [dmin1 dmax1 - -]
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -75,6 +86,79 @@ struct Builder {
   std::vector<int32_t> order;
   std::vector<float4> nodes;
   int per_node;
+  std::vector<float4> slabs;
+  const float* V = nullptr;
+  const int32_t* F = nullptr;
+
+  struct Slab {
+    float n[3], dmin, dmax;
+  };
+  // Slab of the elements order[start .. start + count).
+  Slab slab_of(int64_t start, int64_t count) const {
+    double S[3] = {0, 0, 0}, A = 0.0;
+    for (int64_t i = start; i < start + count; ++i) {
+      const int32_t* f = F + (int64_t)order[i] * dim;
+      double c[3] = {0, 0, 0};
+      if (dim == 2) {
+        c[0] = (double)V[2 * f[1] + 1] - V[2 * f[0] + 1];
+        c[1] = -((double)V[2 * f[1]] - V[2 * f[0]]);
+      } else {
+        double e1[3], e2[3];
+        for (int a = 0; a < 3; ++a) {
+          e1[a] = (double)V[3 * f[1] + a] - V[3 * f[0] + a];
+          e2[a] = (double)V[3 * f[2] + a] - V[3 * f[0] + a];
+        }
+        c[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        c[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        c[2] = e1[0] * e2[1] - e1[1] * e2[0];
+      }
+      for (int a = 0; a < 3; ++a) S[a] += c[a];
+      A += std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    }
+    Slab sl;
+    const double L = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    if (!(L > 0.5 * A) || !(L > 0.0)) {
+      sl.n[0] = sl.n[1] = sl.n[2] = 0.0f;
+      sl.dmin = -3.0e38f;
+      sl.dmax = 3.0e38f;
+      return sl;
+    }
+    for (int a = 0; a < 3; ++a) sl.n[a] = (float)(S[a] / L);
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = start; i < start + count; ++i) {
+      const int32_t* f = F + (int64_t)order[i] * dim;
+      for (int v = 0; v < dim; ++v) {
+        double d = 0.0;
+        for (int a = 0; a < dim; ++a) d += (double)sl.n[a] * V[(int64_t)f[v] * dim + a];
+        lo = std::min(lo, d);
+        hi = std::max(hi, d);
+      }
+    }
+    // outward by a relative 2^-20 of the coordinates' scale (the device's
+    // FP32 dot product is far more accurate than that)
+    double sc = 0.0;
+    for (int64_t i = start; i < start + count; ++i) {
+      const int32_t* f = F + (int64_t)order[i] * dim;
+      for (int v = 0; v < dim; ++v)
+        for (int a = 0; a < dim; ++a) sc = std::max(sc, (double)std::fabs(V[(int64_t)f[v] * dim + a]));
+    }
+    const double pad = std::ldexp(sc, -20);
+    sl.dmin = std::nextafter((float)(lo - pad), -INFINITY);
+    sl.dmax = std::nextafter((float)(hi + pad), INFINITY);
+    return sl;
+  }
+
+  void write_slabs(int64_t id, const Slab& L, const Slab& R) {
+    float4* q = &slabs[id * (dim == 2 ? 2 : 3)];
+    if (dim == 2) {
+      q[0] = make_float4(L.n[0], L.n[1], L.dmin, L.dmax);
+      q[1] = make_float4(R.n[0], R.n[1], R.dmin, R.dmax);
+    } else {
+      q[0] = make_float4(L.n[0], L.n[1], L.n[2], L.dmin);
+      q[1] = make_float4(L.dmax, R.n[0], R.n[1], R.n[2]);
+      q[2] = make_float4(R.dmin, R.dmax, 0.0f, 0.0f);
+    }
+  }
 
   static int32_t leaf(int64_t first, int64_t count) { return ~(int32_t)((first << 4) | count); }
 
@@ -168,10 +252,12 @@ struct Builder {
     if (mid < 0) mid = median_split(start, count, cb);
     const int64_t id = (int64_t)nodes.size() / per_node;
     nodes.resize(nodes.size() + per_node);
+    slabs.resize(slabs.size() + (dim == 2 ? 2 : 3));
     Box bl, br;
     const int32_t cl = build(start, mid - start, depth + 1, bl);
     const int32_t cr = build(mid, start + count - mid, depth + 1, br);
     write_node(id, bl, br, cl, cr);
+    write_slabs(id, slab_of(start, mid - start), slab_of(mid, start + count - mid));
     return (int32_t)id;
   }
 
@@ -198,9 +284,11 @@ struct Builder {
 // 3D: (a, id), (b - a, 0), (c - a, 0); id stored as int bits), ids_out:
 // caller's index per record.  Returns the node count.
 int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::vector<float4>& nodes_out,
-                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out) {
+                  std::vector<float4>& prims_out, std::vector<int32_t>& ids_out, std::vector<float4>* slabs_out) {
   Builder B;
   B.dim = dim;
+  B.V = V;
+  B.F = F;
   B.leaf_max = BVC_LEAF_MAX(dim);
   B.per_node = dim == 2 ? 3 : 4;
   B.pbox.resize(np);
@@ -223,10 +311,11 @@ int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::ve
   }
   // Root is always an internal node.
   B.nodes.resize(B.per_node);
+  B.slabs.resize(dim == 2 ? 2 : 3);
   Box bl, br;
   int32_t cl, cr;
+  int64_t mid = np;  // the root's split (np: one leaf child, the other empty)
   if (np <= B.leaf_max) {
-    Box dummy;
     cl = B.build(0, np, 1, bl);
     br.reset();
     cr = Builder::leaf(0, 0);
@@ -234,13 +323,15 @@ int64_t build_bvh(int dim, const float* V, const int32_t* F, int64_t np, std::ve
     Box cb;
     cb.reset();
     for (int64_t i = 0; i < np; ++i) cb.grow(&B.cen[3 * i]);
-    int64_t mid = B.sah_split(0, np, cb);
+    mid = B.sah_split(0, np, cb);
     if (mid < 0) mid = B.median_split(0, np, cb);
     cl = B.build(0, mid, 1, bl);
     cr = B.build(mid, np - mid, 1, br);
   }
   B.write_node(0, bl, br, cl, cr);
+  B.write_slabs(0, B.slab_of(0, mid), B.slab_of(mid, np - mid));
   nodes_out.swap(B.nodes);
+  if (slabs_out) slabs_out->swap(B.slabs);
   const int per_prim = dim == 2 ? 2 : 3;
   prims_out.assign(np * per_prim, make_float4(0, 0, 0, 0));
   ids_out.resize(np);

@@ -92,6 +92,25 @@ def test_entry_points_reject_null_handles(lib):
                             C.c_uint64(0), C.c_uint64(0), None, None, None, C.c_size_t(0), None) == 1
 
 
+def test_last_error_is_thread_local_and_cleared(lib):
+    import threading
+    lib.bvc_last_error.restype = C.c_int
+    lib.bvc_last_error()  # start clean
+    lib.bvc_query_closest.restype = C.c_int
+    assert lib.bvc_query_closest(None, None, C.c_int64(4), None, None, None, None) == 1
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(lib.bvc_last_error()))
+    t.start()
+    t.join()
+    assert seen == [0]                   # another thread saw no error
+    assert lib.bvc_last_error() == 1     # this thread's last error (invalid argument) ...
+    assert lib.bvc_last_error() == 0     # ... cleared by the read
+    mn, full = C.c_size_t(), C.c_size_t()
+    lib.wos_estimate_workspace_size.restype = C.c_int
+    assert lib.wos_estimate_workspace_size(2, C.c_int64(10), 4, C.byref(mn), C.byref(full)) == 0
+    assert lib.bvc_last_error() == 0     # successful calls leave it alone
+
+
 def test_workspace_size_queries_are_host_only(lib):
     lib.wos_estimate_workspace_size.restype = C.c_int
     mn, full = C.c_size_t(), C.c_size_t()
