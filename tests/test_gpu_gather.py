@@ -107,6 +107,38 @@ def test_gather_full_size_3d_sampled():
     assert np.all(np.isfinite(st.u_bnd.cpu().numpy()))
 
 
+def test_gather_full_size_2d_sampled():
+    # the 2D configuration's sizes: 65,536 boundary samples and 33,983 kept
+    # source samples against the 511,540 gathered points of the 1024^2 grid;
+    # the oracle checks 48 sampled points, the GPU computes all of them
+    w = wl.star_poisson()
+    geom = bvc.Geometry(w.V, w.F)
+    near = bvc.classify_near(geom, bvc.soa(w.eval_pts), w.offset_l).cpu().numpy().astype(bool)
+    pts = w.eval_pts[~near]
+    rng = np.random.default_rng(8)
+    N = w.n_samples
+    z, n, _, jac = oracle.sample_boundary(w.V, w.F, N, w.offset_l, 2)
+    y, cw, ncand = oracle.sample_source2d(w.V, w.F, w.src_grid, 2, w.f, l=w.offset_l)
+    c = {"z": z.astype(np.float32).astype(np.float64), "n": n.astype(np.float32).astype(np.float64),
+         "jac": jac.astype(np.float32).astype(np.float64), "u_hat": rng.standard_normal(N),
+         "q_hat": rng.standard_normal(N), "measure": oracle.boundary_measure(w.V, w.F), "y": y, "c": cw,
+         "n_src": ncand, "N": N}
+    cache = _gpu_cache_from(c, 2, c["measure"])
+    st = bvc.EvalState(bvc.soa(pts))
+    bvc.evaluate(cache, st)
+    torch.cuda.synchronize()
+    sel = rng.choice(pts.shape[0], 48, replace=False)
+    ub, us, gb, gs, ab = oracle.gather(c["z"], c["n"], c["u_hat"], c["q_hat"], c["measure"], pts[sel], y, cw,
+                                       want_abs=True, jac=c["jac"])
+    eu = np.abs(st.u_bnd.cpu().numpy()[sel] - ub) / np.maximum(np.abs(ub), ab[:, 0])
+    eg = np.abs(st.grad_bnd.cpu().numpy().T[sel] - gb) / np.maximum(np.abs(gb), ab[:, 1:3])
+    es = np.abs(st.u_src.cpu().numpy()[sel] - us) / np.maximum(np.abs(us), ab[:, 3])
+    egs = np.abs(st.grad_src.cpu().numpy().T[sel] - gs) / np.maximum(np.abs(gs), ab[:, 4:6])
+    print(f"[gather full 2D] M={pts.shape[0]} N={N} Ms={y.shape[0]} u={eu.max():.2e} g={eg.max():.2e} "
+          f"u_src={es.max():.2e} g_src={egs.max():.2e}")
+    assert eu.max() < TOL and eg.max() < TOL and es.max() < TOL and egs.max() < TOL
+
+
 def test_progressive_accumulation_and_solution():
     w = wl.circle_laplace(n_samples=512, walks=8)
     c1 = oracle_cache(w.V, w.F, w.g, w.f, 512, 8, w.offset_l, w.eps, seed=11)
