@@ -250,10 +250,12 @@ def profile_traffic(kernel: str, workload: str):
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_hash") != kernel_source_hash(kernel):
         return None
-    try:
-        return float(vals["dram_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
-        return None
+    for key in ("dram_bytes_per_launch_full_size", "dram_bytes_per_step_full_size"):
+        try:
+            return float(vals[key])
+        except (KeyError, ValueError):
+            pass
+    return None
 
 
 def optional_part(fn):
@@ -328,6 +330,10 @@ class Solver:
         self.far = bvc.EvalState(self.far_pts)
         self.near = bvc.EvalState(self.near_pts)
         self.ws_eval = bvc.workspace(bvc.evaluate_workspace_size(self.cache, self.far))
+        # gather shape from the library's autotuner, on one cache of this
+        # workload (setup, not timed)
+        bvc.cache_build(self.geom, w.g, w.f, self.opts, self.cache, self.ws_cache)
+        self.gather_shape = bvc.tune_gather(self.cache, self.far, self.ws_eval)
         self.ws_wos = bvc.workspace(bvc.wos_workspace_size(w.dim, max(self.m_near, 1), w.walks)[1])
         self.u_far = torch.empty(self.m_far, dtype=torch.float64, device=device)
         self.g_far = torch.empty((w.dim, self.m_far), dtype=torch.float64, device=device)
@@ -1053,6 +1059,10 @@ class MixedSolver:
         self.far = bvc.EvalState(self.far_pts)
         self.near = bvc.EvalState(self.near_pts)
         self.ws_eval = bvc.workspace(bvc.evaluate_workspace_size(self.cache, self.far))
+        # gather shape from the library's autotuner, on one cache of this
+        # workload (setup, not timed)
+        bvc.mixed_cache_build(self.m, w.g, self.h, w.f, self.opts, self.cache, self.ws_cache)
+        self.gather_shape = bvc.tune_gather(self.cache, self.far, self.ws_eval)
         self.ws_wos = bvc.workspace(bvc.wos_workspace_size(w.dim, max(self.m_near, 1), self.near_walks)[1])
         self.u_far = torch.empty(self.m_far, dtype=torch.float64, device=device)
         self.g_far = torch.empty((w.dim, self.m_far), dtype=torch.float64, device=device)
@@ -1517,6 +1527,7 @@ def main():
     walk_gbs = walk_alg / (walk_ms_step / 1e3) / 1e9
     if dominant == "walk":
         peak = float(peaks["hbm_gbs"])
+        # achieved, traffic: per bench step, over its cache-walk and pointwise-walk launches
         roofline = {"bound": "hbm", "achieved": walk_gbs, "peak": peak, "unit": "GB/s", "frac": walk_gbs / peak,
                     "traffic": profile_traffic("walk", w.name), "kernel": "walk",
                     "peak_source": f"{peak_src} (hbm_gbs)",
@@ -1567,7 +1578,9 @@ def main():
                    "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}",
                    "sums": "fp64",
                    "walk_shape": {"blocks_per_sm": s.walk_shape[0], "chunk": s.walk_shape[1],
-                                  "tuned_ms": s.walk_shape[2]}},
+                                  "tuned_ms": s.walk_shape[2]},
+                   "gather_points_per_thread": {"boundary": s.gather_shape[0][0], "source": s.gather_shape[0][1],
+                                                "tuned_ms": s.gather_shape[1]}},
         "roofline": roofline,
         "kernels": kernels, "rooflines_all": extra,
         "wos_steps_per_s": (steps_cache + steps_near) / max(walk_ms_step / 1e3, 1e-12),

@@ -317,6 +317,24 @@ bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const bvc_eval_st
 bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state, void* workspace, size_t workspace_bytes,
                         bvc_stream stream);
 
+/* Gather autotuner (the gather's analogue of bvc_tune_walks): the gathers
+ * give each thread several evaluation points, every sample staged in shared
+ * memory serving all of them; more points per thread mean fewer shared
+ * loads per pair but more registers.  bvc_tune_gather times two launches of
+ * each supported count (2, 4, 6 for boundary samples, 2, 4 for sources) of
+ * this cache's gathers at the points of `state` (CUDA events on `stream`;
+ * synchronous, so not for stream capture), keeps the fastest for all later
+ * gathers of that dimension and kind in this process, returns them in
+ * pts_out = {boundary, source} and their summed time in best_ms (may be
+ * NULL), and clears the state's sums.  A screened or clamped cache's
+ * boundary gather (a separate kernel) is not tuned.  Workspace as
+ * bvc_evaluate (bvc_evaluate_workspace_size covers every count).
+ * bvc_set_gather_shape sets a count by hand (kind 0 boundary, 1 source;
+ * pts 0 = the built-in default).  Results do not depend on the counts. */
+bvc_status bvc_tune_gather(const bvc_cache* cache, bvc_eval_state* state, void* workspace, size_t workspace_bytes,
+                           bvc_stream stream, int32_t pts_out[2], float* best_ms);
+bvc_status bvc_set_gather_shape(int32_t dim, int32_t kind, int32_t pts);
+
 /* Zero the running sums and counts of a state (cudaMemsetAsync, no kernel). */
 bvc_status bvc_eval_state_reset(const bvc_eval_state* state, bvc_stream stream);
 

@@ -132,6 +132,10 @@ def _declare(lib):
         "wos_estimate": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct), i32, f32, i32,
                              u64, u64, P, sz, P]),
         "bvc_eval_state_reset": (S, [C.POINTER(EvalStateStruct), P]),
+        "bvc_tune_gather": (S, [C.POINTER(CacheStruct), C.POINTER(EvalStateStruct), P, sz, P,
+                                C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+        "bvc_set_gather_shape": (S, [i32, i32, i32]),
+        "bvc_last_error": (S, []),
         "wos_estimate_sigma": (S, [P, C.POINTER(Function), C.POINTER(Function), f64, C.POINTER(EvalStateStruct), i32,
                                    f32, i32, u64, u64, P, sz, P]),
         "wos_estimate_static_scratch": (S, [P, C.POINTER(Function), C.POINTER(Function), C.POINTER(EvalStateStruct),
@@ -692,6 +696,27 @@ def wos_workspace_size(dim: int, m: int, walks: int):
     mn, full = C.c_size_t(), C.c_size_t()
     _check(lib().wos_estimate_workspace_size(dim, m, walks, C.byref(mn), C.byref(full)), "wos workspace size")
     return int(mn.value), int(full.value)
+
+
+def tune_gather(cache: Cache, state: EvalState, ws: torch.Tensor = None, stream=None):
+    """bvc_tune_gather: returns ((boundary, source) points per thread, ms);
+    the state's sums are cleared."""
+    if ws is None:
+        ws = workspace(evaluate_workspace_size(cache, state))
+    pts = (C.c_int32 * 2)()
+    ms = C.c_float()
+    _check(lib().bvc_tune_gather(C.byref(cache.struct), C.byref(state.struct), _ptr(ws), ws.numel(),
+                                 _stream(stream), pts, C.byref(ms)), "bvc_tune_gather")
+    return (int(pts[0]), int(pts[1])), float(ms.value)
+
+
+def set_gather_shape(dim: int, kind: int, pts: int):
+    _check(lib().bvc_set_gather_shape(int(dim), int(kind), int(pts)), "bvc_set_gather_shape")
+
+
+def last_error() -> int:
+    """bvc_last_error: the calling thread's last status other than OK (cleared)."""
+    return int(lib().bvc_last_error())
 
 
 def eval_state_reset(state: EvalState, stream=None):

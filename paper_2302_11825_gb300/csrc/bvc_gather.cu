@@ -41,18 +41,24 @@ constexpr int kTile = 128;  // samples per tile (FP32 partial-sum length)
 // (measured on GB300: boundary tiles are FMA/SFU-bound and gain from reuse
 // of each shared-memory sample across 6 points; source tiles are SFU-bound
 // and gain from occupancy).
-#ifndef BVC_GATHER_PTS_BND
-#define BVC_GATHER_PTS_BND(D) 6
-#endif
-#ifndef BVC_GATHER_MINB_BND
-#define BVC_GATHER_MINB_BND(D) 2
-#endif
-template <int D, int KIND>
+// PTS evaluation points per thread: each sample loaded from shared memory
+// serves PTS points; more points mean fewer loads per pair but more
+// registers.  The supported counts are 2, 4, 6 (boundary) and 2, 4
+// (source); the defaults below are the GB300 measurements' best, and
+// bvc_tune_gather picks per workload.
+template <int PTS>
 struct GatherShape {
-  static constexpr int kPts = KIND == 0 ? BVC_GATHER_PTS_BND(D) : 2;
-  static constexpr int kMinBlocks = KIND == 0 ? BVC_GATHER_MINB_BND(D) : 4;
-  static constexpr int kPtsPerCta = kGBlock * kPts;
+  static constexpr int kPts = PTS;
+  static constexpr int kMinBlocks = PTS <= 2 ? 4 : 2;
+  static constexpr int kPtsPerCta = kGBlock * PTS;
 };
+constexpr int kDefaultPts[2][2] = {{6, 2}, {4, 2}};  // [dim - 2][kind]
+// the tuned counts (0 = default), process-wide: [dim - 2][kind]
+static int g_gather_pts[2][2] = {{0, 0}, {0, 0}};
+static int gather_pts(int D, int kind) {
+  const int p = __atomic_load_n(&g_gather_pts[D - 2][kind], __ATOMIC_RELAXED);
+  return p > 0 ? p : kDefaultPts[D - 2][kind];
+}
 
 __device__ unsigned long long g_gather_status = 0ull;
 
@@ -245,10 +251,10 @@ struct GatherArgs {
   double* part;            // split mode: [n_splits][planes][m]
 };
 
-template <int D, int KIND, bool GRAD>
-__global__ void __launch_bounds__(kGBlock, GatherShape<D, KIND>::kMinBlocks) k_gather(const GatherArgs A) {
-  constexpr int kGPts = GatherShape<D, KIND>::kPts;
-  constexpr int kPtsPerCta = GatherShape<D, KIND>::kPtsPerCta;
+template <int D, int KIND, bool GRAD, int PTS>
+__global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gather(const GatherArgs A) {
+  constexpr int kGPts = GatherShape<PTS>::kPts;
+  constexpr int kPtsPerCta = GatherShape<PTS>::kPtsPerCta;
   constexpr int SPF = KIND == 1 ? 2 : 5;
   constexpr int NA = GRAD ? 1 + D : 1;
   __shared__ __align__(128) float4 tile[2][kTile * SPF];
@@ -460,10 +466,9 @@ struct Plan {
   int64_t split_len;
 };
 
-static Plan plan_gather(int D, int64_t m, int64_t n, int kind, const void* kern) {
+static Plan plan_gather(int pts, int64_t m, int64_t n, const void* kern) {
   Plan P;
-  const int64_t per_cta = kind == 0 ? (D == 2 ? GatherShape<2, 0>::kPtsPerCta : GatherShape<3, 0>::kPtsPerCta)
-                                    : GatherShape<2, 1>::kPtsPerCta;
+  const int64_t per_cta = (int64_t)kGBlock * pts;
   P.pblocks = (int32_t)((m + per_cta - 1) / per_cta);
   const int64_t tiles = (n + kTile - 1) / kTile;
   const int64_t conc = (int64_t)num_sms() * max_blocks_per_sm(kern, kGBlock, 0);
@@ -479,18 +484,28 @@ static Plan plan_gather(int D, int64_t m, int64_t n, int kind, const void* kern)
 }
 
 template <int D, int KIND, bool GRAD>
-static const void* gather_kernel() {
-  return (const void*)k_gather<D, KIND, GRAD>;
+static const void* gather_kernel(int pts) {
+  if (KIND == 1) return pts == 4 ? (const void*)k_gather<D, KIND, GRAD, 4> : (const void*)k_gather<D, KIND, GRAD, 2>;
+  switch (pts) {
+    case 2:
+      return (const void*)k_gather<D, KIND, GRAD, 2>;
+    case 4:
+      return (const void*)k_gather<D, KIND, GRAD, 4>;
+    default:
+      return (const void*)k_gather<D, KIND, GRAD, 6>;
+  }
 }
 
-static const void* pick(int D, int kind, bool grad) {
+static const void* pick(int D, int kind, bool grad, int pts) {
   if (D == 2) {
-    if (kind == 0) return grad ? gather_kernel<2, 0, true>() : gather_kernel<2, 0, false>();
-    return grad ? gather_kernel<2, 1, true>() : gather_kernel<2, 1, false>();
+    if (kind == 0) return grad ? gather_kernel<2, 0, true>(pts) : gather_kernel<2, 0, false>(pts);
+    return grad ? gather_kernel<2, 1, true>(pts) : gather_kernel<2, 1, false>(pts);
   }
-  if (kind == 0) return grad ? gather_kernel<3, 0, true>() : gather_kernel<3, 0, false>();
-  return grad ? gather_kernel<3, 1, true>() : gather_kernel<3, 1, false>();
+  if (kind == 0) return grad ? gather_kernel<3, 0, true>(pts) : gather_kernel<3, 0, false>(pts);
+  return grad ? gather_kernel<3, 1, true>(pts) : gather_kernel<3, 1, false>(pts);
 }
+
+static bool pts_supported(int kind, int pts) { return pts == 2 || pts == 4 || (kind == 0 && pts == 6); }
 
 static size_t part_bytes(const Plan& P, int planes, int64_t m) {
   return P.n_splits > 1 ? (size_t)P.n_splits * planes * (size_t)m * sizeof(double) : 0;
@@ -677,15 +692,19 @@ static bvc_status bvc_evaluate_workspace_size_impl(const bvc_cache* cache, const
   const int D = cache->dim;
   const bool grad = state->grad_bnd != nullptr;
   const int planes = grad ? 1 + D : 1;
+  // the largest over the supported points-per-thread counts, so that any
+  // shape bvc_tune_gather picks fits
   size_t b = 0;
-  if (cache->n > 0) {
-    const Plan P = plan_gather(D, state->m, cache->n, 0, pick(D, 0, grad));
-    b = part_bytes(P, planes, state->m);
-  }
-  if (cache->n_src_cand > 0) {
-    const Plan P = plan_gather(D, state->m, cache->n_src_cand, 1, pick(D, 1, grad));
-    const size_t bs = part_bytes(P, planes, state->m);
-    b = bs > b ? bs : b;
+  for (int pts = 2; pts <= 6; pts += 2) {
+    if (cache->n > 0) {
+      const size_t bb = part_bytes(plan_gather(pts, state->m, cache->n, pick(D, 0, grad, pts)), planes, state->m);
+      b = bb > b ? bb : b;
+    }
+    if (cache->n_src_cand > 0 && pts_supported(1, pts)) {
+      const Plan P = plan_gather(pts, state->m, cache->n_src_cand, pick(D, 1, grad, pts));
+      const size_t bs = part_bytes(P, planes, state->m);
+      b = bs > b ? bs : b;
+    }
   }
   *bytes = b;
   return BVC_OK;
@@ -696,9 +715,11 @@ extern "C" bvc_status bvc_evaluate_workspace_size(const bvc_cache* cache, const 
 }
 
 static bvc_status run_part(int D, int kind, bool grad, const float* x, int64_t m, const float4* samples, int64_t n,
-                           const int64_t* n_dev, double* u, double* g, void* ws, size_t ws_bytes, cudaStream_t s) {
-  const void* kern = pick(D, kind, grad);
-  const Plan P = plan_gather(D, m, n, kind, kern);
+                           const int64_t* n_dev, double* u, double* g, void* ws, size_t ws_bytes, cudaStream_t s,
+                           int pts = 0) {
+  if (pts == 0) pts = gather_pts(D, kind);
+  const void* kern = pick(D, kind, grad, pts);
+  const Plan P = plan_gather(pts, m, n, kern);
   const int planes = grad ? 1 + D : 1;
   GatherArgs A{};
   A.x = x;
@@ -802,6 +823,85 @@ static bvc_status bvc_evaluate_impl(const bvc_cache* cache, bvc_eval_state* stat
 extern "C" bvc_status bvc_evaluate(const bvc_cache* cache, bvc_eval_state* state, void* workspace,
                                    size_t workspace_bytes, bvc_stream stream) {
   return bvc::note_status(bvc_evaluate_impl(cache, state, workspace, workspace_bytes, stream));
+}
+
+// The gather autotuner: for each kind of samples the cache has (boundary
+// with the plain Poisson kernel, sources), times two launches of every
+// supported points-per-thread count on this cache and these points and
+// keeps the fastest for all later gathers of that dimension and kind.
+static bvc_status bvc_tune_gather_impl(const bvc_cache* cache, bvc_eval_state* state, void* workspace,
+                                      size_t workspace_bytes, bvc_stream stream, int32_t pts_out[2],
+                                      float* best_ms) {
+  if (cache == nullptr || state == nullptr || cache->dim != state->dim || (cache->dim != 2 && cache->dim != 3) ||
+      state->m < 1 || state->x == nullptr || state->u_bnd == nullptr || state->u_src == nullptr ||
+      state->counts == nullptr || pts_out == nullptr)
+    return BVC_ERR_INVALID_ARG;
+  const int D = cache->dim;
+  const bool grad = state->grad_bnd != nullptr;
+  if (grad != (state->grad_src != nullptr)) return BVC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  BVC_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return BVC_ERR_CUDA;
+  }
+  bvc_status st = BVC_OK;
+  float total = 0.0f;
+  for (int kind = 0; kind < 2 && st == BVC_OK; ++kind) {
+    pts_out[kind] = gather_pts(D, kind);
+    const bool have = kind == 0 ? (cache->n > 0 && cache->packed != nullptr && cache->sigma == 0.0 &&
+                                   cache->clamp_c == 0.0)
+                                : (cache->n_src_cand > 0 && cache->src_packed != nullptr && cache->n_src_dev != nullptr);
+    if (!have) continue;
+    const float4* T = (const float4*)(kind == 0 ? cache->packed : cache->src_packed);
+    const int64_t n = kind == 0 ? cache->n : cache->n_src_cand;
+    const int64_t* nd = kind == 0 ? nullptr : cache->n_src_dev;
+    float best = INFINITY;
+    int best_pts = pts_out[kind];
+    for (int pts = 2; pts <= 6 && st == BVC_OK; pts += 2) {
+      if (!pts_supported(kind, pts)) continue;
+      for (int rep = 0; rep < 2 && st == BVC_OK; ++rep) {
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = BVC_ERR_CUDA;
+        if (st == BVC_OK)
+          st = run_part(D, kind, grad, state->x, state->m, T, n, nd, kind == 0 ? state->u_bnd : state->u_src,
+                        kind == 0 ? state->grad_bnd : state->grad_src, workspace, workspace_bytes, s, pts);
+        float ms = 0.0f;
+        if (st == BVC_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          st = BVC_ERR_CUDA;
+        if (st == BVC_OK && ms < best) {
+          best = ms;
+          best_pts = pts;
+        }
+      }
+    }
+    if (st == BVC_OK) {
+      __atomic_store_n(&g_gather_pts[D - 2][kind], best_pts, __ATOMIC_RELAXED);
+      pts_out[kind] = best_pts;
+      total += best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != BVC_OK) return st;
+  if (best_ms) *best_ms = total;
+  return bvc_eval_state_reset(state, stream);
+}
+extern "C" bvc_status bvc_tune_gather(const bvc_cache* cache, bvc_eval_state* state, void* workspace,
+                                      size_t workspace_bytes, bvc_stream stream, int32_t pts_out[2],
+                                      float* best_ms) {
+  return bvc::note_status(bvc_tune_gather_impl(cache, state, workspace, workspace_bytes, stream, pts_out, best_ms));
+}
+
+static bvc_status bvc_set_gather_shape_impl(int32_t dim, int32_t kind, int32_t pts) {
+  if ((dim != 2 && dim != 3) || (kind != 0 && kind != 1) || (pts != 0 && !pts_supported(kind, pts)))
+    return BVC_ERR_INVALID_ARG;
+  __atomic_store_n(&g_gather_pts[dim - 2][kind], pts, __ATOMIC_RELAXED);
+  return BVC_OK;
+}
+extern "C" bvc_status bvc_set_gather_shape(int32_t dim, int32_t kind, int32_t pts) {
+  return bvc::note_status(bvc_set_gather_shape_impl(dim, kind, pts));
 }
 
 static bvc_status bvc_eval_state_reset_impl(const bvc_eval_state* state, bvc_stream stream) {

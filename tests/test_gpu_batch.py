@@ -152,3 +152,35 @@ def test_batch_argument_checks():
     b = bvc.Batch([(g, 10, 1e-2, 2e-3, 10)], 4, 100, 3)
     with pytest.raises(ValueError):
         b.build(torch.zeros((1, 2, 15), dtype=torch.float64, device="cuda"), 0, b.cache())
+
+
+def test_batch_central_differences_in_the_boundary_data():
+    """Central differences of the batched solution in the right-hand sides'
+    coefficients: with fixed seeds the walks do not depend on the data, so
+    (u(C + h D) - u(C - h D)) / (2 h) must equal the solution for data D
+    alone (the derivative of the batched estimator along D), per mesh and
+    right-hand side, from one build and three re-projections."""
+    meshes = _meshes_3d()[:3]
+    n_list, m_list = [700, 1500, 333], [1000, 257, 600]
+    K, W, seed = 33, 8, 4
+    batch, specs, C, P, pts, Cs = _setup(meshes, 3, n_list, m_list, K, W, seed)
+    cache = batch.build(C, seed, batch.cache())
+    rng = np.random.default_rng(6)
+    Dd = torch.tensor(rng.standard_normal(tuple(C.shape)), dtype=torch.float64, device="cuda")
+    # the estimator is exactly linear in the data (the walks do not depend on
+    # it), so the difference quotient has no truncation error at any h; a
+    # step of the data's own size keeps the FP32 rounding of the gather tiles
+    # from being amplified by 1/h
+    h = 0.5
+    batch.project(C + h * Dd, cache)
+    up = batch.evaluate(cache, P).clone()
+    batch.project(C - h * Dd, cache)
+    um = batch.evaluate(cache, P).clone()
+    batch.project(Dd, cache)
+    ud = batch.evaluate(cache, P).clone()
+    torch.cuda.synchronize()
+    fd = (up - um) / (2 * h)
+    err = (fd - ud).abs().max().item() / ud.abs().max().item()
+    print(f"[batch FD] meshes={len(specs)} K={K} points={P.shape[1]} max rel difference {err:.2e}")
+    # FP32 tiles and pair terms, FP64 sums: a few 1e-6 of the scale
+    assert err < 1e-4

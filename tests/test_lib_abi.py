@@ -111,6 +111,15 @@ def test_last_error_is_thread_local_and_cleared(lib):
     assert lib.bvc_last_error() == 0     # successful calls leave it alone
 
 
+def test_gather_shape_host_checks(lib):
+    lib.bvc_set_gather_shape.restype = C.c_int
+    assert lib.bvc_set_gather_shape(2, 0, 5) == 1 and lib.bvc_set_gather_shape(4, 0, 4) == 1
+    assert lib.bvc_set_gather_shape(3, 1, 6) == 1 and lib.bvc_set_gather_shape(3, 2, 4) == 1
+    assert lib.bvc_set_gather_shape(3, 0, 4) == 0 and lib.bvc_set_gather_shape(3, 0, 0) == 0
+    lib.bvc_tune_gather.restype = C.c_int
+    assert lib.bvc_tune_gather(None, None, None, C.c_size_t(0), None, None, None) == 1
+
+
 def test_workspace_size_queries_are_host_only(lib):
     lib.wos_estimate_workspace_size.restype = C.c_int
     mn, full = C.c_size_t(), C.c_size_t()
