@@ -552,6 +552,48 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
     return out
 
 
+def reference_rmse(device, s, walks_per_point: int = 1 << 16, sub: int = 64):
+    """RMSE of the timed solve against a high-count pointwise reference, for
+    workloads without a closed form (the 2D Poisson star as configured): the
+    points of a sub x sub subgrid of the evaluation grid get pointwise walk on
+    spheres with walks_per_point walks each on the GPU; the RMSE of the
+    solve's u there is reported beside the reference's own standard error
+    (the oracle spot-checks this reference in the GPU tests)."""
+    import torch
+    from paper_2302_11825_gb300 import bvc
+    w = s.w
+    allp = np.concatenate([s.far_pts.cpu().numpy().T, s.near_pts.cpu().numpy().T])
+    u_all = np.concatenate([s.u_far.cpu().numpy(), s.u_near.cpu().numpy()])
+    lo, hi = w.V.min(0).astype(np.float64), w.V.max(0).astype(np.float64)
+    n = 1024  # the configured evaluation grid is n x n cell centres over the bounding box
+    # cells of a sub x sub subgrid of the n x n cell-centre grid: every (n/sub)-th centre
+    h = (hi - lo) / n
+    idx = np.floor((allp - lo) / h[None, :]).astype(np.int64)
+    step = max(n // sub, 1)
+    keep = np.all(idx % step == step // 2, axis=1)
+    pts, u_sol = allp[keep], u_all[keep]
+    st = bvc.EvalState(bvc.soa(pts.astype(np.float32)), grad=False)
+    ws = bvc.workspace(bvc.wos_workspace_size(w.dim, st.m, 1024)[1])
+    u_sum = np.zeros(st.m)
+    u_sq = np.zeros(st.m)
+    chunks = walks_per_point // 1024
+    t0 = time.perf_counter()
+    for c in range(chunks):
+        bvc.eval_state_reset(st)
+        bvc.wos_estimate(s.geom, w.g, w.f, st, 1024, w.eps, MAX_STEPS, 777, c * st.m * 1024, ws)
+        u, _ = bvc.get_solution(st)
+        torch.cuda.synchronize()
+        u = u.cpu().numpy()
+        u_sum += u
+        u_sq += u * u
+    ref = u_sum / chunks
+    se = np.sqrt(np.maximum(u_sq / chunks - ref ** 2, 0.0) / chunks)  # SE from the 1024-walk batch means
+    return {"points": int(st.m), "walks_per_point": int(chunks * 1024),
+            "rmse_vs_reference": float(np.sqrt(np.mean((u_sol - ref) ** 2))),
+            "reference_se_rms": float(np.sqrt(np.mean(se ** 2))),
+            "seconds": time.perf_counter() - t0}
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_sample_rates(w, budget_s: float = 20.0):
     """Times the FP64 oracle on bounded samples of the workload and
@@ -1593,6 +1635,10 @@ def main():
         "walk_caps": run_stats["capped"],
     }
     if rank == 0 and ws == 1 and not args.no_fixed_rmse:
+        if w.exact is None:
+            # no closed form: the RMSE of the last timed solve against a
+            # 2^16-walk pointwise reference on a 64 x 64 subgrid
+            out["reference"] = optional_part(lambda: reference_rmse(device, s))
         out["fixed_rmse"] = optional_part(lambda: fixed_rmse_comparison(device, w, s))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         def cpu():

@@ -141,3 +141,37 @@ def test_counting_mode_gives_same_walks():
     geom.set_counting(False)
     assert torch.equal(a.u_hat, b.u_hat) and torch.equal(a.dudn_hat, b.dudn_hat)
     assert s["nodes"] >= s["steps"] > 0 and s["prims"] >= s["steps"]
+
+
+def test_star_reference_spot_checked_by_the_oracle():
+    """The literal 2D Poisson configuration has no closed form; its RMSE
+    reference (bench.py) is high-count pointwise walk on spheres on the GPU.
+    On 256 of the reference's points the oracle's FP64 walks (other Philox
+    streams) agree with the GPU's within 4 combined standard errors."""
+    w = wl.star_poisson(grid=64)
+    geom = bvc.Geometry(w.V, w.F)
+    near = bvc.classify_near(geom, bvc.soa(w.eval_pts), w.offset_l).cpu().numpy().astype(bool)
+    pts = w.eval_pts[~near][::max(1, int((~near).sum()) // 256)][:256]
+    Wg, Wo = 1 << 16, 1 << 11
+    st = bvc.EvalState(bvc.soa(pts), grad=False)
+    ws = bvc.workspace(bvc.wos_workspace_size(2, st.m, 4096)[1])
+    s1, s2 = np.zeros(st.m), np.zeros(st.m)
+    for c in range(Wg // 4096):
+        bvc.eval_state_reset(st)
+        bvc.wos_estimate(geom, w.g, w.f, st, 4096, w.eps, 1 << 14, 777, c * st.m * 4096, ws)
+        u, _ = bvc.get_solution(st)
+        torch.cuda.synchronize()
+        u = u.cpu().numpy()
+        s1 += u
+        s2 += u * u
+    k = Wg // 4096
+    ref = s1 / k
+    se_g = np.sqrt(np.maximum(s2 / k - ref ** 2, 0.0) / k)
+    o = oracle.walks(oracle.BVH(w.V, w.F), w.g, w.f, pts, Wo, w.eps, 1 << 14, 31, 0, oracle.TAG_POINTWISE)
+    U = o["U"].reshape(-1, Wo)
+    uo, se_o = U.mean(1), U.std(1, ddof=1) / np.sqrt(Wo)
+    z = (ref - uo) / np.sqrt(se_g ** 2 + se_o ** 2)
+    print(f"[star reference] points={st.m} GPU {Wg} walks (SE rms {np.sqrt(np.mean(se_g ** 2)):.2e}) vs oracle "
+          f"{Wo} walks (SE rms {np.sqrt(np.mean(se_o ** 2)):.2e}): rms z {np.sqrt(np.mean(z * z)):.2f}, "
+          f"max |z| {np.abs(z).max():.2f}")
+    assert np.mean(np.abs(z) < 4) >= 0.99 and np.sqrt(np.mean(z * z)) < 1.3
