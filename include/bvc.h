@@ -54,7 +54,8 @@ typedef enum {
   BVC_ERR_TIMEOUT = 5,         /* a bounded in-kernel wait ran out (device status) */
   BVC_ERR_UNSUPPORTED = 6,     /* valid request the library does not implement */
   BVC_ERR_WORKSPACE = 7,       /* workspace too small for even one chunk */
-  BVC_WARN_WALK_CAP = 8        /* some walks stopped at max_steps (device status) */
+  BVC_WARN_WALK_CAP = 8,       /* some walks stopped at max_steps (device status) */
+  BVC_ERR_BOUNDS = 9           /* a debug build's device bounds check failed (device status) */
 } bvc_status;
 
 /* ------------------------------------------------------------------ g, f */
@@ -128,11 +129,13 @@ bvc_status bvc_geometry_get_info(bvc_geometry g, bvc_geometry_info* info);
 
 /* Device status/statistics block: out[0] total walk steps (closest-point
  * queries made by walks), out[1] walks stopped at max_steps, out[2] error
- * flags (bit 0: timeout), out[3] internal, out[4] BVH nodes fetched and
+ * flags (bit 0: timeout, bit 1: a bounds check of a debug build failed),
+ * out[3] internal, out[4] BVH nodes fetched and
  * out[5] primitives tested by walks while counting is on, out[6..7]
  * reserved.  Synchronises `stream`.  With reset != 0 the block is cleared
- * after reading.  Returns BVC_ERR_TIMEOUT if the error bit is set,
- * BVC_WARN_WALK_CAP if capped walks were seen. */
+ * after reading.  Returns BVC_ERR_BOUNDS if bit 1 is set, else
+ * BVC_ERR_TIMEOUT if bit 0 is, else BVC_WARN_WALK_CAP if capped walks were
+ * seen. */
 bvc_status bvc_geometry_stats(bvc_geometry g, uint64_t out[8], int32_t reset, bvc_stream stream);
 
 /* Counting mode (on != 0): later walks on this geometry run a variant that
@@ -733,6 +736,26 @@ const char* bvc_status_string(bvc_status s);
 bvc_status bvc_last_error(void);
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t bvc_version(void);
+
+/* ----------------------------------------------------------- debug build */
+/* A debug build of the library (compiled with BVC_DEBUG=1) checks, in every
+ * BVH traversal on the device (closest point, ray, silhouette, Neumann
+ * descent), each node index against the tree size, each leaf's primitive
+ * range against the primitive count and each traversal stack push against
+ * the stack depth, before the access.  A failed check skips the access,
+ * sets bit 1 of the geometry's status flags and lets the kernel finish;
+ * bvc_geometry_stats (bvc_batch_stats for a forest) then returns
+ * BVC_ERR_BOUNDS.  Release builds compile the checks out.
+ * bvc_debug_build returns 1 in a debug build, 0 otherwise. */
+int32_t bvc_debug_build(void);
+/* Test hook of the debug build: overwrites child `side` (0 left, 1 right)
+ * of internal node `node` of g's BVH with the raw link `link` (>= 0 an
+ * internal node index, < 0 the complement of a leaf's (first << 4) | count)
+ * on `stream`; the host copy of the tree is not changed.  Used to check that
+ * a corrupted link is caught: the library never writes a link that the
+ * checks above would reject.  Release builds: BVC_ERR_UNSUPPORTED, nothing
+ * written.  node outside [0, n_nodes) or side not 0/1: BVC_ERR_INVALID_ARG. */
+bvc_status bvc_debug_set_link(bvc_geometry g, int64_t node, int32_t side, int32_t link, bvc_stream stream);
 
 #ifdef __cplusplus
 }

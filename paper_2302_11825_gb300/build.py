@@ -1,6 +1,8 @@
 """Build ``libbvc.so`` in-tree: every CUDA/C++ source of ``csrc/`` compiled
 for sm_103a only, in parallel, then linked against the shared CUDA runtime
-(the same ``libcudart.so`` PyTorch loads)."""
+(the same ``libcudart.so`` PyTorch loads).  ``build(debug=True)`` makes
+``libbvc_debug.so`` instead: the same sources with ``BVC_DEBUG=1``, whose
+device BVH traversals check every node index, leaf range and stack push."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -13,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbvc.so")
+LIB_DEBUG = os.path.join(OUT_DIR, "libbvc_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,17 +43,20 @@ def _stale(lib: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale(LIB):
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not _stale(lib):
+        return lib
+    obj_dir = os.path.join(OUT_DIR, "debug") if debug else OUT_DIR
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
+    flags = COMMON + (["-DBVC_DEBUG=1"] if debug else [])
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
         objs.append(obj)
-        cmds.append([nvcc, *ARCH, *COMMON, "-c", src, "-o", obj])
+        cmds.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,11 +67,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(cmds))) as ex:
         list(ex.map(run, cmds))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

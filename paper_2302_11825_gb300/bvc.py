@@ -23,7 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, ERR_INVALID_ARG, ERR_DEGENERATE_MESH, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_WORKSPACE, \
-    WARN_WALK_CAP = range(9)
+    WARN_WALK_CAP, ERR_BOUNDS = range(10)
 FN_POLY, FN_GAUSS, FN_GAUSS_LAPLACIAN, FN_EXP_TRIG = 1, 2, 3, 4
 MAX_TERMS = 4
 TAG_WALK, TAG_BOUNDARY, TAG_SOURCE, TAG_POINTWISE = 0, 1, 2, 3
@@ -184,6 +184,8 @@ def _declare(lib):
         "bvc_wait_selftest": (S, [i64, P]),
         "bvc_status_string": (C.c_char_p, [S]),
         "bvc_version": (i32, []),
+        "bvc_debug_build": (i32, []),
+        "bvc_debug_set_link": (S, [P, i64, i32, i32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -192,13 +194,16 @@ def _declare(lib):
 
 
 def lib():
-    """The loaded CUDA library (built in-tree on first use)."""
+    """The loaded CUDA library (built in-tree on first use).  With the
+    environment variable BVC_DEBUG=1 at first use, the debug build
+    (libbvc_debug.so: device bounds checks in every BVH traversal)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            debug = os.environ.get("BVC_DEBUG", "0") == "1"
+            path = _build.LIB_DEBUG if debug else _build.LIB
             if not os.path.exists(path) or _build._stale(path):
-                path = _build.build()
+                path = _build.build(debug=debug)
             handle = C.CDLL(path)
             _declare(handle)
             _lib = handle
@@ -286,12 +291,18 @@ class Geometry:
     def stats(self, reset=False, stream=None):
         out = (C.c_uint64 * 8)()
         st = lib().bvc_geometry_stats(self.h, out, int(bool(reset)), _stream(stream))
-        _check(st, "bvc_geometry_stats", allow=(OK, WARN_WALK_CAP))
+        _check(st, "bvc_geometry_stats", allow=(OK, WARN_WALK_CAP, ERR_BOUNDS))
         return {"steps": int(out[0]), "capped": int(out[1]), "flags": int(out[2]), "nodes": int(out[4]),
                 "prims": int(out[5]), "status": st}
 
     def set_counting(self, on: bool):
         _check(lib().bvc_geometry_set_counting(self.h, int(bool(on))), "bvc_geometry_set_counting")
+
+    def debug_set_link(self, node: int, side: int, link: int, stream=None):
+        """bvc_debug_set_link (debug builds only): overwrite one child link of
+        the device BVH, to check that the traversal's bounds checks catch it."""
+        _check(lib().bvc_debug_set_link(self.h, int(node), int(side), int(link), _stream(stream)),
+               "bvc_debug_set_link")
 
     def close(self):
         if getattr(self, "h", None):
@@ -719,6 +730,11 @@ def last_error() -> int:
     return int(lib().bvc_last_error())
 
 
+def debug_build() -> bool:
+    """True when the loaded library is the debug build (BVC_DEBUG=1)."""
+    return bool(lib().bvc_debug_build())
+
+
 def eval_state_reset(state: EvalState, stream=None):
     _check(lib().bvc_eval_state_reset(C.byref(state.struct), _stream(stream)), "bvc_eval_state_reset")
 
@@ -883,7 +899,7 @@ class Batch:
     def stats(self, reset=False, stream=None):
         out = (C.c_uint64 * 8)()
         st = lib().bvc_batch_stats(self.h, out, 1 if reset else 0, _stream(stream))
-        _check(st, "bvc_batch_stats", allow=(OK, WARN_WALK_CAP))
+        _check(st, "bvc_batch_stats", allow=(OK, WARN_WALK_CAP, ERR_BOUNDS))
         return {"steps": out[0], "capped": out[1], "flags": out[2], "nodes": out[4], "prims": out[5]}
 
     def project(self, coeffs: torch.Tensor, cache: MultiCache, stream=None):

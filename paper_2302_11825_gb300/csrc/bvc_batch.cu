@@ -123,6 +123,7 @@ static bvc_status bvc_batch_create_impl(const bvc_batch_mesh* meshes, int32_t co
   b->sample_mesh = (int32_t*)(base += b_stats);
   b->table = (BatchMeshDev*)(base += b_mesh);
   F.n_prims = n_prims;
+  F.n_nodes = n_nodes;
   F.tau = tau;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<int32_t> smesh((size_t)n_total);
@@ -193,6 +194,7 @@ static bvc_status bvc_batch_stats_impl(bvc_batch b, uint64_t out[8], int32_t res
   if (reset) BVC_CUDA_TRY(cudaMemsetAsync(b->forest.stats, 0, sizeof(h), s));
   BVC_CUDA_TRY(cudaStreamSynchronize(s));
   for (int i = 0; i < 8; ++i) out[i] = h[i];
+  if (h[kStatFlags] & kFlagBounds) return BVC_ERR_BOUNDS;
   if (h[kStatFlags] & kFlagTimeout) return BVC_ERR_TIMEOUT;
   if (h[kStatCapped]) return BVC_WARN_WALK_CAP;
   return BVC_OK;

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kRayBlock) k_rays(const RayParams R) {
     for (;;) {
       int32_t ch[2];
       bool hit[2];
+      if (dbg_bad(G, node < 0 || node >= G.n_nodes)) break;
       if (D == 2) {
         const float4 L = __ldg(&G.nodes[3 * node]), Rb = __ldg(&G.nodes[3 * node + 1]);
         const float4 Cc = __ldg(&G.nodes[3 * node + 2]);
@@ -117,11 +118,15 @@ __global__ void __launch_bounds__(kRayBlock) k_rays(const RayParams R) {
       for (int k = 0; k < 2; ++k) {
         if (!hit[k]) continue;
         if (ch[k] >= 0) {
-          if (sp < kRayStack) stk[sp++] = ch[k];
+          if (sp < kRayStack)
+            stk[sp++] = ch[k];
+          else
+            dbg_bad(G, true);
           continue;
         }
         const int32_t enc = ~ch[k];
         const int32_t first = enc >> 4, count = enc & 15;
+        if (dbg_bad(G, first < 0 || (int64_t)first + count > G.n_prims)) continue;
         for (int32_t pq = first; pq < first + count; ++pq) {
           float t = -1.0f, nw = 0.0f;
           if (D == 2) {

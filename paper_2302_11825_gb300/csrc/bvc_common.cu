@@ -204,6 +204,7 @@ extern "C" const char* bvc_status_string(bvc_status s) {
     case BVC_ERR_UNSUPPORTED: return "unsupported";
     case BVC_ERR_WORKSPACE: return "workspace too small";
     case BVC_WARN_WALK_CAP: return "walks stopped at max_steps";
+    case BVC_ERR_BOUNDS: return "device bounds check failed (debug build)";
   }
   return "unknown status";
 }

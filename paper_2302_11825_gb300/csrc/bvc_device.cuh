@@ -31,6 +31,24 @@ namespace bvc {
 
 constexpr float kPiF = 3.14159265358979323846f;
 
+// Debug builds (BVC_DEBUG=1) check the tree links, leaf ranges and
+// traversal stack depth before every access; a failed check sets the
+// geometry's status flag kFlagBounds (bvc_geometry_stats returns
+// BVC_ERR_BOUNDS), skips the access and lets the query finish.  Release
+// builds compile the checks out.
+#ifndef BVC_DEBUG
+#define BVC_DEBUG 0
+#endif
+constexpr int kTravStack = 24;  // traversal stack entries; the BVH builder bounds the depth by 24
+__device__ __forceinline__ bool dbg_bad_at(unsigned long long* stats, bool bad) {
+  if (BVC_DEBUG && bad) {
+    atomicOr(&stats[kStatFlags], kFlagBounds);
+    return true;
+  }
+  return false;
+}
+__device__ __forceinline__ bool dbg_bad(const DevGeometry& G, bool bad) { return dbg_bad_at(G.stats, bad); }
+
 // ----------------------------------------------------------------- Philox
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32
 // multiplies by the round constants, xor of the high halves with the other
@@ -235,6 +253,11 @@ __device__ __forceinline__ void eval_fn_grad(const DevFunction& fn, const float*
 template <int D>
 __device__ __forceinline__ void vertex_weights(const DevGeometry& G, int32_t e, const float* p, int32_t* vid,
                                                float* w) {
+  if (dbg_bad(G, e < 0 || e >= G.n_prims)) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) vid[a] = 0, w[a] = 0.0f;
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < D; ++a) vid[a] = __ldg(&G.idx[(int64_t)e * D + a]);
   if (D == 2) {
@@ -520,6 +543,11 @@ __device__ __forceinline__ float slab_d2(float nx, float ny, float nz, float dmi
 template <int D>
 __device__ __forceinline__ void node_bounds(const DevGeometry& G, int node, const float* p, float& dl, float& dr,
                                             int32_t& cl, int32_t& cr) {
+  if (dbg_bad(G, node < 0 || node >= G.n_nodes)) {  // both children out of reach
+    dl = dr = __int_as_float(0x7f800000);
+    cl = cr = ~0;
+    return;
+  }
   if (D == 2) {
     const float4 L = __ldg(&G.nodes[3 * node]), R = __ldg(&G.nodes[3 * node + 1]);
     const float4 C = __ldg(&G.nodes[3 * node + 2]);
@@ -550,6 +578,7 @@ __device__ __forceinline__ void test_leaf(const DevGeometry& G, int32_t enc, con
                                           TravCount& tc) {
   const int32_t e = ~enc;
   const int32_t first = e >> 4, count = e & 15;
+  if (dbg_bad(G, first < 0 || (int64_t)first + count > G.n_prims)) return;
   if (CNT) tc.prims += (uint32_t)count;
   for (int32_t q = first; q < first + count; ++q) {
     if (D == 2) {
@@ -626,9 +655,11 @@ __device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p
       tr = false;
     }
     if (tl && tr) {
-      snode[sp * stride] = cr;
-      sdist[sp * stride] = dr;
-      ++sp;
+      if (!dbg_bad(G, sp >= kTravStack)) {
+        snode[sp * stride] = cr;
+        sdist[sp * stride] = dr;
+        ++sp;
+      }
       node = cl;
       continue;
     }

@@ -341,6 +341,7 @@ static bvc_status bvc_geometry_create_impl(int32_t dim, const float* verts, int6
   d.stats = (unsigned long long*)(base += b_disp);
   d.n_prims = n_prims;
   d.n_verts = n_verts;
+  d.n_nodes = n_nodes;
   d.tau = (float)(std::ldexp(1.0, -18) * (diag > 0 ? diag : 1.0));
   d.reach = std::nextafter((float)reach, INFINITY);
   for (int a = 0; a < 3; ++a) {
@@ -417,6 +418,31 @@ extern "C" bvc_status bvc_geometry_set_counting(bvc_geometry g, int32_t on) {
   return bvc::note_status(bvc_geometry_set_counting_impl(g, on));
 }
 
+extern "C" int32_t bvc_debug_build(void) {
+#if defined(BVC_DEBUG) && BVC_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+static bvc_status bvc_debug_set_link_impl(bvc_geometry g, int64_t node, int32_t side, int32_t link,
+                                          bvc_stream stream) {
+  if (g == nullptr || node < 0 || node >= g->n_nodes || (side != 0 && side != 1)) return BVC_ERR_INVALID_ARG;
+  if (!bvc_debug_build()) return BVC_ERR_UNSUPPORTED;
+  // children sit in the last float4 of a node (x: left, y: right)
+  const int per = g->dim == 2 ? 3 : 4;
+  float* dst = (float*)(g->dev.nodes + node * per + (per - 1)) + side;
+  cudaStream_t s = (cudaStream_t)stream;
+  BVC_CUDA_TRY(cudaMemcpyAsync(dst, &link, sizeof(link), cudaMemcpyHostToDevice, s));
+  BVC_CUDA_TRY(cudaStreamSynchronize(s));
+  return BVC_OK;
+}
+extern "C" bvc_status bvc_debug_set_link(bvc_geometry g, int64_t node, int32_t side, int32_t link,
+                                         bvc_stream stream) {
+  return bvc::note_status(bvc_debug_set_link_impl(g, node, side, link, stream));
+}
+
 static bvc_status bvc_geometry_stats_impl(bvc_geometry g, uint64_t out[8], int32_t reset, bvc_stream stream) {
   if (g == nullptr || out == nullptr) return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -425,6 +451,7 @@ static bvc_status bvc_geometry_stats_impl(bvc_geometry g, uint64_t out[8], int32
   if (reset) BVC_CUDA_TRY(cudaMemsetAsync(g->dev.stats, 0, sizeof(h), s));
   BVC_CUDA_TRY(cudaStreamSynchronize(s));
   for (int i = 0; i < 8; ++i) out[i] = h[i];
+  if (h[kStatFlags] & kFlagBounds) return BVC_ERR_BOUNDS;
   if (h[kStatFlags] & kFlagTimeout) return BVC_ERR_TIMEOUT;
   if (h[kStatCapped]) return BVC_WARN_WALK_CAP;
   return BVC_OK;

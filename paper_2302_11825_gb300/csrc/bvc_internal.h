@@ -45,7 +45,7 @@ struct DevGeometry {
   const int32_t* idx;     // [n_prims][dim] caller's element indices
   const double* disp;     // [n_verts][dim] offset-boundary displacements m_v (Sec. 3.2)
   unsigned long long* stats;  // [4] status block
-  int64_t n_prims, n_verts;
+  int64_t n_prims, n_verts, n_nodes;
   float tau;              // traversal slack, 2^-18 x bbox diagonal
   float reach;            // max_v |m_v| (FP32, rounded up)
   float lo[3], hi[3];     // bbox
@@ -64,6 +64,7 @@ struct BatchMeshDev {
 
 constexpr int kStatSteps = 0, kStatCapped = 1, kStatFlags = 2, kStatCounter = 3, kStatNodes = 4, kStatPrims = 5;
 constexpr unsigned long long kFlagTimeout = 1ull;
+constexpr unsigned long long kFlagBounds = 2ull;  // a debug build's bounds check failed
 
 }  // namespace bvc
 

@@ -39,7 +39,7 @@ namespace bvc {
 #define BVC_WALK_WARM 1
 #endif
 constexpr int kWalkBlock = 128;
-constexpr int kStack = 24;  // the BVH builder bounds the depth by 24
+constexpr int kStack = kTravStack;
 constexpr int64_t kChunk = 128;  // default walks per warp refill
 
 struct WalkParams {
@@ -315,9 +315,11 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
         }
         const bool tl = dl <= thr, tr = dr <= thr;
         if (tl && tr) {
-          stk_node[sp * kWalkBlock] = cr;
-          stk_dist[sp * kWalkBlock] = __float2half_rd(dr);
-          ++sp;
+          if (!dbg_bad(G, sp >= kStack)) {
+            stk_node[sp * kWalkBlock] = cr;
+            stk_dist[sp * kWalkBlock] = __float2half_rd(dr);
+            ++sp;
+          }
           cur = cl;
         } else if (tl) {
           cur = cl;

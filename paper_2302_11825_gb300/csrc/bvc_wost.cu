@@ -36,7 +36,9 @@ struct DevSil {
   // per node, per child: a cone (axis.xyz, cos half-angle) holding the normals
   // of every candidate below (cos <= 0: no bound, e.g. an unconditional one)
   const float4* cones;
-  int64_t n;
+  int64_t n;        // candidates
+  int64_t n_nodes;  // tree nodes
+  unsigned long long* stats;  // the whole boundary's status block (debug bounds flag)
   float tau;  // |n_k . a| <= tau counts as zero
   // (1 - gap)^2: a node is visited only when its squared box distance is
   // below shrink2 x the running best (1: the exact closest silhouette)
@@ -102,7 +104,7 @@ struct bvc_mixed_s {
 namespace bvc {
 
 constexpr int kWostBlock = 128;
-constexpr int kWStack = 24;  // the BVH builder bounds tree depth by 24
+constexpr int kWStack = kTravStack;
 constexpr float kRayInfl = 1e-6f;  // parametric slack of the crossing tests
 constexpr int kRecGnW = 0, kRecGradW = 1;
 
@@ -149,6 +151,11 @@ template <int D>
 __device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float& best2, float& skip2, int& node,
                                           int& sp, int* snode, float* sdist, TravCount& tcn) {
   ++tcn.nodes;
+  if (dbg_bad_at(S.stats, node < 0 || node >= S.n_nodes)) {
+    sp = 0;  // abandon the query
+    node = -1;
+    return true;
+  }
   int32_t ch[2];
   float dc[2], blo[2][3], bhi[2][3];
   if (D == 2) {
@@ -181,6 +188,10 @@ __device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float
     if (go[k] && ch[k] < 0) {
       const int32_t enc = ~ch[k];
       const int32_t first = enc >> 4, count = enc & 15;
+      if (dbg_bad_at(S.stats, first < 0 || (int64_t)first + count > S.n)) {
+        go[k] = false;
+        continue;
+      }
       tcn.prims += (uint32_t)count;
       for (int32_t q = first; q < first + count; ++q) {
         float ax, ay, az = 0.0f, d0, d1, d2;
@@ -227,9 +238,11 @@ __device__ __forceinline__ bool sil_visit(const DevSil& S, const float* x, float
     }
   if (go[0] && go[1]) {
     const int nearer = dc[1] < dc[0] ? 1 : 0;
-    snode[sp * kWostBlock] = ch[1 - nearer];
-    sdist[sp * kWostBlock] = dc[1 - nearer];
-    ++sp;
+    if (!dbg_bad_at(S.stats, sp >= kWStack)) {
+      snode[sp * kWostBlock] = ch[1 - nearer];
+      sdist[sp * kWostBlock] = dc[1 - nearer];
+      ++sp;
+    }
     node = ch[nearer];
     return false;
   }
@@ -303,6 +316,11 @@ __device__ __forceinline__ bool ray_visit(const DevGeometry& G, const float* o, 
                                           float tmin, int skip, int skip2, bool vis, float& best, int& bid, int& bq,
                                           int& node, int& sp, int* snode, float* sdist, TravCount& tcn) {
   ++tcn.nodes;
+  if (dbg_bad(G, node < 0 || node >= G.n_nodes)) {
+    sp = 0;  // abandon the query
+    node = -1;
+    return true;
+  }
   int32_t ch[2];
   float tc[2];
   if (D == 2) {
@@ -330,6 +348,10 @@ __device__ __forceinline__ bool ray_visit(const DevGeometry& G, const float* o, 
     if (go[k] && ch[k] < 0) {
       const int32_t enc = ~ch[k];
       const int32_t first = enc >> 4, count = enc & 15;
+      if (dbg_bad(G, first < 0 || (int64_t)first + count > G.n_prims)) {
+        go[k] = false;
+        continue;
+      }
       tcn.prims += (uint32_t)count;
       for (int32_t q = first; q < first + count; ++q) {
         float tt;
@@ -386,9 +408,11 @@ __device__ __forceinline__ bool ray_visit(const DevGeometry& G, const float* o, 
   go[1] = go[1] && tc[1] <= best;
   if (go[0] && go[1]) {
     const int nearer = tc[1] < tc[0] ? 1 : 0;
-    snode[sp * kWostBlock] = ch[1 - nearer];
-    sdist[sp * kWostBlock] = tc[1 - nearer];
-    ++sp;
+    if (!dbg_bad(G, sp >= kWStack)) {
+      snode[sp * kWostBlock] = ch[1 - nearer];
+      sdist[sp * kWostBlock] = tc[1 - nearer];
+      ++sp;
+    }
     node = ch[nearer];
     return false;
   }
@@ -472,6 +496,7 @@ __device__ __forceinline__ int descent_visit(const DevGeometry& G, const float2*
                                              float R2, const U4& r, int& level, int& node, float& pdf, float* z,
                                              float* nz, int& id, float& ipdf, TravCount& tcn) {
   ++tcn.nodes;
+  if (dbg_bad(G, node < 0 || node >= G.n_nodes)) return 2;
   int32_t ch[2];
   float dc[2];
   if (D == 2) {
@@ -510,6 +535,7 @@ __device__ __forceinline__ int descent_visit(const DevGeometry& G, const float2*
     const float cz = fmaf(B.x, Cc.y, -B.y * Cc.x);
     return 0.5f * sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
   };
+  if (dbg_bad(G, first < 0 || count == 0 || (int64_t)first + count > G.n_prims)) return 2;
   tcn.prims += (uint32_t)count;
   float tot = 0.0f;
   for (int32_t q = first; q < first + count; ++q) tot += elem_measure(q);
@@ -1115,6 +1141,10 @@ static bool fill_params(bvc_mixed m, const bvc_function* gfn, const bvc_neumann*
   P.Gd = m->dir->dev;
   P.Ga = m->whole->dev;
   if (m->neu) P.Gn = m->neu->dev;
+  // one status block for the solve: debug bounds flags of the parts land in
+  // the whole boundary's
+  P.Gd.stats = P.Ga.stats;
+  P.Gn.stats = P.Ga.stats;
   P.has_neu = m->neu != nullptr;
   P.S = m->sil;
   P.neu_local = m->neu_local;
@@ -1330,6 +1360,8 @@ static bvc_status bvc_mixed_create_impl(int32_t dim, const float* verts, int64_t
   m->sil.cones = (const float4*)(base += b_nq);
   m->disp = (const double*)(base += b_cone);
   m->sil.n = ns;
+  m->sil.n_nodes = m->n_sil_nodes;
+  m->sil.stats = m->whole->dev.stats;
   m->sil.tau = m->whole->dev.tau;
   m->sil.shrink2 = 1.0f;
   cudaStream_t s = (cudaStream_t)stream;

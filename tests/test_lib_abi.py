@@ -45,6 +45,13 @@ def test_host_only_calls(lib):
     lib.bvc_status_string.argtypes = [C.c_int]
     assert lib.bvc_status_string(0) == b"ok"
     assert b"workspace" in lib.bvc_status_string(7)
+    assert b"bounds" in lib.bvc_status_string(9)
+    # the release build: no device bounds checks, the link hook refused
+    lib.bvc_debug_build.restype = C.c_int32
+    assert lib.bvc_debug_build() == 0
+    lib.bvc_debug_set_link.restype = C.c_int
+    lib.bvc_debug_set_link.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p]
+    assert lib.bvc_debug_set_link(None, 0, 0, 0, None) == 1  # BVC_ERR_INVALID_ARG
 
 
 def _create(lib, V, F):
@@ -90,6 +97,19 @@ def test_entry_points_reject_null_handles(lib):
     lib.wos_estimate.restype = C.c_int
     assert lib.wos_estimate(None, None, None, None, C.c_int64(1), C.c_int32(1), C.c_float(1e-3), C.c_int32(1),
                             C.c_uint64(0), C.c_uint64(0), None, None, None, C.c_size_t(0), None) == 1
+
+
+def test_debug_build_is_a_separate_library(work_dir):
+    # the debug variant compiles (BVC_DEBUG=1) and says so; the release
+    # library is left as it was
+    from paper_2302_11825_gb300 import build
+    path = build.build(debug=True)
+    assert path.endswith("libbvc_debug.so") and path != build.LIB
+    dbg = C.CDLL(path)
+    dbg.bvc_debug_build.restype = C.c_int32
+    assert dbg.bvc_debug_build() == 1
+    missing = [n for n in _declared() if not hasattr(dbg, n)]
+    assert not missing, missing
 
 
 def test_last_error_is_thread_local_and_cleared(lib):
