@@ -48,6 +48,7 @@ METRIC = "interior pts/s at fixed RMSE (BVC vs pointwise WoS, 1 GB300); WoS step
 UNIT = "interior pts/s"
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
+GRAD_BAND_L = 4.0  # the gradient policy's band: pointwise grad u within 4 l of the boundary
 MAX_STEPS = 1 << 14
 
 # Algorithmic work per unit: bytes per BVH node fetch (two child boxes and
@@ -415,8 +416,16 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
     # gradient error is reported for all gathered points and for those at
     # least 4 l from the boundary
     d2f, _, _ = bvc.query_closest(s.geom, s.far_pts)
-    deep_far = np.sqrt(d2f.cpu().numpy()) >= 4.0 * w.offset_l
-    mse, gmse, gmse_deep, mse_far, mse_near = [], [], [], [], []
+    deep_far = np.sqrt(d2f.cpu().numpy()) >= GRAD_BAND_L * w.offset_l
+    _, gx_near = wl.eval_terms(w.exact, w.dim, s.near_pts.cpu().numpy().T.astype(np.float64))
+    # the gradient policy: grad u by pointwise walks (as many per point as the
+    # pointwise u band) at gathered points within GRAD_BAND_L l of the boundary
+    band_idx = torch.from_numpy(np.nonzero(~deep_far)[0]).to(s.far_pts.device)
+    band_pts = s.far_pts[:, band_idx].contiguous()
+    st_band = bvc.EvalState(band_pts, grad=True)
+    ws_band = bvc.workspace(bvc.wos_workspace_size(w.dim, max(st_band.m, 1), w.walks)[1])
+    gx_band = gx_far[~deep_far]
+    mse, gmse, gmse_deep, mse_far, mse_near, gmse_policy, t_band = [], [], [], [], [], [], []
     for seed in (7, 8, 9, 10):
         s.step(seed)
         torch.cuda.synchronize()
@@ -428,6 +437,19 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
         ge = np.sum((s.g_far.cpu().numpy().T - gx_far) ** 2, 1)
         gmse.append(float(np.mean(ge)))
         gmse_deep.append(float(np.mean(ge[deep_far])))
+        gn = np.sum((s.g_near.cpu().numpy().T - gx_near) ** 2, 1) if s.m_near else np.zeros(0)
+        gb = np.zeros(0)
+        if st_band.m:
+            bvc.eval_state_reset(st_band)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bvc.wos_estimate(s.geom, w.g, w.f, st_band, w.walks, w.eps, MAX_STEPS, 1000 + seed, 0, ws_band)
+            _, grb = bvc.get_solution(st_band)
+            e1.record()
+            torch.cuda.synchronize()
+            t_band.append(e0.elapsed_time(e1) / 1e3)
+            gb = np.sum((grb.cpu().numpy().T - gx_band) ** 2, 1)
+        gmse_policy.append(float((np.sum(ge[deep_far]) + np.sum(gb) + np.sum(gn)) / (s.m_far + s.m_near)))
     tau = float(np.sqrt(np.mean(mse)))
     bvc_grad = (float(np.sqrt(np.mean(gmse))), float(np.sqrt(np.mean(gmse_deep))))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -437,6 +459,10 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
     ev1.record()
     torch.cuda.synchronize()
     bvc_rate = (s.m_far + s.m_near) * 3 / (ev0.elapsed_time(ev1) / 1e3)
+    t_step = ev0.elapsed_time(ev1) / 1e3 / 3
+    policy = {"band_l": GRAD_BAND_L, "walks_per_point": int(w.walks), "band_points": int(st_band.m),
+              "near_points": int(s.m_near), "rmse": float(np.sqrt(np.mean(gmse_policy))),
+              "pts_per_s": (s.m_far + s.m_near) / (t_step + (float(np.mean(t_band)) if t_band else 0.0))}
     # pointwise walk on spheres on a random subset of interior points
     rng = np.random.default_rng(3)
     allp = np.concatenate([s.far_pts.cpu().numpy().T, s.near_pts.cpu().numpy().T])
@@ -488,7 +514,9 @@ def fixed_rmse_comparison(device, w_lit, solver=None):
                          "wos_beyond_4l": last_grad[1], "wos_walks_per_point": k,
                          # WoS at the BVC's time per point: k / ratio walks, the
                          # error of independent walks growing as sqrt(ratio)
-                         "wos_beyond_4l_equal_time": last_grad[1] * float(np.sqrt(bvc_rate / wos_rate))}}
+                         "wos_beyond_4l_equal_time": last_grad[1] * float(np.sqrt(bvc_rate / wos_rate)),
+                         # every interior point: pointwise within band_l x l, BVC beyond
+                         "policy": policy}}
     # the same at tau = 1e-2 and 3e-3 of the range of u: where the target is
     # below the configured cache's RMSE, the boundary and source caches grow
     # by the squared ratio (RMSE ~ N^-1/2, M^-1/2; capped at 16x) and the

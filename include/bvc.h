@@ -274,10 +274,11 @@ typedef struct {
   uint64_t walk_id_base;    /* first walk id: distinct caches of one seed use disjoint ranges */
   int32_t src_grid[3];      /* source candidate grid (2D: [0] x [1], [2] unused; 3D: all three),
                                all 0 = no source cache */
-  double sigma;             /* screened Poisson (Delta - sigma) u = 0 when > 0 (Eq. 1): f must be
-                               zero and there is no source cache; the walks weight each ball by its
-                               screened mean-value factor and the gather uses the screened Green's
-                               functions of App. A.  0 = Poisson. */
+  double sigma;             /* screened Poisson (Delta - sigma) u = f when > 0 (Eq. 1): the walks
+                               weight each ball by its screened mean-value factor and each step's
+                               source sample by the screened ball Green's function (see
+                               wos_estimate_sigma); the gather uses the screened Green's functions
+                               of App. A for the boundary and the source samples.  0 = Poisson. */
   double clamp_c;           /* > 0: the gather clamps dG/dn in the u term to [-c, c] (Sec. 3.3,
                                Eq. 8-9); bvc_clamp_correction estimates the remainder.  0 = none. */
   int32_t reuse_sources;    /* != 0: cache->src_y and n_src_dev already hold the kept source
@@ -449,7 +450,8 @@ bvc_status bvc_evaluate_adjoint_workspace_size(int64_t m, size_t* bytes);
  * bvc_evaluate of this cache (one cache per evaluation state, so u = sums /
  * (n, n_src_cand)).  Writes adj_u, adj_q (device double[n]) and, if
  * adj_src is non-NULL and the cache has source candidates, adj_src (device
- * double[n_src_cand], zero past the kept ones). */
+ * double[n_src_cand], zero past the kept ones).  Poisson caches only: a
+ * screened or clamped cache returns BVC_ERR_UNSUPPORTED. */
 bvc_status bvc_evaluate_adjoint(const bvc_cache* cache, const float* pts, int64_t m, const double* lam,
                                 double* adj_u, double* adj_q, double* adj_src, void* workspace,
                                 size_t workspace_bytes, bvc_stream stream);
@@ -466,16 +468,23 @@ bvc_status bvc_cache_adjoint(bvc_geometry g, const bvc_function* ffn, const bvc_
                              bvc_stream stream);
 
 /* ---------------------------------------------- many right-hand sides */
-/* Batching of right-hand sides for the Laplace equation (f = 0): K
- * Dirichlet data g_k = sum_m C[k][m] phi_m over the BVC_FN_POLY monomials
- * phi_m (total degree <= 4; bvc_poly_terms(dim) = 15 in 2D, 35 in 3D).
+/* Batching of right-hand sides: K Dirichlet data g_k = sum_m C[k][m] phi_m
+ * over the BVC_FN_POLY monomials phi_m (total degree <= 4;
+ * bvc_poly_terms(dim) = 15 in 2D, 35 in 3D), and, with
+ * bvc_multi_cache_build_source, K sources f_k = sum_b A[k][b] psi_b over the
+ * bumps psi_b of one shared GAUSS or GAUSS_LAPLACIAN term.
  * Without a source term a walk's path does not depend on g and each walk's
  * U and n.grad (Sec. 3.1, Eq. 7) are linear in g, so one set of walks per
  * cache serves every right-hand side: the walks record their end points,
  * per-sample moments of the monomials are reduced once (FP64), and each
  * right-hand side's u^ and du/dn^ are projections of the moments -- the
  * estimates the single-RHS path gives for g_k, up to rounding.  The gather
- * then evaluates Eq. 3 for all right-hand sides at once.  All arrays are
+ * then evaluates Eq. 3 for all right-hand sides at once.  With a source the
+ * walks' paths still do not depend on (g, f) (a step's source point is drawn
+ * from the step's own ball), each walk also records, per bump, its source
+ * sums; their per-sample means join the moments, and the source candidates
+ * of Eq. 4 join the gather as extra rows whose per-RHS weights are
+ * projections of the candidates' bump values.  All arrays are
  * caller-owned device memory. */
 #define BVC_MULTI_GROUP 32 /* right-hand sides per gather pass */
 typedef struct {
@@ -489,8 +498,16 @@ typedef struct {
   double* mom_q;       /* [n][bvc_poly_terms(dim)] means of s (phi_m(end) - phi_m(p0)) */
   double* u_hat;       /* [k][n] */
   double* dudn_hat;    /* [k][n] */
-  float* packed;       /* [ceil(k/32)][n][8 + 64] gather tiles */
+  float* packed;       /* [ceil(k/32)][n + n_src_cand][8 + 64] gather tiles */
   double bnd_measure;  /* |dOmega|, set by the build */
+  /* Source part (bvc_multi_cache_build_source; 0 / NULL for Laplace): */
+  int32_t n_bumps;     /* B <= 8 bumps of the shared source term (set by the build) */
+  double* mom_su;      /* [n][8] per-sample means over walks of sum_steps w_u psi_b(y) */
+  double* mom_sq;      /* [n][8] per-sample means of bump b's part of the du/dn sample */
+  int64_t n_src_cand;  /* M source candidates (the grid of opts->src_grid) */
+  float* src_y;        /* [dim][M] kept candidates first (Eq. 4 points) */
+  float* src_psi;      /* [M][8] |box| psi_b(y_j) of the kept candidates */
+  int64_t* n_src_dev;  /* device int64: candidates kept */
 } bvc_multi_cache;
 
 int32_t bvc_poly_terms(int32_t dim);
@@ -501,11 +518,27 @@ bvc_status bvc_multi_cache_build_workspace_size(bvc_geometry g, int64_t n, int32
  * opts->src_grid must be {0, 0} (BVC_ERR_UNSUPPORTED otherwise). */
 bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs, const bvc_cache_opts* opts,
                                  bvc_multi_cache* cache, void* workspace, size_t workspace_bytes, bvc_stream stream);
-/* Re-project the stored moments onto new coefficients (no walks). */
+/* The same with a source term: f_k = sum_b A[k][b] psi_b, psi_b the bumps of
+ * `shape` (one term of kind BVC_FN_GAUSS or BVC_FN_GAUSS_LAPLACIAN, 1..8
+ * bumps; its amplitudes are not used).  coeffs: device double[k][terms + B]
+ * (each row: the monomial coefficients of g_k, then A[k][0..B)).  The
+ * walks, their draws and the source candidates (opts->src_grid >= 1 each,
+ * cache->n_src_cand = their count; seed opts->seed; kept inside the offset
+ * boundary at opts->offset_l) are those of bvc_cache_build with f_k, so each
+ * right-hand side's u^, du/dn^ and Eq. 3 + Eq. 4 value equal the single-RHS
+ * results up to rounding.  Workspace: bvc_multi_cache_build_source_workspace_size. */
+bvc_status bvc_multi_cache_build_source_workspace_size(bvc_geometry g, const bvc_cache_opts* opts, size_t* min_bytes,
+                                                       size_t* full_bytes);
+bvc_status bvc_multi_cache_build_source(bvc_geometry g, const bvc_function* shape, const double* coeffs,
+                                        const bvc_cache_opts* opts, bvc_multi_cache* cache, void* workspace,
+                                        size_t workspace_bytes, bvc_stream stream);
+/* Re-project the stored moments onto new coefficients (no walks); with a
+ * source (cache->n_bumps > 0) the rows of coeffs hold terms + n_bumps values. */
 bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_cache* cache, bvc_stream stream);
 /* Eq. 3 for every right-hand side at m points: u[k][x] = (1/n) sum_i
- * (dG/dn(x, z_i) u^_ik - G(x, z_i) du/dn^_ik) / p  (overwritten; u only).
- * pts: device [dim][m]; u: device double[k][m]. */
+ * (dG/dn(x, z_i) u^_ik - G(x, z_i) du/dn^_ik) / p  (overwritten; u only),
+ * plus Eq. 4's (1/M) sum_j G(x, y_j) c_jk over the kept candidates when the
+ * cache has a source.  pts: device [dim][m]; u: device double[k][m]. */
 bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const float* pts, int64_t m, double* u,
                               bvc_stream stream);
 
@@ -558,13 +591,21 @@ bvc_status bvc_batch_project(bvc_batch b, const double* coeffs, bvc_multi_cache*
 bvc_status bvc_batch_evaluate(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
                               bvc_stream stream);
 
-/* wos_estimate for the screened equation (Delta - sigma) u = 0 (sigma >= 0;
- * f must be zero when sigma > 0, else BVC_ERR_UNSUPPORTED).  Each ball of
- * radius R multiplies the walk's weight by its screened mean-value factor
- * (R sqrt(sigma)) / sinh(R sqrt(sigma)) (3D) or 1 / I0(R sqrt(sigma)) (2D);
- * the first ball's gradient uses (dim / R) Qg with Qg = t^3 / (3 (t cosh t
- * - sinh t)) (3D) or t / (2 I1(t)) (2D), t = R sqrt(sigma).  sigma = 0 is
- * wos_estimate. */
+/* wos_estimate for the screened equation (Delta - sigma) u = f (sigma >= 0).
+ * Each ball of radius R multiplies the walk's weight by its screened
+ * mean-value factor (R sqrt(sigma)) / sinh(R sqrt(sigma)) (3D) or
+ * 1 / I0(R sqrt(sigma)) (2D); the first ball's gradient uses (dim / R) Qg
+ * with Qg = t^3 / (3 (t cosh t - sinh t)) (3D) or t / (2 I1(t)) (2D),
+ * t = R sqrt(sigma).  With a source, each step's sample y = x + rho w
+ * (rho = R u, as for Poisson) adds, times the weight into the ball,
+ * -|S| R rho^(d-1) G(rho) f(y) with G the Green's function of
+ * (sigma - Delta) on the ball, zero on its sphere, seen from the centre:
+ * [K0(k rho) - K0(kR) I0(k rho)/I0(kR)]/(2 pi) (2D), sinh(k (R - rho)) /
+ * (4 pi rho sinh kR) (3D), k = sqrt(sigma); the gradient's first-step source
+ * term uses the l = 1 radial mode of that Green's function instead (k [K1(k
+ * rho) - K1(kR) I1(k rho)/I1(kR)]/(2 pi); [Q(rho) - Q(R) J(k rho)/J(kR)] /
+ * (4 pi rho^2), Q(r) = e^(-kr)(kr + 1), J(t) = t cosh t - sinh t).  At sigma
+ * -> 0 these are the Poisson weights.  sigma = 0 is wos_estimate. */
 bvc_status wos_estimate_sigma(bvc_geometry g, const bvc_function* gfn, const bvc_function* ffn, double sigma,
                               bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
                               uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream);

@@ -18,7 +18,10 @@ mean-value property or published known answers, except as noted:
   the offset boundary of Sec. 3.2 (``offset_disp``, ``offset_vertices``, the
   samplers) by Green's representation formula over the moved mesh, crossing
   signs of rays, distances to the elements' lines and the offset region's
-  area, see tests/test_oracle_offset.py)
+  area, see tests/test_oracle_offset.py; the screened source weights of a
+  walk step (``screened_step_weights``, reading of Eq. 1 with sigma > 0) by
+  their sigma -> 0 limit, two closed-form integrals over the ball and walk
+  means against a closed-form solution, see tests/test_oracle_screened.py)
 """
 from __future__ import annotations
 
@@ -88,6 +91,7 @@ def _load():
                 "orc_bessel_k": (f64, [C.c_int, f64]),
                 "orc_green_sigma": (None, [C.c_int, f64, P, P, P, P]),
                 "orc_screened_factors": (None, [C.c_int, f64, P, P]),
+                "orc_screened_step_weights": (None, [C.c_int, f64, f64, f64, P, P]),
                 "orc_walks_sigma": (None, [P, P, P, P, f64, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P, P, P]),
                 "orc_gather_sigma": (None, [C.c_int, f64, i64, P, P, P, P, f64, i64, P, P, i64, P, P, P, P, P, P]),
                 "orc_gather_full": (None, [C.c_int, f64, f64, i64, P, P, P, P, f64, P, i64, P, P, i64, P, P, P, P,
@@ -208,6 +212,16 @@ def screened_factors(dim: int, t: float):
     return C_.value, Q_.value
 
 
+def screened_step_weights(dim: int, sigma: float, R: float, rho: float):
+    """(w_u, w_g) of a screened step's source sample at radius rho in the ball
+    of radius R: minus |S| R rho^(d-1) times the ball's Green's function of
+    (sigma - Delta) and of its centre gradient's radial mode."""
+    wu, wg = C.c_double(), C.c_double()
+    _load().orc_screened_step_weights(int(dim), float(np.sqrt(sigma)), float(R), float(rho), C.byref(wu),
+                                      C.byref(wg))
+    return wu.value, wg.value
+
+
 # ---------------------------------------------------------------- geometry
 def closest_brute64(V, F, pts):
     lib = _load()
@@ -317,7 +331,9 @@ def walks(bvh: BVH, g_terms, f_terms, starts, W: int, eps: float, max_steps: int
 
     g_vertex: optional per-vertex values of g (then g_terms is ignored): g at
     a boundary point is interpolated linearly on the closest element.
-    sigma > 0: the screened equation (Delta - sigma) u = 0 (f must be zero).
+    sigma > 0: the screened equation (Delta - sigma) u = f, each step's
+    source term weighted by the ball's screened Green's function and by the
+    throughput of the balls before it.
     Returns dict with per-walk U, grad[.., dim], steps, prim, scale[.., 2]
     (magnitudes of the terms forming U and the gradient, for error scaling)
     and, if asked, pend (final closest point)."""

@@ -1171,6 +1171,44 @@ void orc_sphere_step(int dim, double R, double u0, double u1, double u2, double*
   *wg = -R * (1.0 - ipow(r / R, dim));
 }
 
+/* Screened source weights of one step (Delta u - sigma u = f, k = sqrt(   */
+/* sigma)).  The ball B(x, R) gives u(x) = C avg_sphere u - int_B G f with  */
+/* G the Green's function of (sigma - Delta) on the ball, zero on its       */
+/* sphere, seen from the centre (r = |y - x|):                              */
+/*   2D  G = [K0(kr) - K0(kR) I0(kr) / I0(kR)] / (2 pi)                     */
+/*   3D  G = sinh(k (R - r)) / (4 pi r sinh(kR))                            */
+/* (the fundamental solution minus the regular solution that matches it on */
+/* the sphere).  Its gradient in the evaluation point at the centre, for    */
+/* the gradient estimate, is w phi(r), w = (y - x)/r, with phi the l = 1    */
+/* radial mode that has the singular part -d/dr of the fundamental solution */
+/* and vanishes at R:                                                       */
+/*   2D  phi = k [K1(kr) - K1(kR) I1(kr) / I1(kR)] / (2 pi)                 */
+/*   3D  phi = [Q(r) - Q(R) J(kr) / J(kR)] / (4 pi r^2),                   */
+/*       Q(r) = e^(-kr) (kr + 1),  J(t) = t cosh t - sinh t                 */
+/* With the step's sample y = x + rho w, rho = R u2 (density 1 / (R |S|     */
+/* rho^(d-1))), the weights are w_u = -|S| R rho^(d-1) G(rho) and w_g =     */
+/* -|S| R rho^(d-1) phi(rho); at k -> 0 they are the Poisson weights of     */
+/* orc_sphere_step.                                                         */
+static double orc_j_cosh(double t) { /* t cosh t - sinh t */
+  if (t < 0.1) {
+    const double t2 = t * t;
+    return t * t2 / 3.0 * (1.0 + t2 / 10.0 + t2 * t2 / 280.0 + t2 * t2 * t2 / 15120.0);
+  }
+  return t * cosh(t) - sinh(t);
+}
+void orc_screened_step_weights(int dim, double k, double R, double rho, double* wu, double* wg) {
+  const double tr = k * rho, tR = k * R;
+  if (dim == 2) {
+    const double G = orc_bessel_k(0, tr) - orc_bessel_k(0, tR) * orc_bessel_i(0, tr) / orc_bessel_i(0, tR);
+    const double phi = k * (orc_bessel_k(1, tr) - orc_bessel_k(1, tR) * orc_bessel_i(1, tr) / orc_bessel_i(1, tR));
+    *wu = -R * rho * G;   /* 2 pi R rho x G / (2 pi) */
+    *wg = -R * rho * phi;
+  } else {
+    *wu = -R * rho * sinh(tR - tr) / sinh(tR); /* 4 pi R rho^2 x G / (4 pi) */
+    *wg = -R * (exp(-tr) * (tr + 1.0) - exp(-tR) * (tR + 1.0) * orc_j_cosh(tr) / orc_j_cosh(tR));
+  }
+}
+
 static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double* U_out, double* grad_out,
                      int32_t* steps_out, int32_t* prim_out, double* pend_out, double* scale_out) {
   const int dim = w->bvh->m.dim;
@@ -1189,6 +1227,7 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
     if (k == 1) cv = g_at(w, pbar, prim);
     if (d < w->eps || k >= w->max_steps) break;
     const double R = d;
+    const double thr_in = thr; /* throughput into this ball: weighs its source term */
     if (w->sqs > 0.0) {
       double Cs, Qs;
       orc_screened_factors(dim, w->sqs * R, &Cs, &Qs);
@@ -1203,11 +1242,12 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
     double om[3] = {0, 0, 0}, rho, wu, wg;
     orc_sphere_step(dim, R, u[0], u[1], u[2], om, &rho, &wu, &wg);
     if (has_f) {
+      if (w->sqs > 0.0) orc_screened_step_weights(dim, w->sqs, R, rho, &wu, &wg);
       double y[3] = {0, 0, 0};
       for (int a = 0; a < dim; ++a) y[a] = x[a] + rho * om[a];
       const double fy = orc_fn_eval(w->f, dim, y);
-      usrc += wu * fy;
-      uabs += fabs(wu * fy);
+      usrc += thr_in * wu * fy;
+      uabs += fabs(thr_in * wu * fy);
       if (k == 1) {
         wf0 = wu * fy;
         wg0 = wg * fy;
@@ -1230,8 +1270,8 @@ static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double
   if (k == 1) {
     for (int a = 0; a < dim; ++a) grad_out[a] = 0.0;
   } else {
-    /* screened (f = 0): U / C0 estimates u at the first sphere point */
-    const double s = w->sqs > 0.0 ? ((double)dim / R0) * Qg0 * (U / C0 - cv)
+    /* screened: (U - wf0) / C0 estimates u at the first sphere point */
+    const double s = w->sqs > 0.0 ? ((double)dim / R0) * Qg0 * ((U - wf0) / C0 - cv) + wg0
                                   : ((double)dim / R0) * (U - wf0 - cv) + wg0;
     for (int a = 0; a < dim; ++a) grad_out[a] = s * nu[a];
   }

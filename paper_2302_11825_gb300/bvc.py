@@ -67,7 +67,9 @@ class CacheOpts(C.Structure):
 class MultiCacheStruct(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("k", C.c_int32), ("z", C.c_void_p), ("nrm", C.c_void_p),
                 ("jac", C.c_void_p), ("mom_u", C.c_void_p), ("mom_q", C.c_void_p), ("u_hat", C.c_void_p), ("dudn_hat", C.c_void_p),
-                ("packed", C.c_void_p), ("bnd_measure", C.c_double)]
+                ("packed", C.c_void_p), ("bnd_measure", C.c_double), ("n_bumps", C.c_int32), ("mom_su", C.c_void_p),
+                ("mom_sq", C.c_void_p), ("n_src_cand", C.c_int64), ("src_y", C.c_void_p), ("src_psi", C.c_void_p),
+                ("n_src_dev", C.c_void_p)]
 
 
 class BatchMeshStruct(C.Structure):
@@ -145,6 +147,9 @@ def _declare(lib):
         "bvc_multi_cache_build_workspace_size": (S, [P, i64, i32, C.POINTER(sz), C.POINTER(sz)]),
         "bvc_multi_cache_build": (S, [P, P, C.POINTER(CacheOpts), C.POINTER(MultiCacheStruct), P, sz, P]),
         "bvc_multi_cache_project": (S, [P, C.POINTER(MultiCacheStruct), P]),
+        "bvc_multi_cache_build_source_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz), C.POINTER(sz)]),
+        "bvc_multi_cache_build_source": (S, [P, C.POINTER(Function), P, C.POINTER(CacheOpts),
+                                             C.POINTER(MultiCacheStruct), P, sz, P]),
         "bvc_evaluate_multi": (S, [C.POINTER(MultiCacheStruct), P, i64, P, P]),
         "bvc_batch_create": (S, [P, i32, i32, i32, i32, P, C.POINTER(C.c_void_p)]),
         "bvc_batch_destroy": (S, [P]),
@@ -777,11 +782,15 @@ def poly_terms(dim: int) -> int:
     return int(lib().bvc_poly_terms(dim))
 
 
-class MultiCache:
-    """Caller-owned device buffers of a bvc_multi_cache (k right-hand sides)."""
+MAX_BUMPS = 8
 
-    def __init__(self, dim: int, n: int, k: int, device="cuda"):
-        self.dim, self.n, self.k = dim, n, k
+
+class MultiCache:
+    """Caller-owned device buffers of a bvc_multi_cache (k right-hand sides);
+    n_src_cand > 0 adds the source part (bvc_multi_cache_build_source)."""
+
+    def __init__(self, dim: int, n: int, k: int, n_src_cand: int = 0, device="cuda"):
+        self.dim, self.n, self.k, self.n_src_cand = dim, n, k, n_src_cand
         t = poly_terms(dim)
         groups = (k + MULTI_GROUP - 1) // MULTI_GROUP
         self.z = torch.zeros((dim, n), dtype=torch.float32, device=device)
@@ -791,14 +800,27 @@ class MultiCache:
         self.mom_q = torch.zeros((n, t), dtype=torch.float64, device=device)
         self.u_hat = torch.zeros((k, n), dtype=torch.float64, device=device)
         self.dudn_hat = torch.zeros((k, n), dtype=torch.float64, device=device)
-        self.packed = torch.zeros((groups, n, 8 + 2 * MULTI_GROUP), dtype=torch.float32, device=device)
+        self.packed = torch.zeros((groups, n + n_src_cand, 8 + 2 * MULTI_GROUP), dtype=torch.float32, device=device)
         st = MultiCacheStruct()
         st.dim, st.n, st.k = dim, n, k
         st.z, st.nrm, st.mom_u, st.mom_q = _ptr(self.z), _ptr(self.nrm), _ptr(self.mom_u), _ptr(self.mom_q)
         st.jac = _ptr(self.jac)
         st.u_hat, st.dudn_hat, st.packed = _ptr(self.u_hat), _ptr(self.dudn_hat), _ptr(self.packed)
         st.bnd_measure = 0.0
+        if n_src_cand > 0:
+            self.mom_su = torch.zeros((n, MAX_BUMPS), dtype=torch.float64, device=device)
+            self.mom_sq = torch.zeros((n, MAX_BUMPS), dtype=torch.float64, device=device)
+            self.src_y = torch.zeros((dim, n_src_cand), dtype=torch.float32, device=device)
+            self.src_psi = torch.zeros((n_src_cand, MAX_BUMPS), dtype=torch.float32, device=device)
+            self.n_src_dev = torch.zeros(1, dtype=torch.int64, device=device)
+            st.mom_su, st.mom_sq = _ptr(self.mom_su), _ptr(self.mom_sq)
+            st.n_src_cand = n_src_cand
+            st.src_y, st.src_psi, st.n_src_dev = _ptr(self.src_y), _ptr(self.src_psi), _ptr(self.n_src_dev)
         self.struct = st
+
+    @property
+    def n_bumps(self) -> int:
+        return int(self.struct.n_bumps)
 
 
 def multi_cache_build_workspace_size(geom: Geometry, n: int, walks: int):
@@ -821,16 +843,42 @@ def multi_cache_build(geom: Geometry, coeffs: torch.Tensor, opts: CacheOpts, cac
     return cache
 
 
+def multi_cache_build_source(geom: Geometry, shape_terms, coeffs: torch.Tensor, opts: CacheOpts, cache: MultiCache,
+                             ws: torch.Tensor = None, stream=None):
+    """bvc_multi_cache_build_source.  shape_terms: one (GAUSS | GAUSS_LAPLACIAN,
+    coeffs) term whose B bumps are the source basis; coeffs: CUDA float64
+    [k][poly_terms(dim) + B] (g_k's monomial coefficients, then f_k's bump
+    amplitudes)."""
+    _dev(coeffs, torch.float64)
+    if len(shape_terms) != 1:
+        raise ValueError("the source shape is one GAUSS or GAUSS_LAPLACIAN term")
+    kind, cs = shape_terms[0]
+    head = 3 if kind == FN_GAUSS_LAPLACIAN else 1
+    nb = (len(cs) - head) // (1 + cache.dim)
+    if tuple(coeffs.shape) != (cache.k, poly_terms(cache.dim) + nb):
+        raise ValueError("coefficients must be [k][poly_terms(dim) + bumps]")
+    if ws is None:
+        mn, full = C.c_size_t(), C.c_size_t()
+        _check(lib().bvc_multi_cache_build_source_workspace_size(geom.h, C.byref(opts), C.byref(mn), C.byref(full)),
+               "bvc_multi_cache_build_source_workspace_size")
+        ws = workspace(int(full.value))
+    f = make_function(shape_terms)
+    _check(lib().bvc_multi_cache_build_source(geom.h, C.byref(f), _ptr(coeffs), C.byref(opts), C.byref(cache.struct),
+                                              _ptr(ws), ws.numel(), _stream(stream)), "bvc_multi_cache_build_source")
+    return cache
+
+
 def multi_cache_project(coeffs: torch.Tensor, cache: MultiCache, stream=None):
     _dev(coeffs, torch.float64)
-    if tuple(coeffs.shape) != (cache.k, poly_terms(cache.dim)):
-        raise ValueError("coefficients must be [k][poly_terms(dim)]")
+    if tuple(coeffs.shape) != (cache.k, poly_terms(cache.dim) + cache.n_bumps):
+        raise ValueError("coefficients must be [k][poly_terms(dim) + bumps]")
     _check(lib().bvc_multi_cache_project(_ptr(coeffs), C.byref(cache.struct), _stream(stream)),
            "bvc_multi_cache_project")
 
 
 def evaluate_multi(cache: MultiCache, pts: torch.Tensor, u: torch.Tensor = None, stream=None):
-    """u[k][x] for every right-hand side (Eq. 3, boundary term only)."""
+    """u[k][x] for every right-hand side (Eq. 3, plus Eq. 4's source term
+    when the cache has one)."""
     _dev(pts, torch.float32)
     m = pts.shape[1]
     if u is None:
@@ -868,7 +916,7 @@ class Batch:
         return int(mn.value), int(full.value)
 
     def cache(self, device="cuda") -> MultiCache:
-        return MultiCache(self.dim, self.n_total, self.k, device)
+        return MultiCache(self.dim, self.n_total, self.k, device=device)
 
     def build(self, coeffs: torch.Tensor, seed, cache: MultiCache, ws: torch.Tensor = None, stream=None):
         """coeffs: CUDA float64 [meshes][k][poly_terms(dim)].  seed: an int,

@@ -413,6 +413,63 @@ __device__ __forceinline__ void screened_factors(float t, float& C, float& Qg) {
   }
 }
 
+// Exponentially scaled forms for all t > 0, so that ratios of large
+// arguments never overflow: e^t K0(t), e^t K1(t), e^-t I0(t), e^-t I1(t).
+__device__ __forceinline__ float bessel_k0e(float t) {
+  return t <= 2.0f ? bessel_k0_small(t) * __expf(t) : bessel_k0s_large(t) * rsqrtf(t);
+}
+__device__ __forceinline__ float bessel_k1e(float t) {
+  return t <= 2.0f ? bessel_k1_small(t) * __expf(t) : bessel_k1s_large(t) * rsqrtf(t);
+}
+__device__ __forceinline__ float bessel_i0e(float t) {
+  return t <= 3.75f ? bessel_i0_small(t) * __expf(-t) : bessel_i0s_large(t) * rsqrtf(t);
+}
+__device__ __forceinline__ float bessel_i1e(float t) {
+  return t <= 3.75f ? bessel_i1_small(t) * __expf(-t) : bessel_i1s_large(t) * rsqrtf(t);
+}
+// e^-t (t cosh t - sinh t): the series t^3/3 (1 + t^2/10 + t^4/280 + t^6/15120)
+// below 0.5, else ((t - 1) + e^-2t (t + 1)) / 2.
+__device__ __forceinline__ float jcosh_e(float t) {
+  if (t < 0.5f) {
+    const float t2 = t * t;
+    return __expf(-t) * (t * t2 * (1.0f / 3.0f)) *
+           fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 15120.0f, 1.0f / 280.0f), 0.1f), 1.0f);
+  }
+  return 0.5f * fmaf(__expf(-2.0f * t), t + 1.0f, t - 1.0f);
+}
+
+// Source weights of one screened step ((Delta - sigma) u = f, k = sqrt(sigma)):
+// the ball B(x, R) gives u(x) = C avg_sphere u - int_B G f, G the Green's
+// function of (sigma - Delta) on the ball (zero on its sphere) seen from the
+// centre, and the centre gradient of the source integral int_B w phi f, phi
+// the l = 1 radial mode that vanishes at R:
+//   2D  G = [K0(kr) - K0(kR) I0(kr)/I0(kR)] / (2 pi)
+//       phi = k [K1(kr) - K1(kR) I1(kr)/I1(kR)] / (2 pi)
+//   3D  G = sinh(k (R - r)) / (4 pi r sinh kR)
+//       phi = [Q(r) - Q(R) J(kr)/J(kR)] / (4 pi r^2),  Q(r) = e^-kr (kr + 1), J(t) = t cosh t - sinh t.
+// With the step's sample at radius rho (density 1 / (R |S| rho^(D-1))):
+// wu = -|S| R rho^(D-1) G(rho) and wg = -|S| R rho^(D-1) phi(rho) -- at k ->
+// 0 the Poisson weights -R rho ln(R/rho), -rho (R - rho) and -R (1 - (rho/R)^D).
+template <int D>
+__device__ __forceinline__ void screened_step_weights(float k, float R, float rho, bool want_g, float& wu,
+                                                      float& wg) {
+  const float tr = k * rho, tR = k * R;
+  if (D == 2) {
+    const float er = __expf(-tr), cross = __expf(tr - 2.0f * tR);
+    const float G = fmaf(-cross * bessel_k0e(tR), bessel_i0e(tr) / bessel_i0e(tR), er * bessel_k0e(tr));
+    wu = -R * rho * G;
+    if (want_g) {
+      const float phi = fmaf(-cross * bessel_k1e(tR), bessel_i1e(tr) / bessel_i1e(tR), er * bessel_k1e(tr));
+      wg = -R * tr * phi;
+    }
+  } else {
+    // sinh(tR - tr) / sinh(tR) = e^-tr (1 - e^-2(tR - tr)) / (1 - e^-2tR)
+    wu = -R * rho * __expf(-tr) * (expm1f(-2.0f * (tR - tr)) / expm1f(-2.0f * tR));
+    if (want_g)
+      wg = -R * fmaf(-(tR + 1.0f) * __expf(tr - 2.0f * tR), jcosh_e(tr) / jcosh_e(tR), __expf(-tr) * (tr + 1.0f));
+  }
+}
+
 // ------------------------------------------- canonical closest-point distance
 // S = (a.x, a.y, ab.x, ab.y), inv = 1/|ab|^2.
 __device__ __forceinline__ float seg_d2(const float4 S, float inv, float px, float py) {
@@ -619,68 +676,83 @@ __device__ __forceinline__ void finish_hit(const DevGeometry& G, const float* p,
   }
 }
 
-// Closest primitive to p.  Stack in shared memory: stack[k * stride + lane_slot].
+// One node of the closest-primitive traversal: the children's bounds, leaf
+// children tested, then the nearer child still within reach next (the
+// farther one stacked when both are), else the nearest stacked node still
+// within reach.  Returns true when the query is complete (call finish_hit).
+// Stack in shared memory: stack[k * stride + lane_slot].
 template <int D, bool CNT = false>
-__device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p, Hit<D>& h, int* snode,
-                                            float* sdist, int stride, TravCount& tc, int root = 0) {
+__device__ __forceinline__ bool closest_visit(const DevGeometry& G, const float* p, Hit<D>& h, float& thr,
+                                              int& node, int& sp, int* snode, float* sdist, int stride,
+                                              TravCount& tc) {
+  int32_t cl, cr;
+  float dl, dr;
+  if (CNT) ++tc.nodes;
+  node_bounds<D>(G, node, p, dl, dr, cl, cr);
+  if (dr < dl) {
+    const int32_t ti = cl;
+    cl = cr;
+    cr = ti;
+    const float td = dl;
+    dl = dr;
+    dr = td;
+  }
+  bool tl = dl <= thr, tr = dr <= thr;
+  if (tl && cl < 0) {
+    test_leaf<D, CNT>(G, cl, p, h, thr, tc);
+    tl = false;
+    tr = dr <= thr;
+  }
+  if (tr && cr < 0) {
+    test_leaf<D, CNT>(G, cr, p, h, thr, tc);
+    tr = false;
+  }
+  if (tl && tr) {
+    if (!dbg_bad(G, sp >= kTravStack)) {
+      snode[sp * stride] = cr;
+      sdist[sp * stride] = dr;
+      ++sp;
+    }
+    node = cl;
+    return false;
+  }
+  if (tl) {
+    node = cl;
+    return false;
+  }
+  if (tr) {
+    node = cr;
+    return false;
+  }
+  while (sp > 0) {
+    --sp;
+    if (sdist[sp * stride] <= thr) {
+      node = snode[sp * stride];
+      return false;
+    }
+  }
+  return true;
+}
+
+// An empty hit: no primitive yet, infinite distance.
+template <int D>
+__device__ __forceinline__ void hit_reset(Hit<D>& h) {
   h.d2 = __int_as_float(0x7f800000);
   h.id = 0x7fffffff;
   h.q = -1;
 #pragma unroll
   for (int a = 0; a < D; ++a) h.df[a] = 0.0f;
+}
+
+// Closest primitive to p.  Stack in shared memory: stack[k * stride + lane_slot].
+template <int D, bool CNT = false>
+__device__ __forceinline__ void bvh_closest(const DevGeometry& G, const float* p, Hit<D>& h, int* snode,
+                                            float* sdist, int stride, TravCount& tc, int root = 0) {
+  hit_reset<D>(h);
   float thr = __int_as_float(0x7f800000);
   int sp = 0;
   int node = root;
-  for (;;) {
-    int32_t cl, cr;
-    float dl, dr;
-    if (CNT) ++tc.nodes;
-    node_bounds<D>(G, node, p, dl, dr, cl, cr);
-    if (dr < dl) {
-      const int32_t tc = cl;
-      cl = cr;
-      cr = tc;
-      const float td = dl;
-      dl = dr;
-      dr = td;
-    }
-    bool tl = dl <= thr, tr = dr <= thr;
-    if (tl && cl < 0) {
-      test_leaf<D, CNT>(G, cl, p, h, thr, tc);
-      tl = false;
-      tr = dr <= thr;
-    }
-    if (tr && cr < 0) {
-      test_leaf<D, CNT>(G, cr, p, h, thr, tc);
-      tr = false;
-    }
-    if (tl && tr) {
-      if (!dbg_bad(G, sp >= kTravStack)) {
-        snode[sp * stride] = cr;
-        sdist[sp * stride] = dr;
-        ++sp;
-      }
-      node = cl;
-      continue;
-    }
-    if (tl) {
-      node = cl;
-      continue;
-    }
-    if (tr) {
-      node = cr;
-      continue;
-    }
-    bool found = false;
-    while (sp > 0) {
-      --sp;
-      if (sdist[sp * stride] <= thr) {
-        node = snode[sp * stride];
-        found = true;
-        break;
-      }
-    }
-    if (!found) break;
+  while (!closest_visit<D, CNT>(G, p, h, thr, node, sp, snode, sdist, stride, tc)) {
   }
   finish_hit<D>(G, p, h);
 }

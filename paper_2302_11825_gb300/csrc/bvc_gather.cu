@@ -540,12 +540,27 @@ __global__ void __launch_bounds__(256) k_pack_bnd_scr(const bvc_cache C) {
   o[1] = make_float4(C.nrm[i], C.nrm[C.n + i], D == 3 ? C.nrm[2 * C.n + i] : 0.0f, (float)(C.dudn_hat[i] * ca));
 }
 
+// Source samples of a screened cache use the same tiles: (y, A = 0) and
+// (0, B = -c / w), so that u += B K0 (2D) or B exp(-t)/r (3D) = G(x, y) c and
+// grad u += B Q d / r^D = c dG/dx; n_dev (device) then holds the kept count.
+template <int D>
+__global__ void __launch_bounds__(256) k_pack_src_scr(const bvc_cache C) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= C.n_src_cand || j >= *C.n_src_dev) return;
+  const int64_t M = C.n_src_cand;
+  const double w = D == 2 ? 6.283185307179586476925 : 12.566370614359172953850;
+  float4* o = (float4*)C.src_packed + 2 * j;
+  o[0] = make_float4(C.src_y[j], C.src_y[M + j], D == 3 ? C.src_y[2 * M + j] : 0.0f, 0.0f);
+  o[1] = make_float4(0.0f, 0.0f, 0.0f, (float)(-C.src_c[j] / w));
+}
+
 template <int D, bool GRAD, bool SCR, bool CLAMP>
 __global__ void __launch_bounds__(256) k_gather_scr(const float* __restrict__ x, int64_t m, const float4* __restrict__ T,
-                                                   int64_t n, float k, float cw, double* __restrict__ u,
-                                                   double* __restrict__ grad) {
+                                                   int64_t n, const int64_t* __restrict__ n_dev, float k, float cw,
+                                                   double* __restrict__ u, double* __restrict__ grad) {
   __shared__ __align__(128) float4 tile[2][2 * kSTile];
   __shared__ __align__(8) uint64_t bar[2];
+  if (n_dev != nullptr) n = min64(n, *n_dev);
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   float pc[3];
 #pragma unroll
@@ -674,10 +689,16 @@ static bvc_status bvc_cache_pack_impl(const bvc_cache* cache, bvc_stream stream)
     if (!cache->src_y || !cache->src_c || !cache->src_packed || !cache->n_src_dev) return BVC_ERR_INVALID_ARG;
     const unsigned grid = (unsigned)((cache->n_src_cand + 255) / 256);
     ProfScope ps("pack_source", s);
-    if (cache->dim == 2)
+    if (cache->sigma > 0.0) {  // the screened gather's tile layout
+      if (cache->dim == 2)
+        k_pack_src_scr<2><<<grid, 256, 0, s>>>(*cache);
+      else
+        k_pack_src_scr<3><<<grid, 256, 0, s>>>(*cache);
+    } else if (cache->dim == 2) {
       k_pack_src<2><<<grid, 256, 0, s>>>(*cache);
-    else
+    } else {
       k_pack_src<3><<<grid, 256, 0, s>>>(*cache);
+    }
   }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
@@ -766,7 +787,6 @@ static bvc_status bvc_evaluate_impl(const bvc_cache* cache, bvc_eval_state* stat
       (cache->n_src_cand > 0 && (cache->src_packed == nullptr || cache->n_src_dev == nullptr)))
     return BVC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cache->sigma > 0.0 && cache->n_src_cand > 0) return BVC_ERR_UNSUPPORTED;  // screened: f = 0
   if (state->m > 0) {
     if (cache->n > 0 && (cache->sigma > 0.0 || cache->clamp_c > 0.0)) {
       const unsigned grid = (unsigned)((state->m + 255) / 256);
@@ -776,7 +796,7 @@ static bvc_status bvc_evaluate_impl(const bvc_cache* cache, bvc_eval_state* stat
       const float4* T = (const float4*)cache->packed;
       ProfScope ps(scr ? "gather_screened" : "gather_clamped", s);
 #define BVC_FLEX(DD, GG, SS, CC) \
-  k_gather_scr<DD, GG, SS, CC><<<grid, 256, 0, s>>>(state->x, state->m, T, cache->n, k, cw, state->u_bnd, \
+  k_gather_scr<DD, GG, SS, CC><<<grid, 256, 0, s>>>(state->x, state->m, T, cache->n, nullptr, k, cw, state->u_bnd, \
                                                     GG ? state->grad_bnd : nullptr)
 #define BVC_FLEX_D(DD) \
   if (grad) {                                                  \
@@ -807,7 +827,31 @@ static bvc_status bvc_evaluate_impl(const bvc_cache* cache, bvc_eval_state* stat
                                state->u_bnd, state->grad_bnd, workspace, workspace_bytes, s);
       if (st != BVC_OK) return st;
     }
-    if (cache->n_src_cand > 0) {
+    if (cache->n_src_cand > 0 && cache->sigma > 0.0) {
+      // screened source samples: G^sigma(x, y) c through the screened gather
+      const unsigned grid = (unsigned)((state->m + 255) / 256);
+      const float k = (float)sqrt(cache->sigma);
+      const float4* T = (const float4*)cache->src_packed;
+      ProfScope ps("gather_screened_source", s);
+      if (D == 2) {
+        if (grad)
+          k_gather_scr<2, true, true, false><<<grid, 256, 0, s>>>(state->x, state->m, T, cache->n_src_cand,
+                                                                  cache->n_src_dev, k, 0.0f, state->u_src,
+                                                                  state->grad_src);
+        else
+          k_gather_scr<2, false, true, false><<<grid, 256, 0, s>>>(state->x, state->m, T, cache->n_src_cand,
+                                                                   cache->n_src_dev, k, 0.0f, state->u_src, nullptr);
+      } else {
+        if (grad)
+          k_gather_scr<3, true, true, false><<<grid, 256, 0, s>>>(state->x, state->m, T, cache->n_src_cand,
+                                                                  cache->n_src_dev, k, 0.0f, state->u_src,
+                                                                  state->grad_src);
+        else
+          k_gather_scr<3, false, true, false><<<grid, 256, 0, s>>>(state->x, state->m, T, cache->n_src_cand,
+                                                                   cache->n_src_dev, k, 0.0f, state->u_src, nullptr);
+      }
+      BVC_LAUNCH_CHECK();
+    } else if (cache->n_src_cand > 0) {
       bvc_status st = run_part(D, 1, grad, state->x, state->m, (const float4*)cache->src_packed, cache->n_src_cand,
                                cache->n_src_dev, state->u_src, state->grad_src, workspace, workspace_bytes, s);
       if (st != BVC_OK) return st;
@@ -852,7 +896,8 @@ static bvc_status bvc_tune_gather_impl(const bvc_cache* cache, bvc_eval_state* s
     pts_out[kind] = gather_pts(D, kind);
     const bool have = kind == 0 ? (cache->n > 0 && cache->packed != nullptr && cache->sigma == 0.0 &&
                                    cache->clamp_c == 0.0)
-                                : (cache->n_src_cand > 0 && cache->src_packed != nullptr && cache->n_src_dev != nullptr);
+                                : (cache->n_src_cand > 0 && cache->src_packed != nullptr && cache->n_src_dev != nullptr &&
+                                   cache->sigma == 0.0);
     if (!have) continue;
     const float4* T = (const float4*)(kind == 0 ? cache->packed : cache->src_packed);
     const int64_t n = kind == 0 ? cache->n : cache->n_src_cand;
@@ -999,7 +1044,10 @@ constexpr int kMTile = 32;
 constexpr int kMFlush = 4;
 constexpr int kMStride = 8 + 2 * kMG;  // floats per packed sample row
 
-// One mesh (meshes == null): m points [D][m] against n samples.  A batch:
+// One mesh (meshes == null): m points [D][m] against n samples, then (a
+// cache with a source) the *extra kept source rows (at most n_extra) that
+// follow them in each group's block of rows_g rows; the sums are divided by
+// n either way (the source rows carry the factor n/M).  A batch:
 // block x belongs to the mesh whose gather blocks hold it; its points lie in
 // that mesh's range of the [D][m] point planes and its samples in that
 // mesh's range of the n sample rows of each group.
@@ -1017,7 +1065,8 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
                                                                const float* __restrict__ packed, int64_t n, int32_t K,
                                                                double* __restrict__ u,
                                                                const BatchMeshDev* __restrict__ meshes,
-                                                               int32_t count) {
+                                                               int32_t count, int64_t rows_g,
+                                                               const int64_t* __restrict__ extra, int64_t n_extra) {
   __shared__ __align__(128) float tile[2][kMTile * kMStride];
   __shared__ __align__(8) uint64_t bar[2];
   extern __shared__ double s64[];  // [2 * kMG][kMThreads]
@@ -1040,7 +1089,9 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
     smp_off = M.smp_off;
     n_smp = M.n_smp;
   }
-  const float* base = packed + ((int64_t)g * n + smp_off) * kMStride;
+  const float* base = packed + ((int64_t)g * rows_g + smp_off) * kMStride;
+  int64_t n_rows = n_smp;
+  if (extra != nullptr) n_rows += min64(*extra, n_extra);
   const int64_t pl0 = blk * (2 * kMThreads) + tid, pl1 = pl0 + kMThreads;  // points within the mesh
   float pa[3], pb[3];
 #pragma unroll
@@ -1051,7 +1102,7 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
   float acc0[kMG], acc1[kMG];
 #pragma unroll
   for (int q = 0; q < 2 * kMG; ++q) s64[q * kMThreads + tid] = 0.0;
-  const int64_t nt = (n_smp + kMTile - 1) / kMTile;
+  const int64_t nt = (n_rows + kMTile - 1) / kMTile;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -1061,7 +1112,7 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
   if (tid == 0) {
     for (int b = 0; b < 2 && b < nt; ++b) {
       const int64_t st = (int64_t)b * kMTile;
-      const uint32_t bytes = (uint32_t)min64(kMTile, n_smp - st) * kMStride * 4u;
+      const uint32_t bytes = (uint32_t)min64(kMTile, n_rows - st) * kMStride * 4u;
       mbar_expect_tx(&bar[b], bytes);
       bulk_g2s(&tile[b][0], base + st * kMStride, bytes, &bar[b]);
     }
@@ -1077,7 +1128,7 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
       }
       return;
     }
-    const int cnt = (int)min64(kMTile, n_smp - it * kMTile);
+    const int cnt = (int)min64(kMTile, n_rows - it * kMTile);
     if (it % kMFlush == 0) {
 #pragma unroll
       for (int q = 0; q < kMG; ++q) acc0[q] = acc1[q] = 0.0f;
@@ -1137,7 +1188,7 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
     if (tid == 0 && it + 2 < nt) {
       fence_proxy_async();
       const int64_t st = (it + 2) * kMTile;
-      const uint32_t bytes = (uint32_t)min64(kMTile, n_smp - st) * kMStride * 4u;
+      const uint32_t bytes = (uint32_t)min64(kMTile, n_rows - st) * kMStride * 4u;
       mbar_expect_tx(&bar[b], bytes);
       bulk_g2s(&tile[b][0], base + st * kMStride, bytes, &bar[b]);
     }
@@ -1301,6 +1352,10 @@ static bvc_status bvc_evaluate_multi_impl(const bvc_multi_cache* cache, const fl
     return BVC_ERR_INVALID_ARG;
   const int groups = (cache->k + kMG - 1) / kMG;
   if (groups > 65535) return BVC_ERR_INVALID_ARG;  // grid.y limit
+  const int64_t M = cache->n_src_cand > 0 ? cache->n_src_cand : 0;
+  if (M > 0 && cache->n_src_dev == nullptr) return BVC_ERR_INVALID_ARG;
+  const int64_t rows = cache->n + M;
+  const int64_t* extra = M > 0 ? cache->n_src_dev : nullptr;
   if (m == 0) return BVC_OK;
   const dim3 grid((unsigned)((m + 255) / 256), (unsigned)groups);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1308,9 +1363,11 @@ static bvc_status bvc_evaluate_multi_impl(const bvc_multi_cache* cache, const fl
   const bvc_status at = cache->dim == 2 ? multi_gather_attr<2>() : multi_gather_attr<3>();
   if (at != BVC_OK) return at;
   if (cache->dim == 2)
-    k_gather_multi<2><<<grid, kMThreads, kMSum64, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
+    k_gather_multi<2><<<grid, kMThreads, kMSum64, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0,
+                                                       rows, extra, M);
   else
-    k_gather_multi<3><<<grid, kMThreads, kMSum64, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0);
+    k_gather_multi<3><<<grid, kMThreads, kMSum64, s>>>(pts, m, cache->packed, cache->n, cache->k, u, nullptr, 0,
+                                                       rows, extra, M);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -1322,7 +1379,7 @@ extern "C" bvc_status bvc_evaluate_multi(const bvc_multi_cache* cache, const flo
 static bvc_status bvc_batch_evaluate_impl(bvc_batch b, const bvc_multi_cache* cache, const float* pts, double* u,
                                          bvc_stream stream) {
   if (b == nullptr || cache == nullptr || cache->dim != b->dim || cache->n != b->n_total || cache->k != b->k ||
-      cache->packed == nullptr || (b->m_total > 0 && (pts == nullptr || u == nullptr)))
+      cache->packed == nullptr || cache->n_src_cand != 0 || (b->m_total > 0 && (pts == nullptr || u == nullptr)))
     return BVC_ERR_INVALID_ARG;
   const int groups = (cache->k + kMG - 1) / kMG;
   if (groups > 65535 || b->blocks_total > 0x7fffffffLL) return BVC_ERR_INVALID_ARG;  // grid limits
@@ -1334,10 +1391,10 @@ static bvc_status bvc_batch_evaluate_impl(bvc_batch b, const bvc_multi_cache* ca
   if (at != BVC_OK) return at;
   if (b->dim == 2)
     k_gather_multi<2><<<grid, kMThreads, kMSum64, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u,
-                                                       b->table, b->count);
+                                                       b->table, b->count, b->n_total, nullptr, 0);
   else
     k_gather_multi<3><<<grid, kMThreads, kMSum64, s>>>(pts, b->m_total, cache->packed, b->n_total, cache->k, u,
-                                                       b->table, b->count);
+                                                       b->table, b->count, b->n_total, nullptr, 0);
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -1364,6 +1421,7 @@ static bvc_status bvc_evaluate_adjoint_impl(const bvc_cache* cache, const float*
     return BVC_ERR_INVALID_ARG;
   const bool src = adj_src != nullptr && cache->n_src_cand > 0;
   if (src && (cache->src_y == nullptr || cache->n_src_dev == nullptr)) return BVC_ERR_INVALID_ARG;
+  if (cache->sigma != 0.0 || cache->clamp_c != 0.0) return BVC_ERR_UNSUPPORTED;  // the Poisson gather's transpose
   if (workspace_bytes < 256 + (size_t)m * 16) return BVC_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   const int D = cache->dim;

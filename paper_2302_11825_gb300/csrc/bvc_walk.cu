@@ -121,6 +121,11 @@ constexpr int kStep = 2;   // query done: termination test, sphere sample, sourc
 //            rec[D total + t] = (D / R0)(n . w0) (0 if the walk stopped at
 //            its start); for f = 0 a walk's path does not depend on g, and
 //            U = g(end), n . grad = rec[D] (g(end) - g(closest point of start)).
+//            With a one-term bump source f = sum_b A_b psi_b (kMaxBumps
+//            bumps), also rec[(D + 1 + b) total + t] = sum over steps of
+//            w_u psi_b(y) and rec[(D + 1 + kMaxBumps + b) total + t] = bump
+//            b's part of the n . grad sample, so that U and n . grad stay
+//            linear in (g, A): U = g(end) + sum_b A_b rec[D + 1 + b], etc.
 //   kRecAdj  the adjoint replay of a kRecGn walk (same path, same draws):
 //            with cu = dL/du^ / W and cq = dL/d(du/dn^) / W of its start,
 //            U and n . grad are linear in the vertex values of g and the
@@ -134,11 +139,14 @@ constexpr int kRecGn = 0, kRecGrad = 1, kRecEnd = 2, kRecAdj = 3;
 // FM: 0 Laplace (f = 0), 1 Poisson with a source term, 2 screened Poisson
 // (sigma > 0, f = 0): every ball multiplies the walk's throughput by its
 // screened mean-value factor C (value) and the first ball's Qg scales the
-// gradient estimate (screened_factors).
+// gradient estimate (screened_factors); 3 screened Poisson with a source
+// term, each ball's source sample weighted by the screened ball Green's
+// function (screened_step_weights) and by the throughput into the ball.
 template <int D, int FM, int REC, bool CNT>
-__global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB(D)) k_walk(const WalkParams P) {
-  constexpr bool HAS_F = FM == 1;
-  constexpr bool SCR = FM == 2;
+__global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj || (REC == kRecEnd && FM == 1) ? 4 : BVC_WALK_MINB(D))
+    k_walk(const WalkParams P) {
+  constexpr bool HAS_F = FM == 1 || FM == 3;
+  constexpr bool SCR = FM >= 2;
   // Traversal stacks: node links and box distances, the latter in FP16
   // rounded down (a smaller stored distance can only cost an extra visit,
   // never prune a box that must be visited).
@@ -171,6 +179,12 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
   double gA[REC == kRecAdj && HAS_F ? kMaxBumps : 1];
 #pragma unroll
   for (int b = 0; b < (REC == kRecAdj && HAS_F ? kMaxBumps : 1); ++b) gA[b] = 0.0;
+  // end-point walks with a source: per bump b, sum_steps w_u psi_b(y) and
+  // the first step's part of the du/dn sample, (n.w0)(w_g - (D/R0) w_u) psi_b
+  constexpr int NB = REC == kRecEnd && HAS_F ? kMaxBumps : 1;
+  float sbu[NB], sbc[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) sbu[b] = sbc[b] = 0.0f;
   // query state
   int cur = 0, sp = 0;
   float thr = kInf;
@@ -261,6 +275,9 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
         k = 0;
         R0 = usrc = wf0 = wg0 = cv = 0.0f;
         if (SCR) wthr = C0 = Qg0 = 1.0f;
+        if (REC == kRecEnd && HAS_F)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) sbu[b] = sbc[b] = 0.0f;
         if (P.first) {
           const int64_t c = P.total / P.W;
           h.d2 = P.first[r];
@@ -355,7 +372,14 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
             float nn2 = 0.0f;
 #pragma unroll
             for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], nu[a], nn2);
-            P.rec[D * P.total + t] = k > 1 ? ((float)D / R0) * nn2 : 0.0f;
+            const float sj = k > 1 ? ((float)D / R0) * nn2 : 0.0f;
+            P.rec[D * P.total + t] = sj;
+            if (HAS_F)
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                P.rec[(D + 1 + b) * P.total + t] = sbu[b];
+                P.rec[(D + 1 + kMaxBumps + b) * P.total + t] = k > 1 ? fmaf(sj, sbu[b], sbc[b]) : 0.0f;
+              }
           } else if (REC == kRecAdj) {
             const float s0 = k > 1 ? cq * ((float)D / R0) * nw0 : 0.0f;
             int32_t vid[D];
@@ -367,8 +391,9 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
           } else {
             const float gend = P.gv ? vertex_g<D>(G, P.gv, h.id, pbar) : eval_fn<D, true>(P.g, pbar);
             const float U = (k == 1 ? cv : (SCR ? wthr * gend : gend)) + usrc;
-            // screened: U / C0 estimates u at the first sphere point
-            const float sc = k > 1 ? (SCR ? ((float)D / R0) * Qg0 * (U / C0 - cv) : ((float)D / R0) * (U - wf0 - cv) + wg0)
+            // screened: (U - wf0) / C0 estimates u at the first sphere point
+            const float sc = k > 1 ? (SCR ? fmaf(((float)D / R0) * Qg0, (U - wf0) / C0 - cv, wg0)
+                                          : ((float)D / R0) * (U - wf0 - cv) + wg0)
                                    : 0.0f;
             P.rec[t] = U;
             if (REC == kRecGn) {
@@ -388,6 +413,7 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
           phase = kIdle;
         } else {
           const float R = d;
+          const float thr_in = wthr;  // screened: the throughput into this ball weighs its source term
           if (SCR) {
             float Cs, Qs;
             screened_factors<D>(P.sqs * R, Cs, Qs);
@@ -422,7 +448,29 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
             for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], om[a], nn2);
             nw0 = nn2;
           }
-          if (HAS_F && REC == kRecAdj) {
+          if (HAS_F && REC == kRecEnd) {
+            // the source terms per bump (Sec. 3.1 ball Green's function
+            // weights, as the single right-hand side walk draws them)
+            const float u2 = u01f(r.z);
+            const float rho = R * u2;
+            float y[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
+            const float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho);
+            float psi[kMaxBumps];
+            bump_shapes<D>(P.f, y, psi);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) sbu[b] = fmaf(wu, psi[b], sbu[b]);
+            if (k == 1) {
+              float nn2 = 0.0f;
+#pragma unroll
+              for (int a = 0; a < D; ++a) nn2 = fmaf(P.nrm[a * P.pt_stride + i], om[a], nn2);
+              const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
+              const float c1 = nn2 * fmaf(-((float)D / R), wu, -R * (1.0f - q));
+#pragma unroll
+              for (int b = 0; b < NB; ++b) sbc[b] = c1 * psi[b];
+            }
+          } else if (HAS_F && REC == kRecAdj) {
             // d/dA_k of the source terms: U gains w_u psi_k(y) at every step;
             // n.grad gains (D/R0)(n.w0) w_u psi_k(y) at steps after the first
             // and (n.w0) w_g psi_k(y0) at the first (w_g = -R (1 - (rho/R)^D))
@@ -451,12 +499,13 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj ? 4 : BVC_WALK_MINB
             for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
             const float fy = eval_fn<D, true>(P.f, y);
             // ball Green's function weights: -R rho ln(R/rho) (2D), -rho (R - rho) (3D)
-            const float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho);
-            usrc = fmaf(wu, fy, usrc);
+            float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho), wg = 0.0f;
+            if (SCR) screened_step_weights<D>(P.sqs, R, rho, k == 1, wu, wg);
+            usrc = fmaf(SCR ? thr_in * wu : wu, fy, usrc);
             if (k == 1) {
               wf0 = wu * fy;
               const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
-              wg0 = -R * (1.0f - q) * fy;
+              wg0 = (SCR ? wg : -R * (1.0f - q)) * fy;
             }
           }
           if (k == 1) {
@@ -528,16 +577,24 @@ static const void* walk_kernel(bool cnt) {
   return cnt ? (const void*)k_walk<D, FM, REC, true> : (const void*)k_walk<D, FM, REC, false>;
 }
 
-// rec: kRecGn / kRecGrad / kRecEnd (f = 0 only) / kRecAdj (no counting);
-// scr: screened Poisson (f = 0, kRecGn / kRecGrad).
+// rec: kRecGn / kRecGrad / kRecEnd (f = 0, or a one-term bump source with
+// per-bump records) / kRecAdj (no counting); scr: screened Poisson (kRecGn /
+// kRecGrad, with or without a source).
 static const void* pick_walk(int dim, bool has_f, int rec, bool cnt, bool scr = false) {
-  if (rec == kRecEnd) return dim == 2 ? walk_kernel<2, 0, kRecEnd>(cnt) : walk_kernel<3, 0, kRecEnd>(cnt);
+  if (rec == kRecEnd) {
+    if (has_f) return dim == 2 ? walk_kernel<2, 1, kRecEnd>(cnt) : walk_kernel<3, 1, kRecEnd>(cnt);
+    return dim == 2 ? walk_kernel<2, 0, kRecEnd>(cnt) : walk_kernel<3, 0, kRecEnd>(cnt);
+  }
   if (rec == kRecAdj) {
     if (dim == 2) return has_f ? (const void*)k_walk<2, 1, kRecAdj, false> : (const void*)k_walk<2, 0, kRecAdj, false>;
     return has_f ? (const void*)k_walk<3, 1, kRecAdj, false> : (const void*)k_walk<3, 0, kRecAdj, false>;
   }
   const bool gn = rec == kRecGn;
   if (scr) {
+    if (has_f) {
+      if (dim == 2) return gn ? walk_kernel<2, 3, kRecGn>(cnt) : walk_kernel<2, 3, kRecGrad>(cnt);
+      return gn ? walk_kernel<3, 3, kRecGn>(cnt) : walk_kernel<3, 3, kRecGrad>(cnt);
+    }
     if (dim == 2) return gn ? walk_kernel<2, 2, kRecGn>(cnt) : walk_kernel<2, 2, kRecGrad>(cnt);
     return gn ? walk_kernel<3, 2, kRecGn>(cnt) : walk_kernel<3, 2, kRecGrad>(cnt);
   }
@@ -719,8 +776,6 @@ static bvc_status cache_build(bvc_geometry g, bvc_geometry gs, const bvc_functio
   if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
   if (!std::isfinite(opts->sigma) || opts->sigma < 0.0 || !std::isfinite(opts->clamp_c) || opts->clamp_c < 0.0)
     return BVC_ERR_INVALID_ARG;
-  // screened Poisson: f = 0 and no source cache
-  if (opts->sigma > 0.0 && ((ffn != nullptr && ffn->n_terms > 0) || ncand > 0)) return BVC_ERR_UNSUPPORTED;
   WalkParams P{};
   P.G = g->dev;
   P.chunk = g->tune_chunk;
@@ -1081,7 +1136,6 @@ bvc_status walk_points_u(bvc_geometry g, const bvc_function* gfn, const bvc_func
   P.chunk = g->tune_chunk;
   P.blocks_per_sm = g->tune_blocks_per_sm;
   if (!make_dev_function(gfn, D, &P.g) || !make_dev_function(ffn, D, &P.f)) return BVC_ERR_INVALID_ARG;
-  if (sigma > 0.0 && P.f.n_terms > 0) return BVC_ERR_UNSUPPORTED;
   P.starts = starts;
   P.nrm = nullptr;
   P.pt_stride = pt_stride;
@@ -1130,7 +1184,6 @@ static bvc_status wos_estimate_sigma_impl(bvc_geometry g, const bvc_function* gf
   if (g == nullptr || state == nullptr || state->dim != g->dim || state->m < 0 || state->counts == nullptr ||
       !valid_walk_args(eps, max_steps, walks) || !std::isfinite(sigma) || sigma < 0.0)
     return BVC_ERR_INVALID_ARG;
-  if (sigma > 0.0 && ffn != nullptr && ffn->n_terms > 0) return BVC_ERR_UNSUPPORTED;  // screened: f = 0
   const int64_t m = state->m;
   if (m > 0 && (state->x == nullptr || state->u_bnd == nullptr || workspace == nullptr)) return BVC_ERR_INVALID_ARG;
   const int D = g->dim;
@@ -1340,15 +1393,60 @@ __global__ void __launch_bounds__(256) k_moments(const float* __restrict__ rec, 
   }
 }
 
+// Per sample, the walk means of the per-bump source records (the end-point
+// walks' planes D + 1 .. D + 2 kMaxBumps): FP32 partials per lane over its
+// walks, FP64 fixed-order warp sums, as k_moments.
+__global__ void __launch_bounds__(256) k_src_moments(const float* __restrict__ rec, int64_t c, int32_t W, int32_t D,
+                                                     int64_t i0, double* __restrict__ mom_su,
+                                                     double* __restrict__ mom_sq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = c * (int64_t)W;
+  const float* ru = rec + (int64_t)(D + 1) * total;
+  const float* rq = rec + (int64_t)(D + 1 + kMaxBumps) * total;
+  for (int64_t r = warp; r < c; r += nwarps) {
+    float au[kMaxBumps], aq[kMaxBumps];
+#pragma unroll
+    for (int b = 0; b < kMaxBumps; ++b) au[b] = aq[b] = 0.0f;
+    for (int j = lane; j < W; j += 32) {
+      const int64_t t = r * W + j;
+#pragma unroll
+      for (int b = 0; b < kMaxBumps; ++b) {
+        au[b] += ru[b * total + t];
+        aq[b] += rq[b * total + t];
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kMaxBumps; ++b) {
+      double su = (double)au[b], sq = (double)aq[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      }
+      if (lane == 0) {
+        mom_su[(i0 + r) * kMaxBumps + b] = su / (double)W;
+        mom_sq[(i0 + r) * kMaxBumps + b] = sq / (double)W;
+      }
+    }
+  }
+}
+
 // Per sample: u^_k, du/dn^_k for every right-hand side (FP64) and the
 // gather tiles, grouped by BVC_MULTI_GROUP right-hand sides:
 // [group][sample][8 + 2 G] floats = z (4), n (4), a_k (G), b_k (G) with
 // 1/p = |dOmega| jac (the sample's offset element, Sec. 3.2) and
 //   2D  a = u^ /(2 pi p),  b = -du/dn^ /(2 pi p) ln2/2   (u += a (n.d)/r^2 + b lg2 r^2)
 //   3D  a = u^ /(4 pi p),  b = du/dn^ /(4 pi p)          (u += a (n.d)/r^3 + b/r)
+// With a source (B > 0 bumps) each coefficient row holds NM + B values and
+// the source moments add sum_b A[k][b] mom_s?[i][b]; rows_g is the number
+// of rows of each group's tile block (n, plus the source candidates).
 template <int D>
 __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, int32_t K, int64_t n,
                                                  const double* __restrict__ mom_u, const double* __restrict__ mom_q,
+                                                 int32_t B, const double* __restrict__ mom_su,
+                                                 const double* __restrict__ mom_sq, int64_t rows_g,
                                                  const float* __restrict__ z, const float* __restrict__ nrm,
                                                  const float* __restrict__ jac, double meas,
                                                  double* __restrict__ u_hat,
@@ -1360,6 +1458,7 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
   constexpr int S = 8 + 2 * G;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int CS = NM + B;  // coefficient row length
   double mu[NM], mq[NM];
 #pragma unroll
   for (int m = 0; m < NM; ++m) {
@@ -1376,7 +1475,7 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
   const double ca = D == 2 ? ip / 6.283185307179586476925 : ip / 12.566370614359172953850;
   const double cb = D == 2 ? -ca * 0.34657359027997265471 : ca;
   for (int g = 0; g < groups; ++g) {
-    float* row = packed + ((int64_t)g * n + i) * S;
+    float* row = packed + ((int64_t)g * rows_g + i) * S;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       row[a] = a < D ? z[a * n + i] : 0.0f;
@@ -1388,8 +1487,12 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
       if (k < K) {
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-          u = fma(C[k * NM + m], mu[m], u);
-          q = fma(C[k * NM + m], mq[m], q);
+          u = fma(C[k * CS + m], mu[m], u);
+          q = fma(C[k * CS + m], mq[m], q);
+        }
+        for (int b = 0; b < B; ++b) {
+          u = fma(C[k * CS + NM + b], mom_su[i * kMaxBumps + b], u);
+          q = fma(C[k * CS + NM + b], mom_sq[i * kMaxBumps + b], q);
         }
         u_hat[(int64_t)k * n + i] = u;
         q_hat[(int64_t)k * n + i] = q;
@@ -1400,23 +1503,95 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ C, i
   }
 }
 
+// Source candidate rows of the gather tiles, after the n sample rows of each
+// group: (y, 0 normal), a_k = 0 and b_k the Eq. 4 weight of right-hand side
+// k, c_jk = sum_b A[k][b] |box| psi_b(y_j), scaled so that the gather's 1/n
+// over all rows gives 1/M over the candidates:
+//   2D  b = (n/M) c/(2 pi) ln2/2  (u += b lg2 r^2)     3D  b = -(n/M) c/(4 pi)  (u += b/r)
+template <int D>
+__global__ void __launch_bounds__(128) k_project_src(const double* __restrict__ C, int32_t K, int32_t B, int64_t n,
+                                                     int64_t M, const int64_t* __restrict__ kept,
+                                                     const float* __restrict__ src_y,
+                                                     const float* __restrict__ src_psi, float* __restrict__ packed) {
+  constexpr int NM = Mono<D>::kN;
+  constexpr int G = BVC_MULTI_GROUP;
+  constexpr int S = 8 + 2 * G;
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M || j >= *kept) return;
+  const int CS = NM + B;
+  const double scale = D == 2 ? (double)n / (double)M / 6.283185307179586476925 * 0.34657359027997265471
+                              : -(double)n / (double)M / 12.566370614359172953850;
+  double psi[kMaxBumps];
+#pragma unroll
+  for (int b = 0; b < kMaxBumps; ++b) psi[b] = (double)src_psi[j * kMaxBumps + b];
+  const int groups = (K + G - 1) / G;
+  for (int g = 0; g < groups; ++g) {
+    float* row = packed + ((int64_t)g * (n + M) + n + j) * S;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      row[a] = a < D ? src_y[a * M + j] : 0.0f;
+      row[4 + a] = 0.0f;
+    }
+    for (int s = 0; s < G; ++s) {
+      const int k = g * G + s;
+      double c = 0.0;
+      if (k < K)
+        for (int b = 0; b < B; ++b) c = fma(C[k * CS + NM + b], psi[b], c);
+      row[8 + s] = 0.0f;
+      row[8 + G + s] = (float)(c * scale);
+    }
+  }
+}
+
+// |box| psi_b(y_j) of the kept candidates (psi_b the shape's bumps).
+template <int D>
+__global__ void __launch_bounds__(256) k_src_psi(DevFunction shape, const float* __restrict__ src_y, int64_t M,
+                                                 const int64_t* __restrict__ kept, double box,
+                                                 float* __restrict__ src_psi) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M || j >= *kept) return;
+  float y[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) y[a] = src_y[a * M + j];
+  float psi[kMaxBumps];
+  bump_shapes<D>(shape, y, psi);
+#pragma unroll
+  for (int b = 0; b < kMaxBumps; ++b) src_psi[j * kMaxBumps + b] = (float)((double)psi[b] * box);
+}
+
 }  // namespace bvc
 
 static bool valid_multi(const bvc_multi_cache* c, int dim) {
-  return c != nullptr && c->dim == dim && c->n >= 1 && c->k >= 1 && c->z && c->nrm && c->jac && c->mom_u && c->mom_q &&
-         c->u_hat && c->dudn_hat && c->packed;
+  if (!(c != nullptr && c->dim == dim && c->n >= 1 && c->k >= 1 && c->z && c->nrm && c->jac && c->mom_u && c->mom_q &&
+        c->u_hat && c->dudn_hat && c->packed))
+    return false;
+  if (c->n_bumps < 0 || c->n_bumps > kMaxBumps || c->n_src_cand < 0) return false;
+  if (c->n_bumps > 0 && (c->mom_su == nullptr || c->mom_sq == nullptr)) return false;
+  if (c->n_src_cand > 0 && (c->n_bumps == 0 || !c->src_y || !c->src_psi || !c->n_src_dev)) return false;
+  return true;
 }
 
 static bvc_status launch_project(const double* coeffs, bvc_multi_cache* c, cudaStream_t s,
                                  const int32_t* sample_mesh = nullptr, const BatchMeshDev* meshes = nullptr) {
   const unsigned grid = (unsigned)((c->n + 127) / 128);
+  const int32_t B = c->n_bumps;
+  const int64_t M = c->n_src_cand, rows = c->n + M;
   ProfScope ps("multi_project", s);
   if (c->dim == 2)
-    k_project<2><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->jac, c->bnd_measure,
-                                      c->u_hat, c->dudn_hat, c->packed, sample_mesh, meshes);
+    k_project<2><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, B, c->mom_su, c->mom_sq, rows, c->z,
+                                      c->nrm, c->jac, c->bnd_measure, c->u_hat, c->dudn_hat, c->packed, sample_mesh,
+                                      meshes);
   else
-    k_project<3><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, c->z, c->nrm, c->jac, c->bnd_measure,
-                                      c->u_hat, c->dudn_hat, c->packed, sample_mesh, meshes);
+    k_project<3><<<grid, 128, 0, s>>>(coeffs, c->k, c->n, c->mom_u, c->mom_q, B, c->mom_su, c->mom_sq, rows, c->z,
+                                      c->nrm, c->jac, c->bnd_measure, c->u_hat, c->dudn_hat, c->packed, sample_mesh,
+                                      meshes);
+  if (M > 0) {
+    const unsigned gs = (unsigned)((M + 127) / 128);
+    if (c->dim == 2)
+      k_project_src<2><<<gs, 128, 0, s>>>(coeffs, c->k, B, c->n, M, c->n_src_dev, c->src_y, c->src_psi, c->packed);
+    else
+      k_project_src<3><<<gs, 128, 0, s>>>(coeffs, c->k, B, c->n, M, c->n_src_dev, c->src_y, c->src_psi, c->packed);
+  }
   BVC_LAUNCH_CHECK();
   return BVC_OK;
 }
@@ -1435,6 +1610,8 @@ struct EndWalks {
   const int32_t* sample_mesh;
   const BatchMeshDev* meshes;
   const uint64_t* seed_dev;
+  bool src;       // a bump source: per-bump records and their moments
+  DevFunction f;  // its shape (src only)
 };
 
 static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void* workspace, int64_t chunk,
@@ -1455,6 +1632,7 @@ static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void*
   P.sample_mesh = E.sample_mesh;
   P.meshes = E.meshes;
   P.seed_dev = E.seed_dev;
+  if (E.src) P.f = E.f;
   for (int64_t i0 = 0; i0 < N; i0 += chunk) {
     const int64_t c = (N - i0) < chunk ? (N - i0) : chunk;
     P.i0 = i0;
@@ -1465,7 +1643,7 @@ static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void*
     P.first = fh;
     bvc_status st = launch_first_hits(D, E.G, P.starts, N, i0, c, fh, s, E.sample_mesh, E.meshes);
     if (st != BVC_OK) return st;
-    st = launch_walk(D, false, kRecEnd, E.counting, P, s);
+    st = launch_walk(D, E.src, kRecEnd, E.counting, P, s);
     if (st != BVC_OK) return st;
     int64_t blocks = (c * 32 + 255) / 256;
     const int64_t cap = (int64_t)num_sms() * 16;
@@ -1475,6 +1653,8 @@ static bvc_status run_end_walks(const EndWalks& E, bvc_multi_cache* cache, void*
       k_moments<2><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, E.W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
     else
       k_moments<3><<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, E.W, P.starts, N, i0, fh, cache->mom_u, cache->mom_q);
+    if (E.src)
+      k_src_moments<<<(unsigned)blocks, 256, 0, s>>>(P.rec, c, E.W, D, i0, cache->mom_su, cache->mom_sq);
     BVC_LAUNCH_CHECK();
   }
   return BVC_OK;
@@ -1498,10 +1678,13 @@ extern "C" bvc_status bvc_multi_cache_build_workspace_size(bvc_geometry g, int64
 static bvc_status bvc_multi_cache_build_impl(bvc_geometry g, const double* coeffs, const bvc_cache_opts* opts,
                                             bvc_multi_cache* cache, void* workspace, size_t workspace_bytes,
                                             bvc_stream stream) {
-  if (g == nullptr || opts == nullptr || coeffs == nullptr || workspace == nullptr) return BVC_ERR_INVALID_ARG;
+  if (g == nullptr || opts == nullptr || coeffs == nullptr || workspace == nullptr || cache == nullptr)
+    return BVC_ERR_INVALID_ARG;
   const int D = g->dim;
   const int64_t N = opts->n_samples;
   const int32_t W = opts->walks_per_sample;
+  if (cache->n_src_cand != 0) return BVC_ERR_INVALID_ARG;  // a source cache: bvc_multi_cache_build_source
+  cache->n_bumps = 0;
   if (!valid_multi(cache, D) || cache->n != N || !valid_walk_args((float)opts->eps, opts->max_steps, W) ||
       !(opts->offset_l > 0.0))
     return BVC_ERR_INVALID_ARG;
@@ -1534,6 +1717,108 @@ extern "C" bvc_status bvc_multi_cache_build(bvc_geometry g, const double* coeffs
   return bvc::note_status(bvc_multi_cache_build_impl(g, coeffs, opts, cache, workspace, workspace_bytes, stream));
 }
 
+// The source variant: records D + 1 + 2 kMaxBumps planes per walk; the
+// source candidates' sampling scratch follows in the same workspace (used
+// after the walks).
+static size_t multi_src_scratch(int64_t ncand) {
+  size_t b = 0;
+  bvc_sample_source_workspace_size(ncand, &b);
+  return b + ((size_t)ncand * 8 + 255) / 256 * 256;  // + the candidates' f(y) |box| (unused)
+}
+static bvc_status bvc_multi_cache_build_source_workspace_size_impl(bvc_geometry g, const bvc_cache_opts* opts,
+                                                                  size_t* min_bytes, size_t* full_bytes) {
+  if (g == nullptr || opts == nullptr || opts->n_samples < 1 || opts->walks_per_sample < 1) return BVC_ERR_INVALID_ARG;
+  const int64_t ncand = src_candidates(opts, g->dim);
+  if (ncand < 1) return BVC_ERR_INVALID_ARG;
+  const size_t per = ws_per_start(g->dim, opts->walks_per_sample, g->dim + 2 * kMaxBumps);
+  const size_t src = multi_src_scratch(ncand);
+  if (min_bytes) *min_bytes = std::max(2 * kWsHead + per, src);
+  if (full_bytes) *full_bytes = std::max(2 * kWsHead + per * (size_t)opts->n_samples, src);
+  return BVC_OK;
+}
+extern "C" bvc_status bvc_multi_cache_build_source_workspace_size(bvc_geometry g, const bvc_cache_opts* opts,
+                                                                  size_t* min_bytes, size_t* full_bytes) {
+  return bvc::note_status(bvc_multi_cache_build_source_workspace_size_impl(g, opts, min_bytes, full_bytes));
+}
+
+static bvc_status bvc_multi_cache_build_source_impl(bvc_geometry g, const bvc_function* shape, const double* coeffs,
+                                                   const bvc_cache_opts* opts, bvc_multi_cache* cache,
+                                                   void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  if (g == nullptr || opts == nullptr || coeffs == nullptr || workspace == nullptr || shape == nullptr ||
+      cache == nullptr)
+    return BVC_ERR_INVALID_ARG;
+  const int D = g->dim;
+  const int64_t N = opts->n_samples;
+  const int32_t W = opts->walks_per_sample;
+  const int64_t ncand = src_candidates(opts, D);
+  if (opts->src_grid[0] < 1 || opts->src_grid[1] < 1 || (D == 3 && opts->src_grid[2] < 1)) return BVC_ERR_INVALID_ARG;
+  if (shape->n_terms != 1 || (shape->terms[0].kind != BVC_FN_GAUSS && shape->terms[0].kind != BVC_FN_GAUSS_LAPLACIAN))
+    return BVC_ERR_UNSUPPORTED;
+  const int head = shape->terms[0].kind == BVC_FN_GAUSS_LAPLACIAN ? 3 : 1;
+  const int nc = shape->terms[0].n_coeffs;
+  const int B = (nc - head) / (1 + D);
+  if (nc < head + 1 + D || (nc - head) % (1 + D) != 0 || B > kMaxBumps) return BVC_ERR_INVALID_ARG;
+  cache->n_bumps = B;
+  if (!valid_multi(cache, D) || cache->n != N || cache->n_src_cand != ncand ||
+      !valid_walk_args((float)opts->eps, opts->max_steps, W) || !(opts->offset_l > 0.0))
+    return BVC_ERR_INVALID_ARG;
+  if (opts->sigma != 0.0) return BVC_ERR_UNSUPPORTED;
+  DevFunction f;
+  if (!make_dev_function(shape, D, &f)) return BVC_ERR_INVALID_ARG;
+  const size_t per = ws_per_start(D, W, D + 2 * kMaxBumps);
+  int64_t chunk = ws_chunk(workspace_bytes, per);
+  if (chunk < 1 || workspace_bytes < multi_src_scratch(ncand)) return BVC_ERR_WORKSPACE;
+  if (chunk > N) chunk = N;
+  cudaStream_t s = (cudaStream_t)stream;
+  cache->bnd_measure = g->measure;
+  bvc_status st =
+      bvc_sample_boundary(g, N, opts->offset_l, opts->seed, cache->z, cache->nrm, cache->jac, nullptr, stream);
+  if (st != BVC_OK) return st;
+  EndWalks E{};
+  E.G = g->dev;
+  E.dim = D;
+  E.counting = g->counting != 0;
+  E.W = W;
+  E.eps = (float)opts->eps;
+  E.max_steps = opts->max_steps;
+  E.seed = opts->seed;
+  E.wid_base = opts->walk_id_base;
+  E.src = true;
+  E.f = f;
+  st = run_end_walks(E, cache, workspace, chunk, s);
+  if (st != BVC_OK) return st;
+  // Eq. 4's candidates, as bvc_cache_build samples them (the shape's f(y)
+  // |box| goes to scratch; the bump values are kept instead)
+  size_t sw = 0;
+  bvc_sample_source_workspace_size(ncand, &sw);
+  bvc_cache tmp{};
+  tmp.dim = D;
+  tmp.n_src_cand = ncand;
+  tmp.src_y = cache->src_y;
+  tmp.src_c = (double*)((char*)workspace + sw);
+  tmp.n_src_dev = cache->n_src_dev;
+  st = bvc_sample_source(g, shape, opts->src_grid, opts->seed, opts->offset_l, &tmp, workspace, sw, stream);
+  if (st != BVC_OK) return st;
+  double box = 1.0;
+  for (int a = 0; a < D; ++a) box *= (double)g->hi[a] - (double)g->lo[a];
+  {
+    ProfScope ps("multi_source_psi", s);
+    const unsigned gs = (unsigned)((ncand + 255) / 256);
+    if (D == 2)
+      k_src_psi<2><<<gs, 256, 0, s>>>(f, cache->src_y, ncand, cache->n_src_dev, box, cache->src_psi);
+    else
+      k_src_psi<3><<<gs, 256, 0, s>>>(f, cache->src_y, ncand, cache->n_src_dev, box, cache->src_psi);
+    BVC_LAUNCH_CHECK();
+  }
+  return launch_project(coeffs, cache, s);
+}
+extern "C" bvc_status bvc_multi_cache_build_source(bvc_geometry g, const bvc_function* shape, const double* coeffs,
+                                                   const bvc_cache_opts* opts, bvc_multi_cache* cache,
+                                                   void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(
+      bvc_multi_cache_build_source_impl(g, shape, coeffs, opts, cache, workspace, workspace_bytes, stream));
+}
+
 static bvc_status bvc_multi_cache_project_impl(const double* coeffs, bvc_multi_cache* cache, bvc_stream stream) {
   if (coeffs == nullptr || cache == nullptr || (cache->dim != 2 && cache->dim != 3) || !valid_multi(cache, cache->dim))
     return BVC_ERR_INVALID_ARG;
@@ -1548,7 +1833,9 @@ extern "C" bvc_status bvc_multi_cache_project(const double* coeffs, bvc_multi_ca
 // end-point walks of all meshes in one launch per workspace chunk over the
 // forest, the moments and one projection with per-mesh coefficients.
 static bool valid_batch_cache(const bvc_batch_s* b, const bvc_multi_cache* c) {
-  return b != nullptr && valid_multi(c, b->dim) && c->n == b->n_total && c->k == b->k;
+  // batches solve Laplace problems: no source part
+  return b != nullptr && valid_multi(c, b->dim) && c->n == b->n_total && c->k == b->k && c->n_bumps == 0 &&
+         c->n_src_cand == 0;
 }
 
 static bvc_status bvc_batch_build_workspace_size_impl(bvc_batch b, size_t* min_bytes, size_t* full_bytes) {

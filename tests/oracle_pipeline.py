@@ -43,6 +43,31 @@ def oracle_evaluate(cache, pts):
     return u, grad
 
 
+def difference_bound(cache, du, dq, pts, dc=None, rel=1e-5):
+    """Element-wise bound on |u_gpu(x) - u_oracle(x)| for two caches on the
+    same samples whose estimates differ by du, dq (per boundary sample) and dc
+    (per kept source candidate): the triangle inequality over Eq. 3 and Eq. 4,
+        sum_i (|dG/dn| |du_i| + |G| |dq_i|) / (p N) + sum_j |G| |dc_j| / M,
+    plus rel x the sum of |terms| (the gather's own FP32 tolerance)."""
+    z, n, jac = cache["z"], cache["n"], cache["jac"]
+    N = cache["N"]
+    _, _, _, _, ab_u = oracle.gather(z, n, du, np.zeros_like(du), cache["measure"], pts, want_abs=True, jac=jac,
+                                     sigma=cache.get("sigma", 0.0))
+    _, _, _, _, ab_q = oracle.gather(z, n, np.zeros_like(dq), dq, cache["measure"], pts, want_abs=True, jac=jac,
+                                     sigma=cache.get("sigma", 0.0))
+    _, _, _, _, ab = oracle.gather(z, n, cache["u_hat"], cache["q_hat"], cache["measure"], pts, cache["y"],
+                                   cache["c"], want_abs=True, jac=jac, sigma=cache.get("sigma", 0.0))
+    dim = pts.shape[1]
+    bound = (ab_u[:, 0] + ab_q[:, 0]) / N + rel * ab[:, 0] / N
+    if cache["n_src"]:
+        if dc is not None:
+            _, _, _, _, ab_c = oracle.gather(np.zeros((0, dim)), np.zeros((0, dim)), np.zeros(0), np.zeros(0), 1.0,
+                                             pts, cache["y"], dc, want_abs=True, sigma=cache.get("sigma", 0.0))
+            bound = bound + ab_c[:, 1 + dim] / cache["n_src"]
+        bound = bound + rel * ab[:, 1 + dim] / cache["n_src"]
+    return bound
+
+
 def oracle_bvc(V, F, g, f, N, W, l, eps, pts, seed, src_grid=None, max_steps=1 << 14, bvh=None, g_vertex=None,
                sigma=0.0):
     cache = oracle_cache(V, F, g, f, N, W, l, eps, seed, src_grid, max_steps, bvh, g_vertex, sigma)

@@ -134,3 +134,67 @@ def test_screened_walks_match_closed_form(dim):
     gexact[-1] = alpha * exact[0]
     gse = o["grad"].reshape(3, W, dim)[0].std(0) / np.sqrt(W)
     assert np.all(np.abs(gr - gexact) < 4 * gse + 1e-2), (gr, gexact, gse)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_screened_step_weights(dim):
+    """The screened source weights of a step against what fixes them: their
+    Poisson limit (sigma -> 0), the zero of the ball's Green's function on
+    its sphere, and two integrals over the ball with closed forms.  With
+    (sigma - Delta) v = 1 in B(0, R), v = 0 on the sphere, v(0) = (1 - C)/sigma,
+    and v(0) = int_B G = (1/R) int_0^R -w_u(rho) drho; with (sigma - Delta) v =
+    e.y, grad v(0) = e (1 - Qg)/sigma = -(e/(d R)) int_0^R w_g(rho) rho drho
+    (C, Qg the ball factors of the same t = R sqrt(sigma))."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    for R in (0.1, 0.8, 2.0):
+        for rho in (1e-3 * R, 0.37 * R, 0.9 * R):
+            _, _, wu0, wg0 = oracle.sphere_step(dim, R, 0.1, 0.2, rho / R)
+            wu, wg = oracle.screened_step_weights(dim, 1e-14, R, rho)
+            assert abs(wu - wu0) <= 1e-9 * abs(wu0) and abs(wg - wg0) <= 1e-9 * abs(wg0), (R, rho, wu, wu0, wg, wg0)
+        for sigma in (0.5, 4.0, 30.0):
+            t = R * np.sqrt(sigma)
+            Cf, Qg = oracle.screened_factors(dim, t)
+            wu_R, _ = oracle.screened_step_weights(dim, sigma, R, R * (1 - 1e-12))
+            assert abs(wu_R) < 1e-9 * R * R
+            iv = quad(lambda r: -oracle.screened_step_weights(dim, sigma, R, r)[0], 0.0, R, limit=200,
+                      epsabs=1e-14, epsrel=1e-11)[0] / R
+            assert abs(iv - (1.0 - Cf) / sigma) <= 1e-9 * (1.0 - Cf) / sigma, (dim, R, sigma, iv, (1 - Cf) / sigma)
+            ig = -quad(lambda r: oracle.screened_step_weights(dim, sigma, R, r)[1] * r, 0.0, R, limit=200,
+                       epsabs=1e-14, epsrel=1e-11)[0] / (dim * R)
+            assert abs(ig - (1.0 - Qg) / sigma) <= 1e-9 * abs(1.0 - Qg) / sigma, (dim, R, sigma, ig, (1 - Qg) / sigma)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_screened_walks_with_source_match_closed_form(dim):
+    """(Delta - sigma) u = f with u = exp(alpha x_last) cos(beta x_0) and
+    sigma != alpha^2 - beta^2, so f = (alpha^2 - beta^2 - sigma) u: the walks'
+    mean value and gradient at three points against u and grad u."""
+    alpha, beta, sigma = 1.5, 1.0, 3.0
+    lam = alpha ** 2 - beta ** 2 - sigma
+    if dim == 2:
+        V, F = wl.circle_polygon(512)
+    else:
+        V, F = wl.icosphere(4)
+        V = V.astype(np.float32)
+    g = [(EXP_COS, [1.0, alpha, beta])]
+    f = [(EXP_COS, [lam, alpha, beta])]
+    bvh = oracle.BVH(V, F)
+    starts = np.array([[0.0, 0.0, 0.0][:dim], [0.3, -0.2, 0.1][:dim], [-0.5, 0.1, 0.2][:dim]], np.float32)
+    W = 20000
+    o = oracle.walks(bvh, g, f, starts, W, 1e-4, 1 << 14, 5, sigma=sigma)
+    U = o["U"].reshape(3, W)
+    s64 = starts.astype(np.float64)
+    exact = np.exp(alpha * s64[:, -1]) * np.cos(beta * s64[:, 0])
+    se = U.std(1) / np.sqrt(W)
+    assert np.all(np.abs(U.mean(1) - exact) < 4 * se + 2e-3 * np.abs(exact)), (U.mean(1), exact, se)
+    for j in range(3):
+        gr = o["grad"].reshape(3, W, dim)[j].mean(0)
+        gexact = np.zeros(dim)
+        gexact[0] = -beta * np.exp(alpha * s64[j, -1]) * np.sin(beta * s64[j, 0])
+        gexact[-1] = alpha * exact[j]
+        gse = o["grad"].reshape(3, W, dim)[j].std(0) / np.sqrt(W)
+        assert np.all(np.abs(gr - gexact) < 4 * gse + 1e-2), (j, gr, gexact, gse)
+    # the source matters: without it the walks miss u by many standard errors
+    o0 = oracle.walks(bvh, g, [], starts, 4000, 1e-4, 1 << 14, 5, sigma=sigma)
+    U0 = o0["U"].reshape(3, 4000)
+    assert np.any(np.abs(U0.mean(1) - exact) > 10 * U0.std(1) / np.sqrt(4000))
