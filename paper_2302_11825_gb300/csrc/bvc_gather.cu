@@ -36,7 +36,18 @@
 namespace bvc {
 
 constexpr int kGBlock = 256;
-constexpr int kTile = 128;  // samples per tile (FP32 partial-sum length)
+// Tiles of 128 samples: FP32 partial sums over at most 128 samples keep the
+// worst-case rounding below 128 x 2^-24 = 7.6e-6 of the sum of |terms|, inside
+// the gather's 1e-5 tolerance.  (256-sample tiles, or flushing every 2 or 4
+// tiles, were 1-4% faster on GB300 but double that worst case.)
+#ifndef BVC_GATHER_TILE
+#define BVC_GATHER_TILE 128
+#endif
+#ifndef BVC_GATHER_FLUSH
+#define BVC_GATHER_FLUSH 1
+#endif
+constexpr int kTile = BVC_GATHER_TILE;    // samples per tile copy
+constexpr int kFlush = BVC_GATHER_FLUSH;  // tiles per FP32 partial sum (then added in FP64)
 // Evaluation points per thread and resident CTAs per SM, per kind of sample
 // (measured on GB300: boundary tiles are FMA/SFU-bound and gain from reuse
 // of each shared-memory sample across 6 points; source tiles are SFU-bound
@@ -291,6 +302,7 @@ __global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gathe
   for (int j = 0; j < kGPts; ++j)
 #pragma unroll
     for (int q = 0; q < NA; ++q) acc64[j][q] = 0.0;
+  f2 acc[NP][NA];  // FP32 partial sums over kFlush tiles
 
   if (nt > 0) {
     if (threadIdx.x == 0) {
@@ -320,11 +332,11 @@ __global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gathe
         return;
       }
       const int cnt = (int)min64(kTile, s1 - (s0 + it * kTile));
-      f2 acc[NP][NA];
+      if (it % kFlush == 0)
 #pragma unroll
-      for (int j = 0; j < NP; ++j)
+        for (int j = 0; j < NP; ++j)
 #pragma unroll
-        for (int q = 0; q < NA; ++q) acc[j][q] = 0ull;
+          for (int q = 0; q < NA; ++q) acc[j][q] = 0ull;
       const ulonglong2* T = reinterpret_cast<const ulonglong2*>(tile[b]);
 #pragma unroll 2
       for (int s = 0; s < cnt; ++s) {
@@ -339,15 +351,16 @@ __global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gathe
             pair_bnd3<GRAD>(Ts, px[j], py[j], pz[j], acc[j]);
         }
       }
+      if (it % kFlush == kFlush - 1 || it == nt - 1)
 #pragma unroll
-      for (int j = 0; j < NP; ++j)
+        for (int j = 0; j < NP; ++j)
 #pragma unroll
-        for (int q = 0; q < NA; ++q) {
-          float lo, hi;
-          upk(acc[j][q], lo, hi);
-          acc64[2 * j][q] += (double)lo;
-          acc64[2 * j + 1][q] += (double)hi;
-        }
+          for (int q = 0; q < NA; ++q) {
+            float lo, hi;
+            upk(acc[j][q], lo, hi);
+            acc64[2 * j][q] += (double)lo;
+            acc64[2 * j + 1][q] += (double)hi;
+          }
       __syncthreads();  // every thread is done with tile[b]
       if (threadIdx.x == 0 && it + 2 < nt) {
         fence_proxy_async();

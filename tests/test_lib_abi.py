@@ -221,6 +221,11 @@ def test_multi_rhs_host_checks(lib):
     assert lib.bvc_multi_cache_project(None, None, None) == 1
     lib.bvc_evaluate_multi.restype = C.c_int
     assert lib.bvc_evaluate_multi(None, None, C.c_int64(0), None, None) == 1
+    # the source variant: null handles and arguments are argument errors
+    lib.bvc_multi_cache_build_source_workspace_size.restype = C.c_int
+    assert lib.bvc_multi_cache_build_source_workspace_size(None, None, C.byref(mn), None) == 1
+    lib.bvc_multi_cache_build_source.restype = C.c_int
+    assert lib.bvc_multi_cache_build_source(None, None, None, None, None, None, C.c_size_t(0), None) == 1
 
 
 def test_harmonic_polynomial_generator():
