@@ -25,7 +25,11 @@
 // copies (cp.async.bulk, completion on an mbarrier), double-buffered; one
 // thread issues them while 256 threads each carry 6 (boundary) or 2
 // (source) evaluation points.  The
-// FP32 sums over a tile are added to FP64 accumulators once per tile.
+// FP32 sums over a tile are added to FP64 accumulators once per tile
+// (registers at 2 points per thread; shared memory, one slot per thread,
+// point and plane, at 4 and 6, which frees the registers the wider shapes
+// need: on GB300 the 6-point boundary gather went from 234 to 212 ms on
+// the 1.31M-triangle sphere, ahead of the 2-point shape's 224 ms).
 // Large cache sizes are split across CTAs; split partials are reduced in a
 // fixed order, so results are deterministic.
 #include <cmath>
@@ -60,7 +64,11 @@ constexpr int kFlush = BVC_GATHER_FLUSH;  // tiles per FP32 partial sum (then ad
 template <int PTS>
 struct GatherShape {
   static constexpr int kPts = PTS;
-  static constexpr int kMinBlocks = PTS <= 2 ? 4 : 2;
+  static constexpr int kMinBlocks = PTS <= 2 ? 4 : (PTS == 4 ? 3 : 2);
+  // FP64 per-point sums in shared memory (one slot per thread, point and
+  // plane) instead of registers: frees 4 registers per sum for the wider
+  // shapes, which only touch them once per tile
+  static constexpr bool kSmemAcc = PTS >= 4;
   static constexpr int kPtsPerCta = kGBlock * PTS;
 };
 constexpr int kDefaultPts[2][2] = {{6, 2}, {4, 2}};  // [dim - 2][kind]
@@ -297,11 +305,18 @@ __global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gathe
     py[j] = pk(c[0][1], c[1][1]);
     pz[j] = pk(c[0][2], c[1][2]);
   }
-  double acc64[kGPts][NA];
+  constexpr bool SA = GatherShape<PTS>::kSmemAcc;
+  __shared__ double sacc[SA ? kGPts * NA * kGBlock : 1];
+  double acc64[SA ? 1 : kGPts][SA ? 1 : NA];
 #pragma unroll
   for (int j = 0; j < kGPts; ++j)
 #pragma unroll
-    for (int q = 0; q < NA; ++q) acc64[j][q] = 0.0;
+    for (int q = 0; q < NA; ++q) {
+      if (SA)
+        sacc[(j * NA + q) * kGBlock + threadIdx.x] = 0.0;
+      else
+        acc64[SA ? 0 : j][SA ? 0 : q] = 0.0;
+    }
   f2 acc[NP][NA];  // FP32 partial sums over kFlush tiles
 
   if (nt > 0) {
@@ -358,8 +373,13 @@ __global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gathe
           for (int q = 0; q < NA; ++q) {
             float lo, hi;
             upk(acc[j][q], lo, hi);
-            acc64[2 * j][q] += (double)lo;
-            acc64[2 * j + 1][q] += (double)hi;
+            if (SA) {
+              sacc[((2 * j) * NA + q) * kGBlock + threadIdx.x] += (double)lo;
+              sacc[((2 * j + 1) * NA + q) * kGBlock + threadIdx.x] += (double)hi;
+            } else {
+              acc64[SA ? 0 : 2 * j][SA ? 0 : q] += (double)lo;
+              acc64[SA ? 0 : 2 * j + 1][SA ? 0 : q] += (double)hi;
+            }
           }
       __syncthreads();  // every thread is done with tile[b]
       if (threadIdx.x == 0 && it + 2 < nt) {
@@ -379,10 +399,13 @@ __global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gathe
     if (A.n_splits == 1) {
       if (nt > 0)
 #pragma unroll
-        for (int q = 0; q < NA; ++q) A.out[q][k] += acc64[j][q];
+        for (int q = 0; q < NA; ++q)
+          A.out[q][k] += SA ? sacc[(j * NA + q) * kGBlock + threadIdx.x] : acc64[SA ? 0 : j][SA ? 0 : q];
     } else {
 #pragma unroll
-      for (int q = 0; q < NA; ++q) A.part[((int64_t)sp * NA + q) * A.m + k] = acc64[j][q];
+      for (int q = 0; q < NA; ++q)
+        A.part[((int64_t)sp * NA + q) * A.m + k] =
+            SA ? sacc[(j * NA + q) * kGBlock + threadIdx.x] : acc64[SA ? 0 : j][SA ? 0 : q];
     }
   }
 }
