@@ -21,7 +21,13 @@ mean-value property or published known answers, except as noted:
   area, see tests/test_oracle_offset.py; the screened source weights of a
   walk step (``screened_step_weights``, reading of Eq. 1 with sigma > 0) by
   their sigma -> 0 limit, two closed-form integrals over the ball and walk
-  means against a closed-form solution, see tests/test_oracle_screened.py)
+  means against a closed-form solution, see tests/test_oracle_screened.py;
+  the screened walk on stars (``ball_green_sigma``, ``star_kernel_sigma``,
+  ``Wost.walks(sigma=...)``) by the radial equation and boundary value of
+  the ball's Green's function, its unit flux at the centre, Green's
+  identity on a sphere inside the ball for e^(a.x), the sigma -> 0 limits
+  and walk means against closed-form solutions with Neumann data, see
+  tests/test_oracle_wost_screened.py)
 """
 from __future__ import annotations
 
@@ -110,6 +116,10 @@ def _load():
                 "orc_wost_free": (None, [P]),
                 "orc_wost_counts": (i64, [P, P]),
                 "orc_wost_walks": (None, [P, P, P, P, P, P, P, i64, i32, f64, i32, u64, u64, u32, P, P, P, P]),
+                "orc_wost_walks_sigma": (None, [P, P, P, P, P, f64, P, P, i64, i32, f64, i32, u64, u64, u32, P, P,
+                                                P, P]),
+                "orc_ball_green_sigma": (f64, [C.c_int, f64, f64, f64]),
+                "orc_star_kernel_sigma": (f64, [C.c_int, f64, f64, f64]),
                 "orc_wost_query": (None, [P, P, i64, P, P]),
                 "orc_wost_rays": (None, [P, P, P, P, i64, f64, P, P]),
             }
@@ -220,6 +230,20 @@ def screened_step_weights(dim: int, sigma: float, R: float, rho: float):
     _load().orc_screened_step_weights(int(dim), float(np.sqrt(sigma)), float(R), float(rho), C.byref(wu),
                                       C.byref(wg))
     return wu.value, wg.value
+
+
+def ball_green_sigma(dim: int, sigma: float, R: float, rho: float) -> float:
+    """The Green's function of (sigma - Delta) on the ball of radius R that
+    vanishes on its sphere, seen from the centre at distance rho (sigma = 0:
+    the Laplace ball's)."""
+    return _load().orc_ball_green_sigma(int(dim), float(np.sqrt(sigma)), float(R), float(rho))
+
+
+def star_kernel_sigma(dim: int, sigma: float, R: float, r: float) -> float:
+    """Throughput factor W(r) = -|S| r^(d-1) G'(r) of a screened walk-on-stars
+    step whose direction first meets the boundary at distance r (1 for
+    sigma = 0)."""
+    return _load().orc_star_kernel_sigma(int(dim), float(np.sqrt(sigma)), float(R), float(r))
 
 
 # ---------------------------------------------------------------- geometry
@@ -559,10 +583,12 @@ class Wost:
         return t, e
 
     def walks(self, g_terms, h_value, h_potential, f_terms, starts, start_elem, W: int, eps: float,
-              max_steps: int, seed: int, id_base: int = 0, tag: int = TAG_WALK):
+              max_steps: int, seed: int, id_base: int = 0, tag: int = TAG_WALK, sigma: float = 0.0):
         """W walks from each FP32 start; start_elem[i] >= 0 puts start i on
         that Neumann element.  Returns per-walk U, grad[.., dim], steps and
-        the Dirichlet element of the end."""
+        the Dirichlet element of the end.  sigma > 0: the screened equation
+        (Delta - sigma) u = f (each step's throughput factor W(r), the ball's
+        screened Green's function in the Neumann and source terms)."""
         starts = _f32(starts)
         n, dim = starts.shape
         T = n * W
@@ -570,9 +596,9 @@ class Wost:
         steps, prim = np.zeros(T, np.int32), np.zeros(T, np.int32)
         se = None if start_elem is None else _i32(start_elem)
         g, hv, hp, f = (encode_function(t) for t in (g_terms, h_value, h_potential, f_terms))
-        self._lib.orc_wost_walks(self.h, _p(g), _p(hv), _p(hp), _p(f), _p(starts), _p(se), n, int(W), float(eps),
-                                 int(max_steps), int(seed), int(id_base), int(tag), _p(U), _p(grad), _p(steps),
-                                 _p(prim))
+        self._lib.orc_wost_walks_sigma(self.h, _p(g), _p(hv), _p(hp), _p(f), float(np.sqrt(sigma)), _p(starts),
+                                       _p(se), n, int(W), float(eps), int(max_steps), int(seed), int(id_base),
+                                       int(tag), _p(U), _p(grad), _p(steps), _p(prim))
         return {"U": U, "grad": grad, "steps": steps, "prim": prim}
 
     def __del__(self):

@@ -1209,6 +1209,46 @@ void orc_screened_step_weights(int dim, double k, double R, double rho, double* 
   }
 }
 
+/* The ball's screened Green's function seen from its centre, for a point at */
+/* distance rho (0 < rho <= R): the Green's function of (sigma - Delta) on   */
+/* B(x, R) that vanishes on the sphere (k = sqrt(sigma); see                 */
+/* orc_screened_step_weights); k = 0 gives the Laplace ball's ln(R/rho)/(2   */
+/* pi) (2D) and (1/rho - 1/R)/(4 pi) (3D).                                   */
+double orc_ball_green_sigma(int dim, double k, double R, double rho) {
+  if (!(k > 0.0))
+    return dim == 2 ? log(R / rho) / (2.0 * ORC_PI) : (1.0 / rho - 1.0 / R) / (4.0 * ORC_PI);
+  const double tr = k * rho, tR = k * R;
+  if (dim == 2)
+    return (orc_bessel_k(0, tr) - orc_bessel_k(0, tR) * orc_bessel_i(0, tr) / orc_bessel_i(0, tR)) / (2.0 * ORC_PI);
+  if (tR > 20.0) /* sinh(a)/sinh(b) written with decaying exponentials */
+    return exp(-tr) * (1.0 - exp(-2.0 * (tR - tr))) / ((1.0 - exp(-2.0 * tR)) * 4.0 * ORC_PI * rho);
+  return sinh(tR - tr) / (4.0 * ORC_PI * rho * sinh(tR));
+}
+
+/* Throughput factor of a walk-on-stars step of the screened equation.  On a */
+/* region St star-shaped about x inside B(x, R), Green's second identity     */
+/* with the ball's Green's function G (above) gives u(x) as the integral of  */
+/* u(z) (-dG/dn_z) over the parts of the boundary of St, plus the G-weighted */
+/* Neumann and source terms.  G depends on r = |z - x| only, and a boundary  */
+/* element seen from x under the solid angle dw has n_z . (z - x)/r dz =     */
+/* r^(d-1) dw, so a direction drawn uniformly on the sphere (the walk's step) */
+/* carries the factor W(r) = -|S| r^(d-1) G'(r) at the first boundary point  */
+/* z it meets, r its distance:                                               */
+/*   2D  W = kr [K1(kr) + K0(kR) I1(kr) / I0(kR)]                            */
+/*   3D  W = [kr cosh(k(R - r)) + sinh(k(R - r))] / sinh(kR)                 */
+/* W(R) is the screened mean-value factor of the ball and W -> 1 as r -> 0;  */
+/* for k = 0 (Laplace) W = 1 for every r, the walk on stars of Sec. 3.1.     */
+double orc_star_kernel_sigma(int dim, double k, double R, double r) {
+  if (!(k > 0.0)) return 1.0;
+  if (!(r > 0.0)) return 1.0;
+  const double tr = k * r, tR = k * R;
+  if (dim == 2)
+    return tr * (orc_bessel_k(1, tr) + orc_bessel_k(0, tR) * orc_bessel_i(1, tr) / orc_bessel_i(0, tR));
+  if (tR > 20.0)
+    return exp(-tr) * (tr * (1.0 + exp(-2.0 * (tR - tr))) + (1.0 - exp(-2.0 * (tR - tr)))) / (1.0 - exp(-2.0 * tR));
+  return (tr * cosh(tR - tr) + sinh(tR - tr)) / sinh(tR);
+}
+
 static void walk_one(const walk_ctx_t* w, const double* x0, uint64_t wid, double* U_out, double* grad_out,
                      int32_t* steps_out, int32_t* prim_out, double* pend_out, double* scale_out) {
   const int dim = w->bvh->m.dim;
@@ -2078,6 +2118,7 @@ typedef struct {
   int max_steps;
   uint64_t seed;
   uint32_t tag;
+  double sqs; /* sqrt(sigma) of the screened equation; 0 = Poisson */
 } wost_ctx_t;
 
 /* The Neumann term of one star step (see above). */
@@ -2138,7 +2179,7 @@ static double wost_neumann_term(const wost_ctx_t* c, const double* x, int on_n, 
     if (fabs(cs) < 1e-4) continue; /* grazing elements do not occlude */
     if (ray_elem(w, e, x, dir, &th) && th < r * (1.0 - 1e-9)) return 0.0;
   }
-  const double gb = dim == 2 ? log(R / r) / (2.0 * ORC_PI) : (1.0 / r - 1.0 / R) / (4.0 * ORC_PI);
+  const double gb = orc_ball_green_sigma(dim, c->sqs, R, r);
   const double inv_a = on_n ? 2.0 : 1.0;
   return inv_a * gb * orc_neumann_eval(c->hv, c->hp, dim, z, w->nrm + pick * dim) * total;
 }
@@ -2173,7 +2214,7 @@ static double wost_own_term(const wost_ctx_t* c, const double* x, int64_t self, 
     if (!(rmax > 0.0)) return 0.0;
     rho = u[1] * rmax;
     for (int k = 0; k < 2; ++k) z[k] = x[k] + sgn * rho * t[k];
-    return 2.0 * (log(R / rho) / (2.0 * ORC_PI)) * orc_neumann_eval(c->hv, c->hp, dim, z, n) * 2.0 * rmax;
+    return 2.0 * orc_ball_green_sigma(dim, c->sqs, R, rho) * orc_neumann_eval(c->hv, c->hp, dim, z, n) * 2.0 * rmax;
   }
   const double* P[3] = {w->V + 3 * (int64_t)f[0], w->V + 3 * (int64_t)f[1], w->V + 3 * (int64_t)f[2]};
   double e1[3], e2[3], d[3];
@@ -2206,7 +2247,7 @@ static double wost_own_term(const wost_ctx_t* c, const double* x, int64_t self, 
   if (!(rmax > 0.0)) return 0.0;
   rho = u[1] * rmax;
   for (int k = 0; k < 3; ++k) z[k] = x[k] + rho * d[k];
-  return 2.0 * ((1.0 / rho - 1.0 / R) / (4.0 * ORC_PI)) * orc_neumann_eval(c->hv, c->hp, dim, z, n) *
+  return 2.0 * orc_ball_green_sigma(dim, c->sqs, R, rho) * orc_neumann_eval(c->hv, c->hp, dim, z, n) *
          (2.0 * ORC_PI * rho * rmax);
 }
 
@@ -2222,6 +2263,10 @@ static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uin
   if (on_n)
     for (int a = 0; a < dim; ++a) nx[a] = w->nrm[e0 * dim + a];
   double acc = 0.0, wf0 = 0.0, wg0 = 0.0, R0 = 0.0, cv = 0.0;
+  /* screened: the walk's throughput (the product of its steps' factors: the */
+  /* gradient ball's C, each star step's W(r)) and the gradient ball's C, Qg */
+  const double sk = c->sqs;
+  double thr = 1.0, C0 = 1.0, Qg0 = 1.0;
   int k = 0;
   int64_t prim = -1;
   for (;;) {
@@ -2241,7 +2286,12 @@ static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uin
         /* the gradient ball: B(x, d_all) holds no boundary */
         const double R = dA;
         orc_sphere_step(dim, R, u[0], u[1], u[2], om, &rho, &wu, &wg);
+        if (sk > 0.0) {
+          orc_screened_factors(dim, sk * R, &C0, &Qg0);
+          thr = C0;
+        }
         if (has_f) {
+          if (sk > 0.0) orc_screened_step_weights(dim, sk, R, rho, &wu, &wg);
           double y[3] = {0, 0, 0};
           for (int a = 0; a < dim; ++a) y[a] = x[a] + rho * om[a];
           const double fy = orc_fn_eval(c->f, dim, y);
@@ -2271,17 +2321,25 @@ static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uin
     double th;
     const int64_t eh = wost_ray(w, x, om, R, on_n ? self : -1, &th);
     const double r = eh >= 0 ? th : R;
+    /* this step's source and Neumann terms carry the throughput into it */
     if (has_f && r > 0.0) { /* a crossing at t = 0 leaves no segment */
       const double rr = r * u[2];
       double y[3] = {0, 0, 0};
       for (int a = 0; a < dim; ++a) y[a] = x[a] + rr * om[a];
-      const double wsrc = dim == 2 ? -r * rr * log(R / rr) : -r * rr * (1.0 - rr / R);
-      acc += wsrc * orc_fn_eval(c->f, dim, y);
+      /* -|S| r rr^(d-1) G(rr): the ball's weight at rr scaled by r / R */
+      double wsrc = dim == 2 ? -r * rr * log(R / rr) : -r * rr * (1.0 - rr / R);
+      if (sk > 0.0) {
+        double wb, wgb;
+        orc_screened_step_weights(dim, sk, R, rr, &wb, &wgb);
+        wsrc = (r / R) * wb;
+      }
+      acc += thr * wsrc * orc_fn_eval(c->f, dim, y);
     }
     if (has_h) {
-      acc += wost_neumann_term(c, x, on_n, self, R, wid, (uint32_t)(k - 1));
-      if (on_n) acc += wost_own_term(c, x, self, R, wid, (uint32_t)(k - 1));
+      acc += thr * wost_neumann_term(c, x, on_n, self, R, wid, (uint32_t)(k - 1));
+      if (on_n) acc += thr * wost_own_term(c, x, self, R, wid, (uint32_t)(k - 1));
     }
+    if (sk > 0.0) thr *= orc_star_kernel_sigma(dim, sk, R, r);
     if (eh >= 0) {
       for (int a = 0; a < dim; ++a) {
         x[a] += th * om[a];
@@ -2295,9 +2353,12 @@ static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uin
       self = -1;
     }
   }
-  const double U = orc_fn_eval(c->g, dim, pbar) + acc;
+  const double U = thr * orc_fn_eval(c->g, dim, pbar) + acc;
   *U_out = U;
-  const double s = R0 > 0.0 ? ((double)dim / R0) * (U - wf0 - cv) + wg0 : 0.0;
+  /* screened: (U - wf0) / C0 estimates u at the gradient ball's sphere point */
+  const double s = !(R0 > 0.0) ? 0.0
+                   : sk > 0.0  ? ((double)dim / R0) * Qg0 * ((U - wf0) / C0 - cv) + wg0
+                               : ((double)dim / R0) * (U - wf0 - cv) + wg0;
   for (int a = 0; a < dim; ++a) grad_out[a] = s * nu[a];
   *steps_out = k;
   *prim_out = prim >= 0 ? (int32_t)w->dir_ids[prim] : -1;
@@ -2307,12 +2368,13 @@ static void wost_walk_one(const wost_ctx_t* c, const double* x0, int64_t e0, uin
 /* Neumann element; -1: inside).  Walk j of start i has id                   */
 /* id_base + i*W + j; outputs per walk: U, grad[dim], steps, the Dirichlet   */
 /* element of the end (whole numbering).                                      */
-void orc_wost_walks(void* h, const double* g, const double* hv, const double* hp, const double* f,
-                    const float* starts, const int32_t* start_elem, int64_t n, int32_t W, double eps,
-                    int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
-                    int32_t* steps, int32_t* prim) {
+/* sqs = sqrt(sigma) > 0: the screened equation (Delta - sigma) u = f.      */
+void orc_wost_walks_sigma(void* h, const double* g, const double* hv, const double* hp, const double* f,
+                          double sqs, const float* starts, const int32_t* start_elem, int64_t n, int32_t W,
+                          double eps, int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U,
+                          double* grad, int32_t* steps, int32_t* prim) {
   const wost_t* w = (const wost_t*)h;
-  const wost_ctx_t c = {w, g, hv, hp, f, eps, max_steps, seed, tag};
+  const wost_ctx_t c = {w, g, hv, hp, f, eps, max_steps, seed, tag, sqs};
   const int dim = w->dim;
   const int64_t total = n * (int64_t)W;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -2323,6 +2385,14 @@ void orc_wost_walks(void* h, const double* g, const double* hv, const double* hp
     wost_walk_one(&c, x0, start_elem ? start_elem[i] : -1, id_base + (uint64_t)t, &U[t], &grad[t * dim], &steps[t],
                   &prim[t]);
   }
+}
+
+void orc_wost_walks(void* h, const double* g, const double* hv, const double* hp, const double* f,
+                    const float* starts, const int32_t* start_elem, int64_t n, int32_t W, double eps,
+                    int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, double* U, double* grad,
+                    int32_t* steps, int32_t* prim) {
+  orc_wost_walks_sigma(h, g, hv, hp, f, 0.0, starts, start_elem, n, W, eps, max_steps, seed, id_base, tag, U, grad,
+                       steps, prim);
 }
 
 /* Queries for the tests: distances to the Dirichlet part and to the closest */

@@ -74,22 +74,23 @@ def oracle_bvc(V, F, g, f, N, W, l, eps, pts, seed, src_grid=None, max_steps=1 <
     return oracle_evaluate(cache, pts)
 
 
-def mixed_pipeline(V, F, neu, u, f, N, W, l, eps, seed, pts):
+def mixed_pipeline(V, F, neu, u, f, N, W, l, eps, seed, pts, sigma=0.0):
     """The mixed cache (Sec. 3.2) with the oracle: samples on the Neumann
     part keep offset 0 and carry du/dn = h; Dirichlet samples lie on the
     offset boundary built from the Dirichlet elements and carry walk
-    estimates of u and du/dn; Eq. 3 at the points."""
+    estimates of u and du/dn; Eq. 3 at the points.  sigma > 0: the screened
+    walks on stars and the screened gather of App. A."""
     dim = V.shape[1]
     w = oracle.Wost(V, F, neu)
     z, n, e, jac = oracle.sample_boundary_mixed(V, F, N, l, seed, neu)
     on_n = neu[e] == 1
     se = np.where(on_n, e, -1).astype(np.int32)
-    o = w.walks(u, [], u, f, z.astype(np.float32), se, W, eps, 1 << 16, seed)
+    o = w.walks(u, [], u, f, z.astype(np.float32), se, W, eps, 1 << 16, seed, sigma=sigma)
     u_hat = o["U"].reshape(N, W).mean(1)
     q_walk = np.einsum("iwd,id->i", o["grad"].reshape(N, W, dim), n) / W
     h = oracle.neumann_eval([], u, dim, z.astype(np.float32).astype(np.float64), n.astype(np.float32)
                             .astype(np.float64))
     q_hat = np.where(on_n, h, q_walk)
     ub, _, gb, _ = oracle.gather(z.astype(np.float32), n.astype(np.float32), u_hat, q_hat,
-                                 oracle.boundary_measure(V, F), pts, jac=jac.astype(np.float32))
+                                 oracle.boundary_measure(V, F), pts, jac=jac.astype(np.float32), sigma=sigma)
     return ub / N, gb / N, (z, n, e, u_hat, q_hat)
