@@ -734,11 +734,42 @@ bvc_status bvc_mixed_walk(bvc_mixed m, const bvc_function* gfn, const bvc_neuman
                           float eps, int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, float* rec,
                           int32_t* steps, int32_t* prim, unsigned long long* counter, bvc_stream stream);
 
+/* Walks on stars for the screened equation (Delta - sigma) u = f with u = g
+ * on the Dirichlet part and du/dn = h on the Neumann part (Eq. 1 with
+ * sigma > 0; Sec. 3.1's walk on stars with the screened Green's functions
+ * of App. A).  Arguments, records and draws as bvc_mixed_walk; sigma = 0 is
+ * bvc_mixed_walk, negative or non-finite sigma BVC_ERR_INVALID_ARG.  With
+ * k = sqrt(sigma) and G(rho) the Green's function of (sigma - Delta) on the
+ * step's ball B(x, R) that vanishes on its sphere,
+ *   2D  G = [K0(k rho) - K0(kR) I0(k rho)/I0(kR)] / (2 pi)
+ *   3D  G = sinh(k (R - rho)) / (4 pi rho sinh kR),
+ * every estimate the walk carries past a step is multiplied by that step's
+ * factor: the gradient ball's mean-value factor C (t / sinh t in 3D,
+ * 1 / I0(t) in 2D, t = kR), and for a star step whose direction meets the
+ * boundary first at distance r (r = R when it meets the sphere)
+ * W(r) = -|S| r^(dim-1) G'(r) = kr [K1(kr) + K0(kR) I1(kr)/I0(kR)] (2D),
+ * [kr cosh(k(R - r)) + sinh(k(R - r))] / sinh kR (3D), which is C at r = R
+ * and 1 as r -> 0 (Green's identity on the star-shaped region, whose
+ * boundary elements seen from x under the solid angle dw have
+ * n . (z - x) / r dz = r^(dim-1) dw).  A step's source and Neumann terms use
+ * G in place of the Laplace ball's Green's function (the source sample at
+ * rho = r u2: -|S| r rho^(dim-1) G(rho)), weighted by the product of the
+ * factors of the steps before it; the gradient of a start inside the domain
+ * is (dim/R0) Qg [(U - w_f0)/C - cv] nu + w_g0, as wos_estimate_sigma. */
+bvc_status bvc_mixed_walk_sigma(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
+                                double sigma, const float* starts, const int32_t* start_elem, const float* nrm,
+                                int64_t n, int32_t walks, float eps, int32_t max_steps, uint64_t seed, uint64_t id_base,
+                                uint32_t tag, float* rec, int32_t* steps, int32_t* prim, unsigned long long* counter,
+                                bvc_stream stream);
+
 /* The mixed cache: K1 on the whole boundary (Neumann samples at offset 0,
  * Dirichlet samples on the Dirichlet offset boundary at offset_l), walks on
  * stars (tag 0, ids as bvc_cache_build), K3, source samples (opts->src_grid,
- * inside the whole boundary itself), pack.  dudn_hat of a Neumann sample is h(z).  sigma and
- * clamp_c must be 0.  Workspace as bvc_cache_build on the whole geometry. */
+ * inside the whole boundary itself), pack.  dudn_hat of a Neumann sample is h(z).
+ * opts->sigma > 0: the screened walks of bvc_mixed_walk_sigma, and the cache
+ * records sigma so that bvc_evaluate uses the screened Green's functions of
+ * App. A.  clamp_c must be 0 (BVC_ERR_UNSUPPORTED otherwise).  Workspace as
+ * bvc_cache_build on the whole geometry. */
 bvc_status bvc_mixed_cache_build_workspace_size(bvc_mixed m, const bvc_cache_opts* opts, size_t* min_bytes,
                                                 size_t* full_bytes);
 bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
@@ -751,6 +782,12 @@ bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn, const bvc
 bvc_status wost_estimate(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
                          bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps, uint64_t seed,
                          uint64_t id_base, void* workspace, size_t workspace_bytes, bvc_stream stream);
+/* wost_estimate for the screened equation (Delta - sigma) u = f (sigma >= 0;
+ * the walks of bvc_mixed_walk_sigma).  sigma = 0 is wost_estimate. */
+bvc_status wost_estimate_sigma(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h, const bvc_function* ffn,
+                               double sigma, bvc_eval_state* state, int32_t walks, float eps, int32_t max_steps,
+                               uint64_t seed, uint64_t id_base, void* workspace, size_t workspace_bytes,
+                               bvc_stream stream);
 
 /* ------------------------------------------------------------- profiling */
 /* Between bvc_profile_begin and bvc_profile_end every kernel the library

@@ -178,11 +178,15 @@ def _declare(lib):
         "bvc_mixed_rays": (S, [P, P, P, P, i64, f32, P, P, P]),
         "bvc_mixed_walk": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function), P, P, P, i64,
                                i32, f32, i32, u64, u64, u32, P, P, P, P, P]),
+        "bvc_mixed_walk_sigma": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function), f64, P,
+                                     P, P, i64, i32, f32, i32, u64, u64, u32, P, P, P, P, P]),
         "bvc_mixed_cache_build_workspace_size": (S, [P, C.POINTER(CacheOpts), C.POINTER(sz), C.POINTER(sz)]),
         "bvc_mixed_cache_build": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function),
                                       C.POINTER(CacheOpts), C.POINTER(CacheStruct), P, sz, P]),
         "wost_estimate": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function),
                               C.POINTER(EvalStateStruct), i32, f32, i32, u64, u64, P, sz, P]),
+        "wost_estimate_sigma": (S, [P, C.POINTER(Function), C.POINTER(NeumannStruct), C.POINTER(Function), f64,
+                                    C.POINTER(EvalStateStruct), i32, f32, i32, u64, u64, P, sz, P]),
         "bvc_profile_begin": (S, []),
         "bvc_profile_end": (S, [C.POINTER(KernelTime), i32, C.POINTER(C.c_int32)]),
         "bvc_gather_status": (S, [C.POINTER(C.c_uint64), i32]),
@@ -1091,8 +1095,9 @@ def mixed_rays(m: Mixed, org: torch.Tensor, dirs: torch.Tensor, tmax: float, ski
 
 
 def mixed_walk(m: Mixed, g_terms, h, f_terms, starts, start_elem, nrm, walks: int, eps: float, max_steps: int,
-               seed: int, id_base: int = 0, tag: int = TAG_WALK, debug=False, stream=None):
-    """bvc_mixed_walk: per-walk records (U, and n.grad / h or grad)."""
+               seed: int, id_base: int = 0, tag: int = TAG_WALK, debug=False, stream=None, sigma: float = 0.0):
+    """bvc_mixed_walk: per-walk records (U, and n.grad / h or grad).
+    sigma > 0: the screened equation (bvc_mixed_walk_sigma)."""
     _dev(starts, torch.float32)
     n = starts.shape[1]
     planes = 1 if nrm is not None else m.dim
@@ -1101,6 +1106,12 @@ def mixed_walk(m: Mixed, g_terms, h, f_terms, starts, start_elem, nrm, walks: in
     prim = torch.empty(n * walks, dtype=torch.int32, device="cuda") if debug else None
     counter = torch.zeros(1, dtype=torch.int64, device="cuda")
     g, f, hn = make_function(g_terms), make_function(f_terms), make_neumann(h)
+    if sigma:
+        _check(lib().bvc_mixed_walk_sigma(m.h, C.byref(g), C.byref(hn), C.byref(f), float(sigma), _ptr(starts),
+                                          _ptr(start_elem), _ptr(nrm), n, int(walks), float(eps), int(max_steps),
+                                          int(seed), int(id_base), int(tag), _ptr(rec), _ptr(steps), _ptr(prim),
+                                          _ptr(counter), _stream(stream)), "bvc_mixed_walk_sigma")
+        return rec, steps, prim
     _check(lib().bvc_mixed_walk(m.h, C.byref(g), C.byref(hn), C.byref(f), _ptr(starts), _ptr(start_elem), _ptr(nrm),
                                 n, int(walks), float(eps), int(max_steps), int(seed), int(id_base), int(tag),
                                 _ptr(rec), _ptr(steps), _ptr(prim), _ptr(counter), _stream(stream)),
@@ -1130,12 +1141,18 @@ def mixed_cache_build(m: Mixed, g_terms, h, f_terms, opts: CacheOpts, cache: Cac
 
 
 def wost_estimate(m: Mixed, g_terms, h, f_terms, state: EvalState, walks: int, eps: float, max_steps: int,
-                  seed: int, id_base: int = 0, ws: torch.Tensor = None, stream=None):
+                  seed: int, id_base: int = 0, ws: torch.Tensor = None, stream=None, sigma: float = 0.0):
     """Pointwise walk on stars: adds `walks` walks per point to the state's
-    running sums (finalise with get_solution)."""
+    running sums (finalise with get_solution).  sigma > 0: the screened
+    equation (wost_estimate_sigma)."""
     if ws is None:
         ws = workspace(wos_workspace_size(state.dim, state.m, walks)[1])
     g, f, hn = make_function(g_terms), make_function(f_terms), make_neumann(h)
+    if sigma:
+        _check(lib().wost_estimate_sigma(m.h, C.byref(g), C.byref(hn), C.byref(f), float(sigma),
+                                         C.byref(state.struct), int(walks), float(eps), int(max_steps), int(seed),
+                                         int(id_base), _ptr(ws), ws.numel(), _stream(stream)), "wost_estimate_sigma")
+        return state
     _check(lib().wost_estimate(m.h, C.byref(g), C.byref(hn), C.byref(f), C.byref(state.struct), int(walks),
                                float(eps), int(max_steps), int(seed), int(id_base), _ptr(ws), ws.numel(),
                                _stream(stream)), "wost_estimate")

@@ -470,6 +470,38 @@ __device__ __forceinline__ void screened_step_weights(float k, float R, float rh
   }
 }
 
+// Screened walk on stars (Sec. 3.1 with sigma > 0).  The ball's Green's
+// function G of (sigma - Delta) on B(x, R), zero on its sphere (see
+// screened_step_weights), at distance rho from the centre:
+//   2D  [K0(k rho) - K0(kR) I0(k rho)/I0(kR)] / (2 pi)
+//   3D  sinh(k (R - rho)) / (4 pi rho sinh kR)
+template <int D>
+__device__ __forceinline__ float ball_green_sigma(float k, float R, float rho) {
+  const float tr = k * rho, tR = k * R;
+  if (D == 2) {
+    const float G = fmaf(-__expf(tr - 2.0f * tR) * bessel_k0e(tR), bessel_i0e(tr) / bessel_i0e(tR),
+                         __expf(-tr) * bessel_k0e(tr));
+    return G * (0.5f / kPiF);
+  }
+  return __expf(-tr) * (expm1f(-2.0f * (tR - tr)) / expm1f(-2.0f * tR)) * (0.25f / kPiF) / rho;
+}
+// The factor a step's direction carries to the first boundary point it
+// meets at distance r <= R: W(r) = -|S| r^(D-1) dG/dr (Green's identity on
+// the star-shaped region with the ball's G; W(R) is the ball's mean-value
+// factor, W -> 1 as r -> 0):
+//   2D  kr [K1(kr) + K0(kR) I1(kr)/I0(kR)]
+//   3D  [kr cosh(k (R - r)) + sinh(k (R - r))] / sinh kR
+template <int D>
+__device__ __forceinline__ float star_kernel_sigma(float k, float R, float r) {
+  const float tr = k * r, tR = k * R;
+  if (!(tr > 0.0f)) return 1.0f;
+  if (D == 2)
+    return tr * fmaf(__expf(tr - 2.0f * tR) * bessel_k0e(tR), bessel_i1e(tr) / bessel_i0e(tR),
+                     __expf(-tr) * bessel_k1e(tr));
+  const float ea = expm1f(-2.0f * (tR - tr));  // e^-2(tR - tr) - 1
+  return __expf(-tr) * fmaf(tr, 2.0f + ea, -ea) / -expm1f(-2.0f * tR);
+}
+
 // ------------------------------------------- canonical closest-point distance
 // S = (a.x, a.y, ab.x, ab.y), inv = 1/|ab|^2.
 __device__ __forceinline__ float seg_d2(const float4 S, float inv, float px, float py) {

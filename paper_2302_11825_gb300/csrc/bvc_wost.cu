@@ -132,6 +132,7 @@ struct WostParams {
   const float2* nmeas;  // Neumann tree: subtree measures of each node's children
   const int32_t* neu_q;  // Neumann element -> its position in the Neumann tree's primitive order
   float escape;         // 4 x bounding-box diagonal: a walk farther from the Dirichlet part has escaped
+  float sqs;            // sqrt(sigma) of the screened equation (used by the SCR variant)
   unsigned long long* stats;
   unsigned long long* counter;
 };
@@ -718,7 +719,13 @@ __global__ void __launch_bounds__(128) k_mixed_rays(DevGeometry Gn, int32_t has_
 #ifndef BVC_WOST_MINB
 #define BVC_WOST_MINB 4
 #endif
-template <int D, bool HAS_F, bool HAS_H, int REC>
+// SCR: the screened equation (Delta - sigma) u = f: the gradient ball
+// multiplies the walk's throughput by its mean-value factor C and scales
+// the gradient by Qg (screened_factors); a star step whose direction meets
+// the boundary at distance r multiplies it by W(r) (star_kernel_sigma); the
+// step's source and Neumann terms use the ball's screened Green's function
+// (screened_step_weights, ball_green_sigma) and the throughput into the step.
+template <int D, bool HAS_F, bool HAS_H, int REC, bool SCR>
 __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostParams P) {
   __shared__ int snode[kWStack * kWostBlock];
   __shared__ float sdist[kWStack * kWostBlock];
@@ -737,6 +744,7 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
   bool on_n = false, start_on_n = false;
   int self = -1, k = 0;
   float acc = 0.0f, wf0 = 0.0f, wg0 = 0.0f, R0 = 0.0f, cv = 0.0f;
+  float thr = 1.0f, C0 = 1.0f, Qg0 = 1.0f;  // screened: throughput, gradient ball's factors
   Hit<D> h;
   for (;;) {
     // ---- idle lanes take the next walks
@@ -774,6 +782,7 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
           }
           start_on_n = on_n;
           acc = wf0 = wg0 = R0 = cv = 0.0f;
+          if (SCR) thr = C0 = Qg0 = 1.0f;
           k = 0;
         }
       }
@@ -825,17 +834,22 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
           // the gradient ball B(x, d_all): no boundary inside
           ball = true;
           const float R = dA;
+          if (SCR) {
+            screened_factors<D>(P.sqs * R, C0, Qg0);
+            thr = C0;
+          }
           if (HAS_F) {
             const float rho = R * u2;
             float y[D];
 #pragma unroll
             for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
             const float fy = eval_fn<D, true>(P.f, y);
-            const float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho);
+            float wu = D == 2 ? R * rho * __logf(u2) : -rho * (R - rho), wg = 0.0f;
+            if (SCR) screened_step_weights<D>(P.sqs, R, rho, true, wu, wg);
             acc = fmaf(wu, fy, acc);
             wf0 = wu * fy;
             const float q = D == 2 ? u2 * u2 : u2 * u2 * u2;
-            wg0 = -R * (1.0f - q) * fy;
+            wg0 = (SCR ? wg : -R * (1.0f - q)) * fy;
           }
           R0 = R;
 #pragma unroll
@@ -869,7 +883,13 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
           float y[D];
 #pragma unroll
           for (int a = 0; a < D; ++a) y[a] = fmaf(rho, om[a], x[a]);
-          const float wu = D == 2 ? rl * rho * __logf(rho / R) : -rl * rho * (1.0f - rho / R);
+          float wu = D == 2 ? rl * rho * __logf(rho / R) : -rl * rho * (1.0f - rho / R);
+          if (SCR) {
+            // the ball's weight at rho, scaled by r / R (rho is uniform on [0, r])
+            float wb, wgb;
+            screened_step_weights<D>(P.sqs, R, rho, false, wb, wgb);
+            wu = thr * (rl / R) * wb;
+          }
           acc = fmaf(wu, eval_fn<D, true>(P.f, y), acc);
         }
         if (HAS_H && P.has_neu) {
@@ -895,7 +915,8 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
                   ray_first<D, true>(P.Gn, x, dz, rz * (1.0f - 1e-5f), on_n ? self : -1, ez, 0.0f, tv, nv, sn, sd, tc);
               if (ev < 0) {
                 // G^B of -Laplacian: ln(R/r)/(2 pi) (2D), (1/r - 1/R)/(4 pi) (3D)
-                const float gb = D == 2 ? __logf(R * ir) * (0.5f / kPiF) : (ir - 1.0f / R) * (0.25f / kPiF);
+                const float gb = SCR ? thr * ball_green_sigma<D>(P.sqs, R, rz)
+                                     : (D == 2 ? __logf(R * ir) * (0.5f / kPiF) : (ir - 1.0f / R) * (0.25f / kPiF));
                 acc = fmaf((on_n ? 2.0f : 1.0f) * gb * ipdf, neumann_h<D>(P.hv, P.hp, z, nz), acc);
               }
             }
@@ -904,11 +925,14 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
             const U4 r3 = philox_draw(P.seed, P.wid0 + (uint64_t)t, (uint32_t)(k - 1), P.tag + 12u);
             float rho;
             if (sample_own<D>(P.Gn, P.neu_q[self], x, R, u01f(r3.x), u01f(r3.y), z, nz, rho, ipdf)) {
-              const float gb = D == 2 ? __logf(R / rho) * (0.5f / kPiF) : (1.0f / rho - 1.0f / R) * (0.25f / kPiF);
+              const float gb = SCR ? thr * ball_green_sigma<D>(P.sqs, R, rho)
+                                   : (D == 2 ? __logf(R / rho) * (0.5f / kPiF)
+                                             : (1.0f / rho - 1.0f / R) * (0.25f / kPiF));
               acc = fmaf(2.0f * gb * ipdf, neumann_h<D>(P.hv, P.hp, z, nz), acc);
             }
           }
         }
+        if (SCR) thr *= star_kernel_sigma<D>(P.sqs, R, rl);
         if (eh >= 0) {
 #pragma unroll
           for (int a = 0; a < D; ++a) {
@@ -927,8 +951,12 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
       continue;
     }
     // ---- the walk ended: its records
-    const float U = eval_fn<D, true>(P.g, pbar) + acc;
-    const float sc = R0 > 0.0f ? ((float)D / R0) * (U - wf0 - cv) + wg0 : 0.0f;
+    const float gend = eval_fn<D, true>(P.g, pbar);
+    const float U = (SCR ? thr * gend : gend) + acc;
+    // screened: (U - wf0) / C0 estimates u at the gradient ball's sphere point
+    const float sc = !(R0 > 0.0f) ? 0.0f
+                     : SCR       ? fmaf(((float)D / R0) * Qg0, (U - wf0) / C0 - cv, wg0)
+                                 : ((float)D / R0) * (U - wf0 - cv) + wg0;
     P.rec[t] = U;
     if (REC == kRecGnW) {
       float v;
@@ -973,16 +1001,21 @@ __global__ void __launch_bounds__(kWostBlock, BVC_WOST_MINB) k_wost(const WostPa
   }
 }
 
+// The screened variant always runs the Neumann term (zero data adds zeros).
 template <int D, int REC>
-static const void* wost_kernel(bool has_f, bool has_h) {
-  if (has_f) return has_h ? (const void*)k_wost<D, true, true, REC> : (const void*)k_wost<D, true, false, REC>;
-  return has_h ? (const void*)k_wost<D, false, true, REC> : (const void*)k_wost<D, false, false, REC>;
+static const void* wost_kernel(bool has_f, bool has_h, bool scr) {
+  if (scr) return has_f ? (const void*)k_wost<D, true, true, REC, true> : (const void*)k_wost<D, false, true, REC, true>;
+  if (has_f)
+    return has_h ? (const void*)k_wost<D, true, true, REC, false> : (const void*)k_wost<D, true, false, REC, false>;
+  return has_h ? (const void*)k_wost<D, false, true, REC, false> : (const void*)k_wost<D, false, false, REC, false>;
 }
 
 static bvc_status launch_wost(int dim, int rec, const WostParams& P, cudaStream_t s) {
-  const bool hf = P.f.n_terms > 0, hh = P.hv.n_terms > 0 || P.hp.n_terms > 0;
-  const void* kern = dim == 2 ? (rec == kRecGnW ? wost_kernel<2, kRecGnW>(hf, hh) : wost_kernel<2, kRecGradW>(hf, hh))
-                              : (rec == kRecGnW ? wost_kernel<3, kRecGnW>(hf, hh) : wost_kernel<3, kRecGradW>(hf, hh));
+  const bool hf = P.f.n_terms > 0, hh = P.hv.n_terms > 0 || P.hp.n_terms > 0, sc = P.sqs > 0.0f;
+  const void* kern = dim == 2 ? (rec == kRecGnW ? wost_kernel<2, kRecGnW>(hf, hh, sc)
+                                                : wost_kernel<2, kRecGradW>(hf, hh, sc))
+                              : (rec == kRecGnW ? wost_kernel<3, kRecGnW>(hf, hh, sc)
+                                                : wost_kernel<3, kRecGradW>(hf, hh, sc));
   const int bps = max_blocks_per_sm(kern, kWostBlock, 0);
   int64_t grid = (int64_t)num_sms() * (bps > 0 ? bps : 1);
   const int64_t need = (P.total + kWostBlock - 1) / kWostBlock;
@@ -1168,6 +1201,7 @@ static bool fill_params(bvc_mixed m, const bvc_function* gfn, const bvc_neumann*
 static bool valid_walk(float eps, int32_t max_steps, int32_t walks) {
   return std::isfinite(eps) && eps > 0.0f && max_steps >= 1 && walks >= 1;
 }
+static bool valid_sigma(double sigma) { return std::isfinite(sigma) && sigma >= 0.0; }
 
 }  // namespace bvc
 
@@ -1497,16 +1531,17 @@ extern "C" bvc_status bvc_mixed_rays(bvc_mixed m, const float* org, const float*
 }
 
 static bvc_status bvc_mixed_walk_impl(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
-                                     const bvc_function* ffn, const float* starts, const int32_t* start_elem,
-                                     const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps,
-                                     uint64_t seed, uint64_t id_base, uint32_t tag, float* rec, int32_t* steps,
-                                     int32_t* prim, unsigned long long* counter, bvc_stream stream) {
-  if (m == nullptr || n < 0 || !valid_walk(eps, max_steps, walks)) return BVC_ERR_INVALID_ARG;
+                                     const bvc_function* ffn, double sigma, const float* starts,
+                                     const int32_t* start_elem, const float* nrm, int64_t n, int32_t walks, float eps,
+                                     int32_t max_steps, uint64_t seed, uint64_t id_base, uint32_t tag, float* rec,
+                                     int32_t* steps, int32_t* prim, unsigned long long* counter, bvc_stream stream) {
+  if (m == nullptr || n < 0 || !valid_walk(eps, max_steps, walks) || !valid_sigma(sigma)) return BVC_ERR_INVALID_ARG;
   if (n == 0) return BVC_OK;
   if (starts == nullptr || rec == nullptr || counter == nullptr || (start_elem != nullptr && nrm == nullptr))
     return BVC_ERR_INVALID_ARG;
   WostParams P;
   if (!fill_params(m, gfn, h, ffn, P)) return BVC_ERR_INVALID_ARG;
+  P.sqs = (float)std::sqrt(sigma);
   P.starts = starts;
   P.start_elem = start_elem;
   P.nrm = nrm;
@@ -1530,7 +1565,17 @@ extern "C" bvc_status bvc_mixed_walk(bvc_mixed m, const bvc_function* gfn, const
                                      const float* nrm, int64_t n, int32_t walks, float eps, int32_t max_steps,
                                      uint64_t seed, uint64_t id_base, uint32_t tag, float* rec, int32_t* steps,
                                      int32_t* prim, unsigned long long* counter, bvc_stream stream) {
-  return bvc::note_status(bvc_mixed_walk_impl(m, gfn, h, ffn, starts, start_elem, nrm, n, walks, eps, max_steps, seed, id_base, tag, rec, steps, prim, counter, stream));
+  return bvc::note_status(bvc_mixed_walk_impl(m, gfn, h, ffn, 0.0, starts, start_elem, nrm, n, walks, eps, max_steps,
+                                              seed, id_base, tag, rec, steps, prim, counter, stream));
+}
+extern "C" bvc_status bvc_mixed_walk_sigma(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+                                           const bvc_function* ffn, double sigma, const float* starts,
+                                           const int32_t* start_elem, const float* nrm, int64_t n, int32_t walks,
+                                           float eps, int32_t max_steps, uint64_t seed, uint64_t id_base,
+                                           uint32_t tag, float* rec, int32_t* steps, int32_t* prim,
+                                           unsigned long long* counter, bvc_stream stream) {
+  return bvc::note_status(bvc_mixed_walk_impl(m, gfn, h, ffn, sigma, starts, start_elem, nrm, n, walks, eps,
+                                              max_steps, seed, id_base, tag, rec, steps, prim, counter, stream));
 }
 
 // Workspace of the mixed cache: [0, 256) work counter, the samples' elements
@@ -1568,7 +1613,8 @@ static bvc_status bvc_mixed_cache_build_impl(bvc_mixed m, const bvc_function* gf
       cache->u_hat == nullptr ||
       cache->dudn_hat == nullptr || cache->packed == nullptr || workspace == nullptr)
     return BVC_ERR_INVALID_ARG;
-  if (opts->sigma != 0.0 || opts->clamp_c != 0.0) return BVC_ERR_UNSUPPORTED;
+  if (!valid_sigma(opts->sigma)) return BVC_ERR_INVALID_ARG;
+  if (opts->clamp_c != 0.0) return BVC_ERR_UNSUPPORTED;
   const int64_t ncand = (int64_t)opts->src_grid[0] * opts->src_grid[1] * (D == 3 ? opts->src_grid[2] : 1);
   if (ncand != cache->n_src_cand || ncand < 0) return BVC_ERR_INVALID_ARG;
   WostParams P;
@@ -1579,7 +1625,8 @@ static bvc_status bvc_mixed_cache_build_impl(bvc_mixed m, const bvc_function* gf
   int64_t chunk = (int64_t)((workspace_bytes - head) / per);
   if (chunk > N) chunk = N;
   cudaStream_t s = (cudaStream_t)stream;
-  cache->sigma = 0.0;
+  P.sqs = (float)std::sqrt(opts->sigma);
+  cache->sigma = opts->sigma;
   cache->clamp_c = 0.0;
   cache->bnd_measure = m->whole->measure;
   int32_t* elem = (int32_t*)((char*)workspace + 256);
@@ -1631,17 +1678,18 @@ extern "C" bvc_status bvc_mixed_cache_build(bvc_mixed m, const bvc_function* gfn
 }
 
 static bvc_status wost_estimate_impl(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
-                                    const bvc_function* ffn, bvc_eval_state* state, int32_t walks, float eps,
-                                    int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
+                                    const bvc_function* ffn, double sigma, bvc_eval_state* state, int32_t walks,
+                                    float eps, int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
                                     size_t workspace_bytes, bvc_stream stream) {
   if (m == nullptr || state == nullptr || state->dim != m->dim || state->m < 0 || state->counts == nullptr ||
-      !valid_walk(eps, max_steps, walks))
+      !valid_walk(eps, max_steps, walks) || !valid_sigma(sigma))
     return BVC_ERR_INVALID_ARG;
   const int64_t M = state->m;
   if (M > 0 && (state->x == nullptr || state->u_bnd == nullptr || workspace == nullptr)) return BVC_ERR_INVALID_ARG;
   const int D = m->dim;
   WostParams P;
   if (!fill_params(m, gfn, h, ffn, P)) return BVC_ERR_INVALID_ARG;
+  P.sqs = (float)std::sqrt(sigma);
   cudaStream_t s = (cudaStream_t)stream;
   if (M > 0) {
     const size_t per = (size_t)walks * (1 + D) * sizeof(float);
@@ -1690,5 +1738,13 @@ extern "C" bvc_status wost_estimate(bvc_mixed m, const bvc_function* gfn, const 
                                     const bvc_function* ffn, bvc_eval_state* state, int32_t walks, float eps,
                                     int32_t max_steps, uint64_t seed, uint64_t id_base, void* workspace,
                                     size_t workspace_bytes, bvc_stream stream) {
-  return bvc::note_status(wost_estimate_impl(m, gfn, h, ffn, state, walks, eps, max_steps, seed, id_base, workspace, workspace_bytes, stream));
+  return bvc::note_status(wost_estimate_impl(m, gfn, h, ffn, 0.0, state, walks, eps, max_steps, seed, id_base,
+                                             workspace, workspace_bytes, stream));
+}
+extern "C" bvc_status wost_estimate_sigma(bvc_mixed m, const bvc_function* gfn, const bvc_neumann* h,
+                                          const bvc_function* ffn, double sigma, bvc_eval_state* state, int32_t walks,
+                                          float eps, int32_t max_steps, uint64_t seed, uint64_t id_base,
+                                          void* workspace, size_t workspace_bytes, bvc_stream stream) {
+  return bvc::note_status(wost_estimate_impl(m, gfn, h, ffn, sigma, state, walks, eps, max_steps, seed, id_base,
+                                             workspace, workspace_bytes, stream));
 }
