@@ -302,6 +302,30 @@ def near_band(dim: int) -> float:
     return 1.0 if dim == 2 else 2.0
 
 
+def pick_schedule(step, seed: int = 4321):
+    """Setup, not timed: whether a solve should run its pointwise walks (the
+    points near the boundary) on the main stream before the cache build, or
+    on a second stream beside the cache build and gather.  Times one solve
+    each way (after one of each to warm up) with CUDA events and keeps the
+    faster: two persistent walk launches on two streams share the SMs, which
+    pays off on some workloads and costs on others (measured on GB300: the
+    2D star 59.1 ms overlapped vs 60.0 ms serial, the 3D sphere 587 ms vs
+    498 ms)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for serial in (False, True):
+        step(seed, serial=serial)
+    torch.cuda.synchronize()
+    ev[0].record()
+    step(seed, serial=False)
+    ev[1].record()
+    step(seed, serial=True)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_over, t_ser = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    return t_ser < t_over, {"serial": t_ser < t_over, "overlap_ms": t_over, "serial_ms": t_ser}
+
+
 class Solver:
     """Device buffers and the step sequence of one BVC solve."""
 
@@ -341,13 +365,21 @@ class Solver:
         self.u_near = torch.empty(self.m_near, dtype=torch.float64, device=device)
         self.g_near = torch.empty((w.dim, self.m_near), dtype=torch.float64, device=device)
         # the pointwise estimates near the boundary do not depend on the cache:
-        # they run on a second stream, overlapping the cache build and gather
+        # they run on a second stream, overlapping the cache build and gather,
+        # or before them on the main stream, whichever one solve each way
+        # finds faster (setup, not timed)
         self.side = torch.cuda.Stream(device=device)
+        self.serial = False
+        self.schedule = {"serial": False}
+        if self.m_near:
+            self.serial, self.schedule = pick_schedule(self.step)
 
-    def step(self, seed: int, serial: bool = False):
+    def step(self, seed: int, serial: bool = None):
         """One solve.  serial: the pointwise walks run on the main stream
-        before the cache build (for per-kernel timing)."""
+        before the cache build (None: the schedule picked at setup; True
+        for per-kernel timing)."""
         bvc, w, torch = self.bvc, self.w, self.torch
+        serial = self.serial if serial is None else serial
         main = torch.cuda.current_stream()
         if self.m_near:
             if not serial:
@@ -1139,13 +1171,20 @@ class MixedSolver:
         self.u_near = torch.empty(self.m_near, dtype=torch.float64, device=device)
         self.g_near = torch.empty((w.dim, self.m_near), dtype=torch.float64, device=device)
         self.side = torch.cuda.Stream(device=device)
+        self.serial = False
+        self.schedule = {"serial": False}
+        if self.m_near:
+            self.serial, self.schedule = pick_schedule(self.step)
 
-    def step(self, seed: int):
+    def step(self, seed: int, serial: bool = None):
+        """One solve; serial as Solver.step."""
         bvc, w, torch = self.bvc, self.w, self.torch
+        serial = self.serial if serial is None else serial
         main = torch.cuda.current_stream()
         if self.m_near:
-            self.side.wait_stream(main)
-            with torch.cuda.stream(self.side):
+            if not serial:
+                self.side.wait_stream(main)
+            with torch.cuda.stream(main if serial else self.side):
                 bvc.eval_state_reset(self.near)
                 bvc.wost_estimate(self.m, w.g, self.h, w.f, self.near, self.near_walks, w.eps, MAX_STEPS, seed, 0,
                                   self.ws_wos)
@@ -1155,7 +1194,7 @@ class MixedSolver:
         bvc.mixed_cache_build(self.m, w.g, self.h, w.f, self.opts, self.cache, self.ws_cache)
         bvc.evaluate(self.cache, self.far, self.ws_eval)
         bvc.get_solution(self.far, self.u_far, self.g_far)
-        if self.m_near:
+        if self.m_near and not serial:
             main.wait_stream(self.side)
 
 
@@ -1387,12 +1426,15 @@ def bench_mixed(args, rank, local, ws):
                    "walks_per_sample": w.walks, "src_grid": list(w.src_grid), "src_kept": n_src_kept,
                    "eval_points": int(M), "eval_far": int(s.m_far), "eval_near_pointwise": int(s.m_near),
                    "near_walks": s.near_walks, "eps": w.eps, "offset_l": w.offset_l,
-                   "silhouette_gap": s.silhouette_gap,
+                   "silhouette_gap": s.silhouette_gap, "near_schedule": s.schedule,
                    "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
         "roofline": roofs.get(dominant), "rooflines_all": roofs, "kernels": kernels,
-        "kernels_note": "each launch timed by events on its own stream; the pointwise walks near the Dirichlet "
-                        "part and their reduction run on a second stream beside the cache build, so their "
-                        "times include waiting for SMs",
+        "kernels_note": ("each launch timed by events on its own stream; the pointwise walks near the Dirichlet "
+                         "part run on the main stream before the cache build (the schedule picked at setup)"
+                         if s.serial else
+                         "each launch timed by events on its own stream; the pointwise walks near the Dirichlet "
+                         "part and their reduction run on a second stream beside the cache build (the schedule "
+                         "picked at setup), so their times include waiting for SMs"),
         "e2e": {"value": step_value(M, e2e_steps, ws, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(M * dim * 4), "d2h_bytes_per_step": int(M * (1 + dim) * 8),
                 "steps": e2e_steps},
@@ -1647,6 +1689,7 @@ def main():
                    "near_walks": w.walks, "eps": w.eps, "offset_l": w.offset_l, "near_band_l": s.band,
                    "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{ws}",
                    "sums": "fp64",
+                   "near_schedule": s.schedule,
                    "walk_shape": {"blocks_per_sm": s.walk_shape[0], "chunk": s.walk_shape[1],
                                   "tuned_ms": s.walk_shape[2]},
                    "gather_points_per_thread": {"boundary": s.gather_shape[0][0], "source": s.gather_shape[0][1],
