@@ -56,6 +56,8 @@ MAX_STEPS = 1 << 14
 # primitive test (2D: a segment's two endpoints, 16 B; 3D: three vertices,
 # 48 B), per-walk input/output bytes, FP32 flops per pair.
 BYTES_NODE = {2: 48 + 32, 3: 64 + 48}
+# the node record alone (two child boxes and links), without the slabs
+BYTES_NODE_BOXES = {2: 48, 3: 64}
 BYTES_PRIM = {2: 16, 3: 48}
 # bytes the walk kernel actually loads per primitive test: the 2D record
 # also holds the edge vector, 1/|edge|^2 and the element id (two float4)
@@ -415,11 +417,12 @@ class Solver:
         return cache_stats, near_stats
 
 
-def walk_bytes(stats, dim, n_walks, prim_bytes=None):
+def walk_bytes(stats, dim, n_walks, prim_bytes=None, node_bytes=None):
     """Bytes of a walk launch: node fetches x bytes per node + primitive
     tests x bytes per primitive (algorithmic by default) + per-walk I/O."""
     prim_bytes = BYTES_PRIM if prim_bytes is None else prim_bytes
-    return (stats["nodes"] * BYTES_NODE[dim] + stats["prims"] * prim_bytes[dim]
+    node_bytes = BYTES_NODE if node_bytes is None else node_bytes
+    return (stats["nodes"] * node_bytes[dim] + stats["prims"] * prim_bytes[dim]
             + n_walks * (2 * dim * 4 + 8))
 
 
@@ -1637,6 +1640,10 @@ def main():
     l2_bytes = int(torch.cuda.get_device_properties(local).L2_cache_size)
     resident = s.geom.info().device_bytes < l2_bytes / 2
     walk_gbs = walk_alg / (walk_ms_step / 1e3) / 1e9
+    # the same with the node record alone (48 / 64 B per node fetch, no slabs)
+    walk_boxes_gbs = (walk_bytes(cache_stats, dim, n_walks_cache, BYTES_PRIM, BYTES_NODE_BOXES)
+                      + walk_bytes(near_stats, dim, n_walks_near, BYTES_PRIM, BYTES_NODE_BOXES)) \
+        / (walk_ms_step / 1e3) / 1e9
     if dominant == "walk":
         peak = float(peaks["hbm_gbs"])
         # achieved, traffic: per bench step, over its cache-walk and pointwise-walk launches
@@ -1644,8 +1651,10 @@ def main():
                     "traffic": profile_traffic("walk", w.name), "kernel": "walk",
                     "peak_source": f"{peak_src} (hbm_gbs)",
                     "fetched_gbs": walk_fetch / (walk_ms_step / 1e3) / 1e9,
+                    "achieved_without_slab_bytes_gbs": walk_boxes_gbs,
                     "note": ("tree and mesh fit in half the L2; " if resident else "tree and mesh exceed half the "
-                             "L2; ") + "bytes are algorithmic (node fetches x 48/64 B + primitive tests x 16/48 B "
+                             "L2; ") + "bytes are algorithmic (node fetches x 80/112 B: both child boxes and links, "
+                             "48/64 B, and both children's slabs, 32/48 B; primitive tests x 16/48 B "
                              "+ per-walk I/O) over the walk launches' own time"}
     else:
         kname = dominant
