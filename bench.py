@@ -1305,7 +1305,15 @@ def mixed_oracle_step_s(w, budget_s: float = 20.0):
     pair_rate = 64 * N / (time.perf_counter() - t0)
     M = w.eval_pts.shape[0]
     n_src = w.src_grid[0] * w.src_grid[1] if w.f else 0
-    t_step = N * w.walks / walk_rate + M * (N + 0.45 * n_src) / pair_rate
+    # share of the source candidates inside the domain (kept by K4): the
+    # oracle's inside test on 2,048 uniform points of the bounding box
+    kept_share = 0.0
+    if n_src:
+        lo, hi = w.V.min(0), w.V.max(0)
+        q = np.random.default_rng(2).uniform(lo, hi, (2048, w.dim))
+        inside = (oracle.inside2d_f32(w.V, w.F, q) if w.dim == 2 else oracle.winding3d(w.V, w.F, q) > 0.5)
+        kept_share = float(np.mean(inside > 0))
+    t_step = N * w.walks / walk_rate + M * (N + kept_share * n_src) / pair_rate
 
     def one_core():
         t0 = time.perf_counter()
@@ -1321,7 +1329,8 @@ def mixed_oracle_step_s(w, budget_s: float = 20.0):
     info = {"cores": oracle.num_threads(), "walks_per_s": walk_rate, "pairs_per_s": pair_rate,
             "single_core": single_core(one_core), "cpu_model": cpu_model(),
             "sample": f"{sel.size} samples x {w.walks} walks on stars; 64 points x {N} samples; "
-                      f"extrapolated to one full step"}
+                      f"the kept share of source candidates ({kept_share:.3f}) from an inside test of 2,048 "
+                      f"points; extrapolated to one full step"}
     return t_step, info
 
 
