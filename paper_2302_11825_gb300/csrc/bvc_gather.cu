@@ -50,6 +50,17 @@ constexpr int kGBlock = 256;
 #ifndef BVC_GATHER_FLUSH
 #define BVC_GATHER_FLUSH 1
 #endif
+// Samples per unrolled body of the pair loop (measured on GB300 with the
+// autotuned shapes: 3D 2 / 4 / 8 -> 212.3 / 209.4 / 212.8 ms on the
+// 1.31M-triangle sphere; 2D 2 / 4 / 8 -> 27.3 / 26.2 / 25.6 ms for the
+// 20k-segment star's boundary and source gathers).
+#ifndef BVC_GATHER_UNROLL_2D
+#define BVC_GATHER_UNROLL_2D 8
+#endif
+#ifndef BVC_GATHER_UNROLL_3D
+#define BVC_GATHER_UNROLL_3D 4
+#endif
+constexpr int kUnroll2 = BVC_GATHER_UNROLL_2D, kUnroll3 = BVC_GATHER_UNROLL_3D;
 constexpr int kTile = BVC_GATHER_TILE;    // samples per tile copy
 constexpr int kFlush = BVC_GATHER_FLUSH;  // tiles per FP32 partial sum (then added in FP64)
 // Evaluation points per thread and resident CTAs per SM, per kind of sample
@@ -353,7 +364,7 @@ __global__ void __launch_bounds__(kGBlock, GatherShape<PTS>::kMinBlocks) k_gathe
 #pragma unroll
           for (int q = 0; q < NA; ++q) acc[j][q] = 0ull;
       const ulonglong2* T = reinterpret_cast<const ulonglong2*>(tile[b]);
-#pragma unroll 2
+#pragma unroll(D == 2 ? kUnroll2 : kUnroll3)
       for (int s = 0; s < cnt; ++s) {
         const ulonglong2* Ts = T + s * SPF;
 #pragma unroll
