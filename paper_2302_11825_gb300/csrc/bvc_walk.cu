@@ -38,6 +38,14 @@ namespace bvc {
 #ifndef BVC_WALK_WARM
 #define BVC_WALK_WARM 1
 #endif
+// Internal nodes a lane visits per node iteration of the scheduler (measured
+// on GB300, cache + pointwise walks of the sphere / star workloads: 1 295 /
+// 34.1 ms, 2 286 / 32.6, 3 282 / 31.9, 4 276 / 31.8, 6 281 / 31.7, 8 282 /
+// 31.8, 16 297 / 31.6).
+#ifndef BVC_WALK_NODE_REPS
+#define BVC_WALK_NODE_REPS 4
+#endif
+constexpr int kNodeReps = BVC_WALK_NODE_REPS;
 constexpr int kWalkBlock = 128;
 constexpr int kStack = kTravStack;
 constexpr int64_t kChunk = 128;  // default walks per warp refill
@@ -314,9 +322,9 @@ __global__ void __launch_bounds__(kWalkBlock, REC == kRecAdj || (REC == kRecEnd 
       choice = nl > nn ? 1 : 0;
 
     if (choice == 0) {
-      // ---- up to two internal nodes: order the children, descend into the nearer
+      // ---- up to kNodeReps internal nodes: order the children, descend into the nearer
 #pragma unroll 1
-      for (int rep = 0; rep < 2; ++rep) {
+      for (int rep = 0; rep < kNodeReps; ++rep) {
         if (!(phase == kQuery && cur >= 0)) break;
         if (CNT) ++my_nodes;
         int32_t cl, cr;
