@@ -11,9 +11,11 @@
 // when f is non-zero, one source-term evaluation).  Each lane is always in
 // one of three states -- at an internal BVH node, at a leaf, or at the step
 // -- and on every iteration the warp runs only the most populated kind of
-// work (the step once at least half the working lanes wait for it), so the
-// lanes of a warp execute the same instructions instead of diverging along
-// different tree paths, and no lane waits for the slowest query in its warp.
+// work (the step once at least half the working lanes wait for it; a node
+// iteration descends up to kNodeReps internal nodes per lane, a leaf
+// iteration tests up to 1 (3D) or 2 (2D) leaves), so the lanes of a warp
+// execute the same instructions instead of diverging along different tree
+// paths, and no lane waits for the slowest query in its warp.
 // Per-walk results go to FP32 records; K3 reduces them in FP64 in a fixed
 // order, so results do not depend on scheduling.
 #include <cuda_fp16.h>
