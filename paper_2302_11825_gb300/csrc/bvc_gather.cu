@@ -1102,7 +1102,10 @@ constexpr int kMStride = 8 + 2 * kMG;  // floats per packed sample row
 // 128 threads, two points each (a block covers 256 points): every sample's
 // 32 coefficient pairs, broadcast from shared memory, feed both points, which
 // halves the shared-memory reads per FMA.  The 64 FP32 partial sums of a
-// thread live in registers; the FP64 running sums in shared memory
+// thread live in registers, two right-hand sides per packed FP32x2 register
+// pair (the coefficients of adjacent right-hand sides are adjacent in the
+// tile, so each fma.rn.f32x2 updates two sums: the same rounding as two
+// fmaf, half the issue slots); the FP64 running sums in shared memory
 // (dynamic, kMSum64 bytes), column per thread.
 constexpr int kMThreads = 128;
 constexpr int kMSum64 = 2 * kMG * kMThreads * 8;
@@ -1146,7 +1149,7 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
     pa[a] = (a < D && pl0 < n_pts) ? x[a * m + pt_off + pl0] : 1.0e4f + (float)a;
     pb[a] = (a < D && pl1 < n_pts) ? x[a * m + pt_off + pl1] : 1.0e4f + (float)a;
   }
-  float acc0[kMG], acc1[kMG];
+  f2 acc0[kMG / 2], acc1[kMG / 2];  // (right-hand side 2h, 2h + 1) of the two points
 #pragma unroll
   for (int q = 0; q < 2 * kMG; ++q) s64[q * kMThreads + tid] = 0.0;
   const int64_t nt = (n_rows + kMTile - 1) / kMTile;
@@ -1178,7 +1181,7 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
     const int cnt = (int)min64(kMTile, n_rows - it * kMTile);
     if (it % kMFlush == 0) {
 #pragma unroll
-      for (int q = 0; q < kMG; ++q) acc0[q] = acc1[q] = 0.0f;
+      for (int q = 0; q < kMG / 2; ++q) acc0[q] = acc1[q] = 0ull;
     }
     const float4* T = reinterpret_cast<const float4*>(tile[b]);
     for (int s = 0; s < cnt; ++s) {
@@ -1211,24 +1214,27 @@ __global__ void __launch_bounds__(kMThreads, 2) k_gather_multi(const float* __re
           kb2 = ir;
         }
       }
+      const f2 ka1p = pk(ka1, ka1), ka2p = pk(ka2, ka2), kb1p = pk(kb1, kb1), kb2p = pk(kb2, kb2);
+      const ulonglong2* R2 = reinterpret_cast<const ulonglong2*>(row);
 #pragma unroll
       for (int q = 0; q < kMG / 4; ++q) {
-        const float4 a4 = row[2 + q], b4 = row[2 + kMG / 4 + q];
-        acc0[4 * q + 0] = fmaf(b4.x, ka2, fmaf(a4.x, ka1, acc0[4 * q + 0]));
-        acc0[4 * q + 1] = fmaf(b4.y, ka2, fmaf(a4.y, ka1, acc0[4 * q + 1]));
-        acc0[4 * q + 2] = fmaf(b4.z, ka2, fmaf(a4.z, ka1, acc0[4 * q + 2]));
-        acc0[4 * q + 3] = fmaf(b4.w, ka2, fmaf(a4.w, ka1, acc0[4 * q + 3]));
-        acc1[4 * q + 0] = fmaf(b4.x, kb2, fmaf(a4.x, kb1, acc1[4 * q + 0]));
-        acc1[4 * q + 1] = fmaf(b4.y, kb2, fmaf(a4.y, kb1, acc1[4 * q + 1]));
-        acc1[4 * q + 2] = fmaf(b4.z, kb2, fmaf(a4.z, kb1, acc1[4 * q + 2]));
-        acc1[4 * q + 3] = fmaf(b4.w, kb2, fmaf(a4.w, kb1, acc1[4 * q + 3]));
+        const ulonglong2 a4 = R2[2 + q], b4 = R2[2 + kMG / 4 + q];
+        acc0[2 * q + 0] = fma2(b4.x, ka2p, fma2(a4.x, ka1p, acc0[2 * q + 0]));
+        acc0[2 * q + 1] = fma2(b4.y, ka2p, fma2(a4.y, ka1p, acc0[2 * q + 1]));
+        acc1[2 * q + 0] = fma2(b4.x, kb2p, fma2(a4.x, kb1p, acc1[2 * q + 0]));
+        acc1[2 * q + 1] = fma2(b4.y, kb2p, fma2(a4.y, kb1p, acc1[2 * q + 1]));
       }
     }
     if (it % kMFlush == kMFlush - 1 || it == nt - 1) {
 #pragma unroll
-      for (int q = 0; q < kMG; ++q) {
-        s64[q * kMThreads + tid] += (double)acc0[q];
-        s64[(kMG + q) * kMThreads + tid] += (double)acc1[q];
+      for (int q = 0; q < kMG / 2; ++q) {
+        float a_lo, a_hi, b_lo, b_hi;
+        upk(acc0[q], a_lo, a_hi);
+        upk(acc1[q], b_lo, b_hi);
+        s64[(2 * q) * kMThreads + tid] += (double)a_lo;
+        s64[(2 * q + 1) * kMThreads + tid] += (double)a_hi;
+        s64[(kMG + 2 * q) * kMThreads + tid] += (double)b_lo;
+        s64[(kMG + 2 * q + 1) * kMThreads + tid] += (double)b_hi;
       }
     }
     __syncthreads();
